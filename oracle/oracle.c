@@ -1,0 +1,938 @@
+/*
+ * FuseFSS reference oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-element-at-a-time CPU restatement of what the FuseFSS
+ * online hot path computes (arXiv 2606.09551, "FuseFSS: Efficient Secure LLM
+ * Inference with Function Secret Sharing").  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load this library.  The
+ * CUDA product path shares no code, header, table or constant generator with
+ * it; the two meet only through seeded inputs.
+ *
+ * Everything here follows the paper's definitions step by step, in the paper's
+ * order, with no blocking, fusion or reordering:
+ *   - AES-128 exactly as FIPS-197 defines it (byte-oriented SubBytes,
+ *     ShiftRows, MixColumns, AddRoundKey; S-box computed from its definition
+ *     as the GF(2^8) inverse followed by the affine map).
+ *   - The dealer PRG: AES-128 in counter mode keyed by the run seed.
+ *   - The DCF PRG: fixed-key tweaked Matyas-Meyer-Oseas, H(s,j) = AES_K(s^j)^s^j.
+ *   - The comparison DCF of Boyle, Chandran, Gilboa, Gupta, Ishai, Kumar and
+ *     Rathee (EUROCRYPT 2021), MSB first, over Z_2 (bit payload) and over
+ *     Z_{2^64}^p (vector payload).  The paper itself only says the backend is
+ *     "standard DPF/DCF-style" (Sec. 3.6 / App. I); this construction is the
+ *     reading adopted for it.
+ *   - Per-element compilation (App. F, Protocol "compile a scalar gate"):
+ *     translate, sort, pad to M = min(m+1, 2^k), mask rewrite (Lemma
+ *     "masked rewrite for unsigned comparison" and its low-bit variant, App. E),
+ *     fixed query list, lookup instance.
+ *   - The two-party online protocol (Sec. 5.3, App. C): open x^ = x + r_in,
+ *     packed comparison, vector interval lookup, masked-to-shares, Horner with
+ *     one Beaver multiplication per step (Sec. 3.4), with explicit message
+ *     buffers per party and byte counters.
+ *   - The plaintext operator evaluator (Def. "operator specification", Sec. 4.1).
+ *
+ * Parity pins live in tests/ (FIPS-197 known answers, brute-force DCF
+ * correctness, brute-force lemma checks, the App. N ReLU closed form, the
+ * plaintext evaluator against an independent numpy evaluation).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* AES-128, FIPS-197                                                          */
+/* ------------------------------------------------------------------------ */
+
+static uint8_t SBOX[256];
+static int sbox_ready = 0;
+
+/* multiplication in GF(2^8) modulo x^8 + x^4 + x^3 + x + 1 (FIPS-197 Sec. 4.2) */
+static uint8_t gf_mul(uint8_t a, uint8_t b)
+{
+    uint8_t r = 0;
+    while (b) {
+        if (b & 1) r ^= a;
+        a = (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1b : 0x00));
+        b >>= 1;
+    }
+    return r;
+}
+
+/* S-box by definition (FIPS-197 Sec. 5.1.1): multiplicative inverse in
+ * GF(2^8) (0 maps to 0), then the affine transformation with c = 0x63. */
+void or_init(void)
+{
+    if (sbox_ready) return;
+    for (int x = 0; x < 256; x++) {
+        uint8_t inv = 0;
+        if (x != 0) {
+            for (int y = 1; y < 256; y++)
+                if (gf_mul((uint8_t)x, (uint8_t)y) == 1) { inv = (uint8_t)y; break; }
+        }
+        uint8_t s = 0;
+        for (int i = 0; i < 8; i++) {
+            int bit = ((inv >> i) & 1) ^ ((inv >> ((i + 4) % 8)) & 1) ^ ((inv >> ((i + 5) % 8)) & 1)
+                    ^ ((inv >> ((i + 6) % 8)) & 1) ^ ((inv >> ((i + 7) % 8)) & 1) ^ ((0x63 >> i) & 1);
+            s |= (uint8_t)(bit << i);
+        }
+        SBOX[x] = s;
+    }
+    sbox_ready = 1;
+}
+
+uint8_t or_sbox(uint8_t x) { return SBOX[x]; }
+
+/* Key expansion (FIPS-197 Sec. 5.2): 44 words w[0..43], 11 round keys. */
+typedef struct { uint8_t rk[11][16]; } or_aes_key;
+
+static void aes_expand(const uint8_t key[16], or_aes_key *ks)
+{
+    uint8_t w[44][4];
+    uint8_t rcon = 0x01;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) w[i][j] = key[4 * i + j];
+    for (int i = 4; i < 44; i++) {
+        uint8_t temp[4];
+        memcpy(temp, w[i - 1], 4);
+        if (i % 4 == 0) {
+            uint8_t t0 = temp[0];                 /* RotWord */
+            temp[0] = temp[1]; temp[1] = temp[2]; temp[2] = temp[3]; temp[3] = t0;
+            for (int j = 0; j < 4; j++) temp[j] = SBOX[temp[j]];   /* SubWord */
+            temp[0] ^= rcon;
+            rcon = gf_mul(rcon, 0x02);
+        }
+        for (int j = 0; j < 4; j++) w[i][j] = w[i - 4][j] ^ temp[j];
+    }
+    for (int r = 0; r < 11; r++)
+        for (int c = 0; c < 4; c++)
+            for (int j = 0; j < 4; j++) ks->rk[r][4 * c + j] = w[4 * r + c][j];
+}
+
+/* The state is s[row][col] with in[row + 4*col] (FIPS-197 Sec. 3.4). */
+static void aes_encrypt(const or_aes_key *ks, const uint8_t in[16], uint8_t out[16])
+{
+    uint8_t s[4][4];
+    for (int c = 0; c < 4; c++)
+        for (int r = 0; r < 4; r++) s[r][c] = in[r + 4 * c] ^ ks->rk[0][r + 4 * c];
+    for (int round = 1; round <= 10; round++) {
+        /* SubBytes */
+        for (int r = 0; r < 4; r++)
+            for (int c = 0; c < 4; c++) s[r][c] = SBOX[s[r][c]];
+        /* ShiftRows: row r rotates left by r */
+        for (int r = 1; r < 4; r++) {
+            uint8_t tmp[4];
+            for (int c = 0; c < 4; c++) tmp[c] = s[r][(c + r) % 4];
+            for (int c = 0; c < 4; c++) s[r][c] = tmp[c];
+        }
+        /* MixColumns (omitted in the final round) */
+        if (round != 10) {
+            for (int c = 0; c < 4; c++) {
+                uint8_t a0 = s[0][c], a1 = s[1][c], a2 = s[2][c], a3 = s[3][c];
+                s[0][c] = gf_mul(a0, 2) ^ gf_mul(a1, 3) ^ a2 ^ a3;
+                s[1][c] = a0 ^ gf_mul(a1, 2) ^ gf_mul(a2, 3) ^ a3;
+                s[2][c] = a0 ^ a1 ^ gf_mul(a2, 2) ^ gf_mul(a3, 3);
+                s[3][c] = gf_mul(a0, 3) ^ a1 ^ a2 ^ gf_mul(a3, 2);
+            }
+        }
+        /* AddRoundKey */
+        for (int c = 0; c < 4; c++)
+            for (int r = 0; r < 4; r++) s[r][c] ^= ks->rk[round][r + 4 * c];
+    }
+    for (int c = 0; c < 4; c++)
+        for (int r = 0; r < 4; r++) out[r + 4 * c] = s[r][c];
+}
+
+void or_aes128(const uint8_t key[16], const uint8_t in[16], uint8_t out[16])
+{
+    or_aes_key ks;
+    aes_expand(key, &ks);
+    aes_encrypt(&ks, in, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Little-endian helpers                                                     */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t le64(const uint8_t *b)
+{
+    uint64_t v = 0;
+    for (int i = 7; i >= 0; i--) v = (v << 8) | b[i];
+    return v;
+}
+
+static void put_le32(uint8_t *b, uint32_t v)
+{
+    for (int i = 0; i < 4; i++) b[i] = (uint8_t)(v >> (8 * i));
+}
+
+/* ------------------------------------------------------------------------ */
+/* DCF PRG: fixed-key tweaked MMO, H(s, j) = AES_K(s ^ j) ^ s ^ j, where j   */
+/* is XORed into the low 32 bits (bytes 0..3, little endian).  K is the     */
+/* public constant "FuseFSS-DCF-AES!".                                        */
+/* ------------------------------------------------------------------------ */
+
+static or_aes_key DCF_KEY;
+static int dcf_key_ready = 0;
+
+static void dcf_key_init(void)
+{
+    if (dcf_key_ready) return;
+    or_init();
+    const char *k = "FuseFSS-DCF-AES!";
+    aes_expand((const uint8_t *)k, &DCF_KEY);
+    dcf_key_ready = 1;
+}
+
+void or_setup(void) { or_init(); dcf_key_init(); }
+
+static void mmo(const uint8_t s[16], uint32_t j, uint8_t out[16])
+{
+    uint8_t in[16], jb[4];
+    memcpy(in, s, 16);
+    put_le32(jb, j);
+    for (int i = 0; i < 4; i++) in[i] ^= jb[i];
+    aes_encrypt(&DCF_KEY, in, out);
+    for (int i = 0; i < 16; i++) out[i] ^= in[i];
+}
+
+void or_mmo(const uint8_t s[16], uint32_t j, uint8_t out[16]) { mmo(s, j, out); }
+
+#define MAXK 32     /* view width k <= 32 */
+#define MAXP 4      /* payload length p = r (d + 1) <= 4 */
+
+static int nblocks_for(int p) { return (8 * p + 15) / 16; }   /* V = ceil(8p/16) */
+
+/* Expansion of one child sigma of seed s: the next seed (low two bits
+ * cleared), its control bit t (bit 0) and, for the bit payload, v (bit 1). */
+static void expand_child(const uint8_t s[16], int sigma, uint8_t seed[16], int *t, int *vbit)
+{
+    uint8_t blk[16];
+    mmo(s, (uint32_t)sigma, blk);
+    *t = blk[0] & 1;
+    *vbit = (blk[0] >> 1) & 1;
+    memcpy(seed, blk, 16);
+    seed[0] &= (uint8_t)~3u;
+}
+
+/* Vector payload of child sigma: V blocks H(s, 2 + sigma*V + q), q < V, read
+ * as p little-endian uint64 values. */
+static void convert_child(const uint8_t s[16], int sigma, int p, uint64_t *v)
+{
+    int V = nblocks_for(p);
+    uint8_t buf[16 * 4];
+    for (int q = 0; q < V; q++) mmo(s, (uint32_t)(2 + sigma * V + q), buf + 16 * q);
+    for (int i = 0; i < p; i++) v[i] = le64(buf + 8 * i);
+}
+
+/* Conversion of a leaf seed: H(s, 2 + q), q < V, read as p uint64. */
+static void convert_leaf(const uint8_t s[16], int p, uint64_t *v)
+{
+    int V = nblocks_for(p);
+    uint8_t buf[16 * 4];
+    for (int q = 0; q < V; q++) mmo(s, (uint32_t)(2 + q), buf + 16 * q);
+    for (int i = 0; i < p; i++) v[i] = le64(buf + 8 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* DCF (BCG+21), f(u) = beta * 1[u < alpha] on k-bit u, MSB first.          */
+/* p == 0 selects the bit payload over Z_2 (beta = 1); p >= 1 selects the    */
+/* vector payload over Z_{2^64}^p.                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int k, p;
+    uint8_t root[16];
+    uint8_t scw[MAXK][16];
+    uint8_t tcw_l[MAXK], tcw_r[MAXK];
+    uint8_t vcw_bit[MAXK + 1];            /* bit payload: per level, [k] = leaf */
+    uint64_t vcw[MAXK + 1][MAXP];         /* vector payload: per level, [k] = leaf */
+} or_dcf_key;
+
+/* The packed-comparison keys carry only bit payloads; a smaller record keeps
+ * the per-element material small. */
+typedef struct {
+    int k;
+    uint8_t root[16];
+    uint8_t scw[MAXK][16];
+    uint8_t tcw_l[MAXK], tcw_r[MAXK];
+    uint8_t vcw_bit[MAXK + 1];
+} or_bit_key;
+
+static void bit_key_from(const or_dcf_key *src, or_bit_key *dst)
+{
+    dst->k = src->k;
+    memcpy(dst->root, src->root, 16);
+    memcpy(dst->scw, src->scw, sizeof(dst->scw));
+    memcpy(dst->tcw_l, src->tcw_l, MAXK);
+    memcpy(dst->tcw_r, src->tcw_r, MAXK);
+    memcpy(dst->vcw_bit, src->vcw_bit, MAXK + 1);
+}
+
+static void bit_key_to(const or_bit_key *src, or_dcf_key *dst)
+{
+    memset(dst, 0, sizeof(*dst));
+    dst->k = src->k;
+    dst->p = 0;
+    memcpy(dst->root, src->root, 16);
+    memcpy(dst->scw, src->scw, sizeof(src->scw));
+    memcpy(dst->tcw_l, src->tcw_l, MAXK);
+    memcpy(dst->tcw_r, src->tcw_r, MAXK);
+    memcpy(dst->vcw_bit, src->vcw_bit, MAXK + 1);
+}
+
+void or_dcf_gen(int k, uint64_t alpha, int p, const uint64_t *beta,
+                const uint8_t root0[16], const uint8_t root1[16],
+                or_dcf_key *k0, or_dcf_key *k1)
+{
+    uint8_t s[2][16];
+    int t[2] = {0, 1};
+    uint64_t va[MAXP] = {0};
+    int va_bit = 0;
+    memset(k0, 0, sizeof(*k0));
+    memset(k1, 0, sizeof(*k1));
+    k0->k = k1->k = k;
+    k0->p = k1->p = p;
+    memcpy(s[0], root0, 16);
+    memcpy(s[1], root1, 16);
+    memcpy(k0->root, root0, 16);
+    memcpy(k1->root, root1, 16);
+
+    for (int i = 0; i < k; i++) {
+        int a = (int)((alpha >> (k - 1 - i)) & 1);
+        uint8_t cs[2][2][16];       /* [party][child] seed */
+        int ct[2][2], cvb[2][2];    /* control bit, bit payload */
+        uint64_t cv[2][2][MAXP];    /* vector payload */
+        for (int b = 0; b < 2; b++)
+            for (int sg = 0; sg < 2; sg++) {
+                expand_child(s[b], sg, cs[b][sg], &ct[b][sg], &cvb[b][sg]);
+                if (p > 0) convert_child(s[b], sg, p, cv[b][sg]);
+            }
+        int keep = a, lose = 1 - a;
+        uint8_t scw[16];
+        for (int j = 0; j < 16; j++) scw[j] = cs[0][lose][j] ^ cs[1][lose][j];
+        int tcw_l = ct[0][0] ^ ct[1][0] ^ a ^ 1;
+        int tcw_r = ct[0][1] ^ ct[1][1] ^ a;
+
+        if (p == 0) {
+            /* over Z_2 every sign is +1 and subtraction is XOR */
+            int vcw = cvb[1][lose] ^ cvb[0][lose] ^ va_bit;
+            if (lose == 0) vcw ^= 1;          /* beta = 1 */
+            va_bit = va_bit ^ cvb[1][keep] ^ cvb[0][keep] ^ vcw;
+            k0->vcw_bit[i] = k1->vcw_bit[i] = (uint8_t)vcw;
+        } else {
+            int neg = t[1];                   /* (-1)^{t_1} */
+            for (int q = 0; q < p; q++) {
+                uint64_t d = cv[1][lose][q] - cv[0][lose][q] - va[q];
+                if (lose == 0) d += beta[q];
+                uint64_t vcw = neg ? (uint64_t)0 - d : d;
+                va[q] = va[q] - cv[1][keep][q] + cv[0][keep][q] + (neg ? (uint64_t)0 - vcw : vcw);
+                k0->vcw[i][q] = k1->vcw[i][q] = vcw;
+            }
+        }
+        memcpy(k0->scw[i], scw, 16);
+        memcpy(k1->scw[i], scw, 16);
+        k0->tcw_l[i] = k1->tcw_l[i] = (uint8_t)tcw_l;
+        k0->tcw_r[i] = k1->tcw_r[i] = (uint8_t)tcw_r;
+
+        int tcw_keep = keep ? tcw_r : tcw_l;
+        for (int b = 0; b < 2; b++) {
+            int t_old = t[b];
+            for (int j = 0; j < 16; j++) s[b][j] = cs[b][keep][j] ^ (t_old ? scw[j] : 0);
+            t[b] = ct[b][keep] ^ (t_old & tcw_keep);
+        }
+    }
+    /* final correction word CW_{k+1} */
+    if (p == 0) {
+        int c0 = (s[0][0] >> 2) & 1, c1 = (s[1][0] >> 2) & 1;
+        int cw = c1 ^ c0 ^ va_bit;
+        k0->vcw_bit[k] = k1->vcw_bit[k] = (uint8_t)cw;
+    } else {
+        uint64_t l0[MAXP], l1[MAXP];
+        convert_leaf(s[0], p, l0);
+        convert_leaf(s[1], p, l1);
+        for (int q = 0; q < p; q++) {
+            uint64_t d = l1[q] - l0[q] - va[q];
+            uint64_t cw = t[1] ? (uint64_t)0 - d : d;
+            k0->vcw[k][q] = k1->vcw[k][q] = cw;
+        }
+    }
+}
+
+/* Eval_b on a k-bit public input u.  Bit payload: returns the share bit in
+ * *out_bit.  Vector payload: writes p uint64 shares to out. */
+void or_dcf_eval(int b, const or_dcf_key *key, uint64_t u, int *out_bit, uint64_t *out)
+{
+    int k = key->k, p = key->p;
+    uint8_t s[16];
+    int t = b;
+    int vb = 0;
+    uint64_t v[MAXP] = {0};
+    memcpy(s, key->root, 16);
+    for (int i = 0; i < k; i++) {
+        int x = (int)((u >> (k - 1 - i)) & 1);
+        uint8_t seed[16];
+        int tc, vbit;
+        uint64_t cv[MAXP];
+        expand_child(s, x, seed, &tc, &vbit);
+        if (p > 0) convert_child(s, x, p, cv);
+        int t_old = t;
+        if (t_old) {
+            for (int j = 0; j < 16; j++) seed[j] ^= key->scw[i][j];
+            tc ^= x ? key->tcw_r[i] : key->tcw_l[i];
+        }
+        if (p == 0) {
+            vb ^= vbit ^ (t_old & key->vcw_bit[i]);
+        } else {
+            for (int q = 0; q < p; q++) {
+                uint64_t add = cv[q] + (t_old ? key->vcw[i][q] : 0);
+                v[q] += b ? (uint64_t)0 - add : add;
+            }
+        }
+        memcpy(s, seed, 16);
+        t = tc;
+    }
+    if (p == 0) {
+        vb ^= ((s[0] >> 2) & 1) ^ (t & key->vcw_bit[k]);
+        *out_bit = vb;
+    } else {
+        uint64_t leaf[MAXP];
+        convert_leaf(s, p, leaf);
+        for (int q = 0; q < p; q++) {
+            uint64_t add = leaf[q] + (t ? key->vcw[k][q] : 0);
+            v[q] += b ? (uint64_t)0 - add : add;
+        }
+        for (int q = 0; q < p; q++) out[q] = v[q];
+    }
+}
+
+size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
+
+/* ------------------------------------------------------------------------ */
+/* Operator specification (Def. "operator specification", Sec. 4.1)        */
+/* ------------------------------------------------------------------------ */
+
+#define MAXM 16     /* intervals m <= 16, so at most 16 lookup keys */
+#define MAXPRED 32  /* Boolean outputs */
+#define MAXQ 32     /* packed-comparison queries (one uint32 of atoms) */
+
+typedef struct {
+    uint32_t f;        /* view width */
+    uint64_t c;        /* public shift */
+    uint64_t gamma;    /* threshold in [0, 2^f] */
+    uint32_t negate;
+} or_pred;
+
+typedef struct {
+    /* descriptor */
+    uint32_t k, m, d, r;
+    uint64_t alpha[MAXM + 1];
+    uint64_t coeff[MAXM * MAXP];      /* [piece][out][power], low power first */
+    uint32_t n_out_bits;              /* number of Boolean outputs */
+    or_pred out_pred[MAXPRED];        /* Boolean outputs, each one primitive predicate */
+    /* derived public shape (mask independent) */
+    uint32_t p;                       /* r (d + 1) */
+    uint32_t M;                       /* min(m + 1, 2^k) */
+    uint32_t n_prim;                  /* distinct non-sentinel primitive predicates */
+    or_pred prim[MAXPRED];            /* their (f, c, gamma); negate unused */
+    int32_t out_prim[MAXPRED];        /* per output: index into prim, or -1 for a sentinel */
+    uint32_t out_const[MAXPRED];      /* per output: the sentinel value (when out_prim < 0) */
+    uint32_t T;                       /* query count */
+    uint32_t q_f[MAXQ];               /* per query: view width */
+    uint64_t q_c[MAXQ];               /* per query: view shift */
+    int32_t q_prim[MAXQ];             /* per query: prim index, or -1 for the 1[view < r_f] atom */
+    int32_t prim_qtheta[MAXPRED];     /* per prim: its theta query */
+    int32_t prim_qr[MAXPRED];         /* per prim: the r-atom query of its view */
+} or_spec;
+
+static uint64_t pow2(uint32_t f) { return (uint64_t)1 << f; }
+
+/* Build the public shape.  Boolean outputs: when partition_bits is set the
+ * first m-1 outputs are C_{alpha_i}(x) = 1[x < alpha_i] (i = 1..m-1); the
+ * extra predicates follow.  Query list ("fixed descriptor order", App. F step
+ * 4): views in order of first appearance; within a view the atom 1[v < r_f]
+ * first, then one theta atom per distinct non-sentinel predicate in output
+ * order.  Only spec-level duplicates (same f, c, gamma) are merged. */
+int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
+                  const uint64_t *alpha, const uint64_t *coeff, uint32_t partition_bits,
+                  uint32_t n_extra, const uint32_t *ef, const uint64_t *ec,
+                  const uint64_t *egamma, const uint32_t *eneg)
+{
+    memset(sp, 0, sizeof(*sp));
+    if (k < 1 || k > MAXK || m < 1 || m > MAXM) return -1;
+    if ((uint64_t)m > pow2(k)) return -1;
+    if (r < 1 || r * (d + 1) > MAXP) return -1;
+    sp->k = k; sp->m = m; sp->d = d; sp->r = r;
+    if (alpha[0] != 0 || alpha[m] != pow2(k)) return -1;
+    for (uint32_t i = 0; i < m; i++) if (!(alpha[i] < alpha[i + 1])) return -1;
+    memcpy(sp->alpha, alpha, sizeof(uint64_t) * (m + 1));
+    memcpy(sp->coeff, coeff, sizeof(uint64_t) * m * r * (d + 1));
+    sp->p = r * (d + 1);
+    /* M = min(m+1, 2^k) (App. F); a single-interval spec has an
+     * interval-independent payload and omits the lookup call (App. O). */
+    if (m == 1) sp->M = 1;
+    else sp->M = (uint64_t)(m + 1) < pow2(k) ? m + 1 : (uint32_t)pow2(k);
+
+    uint32_t nb = 0;
+    if (partition_bits)
+        for (uint32_t i = 1; i < m; i++) {
+            if (nb >= MAXPRED) return -1;
+            sp->out_pred[nb].f = k; sp->out_pred[nb].c = 0;
+            sp->out_pred[nb].gamma = alpha[i]; sp->out_pred[nb].negate = 0;
+            nb++;
+        }
+    for (uint32_t i = 0; i < n_extra; i++) {
+        if (nb >= MAXPRED) return -1;
+        if (ef[i] < 1 || ef[i] > k) return -1;
+        if (ec[i] >= pow2(ef[i]) || egamma[i] > pow2(ef[i])) return -1;
+        sp->out_pred[nb].f = ef[i]; sp->out_pred[nb].c = ec[i];
+        sp->out_pred[nb].gamma = egamma[i]; sp->out_pred[nb].negate = eneg[i] & 1;
+        nb++;
+    }
+    sp->n_out_bits = nb;
+
+    /* distinct non-sentinel primitive predicates, in output order */
+    for (uint32_t o = 0; o < nb; o++) {
+        or_pred *op = &sp->out_pred[o];
+        if (op->gamma == 0) { sp->out_prim[o] = -1; sp->out_const[o] = 0; continue; }
+        if (op->gamma == pow2(op->f)) { sp->out_prim[o] = -1; sp->out_const[o] = 1; continue; }
+        int found = -1;
+        for (uint32_t j = 0; j < sp->n_prim; j++)
+            if (sp->prim[j].f == op->f && sp->prim[j].c == op->c && sp->prim[j].gamma == op->gamma) found = (int)j;
+        if (found < 0) {
+            found = (int)sp->n_prim;
+            sp->prim[sp->n_prim] = *op;
+            sp->prim[sp->n_prim].negate = 0;
+            sp->n_prim++;
+        }
+        sp->out_prim[o] = found;
+    }
+
+    /* views in order of first appearance */
+    uint32_t nviews = 0, vf[MAXPRED];
+    uint64_t vc[MAXPRED];
+    for (uint32_t j = 0; j < sp->n_prim; j++) {
+        int seen = 0;
+        for (uint32_t v = 0; v < nviews; v++) if (vf[v] == sp->prim[j].f && vc[v] == sp->prim[j].c) seen = 1;
+        if (!seen) { vf[nviews] = sp->prim[j].f; vc[nviews] = sp->prim[j].c; nviews++; }
+    }
+    uint32_t T = 0;
+    for (uint32_t v = 0; v < nviews; v++) {
+        if (T >= MAXQ) return -1;
+        int qr = (int)T;
+        sp->q_f[T] = vf[v]; sp->q_c[T] = vc[v]; sp->q_prim[T] = -1; T++;
+        for (uint32_t j = 0; j < sp->n_prim; j++) {
+            if (sp->prim[j].f != vf[v] || sp->prim[j].c != vc[v]) continue;
+            if (T >= MAXQ) return -1;
+            sp->q_f[T] = vf[v]; sp->q_c[T] = vc[v]; sp->q_prim[T] = (int)j;
+            sp->prim_qtheta[j] = (int)T;
+            sp->prim_qr[j] = qr;
+            T++;
+        }
+    }
+    sp->T = T;
+    return 0;
+}
+
+size_t or_spec_size(void) { return sizeof(or_spec); }
+
+void or_spec_shape(const or_spec *sp, uint32_t *out)
+{
+    out[0] = sp->T; out[1] = sp->M; out[2] = sp->p; out[3] = sp->d * sp->r;
+    out[4] = sp->n_out_bits; out[5] = sp->n_prim;
+}
+
+void or_spec_query(const or_spec *sp, uint32_t t, uint32_t *f, uint64_t *c, int32_t *prim)
+{
+    *f = sp->q_f[t]; *c = sp->q_c[t]; *prim = sp->q_prim[t];
+}
+
+/* public view_{f,c}(u) = ((u mod 2^f) + c) mod 2^f  (Sec. 3.6) */
+static uint64_t view(uint64_t u, uint32_t f, uint64_t c)
+{
+    uint64_t mask = pow2(f) - 1;
+    return ((u & mask) + c) & mask;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plaintext evaluator: F(x) = (P_i(x), B(x)) for the unique i with          */
+/* (x mod 2^k) in [alpha_i, alpha_{i+1}); Horner over Z_{2^64} on the full   */
+/* 64-bit x.                                                                 */
+/* ------------------------------------------------------------------------ */
+
+void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y, uint32_t *z)
+{
+    for (uint64_t e = 0; e < n; e++) {
+        uint64_t xk = x[e] & (pow2(sp->k) - 1);
+        uint32_t piece = 0;
+        for (uint32_t i = 0; i < sp->m; i++)
+            if (sp->alpha[i] <= xk && xk < sp->alpha[i + 1]) piece = i;
+        for (uint32_t o = 0; o < sp->r; o++) {
+            const uint64_t *c = &sp->coeff[(piece * sp->r + o) * (sp->d + 1)];
+            uint64_t acc = c[sp->d];
+            for (int j = (int)sp->d - 1; j >= 0; j--) acc = acc * x[e] + c[j];
+            y[e * sp->r + o] = acc;
+        }
+        uint32_t bits = 0;
+        for (uint32_t o = 0; o < sp->n_out_bits; o++) {
+            const or_pred *op = &sp->out_pred[o];
+            uint32_t v = view(x[e], op->f, op->c) < op->gamma ? 1u : 0u;
+            bits |= (v ^ op->negate) << o;
+        }
+        z[e] = bits;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dealer PRG: AES-128-CTR keyed by the run seed.  Counter block (four LE   */
+/* u32 words): (draw index, element low 32, element high 32, call id).      */
+/* Ring values are the low 64 bits of the block; bits are bit 0.            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { or_aes_key ks; uint32_t call_id; } or_prg;
+
+static void prg_block(const or_prg *g, uint32_t draw, uint64_t elem, uint8_t out[16])
+{
+    uint8_t ctr[16];
+    put_le32(ctr + 0, draw);
+    put_le32(ctr + 4, (uint32_t)elem);
+    put_le32(ctr + 8, (uint32_t)(elem >> 32));
+    put_le32(ctr + 12, g->call_id);
+    aes_encrypt(&g->ks, ctr, out);
+}
+
+static uint64_t prg_u64(const or_prg *g, uint32_t draw, uint64_t elem)
+{
+    uint8_t b[16];
+    prg_block(g, draw, elem, b);
+    return le64(b);
+}
+
+/* Draw index layout per element (public, spec-determined):
+ *   0 r_in, 1 party-0 share of r_in, 2 party-0 share of x, 3 party-0 carry
+ *   share word (low 32 bits), 4..4+p-1 party-0 shares of v_{M-1},
+ *   then 2 root seeds per DCF key (queries in order, then lookup keys
+ *   j = 1..M-1), then 5 draws per Beaver triple (a, b, a_0, b_0, c_0). */
+#define DRAW_RIN 0
+#define DRAW_RSH 1
+#define DRAW_XSH 2
+#define DRAW_CARRY 3
+#define DRAW_VLAST 4
+
+/* ------------------------------------------------------------------------ */
+/* Per-element preprocessing material (one party)                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t r_share;
+    uint32_t carry_share;
+    uint64_t vlast_share[MAXP];
+    or_bit_key qkey[MAXQ];            /* packed-comparison keys, query order */
+    or_dcf_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
+    uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
+} or_elem_keys;
+
+size_t or_elem_keys_size(void) { return sizeof(or_elem_keys); }
+
+/* Lookup instance for one element: App. F step (1).  Writes B[0..M], ord[0..M-1]. */
+static void compile_lookup(const or_spec *sp, uint64_t r_in, uint64_t *B, uint32_t *ord)
+{
+    uint32_t m = sp->m;
+    uint64_t N = pow2(sp->k);
+    uint64_t rk = r_in & (N - 1);          /* the k-bit view of the mask */
+    uint64_t s[MAXM];
+    uint32_t pi[MAXM];
+    for (uint32_t i = 0; i < m; i++) { s[i] = (sp->alpha[i] + rk) % N; pi[i] = i; }
+    /* sort the translated starts (insertion sort; they are distinct) */
+    for (uint32_t i = 1; i < m; i++) {
+        uint32_t cur = pi[i];
+        int j = (int)i - 1;
+        while (j >= 0 && s[pi[j]] > s[cur]) { pi[j + 1] = pi[j]; j--; }
+        pi[j + 1] = cur;
+    }
+    uint64_t beta[MAXM] = {0};
+    for (uint32_t j = 0; j < m; j++) beta[j] = s[pi[j]];
+    uint32_t nb = 0, no = 0;
+    if (beta[0] == 0) {
+        B[nb++] = 0;
+        for (uint32_t j = 1; j < m; j++) B[nb++] = beta[j];
+        B[nb++] = N;
+        for (uint32_t j = 0; j < m; j++) ord[no++] = pi[j];
+        if ((uint64_t)m < N) {
+            uint32_t jstar = 0;
+            while (!(B[jstar + 1] - B[jstar] >= 2)) jstar++;
+            uint64_t delta = B[jstar] + 1;
+            for (uint32_t j = nb; j > jstar + 1; j--) B[j] = B[j - 1];
+            B[jstar + 1] = delta; nb++;
+            for (uint32_t j = no; j > jstar + 1; j--) ord[j] = ord[j - 1];
+            ord[jstar + 1] = ord[jstar]; no++;
+        }
+    } else {
+        B[nb++] = 0;
+        for (uint32_t j = 0; j < m; j++) B[nb++] = beta[j];
+        B[nb++] = N;
+        ord[no++] = pi[m - 1];
+        for (uint32_t j = 0; j < m; j++) ord[no++] = pi[j];
+    }
+    (void)nb; (void)no;
+}
+
+void or_compile_lookup(const or_spec *sp, uint64_t r_in, uint64_t *B, uint32_t *ord)
+{
+    compile_lookup(sp, r_in, B, ord);
+}
+
+/* Payload of piece i: index o*(d+1)+j = coefficient of x^j of output o. */
+static void payload(const or_spec *sp, uint32_t piece, uint64_t *v)
+{
+    for (uint32_t q = 0; q < sp->p; q++) v[q] = sp->coeff[piece * sp->p + q];
+}
+
+/* Dealer for elements [e0, e0+n): masks, carries, keys, triples, input shares
+ * (Sec. 5.2).  x_plain may be NULL (then x shares are not written). */
+void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
+               uint64_t e0, uint64_t n, const uint64_t *x_plain,
+               or_elem_keys *k0, or_elem_keys *k1, uint64_t *x0, uint64_t *x1,
+               const uint64_t *r_override)
+{
+    or_prg g;
+    aes_expand(seed, &g.ks);
+    g.call_id = call_id;
+    uint32_t p = sp->p, T = sp->T, M = sp->M;
+    uint32_t base_roots = DRAW_VLAST + p;
+    uint32_t base_triples = base_roots + 2 * (T + M - 1);
+
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t e = e0 + i;
+        or_elem_keys *K0 = &k0[i], *K1 = &k1[i];
+        memset(K0, 0, sizeof(*K0));
+        memset(K1, 0, sizeof(*K1));
+        /* r_override (tests only) replaces the drawn mask to cover every r */
+        uint64_t r_in = r_override ? r_override[i] : prg_u64(&g, DRAW_RIN, e);
+        uint64_t r0 = prg_u64(&g, DRAW_RSH, e);
+        K0->r_share = r0;
+        K1->r_share = r_in - r0;
+        if (x_plain) {
+            uint64_t xs = prg_u64(&g, DRAW_XSH, e);
+            x0[i] = xs;
+            x1[i] = x_plain[i] - xs;
+        }
+
+        /* mask rewrite: theta = (r_f + gamma) mod 2^f, w = 1[r_f + gamma >= 2^f] */
+        uint32_t carries = 0;
+        uint64_t theta[MAXPRED];
+        for (uint32_t j = 0; j < sp->n_prim; j++) {
+            uint64_t Nf = pow2(sp->prim[j].f);
+            uint64_t rf = r_in & (Nf - 1);
+            theta[j] = (rf + sp->prim[j].gamma) % Nf;
+            if (rf + sp->prim[j].gamma >= Nf) carries |= 1u << j;
+        }
+        uint8_t cb[16];
+        prg_block(&g, DRAW_CARRY, e, cb);
+        uint32_t cs0 = (uint32_t)le64(cb);
+        K0->carry_share = cs0;
+        K1->carry_share = cs0 ^ carries;
+
+        /* packed comparison keys, query order */
+        for (uint32_t t = 0; t < T; t++) {
+            uint64_t Nf = pow2(sp->q_f[t]);
+            uint64_t a = sp->q_prim[t] < 0 ? (r_in & (Nf - 1)) : theta[sp->q_prim[t]];
+            uint8_t s0[16], s1[16];
+            or_dcf_key g0, g1;
+            prg_block(&g, base_roots + 2 * t, e, s0);
+            prg_block(&g, base_roots + 2 * t + 1, e, s1);
+            or_dcf_gen((int)sp->q_f[t], a, 0, NULL, s0, s1, &g0, &g1);
+            bit_key_from(&g0, &K0->qkey[t]);
+            bit_key_from(&g1, &K1->qkey[t]);
+        }
+
+        /* lookup: M-1 vector DCFs, telescoped:
+         * LUT(u) = v_{M-1} + sum_{j=1}^{M-1} 1[u < B_j] (v_{j-1} - v_j) */
+        uint64_t B[MAXM + 2];
+        uint32_t ord[MAXM + 1];
+        if (M == 1) { B[0] = 0; B[1] = pow2(sp->k); ord[0] = 0; }
+        else compile_lookup(sp, r_in, B, ord);
+        uint64_t v[MAXM + 1][MAXP];
+        for (uint32_t j = 0; j < M; j++) payload(sp, ord[j], v[j]);
+        for (uint32_t j = 1; j < M; j++) {
+            uint64_t beta[MAXP];
+            for (uint32_t q = 0; q < p; q++) beta[q] = v[j - 1][q] - v[j][q];
+            uint8_t s0[16], s1[16];
+            uint32_t di = base_roots + 2 * (T + j - 1);
+            prg_block(&g, di, e, s0);
+            prg_block(&g, di + 1, e, s1);
+            or_dcf_gen((int)sp->k, B[j], (int)p, beta, s0, s1, &K0->lkey[j - 1], &K1->lkey[j - 1]);
+        }
+        for (uint32_t q = 0; q < p; q++) {
+            uint64_t sh = prg_u64(&g, DRAW_VLAST + q, e);
+            K0->vlast_share[q] = sh;
+            K1->vlast_share[q] = v[M - 1][q] - sh;
+        }
+
+        /* Beaver triples (a, b, c = ab) */
+        for (uint32_t mi = 0; mi < sp->d * sp->r; mi++) {
+            uint32_t di = base_triples + 5 * mi;
+            uint64_t a = prg_u64(&g, di + 0, e);
+            uint64_t b = prg_u64(&g, di + 1, e);
+            uint64_t a0 = prg_u64(&g, di + 2, e);
+            uint64_t b0 = prg_u64(&g, di + 3, e);
+            uint64_t c0 = prg_u64(&g, di + 4, e);
+            K0->ta[mi] = a0; K1->ta[mi] = a - a0;
+            K0->tb[mi] = b0; K1->tb[mi] = b - b0;
+            K0->tc[mi] = c0; K1->tc[mi] = a * b - c0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Online protocol (Sec. 5.3), one party's local steps.  Parties talk only  */
+/* through the message buffers passed between the calls below.              */
+/* ------------------------------------------------------------------------ */
+
+/* Packed comparison, Eval_b: XOR shares of the T atoms (bit t = query t). */
+static uint32_t party_pred_atoms(int b, const or_spec *sp, const or_elem_keys *K, uint64_t xhat)
+{
+    uint32_t atoms = 0;
+    for (uint32_t t = 0; t < sp->T; t++) {
+        uint64_t u = view(xhat, sp->q_f[t], sp->q_c[t]);
+        int bit;
+        or_dcf_key key;
+        bit_key_to(&K->qkey[t], &key);
+        or_dcf_eval(b, &key, u, &bit, NULL);
+        atoms |= (uint32_t)bit << t;
+    }
+    return atoms;
+}
+
+/* Local rewrite: share of C(x) = atom_theta ^ atom_r ^ w, then NOT by party 0. */
+static uint32_t party_out_bits(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms)
+{
+    uint32_t z = 0;
+    for (uint32_t o = 0; o < sp->n_out_bits; o++) {
+        uint32_t bit;
+        int j = sp->out_prim[o];
+        if (j < 0) {
+            bit = b == 0 ? sp->out_const[o] : 0;
+        } else {
+            bit = ((atoms >> sp->prim_qtheta[j]) & 1) ^ ((atoms >> sp->prim_qr[j]) & 1)
+                ^ ((K->carry_share >> j) & 1);
+        }
+        if (b == 0) bit ^= sp->out_pred[o].negate;
+        z |= bit << o;
+    }
+    return z;
+}
+
+/* Vector interval lookup, Eval_b: additive shares of v_{i*}. */
+static void party_lookup(int b, const or_spec *sp, const or_elem_keys *K, uint64_t xhat, uint64_t *pay)
+{
+    uint64_t u = view(xhat, sp->k, 0);
+    for (uint32_t q = 0; q < sp->p; q++) pay[q] = K->vlast_share[q];
+    for (uint32_t j = 1; j < sp->M; j++) {
+        uint64_t sh[MAXP];
+        or_dcf_eval(b, &K->lkey[j - 1], u, NULL, sh);
+        for (uint32_t q = 0; q < sp->p; q++) pay[q] += sh[q];
+    }
+}
+
+/* Both parties, elements [0, n).  Optional outputs: atoms0/atoms1/pay0/pay1
+ * (may be NULL).  comm[0], comm[1]: bytes sent by party 0 / party 1. */
+void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys *k1,
+                  const uint64_t *x0, const uint64_t *x1, uint64_t n,
+                  uint64_t *y0, uint64_t *y1, uint32_t *z0, uint32_t *z1,
+                  uint32_t *atoms0, uint32_t *atoms1, uint64_t *pay0, uint64_t *pay1,
+                  uint64_t *xhat_out, uint64_t *comm)
+{
+    const or_elem_keys *KK[2];
+    const uint64_t *xs[2] = {x0, x1};
+    uint64_t *ys[2] = {y0, y1};
+    uint32_t *zs[2] = {z0, z1};
+    uint32_t p = sp->p, d = sp->d, r = sp->r;
+    uint64_t sent[2] = {0, 0};
+    for (uint64_t e = 0; e < n; e++) {
+        KK[0] = &k0[e]; KK[1] = &k1[e];
+        /* (1) shares -> masked opening (App. C): each party sends x_b + r_b */
+        uint64_t msg[2];
+        for (int b = 0; b < 2; b++) { msg[b] = xs[b][e] + KK[b]->r_share; sent[b] += 8; }
+        uint64_t xhat = msg[0] + msg[1];
+        if (xhat_out) xhat_out[e] = xhat;
+
+        uint64_t pay[2][MAXP], xb[2], y[2][MAXP];
+        for (int b = 0; b < 2; b++) {
+            /* (2) packed comparison and local rewrite */
+            uint32_t atoms = party_pred_atoms(b, sp, KK[b], xhat);
+            zs[b][e] = party_out_bits(b, sp, KK[b], atoms);
+            if (b == 0 && atoms0) atoms0[e] = atoms;
+            if (b == 1 && atoms1) atoms1[e] = atoms;
+            /* (3) vector interval lookup */
+            party_lookup(b, sp, KK[b], xhat, pay[b]);
+            if (b == 0 && pay0) for (uint32_t q = 0; q < p; q++) pay0[e * p + q] = pay[0][q];
+            if (b == 1 && pay1) for (uint32_t q = 0; q < p; q++) pay1[e * p + q] = pay[1][q];
+            /* (4) masked -> shares: P0 takes x^ - r_0, P1 takes -r_1 */
+            xb[b] = b == 0 ? xhat - KK[0]->r_share : (uint64_t)0 - KK[1]->r_share;
+            /* Horner starts from the leading coefficient */
+            for (uint32_t o = 0; o < r; o++) y[b][o] = pay[b][o * (d + 1) + d];
+        }
+        /* (5) Horner: y <- y*x + c_j for j = d-1 .. 0; each product is one
+         * Beaver multiplication with a fresh triple (open e = y - a, f = x - b). */
+        for (int j = (int)d - 1; j >= 0; j--) {
+            uint64_t em[2][MAXP], fm[2][MAXP];
+            for (int b = 0; b < 2; b++)
+                for (uint32_t o = 0; o < r; o++) {
+                    uint32_t mi = ((uint32_t)(d - 1 - j)) * r + o;
+                    em[b][o] = y[b][o] - KK[b]->ta[mi];
+                    fm[b][o] = xb[b] - KK[b]->tb[mi];
+                    sent[b] += 16;
+                }
+            for (int b = 0; b < 2; b++)
+                for (uint32_t o = 0; o < r; o++) {
+                    uint32_t mi = ((uint32_t)(d - 1 - j)) * r + o;
+                    uint64_t E = em[0][o] + em[1][o], F = fm[0][o] + fm[1][o];
+                    uint64_t zz = E * KK[b]->tb[mi] + F * KK[b]->ta[mi] + KK[b]->tc[mi];
+                    if (b == 0) zz += E * F;
+                    y[b][o] = zz + pay[b][o * (d + 1) + (uint32_t)j];
+                }
+        }
+        for (int b = 0; b < 2; b++)
+            for (uint32_t o = 0; o < r; o++) ys[b][e * r + o] = y[b][o];
+    }
+    if (comm) { comm[0] = sent[0]; comm[1] = sent[1]; }
+}
+
+/* Reconstruction: y = y0 + y1 (mod 2^64), z = z0 ^ z1. */
+void or_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0, const uint32_t *z1,
+                    uint64_t n, uint32_t r, uint64_t *y, uint32_t *z)
+{
+    for (uint64_t i = 0; i < n * r; i++) y[i] = y0[i] + y1[i];
+    for (uint64_t i = 0; i < n; i++) z[i] = z0[i] ^ z1[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Accessors used by tests to read key material                              */
+/* ------------------------------------------------------------------------ */
+
+void or_elem_qkey(const or_elem_keys *K, uint32_t t, or_dcf_key *out) { bit_key_to(&K->qkey[t], out); }
+const or_dcf_key *or_elem_lkey(const or_elem_keys *K, uint32_t j) { return &K->lkey[j]; }
+
+void or_dcf_key_fields(const or_dcf_key *key, uint8_t *root, uint8_t *scw, uint8_t *tcw_l,
+                       uint8_t *tcw_r, uint8_t *vcw_bit, uint64_t *vcw)
+{
+    int k = key->k, p = key->p;
+    memcpy(root, key->root, 16);
+    for (int i = 0; i < k; i++) {
+        memcpy(scw + 16 * i, key->scw[i], 16);
+        tcw_l[i] = key->tcw_l[i];
+        tcw_r[i] = key->tcw_r[i];
+    }
+    for (int i = 0; i <= k; i++) {
+        vcw_bit[i] = key->vcw_bit[i];
+        for (int q = 0; q < p; q++) vcw[i * (p > 0 ? p : 1) + q] = key->vcw[i][q];
+    }
+}
+
+void or_elem_fields(const or_elem_keys *K, uint32_t p, uint32_t nm, uint64_t *r_share,
+                    uint32_t *carry, uint64_t *vlast, uint64_t *ta, uint64_t *tb, uint64_t *tc)
+{
+    *r_share = K->r_share;
+    *carry = K->carry_share;
+    for (uint32_t q = 0; q < p; q++) vlast[q] = K->vlast_share[q];
+    for (uint32_t i = 0; i < nm; i++) { ta[i] = K->ta[i]; tb[i] = K->tb[i]; tc[i] = K->tc[i]; }
+}

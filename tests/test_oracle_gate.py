@@ -1,0 +1,169 @@
+"""Pins for the oracle's whole gate: compiler correctness (Lemma 'compiler
+correctness'), the App. N ReLU closed form, the plaintext evaluator against an
+independent Python evaluation, communication counts and public shapes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import golden
+from paper_2606_09551_b300 import specs as S
+
+SEED = bytes(range(16))
+M64 = (1 << 64) - 1
+
+
+def ospec(sp):
+    return O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits,
+                  sp.pred_tuples())
+
+
+def python_plain(sp, xs):
+    """Independent plaintext evaluation with Python integers."""
+    ys, zs = [], []
+    bits = []
+    if sp.partition_bits:
+        bits += [(sp.k, 0, a, 0) for a in sp.alpha[1:-1]]
+    bits += sp.pred_tuples()
+    for x in (int(v) for v in xs):
+        xk = x % (1 << sp.k)
+        i = int(np.searchsorted(np.array(sp.alpha[:-1], dtype=object), xk, side="right")) - 1
+        row = []
+        for o in range(sp.n_out):
+            c = [int(v) for v in sp.coeff[i, o]]
+            acc = 0
+            for j in range(sp.degree, -1, -1):
+                acc = (acc * x + c[j]) & M64
+            row.append(acc)
+        ys.append(row)
+        z = 0
+        for t, (f, c, g, neg) in enumerate(bits):
+            v = (((x % (1 << f)) + c) % (1 << f)) < g
+            z |= (int(v) ^ neg) << t
+        zs.append(z)
+    return np.array(ys, dtype=np.uint64), np.array(zs, dtype=np.uint32)
+
+
+def run_gate(sp, x, r_override=None, call_id=0):
+    o = ospec(sp)
+    k0, k1, x0, x1 = O.dealer(o, SEED, call_id, 0, x.size, x, r_override=r_override)
+    res = O.eval_pair(o, k0, k1, x0, x1)
+    y, z = O.reconstruct(res["y0"], res["y1"], res["z0"], res["z1"], sp.n_out)
+    return o, res, y, z
+
+
+def test_plain_evaluator_matches_independent_python():
+    rng = np.random.default_rng(1)
+    for trial in range(12):
+        k = int(rng.integers(3, 25))
+        m = int(rng.integers(1, 17))
+        d = int(rng.integers(0, 4))
+        r = 1 if d > 1 else int(rng.integers(1, 3))
+        sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 4)))
+        x = rng.integers(0, 2 ** 64, size=300, dtype=np.uint64)
+        y, z = ospec(sp).plain_eval(x)
+        yp, zp = python_plain(sp, x)
+        assert (y == yp).all() and (z == zp).all()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_gate_every_mask_every_input(k):
+    """Reconstruction equals F(x) for all x and all masks r (Lemma 'compiler correctness')."""
+    rng = np.random.default_rng(40 + k)
+    N = 2 ** k
+    for trial in range(6):
+        m = int(rng.integers(1, min(N, 16) + 1))
+        d = int(rng.integers(0, 4))
+        sp = S.random_spec(rng, k, m, d, 1, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 3)))
+        hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
+        rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all()
+        # online communication: 8 B for the opening + 16 B per Beaver multiplication
+        assert (res["comm"] == xs.size * (8 + 16 * d * sp.n_out)).all()
+
+
+def test_relu_worked_example_closed_form():
+    """App. N: y = max(x, 0) and z = MSB(x) on signed k-bit inputs, with the
+    stated compiled shapes."""
+    fx = dict(line.split() for line in open(golden("relu_worked_example.txt"))
+              if line.strip() and not line.startswith("#"))
+    k = 16
+    sp = S.relu(k)
+    rng = np.random.default_rng(5)
+    xs_signed = np.concatenate([np.array([0, 1, -1, 2 ** 15 - 1, -(2 ** 15)], dtype=np.int64),
+                                rng.integers(-(2 ** 15), 2 ** 15, size=3000, dtype=np.int64)])
+    o, res, y, z = run_gate(sp, xs_signed.view(np.uint64))
+    assert o.M == int(fx["M"]) and o.p == int(fx["p"]) and o.T == int(fx["T"])
+    assert o.n_mults == int(fx["mults"]) and sp.m == int(fx["m"])
+    assert (y[:, 0].view(np.int64) == np.maximum(xs_signed, 0)).all()
+    assert (z == (xs_signed < 0).astype(np.uint32)).all()
+
+
+def test_relu_every_mask_small_ring():
+    """The same closed form at k = 4 over every (x, r) pair, x sign-extended."""
+    k, N = 4, 16
+    sp = S.relu(k)
+    xs_signed = np.tile(np.arange(-8, 8, dtype=np.int64), N)
+    rs = np.repeat(np.arange(N, dtype=np.uint64), N)
+    o, res, y, z = run_gate(sp, xs_signed.view(np.uint64), r_override=rs)
+    assert (y[:, 0].view(np.int64) == np.maximum(xs_signed, 0)).all()
+    assert (z == (xs_signed < 0).astype(np.uint32)).all()
+
+
+def test_special_cases():
+    rng = np.random.default_rng(9)
+    x = rng.integers(0, 2 ** 64, size=500, dtype=np.uint64)
+    # identity polynomial P(x) = x on one interval: no lookup keys (App. O), y = x
+    coeff = np.zeros((1, 1, 2), np.uint64)
+    coeff[0, 0, 1] = 1
+    sp = S.OperatorSpec("id", 16, 0, 0, 1, 1, 1, [0, 1 << 16], coeff)
+    o, res, y, z = run_gate(sp, x)
+    assert o.M == 1 and o.T == 0
+    assert (y[:, 0] == x).all()
+    # degree 0: no Beaver multiplications, no Horner communication
+    sp = S.random_spec(rng, 12, 5, 0)
+    o, res, y, z = run_gate(sp, x)
+    assert o.n_mults == 0 and (res["comm"] == 8 * x.size).all()
+    assert (y == python_plain(sp, x)[0]).all()
+    # sentinel predicates: C_0 = 0 and C_{2^f} = 1 need no queries
+    sp = S.random_spec(rng, 10, 3, 1, partition_bits=False)
+    sp.preds = [S.PredDesc(10, 0, 0, 0), S.PredDesc(6, 3, 64, 0), S.PredDesc(6, 0, 64, 1)]
+    o, res, y, z = run_gate(sp, x)
+    assert o.T == 0
+    assert (z == 0b010).all()
+
+
+def test_shapes_are_mask_independent_and_match_counts():
+    """Prop. 'mask-independent shape via padding' and App. O counts for the
+    workload specs: T, M, p and the per-element key record do not depend on r."""
+    for sp, T, M, p in [(S.gelu4(), 4, 5, 3), (S.gelu8(), 8, 9, 3), (S.nexp16(), 16, 17, 4),
+                        (S.recip16(), 16, 17, 4), (S.rsqrt16(), 16, 17, 4), (S.silu16(), 16, 17, 4)]:
+        o = ospec(sp)
+        assert (o.T, o.M, o.p) == (T, M, p), sp.name
+        for r in [0, 1, (1 << sp.k) - sp.alpha[1], 12345, (1 << sp.k) - 1, 2 ** 63 + 7]:
+            B, _ = o.compile_lookup(r)
+            assert len(B) == M + 1
+
+
+def test_query_list_order():
+    """The fixed descriptor order: per view the 1[v < r_f] atom first, then one
+    theta atom per distinct predicate; MSB merges with the boundary 2^(k-1)."""
+    o = ospec(S.gelu4())
+    q = o.queries()
+    assert q[0] == (16, 0, -1)
+    assert [x[2] for x in q[1:]] == [0, 1, 2]
+    assert o.n_bool == 4
+
+
+def test_distinct_calls_draw_distinct_masks():
+    sp = S.gelu4()
+    o = ospec(sp)
+    x = np.zeros(64, np.uint64)
+    a0, a1, _, _ = O.dealer(o, SEED, 0, 0, 64, x)
+    b0, b1, _, _ = O.dealer(o, SEED, 1, 0, 64, x)
+    ra = [(a0.fields(o, i)["r_share"] + a1.fields(o, i)["r_share"]) & M64 for i in range(64)]
+    rb = [(b0.fields(o, i)["r_share"] + b1.fields(o, i)["r_share"]) & M64 for i in range(64)]
+    assert len(set(ra) | set(rb)) == 128
