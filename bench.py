@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the FuseFSS online hot path on one B300.
+
+Workload (default): all nonlinearities of one BERT-base layer at batch 1,
+seq 128 (GeLU on 128x3072, softmax nExp on 12x128x128, reciprocal on 12x128,
+LayerNorm rsqrt on 128), one plain fused-gate launch per operator, both
+parties on this GPU.  A step evaluates every operator once on fresh one-time
+keys (generated by the GPU dealer before the timed region; dealer throughput
+is reported separately).  Metric: FSS-evaluated elements/s (both parties,
+open + packed comparison + interval lookup + Horner/Beaver).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs an independent replica of the workload
+on its own GPU (weak scaling, no data-path collective); the timed region is
+bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# ALU-pipe instructions per AES-128 block of the shared-memory T-table code
+# (ncu: smsp__inst_executed_pipe_alu.sum / blocks on the AES micro-kernel;
+# profiles/aes_ttable_microkernel.md).  Used for the ALU roofline.
+ALU_OPS_PER_AES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["bert_layer", "gelu4"], default="bert_layer")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2606_09551_b300 import inputs as I
+    if name == "gelu4":
+        return I.single_gelu4(), {"workload": "gelu4_single_op", "spec": "GeLU-4 k=16 f=12 d=2",
+                                  "elements": 65536, "form": "plain"}
+    calls = I.bert_layer()
+    return calls, {"workload": "bert_base_layer_nonlinearities", "seq_len": 128, "hidden": 768,
+                   "heads": 12, "mlp": 3072, "batch": 1,
+                   "ops": {c.name: {"elements": c.n, "spec": c.spec.name, "k": c.spec.k, "m": c.spec.m,
+                                    "degree": c.spec.degree} for c in calls},
+                   "elements": sum(c.n for c in calls), "form": "plain per-operator launches",
+                   "ring": "Z_2^64", "frac_bits": 12}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, threads over element chunks
+# ---------------------------------------------------------------------------
+
+def oracle_rates(calls, cpu_seconds, threads=None):
+    """Per-op oracle eval seconds per element (wall, all threads), on a
+    bounded sample of each op's elements.  Keys for the sample come from the
+    oracle dealer before timing."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    import oracle as O
+    from paper_2606_09551_b300 import inputs as I
+    threads = threads or os.cpu_count() or 1
+    out, desc = {}, {}
+    for c in calls:
+        o = O.Spec(c.spec.k, c.spec.m, c.spec.degree, c.spec.n_out, c.spec.alpha, c.spec.coeff,
+                   c.spec.partition_bits, c.spec.pred_tuples())
+        # single-core cost estimate: 0.45 us per AES block, both parties
+        per_elem = 0.45e-6 * 2 * (sum(f for f, _, _ in o.queries())
+                                  + (o.M - 1) * (o.k * (1 + (o.p + 1) // 2) + (o.p + 1) // 2))
+        ns = int(min(c.n, max(threads, cpu_seconds / max(per_elem, 1e-9))))
+        chunks = [(i * ns // threads, (i + 1) * ns // threads) for i in range(threads)]
+        chunks = [ch for ch in chunks if ch[1] > ch[0]]
+
+        def deal(ch):
+            return O.dealer(o, I.KEY_SEED, c.call_id, ch[0], ch[1] - ch[0], c.x[ch[0]:ch[1]])
+
+        with ThreadPoolExecutor(len(chunks)) as ex:
+            dealt = list(ex.map(deal, chunks))
+
+        def ev(d):
+            k0, k1, x0, x1 = d
+            return O.eval_pair(o, k0, k1, x0, x1)
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(len(chunks)) as ex:
+            list(ex.map(ev, dealt))
+        dt = time.perf_counter() - t0
+        out[c.name] = dt / ns
+        desc[c.name] = ns
+    return out, desc, threads
+
+
+def cpu_baseline(calls, cpu_seconds):
+    rates, sample, threads = oracle_rates(calls, cpu_seconds)
+    total = sum(c.n for c in calls)
+    t = sum(c.n * rates[c.name] for c in calls)
+    return {"value": total / t, "unit": "elements/s", "cores": threads, "kind": "oracle",
+            "sample": "oracle eval_pair (both parties) on the first " +
+                      ", ".join(f"{sample[k]} {k}" for k in sample) +
+                      " elements; per-op s/element combined with the full layer's op mix"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2606_09551_b300 import build as B
+    from paper_2606_09551_b300 import fusefss as F
+    from paper_2606_09551_b300 import inputs as I
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    ctx = F.Context(local_rank)
+    calls, config = workload(args.workload)
+    css = {c.name: F.CompiledSpec(c.spec, ctx) for c in calls}
+    xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
+    total = sum(c.n for c in calls)
+    stream = torch.cuda.current_stream()
+
+    class KeySet:
+        def __init__(self):
+            self.k = {}
+            for c in calls:
+                cs = css[c.name]
+                x0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
+                self.k[c.name] = (F.Keys(cs, c.n, 0), F.Keys(cs, c.n, 1), x0, torch.empty_like(x0))
+
+        def generate(self, tag):
+            for c in calls:
+                k0, k1, x0, x1 = self.k[c.name]
+                F.keygen(ctx, css[c.name], I.KEY_SEED, c.call_id + 16 * tag, c.n, k0, k1, xp[c.name], x0, x1)
+
+    outs = {}
+    for c in calls:
+        y0 = torch.empty(c.n * c.spec.n_out, dtype=torch.uint64, device=dev)
+        z0 = torch.empty(c.n, dtype=torch.uint32, device=dev)
+        outs[c.name] = (y0, torch.empty_like(y0), z0, torch.empty_like(z0))
+    comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+
+    def step(ks, evs=None):
+        for i, c in enumerate(calls):
+            k0, k1, x0, x1 = ks.k[c.name]
+            y0, y1, z0, z1 = outs[c.name]
+            if evs is not None:
+                evs[i][0].record(stream)
+            F.eval_pair(ctx, css[c.name], k0, k1, x0, x1, y0, y1, z0, z1, comm)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    # warm-up: fresh keys before every warm-up step (keys are one-time)
+    warm = KeySet()
+    for w in range(args.warmup):
+        warm.generate(1000 + w)
+        step(warm)
+    torch.cuda.synchronize()
+    del warm
+    # dealer: K key sets, timed separately
+    sets = [KeySet() for _ in range(args.steps)]
+    kg0, kg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kg0.record(stream)
+    for s, ks in enumerate(sets):
+        ks.generate(s)
+    kg1.record(stream)
+    torch.cuda.synchronize()
+    keygen_ms = kg0.elapsed_time(kg1) / args.steps
+
+    # timed region: K steps, inputs resident in HBM (keys > L2 every step)
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in calls] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t0.record(stream)
+        for s in range(args.steps):
+            step(sets[s], evs[s])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    per_op_ms = {c.name: statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
+                 for i, c in enumerate(calls)}
+    comm_b = [int(v) for v in comm.cpu().tolist()]
+
+    # end to end through the public API: host (pinned) input shares in, shares out
+    e2e = None
+    if not args.no_e2e:
+        for s, ks in enumerate(sets):
+            ks.generate(100 + s)
+        host_in, host_out = {}, {}
+        for c in calls:
+            k0, k1, x0, x1 = sets[0].k[c.name]
+            host_in[c.name] = (x0.cpu().pin_memory(), x1.cpu().pin_memory())
+            y0, y1, z0, z1 = outs[c.name]
+            host_out[c.name] = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (y0, y1, z0, z1))
+        h2d = sum(2 * 8 * c.n for c in calls)
+        d2h = sum(2 * 8 * c.n * c.spec.n_out + 2 * 4 * c.n for c in calls)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(args.steps):
+            for c in calls:
+                k0, k1, x0, x1 = sets[s].k[c.name]
+                x0.copy_(host_in[c.name][0], non_blocking=True)
+                x1.copy_(host_in[c.name][1], non_blocking=True)
+                y0, y1, z0, z1 = outs[c.name]
+                F.eval_pair(ctx, css[c.name], k0, k1, x0, x1, y0, y1, z0, z1)
+                for hd, dd in zip(host_out[c.name], (y0, y1, z0, z1)):
+                    hd.copy_(dd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": total * world / (ems * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+
+    # roofline of the dominant kernel (the op with the largest launch time)
+    dom = max(calls, key=lambda c: per_op_ms[c.name])
+    sh = css[dom.name].shape
+    aes_launch = 2 * sh.aes_per_elem * dom.n
+    key_bytes_launch = 2 * sh.key_bytes_per_elem * dom.n
+    lop3_rate, _ = F.microbench(ctx, 0, 4096)
+    aes_rate, _ = F.microbench(ctx, 1, 2048)
+    dom_s = per_op_ms[dom.name] * 1e-3
+    roof = {
+        "bound": "alu", "kernel": f"gate_kernel ({dom.name}: {dom.spec.name}, {dom.n} elements)",
+        "unit": "Gop/s",
+        "aes_blocks_per_launch": aes_launch,
+        "aes_blocks_per_s": aes_launch / dom_s,
+        "aes_microkernel_blocks_per_s": aes_rate,
+        "lop3_peak_gops_measured": lop3_rate / 1e9,
+        "key_bytes_per_launch": key_bytes_launch,
+        "hbm_gbs_achieved": key_bytes_launch / dom_s / 1e9,
+        "traffic": None,
+    }
+    if ALU_OPS_PER_AES:
+        roof["achieved"] = aes_launch * ALU_OPS_PER_AES / dom_s / 1e9
+        roof["peak"] = lop3_rate / 1e9
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        # until the per-block ALU count is measured: AES rate against the
+        # AES-only micro-kernel of the same code
+        roof["achieved"] = aes_launch / dom_s / 1e9
+        roof["peak"] = aes_rate / 1e9
+        roof["unit"] = "G AES blocks/s"
+        roof["frac"] = roof["achieved"] / roof["peak"]
+
+    res = {
+        "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
+        "value": total * world / (ms * 1e-3),
+        "unit": "elements/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (seeded activations; random masks, keys and triples from the GPU dealer)",
+        "config": dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" %
+                       (sum(2 * css[c.name].shape.key_bytes_per_elem * c.n for c in calls) / 1e9),
+                       parallelism="replicas" if world > 1 else "single GPU, both parties on it"),
+        "per_op_ms": per_op_ms,
+        "keygen": {"ms_per_step": keygen_ms, "elements_per_s": total / (keygen_ms * 1e-3)},
+        "comm_bytes_per_party": comm_b,
+        "gpu_launches": args.steps * len(calls),
+        "clocks": clk.summary(),
+        "roofline": roof,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle (the paper ships no code), on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    calls, config = workload(args.workload)
+    budget = args.cpu_seconds / 4.0
+    for _ in range(args.warmup):
+        oracle_rates(calls, budget / 4.0)
+    times = []
+    threads = None
+    samples = None
+    for _ in range(args.steps):
+        rates, samples, threads = oracle_rates(calls, budget)
+        times.append(sum(c.n * rates[c.name] for c in calls))
+    total = sum(c.n for c in calls)
+    per_step_s = statistics.mean(times)
+    value = total / per_step_s
+    desc = ("oracle eval_pair (both parties) per step on the first " +
+            ", ".join(f"{samples[k]} {k}" for k in samples) + " elements; per-op s/element scaled to the layer")
+    return {
+        "impl": "reference",
+        "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
+        "value": value, "unit": "elements/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ---------------------------------------------------------------------------
+# process group helpers (N > 1 under torchrun)
+# ---------------------------------------------------------------------------
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, dev):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

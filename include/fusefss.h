@@ -1,0 +1,209 @@
+/*
+ * fusefss.h -- C ABI of the B300 (sm_103a) FuseFSS online hot path.
+ *
+ * The library evaluates compiled scalar gates of FuseFSS (arXiv 2606.09551):
+ * an operator specification (Sec. 4.1, Def. "operator specification") is
+ * compiled once into a public shape; a GPU dealer generates per-element
+ * preprocessing material (Sec. 5.2); the online phase (Sec. 5.3) opens the
+ * masked input x^ = x + r_in (App. C), runs ONE packed multi-threshold
+ * comparison (App. I, Def. "multi-view packed predicate primitive") and ONE
+ * vector interval lookup (App. I, Def. "interval lookup with vector payload")
+ * on x^, derives shares of x locally and evaluates the selected polynomial by
+ * Horner's rule with one Beaver multiplication per step (Sec. 4.5, Theorem
+ * "two-call evaluation").
+ *
+ * Conventions for every call below:
+ *  - Return value: FFSS_OK (0) on success, a negative FFSS_ERR_* code on
+ *    failure.  No call throws or aborts.  ffss_last_error() returns a
+ *    thread-local, library-owned description of the most recent failure on the
+ *    calling thread (valid until the next failing call on that thread).
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; they
+ *    must stay valid until the work queued on `stream` has finished.  Pointers
+ *    without that suffix are host pointers, read during the call only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is stream ordered; no call synchronizes the
+ *    device unless it says so.
+ *  - Ring values are uint64 (Z_{2^64}, two's complement fixed point); XOR
+ *    shared bits are packed into uint32 words, bit t = item t.
+ *  - Element arrays are indexed by element; multi-output arrays are
+ *    element-major: y[e * n_out + o], payload[e * p + q].
+ *  - Both parties live on this one GPU.  Party-b code reads only party-b key
+ *    material plus the peer's opened messages; openings pass through device
+ *    buffers and are counted in bytes.
+ */
+#ifndef FUSEFSS_H
+#define FUSEFSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FFSS_OK 0
+#define FFSS_ERR_INVALID (-1)     /* malformed argument or operator specification */
+#define FFSS_ERR_SHAPE (-2)       /* size / shape mismatch, or keys already consumed */
+#define FFSS_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define FFSS_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define FFSS_ERR_BUDGET (-5)      /* key-memory budget exhausted (serving) */
+#define FFSS_ERR_PARTY (-6)       /* party index not 0 or 1, or keys of the wrong party */
+#define FFSS_ERR_UNSUPPORTED (-7) /* shape outside what the kernels are built for */
+
+/* Library limits (checked when a spec is compiled). */
+#define FFSS_MAX_K 32        /* comparison view width k */
+#define FFSS_MAX_M 16        /* intervals m */
+#define FFSS_MAX_P 4         /* payload length p = n_out * (degree + 1) */
+#define FFSS_MAX_BOOL 32     /* Boolean outputs, one uint32 per element */
+#define FFSS_MAX_T 32        /* packed-comparison queries, one uint32 of atoms */
+
+typedef struct ffss_ctx ffss_ctx;     /* per-device state (tables, autotune cache) */
+typedef struct ffss_spec ffss_spec;   /* a compiled operator specification */
+typedef struct ffss_keys ffss_keys;   /* one party's key material for one call */
+
+/* One Boolean output: negate XOR 1[((x mod 2^f) + c) mod 2^f < gamma].
+ * Covers C_beta (f = k), D_{gamma,f} (low bits), MSB(x + c) = NOT 1[view_{k,c} < 2^(k-1)]
+ * and signed compares (c = 2^(k-1)) -- Def. "operator specification" (Sec. 4.1)
+ * and App. J "signed comparisons and MSB(x+c)". */
+typedef struct {
+    uint32_t f;          /* view width, 1 <= f <= k */
+    uint32_t negate;     /* 0 or 1 */
+    uint64_t c;          /* public shift, c < 2^f */
+    uint64_t gamma;      /* threshold, 0 <= gamma <= 2^f (0 and 2^f are constants) */
+} ffss_pred_desc;
+
+/* Operator specification (Sec. 4.1).  Caller-owned; copied by ffss_spec_compile.
+ * alpha: m+1 entries with alpha[0] = 0 < alpha[1] < ... < alpha[m] = 2^k
+ *        (intervals over the canonical k-bit view of x).
+ * coeff: m * n_out * (degree+1) ring elements, index (i*n_out + o)*(degree+1) + j
+ *        = coefficient of x^j of output o on interval i.  The polynomial is
+ *        evaluated over Z_{2^64} on the full 64-bit x.
+ * Boolean outputs: if partition_bits != 0 the first m-1 outputs are
+ *        C_{alpha_i}(x) = 1[(x mod 2^k) < alpha_i], i = 1..m-1; preds[0..n_pred)
+ *        follow. */
+typedef struct {
+    uint32_t k;              /* comparison view width, 1..FFSS_MAX_K */
+    uint32_t frac_bits;      /* fixed-point metadata (not used by the arithmetic) */
+    uint32_t m;              /* intervals, 1..FFSS_MAX_M, m < 2^k */
+    uint32_t degree;         /* d */
+    uint32_t n_out;          /* r, arithmetic outputs */
+    uint32_t partition_bits; /* 0 or 1 */
+    const uint64_t *alpha;
+    const uint64_t *coeff;
+    uint32_t n_pred;
+    const ffss_pred_desc *preds;
+} ffss_spec_desc;
+
+/* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
+ * shape via padding", App. I; counts of App. O). */
+typedef struct {
+    uint32_t k, m, degree, n_out;
+    uint32_t T;              /* packed-comparison queries */
+    uint32_t M;              /* lookup intervals (1 when m = 1: lookup omitted, App. O) */
+    uint32_t p;              /* payload length */
+    uint32_t n_mults;        /* Beaver multiplications per element = degree * n_out */
+    uint32_t n_bool;         /* Boolean outputs */
+    uint32_t n_views;        /* distinct (f, c) views among the queries */
+    uint64_t key_bytes_per_elem;   /* one party, this library's layout */
+    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults */
+    uint64_t aes_per_elem;         /* one party, online AES-128 blocks */
+} ffss_shape;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (makes it current on the calling
+ * thread) and upload the AES tables.  Errors: FFSS_ERR_CUDA. */
+int ffss_ctx_create(int device, ffss_ctx **out);
+int ffss_ctx_destroy(ffss_ctx *ctx);
+const char *ffss_last_error(void);
+
+/* ---- specifications ------------------------------------------------------ */
+
+/* Validate and compile a specification: public query list (App. F step 4,
+ * fixed descriptor order), lookup shape, key layout.  ctx may be NULL for a
+ * host-only compile that answers shape and size queries but cannot be used
+ * for device calls.  Errors: FFSS_ERR_INVALID (malformed),
+ * FFSS_ERR_UNSUPPORTED (beyond the limits), FFSS_ERR_CUDA. */
+int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *desc, ffss_spec **out);
+int ffss_spec_shape(const ffss_spec *spec, ffss_shape *out);
+int ffss_spec_free(ffss_spec *spec);
+
+/* ---- key material -------------------------------------------------------- */
+
+/* Bytes of one party's key material for n elements (this library's layout). */
+int ffss_keys_size(const ffss_spec *spec, uint64_t n, uint64_t *bytes);
+
+#define FFSS_KEYS_EMPTY 0    /* to be filled by ffss_keygen */
+#define FFSS_KEYS_FILLED 1   /* already holds key material in this layout */
+
+/* Bind a caller-owned device buffer of >= ffss_keys_size bytes (256-byte
+ * aligned) as party `party`'s keys for n elements.  The handle records
+ * whether the keys were generated and which online calls consumed them (keys
+ * are one-time, Sec. 3.1).  Errors: FFSS_ERR_INVALID, FFSS_ERR_SHAPE,
+ * FFSS_ERR_PARTY. */
+int ffss_keys_bind(const ffss_spec *spec, uint64_t n, int party, void *buf_dev,
+                   uint64_t buf_bytes, int state, ffss_keys **out);
+int ffss_keys_release(ffss_keys *keys);
+
+/* GPU dealer (Sec. 5.2, App. F): for elements [0, n) of call `call_id`, draw
+ * r_in and its shares, carries and thresholds, translated/padded lookup
+ * boundaries, DCF key pairs (Boyle et al. 2021 comparison DCF, AES-128
+ * fixed-key MMO PRG), shares of the last payload and Beaver triples, all from
+ * AES-128-CTR keyed by `seed`.  If x_plain_dev is not NULL, also splits it
+ * into input shares x0_dev / x1_dev (n uint64 each).  Errors:
+ * FFSS_ERR_SHAPE (handles do not match spec/n), FFSS_ERR_PARTY, FFSS_ERR_CUDA. */
+int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                uint64_t n, const uint64_t *x_plain_dev, ffss_keys *k0, ffss_keys *k1,
+                uint64_t *x0_dev, uint64_t *x1_dev, void *stream);
+
+/* ---- online: single-party FSS calls (local, non-interactive) ------------ */
+
+/* Packed comparison Eval_b on public x^ (App. I, Def. "multi-view packed
+ * predicate primitive"): atoms_dev[e] bit t = XOR share of
+ * 1[view_{k_t,c_t}(x^_e) < theta_t]; bits_dev[e] bit o = XOR share of Boolean
+ * output o after the local mask rewrite (Lemma "masked rewrite for unsigned
+ * comparison", App. E).  Either output pointer may be NULL.  Consumes the
+ * comparison part of the keys. */
+int ffss_eval_pred(ffss_ctx *ctx, const ffss_spec *spec, int party, ffss_keys *keys,
+                   const uint64_t *xhat_dev, uint64_t n, uint32_t *atoms_dev, uint32_t *bits_dev,
+                   void *stream);
+
+/* Vector interval lookup Eval_b on public x^ (App. I, Def. "interval lookup
+ * with vector payload"): payload_dev[e*p + q] = additive share of the active
+ * interval's payload.  Consumes the lookup part of the keys. */
+int ffss_eval_lut(ffss_ctx *ctx, const ffss_spec *spec, int party, ffss_keys *keys,
+                  const uint64_t *xhat_dev, uint64_t n, uint64_t *payload_dev, void *stream);
+
+/* ---- online: the whole two-party gate ----------------------------------- */
+
+/* Both parties, one fused kernel (Sec. 5.3): open x^ (1 round), packed
+ * comparison, interval lookup, masked-to-shares, Horner with d Beaver rounds.
+ * Inputs x0_dev/x1_dev: additive input shares.  Outputs: y_b[e*n_out + o]
+ * additive shares, z_b[e] XOR-shared Boolean outputs.  comm_dev (may be NULL):
+ * two uint64 counters, bytes sent by party 0 and party 1, incremented.
+ * Consumes both handles. */
+int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
+                   const uint64_t *x0_dev, const uint64_t *x1_dev, uint64_t n,
+                   uint64_t *y0_dev, uint64_t *y1_dev, uint32_t *z0_dev, uint32_t *z1_dev,
+                   uint64_t *comm_dev, void *stream);
+
+/* y = y0 + y1 (mod 2^64, n*n_out values), z = z0 ^ z1 (n words).  Either pair
+ * may be NULL. */
+int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint32_t *z0_dev,
+                     const uint32_t *z1_dev, uint64_t n, uint32_t n_out, uint64_t *y_dev,
+                     uint32_t *z_dev, void *stream);
+
+/* ---- measurement support ------------------------------------------------ */
+
+/* Micro-benchmarks behind the roofline figures (no counterpart in the paper,
+ * which reports no roofline).  which = 0: 32-bit LOP3 issue rate, result in
+ * operations/s (iters x 128 LOP3 per thread, 2 CTAs of 1024 threads per SM);
+ * which = 1: AES-128 blocks/s of the shared-memory T-table code the FSS
+ * kernels use (iters chained blocks per thread, one 512-thread CTA per SM).
+ * Synchronizes the device; *ms (may be NULL) receives the kernel time. */
+int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUSEFSS_H */

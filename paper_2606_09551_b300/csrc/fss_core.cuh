@@ -1,0 +1,340 @@
+// Per-element arithmetic of the FuseFSS CUDA path: AES-128 with shared-memory
+// T-tables, the fixed-key MMO PRG, the comparison DCF (Eval and Gen, bit and
+// vector payloads), and the translated/padded lookup partition.
+//
+// AES-128 (FIPS-197) is written as four 32-bit T-table lookups per output
+// column per round.  The tables live in shared memory as 4 tables x 256
+// entries x 32 copies (128 KB): lane l always reads copy l, which sits in bank
+// l, so a warp's 32 random lookups never conflict.  Lookup address of entry e
+// for lane l: table*32768 + e*128 + 4*l.
+#pragma once
+#include <stdint.h>
+#include "layout.h"
+
+#ifdef FFSS_HOST_PROBE
+#define FFSS_CORE __host__ __device__ inline
+#else
+#define FFSS_CORE __device__ __forceinline__
+#endif
+
+namespace ffss {
+
+constexpr uint32_t kTabBytes = 4u * 256u * 32u * 4u;   // 128 KB
+
+// Round keys of the public DCF PRG key K = "FuseFSS-DCF-AES!" (44 LE words).
+__constant__ uint32_t c_rk_dcf[44];
+
+struct Tab {
+  const char *base;     // shared-memory tables
+  uint32_t lane4;       // 4 * (lane id)
+};
+
+FFSS_CORE uint32_t tload(const Tab &tb, uint32_t table, uint32_t idx) {
+  return *reinterpret_cast<const uint32_t *>(tb.base + table * 32768u + idx);
+}
+
+// (byte j of w) * 128 | 4*lane
+FFSS_CORE uint32_t ix0(uint32_t w, uint32_t l4) { return ((w << 7) & 0x7F80u) | l4; }
+FFSS_CORE uint32_t ix1(uint32_t w, uint32_t l4) { return ((w >> 1) & 0x7F80u) | l4; }
+FFSS_CORE uint32_t ix2(uint32_t w, uint32_t l4) { return ((w >> 9) & 0x7F80u) | l4; }
+FFSS_CORE uint32_t ix3(uint32_t w, uint32_t l4) { return ((w >> 17) & 0x7F80u) | l4; }
+
+// AES-128 encryption of one block.  State columns are little-endian words
+// (byte r of column c = input byte 4c + r).  Table 0 entry e holds the column
+// (2S, S, S, 3S) with S = S-box(e); tables 1..3 are its byte rotations.
+template <class RK>
+FFSS_CORE uint4 aes128(uint4 in, const RK &rk, const Tab &tb) {
+  const uint32_t l4 = tb.lane4;
+  uint32_t s0 = in.x ^ rk[0], s1 = in.y ^ rk[1], s2 = in.z ^ rk[2], s3 = in.w ^ rk[3];
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    uint32_t t0 = tload(tb, 0, ix0(s0, l4)) ^ tload(tb, 1, ix1(s1, l4)) ^ tload(tb, 2, ix2(s2, l4)) ^
+                  tload(tb, 3, ix3(s3, l4)) ^ rk[4 * r + 0];
+    uint32_t t1 = tload(tb, 0, ix0(s1, l4)) ^ tload(tb, 1, ix1(s2, l4)) ^ tload(tb, 2, ix2(s3, l4)) ^
+                  tload(tb, 3, ix3(s0, l4)) ^ rk[4 * r + 1];
+    uint32_t t2 = tload(tb, 0, ix0(s2, l4)) ^ tload(tb, 1, ix1(s3, l4)) ^ tload(tb, 2, ix2(s0, l4)) ^
+                  tload(tb, 3, ix3(s1, l4)) ^ rk[4 * r + 2];
+    uint32_t t3 = tload(tb, 0, ix0(s3, l4)) ^ tload(tb, 1, ix1(s0, l4)) ^ tload(tb, 2, ix2(s1, l4)) ^
+                  tload(tb, 3, ix3(s2, l4)) ^ rk[4 * r + 3];
+    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+  }
+  // final round: SubBytes + ShiftRows only; S(e) is byte 0 of table 2, byte 1
+  // of table 3, byte 2 of table 0 and byte 3 of table 1.
+  uint4 o;
+  o.x = ((tload(tb, 2, ix0(s0, l4)) & 0xFFu) | (tload(tb, 3, ix1(s1, l4)) & 0xFF00u) |
+         (tload(tb, 0, ix2(s2, l4)) & 0xFF0000u) | (tload(tb, 1, ix3(s3, l4)) & 0xFF000000u)) ^ rk[40];
+  o.y = ((tload(tb, 2, ix0(s1, l4)) & 0xFFu) | (tload(tb, 3, ix1(s2, l4)) & 0xFF00u) |
+         (tload(tb, 0, ix2(s3, l4)) & 0xFF0000u) | (tload(tb, 1, ix3(s0, l4)) & 0xFF000000u)) ^ rk[41];
+  o.z = ((tload(tb, 2, ix0(s2, l4)) & 0xFFu) | (tload(tb, 3, ix1(s3, l4)) & 0xFF00u) |
+         (tload(tb, 0, ix2(s0, l4)) & 0xFF0000u) | (tload(tb, 1, ix3(s1, l4)) & 0xFF000000u)) ^ rk[42];
+  o.w = ((tload(tb, 2, ix0(s3, l4)) & 0xFFu) | (tload(tb, 3, ix1(s0, l4)) & 0xFF00u) |
+         (tload(tb, 0, ix2(s1, l4)) & 0xFF0000u) | (tload(tb, 1, ix3(s2, l4)) & 0xFF000000u)) ^ rk[43];
+  return o;
+}
+
+FFSS_CORE uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
+FFSS_CORE uint4 and4(uint4 a, uint32_t m) { return make_uint4(a.x & m, a.y & m, a.z & m, a.w & m); }
+FFSS_CORE uint64_t lo64(uint4 a) { return uint64_t(a.x) | (uint64_t(a.y) << 32); }
+FFSS_CORE uint64_t hi64(uint4 a) { return uint64_t(a.z) | (uint64_t(a.w) << 32); }
+
+// DCF PRG: H(s, j) = AES_K(s ^ j) ^ s ^ j, j XORed into the low 32 bits.
+// `aes` is a functor computing AES_K (inlined on the online path, an
+// out-of-line call in the dealer to keep its code small).
+template <class AES>
+FFSS_CORE uint4 mmo(uint4 s, uint32_t j, const AES &aes) {
+  s.x ^= j;
+  return xor4(aes(s), s);
+}
+
+// Public view_{f,c}(u) = ((u mod 2^f) + c) mod 2^f  (Sec. 3.6), f <= 32.
+FFSS_CORE uint32_t view(uint64_t u, uint32_t f, uint64_t c) {
+  uint64_t mask = (uint64_t(1) << f) - 1;
+  return uint32_t(((u & mask) + c) & mask);
+}
+
+// ---------------------------------------------------------------------------
+// DCF Eval_b (Boyle et al. 2021 comparison DCF, MSB first).
+// Expansion of child x of seed s: blk = H(s, x); control bit t = blk bit 0;
+// bit payload v = blk bit 1; next seed = blk with bits 0,1 cleared.  A
+// party with t = 1 XORs the level's correction word into the seed and
+// t_CW^x into t.  Correction words store t_CW^L, t_CW^R in bits 0, 1.
+// ---------------------------------------------------------------------------
+
+// Bit payload (Z_2): returns the XOR share of 1[u < alpha].
+// root: uint4 root[n] of this key; cw level i at root[(1+i)*n]; vcw: V_CW bits.
+template <class AES>
+FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, uint64_t n,
+                                uint64_t vcw, const AES &aes) {
+  uint4 s = root[0];
+  uint32_t t = b, v = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t x = (u >> (k - 1 - i)) & 1u;
+    const uint4 cw = root[(1 + uint64_t(i)) * n];
+    const uint4 blk = mmo(s, x, aes);
+    const uint32_t tm = 0u - t;
+    v ^= (blk.x >> 1) ^ (t & uint32_t(vcw >> i));
+    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
+    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
+    s.y = blk.y ^ (tm & cw.y);
+    s.z = blk.z ^ (tm & cw.z);
+    s.w = blk.w ^ (tm & cw.w);
+    t = tn;
+  }
+  v ^= (s.x >> 2) ^ (t & uint32_t(vcw >> k));
+  return v & 1u;
+}
+
+// Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^x) + t*V_CW) + leaf
+// term into acc (the caller applies the party sign (-1)^b once).
+// root: uint4 root[n]; cw level i at root[(1+i)*n]; vcw: u64 [(k+1)][P][n].
+template <int P, class AES>
+FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root,
+                                const uint64_t *vcw, uint64_t n, uint64_t *acc, const AES &aes) {
+  constexpr int V = (P + 1) / 2;
+  uint4 s = root[0];
+  uint32_t t = b;
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t x = (u >> (k - 1 - i)) & 1u;
+    const uint4 cw = root[(1 + uint64_t(i)) * n];
+    uint64_t vc[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) vc[q] = vcw[(uint64_t(i) * P + q) * n];
+    const uint4 blk = mmo(s, x, aes);
+    uint64_t conv[2 * V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const uint4 c = mmo(s, 2u + x * V + q, aes);
+      conv[2 * q] = lo64(c);
+      conv[2 * q + 1] = hi64(c);
+    }
+    const uint64_t tm64 = 0ull - uint64_t(t);
+#pragma unroll
+    for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vc[q] & tm64);
+    const uint32_t tm = 0u - t;
+    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
+    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
+    s.y = blk.y ^ (tm & cw.y);
+    s.z = blk.z ^ (tm & cw.z);
+    s.w = blk.w ^ (tm & cw.w);
+    t = tn;
+  }
+  uint64_t conv[2 * V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const uint4 c = mmo(s, 2u + q, aes);
+    conv[2 * q] = lo64(c);
+    conv[2 * q + 1] = hi64(c);
+  }
+  const uint64_t tm64 = 0ull - uint64_t(t);
+#pragma unroll
+  for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vcw[(uint64_t(k) * P + q) * n] & tm64);
+}
+
+// ---------------------------------------------------------------------------
+// DCF Gen (both parties in lockstep).  Writes root, per-level correction words
+// (identical for both parties) and the V_CW words into both key sections.
+// ---------------------------------------------------------------------------
+
+template <class AES>
+FFSS_CORE void dcf_bit_gen(uint32_t k, uint32_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
+                           uint64_t *vcw0, uint64_t *vcw1, uint64_t n, const AES &aes) {
+  q0[0] = s0;
+  q1[0] = s1;
+  uint32_t t0 = 0, t1 = 1, va = 0;
+  uint64_t vbits = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
+    const uint4 L0 = mmo(s0, 0, aes), R0 = mmo(s0, 1, aes);
+    const uint4 L1 = mmo(s1, 0, aes), R1 = mmo(s1, 1, aes);
+    const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;   // Lose side
+    const uint4 ke0 = a ? R0 : L0, ke1 = a ? R1 : L1;   // Keep side
+    uint4 scw = xor4(lo0, lo1);
+    scw.x &= ~3u;
+    const uint32_t tl = (L0.x ^ L1.x ^ a ^ 1u) & 1u;
+    const uint32_t tr = (R0.x ^ R1.x ^ a) & 1u;
+    // Lose = L exactly when a = 1; then beta = 1 enters the correction.
+    const uint32_t vc = ((lo1.x >> 1) ^ (lo0.x >> 1) ^ va ^ a) & 1u;
+    va = (va ^ (ke1.x >> 1) ^ (ke0.x >> 1) ^ vc) & 1u;
+    uint4 cw = scw;
+    cw.x |= tl | (tr << 1);
+    q0[(1 + uint64_t(i)) * n] = cw;
+    q1[(1 + uint64_t(i)) * n] = cw;
+    vbits |= uint64_t(vc) << i;
+    const uint32_t tk = a ? tr : tl;
+    const uint32_t m0 = 0u - t0, m1 = 0u - t1;
+    uint4 ns0 = xor4(ke0, and4(scw, m0));
+    uint4 ns1 = xor4(ke1, and4(scw, m1));
+    const uint32_t nt0 = (ke0.x ^ (t0 & tk)) & 1u;
+    const uint32_t nt1 = (ke1.x ^ (t1 & tk)) & 1u;
+    ns0.x &= ~3u;
+    ns1.x &= ~3u;
+    s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
+  }
+  vbits |= uint64_t(((s1.x >> 2) ^ (s0.x >> 2) ^ va) & 1u) << k;
+  vcw0[0] = vbits;
+  vcw1[0] = vbits;
+}
+
+template <int P, class AES>
+FFSS_CORE void conv_blocks(uint4 s, uint32_t j0, uint64_t *out, const AES &aes) {
+  constexpr int V = (P + 1) / 2;
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const uint4 c = mmo(s, j0 + q, aes);
+    out[2 * q] = lo64(c);
+    if (2 * q + 1 < P) out[2 * q + 1] = hi64(c);
+  }
+}
+
+template <int P, class AES>
+FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
+                           uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t n,
+                           const AES &aes) {
+  constexpr uint32_t V = (P + 1) / 2;
+  l0[0] = s0;
+  l1[0] = s1;
+  uint32_t t0 = 0, t1 = 1;
+  uint64_t va[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) va[q] = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
+    const uint32_t keep = a, lose = 1u - a;
+    const uint4 L0 = mmo(s0, 0, aes), R0 = mmo(s0, 1, aes);
+    const uint4 L1 = mmo(s1, 0, aes), R1 = mmo(s1, 1, aes);
+    uint64_t cl0[P + 1], cl1[P + 1], ck0[P + 1], ck1[P + 1];
+    conv_blocks<P>(s0, 2u + lose * V, cl0, aes);
+    conv_blocks<P>(s1, 2u + lose * V, cl1, aes);
+    conv_blocks<P>(s0, 2u + keep * V, ck0, aes);
+    conv_blocks<P>(s1, 2u + keep * V, ck1, aes);
+    const bool neg = t1 != 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      uint64_t d = cl1[q] - cl0[q] - va[q];
+      if (lose == 0) d += beta[q];
+      const uint64_t vc = neg ? 0ull - d : d;
+      va[q] = va[q] - ck1[q] + ck0[q] + (neg ? 0ull - vc : vc);
+      vcw0[(uint64_t(i) * P + q) * n] = vc;
+      vcw1[(uint64_t(i) * P + q) * n] = vc;
+    }
+    const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;
+    const uint4 ke0 = a ? R0 : L0, ke1 = a ? R1 : L1;
+    uint4 scw = xor4(lo0, lo1);
+    scw.x &= ~3u;
+    const uint32_t tl = (L0.x ^ L1.x ^ a ^ 1u) & 1u;
+    const uint32_t tr = (R0.x ^ R1.x ^ a) & 1u;
+    uint4 cw = scw;
+    cw.x |= tl | (tr << 1);
+    l0[(1 + uint64_t(i)) * n] = cw;
+    l1[(1 + uint64_t(i)) * n] = cw;
+    const uint32_t tk = a ? tr : tl;
+    const uint32_t m0 = 0u - t0, m1 = 0u - t1;
+    uint4 ns0 = xor4(ke0, and4(scw, m0));
+    uint4 ns1 = xor4(ke1, and4(scw, m1));
+    const uint32_t nt0 = (ke0.x ^ (t0 & tk)) & 1u;
+    const uint32_t nt1 = (ke1.x ^ (t1 & tk)) & 1u;
+    ns0.x &= ~3u;
+    ns1.x &= ~3u;
+    s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
+  }
+  uint64_t f0[P + 1], f1[P + 1];
+  conv_blocks<P>(s0, 2u, f0, aes);
+  conv_blocks<P>(s1, 2u, f1, aes);
+  const bool neg = t1 != 0;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const uint64_t d = f1[q] - f0[q] - va[q];
+    const uint64_t cw = neg ? 0ull - d : d;
+    vcw0[(uint64_t(k) * P + q) * n] = cw;
+    vcw1[(uint64_t(k) * P + q) * n] = cw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lookup instance of one element (App. F step 1).  The translated starts
+// s_i = (alpha_i + r_k) mod 2^k are a rotation of the sorted alpha: the w
+// starts with alpha_i + r_k < 2^k keep their order and the m - w wrapped ones
+// precede them, so the sorting permutation is pi(j) = (w + j) mod m and no
+// sort is needed.  Writes B[0..M], ord[0..M-1] for M = m + 1 (m < 2^k).
+// ---------------------------------------------------------------------------
+FFSS_CORE void lookup_boundaries(const DevSpec &S, uint64_t r_in, uint64_t *B, uint32_t *ord) {
+  const uint32_t m = S.m;
+  const uint64_t N = uint64_t(1) << S.k;
+  const uint64_t rk = r_in & (N - 1);
+  uint32_t w = 0;
+  for (uint32_t i = 0; i < m; ++i) w += (S.alpha[i] + rk < N) ? 1u : 0u;
+  const uint32_t pi0 = w % m;   // pi(0)
+  const uint64_t beta0 = (S.alpha[pi0] + rk) & (N - 1);
+  if (beta0 == 0) {
+    // no interval wraps: m intervals, pad by the dummy split at the first
+    // gap of length >= 2 (delta = B_{j*} + 1), duplicating its payload
+    uint32_t nb = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+      const uint32_t pj = (pi0 + j) % m;
+      const uint64_t bj = (S.alpha[pj] + rk) & (N - 1);
+      B[nb] = bj;
+      ord[nb] = pj;
+      ++nb;
+    }
+    B[nb] = N;
+    // find j*: smallest j with B[j+1] - B[j] >= 2
+    uint32_t js = 0;
+    while (B[js + 1] - B[js] < 2) ++js;
+    for (uint32_t j = m; j > js; --j) B[j + 1] = B[j];
+    B[js + 1] = B[js] + 1;
+    for (uint32_t j = m - 1; j > js; --j) ord[j + 1] = ord[j];
+    ord[js + 1] = ord[js];
+  } else {
+    // exactly one interval wraps; its payload sits on both sides of 0
+    B[0] = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+      const uint32_t pj = (pi0 + j) % m;
+      B[j + 1] = (S.alpha[pj] + rk) & (N - 1);
+      ord[j + 1] = pj;
+    }
+    B[m + 1] = N;
+    ord[0] = (pi0 + m - 1) % m;
+  }
+}
+
+}  // namespace ffss

@@ -1,0 +1,588 @@
+// C ABI of the FuseFSS CUDA path (declared in include/fusefss.h).
+//
+// Host responsibilities: AES tables and key schedules, the public part of the
+// compilation of an operator specification (query list, lookup shape, key
+// layout; App. F), argument checking, one-time key bookkeeping (Sec. 3.1) and
+// kernel launches.  Every per-element step runs in the kernels of
+// kernels.cuh; there is no host or CPU fallback for any of them.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fusefss.h"
+#include "kernels.cuh"
+
+using namespace ffss;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess) return fail(FFSS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+
+extern "C" const char *ffss_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// AES-128 tables and key schedule (FIPS-197), computed here from GF(2^8)
+// logarithms: 3 generates the multiplicative group, so a^-1 = 3^(255 - log3 a).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct AesTables {
+  uint8_t sbox[256];
+  uint32_t t0[256];
+};
+
+uint8_t xtime(uint8_t a) { return uint8_t((a << 1) ^ ((a >> 7) * 0x1B)); }
+uint8_t rotl8(uint8_t a, int s) { return uint8_t((a << s) | (a >> (8 - s))); }
+
+AesTables make_tables() {
+  AesTables T;
+  uint8_t ex[256], lg[256] = {0};
+  uint8_t a = 1;
+  for (int i = 0; i < 255; ++i) {
+    ex[i] = a;
+    lg[a] = uint8_t(i);
+    a = uint8_t(a ^ xtime(a));   // multiply by 3
+  }
+  for (int v = 0; v < 256; ++v) {
+    const uint8_t inv = v == 0 ? 0 : ex[(255 - lg[v]) % 255];
+    T.sbox[v] = uint8_t(inv ^ rotl8(inv, 1) ^ rotl8(inv, 2) ^ rotl8(inv, 3) ^ rotl8(inv, 4) ^ 0x63);
+  }
+  for (int v = 0; v < 256; ++v) {
+    const uint8_t s = T.sbox[v], s2 = xtime(s), s3 = uint8_t(s2 ^ s);
+    T.t0[v] = uint32_t(s2) | (uint32_t(s) << 8) | (uint32_t(s) << 16) | (uint32_t(s3) << 24);
+  }
+  return T;
+}
+
+const AesTables &tables() {
+  static const AesTables T = make_tables();
+  return T;
+}
+
+// 44 round-key words, little endian (byte j of word i = key byte 4i + j).
+void key_schedule(const uint8_t key[16], uint32_t w[44]) {
+  const AesTables &T = tables();
+  for (int i = 0; i < 4; ++i)
+    w[i] = uint32_t(key[4 * i]) | (uint32_t(key[4 * i + 1]) << 8) | (uint32_t(key[4 * i + 2]) << 16) |
+           (uint32_t(key[4 * i + 3]) << 24);
+  uint8_t rc = 1;
+  for (int i = 4; i < 44; ++i) {
+    uint32_t t = w[i - 1];
+    if (i % 4 == 0) {
+      t = (t >> 8) | (t << 24);   // RotWord on little-endian bytes
+      t = uint32_t(T.sbox[t & 0xFF]) | (uint32_t(T.sbox[(t >> 8) & 0xFF]) << 8) |
+          (uint32_t(T.sbox[(t >> 16) & 0xFF]) << 16) | (uint32_t(T.sbox[t >> 24]) << 24);
+      t ^= rc;
+      rc = xtime(rc);
+    }
+    w[i] = w[i - 4] ^ t;
+  }
+}
+
+const uint8_t kDcfKey[16] = {'F', 'u', 's', 'e', 'F', 'S', 'S', '-', 'D', 'C', 'F', '-', 'A', 'E', 'S', '!'};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+
+struct ffss_ctx {
+  int device;
+  int sm_count;
+  uint32_t *t0_dev;
+};
+
+struct ffss_spec {
+  ffss_ctx *ctx;
+  DevSpec host;
+  DevSpec *dev;
+  ffss_shape shape;
+};
+
+struct ffss_keys {
+  const ffss_spec *spec;
+  uint64_t n;
+  int party;
+  char *buf;
+  uint64_t bytes;
+  int generated;
+  int used;        // bit 0: comparison keys consumed, bit 1: lookup keys consumed
+};
+
+template <class K>
+static int set_smem(K kernel, size_t bytes) {
+  CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  return FFSS_OK;
+}
+
+extern "C" int ffss_ctx_create(int device, ffss_ctx **out) {
+  if (!out) return fail(FFSS_ERR_INVALID, "ffss_ctx_create: out is NULL");
+  CUDA_TRY(cudaSetDevice(device));
+  ffss_ctx *c = new ffss_ctx();
+  c->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->t0_dev, sizeof(uint32_t) * 256);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->t0_dev, tables().t0, sizeof(uint32_t) * 256, cudaMemcpyHostToDevice);
+  uint32_t rk[44];
+  key_schedule(kDcfKey, rk);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rk_dcf, rk, sizeof(rk));
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(FFSS_ERR_CUDA, "ffss_ctx_create: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_ctx_destroy(ffss_ctx *ctx) {
+  if (!ctx) return FFSS_OK;
+  cudaSetDevice(ctx->device);
+  cudaFree(ctx->t0_dev);
+  delete ctx;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// specification compiler (public part, App. F steps 2-4)
+// ---------------------------------------------------------------------------
+
+extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_spec **out) {
+  if (!d || !out) return fail(FFSS_ERR_INVALID, "ffss_spec_compile: NULL argument");
+  if (d->k < 1 || d->k > FFSS_MAX_K) return fail(FFSS_ERR_UNSUPPORTED, "k=%u outside 1..%d", d->k, FFSS_MAX_K);
+  const uint64_t N = uint64_t(1) << d->k;
+  if (d->m < 1 || d->m > FFSS_MAX_M) return fail(FFSS_ERR_UNSUPPORTED, "m=%u outside 1..%d", d->m, FFSS_MAX_M);
+  if (uint64_t(d->m) >= N) return fail(FFSS_ERR_UNSUPPORTED, "m=%u must be < 2^k", d->m);
+  if (d->n_out < 1) return fail(FFSS_ERR_INVALID, "n_out must be >= 1");
+  const uint32_t p = d->n_out * (d->degree + 1);
+  if (p > FFSS_MAX_P) return fail(FFSS_ERR_UNSUPPORTED, "payload p=%u > %d", p, FFSS_MAX_P);
+  if (!d->alpha || !d->coeff) return fail(FFSS_ERR_INVALID, "alpha/coeff NULL");
+  if (d->alpha[0] != 0 || d->alpha[d->m] != N) return fail(FFSS_ERR_INVALID, "alpha must run from 0 to 2^k");
+  for (uint32_t i = 0; i < d->m; ++i)
+    if (!(d->alpha[i] < d->alpha[i + 1])) return fail(FFSS_ERR_INVALID, "alpha not strictly increasing at %u", i);
+
+  DevSpec S;
+  memset(&S, 0, sizeof(S));
+  S.k = d->k; S.m = d->m; S.d = d->degree; S.r = d->n_out; S.p = p;
+  S.V = (p + 1) / 2;
+  S.M = d->m == 1 ? 1 : d->m + 1;
+  for (uint32_t i = 0; i <= d->m; ++i) S.alpha[i] = d->alpha[i];
+  for (uint32_t i = 0; i < d->m * p; ++i) S.coeff[i] = d->coeff[i];
+
+  // Boolean outputs as (f, c, gamma, negate)
+  struct B { uint32_t f; uint64_t c, g; uint32_t neg; };
+  std::vector<B> outs;
+  if (d->partition_bits)
+    for (uint32_t i = 1; i < d->m; ++i) outs.push_back({d->k, 0, d->alpha[i], 0});
+  for (uint32_t i = 0; i < d->n_pred; ++i) {
+    const ffss_pred_desc &q = d->preds[i];
+    if (q.f < 1 || q.f > d->k) return fail(FFSS_ERR_INVALID, "pred %u: f=%u outside 1..k", i, q.f);
+    const uint64_t Nf = uint64_t(1) << q.f;
+    if (q.c >= Nf || q.gamma > Nf) return fail(FFSS_ERR_INVALID, "pred %u: c or gamma out of range", i);
+    outs.push_back({q.f, q.c, q.gamma, q.negate & 1u});
+  }
+  if (outs.size() > FFSS_MAX_BOOL) return fail(FFSS_ERR_UNSUPPORTED, "%zu Boolean outputs > %d", outs.size(), FFSS_MAX_BOOL);
+  S.n_bool = uint32_t(outs.size());
+  // distinct non-sentinel predicates; sentinels C_0 = 0, C_{2^f} = 1 are constants
+  for (uint32_t o = 0; o < S.n_bool; ++o) {
+    const B &q = outs[o];
+    if (q.neg) S.out_neg |= 1u << o;
+    if (q.g == 0 || q.g == (uint64_t(1) << q.f)) {
+      S.out_prim[o] = -1;
+      if (q.g != 0) S.out_const |= 1u << o;
+      continue;
+    }
+    int found = -1;
+    for (uint32_t j = 0; j < S.n_prim; ++j)
+      if (S.prim_f[j] == q.f && S.prim_c[j] == q.c && S.prim_gamma[j] == q.g) found = int(j);
+    if (found < 0) {
+      found = int(S.n_prim);
+      S.prim_f[S.n_prim] = q.f;
+      S.prim_c[S.n_prim] = q.c;
+      S.prim_gamma[S.n_prim] = q.g;
+      ++S.n_prim;
+    }
+    S.out_prim[o] = found;
+  }
+  // query list: views in order of first appearance; per view the r-atom, then
+  // one theta atom per predicate of that view
+  std::vector<std::pair<uint32_t, uint64_t>> views;
+  for (uint32_t j = 0; j < S.n_prim; ++j) {
+    bool seen = false;
+    for (auto &v : views) seen |= (v.first == S.prim_f[j] && v.second == S.prim_c[j]);
+    if (!seen) views.push_back({S.prim_f[j], S.prim_c[j]});
+  }
+  S.n_views = uint32_t(views.size());
+  uint32_t T = 0;
+  for (auto &v : views) {
+    if (T >= FFSS_MAX_T) return fail(FFSS_ERR_UNSUPPORTED, "more than %d queries", FFSS_MAX_T);
+    const uint32_t qr = T;
+    S.q_f[T] = v.first; S.q_c[T] = v.second; S.q_prim[T] = -1; ++T;
+    for (uint32_t j = 0; j < S.n_prim; ++j) {
+      if (S.prim_f[j] != v.first || S.prim_c[j] != v.second) continue;
+      if (T >= FFSS_MAX_T) return fail(FFSS_ERR_UNSUPPORTED, "more than %d queries", FFSS_MAX_T);
+      S.q_f[T] = v.first; S.q_c[T] = v.second; S.q_prim[T] = int32_t(j);
+      S.prim_qtheta[j] = T;
+      S.prim_qr[j] = qr;
+      ++T;
+    }
+  }
+  S.T = T;
+  S.base_roots = kDrawVlast + p;
+  S.base_triples = S.base_roots + 2 * (S.T + S.M - 1);
+
+  ffss_spec *sp = new ffss_spec();
+  sp->ctx = ctx;
+  sp->host = S;
+  sp->dev = nullptr;
+  if (ctx) {   // a NULL context gives a host-only spec (shape and size queries)
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&sp->dev, sizeof(DevSpec));
+    if (e == cudaSuccess) e = cudaMemcpy(sp->dev, &S, sizeof(DevSpec), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (sp->dev) cudaFree(sp->dev);
+      delete sp;
+      return fail(FFSS_ERR_CUDA, "ffss_spec_compile: %s", cudaGetErrorString(e));
+    }
+  }
+  ffss_shape &sh = sp->shape;
+  sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
+  sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.d * S.r; sh.n_bool = S.n_bool;
+  sh.n_views = S.n_views;
+  sh.key_bytes_per_elem = key_bytes_per_elem(S);
+  sh.comm_bytes_per_elem = 8 + 16ull * S.d * S.r;
+  sh.aes_per_elem = aes_per_elem(S);
+  *out = sp;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_spec_shape(const ffss_spec *spec, ffss_shape *out) {
+  if (!spec || !out) return fail(FFSS_ERR_INVALID, "ffss_spec_shape: NULL argument");
+  *out = spec->shape;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_spec_free(ffss_spec *spec) {
+  if (!spec) return FFSS_OK;
+  if (spec->ctx && spec->dev) {
+    cudaSetDevice(spec->ctx->device);
+    cudaFree(spec->dev);
+  }
+  delete spec;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+
+extern "C" int ffss_keys_size(const ffss_spec *spec, uint64_t n, uint64_t *bytes) {
+  if (!spec || !bytes) return fail(FFSS_ERR_INVALID, "ffss_keys_size: NULL argument");
+  *bytes = make_layout(spec->host, n).total;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_keys_bind(const ffss_spec *spec, uint64_t n, int party, void *buf, uint64_t bytes,
+                              int state, ffss_keys **out) {
+  if (!spec || !out) return fail(FFSS_ERR_INVALID, "ffss_keys_bind: NULL argument");
+  if (party != 0 && party != 1) return fail(FFSS_ERR_PARTY, "party must be 0 or 1");
+  if (n == 0) return fail(FFSS_ERR_SHAPE, "n must be >= 1");
+  if (!buf) return fail(FFSS_ERR_INVALID, "key buffer is NULL");
+  if (reinterpret_cast<uintptr_t>(buf) % 256) return fail(FFSS_ERR_INVALID, "key buffer not 256-byte aligned");
+  const uint64_t need = make_layout(spec->host, n).total;
+  if (bytes < need) return fail(FFSS_ERR_SHAPE, "key buffer %llu B < %llu B needed",
+                                (unsigned long long)bytes, (unsigned long long)need);
+  if (state != FFSS_KEYS_EMPTY && state != FFSS_KEYS_FILLED) return fail(FFSS_ERR_INVALID, "bad key state");
+  ffss_keys *k = new ffss_keys();
+  k->spec = spec; k->n = n; k->party = party; k->buf = static_cast<char *>(buf); k->bytes = bytes;
+  k->generated = state == FFSS_KEYS_FILLED;
+  k->used = 0;
+  *out = k;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_keys_release(ffss_keys *k) {
+  delete k;
+  return FFSS_OK;
+}
+
+static int check_device_spec(const ffss_ctx *ctx, const ffss_spec *spec) {
+  if (!spec->dev || spec->ctx != ctx)
+    return fail(FFSS_ERR_INVALID, "spec was not compiled with this context (host-only spec?)");
+  return FFSS_OK;
+}
+
+static int check_keys(const ffss_spec *spec, const ffss_keys *k, int party, uint64_t n, int need_mask) {
+  if (!k) return fail(FFSS_ERR_INVALID, "keys handle is NULL");
+  if (k->spec != spec) return fail(FFSS_ERR_SHAPE, "keys were bound to another spec");
+  if (k->party != party) return fail(FFSS_ERR_PARTY, "keys belong to party %d, not %d", k->party, party);
+  if (k->n != n) return fail(FFSS_ERR_SHAPE, "keys hold %llu elements, call has %llu",
+                             (unsigned long long)k->n, (unsigned long long)n);
+  if (!k->generated) return fail(FFSS_ERR_SHAPE, "keys were never generated");
+  if (k->used & need_mask) return fail(FFSS_ERR_SHAPE, "keys already consumed (one-time material)");
+  return FFSS_OK;
+}
+
+static int grid_for(const ffss_ctx *ctx, uint64_t work_items, uint32_t per_block) {
+  const uint64_t blocks = (work_items + per_block - 1) / per_block;
+  const uint64_t cap = uint64_t(ctx->sm_count);   // one 128 KB-table CTA per SM
+  return int(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+static size_t spec_smem() { return (sizeof(DevSpec) + 15) & ~size_t(15); }
+
+// ---------------------------------------------------------------------------
+// dealer
+// ---------------------------------------------------------------------------
+
+template <int P>
+static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t st) {
+  const size_t smem = kTabBytes + spec_smem() + 44 * 4;
+  static std::once_flag once;
+  int rc = FFSS_OK;
+  std::call_once(once, [&] { rc = set_smem(keygen_kernel<P>, smem); });
+  if (rc) return rc;
+  keygen_kernel<P><<<grid_for(ctx, A.n, 512), 512, smem, st>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                           uint64_t n, const uint64_t *x_plain, ffss_keys *k0, ffss_keys *k1,
+                           uint64_t *x0, uint64_t *x1, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !spec || !seed || !k0 || !k1) return fail(FFSS_ERR_INVALID, "ffss_keygen: NULL argument");
+  if (k0->party != 0 || k1->party != 1) return fail(FFSS_ERR_PARTY, "ffss_keygen: k0 must be party 0, k1 party 1");
+  if (k0->spec != spec || k1->spec != spec || k0->n != n || k1->n != n)
+    return fail(FFSS_ERR_SHAPE, "ffss_keygen: key handles do not match spec / n");
+  if (x_plain && (!x0 || !x1)) return fail(FFSS_ERR_INVALID, "ffss_keygen: x0/x1 needed with x_plain");
+  if (int rc0 = check_device_spec(ctx, spec)) return rc0;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  KeygenArgs A;
+  memset(&A, 0, sizeof(A));
+  A.spec = spec->dev;
+  A.L = make_layout(spec->host, n);
+  A.k0 = k0->buf; A.k1 = k1->buf;
+  A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
+  A.n = n; A.call_id = call_id;
+  key_schedule(seed, A.rk.w);
+  A.t0 = ctx->t0_dev;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  switch (spec->host.p) {
+    case 1: rc = launch_keygen<1>(ctx, A, st); break;
+    case 2: rc = launch_keygen<2>(ctx, A, st); break;
+    case 3: rc = launch_keygen<3>(ctx, A, st); break;
+    case 4: rc = launch_keygen<4>(ctx, A, st); break;
+    default: return fail(FFSS_ERR_UNSUPPORTED, "payload p=%u", spec->host.p);
+  }
+  if (rc) return rc;
+  k0->generated = k1->generated = 1;
+  k0->used = k1->used = 0;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// single-party FSS calls
+// ---------------------------------------------------------------------------
+
+extern "C" int ffss_eval_pred(ffss_ctx *ctx, const ffss_spec *spec, int party, ffss_keys *keys,
+                              const uint64_t *xhat, uint64_t n, uint32_t *atoms, uint32_t *bits,
+                              void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !spec || !xhat) return fail(FFSS_ERR_INVALID, "ffss_eval_pred: NULL argument");
+  if (party != 0 && party != 1) return fail(FFSS_ERR_PARTY, "party must be 0 or 1");
+  int rc = check_device_spec(ctx, spec);
+  if (!rc) rc = check_keys(spec, keys, party, n, 1);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  PartyArgs A;
+  memset(&A, 0, sizeof(A));
+  A.spec = spec->dev; A.L = make_layout(spec->host, n); A.kb = keys->buf; A.party = uint32_t(party);
+  A.xhat = xhat; A.atoms = atoms; A.bits = bits; A.n = n; A.t0 = ctx->t0_dev;
+  const size_t smem = kTabBytes + spec_smem();
+  static std::once_flag once;
+  std::call_once(once, [&] { rc = set_smem(pred_kernel, smem); });
+  if (rc) return rc;
+  pred_kernel<<<grid_for(ctx, n, 512), 512, smem, static_cast<cudaStream_t>(stream)>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  keys->used |= 1;
+  return FFSS_OK;
+}
+
+template <int P>
+static int launch_lut(const ffss_ctx *ctx, const PartyArgs &A, cudaStream_t st) {
+  const size_t smem = kTabBytes + spec_smem();
+  static std::once_flag once;
+  int rc = FFSS_OK;
+  std::call_once(once, [&] { rc = set_smem(lut_kernel<P>, smem); });
+  if (rc) return rc;
+  lut_kernel<P><<<grid_for(ctx, A.n, 512), 512, smem, st>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_eval_lut(ffss_ctx *ctx, const ffss_spec *spec, int party, ffss_keys *keys,
+                             const uint64_t *xhat, uint64_t n, uint64_t *payload, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !spec || !xhat || !payload) return fail(FFSS_ERR_INVALID, "ffss_eval_lut: NULL argument");
+  if (party != 0 && party != 1) return fail(FFSS_ERR_PARTY, "party must be 0 or 1");
+  int rc = check_device_spec(ctx, spec);
+  if (!rc) rc = check_keys(spec, keys, party, n, 2);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  PartyArgs A;
+  memset(&A, 0, sizeof(A));
+  A.spec = spec->dev; A.L = make_layout(spec->host, n); A.kb = keys->buf; A.party = uint32_t(party);
+  A.xhat = xhat; A.payload = payload; A.n = n; A.t0 = ctx->t0_dev;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (spec->host.p) {
+    case 1: rc = launch_lut<1>(ctx, A, st); break;
+    case 2: rc = launch_lut<2>(ctx, A, st); break;
+    case 3: rc = launch_lut<3>(ctx, A, st); break;
+    case 4: rc = launch_lut<4>(ctx, A, st); break;
+    default: return fail(FFSS_ERR_UNSUPPORTED, "payload p=%u", spec->host.p);
+  }
+  if (rc) return rc;
+  keys->used |= 2;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the fused two-party gate
+// ---------------------------------------------------------------------------
+
+constexpr int kGateE = 256;   // elements per tile (2 * kGateE threads per CTA)
+
+template <int R, int D>
+static int launch_gate(const ffss_ctx *ctx, const GateArgs &A, cudaStream_t st) {
+  const size_t smem = kTabBytes + spec_smem() + 2ull * kGateE * R * 16;
+  static std::once_flag once;
+  int rc = FFSS_OK;
+  std::call_once(once, [&] { rc = set_smem(gate_kernel<R, D, kGateE>, smem); });
+  if (rc) return rc;
+  gate_kernel<R, D, kGateE><<<grid_for(ctx, A.n, kGateE), 2 * kGateE, smem, st>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
+                              const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0,
+                              uint64_t *y1, uint32_t *z0, uint32_t *z1, uint64_t *comm, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !spec || !x0 || !x1 || !y0 || !y1 || !z0 || !z1)
+    return fail(FFSS_ERR_INVALID, "ffss_eval_pair: NULL argument");
+  int rc = check_device_spec(ctx, spec);
+  if (!rc) rc = check_keys(spec, k0, 0, n, 3);
+  if (!rc) rc = check_keys(spec, k1, 1, n, 3);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  GateArgs A;
+  memset(&A, 0, sizeof(A));
+  A.spec = spec->dev; A.L = make_layout(spec->host, n);
+  A.k0 = k0->buf; A.k1 = k1->buf; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
+  A.comm = reinterpret_cast<unsigned long long *>(comm);
+  A.n = n; A.t0 = ctx->t0_dev;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t R = spec->host.r, D = spec->host.d;
+  if (R == 1 && D == 0) rc = launch_gate<1, 0>(ctx, A, st);
+  else if (R == 1 && D == 1) rc = launch_gate<1, 1>(ctx, A, st);
+  else if (R == 1 && D == 2) rc = launch_gate<1, 2>(ctx, A, st);
+  else if (R == 1 && D == 3) rc = launch_gate<1, 3>(ctx, A, st);
+  else if (R == 2 && D == 0) rc = launch_gate<2, 0>(ctx, A, st);
+  else if (R == 2 && D == 1) rc = launch_gate<2, 1>(ctx, A, st);
+  else if (R == 3 && D == 0) rc = launch_gate<3, 0>(ctx, A, st);
+  else if (R == 4 && D == 0) rc = launch_gate<4, 0>(ctx, A, st);
+  else return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
+  if (rc) return rc;
+  k0->used |= 3;
+  k1->used |= 3;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0,
+                                const uint32_t *z1, uint64_t n, uint32_t n_out, uint64_t *y, uint32_t *z,
+                                void *stream) {
+  if ((y && (!y0 || !y1)) || (z && (!z0 || !z1))) return fail(FFSS_ERR_INVALID, "ffss_reconstruct: NULL share");
+  if (n == 0) return FFSS_OK;
+  if (n_out < 1) return fail(FFSS_ERR_INVALID, "n_out must be >= 1");
+  const uint64_t work = n * n_out;
+  const int grid = int((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
+  reconstruct_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(y0, y1, z0, z1, n, n_out, y, z);
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// micro-benchmarks (measurement support for the roofline; synchronizing)
+// ---------------------------------------------------------------------------
+
+extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms) {
+  if (!ctx || !rate) return fail(FFSS_ERR_INVALID, "ffss_microbench: NULL argument");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  double work = 0;
+  void *out = nullptr;
+  int rc = FFSS_OK;
+  if (which == 0) {
+    const int blocks = ctx->sm_count * 2, threads = 1024;
+    CUDA_TRY(cudaMalloc(&out, sizeof(uint32_t) * blocks * threads));
+    mb_lop3_kernel<<<blocks, threads>>>(static_cast<uint32_t *>(out), 16);   // warm-up
+    CUDA_TRY(cudaEventRecord(a));
+    mb_lop3_kernel<<<blocks, threads>>>(static_cast<uint32_t *>(out), iters);
+    CUDA_TRY(cudaEventRecord(b));
+    work = double(blocks) * threads * iters * 16.0 * 8.0;
+  } else if (which == 1) {
+    const int blocks = ctx->sm_count, threads = 512;
+    const size_t smem = kTabBytes;
+    static std::once_flag once;
+    std::call_once(once, [&] { rc = set_smem(mb_aes_kernel, smem); });
+    if (rc) return rc;
+    CUDA_TRY(cudaMalloc(&out, sizeof(uint4) * blocks * threads));
+    mb_aes_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), 4);
+    CUDA_TRY(cudaEventRecord(a));
+    mb_aes_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
+    CUDA_TRY(cudaEventRecord(b));
+    work = double(blocks) * threads * iters;
+  } else {
+    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1 (AES)");
+  }
+  cudaError_t e = cudaEventSynchronize(b);
+  float t = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  cudaFree(out);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "ffss_microbench: %s", cudaGetErrorString(e));
+  *rate = work / (double(t) * 1e-3);
+  if (ms) *ms = t;
+  return FFSS_OK;
+}

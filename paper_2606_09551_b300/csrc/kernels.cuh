@@ -1,0 +1,440 @@
+// CUDA kernels of the FuseFSS online path and its dealer (sm_103a).
+//
+//  keygen_kernel<P>      GPU dealer: one thread per element, both parties' keys.
+//  gate_kernel<R,D,E>    the whole two-party gate, both parties of a tile of E
+//                        elements in one CTA, exchanges through shared-memory
+//                        outboxes (the per-party message buffers).
+//  pred_kernel / lut_kernel<P>   single-party FSS calls (Eval_b).
+//  reconstruct_kernel    y = y0 + y1, z = z0 ^ z1.
+//
+// All kernels are persistent-style grid-stride loops sized to the SM count;
+// each CTA stages the AES T-tables (128 KB) and the compiled spec in shared
+// memory once.  No kernel waits on another CTA or on a flag.
+#pragma once
+#include "fss_core.cuh"
+
+namespace ffss {
+
+struct RkParam { uint32_t w[44]; };
+
+struct KeygenArgs {
+  const DevSpec *spec;
+  KeyLayout L;
+  char *k0, *k1;
+  const uint64_t *x_plain;
+  uint64_t *x0, *x1;
+  uint64_t n;
+  uint32_t call_id;
+  RkParam rk;          // AES-128 key schedule of the run seed (dealer PRG)
+  const uint32_t *t0;  // global T-table 0
+};
+
+struct GateArgs {
+  const DevSpec *spec;
+  KeyLayout L;
+  const char *k0, *k1;
+  const uint64_t *x0, *x1;
+  uint64_t *y0, *y1;
+  uint32_t *z0, *z1;
+  unsigned long long *comm;   // [2] bytes sent by party 0 / 1, may be null
+  uint64_t n;
+  const uint32_t *t0;
+};
+
+struct PartyArgs {
+  const DevSpec *spec;
+  KeyLayout L;
+  const char *kb;
+  uint32_t party;
+  const uint64_t *xhat;
+  uint32_t *atoms, *bits;    // pred outputs (may be null)
+  uint64_t *payload;         // lut output
+  uint64_t n;
+  const uint32_t *t0;
+};
+
+struct RkDcf {
+  __device__ __forceinline__ uint32_t operator[](int i) const { return c_rk_dcf[i]; }
+};
+
+// AES_K for the DCF PRG, inlined (online path).
+struct AesDcfInline {
+  Tab tb;
+  __device__ __forceinline__ uint4 operator()(uint4 in) const { return aes128(in, RkDcf(), tb); }
+};
+
+// Out-of-line AES-128 calls for the dealer: one copy of the round code per
+// kernel instead of one per call site.
+__device__ __noinline__ uint4 aes_dcf_call(uint4 in, const char *base, uint32_t lane4) {
+  return aes128(in, RkDcf(), Tab{base, lane4});
+}
+__device__ __noinline__ uint4 aes_rk_call(uint4 in, const uint32_t *rk, const char *base, uint32_t lane4) {
+  return aes128(in, rk, Tab{base, lane4});
+}
+struct AesDcfCall {
+  Tab tb;
+  __device__ __forceinline__ uint4 operator()(uint4 in) const { return aes_dcf_call(in, tb.base, tb.lane4); }
+};
+
+// Stage the four rotated T-tables, 32 lane copies each, and the spec.
+__device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, const uint32_t *t0,
+                                             const DevSpec *spec) {
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
+    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
+    const uint32_t v = t0[e];
+    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+  }
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(spec);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(sspec);
+  for (uint32_t i = threadIdx.x; i < sizeof(DevSpec) / 4; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// party-local steps (party b sees only its own key material kb)
+// ---------------------------------------------------------------------------
+
+// Packed comparison (App. I) + local mask rewrite: returns the XOR share of
+// the Boolean outputs; *atoms_out receives the atom shares.
+__device__ __forceinline__ uint32_t party_pred(uint32_t b, const DevSpec &S, const KeyLayout &L,
+                                               const char *kb, uint64_t e, uint64_t xhat,
+                                               const Tab &tb, uint32_t *atoms_out) {
+  const AesDcfInline aes{tb};
+  uint32_t atoms = 0;
+  for (uint32_t t = 0; t < S.T; ++t) {
+    const char *q = kb + L.off_q[t];
+    const uint32_t f = S.q_f[t];
+    const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
+    const uint64_t vcw = reinterpret_cast<const uint64_t *>(q + 16ull * (f + 1) * L.n)[e];
+    const uint32_t u = view(xhat, f, S.q_c[t]);
+    atoms |= dcf_bit_eval(b, f, u, root, L.n, vcw, aes) << t;
+  }
+  const uint32_t carry = reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e];
+  uint32_t z = 0;
+  for (uint32_t o = 0; o < S.n_bool; ++o) {
+    const int j = S.out_prim[o];
+    if (j >= 0)
+      z |= (((atoms >> S.prim_qtheta[j]) ^ (atoms >> S.prim_qr[j]) ^ (carry >> j)) & 1u) << o;
+  }
+  if (b == 0) z ^= S.out_const ^ S.out_neg;
+  *atoms_out = atoms;
+  return z;
+}
+
+// Vector interval lookup (App. I), telescoped over the M-1 boundary DCFs:
+// LUT(u) = v_{M-1} + sum_{j=1}^{M-1} 1[u < B_j] (v_{j-1} - v_j).
+template <int P>
+__device__ __forceinline__ void party_lut(uint32_t b, const DevSpec &S, const KeyLayout &L,
+                                          const char *kb, uint64_t e, uint64_t xhat, const Tab &tb,
+                                          uint64_t *pay) {
+  const AesDcfInline aes{tb};
+  uint64_t acc[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) acc[q] = 0;
+  const uint32_t k = S.k;
+  const uint32_t u = view(xhat, k, 0);
+  for (uint32_t j = 0; j + 1 < S.M; ++j) {
+    const char *l = kb + L.off_l[j];
+    const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
+    const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e;
+    dcf_vec_eval_acc<P>(b, k, u, root, vcw, L.n, acc, aes);
+  }
+  const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
+#pragma unroll
+  for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * L.n + e] + (b ? 0ull - acc[q] : acc[q]);
+}
+
+// ---------------------------------------------------------------------------
+// the fused two-party gate
+// ---------------------------------------------------------------------------
+
+template <int R, int D, int E>
+__global__ void __launch_bounds__(2 * E, 1) gate_kernel(const __grid_constant__ GateArgs A) {
+  constexpr int P = R * (D + 1);
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
+  // outboxes: [party][element][R] pairs (e_b, f_b); the opening uses the first word
+  ulonglong2 *box = reinterpret_cast<ulonglong2 *>(smem + kTabBytes + ((sizeof(DevSpec) + 15) & ~size_t(15)));
+  stage_shared(tab, sspec, A.t0, A.spec);
+  const DevSpec &S = *sspec;
+  const KeyLayout &L = A.L;
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  const uint32_t b = threadIdx.x >= E ? 1u : 0u;
+  const uint32_t le = threadIdx.x - b * E;
+  const char *kb = b ? A.k1 : A.k0;
+  const uint64_t *xb = b ? A.x1 : A.x0;
+  uint64_t *yb = b ? A.y1 : A.y0;
+  uint32_t *zb = b ? A.z1 : A.z0;
+  const uint64_t *rsh = reinterpret_cast<const uint64_t *>(kb + L.off_r);
+  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  unsigned long long sent = 0;
+  const uint64_t ntiles = (A.n + E - 1) / E;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t e = tile * E + le;
+    const bool valid = e < A.n;
+    // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's
+    uint64_t r_b = 0, msg = 0;
+    if (valid) {
+      r_b = rsh[e];
+      msg = xb[e] + r_b;
+      sent += 8;
+    }
+    box[b * E + le].x = msg;
+    __syncthreads();
+    const uint64_t xhat = box[le].x + box[E + le].x;
+    __syncthreads();
+    // (2)(3) the two FSS calls on the public x^, local to party b
+    uint32_t z = 0, atoms = 0;
+    uint64_t pay[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) pay[q] = 0;
+    if (valid) {
+      z = party_pred(b, S, L, kb, e, xhat, tb, &atoms);
+      if (S.M > 1) {
+        party_lut<P>(b, S, L, kb, e, xhat, tb, pay);
+      } else {
+        const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
+#pragma unroll
+        for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * L.n + e];
+      }
+    }
+    // (4) masked -> shares: P0 holds x^ - r_0, P1 holds -r_1
+    const uint64_t xs = b == 0 ? xhat - r_b : 0ull - r_b;
+    // (5) Horner from the leading coefficient, one Beaver product per step
+    uint64_t y[R];
+#pragma unroll
+    for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
+#pragma unroll
+    for (int jj = D - 1; jj >= 0; --jj) {
+      uint64_t ta[R], tbv[R], tc[R];
+#pragma unroll
+      for (int o = 0; o < R; ++o) {
+        const uint32_t mi = (D - 1 - jj) * R + o;
+        if (valid) {
+          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
+          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
+          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
+        } else {
+          ta[o] = tbv[o] = tc[o] = 0;
+        }
+        box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
+        if (valid) sent += 16;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int o = 0; o < R; ++o) {
+        const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
+        const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
+        uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
+        if (b == 0) zz += Ev * Fv;
+        y[o] = zz + pay[o * (D + 1) + jj];
+      }
+      __syncthreads();
+    }
+    if (valid) {
+#pragma unroll
+      for (int o = 0; o < R; ++o) yb[e * R + o] = y[o];
+      zb[e] = z;
+    }
+  }
+  if (A.comm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sent += __shfl_xor_sync(0xffffffffu, sent, off);
+    if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(A.comm + b, sent);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// single-party FSS calls
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(512, 1) pred_kernel(const __grid_constant__ PartyArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
+  stage_shared(tab, sspec, A.t0, A.spec);
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
+       e += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t atoms;
+    const uint32_t z = party_pred(A.party, *sspec, A.L, A.kb, e, A.xhat[e], tb, &atoms);
+    if (A.atoms) A.atoms[e] = atoms;
+    if (A.bits) A.bits[e] = z;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ PartyArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
+  stage_shared(tab, sspec, A.t0, A.spec);
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
+       e += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t pay[P];
+    if (sspec->M > 1) {
+      party_lut<P>(A.party, *sspec, A.L, A.kb, e, A.xhat[e], tb, pay);
+    } else {
+      const uint64_t *vl = reinterpret_cast<const uint64_t *>(A.kb + A.L.off_vlast);
+#pragma unroll
+      for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * A.L.n + e];
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) A.payload[e * P + q] = pay[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GPU dealer
+// ---------------------------------------------------------------------------
+
+template <int P>
+__global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ KeygenArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
+  uint32_t *rk_prg = reinterpret_cast<uint32_t *>(smem + kTabBytes + ((sizeof(DevSpec) + 15) & ~size_t(15)));
+  if (threadIdx.x < 44) rk_prg[threadIdx.x] = A.rk.w[threadIdx.x];
+  stage_shared(tab, sspec, A.t0, A.spec);
+  const DevSpec &S = *sspec;
+  const KeyLayout &L = A.L;
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  const AesDcfCall rkd{tb};
+  const uint64_t n = A.n;
+  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+       e += uint64_t(gridDim.x) * blockDim.x) {
+    // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id)
+    auto prg = [&](uint32_t dr) {
+      return aes_rk_call(make_uint4(dr, uint32_t(e), uint32_t(e >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
+    };
+    const uint64_t r_in = lo64(prg(kDrawRin));
+    const uint64_t r0 = lo64(prg(kDrawRsh));
+    reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;
+    reinterpret_cast<uint64_t *>(A.k1 + L.off_r)[e] = r_in - r0;
+    if (A.x_plain) {
+      const uint64_t xs = lo64(prg(kDrawXsh));
+      A.x0[e] = xs;
+      A.x1[e] = A.x_plain[e] - xs;
+    }
+    // carries of the masked rewrites: w_j = 1[r_f + gamma_j >= 2^f]
+    uint32_t carries = 0;
+    for (uint32_t j = 0; j < S.n_prim; ++j) {
+      const uint32_t f = S.prim_f[j];
+      const uint64_t sum = (r_in & ((uint64_t(1) << f) - 1)) + S.prim_gamma[j];
+      carries |= uint32_t(sum >> f) << j;
+    }
+    const uint32_t cs0 = prg(kDrawCarry).x;
+    reinterpret_cast<uint32_t *>(A.k0 + L.off_carry)[e] = cs0;
+    reinterpret_cast<uint32_t *>(A.k1 + L.off_carry)[e] = cs0 ^ carries;
+    // packed-comparison keys: alpha = r_f for the r-atom, theta_j otherwise
+    for (uint32_t t = 0; t < S.T; ++t) {
+      const uint32_t f = S.q_f[t];
+      const uint64_t mask = (uint64_t(1) << f) - 1;
+      const int j = S.q_prim[t];
+      const uint64_t alpha = j < 0 ? (r_in & mask) : (((r_in & mask) + S.prim_gamma[j]) & mask);
+      const uint4 s0 = prg(S.base_roots + 2 * t), s1 = prg(S.base_roots + 2 * t + 1);
+      char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
+      dcf_bit_gen(f, uint32_t(alpha), s0, s1, reinterpret_cast<uint4 *>(q0) + e,
+                  reinterpret_cast<uint4 *>(q1) + e,
+                  reinterpret_cast<uint64_t *>(q0 + 16ull * (f + 1) * n) + e,
+                  reinterpret_cast<uint64_t *>(q1 + 16ull * (f + 1) * n) + e, n, rkd);
+    }
+    // lookup instance and its M-1 vector DCFs
+    uint32_t last = 0;
+    if (S.M > 1) {
+      uint64_t B[kMaxM + 2];
+      uint32_t ord[kMaxM + 1];
+      lookup_boundaries(S, r_in, B, ord);
+      for (uint32_t j = 1; j < S.M; ++j) {
+        uint64_t beta[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) beta[q] = S.coeff[ord[j - 1] * P + q] - S.coeff[ord[j] * P + q];
+        const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
+        const uint4 s0 = prg(di), s1 = prg(di + 1);
+        char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
+        dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
+                       reinterpret_cast<uint4 *>(l1) + e,
+                       reinterpret_cast<uint64_t *>(l0 + 16ull * (S.k + 1) * n) + e,
+                       reinterpret_cast<uint64_t *>(l1 + 16ull * (S.k + 1) * n) + e, n, rkd);
+      }
+      last = ord[S.M - 1];
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const uint64_t sh = lo64(prg(kDrawVlast + q));
+      reinterpret_cast<uint64_t *>(A.k0 + L.off_vlast)[uint64_t(q) * n + e] = sh;
+      reinterpret_cast<uint64_t *>(A.k1 + L.off_vlast)[uint64_t(q) * n + e] = S.coeff[last * P + q] - sh;
+    }
+    // Beaver triples (a, b, c = a b), fresh per multiplication
+    uint64_t *tr0 = reinterpret_cast<uint64_t *>(A.k0 + L.off_trip);
+    uint64_t *tr1 = reinterpret_cast<uint64_t *>(A.k1 + L.off_trip);
+    for (uint32_t mi = 0; mi < S.d * S.r; ++mi) {
+      const uint32_t di = S.base_triples + 5 * mi;
+      const uint64_t a = lo64(prg(di)), bb = lo64(prg(di + 1));
+      const uint64_t a0 = lo64(prg(di + 2)), b0 = lo64(prg(di + 3)), c0 = lo64(prg(di + 4));
+      tr0[(uint64_t(mi) * 3 + 0) * n + e] = a0;
+      tr1[(uint64_t(mi) * 3 + 0) * n + e] = a - a0;
+      tr0[(uint64_t(mi) * 3 + 1) * n + e] = b0;
+      tr1[(uint64_t(mi) * 3 + 1) * n + e] = bb - b0;
+      tr0[(uint64_t(mi) * 3 + 2) * n + e] = c0;
+      tr1[(uint64_t(mi) * 3 + 2) * n + e] = a * bb - c0;
+    }
+  }
+}
+
+__global__ void reconstruct_kernel(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0,
+                                   const uint32_t *z1, uint64_t n, uint32_t r, uint64_t *y,
+                                   uint32_t *z) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * r;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    if (y) y[i] = y0[i] + y1[i];
+    if (z && i < n) z[i] = z0[i] ^ z1[i];
+  }
+}
+
+}  // namespace ffss
+
+namespace ffss {
+
+// ---------------------------------------------------------------------------
+// micro-benchmarks for the roofline: 32-bit LOP3 issue rate and the AES-128
+// T-table block rate of the code above (AES only, no key traffic)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) mb_lop3_kernel(uint32_t *out, uint32_t iters) {
+  uint32_t a0 = threadIdx.x, a1 = a0 * 3u + 1u, a2 = a0 * 5u + 2u, a3 = a0 * 7u + 3u;
+  uint32_t a4 = a0 ^ 0x55u, a5 = a0 ^ 0xAAu, a6 = a0 + 17u, a7 = a0 + 31u;
+  for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a0) : "r"(a1), "r"(a2));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a1) : "r"(a2), "r"(a3));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a2) : "r"(a3), "r"(a4));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a3) : "r"(a4), "r"(a5));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a4) : "r"(a5), "r"(a6));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a5) : "r"(a6), "r"(a7));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a6) : "r"(a7), "r"(a0));
+      asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a7) : "r"(a0), "r"(a1));
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+}
+
+__global__ void __launch_bounds__(512, 1) mb_aes_kernel(const uint32_t *t0, uint4 *out, uint32_t iters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
+    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
+    const uint32_t v = t0[e];
+    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+  }
+  __syncthreads();
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  uint4 s = make_uint4(threadIdx.x, blockIdx.x, 7u, 9u);
+  for (uint32_t i = 0; i < iters; ++i) s = aes128(s, RkDcf(), tb);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace ffss

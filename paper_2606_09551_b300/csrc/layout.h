@@ -1,0 +1,108 @@
+// Host/device plain-old-data structures of the FuseFSS CUDA path: the compiled
+// operator specification and the per-party key layout in HBM.
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define FFSS_HD __host__ __device__ __forceinline__
+#else
+#define FFSS_HD inline
+#endif
+
+namespace ffss {
+
+constexpr int kMaxK = 32;
+constexpr int kMaxM = 16;
+constexpr int kMaxP = 4;
+constexpr int kMaxT = 32;
+constexpr int kMaxBool = 32;
+
+// Dealer draw indices per element (public, spec-determined): r_in, party-0
+// share of r_in, party-0 share of x, party-0 carry-share word, p party-0
+// shares of v_{M-1}, two root seeds per DCF key (queries, then lookup keys),
+// five draws per Beaver triple (a, b, a_0, b_0, c_0).
+constexpr uint32_t kDrawRin = 0;
+constexpr uint32_t kDrawRsh = 1;
+constexpr uint32_t kDrawXsh = 2;
+constexpr uint32_t kDrawCarry = 3;
+constexpr uint32_t kDrawVlast = 4;
+
+// Compiled operator specification (public).  Sec. 4.1 descriptor plus the
+// query list of App. F step (4) in its fixed descriptor order.
+struct DevSpec {
+  uint32_t k, m, d, r, p, M, T, n_bool, n_prim, V;   // V = ceil(8p / 16) AES blocks of payload
+  uint32_t q_f[kMaxT];         // query view width
+  int32_t q_prim[kMaxT];       // -1: the 1[view < r_f] atom; else the predicate it thresholds
+  uint64_t q_c[kMaxT];         // query view shift
+  uint32_t prim_f[kMaxBool];   // distinct non-sentinel primitive predicates
+  uint64_t prim_c[kMaxBool];
+  uint64_t prim_gamma[kMaxBool];
+  uint32_t prim_qtheta[kMaxBool];
+  uint32_t prim_qr[kMaxBool];
+  int32_t out_prim[kMaxBool];  // per Boolean output: predicate index or -1 (sentinel)
+  uint32_t out_const;          // sentinel values (bit o), applied by party 0 only
+  uint32_t out_neg;            // negations (bit o), applied by party 0 only
+  uint32_t base_roots, base_triples;  // dealer draw indices
+  uint32_t n_views;
+  uint64_t alpha[kMaxM + 1];
+  uint64_t coeff[kMaxM * kMaxP];      // [piece][q], q = o*(d+1) + j
+};
+
+// Byte offsets of one party's key material for n elements.  Every section is
+// 256-byte aligned; arrays are element-minor so a warp's 32 consecutive
+// elements read contiguous 16-byte (seeds, correction words) or 8-byte (ring
+// values) records.
+//   r share          u64  [n]
+//   carry share      u32  [n]
+//   v_{M-1} share    u64  [p][n]
+//   triples          u64  [n_mults][3][n]          (a, b, c)
+//   query t          uint4 root[n], uint4 cw[k_t][n] (seed CW | t_L | t_R << 1),
+//                    u64 vcw[n] (bit i = V_CW of level i, bit k_t = final CW)
+//   lookup key j     uint4 root[n], uint4 cw[k][n], u64 vcw[k+1][p][n] (level k = final CW)
+struct KeyLayout {
+  uint64_t n;
+  uint64_t off_r, off_carry, off_vlast, off_trip;
+  uint64_t off_q[kMaxT];
+  uint64_t off_l[kMaxM];
+  uint64_t total;
+};
+
+FFSS_HD uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
+
+inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
+  KeyLayout L{};
+  L.n = n;
+  uint64_t o = 0;
+  L.off_r = o; o = align256(o + 8 * n);
+  L.off_carry = o; o = align256(o + 4 * n);
+  L.off_vlast = o; o = align256(o + 8ull * s.p * n);
+  L.off_trip = o; o = align256(o + 24ull * s.d * s.r * n);
+  for (uint32_t t = 0; t < s.T; ++t) {
+    L.off_q[t] = o;
+    o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
+  }
+  for (uint32_t j = 0; j + 1 < s.M; ++j) {
+    L.off_l[j] = o;
+    o = align256(o + 16ull * (s.k + 1) * n + 8ull * (s.k + 1) * s.p * n);
+  }
+  L.total = o < 256 ? 256 : o;
+  return L;
+}
+
+// Per-element key bytes (without alignment padding).
+inline uint64_t key_bytes_per_elem(const DevSpec &s) {
+  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.d * s.r;
+  for (uint32_t t = 0; t < s.T; ++t) b += 16ull * (s.q_f[t] + 1) + 8;
+  if (s.M > 1) b += (s.M - 1) * (16ull * (s.k + 1) + 8ull * (s.k + 1) * s.p);
+  return b;
+}
+
+// Online AES-128 blocks per element per party: k_t per query, k(1+V)+V per lookup key.
+inline uint64_t aes_per_elem(const DevSpec &s) {
+  uint64_t a = 0;
+  for (uint32_t t = 0; t < s.T; ++t) a += s.q_f[t];
+  if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (1 + s.V) + s.V);
+  return a;
+}
+
+}  // namespace ffss

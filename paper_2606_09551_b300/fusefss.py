@@ -1,0 +1,233 @@
+"""Python binding of the FuseFSS C ABI (``include/fusefss.h``).
+
+Argument marshalling only: every step of the gate runs in the CUDA kernels of
+``lib/libfusefss.so``.  PyTorch supplies device memory and streams.  If the
+library is missing or cannot be loaded this module raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import specs as S
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfusefss.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fusefss.h")
+
+FFSS_OK = 0
+ERRORS = {-1: "FFSS_ERR_INVALID", -2: "FFSS_ERR_SHAPE", -3: "FFSS_ERR_CUDA", -4: "FFSS_ERR_TIMEOUT",
+          -5: "FFSS_ERR_BUDGET", -6: "FFSS_ERR_PARTY", -7: "FFSS_ERR_UNSUPPORTED"}
+KEYS_EMPTY, KEYS_FILLED = 0, 1
+
+
+class FfssError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PredDesc(C.Structure):
+    _fields_ = [("f", C.c_uint32), ("negate", C.c_uint32), ("c", C.c_uint64), ("gamma", C.c_uint64)]
+
+
+class SpecDesc(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("frac_bits", C.c_uint32), ("m", C.c_uint32), ("degree", C.c_uint32),
+                ("n_out", C.c_uint32), ("partition_bits", C.c_uint32),
+                ("alpha", C.POINTER(C.c_uint64)), ("coeff", C.POINTER(C.c_uint64)),
+                ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc))]
+
+
+class Shape(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("m", C.c_uint32), ("degree", C.c_uint32), ("n_out", C.c_uint32),
+                ("T", C.c_uint32), ("M", C.c_uint32), ("p", C.c_uint32), ("n_mults", C.c_uint32),
+                ("n_bool", C.c_uint32), ("n_views", C.c_uint32),
+                ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
+                ("aes_per_elem", C.c_uint64)]
+
+    def asdict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+vp = C.c_void_p
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                               "(python -m paper_2606_09551_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        L.ffss_last_error.restype = C.c_char_p
+        L.ffss_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
+        L.ffss_ctx_destroy.argtypes = [vp]
+        L.ffss_spec_compile.argtypes = [vp, C.POINTER(SpecDesc), C.POINTER(vp)]
+        L.ffss_spec_shape.argtypes = [vp, C.POINTER(Shape)]
+        L.ffss_spec_free.argtypes = [vp]
+        L.ffss_keys_size.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64)]
+        L.ffss_keys_bind.argtypes = [vp, C.c_uint64, C.c_int, vp, C.c_uint64, C.c_int, C.POINTER(vp)]
+        L.ffss_keys_release.argtypes = [vp]
+        L.ffss_keygen.argtypes = [vp, vp, C.POINTER(C.c_uint8), C.c_uint32, C.c_uint64, vp, vp, vp, vp, vp, vp]
+        L.ffss_eval_pred.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp, vp]
+        L.ffss_eval_lut.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp]
+        L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
+        L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
+        L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FFSS_OK:
+        raise FfssError(rc, lib().ffss_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Context:
+    """Per-device library state (AES tables, kernel attributes)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = vp()
+        _check(lib().ffss_ctx_create(device, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().ffss_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CompiledSpec:
+    """An operator specification compiled by the library (public shape)."""
+
+    def __init__(self, spec: S.OperatorSpec, ctx: Optional[Context] = None):
+        self.spec = spec
+        self.ctx = ctx
+        alpha = np.ascontiguousarray(np.asarray(spec.alpha, dtype=np.uint64))
+        coeff = np.ascontiguousarray(np.asarray(spec.coeff, dtype=np.uint64).reshape(-1))
+        preds = (PredDesc * max(len(spec.preds), 1))()
+        for i, q in enumerate(spec.preds):
+            preds[i] = PredDesc(q.f, q.negate, q.c, q.gamma)
+        self._keep = (alpha, coeff, preds)
+        d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
+                     alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
+                     len(spec.preds), preds)
+        h = vp()
+        _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
+        self.h = h
+        sh = Shape()
+        _check(lib().ffss_spec_shape(self.h, C.byref(sh)))
+        self.shape = sh
+
+    def key_bytes(self, n: int) -> int:
+        b = C.c_uint64()
+        _check(lib().ffss_keys_size(self.h, n, C.byref(b)))
+        return int(b.value)
+
+    def close(self):
+        if self.h:
+            lib().ffss_spec_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Keys:
+    """One party's key material for one call, in a torch uint8 device buffer."""
+
+    def __init__(self, cs: CompiledSpec, n: int, party: int, buf=None, state: int = KEYS_EMPTY):
+        import torch
+        self.cs, self.n, self.party = cs, n, party
+        nbytes = cs.key_bytes(n)
+        if buf is None:
+            buf = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{cs.ctx.device}")
+        assert buf.numel() >= nbytes and buf.data_ptr() % 256 == 0
+        self.buf = buf
+        h = vp()
+        _check(lib().ffss_keys_bind(cs.h, n, party, buf.data_ptr(), buf.numel(), state, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().ffss_keys_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def keygen(ctx: Context, cs: CompiledSpec, seed: bytes, call_id: int, n: int, k0: Keys, k1: Keys,
+           x_plain=None, x0=None, x1=None, stream=None):
+    sb = (C.c_uint8 * 16).from_buffer_copy(bytes(seed))
+    _check(lib().ffss_keygen(ctx.h, cs.h, sb, call_id, n, _ptr(x_plain), k0.h, k1.h, _ptr(x0), _ptr(x1),
+                             _stream(stream)))
+
+
+def eval_pred(ctx: Context, cs: CompiledSpec, party: int, keys: Keys, xhat, atoms=None, bits=None, stream=None):
+    _check(lib().ffss_eval_pred(ctx.h, cs.h, party, keys.h, _ptr(xhat), xhat.numel(), _ptr(atoms), _ptr(bits),
+                                _stream(stream)))
+
+
+def eval_lut(ctx: Context, cs: CompiledSpec, party: int, keys: Keys, xhat, payload, stream=None):
+    _check(lib().ffss_eval_lut(ctx.h, cs.h, party, keys.h, _ptr(xhat), xhat.numel(), _ptr(payload),
+                               _stream(stream)))
+
+
+def eval_pair(ctx: Context, cs: CompiledSpec, k0: Keys, k1: Keys, x0, x1, y0, y1, z0, z1, comm=None,
+              stream=None):
+    _check(lib().ffss_eval_pair(ctx.h, cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
+                                _ptr(z0), _ptr(z1), _ptr(comm), _stream(stream)))
+
+
+def reconstruct(y0, y1, z0, z1, n_out: int, y, z, stream=None):
+    n = z0.numel() if z0 is not None else y0.numel() // n_out
+    _check(lib().ffss_reconstruct(_ptr(y0), _ptr(y1), _ptr(z0), _ptr(z1), n, n_out, _ptr(y), _ptr(z),
+                                  _stream(stream)))
+
+
+def microbench(ctx: Context, which: int, iters: int):
+    """which 0: LOP3 ops/s; which 1: AES-128 T-table blocks/s.  Returns (rate, ms)."""
+    rate, ms = C.c_double(), C.c_double()
+    _check(lib().ffss_microbench(ctx.h, which, iters, C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
+
+
+def header_functions(path: str = HEADER) -> Sequence[str]:
+    """Names of the functions include/fusefss.h declares."""
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*|uint64_t)\s*\*?\s*(ffss_\w+)\s*\(", src, flags=re.M)))

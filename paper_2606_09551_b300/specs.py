@@ -269,7 +269,13 @@ def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,
     coefficients and random extra predicates (for parity tests)."""
     N = 1 << k
     assert 1 <= m <= N
-    inner = sorted(rng.choice(np.arange(1, N, dtype=np.int64), size=m - 1, replace=False).tolist()) if m > 1 else []
+    if N <= 4096:
+        inner = sorted(rng.choice(np.arange(1, N, dtype=np.int64), size=m - 1, replace=False).tolist()) if m > 1 else []
+    else:
+        chosen = set()
+        while len(chosen) < m - 1:
+            chosen.add(int(rng.integers(1, N)))
+        inner = sorted(chosen)
     alpha = [0] + [int(a) for a in inner] + [N]
     coeff = rng.integers(0, 2 ** 63, size=(m, r, d + 1), dtype=np.uint64) * np.uint64(2) \
         + rng.integers(0, 2, size=(m, r, d + 1), dtype=np.uint64)

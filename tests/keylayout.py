@@ -1,0 +1,159 @@
+"""Test-only mapping between the CUDA library's per-party key layout and the
+oracle's per-element key records.  The layout is the library's own choice
+(element-minor sections, each 256-byte aligned); the oracle compares shares
+and, through this transform, key material."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+
+def _a256(v):
+    return (v + 255) & ~255
+
+
+def offsets(ospec: O.Spec, n: int):
+    """Section offsets for n elements (the library's layout, restated)."""
+    q = ospec.queries()
+    o = 0
+    off = {}
+    off["r"] = o; o = _a256(o + 8 * n)
+    off["carry"] = o; o = _a256(o + 4 * n)
+    off["vlast"] = o; o = _a256(o + 8 * ospec.p * n)
+    off["trip"] = o; o = _a256(o + 24 * ospec.n_mults * n)
+    off["q"] = []
+    for (f, c, pr) in q:
+        off["q"].append(o)
+        o = _a256(o + 16 * (f + 1) * n + 8 * n)
+    off["l"] = []
+    for j in range(ospec.M - 1):
+        off["l"].append(o)
+        o = _a256(o + 16 * (ospec.k + 1) * n + 8 * (ospec.k + 1) * ospec.p * n)
+    off["total"] = max(o, 256)
+    return off
+
+
+def _u64(buf, off, count):
+    return buf[off: off + 8 * count].view(np.uint64)
+
+
+def _u32(buf, off, count):
+    return buf[off: off + 4 * count].view(np.uint32)
+
+
+def _blocks(buf, off, count):
+    return buf[off: off + 16 * count].reshape(count, 16)
+
+
+def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
+    """Key material of element e in the oracle's field vocabulary."""
+    off = offsets(ospec, n)
+    p, k, nm = ospec.p, ospec.k, ospec.n_mults
+    out = dict(
+        r_share=int(_u64(buf, off["r"], n)[e]),
+        carry=int(_u32(buf, off["carry"], n)[e]),
+        vlast=np.array([_u64(buf, off["vlast"], p * n)[q * n + e] for q in range(p)], np.uint64),
+    )
+    trip = _u64(buf, off["trip"], 3 * nm * n)
+    out["ta"] = np.array([trip[(mi * 3 + 0) * n + e] for mi in range(nm)], np.uint64)
+    out["tb"] = np.array([trip[(mi * 3 + 1) * n + e] for mi in range(nm)], np.uint64)
+    out["tc"] = np.array([trip[(mi * 3 + 2) * n + e] for mi in range(nm)], np.uint64)
+    qk = []
+    for t, (f, c, pr) in enumerate(ospec.queries()):
+        blk = _blocks(buf, off["q"][t], (f + 1) * n)
+        root = blk[e].copy()
+        cws = np.stack([blk[(1 + i) * n + e] for i in range(f)]) if f else np.zeros((0, 16), np.uint8)
+        vcw = int(_u64(buf, off["q"][t] + 16 * (f + 1) * n, n)[e])
+        qk.append(dict(root=root, cw=cws, vcw=vcw, k=f))
+    out["q"] = qk
+    lk = []
+    for j in range(ospec.M - 1):
+        blk = _blocks(buf, off["l"][j], (k + 1) * n)
+        root = blk[e].copy()
+        cws = np.stack([blk[(1 + i) * n + e] for i in range(k)])
+        v = _u64(buf, off["l"][j] + 16 * (k + 1) * n, (k + 1) * p * n)
+        vcw = np.array([[v[(i * p + q) * n + e] for q in range(p)] for i in range(k + 1)], np.uint64)
+        lk.append(dict(root=root, cw=cws, vcw=vcw))
+    out["l"] = lk
+    return out
+
+
+def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
+    """The same fields from an oracle key record, correction words packed
+    the library's way (t_L in bit 0, t_R in bit 1 of the seed correction)."""
+    base = keys.fields(ospec, i)
+    out = dict(r_share=base["r_share"], carry=base["carry"], vlast=base["vlast"],
+               ta=base["ta"], tb=base["tb"], tc=base["tc"])
+    qk = []
+    for t, (f, c, pr) in enumerate(ospec.queries()):
+        fl = keys.qkey(i, t).fields(f, 0)
+        cws = fl["scw"].copy()
+        if f:
+            cws[:, 0] |= fl["tcw_l"] | (fl["tcw_r"] << 1)
+        vcw = sum(int(fl["vcw_bit"][lv]) << lv for lv in range(f + 1))
+        qk.append(dict(root=fl["root"], cw=cws, vcw=vcw, k=f))
+    out["q"] = qk
+    lk = []
+    for j in range(1, ospec.M):
+        fl = keys.lkey(i, j).fields(ospec.k, ospec.p)
+        cws = fl["scw"].copy()
+        cws[:, 0] |= fl["tcw_l"] | (fl["tcw_r"] << 1)
+        lk.append(dict(root=fl["root"], cw=cws, vcw=fl["vcw"].astype(np.uint64)))
+    out["l"] = lk
+    return out
+
+
+def fields_equal(a, b) -> bool:
+    if a["r_share"] != b["r_share"] or a["carry"] != b["carry"]:
+        return False
+    for key in ("vlast", "ta", "tb", "tc"):
+        if not np.array_equal(a[key], b[key]):
+            return False
+    for qa, qb in zip(a["q"], b["q"]):
+        if not (np.array_equal(qa["root"], qb["root"]) and np.array_equal(qa["cw"], qb["cw"])
+                and qa["vcw"] == qb["vcw"]):
+            return False
+    for la, lb in zip(a["l"], b["l"]):
+        if not (np.array_equal(la["root"], lb["root"]) and np.array_equal(la["cw"], lb["cw"])
+                and np.array_equal(la["vcw"], lb["vcw"])):
+            return False
+    return len(a["q"]) == len(b["q"]) and len(a["l"]) == len(b["l"])
+
+
+def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
+    """Pack oracle key records of n elements into the library's layout."""
+    off = offsets(ospec, n)
+    buf = np.zeros(off["total"], np.uint8)
+    p, k, nm = ospec.p, ospec.k, ospec.n_mults
+    r = _u64(buf, off["r"], n)
+    cy = _u32(buf, off["carry"], n)
+    vl = _u64(buf, off["vlast"], p * n)
+    tr = _u64(buf, off["trip"], 3 * nm * n)
+    qs = ospec.queries()
+    for e in range(n):
+        fl = oracle_fields(keys, ospec, e)
+        r[e] = fl["r_share"]
+        cy[e] = fl["carry"]
+        for q in range(p):
+            vl[q * n + e] = fl["vlast"][q]
+        for mi in range(nm):
+            tr[(mi * 3 + 0) * n + e] = fl["ta"][mi]
+            tr[(mi * 3 + 1) * n + e] = fl["tb"][mi]
+            tr[(mi * 3 + 2) * n + e] = fl["tc"][mi]
+        for t, (f, c, pr) in enumerate(qs):
+            blk = _blocks(buf, off["q"][t], (f + 1) * n)
+            blk[e] = fl["q"][t]["root"]
+            for i in range(f):
+                blk[(1 + i) * n + e] = fl["q"][t]["cw"][i]
+            _u64(buf, off["q"][t] + 16 * (f + 1) * n, n)[e] = fl["q"][t]["vcw"]
+        for j in range(ospec.M - 1):
+            blk = _blocks(buf, off["l"][j], (k + 1) * n)
+            blk[e] = fl["l"][j]["root"]
+            for i in range(k):
+                blk[(1 + i) * n + e] = fl["l"][j]["cw"][i]
+            v = _u64(buf, off["l"][j] + 16 * (k + 1) * n, (k + 1) * p * n)
+            for i in range(k + 1):
+                for q in range(p):
+                    v[(i * p + q) * n + e] = fl["l"][j]["vcw"][i][q]
+    return buf

@@ -1,0 +1,101 @@
+"""The C-ABI library builds, loads without a GPU, exports every function the
+header declares, and its host-side spec compiler agrees with the oracle on
+the public shapes (no device calls here)."""
+import ctypes as C
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_09551_b300 import build as B
+from paper_2606_09551_b300 import fusefss as F
+from paper_2606_09551_b300 import specs as S
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_exports_every_header_function(libpath):
+    names = F.header_functions()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = C.CDLL(libpath)
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_context_without_gpu_fails_cleanly(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    rc = F.lib().ffss_ctx_create(0, C.byref(h))
+    assert rc == -3 and F.lib().ffss_last_error()
+
+
+def _shape_vs_oracle(sp):
+    cs = F.CompiledSpec(sp)           # host-only compile
+    o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples())
+    sh = cs.shape
+    assert (sh.T, sh.M, sh.p, sh.n_mults, sh.n_bool) == (o.T, o.M, o.p, o.n_mults, o.n_bool)
+    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults
+    qs = o.queries()
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + sum(16 * (f + 1) + 8 for f, _, _ in qs)
+    if o.M > 1:
+        kb += (o.M - 1) * (16 * (o.k + 1) + 8 * (o.k + 1) * o.p)
+    assert sh.key_bytes_per_elem == kb
+    V = (o.p + 1) // 2
+    aes = sum(f for f, _, _ in qs) + ((o.M - 1) * (o.k * (1 + V) + V) if o.M > 1 else 0)
+    assert sh.aes_per_elem == aes
+    return sh
+
+
+def test_workload_spec_shapes():
+    # per-element key bytes and AES blocks of the workload specs
+    sh = _shape_vs_oracle(S.gelu4())
+    assert (sh.T, sh.M, sh.p) == (4, 5, 3) and sh.aes_per_elem == 64 + 4 * (16 * 3 + 2)
+    sh = _shape_vs_oracle(S.gelu8())
+    assert sh.aes_per_elem == 528
+    sh = _shape_vs_oracle(S.nexp16())
+    assert sh.aes_per_elem == 16 * 24 + 16 * (24 * 3 + 2)
+    for sp in (S.recip16(), S.rsqrt16(), S.silu16(), S.relu(16), S.relu(4)):
+        _shape_vs_oracle(sp)
+
+
+def test_random_spec_shapes():
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        k = int(rng.integers(2, 33))
+        m = int(rng.integers(1, min(16, 2 ** k - 1) + 1))
+        d = int(rng.integers(0, 4))
+        r = 1 if d > 1 else int(rng.integers(1, 3))
+        sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(rng.integers(0, 2)),
+                           n_extra=int(rng.integers(0, 6)))
+        _shape_vs_oracle(sp)
+
+
+@pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0"])
+def test_invalid_specs_rejected(bad):
+    sp = S.random_spec(np.random.default_rng(1), 8, 4, 1)
+    if bad == "alpha_order":
+        sp.alpha = [0, 10, 10, 20, 256]
+    elif bad == "alpha_end":
+        sp.alpha = sp.alpha[:-1] + [255]
+    elif bad == "m_too_big":
+        sp = S.random_spec(np.random.default_rng(1), 2, 3, 1)
+        sp.k = 1
+        sp.alpha = [0, 1, 2, 2]
+    elif bad == "payload":
+        sp = S.random_spec(np.random.default_rng(1), 8, 4, 4)
+    elif bad == "pred_f":
+        sp.preds = [S.PredDesc(9, 0, 3, 0)]
+    elif bad == "k0":
+        sp.k = 0
+    with pytest.raises(F.FfssError):
+        F.CompiledSpec(sp)
