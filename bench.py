@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bert_layer", "gelu4"], default="bert_layer")
+    ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small"], default="bert_layer")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
@@ -52,6 +52,12 @@ def parse():
 
 def workload(name):
     from paper_2606_09551_b300 import inputs as I
+    if name == "exp_small":
+        # profiling case: the BERT-layer softmax nExp spec on 65,536 elements (3.4 GB of keys)
+        c = I.bert_layer()[1]
+        c.x = c.x[:65536]
+        return [c], {"workload": "nexp16_65536", "spec": "nExp-16 k=24 f=12 d=3", "elements": 65536,
+                     "form": "plain"}
     if name == "gelu4":
         return I.single_gelu4(), {"workload": "gelu4_single_op", "spec": "GeLU-4 k=16 f=12 d=2",
                                   "elements": 65536, "form": "plain"}
