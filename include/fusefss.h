@@ -116,6 +116,13 @@ int ffss_ctx_create(int device, ffss_ctx **out);
 int ffss_ctx_destroy(ffss_ctx *ctx);
 const char *ffss_last_error(void);
 
+/* Work split of the fused gate (library tuning knob, no counterpart in the
+ * paper): each element's T + M - 1 DCF walks are spread over `slots` threads
+ * (1, 2, 4, 8 or 16; tiles hold 256 / slots elements).  0 (the default) lets
+ * the library choose per call from a waves x slowest-slot cost model.
+ * Results do not depend on it.  Errors: FFSS_ERR_INVALID. */
+int ffss_ctx_set_slots(ffss_ctx *ctx, uint32_t slots);
+
 /* ---- specifications ------------------------------------------------------ */
 
 /* Validate and compile a specification: public query list (App. F step 4,
@@ -198,7 +205,9 @@ int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint3
  * which reports no roofline).  which = 0: 32-bit LOP3 issue rate, result in
  * operations/s (iters x 128 LOP3 per thread, 2 CTAs of 1024 threads per SM);
  * which = 1: AES-128 blocks/s of the shared-memory T-table code the FSS
- * kernels use (iters chained blocks per thread, one 512-thread CTA per SM).
+ * kernels use (iters chained blocks per thread, one 512-thread CTA per SM);
+ * which = 2, 3: the same with table addresses formed by byte permute plus
+ * multiply-add (C, and PTX mad) instead of shift plus mask.
  * Synchronizes the device; *ms (may be NULL) receives the kernel time. */
 int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms);
 

@@ -39,6 +39,52 @@ FFSS_CORE uint32_t ix1(uint32_t w, uint32_t l4) { return ((w >> 1) & 0x7F80u) | 
 FFSS_CORE uint32_t ix2(uint32_t w, uint32_t l4) { return ((w >> 9) & 0x7F80u) | l4; }
 FFSS_CORE uint32_t ix3(uint32_t w, uint32_t l4) { return ((w >> 17) & 0x7F80u) | l4; }
 
+// Address variants (VAR): 0 = shift + mask/or (two integer-ALU ops); 1 =
+// byte permute + integer multiply-add (one ALU op, one FMA-pipe op); 2 = the
+// same with the multiply-add written in PTX.
+#ifndef FFSS_HOST_PROBE
+template <int VAR>
+__device__ __forceinline__ uint32_t ixv(uint32_t w, uint32_t l4, int j) {
+  if (VAR == 0) {
+    return j == 0 ? ix0(w, l4) : j == 1 ? ix1(w, l4) : j == 2 ? ix2(w, l4) : ix3(w, l4);
+  } else {
+    const uint32_t by = __byte_perm(w, 0u, 0x4440u + uint32_t(j));
+    if (VAR == 1) return by * 128u + l4;
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, 128, %2;" : "=r"(r) : "r"(by), "r"(l4));
+    return r;
+  }
+}
+
+template <int VAR, class RK>
+__device__ __forceinline__ uint4 aes128v(uint4 in, const RK &rk, const Tab &tb) {
+  const uint32_t l4 = tb.lane4;
+  uint32_t s0 = in.x ^ rk[0], s1 = in.y ^ rk[1], s2 = in.z ^ rk[2], s3 = in.w ^ rk[3];
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    uint32_t t0 = tload(tb, 0, ixv<VAR>(s0, l4, 0)) ^ tload(tb, 1, ixv<VAR>(s1, l4, 1)) ^
+                  tload(tb, 2, ixv<VAR>(s2, l4, 2)) ^ tload(tb, 3, ixv<VAR>(s3, l4, 3)) ^ rk[4 * r + 0];
+    uint32_t t1 = tload(tb, 0, ixv<VAR>(s1, l4, 0)) ^ tload(tb, 1, ixv<VAR>(s2, l4, 1)) ^
+                  tload(tb, 2, ixv<VAR>(s3, l4, 2)) ^ tload(tb, 3, ixv<VAR>(s0, l4, 3)) ^ rk[4 * r + 1];
+    uint32_t t2 = tload(tb, 0, ixv<VAR>(s2, l4, 0)) ^ tload(tb, 1, ixv<VAR>(s3, l4, 1)) ^
+                  tload(tb, 2, ixv<VAR>(s0, l4, 2)) ^ tload(tb, 3, ixv<VAR>(s1, l4, 3)) ^ rk[4 * r + 2];
+    uint32_t t3 = tload(tb, 0, ixv<VAR>(s3, l4, 0)) ^ tload(tb, 1, ixv<VAR>(s0, l4, 1)) ^
+                  tload(tb, 2, ixv<VAR>(s1, l4, 2)) ^ tload(tb, 3, ixv<VAR>(s2, l4, 3)) ^ rk[4 * r + 3];
+    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+  }
+  uint4 o;
+  o.x = ((tload(tb, 2, ixv<VAR>(s0, l4, 0)) & 0xFFu) | (tload(tb, 3, ixv<VAR>(s1, l4, 1)) & 0xFF00u) |
+         (tload(tb, 0, ixv<VAR>(s2, l4, 2)) & 0xFF0000u) | (tload(tb, 1, ixv<VAR>(s3, l4, 3)) & 0xFF000000u)) ^ rk[40];
+  o.y = ((tload(tb, 2, ixv<VAR>(s1, l4, 0)) & 0xFFu) | (tload(tb, 3, ixv<VAR>(s2, l4, 1)) & 0xFF00u) |
+         (tload(tb, 0, ixv<VAR>(s3, l4, 2)) & 0xFF0000u) | (tload(tb, 1, ixv<VAR>(s0, l4, 3)) & 0xFF000000u)) ^ rk[41];
+  o.z = ((tload(tb, 2, ixv<VAR>(s2, l4, 0)) & 0xFFu) | (tload(tb, 3, ixv<VAR>(s3, l4, 1)) & 0xFF00u) |
+         (tload(tb, 0, ixv<VAR>(s0, l4, 2)) & 0xFF0000u) | (tload(tb, 1, ixv<VAR>(s1, l4, 3)) & 0xFF000000u)) ^ rk[42];
+  o.w = ((tload(tb, 2, ixv<VAR>(s3, l4, 0)) & 0xFFu) | (tload(tb, 3, ixv<VAR>(s0, l4, 1)) & 0xFF00u) |
+         (tload(tb, 0, ixv<VAR>(s1, l4, 2)) & 0xFF0000u) | (tload(tb, 1, ixv<VAR>(s2, l4, 3)) & 0xFF000000u)) ^ rk[43];
+  return o;
+}
+#endif
+
 // AES-128 encryption of one block.  State columns are little-endian words
 // (byte r of column c = input byte 4c + r).  Table 0 entry e holds the column
 // (2S, S, S, 3S) with S = S-box(e); tables 1..3 are its byte rotations.

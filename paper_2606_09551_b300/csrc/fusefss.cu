@@ -9,6 +9,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -116,6 +117,7 @@ struct ffss_ctx {
   int device;
   int sm_count;
   uint32_t *t0_dev;
+  uint32_t force_slots;   // 0: the cost model picks; else slots per element (1..16, power of two)
 };
 
 struct ffss_spec {
@@ -478,16 +480,81 @@ extern "C" int ffss_eval_lut(ffss_ctx *ctx, const ffss_spec *spec, int party, ff
 // the fused two-party gate
 // ---------------------------------------------------------------------------
 
-constexpr int kGateE = 256;   // elements per tile (2 * kGateE threads per CTA)
+// Split one element's T + M - 1 DCF walks over `slots` threads: longest
+// walks first, each to the least-loaded slot (cost = AES blocks).
+static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
+  Sched sc;
+  memset(&sc, 0, sizeof(sc));
+  const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  std::vector<std::pair<uint64_t, uint32_t>> items;
+  for (uint32_t t = 0; t < S.T; ++t) items.push_back({S.q_f[t], t});
+  for (uint32_t j = 0; j + 1 < S.M; ++j) items.push_back({uint64_t(S.k) * (1 + S.V) + S.V, S.T + j});
+  std::stable_sort(items.begin(), items.end(), [](auto &a, auto &b) { return a.first > b.first; });
+  std::vector<uint64_t> load(slots, 0);
+  std::vector<std::vector<uint32_t>> own(slots);
+  for (auto &it : items) {
+    uint32_t best = 0;
+    for (uint32_t q = 1; q < slots; ++q)
+      if (load[q] < load[best]) best = q;
+    load[best] += it.first;
+    own[best].push_back(it.second);
+  }
+  uint32_t pos = 0;
+  for (uint32_t q = 0; q < slots; ++q) {
+    sc.off[q] = uint8_t(pos);
+    std::sort(own[q].begin(), own[q].end());
+    for (uint32_t v : own[q]) sc.item[pos++] = uint8_t(v);
+  }
+  for (uint32_t q = slots; q <= 16; ++q) sc.off[q] = uint8_t(pos);
+  (void)nitems;
+  sc.S = slots;
+  sc.E = 256 / slots;
+  uint64_t mx = 0;
+  for (uint64_t l : load) mx = l > mx ? l : mx;
+  if (max_load) *max_load = mx;
+  return sc;
+}
+
+// Choose the slot count: minimise waves x (AES count of the slowest slot),
+// the time model of a launch whose CTAs each keep one SM busy; ties go to
+// more slots (shorter per-element latency).
+static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
+  const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  Sched best{};
+  double best_cost = 0;
+  bool have = false;
+  for (uint32_t slots = 1; slots <= 16; slots *= 2) {
+    if (slots > 1 && slots > nitems) break;
+    uint64_t mx = 0;
+    Sched sc = make_sched(S, slots, &mx);
+    const uint64_t tiles = (n + sc.E - 1) / sc.E;
+    const uint64_t waves = (tiles + ctx->sm_count - 1) / ctx->sm_count;
+    const double cost = double(waves) * double(mx ? mx : 1);
+    if (!have || cost <= best_cost) {
+      best = sc;
+      best_cost = cost;
+      have = true;
+    }
+  }
+  return best;
+}
 
 template <int R, int D>
-static int launch_gate(const ffss_ctx *ctx, const GateArgs &A, cudaStream_t st) {
-  const size_t smem = kTabBytes + spec_smem() + 2ull * kGateE * R * 16;
+static size_t gate_smem() {
+  constexpr int P = R * (D + 1);
+  return kTabBytes + spec_smem() + 2ull * 256 * R * 16 + 2ull * 256 * 8 * P + 2ull * 256 * 4;
+}
+
+template <int R, int D>
+static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st) {
+  const size_t smem = gate_smem<R, D>();
   static std::once_flag once;
   int rc = FFSS_OK;
-  std::call_once(once, [&] { rc = set_smem(gate_kernel<R, D, kGateE>, smem); });
+  std::call_once(once, [&] { rc = set_smem(gate_kernel<R, D>, smem); });
   if (rc) return rc;
-  gate_kernel<R, D, kGateE><<<grid_for(ctx, A.n, kGateE), 2 * kGateE, smem, st>>>(A);
+  const uint64_t tiles = (A.g.n + A.sched.E - 1) / A.sched.E;
+  const int grid = int(tiles < uint64_t(ctx->sm_count) ? tiles : uint64_t(ctx->sm_count));
+  gate_kernel<R, D><<<grid, kGateThreads, smem, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
 }
@@ -503,22 +570,25 @@ extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k
   if (!rc) rc = check_keys(spec, k1, 1, n, 3);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  GateArgs A;
-  memset(&A, 0, sizeof(A));
+  GateArgsS AS;
+  memset(&AS, 0, sizeof(AS));
+  GateArgs &A = AS.g;
   A.spec = spec->dev; A.L = make_layout(spec->host, n);
   A.k0 = k0->buf; A.k1 = k1->buf; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
   A.comm = reinterpret_cast<unsigned long long *>(comm);
   A.n = n; A.t0 = ctx->t0_dev;
+  AS.sched = ctx->force_slots ? make_sched(spec->host, ctx->force_slots, nullptr)
+                              : choose_sched(ctx, spec->host, n);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint32_t R = spec->host.r, D = spec->host.d;
-  if (R == 1 && D == 0) rc = launch_gate<1, 0>(ctx, A, st);
-  else if (R == 1 && D == 1) rc = launch_gate<1, 1>(ctx, A, st);
-  else if (R == 1 && D == 2) rc = launch_gate<1, 2>(ctx, A, st);
-  else if (R == 1 && D == 3) rc = launch_gate<1, 3>(ctx, A, st);
-  else if (R == 2 && D == 0) rc = launch_gate<2, 0>(ctx, A, st);
-  else if (R == 2 && D == 1) rc = launch_gate<2, 1>(ctx, A, st);
-  else if (R == 3 && D == 0) rc = launch_gate<3, 0>(ctx, A, st);
-  else if (R == 4 && D == 0) rc = launch_gate<4, 0>(ctx, A, st);
+  if (R == 1 && D == 0) rc = launch_gate<1, 0>(ctx, AS, st);
+  else if (R == 1 && D == 1) rc = launch_gate<1, 1>(ctx, AS, st);
+  else if (R == 1 && D == 2) rc = launch_gate<1, 2>(ctx, AS, st);
+  else if (R == 1 && D == 3) rc = launch_gate<1, 3>(ctx, AS, st);
+  else if (R == 2 && D == 0) rc = launch_gate<2, 0>(ctx, AS, st);
+  else if (R == 2 && D == 1) rc = launch_gate<2, 1>(ctx, AS, st);
+  else if (R == 3 && D == 0) rc = launch_gate<3, 0>(ctx, AS, st);
+  else if (R == 4 && D == 0) rc = launch_gate<4, 0>(ctx, AS, st);
   else return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
   if (rc) return rc;
   k0->used |= 3;
@@ -560,20 +630,25 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
     mb_lop3_kernel<<<blocks, threads>>>(static_cast<uint32_t *>(out), iters);
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters * 16.0 * 8.0;
-  } else if (which == 1) {
+  } else if (which >= 1 && which <= 3) {
     const int blocks = ctx->sm_count, threads = 512;
     const size_t smem = kTabBytes;
     static std::once_flag once;
-    std::call_once(once, [&] { rc = set_smem(mb_aes_kernel, smem); });
+    std::call_once(once, [&] {
+      rc = set_smem(mb_aes_kernel<0>, smem);
+      if (!rc) rc = set_smem(mb_aes_kernel<1>, smem);
+      if (!rc) rc = set_smem(mb_aes_kernel<2>, smem);
+    });
     if (rc) return rc;
+    auto kern = which == 1 ? mb_aes_kernel<0> : which == 2 ? mb_aes_kernel<1> : mb_aes_kernel<2>;
     CUDA_TRY(cudaMalloc(&out, sizeof(uint4) * blocks * threads));
-    mb_aes_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), 4);
+    kern<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), 4);
     CUDA_TRY(cudaEventRecord(a));
-    mb_aes_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
+    kern<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters;
   } else {
-    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1 (AES)");
+    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1..3 (AES variants)");
   }
   cudaError_t e = cudaEventSynchronize(b);
   float t = 0;
@@ -584,5 +659,13 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
   if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "ffss_microbench: %s", cudaGetErrorString(e));
   *rate = work / (double(t) * 1e-3);
   if (ms) *ms = t;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_ctx_set_slots(ffss_ctx *ctx, uint32_t slots) {
+  if (!ctx) return fail(FFSS_ERR_INVALID, "ffss_ctx_set_slots: NULL context");
+  if (slots != 0 && (slots > 16 || (slots & (slots - 1)) != 0))
+    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 16");
+  ctx->force_slots = slots;
   return FFSS_OK;
 }

@@ -94,21 +94,33 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // party-local steps (party b sees only its own key material kb)
 // ---------------------------------------------------------------------------
 
-// Packed comparison (App. I) + local mask rewrite: returns the XOR share of
-// the Boolean outputs; *atoms_out receives the atom shares.
-__device__ __forceinline__ uint32_t party_pred(uint32_t b, const DevSpec &S, const KeyLayout &L,
-                                               const char *kb, uint64_t e, uint64_t xhat,
-                                               const Tab &tb, uint32_t *atoms_out) {
-  const AesDcfInline aes{tb};
-  uint32_t atoms = 0;
-  for (uint32_t t = 0; t < S.T; ++t) {
-    const char *q = kb + L.off_q[t];
-    const uint32_t f = S.q_f[t];
-    const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
-    const uint64_t vcw = reinterpret_cast<const uint64_t *>(q + 16ull * (f + 1) * L.n)[e];
-    const uint32_t u = view(xhat, f, S.q_c[t]);
-    atoms |= dcf_bit_eval(b, f, u, root, L.n, vcw, aes) << t;
-  }
+// One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
+__device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const KeyLayout &L,
+                                             const char *kb, uint64_t e, uint64_t xhat, uint32_t t,
+                                             const AesDcfInline &aes) {
+  const char *q = kb + L.off_q[t];
+  const uint32_t f = S.q_f[t];
+  const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
+  const uint64_t vcw = reinterpret_cast<const uint64_t *>(q + 16ull * (f + 1) * L.n)[e];
+  return dcf_bit_eval(b, f, view(xhat, f, S.q_c[t]), root, L.n, vcw, aes);
+}
+
+// One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
+template <int P>
+__device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
+                                         uint64_t e, uint64_t xhat, uint32_t j, uint64_t *acc,
+                                         const AesDcfInline &aes) {
+  const uint32_t k = S.k;
+  const char *l = kb + L.off_l[j];
+  const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e;
+  dcf_vec_eval_acc<P>(b, k, view(xhat, k, 0), root, vcw, L.n, acc, aes);
+}
+
+// Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
+// share of C(x) = atom_theta ^ atom_r ^ <w>, constants and negations by party 0.
+__device__ __forceinline__ uint32_t combine_bits(uint32_t b, const DevSpec &S, const KeyLayout &L,
+                                                 const char *kb, uint64_t e, uint32_t atoms) {
   const uint32_t carry = reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e];
   uint32_t z = 0;
   for (uint32_t o = 0; o < S.n_bool; ++o) {
@@ -117,28 +129,14 @@ __device__ __forceinline__ uint32_t party_pred(uint32_t b, const DevSpec &S, con
       z |= (((atoms >> S.prim_qtheta[j]) ^ (atoms >> S.prim_qr[j]) ^ (carry >> j)) & 1u) << o;
   }
   if (b == 0) z ^= S.out_const ^ S.out_neg;
-  *atoms_out = atoms;
   return z;
 }
 
-// Vector interval lookup (App. I), telescoped over the M-1 boundary DCFs:
+// Lookup output: share of v_{M-1} plus (-1)^b times the summed DCF terms,
 // LUT(u) = v_{M-1} + sum_{j=1}^{M-1} 1[u < B_j] (v_{j-1} - v_j).
 template <int P>
-__device__ __forceinline__ void party_lut(uint32_t b, const DevSpec &S, const KeyLayout &L,
-                                          const char *kb, uint64_t e, uint64_t xhat, const Tab &tb,
-                                          uint64_t *pay) {
-  const AesDcfInline aes{tb};
-  uint64_t acc[P];
-#pragma unroll
-  for (int q = 0; q < P; ++q) acc[q] = 0;
-  const uint32_t k = S.k;
-  const uint32_t u = view(xhat, k, 0);
-  for (uint32_t j = 0; j + 1 < S.M; ++j) {
-    const char *l = kb + L.off_l[j];
-    const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
-    const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e;
-    dcf_vec_eval_acc<P>(b, k, u, root, vcw, L.n, acc, aes);
-  }
+__device__ __forceinline__ void finish_lut(uint32_t b, const KeyLayout &L, const char *kb, uint64_t e,
+                                           const uint64_t *acc, uint64_t *pay) {
   const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
 #pragma unroll
   for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * L.n + e] + (b ? 0ull - acc[q] : acc[q]);
@@ -146,22 +144,61 @@ __device__ __forceinline__ void party_lut(uint32_t b, const DevSpec &S, const Ke
 
 // ---------------------------------------------------------------------------
 // the fused two-party gate
+//
+// A CTA of 512 threads works on tiles of E = 256 / S elements.  Thread
+// (party b, slot s, element le) evaluates the DCF walks the host schedule
+// assigns to slot s (the T comparison keys and M-1 lookup keys of an element
+// split into S groups of near-equal AES count), so one element's walks run
+// on S threads at once.  Slot partials meet in shared memory; the slot-0
+// thread of each (party, element) then rewrites the bits, finishes the
+// lookup and runs the Horner/Beaver rounds, exchanging openings with the
+// peer party through the shared-memory outbox.
 // ---------------------------------------------------------------------------
 
-template <int R, int D, int E>
-__global__ void __launch_bounds__(2 * E, 1) gate_kernel(const __grid_constant__ GateArgs A) {
+constexpr uint32_t kGateThreads = 512;
+constexpr uint32_t kMaxItems = kMaxT + kMaxM;
+
+struct Sched {
+  uint32_t S, E;                 // slots per element, elements per tile (S * E = 256)
+  uint8_t off[17];               // slot s owns items [off[s], off[s+1])
+  uint8_t item[kMaxItems];       // < T: comparison key; >= T: lookup key item - T
+};
+
+struct GateArgsS {
+  GateArgs g;
+  Sched sched;
+};
+
+template <int P>
+__host__ __device__ constexpr size_t gate_red_bytes() {
+  return 2ull * 256 * (4 + 8 * P);
+}
+
+template <int R, int D>
+__global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_constant__ GateArgsS AS) {
   constexpr int P = R * (D + 1);
+  const GateArgs &A = AS.g;
+  const Sched &SC = AS.sched;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
-  DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
-  // outboxes: [party][element][R] pairs (e_b, f_b); the opening uses the first word
-  ulonglong2 *box = reinterpret_cast<ulonglong2 *>(smem + kTabBytes + ((sizeof(DevSpec) + 15) & ~size_t(15)));
+  unsigned char *p = smem + kTabBytes;
+  DevSpec *sspec = reinterpret_cast<DevSpec *>(p);
+  p += (sizeof(DevSpec) + 15) & ~size_t(15);
+  ulonglong2 *box = reinterpret_cast<ulonglong2 *>(p);        // [party][le][R] openings
+  p += 2ull * 256 * R * 16;
+  uint64_t *red_acc = reinterpret_cast<uint64_t *>(p);        // [party][slot][le][P]
+  p += 2ull * 256 * 8 * P;
+  uint32_t *red_atoms = reinterpret_cast<uint32_t *>(p);      // [party][slot][le]
   stage_shared(tab, sspec, A.t0, A.spec);
   const DevSpec &S = *sspec;
   const KeyLayout &L = A.L;
-  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
-  const uint32_t b = threadIdx.x >= E ? 1u : 0u;
-  const uint32_t le = threadIdx.x - b * E;
+  const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
+  const uint32_t NS = SC.S, E = SC.E;
+  const uint32_t b = threadIdx.x >> 8;
+  const uint32_t rem = threadIdx.x & 255u;
+  const uint32_t slot = rem / E, le = rem - slot * E;
+  const bool lead = slot == 0;
+  const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
   const char *kb = b ? A.k1 : A.k0;
   const uint64_t *xb = b ? A.x1 : A.x0;
   uint64_t *yb = b ? A.y1 : A.y0;
@@ -173,70 +210,100 @@ __global__ void __launch_bounds__(2 * E, 1) gate_kernel(const __grid_constant__ 
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t e = tile * E + le;
     const bool valid = e < A.n;
-    // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's
-    uint64_t r_b = 0, msg = 0;
-    if (valid) {
-      r_b = rsh[e];
-      msg = xb[e] + r_b;
-      sent += 8;
+    // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's.
+    // The outbox word .y keeps the sender's own r_b until the DCF walks end.
+    if (lead) {
+      uint64_t msg = 0, rr = 0;
+      if (valid) {
+        rr = rsh[e];
+        msg = xb[e] + rr;
+        sent += 8;
+      }
+      box[b * E + le] = make_ulonglong2(msg, rr);
     }
-    box[b * E + le].x = msg;
     __syncthreads();
     const uint64_t xhat = box[le].x + box[E + le].x;
-    __syncthreads();
-    // (2)(3) the two FSS calls on the public x^, local to party b
-    uint32_t z = 0, atoms = 0;
-    uint64_t pay[P];
+    // (2)(3) this slot's share of the two FSS calls on the public x^
+    uint32_t atoms = 0;
+    uint64_t acc[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) pay[q] = 0;
+    for (int q = 0; q < P; ++q) acc[q] = 0;
     if (valid) {
-      z = party_pred(b, S, L, kb, e, xhat, tb, &atoms);
-      if (S.M > 1) {
-        party_lut<P>(b, S, L, kb, e, xhat, tb, pay);
-      } else {
-        const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
-#pragma unroll
-        for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * L.n + e];
+      // a slot's items are sorted: comparison keys (< T) first, then lookup keys
+      uint32_t it = it0;
+      for (; it < it1 && SC.item[it] < S.T; ++it) {
+        const uint32_t t = SC.item[it];
+        atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
       }
+      for (; it < it1; ++it) vec_item<P>(b, S, L, kb, e, xhat, SC.item[it] - S.T, acc, aes);
     }
-    // (4) masked -> shares: P0 holds x^ - r_0, P1 holds -r_1
-    const uint64_t xs = b == 0 ? xhat - r_b : 0ull - r_b;
-    // (5) Horner from the leading coefficient, one Beaver product per step
-    uint64_t y[R];
+    const uint64_t r_b = lead ? box[b * E + le].y : 0;
+    const uint32_t ri = (b * NS + slot) * E + le;
+    red_atoms[ri] = atoms;
 #pragma unroll
-    for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
+    for (int q = 0; q < P; ++q) red_acc[uint64_t(ri) * P + q] = acc[q];
+    __syncthreads();
+    uint32_t z = 0;
+    uint64_t pay[P];
+    uint64_t y[R];
+    uint64_t xs = 0;
+    if (lead) {
+      for (uint32_t s2 = 1; s2 < NS; ++s2) {
+        const uint32_t rj = (b * NS + s2) * E + le;
+        atoms |= red_atoms[rj];
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc[q] += red_acc[uint64_t(rj) * P + q];
+      }
+      if (valid) {
+        z = combine_bits(b, S, L, kb, e, atoms);
+        finish_lut<P>(b, L, kb, e, acc, pay);
+      } else {
+#pragma unroll
+        for (int q = 0; q < P; ++q) pay[q] = 0;
+      }
+      // (4) masked -> shares: P0 holds x^ - r_0, P1 holds -r_1
+      xs = b == 0 ? xhat - r_b : 0ull - r_b;
+#pragma unroll
+      for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
+    }
+    // (5) Horner from the leading coefficient, one Beaver product per step
 #pragma unroll
     for (int jj = D - 1; jj >= 0; --jj) {
       uint64_t ta[R], tbv[R], tc[R];
+      if (lead) {
 #pragma unroll
-      for (int o = 0; o < R; ++o) {
-        const uint32_t mi = (D - 1 - jj) * R + o;
-        if (valid) {
-          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
-          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
-          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
-        } else {
-          ta[o] = tbv[o] = tc[o] = 0;
+        for (int o = 0; o < R; ++o) {
+          const uint32_t mi = (D - 1 - jj) * R + o;
+          if (valid) {
+            ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
+            tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
+            tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
+            sent += 16;
+          } else {
+            ta[o] = tbv[o] = tc[o] = 0;
+          }
+          box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
         }
-        box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
-        if (valid) sent += 16;
       }
       __syncthreads();
+      if (lead) {
 #pragma unroll
-      for (int o = 0; o < R; ++o) {
-        const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
-        const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
-        uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
-        if (b == 0) zz += Ev * Fv;
-        y[o] = zz + pay[o * (D + 1) + jj];
+        for (int o = 0; o < R; ++o) {
+          const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
+          const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
+          uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
+          if (b == 0) zz += Ev * Fv;
+          y[o] = zz + pay[o * (D + 1) + jj];
+        }
       }
       __syncthreads();
     }
-    if (valid) {
+    if (lead && valid) {
 #pragma unroll
       for (int o = 0; o < R; ++o) yb[e * R + o] = y[o];
       zb[e] = z;
     }
+    __syncthreads();   // the outbox and reduction buffers are reused by the next tile
   }
   if (A.comm) {
 #pragma unroll
@@ -254,13 +321,14 @@ __global__ void __launch_bounds__(512, 1) pred_kernel(const __grid_constant__ Pa
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
   stage_shared(tab, sspec, A.t0, A.spec);
-  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
        e += uint64_t(gridDim.x) * blockDim.x) {
-    uint32_t atoms;
-    const uint32_t z = party_pred(A.party, *sspec, A.L, A.kb, e, A.xhat[e], tb, &atoms);
+    const uint64_t xhat = A.xhat[e];
+    uint32_t atoms = 0;
+    for (uint32_t t = 0; t < sspec->T; ++t) atoms |= bit_item(A.party, *sspec, A.L, A.kb, e, xhat, t, aes) << t;
     if (A.atoms) A.atoms[e] = atoms;
-    if (A.bits) A.bits[e] = z;
+    if (A.bits) A.bits[e] = combine_bits(A.party, *sspec, A.L, A.kb, e, atoms);
   }
 }
 
@@ -270,17 +338,15 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
   stage_shared(tab, sspec, A.t0, A.spec);
-  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
        e += uint64_t(gridDim.x) * blockDim.x) {
-    uint64_t pay[P];
-    if (sspec->M > 1) {
-      party_lut<P>(A.party, *sspec, A.L, A.kb, e, A.xhat[e], tb, pay);
-    } else {
-      const uint64_t *vl = reinterpret_cast<const uint64_t *>(A.kb + A.L.off_vlast);
+    const uint64_t xhat = A.xhat[e];
+    uint64_t acc[P], pay[P];
 #pragma unroll
-      for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * A.L.n + e];
-    }
+    for (int q = 0; q < P; ++q) acc[q] = 0;
+    for (uint32_t j = 0; j + 1 < sspec->M; ++j) vec_item<P>(A.party, *sspec, A.L, A.kb, e, xhat, j, acc, aes);
+    finish_lut<P>(A.party, A.L, A.kb, e, acc, pay);
 #pragma unroll
     for (int q = 0; q < P; ++q) A.payload[e * P + q] = pay[q];
   }
@@ -422,6 +488,7 @@ __global__ void __launch_bounds__(1024) mb_lop3_kernel(uint32_t *out, uint32_t i
   out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
 }
 
+template <int VAR>
 __global__ void __launch_bounds__(512, 1) mb_aes_kernel(const uint32_t *t0, uint4 *out, uint32_t iters) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
@@ -433,7 +500,7 @@ __global__ void __launch_bounds__(512, 1) mb_aes_kernel(const uint32_t *t0, uint
   __syncthreads();
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
   uint4 s = make_uint4(threadIdx.x, blockIdx.x, 7u, 9u);
-  for (uint32_t i = 0; i < iters; ++i) s = aes128(s, RkDcf(), tb);
+  for (uint32_t i = 0; i < iters; ++i) s = aes128v<VAR>(s, RkDcf(), tb);
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 

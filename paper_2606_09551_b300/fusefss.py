@@ -80,6 +80,7 @@ def lib():
         L.ffss_eval_lut.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp]
         L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
+        L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
         L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -110,6 +111,10 @@ class Context:
         h = vp()
         _check(lib().ffss_ctx_create(device, C.byref(h)))
         self.h = h
+
+    def set_slots(self, slots: int):
+        """Force the gate's DCF walks per element onto `slots` threads (0: automatic)."""
+        _check(lib().ffss_ctx_set_slots(self.h, slots))
 
     def close(self):
         if self.h:
