@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small"], default="bert_layer")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
@@ -297,6 +298,39 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": total * world / (ems * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ems}
 
+    # batched form: the same layer as ONE persistent launch per step (graph replay)
+    batched = None
+    if not args.no_batch:
+        bt = F.Batch(ctx, max(len(calls), 1))
+        warm = KeySet()
+
+        def batch_step(ks):
+            bt.eval([(css[c.name],) + ks.k[c.name] + outs[c.name] for c in calls], comm=None)
+
+        for w in range(2):                       # captures both plan slots' graphs
+            warm.generate(2000 + w)
+            batch_step(warm)
+        del warm
+        for s, ks in enumerate(sets):
+            ks.generate(300 + s)
+        torch.cuda.synchronize()
+        bev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            bev[s][0].record(stream)
+            batch_step(sets[s])
+            bev[s][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        steps_ms = sorted(b0.elapsed_time(b1) for b0, b1 in bev)
+        bms = max_over_ranks(statistics.mean(steps_ms), world, dev)
+        batched = {"value": total * world / (bms * 1e-3), "unit": "elements/s", "ms_per_step": bms,
+                   "step_ms_p50": statistics.median(steps_ms), "step_ms_max": steps_ms[-1],
+                   "vs_plain": ms / bms, "launches_per_step": 1,
+                   "form": "one persistent work-queue launch per layer, CUDA graph replay"}
+        bt.close()
+
     # roofline of the dominant kernel (the op with the largest launch time)
     dom = max(calls, key=lambda c: per_op_ms[c.name])
     sh = css[dom.name].shape
@@ -350,6 +384,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "roofline": roof,
         "e2e": e2e,
+        "batched": batched,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)

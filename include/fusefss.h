@@ -193,6 +193,44 @@ int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_key
                    uint64_t *y0_dev, uint64_t *y1_dev, uint32_t *z0_dev, uint32_t *z1_dev,
                    uint64_t *comm_dev, void *stream);
 
+/* ---- online: batched form ----------------------------------------------- */
+
+/* One operator call of a batch: the arguments of ffss_eval_pair. */
+typedef struct {
+    const ffss_spec *spec;
+    ffss_keys *k0, *k1;
+    const uint64_t *x0_dev, *x1_dev;
+    uint64_t n;
+    uint64_t *y0_dev, *y1_dev;
+    uint32_t *z0_dev, *z1_dev;
+} ffss_call;
+
+typedef struct ffss_batch ffss_batch;
+
+/* A reusable launch plan for up to max_calls (<= 512) calls per batch: two
+ * pinned/device call-table slots, each with its own work-queue counter and a
+ * CUDA graph (table upload, counter reset, persistent kernel) captured on
+ * first use.  Errors: FFSS_ERR_UNSUPPORTED, FFSS_ERR_CUDA. */
+int ffss_batch_create(ffss_ctx *ctx, uint32_t max_calls, ffss_batch **out);
+int ffss_batch_destroy(ffss_batch *batch);
+
+/* Evaluate many two-party gate calls (different specs and sizes) in ONE
+ * persistent launch: a work queue of tiles (call, element range) drained by
+ * one CTA per SM, costliest tiles first; per element the same steps and the
+ * same shares as ffss_eval_pair (Sec. 5.3).  Program reuse across calls is
+ * the compiled spec (Sec. 6, "program reuse across layers").  Ordered after
+ * the work already queued on `stream`; later work on `stream` waits for it.
+ * May block the host until the plan slot used two calls earlier is free.
+ * Consumes all key handles.  comm_dev: two uint64 byte counters or NULL.
+ * Errors: as ffss_eval_pair, plus FFSS_ERR_SHAPE when n_calls > max_calls or
+ * two calls share key handles. */
+int ffss_batch_eval(ffss_batch *batch, const ffss_call *calls, uint32_t n_calls, uint64_t *comm_dev,
+                    void *stream);
+
+/* Work split of the batched launch (0 = library default of 8 threads per
+ * element, capped by the number of DCF walks).  Errors: FFSS_ERR_INVALID. */
+int ffss_batch_set_slots(ffss_batch *batch, uint32_t slots);
+
 /* y = y0 + y1 (mod 2^64, n*n_out values), z = z0 ^ z1 (n words).  Either pair
  * may be NULL. */
 int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint32_t *z0_dev,

@@ -540,14 +540,8 @@ static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
 }
 
 template <int R, int D>
-static size_t gate_smem() {
-  constexpr int P = R * (D + 1);
-  return kTabBytes + spec_smem() + 2ull * 256 * R * 16 + 2ull * 256 * 8 * P + 2ull * 256 * 4;
-}
-
-template <int R, int D>
 static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st) {
-  const size_t smem = gate_smem<R, D>();
+  const size_t smem = gate_smem_bytes();
   static std::once_flag once;
   int rc = FFSS_OK;
   std::call_once(once, [&] { rc = set_smem(gate_kernel<R, D>, smem); });
@@ -593,6 +587,178 @@ extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k
   if (rc) return rc;
   k0->used |= 3;
   k1->used |= 3;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form
+// ---------------------------------------------------------------------------
+
+struct ffss_batch {
+  ffss_ctx *ctx;
+  uint32_t cap;
+  size_t table_bytes;
+  cudaStream_t own;
+  cudaEvent_t in_ready, out_ready;
+  uint32_t force_slots;
+  struct Slot {
+    void *host = nullptr;                  // pinned call table
+    void *dev = nullptr;                   // device call table
+    unsigned long long *counter = nullptr; // work-queue head
+    cudaEvent_t done = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool used = false;
+  } slot[2];
+  int next;
+};
+
+static size_t batch_table_bytes(uint32_t cap) {
+  return align256(sizeof(BatchHdr)) + size_t(cap) * sizeof(BatchCall);
+}
+
+extern "C" int ffss_batch_destroy(ffss_batch *bt) {
+  if (!bt) return FFSS_OK;
+  cudaSetDevice(bt->ctx->device);
+  for (auto &sl : bt->slot) {
+    if (sl.done) cudaEventSynchronize(sl.done);
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (sl.host) cudaFreeHost(sl.host);
+    if (sl.dev) cudaFree(sl.dev);
+    if (sl.counter) cudaFree(sl.counter);
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
+  if (bt->in_ready) cudaEventDestroy(bt->in_ready);
+  if (bt->out_ready) cudaEventDestroy(bt->out_ready);
+  if (bt->own) cudaStreamDestroy(bt->own);
+  delete bt;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_batch_create(ffss_ctx *ctx, uint32_t max_calls, ffss_batch **out) {
+  if (!ctx || !out) return fail(FFSS_ERR_INVALID, "ffss_batch_create: NULL argument");
+  if (max_calls < 1 || max_calls > kBatchMaxCalls)
+    return fail(FFSS_ERR_UNSUPPORTED, "max_calls must be 1..%u", kBatchMaxCalls);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  ffss_batch *bt = new ffss_batch();
+  bt->ctx = ctx;
+  bt->cap = max_calls;
+  bt->table_bytes = batch_table_bytes(max_calls);
+  bt->next = 0;
+  bt->force_slots = 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&bt->own, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->in_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->out_ready, cudaEventDisableTiming);
+  for (auto &sl : bt->slot) {
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.host, bt->table_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.dev, bt->table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sl.counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) {
+    static std::once_flag once;
+    int rc = FFSS_OK;
+    std::call_once(once, [&] { rc = set_smem(batch_kernel, gate_smem_bytes()); });
+    if (rc) e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) {
+    ffss_batch_destroy(bt);
+    return fail(FFSS_ERR_CUDA, "ffss_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = bt;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_batch_set_slots(ffss_batch *bt, uint32_t slots) {
+  if (!bt) return fail(FFSS_ERR_INVALID, "ffss_batch_set_slots: NULL batch");
+  if (slots != 0 && (slots > 16 || (slots & (slots - 1)) != 0))
+    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 16");
+  bt->force_slots = slots;
+  return FFSS_OK;
+}
+
+static uint32_t batch_slots(const ffss_batch *bt, const DevSpec &S) {
+  const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  uint32_t want = bt->force_slots ? bt->force_slots : 8;
+  uint32_t s = 1;
+  while (s * 2 <= want && s * 2 <= (nitems ? nitems : 1)) s *= 2;
+  return s;
+}
+
+extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t n_calls, uint64_t *comm,
+                               void *stream) {
+  if (!bt || (n_calls && !calls)) return fail(FFSS_ERR_INVALID, "ffss_batch_eval: NULL argument");
+  if (n_calls > bt->cap) return fail(FFSS_ERR_SHAPE, "%u calls > batch capacity %u", n_calls, bt->cap);
+  ffss_ctx *ctx = bt->ctx;
+  // validate every call before touching any state
+  struct Item { BatchCall c; uint64_t tile_cost; uint64_t tiles; };
+  std::vector<Item> items;
+  for (uint32_t i = 0; i < n_calls; ++i) {
+    const ffss_call &c = calls[i];
+    if (c.n == 0) continue;
+    if (!c.spec || !c.x0_dev || !c.x1_dev || !c.y0_dev || !c.y1_dev || !c.z0_dev || !c.z1_dev)
+      return fail(FFSS_ERR_INVALID, "call %u: NULL argument", i);
+    int rc = check_device_spec(ctx, c.spec);
+    if (!rc) rc = check_keys(c.spec, c.k0, 0, c.n, 3);
+    if (!rc) rc = check_keys(c.spec, c.k1, 1, c.n, 3);
+    if (rc) return rc;
+    for (uint32_t j = 0; j < i; ++j)
+      if (calls[j].k0 == c.k0 || calls[j].k1 == c.k1) return fail(FFSS_ERR_SHAPE, "call %u reuses keys of call %u", i, j);
+    const DevSpec &S = c.spec->host;
+    Item it;
+    memset(&it.c, 0, sizeof(it.c));
+    it.c.spec = c.spec->dev;
+    it.c.k0 = c.k0->buf; it.c.k1 = c.k1->buf;
+    it.c.x0 = c.x0_dev; it.c.x1 = c.x1_dev; it.c.y0 = c.y0_dev; it.c.y1 = c.y1_dev;
+    it.c.z0 = c.z0_dev; it.c.z1 = c.z1_dev;
+    it.c.n = c.n;
+    it.c.rd = S.r * 16 + S.d;
+    uint64_t mx = 0;
+    it.c.sched = make_sched(S, batch_slots(bt, S), &mx);
+    it.tile_cost = mx;
+    it.tiles = (c.n + it.c.sched.E - 1) / it.c.sched.E;
+    items.push_back(it);
+  }
+  // costliest tiles first (longest-processing-time order shortens the tail)
+  std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.tile_cost > b.tile_cost; });
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  ffss_batch::Slot &sl = bt->slot[bt->next];
+  bt->next ^= 1;
+  if (sl.used) CUDA_TRY(cudaEventSynchronize(sl.done));   // the pinned table is free again
+  BatchHdr *hdr = static_cast<BatchHdr *>(sl.host);
+  BatchCall *tbl = reinterpret_cast<BatchCall *>(static_cast<char *>(sl.host) + align256(sizeof(BatchHdr)));
+  uint64_t tiles = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    items[i].c.tile_begin = tiles;
+    tiles += items[i].tiles;
+    tbl[i] = items[i].c;
+  }
+  hdr->n_calls = uint32_t(items.size());
+  hdr->total_tiles = tiles;
+  hdr->comm = reinterpret_cast<unsigned long long *>(comm);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!sl.exec) {
+    // capture: table upload, queue reset, persistent kernel
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(bt->own, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(sl.dev, sl.host, bt->table_bytes, cudaMemcpyHostToDevice, bt->own);
+    cudaMemsetAsync(sl.counter, 0, sizeof(unsigned long long), bt->own);
+    const BatchHdr *dh = static_cast<const BatchHdr *>(sl.dev);
+    const BatchCall *dc = reinterpret_cast<const BatchCall *>(static_cast<char *>(sl.dev) + align256(sizeof(BatchHdr)));
+    batch_kernel<<<ctx->sm_count, kGateThreads, gate_smem_bytes(), bt->own>>>(dh, dc, sl.counter, ctx->t0_dev);
+    CUDA_TRY(cudaStreamEndCapture(bt->own, &g));
+    cudaError_t e = cudaGraphInstantiate(&sl.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  // order: caller stream -> batch stream (graph) -> caller stream
+  CUDA_TRY(cudaEventRecord(bt->in_ready, st));
+  CUDA_TRY(cudaStreamWaitEvent(bt->own, bt->in_ready, 0));
+  CUDA_TRY(cudaGraphLaunch(sl.exec, bt->own));
+  CUDA_TRY(cudaEventRecord(sl.done, bt->own));
+  CUDA_TRY(cudaStreamWaitEvent(st, sl.done, 0));
+  sl.used = true;
+  for (uint32_t i = 0; i < n_calls; ++i)
+    if (calls[i].n) { calls[i].k0->used |= 3; calls[i].k1->used |= 3; }
   return FFSS_OK;
 }
 

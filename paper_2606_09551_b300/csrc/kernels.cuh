@@ -57,19 +57,25 @@ struct RkDcf {
   __device__ __forceinline__ uint32_t operator[](int i) const { return c_rk_dcf[i]; }
 };
 
+// Table addressing used by every kernel: byte permute + multiply-add, which
+// moves a third of the round's integer work from the ALU pipe to the FMA pipe
+// (240 instead of 360 ALU operations per block; the shared-memory lookups,
+// 160 per block, become the limit).
+constexpr int kAesVariant = 1;
+
 // AES_K for the DCF PRG, inlined (online path).
 struct AesDcfInline {
   Tab tb;
-  __device__ __forceinline__ uint4 operator()(uint4 in) const { return aes128(in, RkDcf(), tb); }
+  __device__ __forceinline__ uint4 operator()(uint4 in) const { return aes128v<kAesVariant>(in, RkDcf(), tb); }
 };
 
 // Out-of-line AES-128 calls for the dealer: one copy of the round code per
 // kernel instead of one per call site.
 __device__ __noinline__ uint4 aes_dcf_call(uint4 in, const char *base, uint32_t lane4) {
-  return aes128(in, RkDcf(), Tab{base, lane4});
+  return aes128v<kAesVariant>(in, RkDcf(), Tab{base, lane4});
 }
 __device__ __noinline__ uint4 aes_rk_call(uint4 in, const uint32_t *rk, const char *base, uint32_t lane4) {
-  return aes128(in, rk, Tab{base, lane4});
+  return aes128v<kAesVariant>(in, rk, Tab{base, lane4});
 }
 struct AesDcfCall {
   Tab tb;
@@ -169,30 +175,44 @@ struct GateArgsS {
   Sched sched;
 };
 
-template <int P>
-__host__ __device__ constexpr size_t gate_red_bytes() {
-  return 2ull * 256 * (4 + 8 * P);
+
+// Shared-memory carve-up of a gate CTA (after the T-tables).
+struct GateSmem {
+  DevSpec *spec;
+  ulonglong2 *box;        // [party][le][R] openings (the first word also carries x_b + r_b)
+  uint64_t *red_acc;      // [party][slot][le][P]
+  uint32_t *red_atoms;    // [party][slot][le]
+};
+
+__host__ __device__ constexpr size_t gate_smem_bytes() {
+  // tables + spec + outbox (R <= 4) + slot partials (P <= 4)
+  return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 2ull * 256 * 4 * 16 +
+         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4;
 }
 
-template <int R, int D>
-__global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_constant__ GateArgsS AS) {
-  constexpr int P = R * (D + 1);
-  const GateArgs &A = AS.g;
-  const Sched &SC = AS.sched;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+__device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
+  GateSmem g;
   unsigned char *p = smem + kTabBytes;
-  DevSpec *sspec = reinterpret_cast<DevSpec *>(p);
+  g.spec = reinterpret_cast<DevSpec *>(p);
   p += (sizeof(DevSpec) + 15) & ~size_t(15);
-  ulonglong2 *box = reinterpret_cast<ulonglong2 *>(p);        // [party][le][R] openings
-  p += 2ull * 256 * R * 16;
-  uint64_t *red_acc = reinterpret_cast<uint64_t *>(p);        // [party][slot][le][P]
-  p += 2ull * 256 * 8 * P;
-  uint32_t *red_atoms = reinterpret_cast<uint32_t *>(p);      // [party][slot][le]
-  stage_shared(tab, sspec, A.t0, A.spec);
-  const DevSpec &S = *sspec;
+  g.box = reinterpret_cast<ulonglong2 *>(p);
+  p += 2ull * 256 * 4 * 16;
+  g.red_acc = reinterpret_cast<uint64_t *>(p);
+  p += 2ull * 256 * 8 * kMaxP;
+  g.red_atoms = reinterpret_cast<uint32_t *>(p);
+  return g;
+}
+
+// One tile of one call: E = 256 / S elements, both parties.  All 512 threads
+// of the CTA enter together (the barriers inside are CTA-wide).
+template <int R, int D>
+__device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
+                                          uint64_t tile, unsigned long long *sent_io) {
+  constexpr int P = R * (D + 1);
+  const DevSpec &S = *G.spec;
   const KeyLayout &L = A.L;
-  const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
+  const AesDcfInline aes{tb};
+  ulonglong2 *box = G.box;
   const uint32_t NS = SC.S, E = SC.E;
   const uint32_t b = threadIdx.x >> 8;
   const uint32_t rem = threadIdx.x & 255u;
@@ -200,116 +220,263 @@ __global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_cons
   const bool lead = slot == 0;
   const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
   const char *kb = b ? A.k1 : A.k0;
-  const uint64_t *xb = b ? A.x1 : A.x0;
-  uint64_t *yb = b ? A.y1 : A.y0;
-  uint32_t *zb = b ? A.z1 : A.z0;
-  const uint64_t *rsh = reinterpret_cast<const uint64_t *>(kb + L.off_r);
-  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  const uint64_t e = tile * E + le;
+  const bool valid = e < A.n;
   unsigned long long sent = 0;
-  const uint64_t ntiles = (A.n + E - 1) / E;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t e = tile * E + le;
-    const bool valid = e < A.n;
-    // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's.
-    // The outbox word .y keeps the sender's own r_b until the DCF walks end.
-    if (lead) {
-      uint64_t msg = 0, rr = 0;
-      if (valid) {
-        rr = rsh[e];
-        msg = xb[e] + rr;
-        sent += 8;
-      }
-      box[b * E + le] = make_ulonglong2(msg, rr);
-    }
-    __syncthreads();
-    const uint64_t xhat = box[le].x + box[E + le].x;
-    // (2)(3) this slot's share of the two FSS calls on the public x^
-    uint32_t atoms = 0;
-    uint64_t acc[P];
-#pragma unroll
-    for (int q = 0; q < P; ++q) acc[q] = 0;
+  // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's.
+  // The outbox word .y keeps the sender's own r_b until the DCF walks end.
+  if (lead) {
+    uint64_t msg = 0, rr = 0;
     if (valid) {
-      // a slot's items are sorted: comparison keys (< T) first, then lookup keys
-      uint32_t it = it0;
-      for (; it < it1 && SC.item[it] < S.T; ++it) {
-        const uint32_t t = SC.item[it];
-        atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
-      }
-      for (; it < it1; ++it) vec_item<P>(b, S, L, kb, e, xhat, SC.item[it] - S.T, acc, aes);
+      rr = reinterpret_cast<const uint64_t *>(kb + L.off_r)[e];
+      msg = (b ? A.x1 : A.x0)[e] + rr;
+      sent += 8;
     }
-    const uint64_t r_b = lead ? box[b * E + le].y : 0;
-    const uint32_t ri = (b * NS + slot) * E + le;
-    red_atoms[ri] = atoms;
+    box[b * E + le] = make_ulonglong2(msg, rr);
+  }
+  __syncthreads();
+  const uint64_t xhat = box[le].x + box[E + le].x;
+  // (2)(3) this slot's share of the two FSS calls on the public x^
+  uint32_t atoms = 0;
+  uint64_t acc[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) red_acc[uint64_t(ri) * P + q] = acc[q];
-    __syncthreads();
-    uint32_t z = 0;
-    uint64_t pay[P];
-    uint64_t y[R];
-    uint64_t xs = 0;
+  for (int q = 0; q < P; ++q) acc[q] = 0;
+  if (valid) {
+    // a slot's items are sorted: comparison keys (< T) first, then lookup keys
+    uint32_t it = it0;
+    for (; it < it1 && SC.item[it] < S.T; ++it) {
+      const uint32_t t = SC.item[it];
+      atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
+    }
+    for (; it < it1; ++it) vec_item<P>(b, S, L, kb, e, xhat, SC.item[it] - S.T, acc, aes);
+  }
+  const uint64_t r_b = lead ? box[b * E + le].y : 0;
+  const uint32_t ri = (b * NS + slot) * E + le;
+  G.red_atoms[ri] = atoms;
+#pragma unroll
+  for (int q = 0; q < P; ++q) G.red_acc[uint64_t(ri) * P + q] = acc[q];
+  __syncthreads();
+  uint32_t z = 0;
+  uint64_t pay[P];
+  uint64_t y[R];
+  uint64_t xs = 0;
+  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  if (lead) {
+    for (uint32_t s2 = 1; s2 < NS; ++s2) {
+      const uint32_t rj = (b * NS + s2) * E + le;
+      atoms |= G.red_atoms[rj];
+#pragma unroll
+      for (int q = 0; q < P; ++q) acc[q] += G.red_acc[uint64_t(rj) * P + q];
+    }
+    if (valid) {
+      z = combine_bits(b, S, L, kb, e, atoms);
+      finish_lut<P>(b, L, kb, e, acc, pay);
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) pay[q] = 0;
+    }
+    // (4) masked -> shares: P0 holds x^ - r_0, P1 holds -r_1
+    xs = b == 0 ? xhat - r_b : 0ull - r_b;
+#pragma unroll
+    for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
+  }
+  // (5) Horner from the leading coefficient, one Beaver product per step
+#pragma unroll
+  for (int jj = D - 1; jj >= 0; --jj) {
+    uint64_t ta[R], tbv[R], tc[R];
     if (lead) {
-      for (uint32_t s2 = 1; s2 < NS; ++s2) {
-        const uint32_t rj = (b * NS + s2) * E + le;
-        atoms |= red_atoms[rj];
 #pragma unroll
-        for (int q = 0; q < P; ++q) acc[q] += red_acc[uint64_t(rj) * P + q];
+      for (int o = 0; o < R; ++o) {
+        const uint32_t mi = (D - 1 - jj) * R + o;
+        if (valid) {
+          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
+          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
+          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
+          sent += 16;
+        } else {
+          ta[o] = tbv[o] = tc[o] = 0;
+        }
+        box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
       }
-      if (valid) {
-        z = combine_bits(b, S, L, kb, e, atoms);
-        finish_lut<P>(b, L, kb, e, acc, pay);
+    }
+    __syncthreads();
+    if (lead) {
+#pragma unroll
+      for (int o = 0; o < R; ++o) {
+        const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
+        const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
+        uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
+        if (b == 0) zz += Ev * Fv;
+        y[o] = zz + pay[o * (D + 1) + jj];
+      }
+    }
+    __syncthreads();
+  }
+  if (lead && valid) {
+#pragma unroll
+    for (int o = 0; o < R; ++o) (b ? A.y1 : A.y0)[e * R + o] = y[o];
+    (b ? A.z1 : A.z0)[e] = z;
+  }
+  __syncthreads();   // the outbox and partial buffers are reused by the next tile
+  *sent_io += sent;
+}
+
+// Out-of-line copy for the batch kernel, which dispatches per tile on (R, D).
+template <int R, int D>
+__device__ __noinline__ void gate_tile_call(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
+                                            uint64_t tile, unsigned long long *sent_io) {
+  gate_tile<R, D>(A, SC, G, tb, tile, sent_io);
+}
+
+__device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned long long sent) {
+  if (!comm) return;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sent += __shfl_xor_sync(0xffffffffu, sent, off);
+  if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(comm + (threadIdx.x >> 8), sent);
+}
+
+// Plain form: one launch per operator call, tiles dealt round-robin to the CTAs.
+template <int R, int D>
+__global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_constant__ GateArgsS AS) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GateSmem G = carve_gate_smem(smem);
+  stage_shared(reinterpret_cast<uint32_t *>(smem), G.spec, AS.g.t0, AS.g.spec);
+  const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
+  unsigned long long sent = 0;
+  const uint64_t ntiles = (AS.g.n + AS.sched.E - 1) / AS.sched.E;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) gate_tile<R, D>(AS.g, AS.sched, G, tb, tile, &sent);
+  flush_comm(AS.g.comm, sent);
+}
+
+// ---------------------------------------------------------------------------
+// batched form: one persistent launch over the tiles of many calls
+//
+// The call table (in device memory) lists each call's spec, key and I/O
+// pointers, work split and first global tile.  CTAs (one per SM) take tiles
+// from a global counter; the calls are ordered by the host so the costliest
+// tiles go first.  When a CTA moves to a tile of another call it re-stages
+// that call's spec and key layout in shared memory.
+// ---------------------------------------------------------------------------
+
+struct BatchCall {
+  const DevSpec *spec;
+  const char *k0, *k1;
+  const uint64_t *x0, *x1;
+  uint64_t *y0, *y1;
+  uint32_t *z0, *z1;
+  uint64_t n;
+  uint64_t tile_begin;     // first global tile of this call
+  uint32_t rd;             // n_out * 16 + degree
+  uint32_t pad;
+  Sched sched;
+};
+
+struct BatchHdr {
+  uint32_t n_calls;
+  uint32_t pad;
+  uint64_t total_tiles;
+  unsigned long long *comm;   // [2] bytes sent per party, may be null
+  uint64_t pad2;
+};
+
+constexpr uint32_t kBatchMaxCalls = 512;
+
+__device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n) {
+  KeyLayout L;
+  L.n = n;
+  uint64_t o = 0;
+  L.off_r = o; o = align256(o + 8 * n);
+  L.off_carry = o; o = align256(o + 4 * n);
+  L.off_vlast = o; o = align256(o + 8ull * s.p * n);
+  L.off_trip = o; o = align256(o + 24ull * s.d * s.r * n);
+  for (uint32_t t = 0; t < s.T; ++t) {
+    L.off_q[t] = o;
+    o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
+  }
+  for (uint32_t j = 0; j + 1 < s.M; ++j) {
+    L.off_l[j] = o;
+    o = align256(o + 16ull * (s.k + 1) * n + 8ull * (s.k + 1) * s.p * n);
+  }
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *hdr, const BatchCall *calls,
+                                                                unsigned long long *counter, const uint32_t *t0) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GateSmem G = carve_gate_smem(smem);
+  __shared__ GateArgs cur;
+  __shared__ Sched cur_sched;
+  __shared__ uint32_t cur_rd;
+  __shared__ int cur_call;
+  __shared__ int restage;
+  __shared__ unsigned long long next_tile;
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
+    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
+    const uint32_t v = t0[e];
+    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+  }
+  if (threadIdx.x == 0) cur_call = -1;
+  const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
+  const uint32_t n_calls = hdr->n_calls;
+  const unsigned long long total = hdr->total_tiles;
+  unsigned long long sent = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long tile = atomicAdd(counter, 1ull);
+      restage = 0;
+      if (tile < total) {
+        // the call holding this tile: the last call with tile_begin <= tile
+        uint32_t lo = 0, hi = n_calls;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (calls[mid].tile_begin <= tile) lo = mid; else hi = mid;
+        }
+        const BatchCall &c = calls[lo];
+        if (int(lo) != cur_call) {
+          cur_call = int(lo);
+          restage = 1;
+          cur.spec = c.spec;
+          cur.k0 = c.k0; cur.k1 = c.k1; cur.x0 = c.x0; cur.x1 = c.x1;
+          cur.y0 = c.y0; cur.y1 = c.y1; cur.z0 = c.z0; cur.z1 = c.z1;
+          cur.n = c.n;
+          cur.comm = nullptr;
+          cur.t0 = t0;
+          cur_sched = c.sched;
+          cur_rd = c.rd;
+        }
+        next_tile = tile - c.tile_begin;     // tile index within the call
       } else {
-#pragma unroll
-        for (int q = 0; q < P; ++q) pay[q] = 0;
+        next_tile = ~0ull;
       }
-      // (4) masked -> shares: P0 holds x^ - r_0, P1 holds -r_1
-      xs = b == 0 ? xhat - r_b : 0ull - r_b;
-#pragma unroll
-      for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
     }
-    // (5) Horner from the leading coefficient, one Beaver product per step
-#pragma unroll
-    for (int jj = D - 1; jj >= 0; --jj) {
-      uint64_t ta[R], tbv[R], tc[R];
-      if (lead) {
-#pragma unroll
-        for (int o = 0; o < R; ++o) {
-          const uint32_t mi = (D - 1 - jj) * R + o;
-          if (valid) {
-            ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
-            tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
-            tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
-            sent += 16;
-          } else {
-            ta[o] = tbv[o] = tc[o] = 0;
-          }
-          box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
-        }
-      }
+    __syncthreads();
+    if (next_tile == ~0ull) break;
+    if (restage) {
+      // stage the new call's spec and derive its key layout
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(cur.spec);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(G.spec);
+      for (uint32_t i = threadIdx.x; i < sizeof(DevSpec) / 4; i += blockDim.x) dst[i] = src[i];
       __syncthreads();
-      if (lead) {
-#pragma unroll
-        for (int o = 0; o < R; ++o) {
-          const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
-          const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
-          uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
-          if (b == 0) zz += Ev * Fv;
-          y[o] = zz + pay[o * (D + 1) + jj];
-        }
-      }
+      if (threadIdx.x == 0) cur.L = device_layout(*G.spec, cur.n);
       __syncthreads();
     }
-    if (lead && valid) {
-#pragma unroll
-      for (int o = 0; o < R; ++o) yb[e * R + o] = y[o];
-      zb[e] = z;
+    const uint64_t local = next_tile;
+    // one output of degree 1..3 (the transformer nonlinearities) inlined;
+    // the other shapes through out-of-line calls
+    switch (cur_rd) {
+      case 16 + 0: gate_tile_call<1, 0>(cur, cur_sched, G, tb, local, &sent); break;
+      case 16 + 1: gate_tile<1, 1>(cur, cur_sched, G, tb, local, &sent); break;
+      case 16 + 2: gate_tile<1, 2>(cur, cur_sched, G, tb, local, &sent); break;
+      case 16 + 3: gate_tile<1, 3>(cur, cur_sched, G, tb, local, &sent); break;
+      case 32 + 0: gate_tile_call<2, 0>(cur, cur_sched, G, tb, local, &sent); break;
+      case 32 + 1: gate_tile_call<2, 1>(cur, cur_sched, G, tb, local, &sent); break;
+      case 48 + 0: gate_tile_call<3, 0>(cur, cur_sched, G, tb, local, &sent); break;
+      default: gate_tile_call<4, 0>(cur, cur_sched, G, tb, local, &sent); break;
     }
-    __syncthreads();   // the outbox and reduction buffers are reused by the next tile
   }
-  if (A.comm) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sent += __shfl_xor_sync(0xffffffffu, sent, off);
-    if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(A.comm + b, sent);
-  }
+  flush_comm(hdr->comm, sent);
 }
 
 // ---------------------------------------------------------------------------

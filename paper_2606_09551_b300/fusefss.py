@@ -58,6 +58,11 @@ _lib = None
 vp = C.c_void_p
 
 
+class CallDesc(C.Structure):
+    _fields_ = [("spec", vp), ("k0", vp), ("k1", vp), ("x0", vp), ("x1", vp), ("n", C.c_uint64),
+                ("y0", vp), ("y1", vp), ("z0", vp), ("z1", vp)]
+
+
 def lib():
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
@@ -81,6 +86,10 @@ def lib():
         L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
         L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
+        L.ffss_batch_create.argtypes = [vp, C.c_uint32, C.POINTER(vp)]
+        L.ffss_batch_destroy.argtypes = [vp]
+        L.ffss_batch_eval.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
+        L.ffss_batch_set_slots.argtypes = [vp, C.c_uint32]
         L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -215,6 +224,38 @@ def eval_pair(ctx: Context, cs: CompiledSpec, k0: Keys, k1: Keys, x0, x1, y0, y1
               stream=None):
     _check(lib().ffss_eval_pair(ctx.h, cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
                                 _ptr(z0), _ptr(z1), _ptr(comm), _stream(stream)))
+
+
+class Batch:
+    """A reusable batched-launch plan (persistent kernel + CUDA graph)."""
+
+    def __init__(self, ctx: Context, max_calls: int = 64):
+        self.ctx = ctx
+        h = vp()
+        _check(lib().ffss_batch_create(ctx.h, max_calls, C.byref(h)))
+        self.h = h
+
+    def set_slots(self, slots: int):
+        _check(lib().ffss_batch_set_slots(self.h, slots))
+
+    def eval(self, calls, comm=None, stream=None):
+        """calls: sequence of (CompiledSpec, Keys k0, Keys k1, x0, x1, y0, y1, z0, z1)."""
+        arr = (CallDesc * max(len(calls), 1))()
+        for i, (cs, k0, k1, x0, x1, y0, y1, z0, z1) in enumerate(calls):
+            arr[i] = CallDesc(cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
+                              _ptr(z0), _ptr(z1))
+        _check(lib().ffss_batch_eval(self.h, arr, len(calls), _ptr(comm), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            lib().ffss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def reconstruct(y0, y1, z0, z1, n_out: int, y, z, stream=None):
