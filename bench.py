@@ -31,10 +31,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# ALU-pipe instructions per AES-128 block of the shared-memory T-table code
-# (ncu: smsp__inst_executed_pipe_alu.sum / blocks on the AES micro-kernel;
-# profiles/aes_ttable_microkernel.md).  Used for the ALU roofline.
-ALU_OPS_PER_AES = None
+# Per AES-128 block of the shared-memory T-table code with byte-permute +
+# multiply-add addressing, measured by ncu on the AES-only micro-kernel
+# (smsp__inst_executed_pipe_alu.sum and shared wavefronts x 32 / blocks):
+ALU_OPS_PER_AES = 240
+LDS_PER_AES = 160
+SMS = 148
+SM_MAX_MHZ = 2032.0
+HBM_GBS = 6491.5        # measured copy bandwidth of the B300s
 
 
 def parse():
@@ -351,17 +355,17 @@ def run_ours(args, rank, world, local_rank):
         "hbm_gbs_achieved": key_bytes_launch / dom_s / 1e9,
         "traffic": None,
     }
-    if ALU_OPS_PER_AES:
-        roof["achieved"] = aes_launch * ALU_OPS_PER_AES / dom_s / 1e9
-        roof["peak"] = lop3_rate / 1e9
-        roof["frac"] = roof["achieved"] / roof["peak"]
-    else:
-        # until the per-block ALU count is measured: AES rate against the
-        # AES-only micro-kernel of the same code
-        roof["achieved"] = aes_launch / dom_s / 1e9
-        roof["peak"] = aes_rate / 1e9
-        roof["unit"] = "G AES blocks/s"
-        roof["frac"] = roof["achieved"] / roof["peak"]
+    # AES roofline: per SM a T-table block needs ALU_OPS_PER_AES integer-ALU
+    # ops at 64/clock and LDS_PER_AES shared-memory lookups at 32/clock; the
+    # slower pipe sets the block rate (148 SMs at the 2,032 MHz maximum clock).
+    cyc = max(ALU_OPS_PER_AES / 64.0, LDS_PER_AES / 32.0)
+    roof["achieved"] = aes_launch / dom_s / 1e9
+    roof["peak"] = SMS * SM_MAX_MHZ * 1e6 / cyc / 1e9
+    roof["unit"] = "G AES blocks/s"
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_basis"] = ("derived: 148 SMs x 2032 MHz / max(%d ALU ops / 64 lanes, %d shared lookups / 32 banks) "
+                          "per block; ops per block measured by ncu on the AES micro-kernel" % (ALU_OPS_PER_AES, LDS_PER_AES))
+    roof["hbm_frac_of_measured"] = roof["hbm_gbs_achieved"] / HBM_GBS
 
     res = {
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
