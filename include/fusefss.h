@@ -231,6 +231,27 @@ int ffss_batch_eval(ffss_batch *batch, const ffss_call *calls, uint32_t n_calls,
  * element, capped by the number of DCF walks).  Errors: FFSS_ERR_INVALID. */
 int ffss_batch_set_slots(ffss_batch *batch, uint32_t slots);
 
+/* The batched evaluation for callers that cannot allocate device memory when
+ * they call: a host whose framework owns all device memory through its own
+ * allocator, a process under a hard device-memory cap, or a latency-critical
+ * loop that cannot afford cudaMalloc's implicit synchronisation.  The paper
+ * has no counterpart; this is a library convenience.
+ *
+ * Same result as ffss_batch_eval for the same calls, and it allocates
+ * nothing: its scratch (work-queue head and call table) is a fixed array in
+ * device memory that every GPU loading this library holds until the process
+ * exits, sized for at most 32 calls per batch (more is rejected with
+ * FFSS_ERR_SHAPE).  The call table is staged from host memory before the
+ * call returns; the queue head is cleared on every call.  All calls on a
+ * device share that one array: calls whose work overlaps on the GPU (on
+ * different streams, or from different threads without ordering) race and
+ * must not be issued.  The first call on a device resolves the array's device
+ * address and sets the kernel's shared-memory limit; make that first call
+ * before any stream capture.  Consumes all key handles.  Errors: as
+ * ffss_batch_eval. */
+int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, uint32_t n_calls, uint64_t *comm_dev,
+                            void *stream);
+
 /* y = y0 + y1 (mod 2^64, n*n_out values), z = z0 ^ z1 (n words).  Either pair
  * may be NULL. */
 int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint32_t *z0_dev,

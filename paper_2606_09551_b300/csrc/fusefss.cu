@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -757,6 +758,161 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
   CUDA_TRY(cudaEventRecord(sl.done, bt->own));
   CUDA_TRY(cudaStreamWaitEvent(st, sl.done, 0));
   sl.used = true;
+  for (uint32_t i = 0; i < n_calls; ++i)
+    if (calls[i].n) { calls[i].k0->used |= 3; calls[i].k1->used |= 3; }
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched form without allocation
+//
+// For callers that cannot allocate device memory at call time (a host whose
+// framework owns all device memory through its own allocator, a process that
+// runs under a hard memory cap, a latency-critical loop that must not pay
+// cudaMalloc's implicit synchronisation).  The scratch the batched kernel
+// needs -- the work-queue head and the call table -- lives in the static
+// device array below instead of a plan's buffers; every GPU that loads this
+// library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kNoAllocMaxCalls = 32;
+constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocTableBytes = ((sizeof(BatchHdr) + 255) & ~size_t(255)) + kNoAllocMaxCalls * sizeof(BatchCall);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocCounterBytes + kNoAllocTableBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];   // device address of g_noalloc_scratch, per device
+
+// Once per device, with that device current: resolve the array's device
+// address (the host-side symbol is only a stand-in) and raise the kernel's
+// shared-memory limit.
+static int noalloc_setup(int device, unsigned char **out) {
+  if (device < 0 || device >= 64) return fail(FFSS_ERR_UNSUPPORTED, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    CUDA_TRY(cudaSetDevice(device));
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(FFSS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gate_smem_bytes()));
+    if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    g_noalloc_addr[device] = ptr;
+  }
+  *out = static_cast<unsigned char *>(g_noalloc_addr[device]);
+  return FFSS_OK;
+}
+
+// Longest-first split of one element's DCF walks over `slots` threads, with
+// fixed-size arrays only.
+static Sched noalloc_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
+  Sched sc;
+  memset(&sc, 0, sizeof(sc));
+  uint32_t id[kMaxItems];
+  uint64_t cost[kMaxItems];
+  uint32_t n = 0;
+  for (uint32_t t = 0; t < S.T; ++t) { id[n] = t; cost[n] = S.q_f[t]; ++n; }
+  for (uint32_t j = 0; j + 1 < S.M; ++j) { id[n] = S.T + j; cost[n] = uint64_t(S.k) * (1 + S.V) + S.V; ++n; }
+  for (uint32_t a = 1; a < n; ++a)   // stable insertion sort, costliest first
+    for (uint32_t b = a; b > 0 && cost[b] > cost[b - 1]; --b) {
+      std::swap(cost[b], cost[b - 1]);
+      std::swap(id[b], id[b - 1]);
+    }
+  uint64_t load[16] = {0};
+  uint32_t owner[kMaxItems];
+  for (uint32_t i = 0; i < n; ++i) {
+    uint32_t best = 0;
+    for (uint32_t q = 1; q < slots; ++q)
+      if (load[q] < load[best]) best = q;
+    load[best] += cost[i];
+    owner[i] = best;
+  }
+  uint32_t pos = 0;
+  for (uint32_t q = 0; q < slots; ++q) {
+    sc.off[q] = uint8_t(pos);
+    for (uint32_t v = 0; v < S.T + S.M; ++v)   // items of slot q in ascending order
+      for (uint32_t i = 0; i < n; ++i)
+        if (owner[i] == q && id[i] == v) sc.item[pos++] = uint8_t(v);
+  }
+  for (uint32_t q = slots; q <= 16; ++q) sc.off[q] = uint8_t(pos);
+  sc.S = slots;
+  sc.E = 256 / slots;
+  uint64_t mx = 0;
+  for (uint32_t q = 0; q < slots; ++q) mx = load[q] > mx ? load[q] : mx;
+  *max_load = mx;
+  return sc;
+}
+
+extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, uint32_t n_calls, uint64_t *comm,
+                                       void *stream) {
+  if (!ctx || (n_calls && !calls)) return fail(FFSS_ERR_INVALID, "ffss_batch_eval_noalloc: NULL argument");
+  if (n_calls > kNoAllocMaxCalls)
+    return fail(FFSS_ERR_SHAPE, "ffss_batch_eval_noalloc: %u calls exceed the fixed scratch of %u calls",
+                n_calls, kNoAllocMaxCalls);
+  unsigned char *scratch = nullptr;
+  int rc = noalloc_setup(ctx->device, &scratch);
+  if (rc) return rc;
+  struct Table {
+    BatchHdr hdr;
+    unsigned char pad[(sizeof(BatchHdr) + 255) / 256 * 256 - sizeof(BatchHdr)];
+    BatchCall c[kNoAllocMaxCalls];
+  } tbl;
+  static_assert(sizeof(Table) <= kNoAllocTableBytes, "table fits the scratch");
+  memset(&tbl, 0, sizeof(tbl));
+  uint64_t cost[kNoAllocMaxCalls], ntiles[kNoAllocMaxCalls];
+  uint32_t m = 0;
+  for (uint32_t i = 0; i < n_calls; ++i) {
+    const ffss_call &c = calls[i];
+    if (c.n == 0) continue;
+    if (!c.spec || !c.x0_dev || !c.x1_dev || !c.y0_dev || !c.y1_dev || !c.z0_dev || !c.z1_dev)
+      return fail(FFSS_ERR_INVALID, "call %u: NULL argument", i);
+    rc = check_device_spec(ctx, c.spec);
+    if (!rc) rc = check_keys(c.spec, c.k0, 0, c.n, 3);
+    if (!rc) rc = check_keys(c.spec, c.k1, 1, c.n, 3);
+    if (rc) return rc;
+    for (uint32_t j = 0; j < i; ++j)
+      if (calls[j].k0 == c.k0 || calls[j].k1 == c.k1) return fail(FFSS_ERR_SHAPE, "call %u reuses keys of call %u", i, j);
+    const DevSpec &S = c.spec->host;
+    const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+    uint32_t slots = 1;
+    while (slots * 2 <= 8 && slots * 2 <= (nitems ? nitems : 1)) slots *= 2;
+    BatchCall &b = tbl.c[m];
+    b.spec = c.spec->dev;
+    b.k0 = c.k0->buf; b.k1 = c.k1->buf;
+    b.x0 = c.x0_dev; b.x1 = c.x1_dev; b.y0 = c.y0_dev; b.y1 = c.y1_dev; b.z0 = c.z0_dev; b.z1 = c.z1_dev;
+    b.n = c.n;
+    b.rd = S.r * 16 + S.d;
+    b.sched = noalloc_sched(S, slots, &cost[m]);
+    ntiles[m] = (c.n + b.sched.E - 1) / b.sched.E;
+    ++m;
+  }
+  for (uint32_t a = 1; a < m; ++a)   // costliest tiles first
+    for (uint32_t b = a; b > 0 && cost[b] > cost[b - 1]; --b) {
+      std::swap(cost[b], cost[b - 1]);
+      std::swap(ntiles[b], ntiles[b - 1]);
+      std::swap(tbl.c[b], tbl.c[b - 1]);
+    }
+  uint64_t tiles = 0;
+  for (uint32_t i = 0; i < m; ++i) {
+    tbl.c[i].tile_begin = tiles;
+    tiles += ntiles[i];
+  }
+  tbl.hdr.n_calls = m;
+  tbl.hdr.total_tiles = tiles;
+  tbl.hdr.comm = reinterpret_cast<unsigned long long *>(comm);
+  if (m == 0) return FFSS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long *counter = reinterpret_cast<unsigned long long *>(scratch);
+  unsigned char *dtab = scratch + kNoAllocCounterBytes;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  // the table is staged from host memory before this call returns; the queue
+  // head must start at zero on every call
+  CUDA_TRY(cudaMemcpyAsync(dtab, &tbl, sizeof(tbl), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+  batch_kernel<<<ctx->sm_count, kGateThreads, gate_smem_bytes(), st>>>(
+      reinterpret_cast<const BatchHdr *>(dtab), reinterpret_cast<const BatchCall *>(dtab + offsetof(Table, c)),
+      counter, ctx->t0_dev);
+  CUDA_TRY(cudaGetLastError());
   for (uint32_t i = 0; i < n_calls; ++i)
     if (calls[i].n) { calls[i].k0->used |= 3; calls[i].k1->used |= 3; }
   return FFSS_OK;

@@ -90,6 +90,7 @@ def lib():
         L.ffss_batch_destroy.argtypes = [vp]
         L.ffss_batch_eval.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
         L.ffss_batch_set_slots.argtypes = [vp, C.c_uint32]
+        L.ffss_batch_eval_noalloc.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
         L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
@@ -256,6 +257,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def batch_eval_noalloc(ctx: Context, calls, comm=None, stream=None):
+    """Batched evaluation that allocates no device memory (at most 32 calls).
+    calls: sequence of (CompiledSpec, Keys k0, Keys k1, x0, x1, y0, y1, z0, z1)."""
+    arr = (CallDesc * max(len(calls), 1))()
+    for i, (cs, k0, k1, x0, x1, y0, y1, z0, z1) in enumerate(calls):
+        arr[i] = CallDesc(cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
+                          _ptr(z0), _ptr(z1))
+    _check(lib().ffss_batch_eval_noalloc(ctx.h, arr, len(calls), _ptr(comm), _stream(stream)))
 
 
 def reconstruct(y0, y1, z0, z1, n_out: int, y, z, stream=None):
