@@ -252,6 +252,78 @@ int ffss_batch_set_slots(ffss_batch *batch, uint32_t slots);
 int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, uint32_t n_calls, uint64_t *comm_dev,
                             void *stream);
 
+/* ---- online: served form (continuous batching) -------------------------- */
+
+typedef struct ffss_server ffss_server;
+
+typedef struct {
+    uint64_t key_budget_bytes;  /* device key pool, split in two halves (double buffering) */
+    uint32_t max_active;        /* requests admitted at once */
+    uint32_t pad;
+    uint64_t chunk_elems;       /* largest piece of one operator call per step */
+    uint8_t seed[16];           /* dealer AES-128 seed */
+} ffss_server_cfg;
+
+/* One operator call of a request layer.  The dealer splits the plaintext
+ * input x_plain_dev into the parties' input shares (a synthetic client);
+ * output shares go to y*_dev (n * n_out) and z*_dev (n). */
+typedef struct {
+    const ffss_spec *spec;
+    uint64_t n;                 /* >= 1 */
+    const uint64_t *x_plain_dev;
+    uint64_t *y0_dev, *y1_dev;
+    uint32_t *z0_dev, *z1_dev;
+} ffss_op;
+
+/* A secure-inference request: n_layers x ops_per_layer operator calls,
+ * layer-major; layer l + 1 starts after layer l is written.  Masks of op
+ * (l, i) come from dealer call id call_id_base + l * ops_per_layer + i. */
+typedef struct {
+    uint32_t n_layers, ops_per_layer;
+    uint32_t call_id_base, pad;
+    const ffss_op *ops;
+} ffss_request;
+
+typedef struct {
+    uint32_t state;             /* 0 queued, 1 admitted, 2 done */
+    uint32_t layers_done;
+    double arrival_ms, admitted_ms, done_ms;   /* server clock */
+} ffss_request_stats;
+
+typedef struct {
+    uint64_t elements, steps, chunks, layers;
+    double first_admit_ms, last_done_ms;
+    double layer_ms_p50, layer_ms_p99, layer_ms_max;
+} ffss_server_stats;
+
+/* The served form (no counterpart in the paper, which evaluates one model at
+ * a time; keys are produced on the device chunk by chunk as in the paper's
+ * host key streaming for large models, Sec. 6 / App. B).  Up to max_active
+ * requests are admitted; each step packs round-robin chunks of every
+ * admitted request's ready layer until half the key pool is used, has the
+ * GPU dealer fill that half on its own stream, and evaluates all chunks in
+ * ONE batched launch while the dealer fills the other half for the next
+ * step.  A chunk's keys depend only on (request, layer, op, element), so a
+ * request's shares are the same whether it runs alone or among others.
+ * Errors: FFSS_ERR_INVALID, FFSS_ERR_BUDGET (pool), FFSS_ERR_CUDA. */
+int ffss_server_create(ffss_ctx *ctx, const ffss_server_cfg *cfg, ffss_server **out);
+int ffss_server_destroy(ffss_server *server);
+/* Queue a request arriving at arrival_s seconds on the server clock (0 =
+ * at creation).  The op descriptors are copied; the device buffers they
+ * name must stay valid until the request is done. */
+int ffss_server_submit(ffss_server *server, const ffss_request *req, double arrival_s, uint32_t *id);
+/* One scheduling step: retire finished work, admit arrived requests, issue
+ * the next batch.  *idle = 1 when every submitted request is done.  May
+ * block while the GPU is busy. */
+int ffss_server_step(ffss_server *server, int *idle);
+/* Wait for all issued work and retire it. */
+int ffss_server_drain(ffss_server *server);
+/* Milliseconds since the server was created (the clock arrivals use). */
+int ffss_server_clock(ffss_server *server, double *ms);
+int ffss_server_request_info(ffss_server *server, uint32_t id, ffss_request_stats *out, double *layer_ms,
+                              uint32_t max_layers);
+int ffss_server_summary(ffss_server *server, ffss_server_stats *out);
+
 /* y = y0 + y1 (mod 2^64, n*n_out values), z = z0 ^ z1 (n words).  Either pair
  * may be NULL. */
 int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint32_t *z0_dev,

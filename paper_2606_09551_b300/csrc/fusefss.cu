@@ -393,7 +393,7 @@ extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t s
   A.L = make_layout(spec->host, n);
   A.k0 = k0->buf; A.k1 = k1->buf;
   A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
-  A.n = n; A.call_id = call_id;
+  A.n = n; A.e0 = 0; A.call_id = call_id;
   key_schedule(seed, A.rk.w);
   A.t0 = ctx->t0_dev;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -917,6 +917,8 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
     if (calls[i].n) { calls[i].k0->used |= 3; calls[i].k1->used |= 3; }
   return FFSS_OK;
 }
+
+#include "server.cuh"
 
 extern "C" int ffss_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0,
                                 const uint32_t *z1, uint64_t n, uint32_t n_out, uint64_t *y, uint32_t *z,

@@ -24,6 +24,7 @@ struct KeygenArgs {
   const uint64_t *x_plain;
   uint64_t *x0, *x1;
   uint64_t n;
+  uint64_t e0;         // element index of this launch's first element within its call
   uint32_t call_id;
   RkParam rk;          // AES-128 key schedule of the run seed (dealer PRG)
   const uint32_t *t0;  // global T-table 0
@@ -417,24 +418,31 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
     const uint32_t v = t0[e];
     tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
   }
+  __shared__ unsigned long long s_begin[kBatchMaxCalls];   // first tile of each call
+  const uint32_t n_calls = hdr->n_calls;
+  for (uint32_t i = threadIdx.x; i < n_calls; i += blockDim.x) s_begin[i] = calls[i].tile_begin;
   if (threadIdx.x == 0) cur_call = -1;
   const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
-  const uint32_t n_calls = hdr->n_calls;
   const unsigned long long total = hdr->total_tiles;
   unsigned long long sent = 0;
+  // thread 0 claims the next tile one tile ahead, so the atomic's round trip
+  // overlaps the current tile's work
+  unsigned long long ahead = threadIdx.x == 0 ? atomicAdd(counter, 1ull) : 0ull;
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) {
-      const unsigned long long tile = atomicAdd(counter, 1ull);
+      const unsigned long long tile = ahead;
       restage = 0;
       if (tile < total) {
+        ahead = atomicAdd(counter, 1ull);
         // the call holding this tile: the last call with tile_begin <= tile
         uint32_t lo = 0, hi = n_calls;
         while (hi - lo > 1) {
           const uint32_t mid = (lo + hi) >> 1;
-          if (calls[mid].tile_begin <= tile) lo = mid; else hi = mid;
+          if (s_begin[mid] <= tile) lo = mid; else hi = mid;
         }
-        const BatchCall &c = calls[lo];
         if (int(lo) != cur_call) {
+          const BatchCall &c = calls[lo];
           cur_call = int(lo);
           restage = 1;
           cur.spec = c.spec;
@@ -446,7 +454,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
           cur_sched = c.sched;
           cur_rd = c.rd;
         }
-        next_tile = tile - c.tile_begin;     // tile index within the call
+        next_tile = tile - s_begin[lo];      // tile index within the call
       } else {
         next_tile = ~0ull;
       }
@@ -538,9 +546,12 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
   const uint64_t n = A.n;
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += uint64_t(gridDim.x) * blockDim.x) {
-    // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id)
+    // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id);
+    // the counter uses the element's index within the whole call, so a call
+    // dealt in chunks gets the same material as in one launch
+    const uint64_t ge = A.e0 + e;
     auto prg = [&](uint32_t dr) {
-      return aes_rk_call(make_uint4(dr, uint32_t(e), uint32_t(e >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
+      return aes_rk_call(make_uint4(dr, uint32_t(ge), uint32_t(ge >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
     };
     const uint64_t r_in = lo64(prg(kDrawRin));
     const uint64_t r0 = lo64(prg(kDrawRsh));

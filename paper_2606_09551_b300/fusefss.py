@@ -58,6 +58,35 @@ _lib = None
 vp = C.c_void_p
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("key_budget_bytes", C.c_uint64), ("max_active", C.c_uint32), ("pad", C.c_uint32),
+                ("chunk_elems", C.c_uint64), ("seed", C.c_uint8 * 16)]
+
+
+class OpDesc(C.Structure):
+    _fields_ = [("spec", C.c_void_p), ("n", C.c_uint64), ("x", C.c_void_p), ("y0", C.c_void_p),
+                ("y1", C.c_void_p), ("z0", C.c_void_p), ("z1", C.c_void_p)]
+
+
+class RequestDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_uint32), ("ops_per_layer", C.c_uint32), ("call_id_base", C.c_uint32),
+                ("pad", C.c_uint32), ("ops", C.POINTER(OpDesc))]
+
+
+class RequestStats(C.Structure):
+    _fields_ = [("state", C.c_uint32), ("layers_done", C.c_uint32), ("arrival_ms", C.c_double),
+                ("admitted_ms", C.c_double), ("done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("elements", C.c_uint64), ("steps", C.c_uint64), ("chunks", C.c_uint64), ("layers", C.c_uint64),
+                ("first_admit_ms", C.c_double), ("last_done_ms", C.c_double), ("layer_ms_p50", C.c_double),
+                ("layer_ms_p99", C.c_double), ("layer_ms_max", C.c_double)]
+
+    def asdict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class CallDesc(C.Structure):
     _fields_ = [("spec", vp), ("k0", vp), ("k1", vp), ("x0", vp), ("x1", vp), ("n", C.c_uint64),
                 ("y0", vp), ("y1", vp), ("z0", vp), ("z1", vp)]
@@ -90,6 +119,15 @@ def lib():
         L.ffss_batch_destroy.argtypes = [vp]
         L.ffss_batch_eval.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
         L.ffss_batch_set_slots.argtypes = [vp, C.c_uint32]
+        L.ffss_server_create.argtypes = [vp, C.POINTER(ServerCfg), C.POINTER(vp)]
+        L.ffss_server_destroy.argtypes = [vp]
+        L.ffss_server_submit.argtypes = [vp, C.POINTER(RequestDesc), C.c_double, C.POINTER(C.c_uint32)]
+        L.ffss_server_step.argtypes = [vp, C.POINTER(C.c_int)]
+        L.ffss_server_drain.argtypes = [vp]
+        L.ffss_server_clock.argtypes = [vp, C.POINTER(C.c_double)]
+        L.ffss_server_request_info.argtypes = [vp, C.c_uint32, C.POINTER(RequestStats), C.POINTER(C.c_double),
+                                               C.c_uint32]
+        L.ffss_server_summary.argtypes = [vp, C.POINTER(ServerStats)]
         L.ffss_batch_eval_noalloc.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
         L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
@@ -250,6 +288,74 @@ class Batch:
     def close(self):
         if self.h:
             lib().ffss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (native scheduler in the library)."""
+
+    def __init__(self, ctx: Context, key_budget_bytes: int, max_active: int, chunk_elems: int,
+                 seed: bytes):
+        self.ctx = ctx
+        cfg = ServerCfg(key_budget_bytes, max_active, 0, chunk_elems,
+                        (C.c_uint8 * 16).from_buffer_copy(bytes(seed)))
+        h = vp()
+        _check(lib().ffss_server_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def submit(self, layers, arrival_s: float = 0.0, call_id_base: int = 0) -> int:
+        """layers: list of layers, each a list of (CompiledSpec, x_plain, y0, y1, z0, z1)."""
+        per = len(layers[0])
+        ops = (OpDesc * (len(layers) * per))()
+        i = 0
+        for layer in layers:
+            assert len(layer) == per
+            for cs, x, y0, y1, z0, z1 in layer:
+                ops[i] = OpDesc(cs.h, x.numel(), _ptr(x), _ptr(y0), _ptr(y1), _ptr(z0), _ptr(z1))
+                i += 1
+        rq = RequestDesc(len(layers), per, call_id_base, 0, ops)
+        rid = C.c_uint32()
+        _check(lib().ffss_server_submit(self.h, C.byref(rq), arrival_s, C.byref(rid)))
+        self._keep.append(layers)
+        return rid.value
+
+    def step(self) -> bool:
+        idle = C.c_int()
+        _check(lib().ffss_server_step(self.h, C.byref(idle)))
+        return bool(idle.value)
+
+    def run(self):
+        while not self.step():
+            pass
+        _check(lib().ffss_server_drain(self.h))
+
+    def clock_ms(self) -> float:
+        v = C.c_double()
+        _check(lib().ffss_server_clock(self.h, C.byref(v)))
+        return v.value
+
+    def request_info(self, rid: int, max_layers: int = 256):
+        st = RequestStats()
+        lat = (C.c_double * max_layers)()
+        _check(lib().ffss_server_request_info(self.h, rid, C.byref(st), lat, max_layers))
+        return dict(state=st.state, layers_done=st.layers_done, arrival_ms=st.arrival_ms,
+                    admitted_ms=st.admitted_ms, done_ms=st.done_ms, layer_ms=list(lat[: st.layers_done]))
+
+    def summary(self):
+        st = ServerStats()
+        _check(lib().ffss_server_summary(self.h, C.byref(st)))
+        return st.asdict()
+
+    def close(self):
+        if self.h:
+            lib().ffss_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,108 @@
+"""Served form (continuous batching with on-device key streaming): a
+request's shares are bit-identical whether it runs alone or among other
+requests under a key budget that forces chunking, and identical to the plain
+per-operator launch with the same dealer call ids."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_09551_b300 import fusefss as F
+from paper_2606_09551_b300 import inputs as I
+from paper_2606_09551_b300 import specs as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2606_09551_b300 import build
+    build.build()
+    return F.Context(0)
+
+
+def _request(ctx, css, sizes, seed_tag):
+    """Two layers of (GeLU-8, nExp-16) with their own output buffers."""
+    import torch
+    layers = []
+    for layer in range(2):
+        ops = []
+        for j, (cs, n) in enumerate(zip(css, sizes)):
+            x = torch.from_numpy(I.uniform_x(n, cs.spec.k, seed_tag * 10 + layer * 2 + j)).cuda()
+            y0 = torch.zeros(n, dtype=torch.uint64, device="cuda:0")
+            z0 = torch.zeros(n, dtype=torch.uint32, device="cuda:0")
+            ops.append((cs, x, y0, torch.zeros_like(y0), z0, torch.zeros_like(z0)))
+        layers.append(ops)
+    return layers
+
+
+def _shares(layers):
+    return [[tuple(t.cpu().numpy().copy() for t in op[2:]) for op in layer] for layer in layers]
+
+
+def test_alone_equals_mixed_and_plain(ctx):
+    import torch
+    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    sizes = [[2500, 900], [700, 1300], [4000, 64], [300, 2000]]
+    # alone, roomy budget
+    sv = F.Server(ctx, 256 << 20, 4, 1 << 20, I.KEY_SEED)
+    alone = _request(ctx, css, sizes[0], 1)
+    sv.submit(alone, 0.0, call_id_base=100)
+    sv.run()
+    ref = _shares(alone)
+    sv.close()
+    # four requests, tight budget: layers are chunked and interleaved
+    sv = F.Server(ctx, 48 << 20, 3, 997, I.KEY_SEED)
+    reqs = [_request(ctx, css, sz, 1 + i) for i, sz in enumerate(sizes)]
+    ids = [sv.submit(r, 0.0, call_id_base=100 + 50 * i) for i, r in enumerate(reqs)]
+    sv.run()
+    st = sv.summary()
+    assert st["steps"] > 4 and st["chunks"] > st["steps"]          # chunked, several per step
+    assert st["layers"] == 8 and st["layer_ms_p99"] >= st["layer_ms_p50"] > 0
+    mixed = _shares(reqs[0])
+    for la, lb in zip(ref, mixed):
+        for oa, ob in zip(la, lb):
+            for a, b in zip(oa, ob):
+                assert np.array_equal(a, b)
+    for i, r in enumerate(ids):
+        info = sv.request_info(r)
+        assert info["state"] == 2 and len(info["layer_ms"]) == 2
+    # the same dealer call ids through the plain launch give the same shares
+    for li, layer in enumerate(reqs[2]):
+        for j, (cs, x, y0, y1, z0, z1) in enumerate(layer):
+            n = x.numel()
+            k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
+            x0, x1 = torch.empty_like(x), torch.empty_like(x)
+            F.keygen(ctx, cs, I.KEY_SEED, 100 + 50 * 2 + li * 2 + j, n, k0, k1, x, x0, x1)
+            p0, p1 = torch.empty_like(y0), torch.empty_like(y1)
+            q0, q1 = torch.empty_like(z0), torch.empty_like(z1)
+            F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
+            assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)
+            sp = cs.spec
+            o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples())
+            yp, zp = o.plain_eval(x.cpu().numpy())
+            assert np.array_equal((y0 + y1).cpu().numpy(), yp[:, 0])
+            assert np.array_equal((z0 ^ z1).cpu().numpy(), zp)
+
+
+def test_admission_limits(ctx):
+    css = [F.CompiledSpec(S.gelu4(), ctx)]
+    sv = F.Server(ctx, 16 << 20, 1, 4096, I.KEY_SEED)
+    reqs = [_request(ctx, css, [3000], 30 + i) for i in range(3)]
+    ids = [sv.submit(r, 0.0, call_id_base=10 * i) for i, r in enumerate(reqs)]
+    sv.run()
+    infos = [sv.request_info(i) for i in ids]
+    # max_active = 1: each request is admitted only after the previous one is done
+    for a, b in zip(infos, infos[1:]):
+        assert b["admitted_ms"] >= a["done_ms"] - 1.0
+    # a request whose single element cannot fit the key budget is refused
+    big = F.CompiledSpec(S.nexp16(), ctx)
+    tiny = F.Server(ctx, 2 << 20, 1, 16, I.KEY_SEED)
+    import torch
+    x = torch.zeros(4, dtype=torch.uint64, device="cuda:0")
+    y = torch.zeros(4, dtype=torch.uint64, device="cuda:0")
+    z = torch.zeros(4, dtype=torch.uint32, device="cuda:0")
+    tiny.submit([[(big, x, y, y.clone(), z, z.clone())]] * 1, 0.0)   # 51.7 KB per element fits 1 MiB halves
+    with pytest.raises(F.FfssError):
+        F.Server(ctx, 1 << 20, 1, 16, I.KEY_SEED)
