@@ -216,6 +216,51 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
   for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vcw[(uint64_t(k) * P + q) * n] & tm64);
 }
 
+// Same walk with the payload length p (<= 2V) known only at run time: the
+// V payload blocks per level are fixed by V, the accumulated words by p.
+template <int V, class AES>
+FFSS_CORE void dcf_vec_eval_acc_rt(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint64_t *vcw,
+                                   uint64_t n, uint32_t p, uint64_t *acc, const AES &aes) {
+  uint4 s = root[0];
+  uint32_t t = b;
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint32_t x = (u >> (k - 1 - i)) & 1u;
+    const uint4 cw = root[(1 + uint64_t(i)) * n];
+    uint64_t vc[2 * V];
+#pragma unroll
+    for (int q = 0; q < 2 * V; ++q) vc[q] = q < int(p) ? vcw[(uint64_t(i) * p + q) * n] : 0ull;
+    const uint4 blk = mmo(s, x, aes);
+    uint64_t conv[2 * V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const uint4 c = mmo(s, 2u + x * V + q, aes);
+      conv[2 * q] = lo64(c);
+      conv[2 * q + 1] = hi64(c);
+    }
+    const uint64_t tm64 = 0ull - uint64_t(t);
+#pragma unroll
+    for (int q = 0; q < 2 * V; ++q) acc[q] += conv[q] + (vc[q] & tm64);
+    const uint32_t tm = 0u - t;
+    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
+    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
+    s.y = blk.y ^ (tm & cw.y);
+    s.z = blk.z ^ (tm & cw.z);
+    s.w = blk.w ^ (tm & cw.w);
+    t = tn;
+  }
+  uint64_t conv[2 * V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) {
+    const uint4 c = mmo(s, 2u + q, aes);
+    conv[2 * q] = lo64(c);
+    conv[2 * q + 1] = hi64(c);
+  }
+  const uint64_t tm64 = 0ull - uint64_t(t);
+#pragma unroll
+  for (int q = 0; q < 2 * V; ++q)
+    acc[q] += conv[q] + ((q < int(p) ? vcw[(uint64_t(k) * p + q) * n] : 0ull) & tm64);
+}
+
 // ---------------------------------------------------------------------------
 // DCF Gen (both parties in lockstep).  Writes root, per-level correction words
 // (identical for both parties) and the V_CW words into both key sections.

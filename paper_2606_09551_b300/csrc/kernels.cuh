@@ -322,11 +322,140 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   *sent_io += sent;
 }
 
-// Out-of-line copy for the batch kernel, which dispatches per tile on (R, D).
-template <int R, int D>
-__device__ __noinline__ void gate_tile_call(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
-                                            uint64_t tile, unsigned long long *sent_io) {
-  gate_tile<R, D>(A, SC, G, tb, tile, sent_io);
+// The same tile with the output count r, degree d and payload length
+// p = r (d + 1) known only at run time (batch kernel: one CTA meets calls of
+// every shape).  Only the payload block count V (1 for p <= 2, 2 for p <= 4)
+// is compiled in, so the DCF walks, which hold all the work, exist once per
+// V; the reduction and Horner rounds index fixed-size register arrays.
+template <int V>
+__device__ __forceinline__ void gate_tile_rt(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
+                                             uint64_t tile, unsigned long long *sent_io) {
+  constexpr int PM = 2 * V;
+  const DevSpec &S = *G.spec;
+  const KeyLayout &L = A.L;
+  const AesDcfInline aes{tb};
+  ulonglong2 *box = G.box;
+  const uint32_t R = S.r, D = S.d, P = S.p;
+  const uint32_t NS = SC.S, E = SC.E;
+  const uint32_t b = threadIdx.x >> 8;
+  const uint32_t rem = threadIdx.x & 255u;
+  const uint32_t slot = rem / E, le = rem - slot * E;
+  const bool lead = slot == 0;
+  const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
+  const char *kb = b ? A.k1 : A.k0;
+  const uint64_t e = tile * E + le;
+  const bool valid = e < A.n;
+  unsigned long long sent = 0;
+  // (1) shares -> masked opening (App. C); .y keeps the sender's own r_b
+  if (lead) {
+    uint64_t msg = 0, rr = 0;
+    if (valid) {
+      rr = reinterpret_cast<const uint64_t *>(kb + L.off_r)[e];
+      msg = (b ? A.x1 : A.x0)[e] + rr;
+      sent += 8;
+    }
+    box[b * E + le] = make_ulonglong2(msg, rr);
+  }
+  __syncthreads();
+  const uint64_t xhat = box[le].x + box[E + le].x;
+  // (2)(3) this slot's DCF walks
+  uint32_t atoms = 0;
+  uint64_t acc[PM];
+#pragma unroll
+  for (int q = 0; q < PM; ++q) acc[q] = 0;
+  if (valid) {
+    uint32_t it = it0;
+    for (; it < it1 && SC.item[it] < S.T; ++it) {
+      const uint32_t t = SC.item[it];
+      atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
+    }
+    const uint32_t k = S.k;
+    const uint32_t u = view(xhat, k, 0);
+    for (; it < it1; ++it) {
+      const char *l = kb + L.off_l[SC.item[it] - S.T];
+      dcf_vec_eval_acc_rt<V>(b, k, u, reinterpret_cast<const uint4 *>(l) + e,
+                             reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e, L.n, P, acc, aes);
+    }
+  }
+  const uint64_t r_b = lead ? box[b * E + le].y : 0;
+  const uint32_t ri = (b * NS + slot) * E + le;
+  G.red_atoms[ri] = atoms;
+#pragma unroll
+  for (int q = 0; q < PM; ++q) G.red_acc[uint64_t(ri) * kMaxP + q] = acc[q];
+  __syncthreads();
+  uint32_t z = 0;
+  uint64_t pay[PM], y[kMaxP];
+  uint64_t xs = 0;
+  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  if (lead) {
+    for (uint32_t s2 = 1; s2 < NS; ++s2) {
+      const uint32_t rj = (b * NS + s2) * E + le;
+      atoms |= G.red_atoms[rj];
+#pragma unroll
+      for (int q = 0; q < PM; ++q) acc[q] += G.red_acc[uint64_t(rj) * kMaxP + q];
+    }
+    const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
+#pragma unroll
+    for (int q = 0; q < PM; ++q)
+      pay[q] = (valid && q < int(P)) ? vl[uint64_t(q) * L.n + e] + (b ? 0ull - acc[q] : acc[q]) : 0ull;
+    if (valid) z = combine_bits(b, S, L, kb, e, atoms);
+    xs = b == 0 ? xhat - r_b : 0ull - r_b;
+    // y_o = c_{o,d}: payload word o (d + 1) + d
+#pragma unroll
+    for (int o = 0; o < kMaxP; ++o) {
+      y[o] = 0;
+#pragma unroll
+      for (int q = 0; q < PM; ++q)
+        if (uint32_t(o) < R && uint32_t(q) == o * (D + 1) + D) y[o] = pay[q];
+    }
+  }
+  // (5) Horner: d Beaver rounds
+  for (int jj = int(D) - 1; jj >= 0; --jj) {
+    uint64_t ta[kMaxP], tbv[kMaxP], tc[kMaxP];
+    if (lead) {
+#pragma unroll
+      for (int o = 0; o < kMaxP; ++o) {
+        if (uint32_t(o) >= R) break;
+        const uint32_t mi = (D - 1 - jj) * R + o;
+        if (valid) {
+          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
+          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
+          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
+          sent += 16;
+        } else {
+          ta[o] = tbv[o] = tc[o] = 0;
+        }
+        box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
+      }
+    }
+    __syncthreads();
+    if (lead) {
+#pragma unroll
+      for (int o = 0; o < kMaxP; ++o) {
+        if (uint32_t(o) >= R) break;
+        const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
+        const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
+        uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
+        if (b == 0) zz += Ev * Fv;
+        uint64_t c = 0;
+#pragma unroll
+        for (int q = 0; q < PM; ++q)
+          if (uint32_t(q) == o * (D + 1) + jj) c = pay[q];
+        y[o] = zz + c;
+      }
+    }
+    __syncthreads();
+  }
+  if (lead && valid) {
+#pragma unroll
+    for (int o = 0; o < kMaxP; ++o) {
+      if (uint32_t(o) >= R) break;
+      (b ? A.y1 : A.y0)[e * R + o] = y[o];
+    }
+    (b ? A.z1 : A.z0)[e] = z;
+  }
+  __syncthreads();
+  *sent_io += sent;
 }
 
 __device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned long long sent) {
@@ -408,7 +537,6 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
   const GateSmem G = carve_gate_smem(smem);
   __shared__ GateArgs cur;
   __shared__ Sched cur_sched;
-  __shared__ uint32_t cur_rd;
   __shared__ int cur_call;
   __shared__ int restage;
   __shared__ unsigned long long next_tile;
@@ -452,7 +580,6 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
           cur.comm = nullptr;
           cur.t0 = t0;
           cur_sched = c.sched;
-          cur_rd = c.rd;
         }
         next_tile = tile - s_begin[lo];      // tile index within the call
       } else {
@@ -471,18 +598,8 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
       __syncthreads();
     }
     const uint64_t local = next_tile;
-    // one output of degree 1..3 (the transformer nonlinearities) inlined;
-    // the other shapes through out-of-line calls
-    switch (cur_rd) {
-      case 16 + 0: gate_tile_call<1, 0>(cur, cur_sched, G, tb, local, &sent); break;
-      case 16 + 1: gate_tile<1, 1>(cur, cur_sched, G, tb, local, &sent); break;
-      case 16 + 2: gate_tile<1, 2>(cur, cur_sched, G, tb, local, &sent); break;
-      case 16 + 3: gate_tile<1, 3>(cur, cur_sched, G, tb, local, &sent); break;
-      case 32 + 0: gate_tile_call<2, 0>(cur, cur_sched, G, tb, local, &sent); break;
-      case 32 + 1: gate_tile_call<2, 1>(cur, cur_sched, G, tb, local, &sent); break;
-      case 48 + 0: gate_tile_call<3, 0>(cur, cur_sched, G, tb, local, &sent); break;
-      default: gate_tile_call<4, 0>(cur, cur_sched, G, tb, local, &sent); break;
-    }
+    if (G.spec->V == 1) gate_tile_rt<1>(cur, cur_sched, G, tb, local, &sent);
+    else gate_tile_rt<2>(cur, cur_sched, G, tb, local, &sent);
   }
   flush_comm(hdr->comm, sent);
 }

@@ -82,8 +82,8 @@ def test_alone_equals_mixed_and_plain(ctx):
             sp = cs.spec
             o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples())
             yp, zp = o.plain_eval(x.cpu().numpy())
-            assert np.array_equal((y0 + y1).cpu().numpy(), yp[:, 0])
-            assert np.array_equal((z0 ^ z1).cpu().numpy(), zp)
+            assert np.array_equal(y0.cpu().numpy() + y1.cpu().numpy(), yp[:, 0])
+            assert np.array_equal(z0.cpu().numpy() ^ z1.cpu().numpy(), zp)
 
 
 def test_admission_limits(ctx):
