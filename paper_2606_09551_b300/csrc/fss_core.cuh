@@ -132,6 +132,21 @@ FFSS_CORE uint4 mmo(uint4 s, uint32_t j, const AES &aes) {
   return xor4(aes(s), s);
 }
 
+// Four independent MMO blocks through a 4-block AES functor
+// (aes4(in[4]) -> AES_K of each), so one call carries four encryptions.
+struct Blk4 { uint4 v[4]; };
+
+template <class AES4>
+FFSS_CORE Blk4 mmo4(uint4 s0, uint32_t j0, uint4 s1, uint32_t j1, uint4 s2, uint32_t j2, uint4 s3, uint32_t j3,
+                    const AES4 &aes4) {
+  s0.x ^= j0; s1.x ^= j1; s2.x ^= j2; s3.x ^= j3;
+  Blk4 in{{s0, s1, s2, s3}};
+  Blk4 o = aes4(in);
+  o.v[0] = xor4(o.v[0], s0); o.v[1] = xor4(o.v[1], s1);
+  o.v[2] = xor4(o.v[2], s2); o.v[3] = xor4(o.v[3], s3);
+  return o;
+}
+
 // Public view_{f,c}(u) = ((u mod 2^f) + c) mod 2^f  (Sec. 3.6), f <= 32.
 FFSS_CORE uint32_t view(uint64_t u, uint32_t f, uint64_t c) {
   uint64_t mask = (uint64_t(1) << f) - 1;
@@ -216,67 +231,22 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
   for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vcw[(uint64_t(k) * P + q) * n] & tm64);
 }
 
-// Same walk with the payload length p (<= 2V) known only at run time: the
-// V payload blocks per level are fixed by V, the accumulated words by p.
-template <int V, class AES>
-FFSS_CORE void dcf_vec_eval_acc_rt(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint64_t *vcw,
-                                   uint64_t n, uint32_t p, uint64_t *acc, const AES &aes) {
-  uint4 s = root[0];
-  uint32_t t = b;
-  for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t x = (u >> (k - 1 - i)) & 1u;
-    const uint4 cw = root[(1 + uint64_t(i)) * n];
-    uint64_t vc[2 * V];
-#pragma unroll
-    for (int q = 0; q < 2 * V; ++q) vc[q] = q < int(p) ? vcw[(uint64_t(i) * p + q) * n] : 0ull;
-    const uint4 blk = mmo(s, x, aes);
-    uint64_t conv[2 * V];
-#pragma unroll
-    for (int q = 0; q < V; ++q) {
-      const uint4 c = mmo(s, 2u + x * V + q, aes);
-      conv[2 * q] = lo64(c);
-      conv[2 * q + 1] = hi64(c);
-    }
-    const uint64_t tm64 = 0ull - uint64_t(t);
-#pragma unroll
-    for (int q = 0; q < 2 * V; ++q) acc[q] += conv[q] + (vc[q] & tm64);
-    const uint32_t tm = 0u - t;
-    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
-    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
-    s.y = blk.y ^ (tm & cw.y);
-    s.z = blk.z ^ (tm & cw.z);
-    s.w = blk.w ^ (tm & cw.w);
-    t = tn;
-  }
-  uint64_t conv[2 * V];
-#pragma unroll
-  for (int q = 0; q < V; ++q) {
-    const uint4 c = mmo(s, 2u + q, aes);
-    conv[2 * q] = lo64(c);
-    conv[2 * q + 1] = hi64(c);
-  }
-  const uint64_t tm64 = 0ull - uint64_t(t);
-#pragma unroll
-  for (int q = 0; q < 2 * V; ++q)
-    acc[q] += conv[q] + ((q < int(p) ? vcw[(uint64_t(k) * p + q) * n] : 0ull) & tm64);
-}
-
 // ---------------------------------------------------------------------------
 // DCF Gen (both parties in lockstep).  Writes root, per-level correction words
 // (identical for both parties) and the V_CW words into both key sections.
 // ---------------------------------------------------------------------------
 
-template <class AES>
+template <class AES4>
 FFSS_CORE void dcf_bit_gen(uint32_t k, uint32_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
-                           uint64_t *vcw0, uint64_t *vcw1, uint64_t n, const AES &aes) {
+                           uint64_t *vcw0, uint64_t *vcw1, uint64_t n, const AES4 &aes4) {
   q0[0] = s0;
   q1[0] = s1;
   uint32_t t0 = 0, t1 = 1, va = 0;
   uint64_t vbits = 0;
   for (uint32_t i = 0; i < k; ++i) {
     const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
-    const uint4 L0 = mmo(s0, 0, aes), R0 = mmo(s0, 1, aes);
-    const uint4 L1 = mmo(s1, 0, aes), R1 = mmo(s1, 1, aes);
+    const Blk4 ex = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
+    const uint4 L0 = ex.v[0], R0 = ex.v[1], L1 = ex.v[2], R1 = ex.v[3];
     const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;   // Lose side
     const uint4 ke0 = a ? R0 : L0, ke1 = a ? R1 : L1;   // Keep side
     uint4 scw = xor4(lo0, lo1);
@@ -306,21 +276,26 @@ FFSS_CORE void dcf_bit_gen(uint32_t k, uint32_t alpha, uint4 s0, uint4 s1, uint4
   vcw1[0] = vbits;
 }
 
-template <int P, class AES>
-FFSS_CORE void conv_blocks(uint4 s, uint32_t j0, uint64_t *out, const AES &aes) {
+// Payload words of V consecutive MMO blocks starting at tweak j0, for the
+// four (seed, j0) pairs of a Gen level, computed four blocks per call.
+template <int P, class AES4>
+FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1], const AES4 &aes4) {
   constexpr int V = (P + 1) / 2;
 #pragma unroll
   for (int q = 0; q < V; ++q) {
-    const uint4 c = mmo(s, j0 + q, aes);
-    out[2 * q] = lo64(c);
-    if (2 * q + 1 < P) out[2 * q + 1] = hi64(c);
+    const Blk4 c = mmo4(sd[0], j0[0] + q, sd[1], j0[1] + q, sd[2], j0[2] + q, sd[3], j0[3] + q, aes4);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      out[w][2 * q] = lo64(c.v[w]);
+      if (2 * q + 1 < P) out[w][2 * q + 1] = hi64(c.v[w]);
+    }
   }
 }
 
-template <int P, class AES>
+template <int P, class AES4>
 FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
                            uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t n,
-                           const AES &aes) {
+                           const AES4 &aes4) {
   constexpr uint32_t V = (P + 1) / 2;
   l0[0] = s0;
   l1[0] = s1;
@@ -331,20 +306,20 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
   for (uint32_t i = 0; i < k; ++i) {
     const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
     const uint32_t keep = a, lose = 1u - a;
-    const uint4 L0 = mmo(s0, 0, aes), R0 = mmo(s0, 1, aes);
-    const uint4 L1 = mmo(s1, 0, aes), R1 = mmo(s1, 1, aes);
-    uint64_t cl0[P + 1], cl1[P + 1], ck0[P + 1], ck1[P + 1];
-    conv_blocks<P>(s0, 2u + lose * V, cl0, aes);
-    conv_blocks<P>(s1, 2u + lose * V, cl1, aes);
-    conv_blocks<P>(s0, 2u + keep * V, ck0, aes);
-    conv_blocks<P>(s1, 2u + keep * V, ck1, aes);
+    const Blk4 ex = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
+    const uint4 L0 = ex.v[0], R0 = ex.v[1], L1 = ex.v[2], R1 = ex.v[3];
+    // payloads: [0] party 0 lose side, [1] party 1 lose, [2] party 0 keep, [3] party 1 keep
+    const uint4 sd[4] = {s0, s1, s0, s1};
+    const uint32_t j0[4] = {2u + lose * V, 2u + lose * V, 2u + keep * V, 2u + keep * V};
+    uint64_t cv[4][P + 1];
+    conv4<P>(sd, j0, cv, aes4);
     const bool neg = t1 != 0;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      uint64_t d = cl1[q] - cl0[q] - va[q];
+      uint64_t d = cv[1][q] - cv[0][q] - va[q];
       if (lose == 0) d += beta[q];
       const uint64_t vc = neg ? 0ull - d : d;
-      va[q] = va[q] - ck1[q] + ck0[q] + (neg ? 0ull - vc : vc);
+      va[q] = va[q] - cv[3][q] + cv[2][q] + (neg ? 0ull - vc : vc);
       vcw0[(uint64_t(i) * P + q) * n] = vc;
       vcw1[(uint64_t(i) * P + q) * n] = vc;
     }
@@ -368,13 +343,15 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
     ns1.x &= ~3u;
     s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
   }
-  uint64_t f0[P + 1], f1[P + 1];
-  conv_blocks<P>(s0, 2u, f0, aes);
-  conv_blocks<P>(s1, 2u, f1, aes);
+  // final correction word from the leaf conversions H(s, 2 + q) of both parties
+  const uint4 sd[4] = {s0, s1, s0, s1};
+  const uint32_t j0[4] = {2u, 2u, 2u, 2u};
+  uint64_t f[4][P + 1];
+  conv4<P>(sd, j0, f, aes4);
   const bool neg = t1 != 0;
 #pragma unroll
   for (int q = 0; q < P; ++q) {
-    const uint64_t d = f1[q] - f0[q] - va[q];
+    const uint64_t d = f[1][q] - f[0][q] - va[q];
     const uint64_t cw = neg ? 0ull - d : d;
     vcw0[(uint64_t(k) * P + q) * n] = cw;
     vcw1[(uint64_t(k) * P + q) * n] = cw;

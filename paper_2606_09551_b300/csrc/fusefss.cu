@@ -600,18 +600,52 @@ struct ffss_batch {
   uint32_t cap;
   size_t table_bytes;
   cudaStream_t own;
+  cudaStream_t branch[kShapeClasses];      // one per shape class (graph branches)
+  cudaEvent_t fork, join[kShapeClasses];
   cudaEvent_t in_ready, out_ready;
   uint32_t force_slots;
   struct Slot {
     void *host = nullptr;                  // pinned call table
     void *dev = nullptr;                   // device call table
-    unsigned long long *counter = nullptr; // work-queue head
+    unsigned long long *counter = nullptr; // work-queue heads, one per shape class
     cudaEvent_t done = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint32_t mask = 0;                     // shape classes the captured graph launches
+    uint32_t grid[kShapeClasses] = {0};    // CTAs per class in the captured graph
     bool used = false;
   } slot[2];
   int next;
 };
+
+// Launch the persistent kernel of shape class c.
+static cudaError_t launch_batch_class(int c, int grid, const BatchHdr *hdr, const BatchCall *calls,
+                                      unsigned long long *counters, const uint32_t *t0, cudaStream_t st) {
+  const size_t smem = gate_smem_bytes();
+  switch (c) {
+    case 0: batch_kernel<1, 0><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 1: batch_kernel<1, 1><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 2: batch_kernel<1, 2><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 3: batch_kernel<1, 3><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 4: batch_kernel<2, 0><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 5: batch_kernel<2, 1><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    case 6: batch_kernel<3, 0><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+    default: batch_kernel<4, 0><<<grid, kGateThreads, smem, st>>>(hdr, calls, counters, t0); break;
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t set_batch_smem() {
+  const int smem = int(gate_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(batch_kernel<4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
 
 static size_t batch_table_bytes(uint32_t cap) {
   return align256(sizeof(BatchHdr)) + size_t(cap) * sizeof(BatchCall);
@@ -630,6 +664,11 @@ extern "C" int ffss_batch_destroy(ffss_batch *bt) {
   }
   if (bt->in_ready) cudaEventDestroy(bt->in_ready);
   if (bt->out_ready) cudaEventDestroy(bt->out_ready);
+  if (bt->fork) cudaEventDestroy(bt->fork);
+  for (int c = 0; c < kShapeClasses; ++c) {
+    if (bt->join[c]) cudaEventDestroy(bt->join[c]);
+    if (bt->branch[c]) cudaStreamDestroy(bt->branch[c]);
+  }
   if (bt->own) cudaStreamDestroy(bt->own);
   delete bt;
   return FFSS_OK;
@@ -649,18 +688,18 @@ extern "C" int ffss_batch_create(ffss_ctx *ctx, uint32_t max_calls, ffss_batch *
   cudaError_t e = cudaStreamCreateWithFlags(&bt->own, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->in_ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->out_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming);
+  for (int c = 0; c < kShapeClasses; ++c) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->branch[c], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bt->join[c], cudaEventDisableTiming);
+  }
   for (auto &sl : bt->slot) {
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.host, bt->table_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&sl.dev, bt->table_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&sl.counter, sizeof(unsigned long long) * kShapeClasses);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) {
-    static std::once_flag once;
-    int rc = FFSS_OK;
-    std::call_once(once, [&] { rc = set_smem(batch_kernel, gate_smem_bytes()); });
-    if (rc) e = cudaErrorInvalidValue;
-  }
+  if (e == cudaSuccess) e = set_batch_smem();
   if (e != cudaSuccess) {
     ffss_batch_destroy(bt);
     return fail(FFSS_ERR_CUDA, "ffss_batch_create: %s", cudaGetErrorString(e));
@@ -691,7 +730,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
   if (n_calls > bt->cap) return fail(FFSS_ERR_SHAPE, "%u calls > batch capacity %u", n_calls, bt->cap);
   ffss_ctx *ctx = bt->ctx;
   // validate every call before touching any state
-  struct Item { BatchCall c; uint64_t tile_cost; uint64_t tiles; };
+  struct Item { BatchCall c; int cls; uint64_t tile_cost; uint64_t tiles; };
   std::vector<Item> items;
   for (uint32_t i = 0; i < n_calls; ++i) {
     const ffss_call &c = calls[i];
@@ -713,44 +752,74 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
     it.c.z0 = c.z0_dev; it.c.z1 = c.z1_dev;
     it.c.n = c.n;
     it.c.rd = S.r * 16 + S.d;
+    it.cls = shape_class(S.r, S.d);
+    if (it.cls < 0) return fail(FFSS_ERR_UNSUPPORTED, "call %u: n_out=%u degree=%u", i, S.r, S.d);
     uint64_t mx = 0;
     it.c.sched = make_sched(S, batch_slots(bt, S), &mx);
     it.tile_cost = mx;
     it.tiles = (c.n + it.c.sched.E - 1) / it.c.sched.E;
     items.push_back(it);
   }
-  // costliest tiles first (longest-processing-time order shortens the tail)
-  std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.tile_cost > b.tile_cost; });
+  // group by shape class; within a class the costliest tiles go first
+  std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+    return a.cls != b.cls ? a.cls < b.cls : a.tile_cost > b.tile_cost;
+  });
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_batch::Slot &sl = bt->slot[bt->next];
   bt->next ^= 1;
   if (sl.used) CUDA_TRY(cudaEventSynchronize(sl.done));   // the pinned table is free again
   BatchHdr *hdr = static_cast<BatchHdr *>(sl.host);
   BatchCall *tbl = reinterpret_cast<BatchCall *>(static_cast<char *>(sl.host) + align256(sizeof(BatchHdr)));
-  uint64_t tiles = 0;
+  memset(hdr, 0, sizeof(BatchHdr));
+  uint32_t mask = 0;
+  uint32_t grid[kShapeClasses] = {0};
   for (size_t i = 0; i < items.size(); ++i) {
-    items[i].c.tile_begin = tiles;
-    tiles += items[i].tiles;
+    BatchClass &bc = hdr->cls[items[i].cls];
+    if (!(mask >> items[i].cls & 1u)) bc.first = uint32_t(i);
+    mask |= 1u << items[i].cls;
+    items[i].c.tile_begin = bc.total_tiles;
+    bc.total_tiles += items[i].tiles;
+    bc.count += 1;
     tbl[i] = items[i].c;
   }
+  for (int c = 0; c < kShapeClasses; ++c)
+    grid[c] = uint32_t(std::min<uint64_t>(hdr->cls[c].total_tiles, uint64_t(ctx->sm_count)));
   hdr->n_calls = uint32_t(items.size());
-  hdr->total_tiles = tiles;
   hdr->comm = reinterpret_cast<unsigned long long *>(comm);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!sl.exec) {
-    // capture: table upload, queue reset, persistent kernel
+  if (sl.exec && (sl.mask != mask || memcmp(sl.grid, grid, sizeof(grid)) != 0)) {
+    cudaGraphExecDestroy(sl.exec);
+    sl.exec = nullptr;
+  }
+  if (!sl.exec && mask) {
+    // capture: table upload, queue reset, then one persistent kernel per
+    // shape class present, as parallel branches that join on the plan stream
     cudaGraph_t g;
     CUDA_TRY(cudaStreamBeginCapture(bt->own, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(sl.dev, sl.host, bt->table_bytes, cudaMemcpyHostToDevice, bt->own);
-    cudaMemsetAsync(sl.counter, 0, sizeof(unsigned long long), bt->own);
+    cudaMemsetAsync(sl.counter, 0, sizeof(unsigned long long) * kShapeClasses, bt->own);
+    cudaEventRecord(bt->fork, bt->own);
     const BatchHdr *dh = static_cast<const BatchHdr *>(sl.dev);
     const BatchCall *dc = reinterpret_cast<const BatchCall *>(static_cast<char *>(sl.dev) + align256(sizeof(BatchHdr)));
-    batch_kernel<<<ctx->sm_count, kGateThreads, gate_smem_bytes(), bt->own>>>(dh, dc, sl.counter, ctx->t0_dev);
-    CUDA_TRY(cudaStreamEndCapture(bt->own, &g));
-    cudaError_t e = cudaGraphInstantiate(&sl.exec, g, 0);
+    cudaError_t le = cudaSuccess;
+    for (int c = 0; c < kShapeClasses; ++c) {
+      if (!(mask >> c & 1u)) continue;
+      cudaStreamWaitEvent(bt->branch[c], bt->fork, 0);
+      cudaError_t e2 = launch_batch_class(c, int(grid[c]), dh, dc, sl.counter, ctx->t0_dev, bt->branch[c]);
+      if (e2 != cudaSuccess && le == cudaSuccess) le = e2;
+      cudaEventRecord(bt->join[c], bt->branch[c]);
+      cudaStreamWaitEvent(bt->own, bt->join[c], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(bt->own, &g);
+    if (le != cudaSuccess) return fail(FFSS_ERR_CUDA, "batch capture: %s", cudaGetErrorString(le));
+    if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&sl.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    sl.mask = mask;
+    memcpy(sl.grid, grid, sizeof(grid));
   }
+  if (!mask) return FFSS_OK;
   // order: caller stream -> batch stream (graph) -> caller stream
   CUDA_TRY(cudaEventRecord(bt->in_ready, st));
   CUDA_TRY(cudaStreamWaitEvent(bt->own, bt->in_ready, 0));
@@ -776,7 +845,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kNoAllocMaxCalls = 32;
-constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocCounterBytes = 256;   // room for the per-class queue heads
 constexpr size_t kNoAllocTableBytes = ((sizeof(BatchHdr) + 255) & ~size_t(255)) + kNoAllocMaxCalls * sizeof(BatchCall);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocCounterBytes + kNoAllocTableBytes];
 
@@ -795,7 +864,7 @@ static int noalloc_setup(int device, unsigned char **out) {
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr)
       return fail(FFSS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(gate_smem_bytes()));
+    e = set_batch_smem();
     if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     g_noalloc_addr[device] = ptr;
   }
@@ -860,6 +929,7 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
   static_assert(sizeof(Table) <= kNoAllocTableBytes, "table fits the scratch");
   memset(&tbl, 0, sizeof(tbl));
   uint64_t cost[kNoAllocMaxCalls], ntiles[kNoAllocMaxCalls];
+  int cls[kNoAllocMaxCalls];
   uint32_t m = 0;
   for (uint32_t i = 0; i < n_calls; ++i) {
     const ffss_call &c = calls[i];
@@ -882,23 +952,30 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
     b.x0 = c.x0_dev; b.x1 = c.x1_dev; b.y0 = c.y0_dev; b.y1 = c.y1_dev; b.z0 = c.z0_dev; b.z1 = c.z1_dev;
     b.n = c.n;
     b.rd = S.r * 16 + S.d;
+    cls[m] = shape_class(S.r, S.d);
+    if (cls[m] < 0) return fail(FFSS_ERR_UNSUPPORTED, "call %u: n_out=%u degree=%u", i, S.r, S.d);
     b.sched = noalloc_sched(S, slots, &cost[m]);
     ntiles[m] = (c.n + b.sched.E - 1) / b.sched.E;
     ++m;
   }
-  for (uint32_t a = 1; a < m; ++a)   // costliest tiles first
-    for (uint32_t b = a; b > 0 && cost[b] > cost[b - 1]; --b) {
+  // group by shape class, costliest tiles first within a class
+  for (uint32_t a = 1; a < m; ++a)
+    for (uint32_t b = a; b > 0 && (cls[b] < cls[b - 1] || (cls[b] == cls[b - 1] && cost[b] > cost[b - 1])); --b) {
+      std::swap(cls[b], cls[b - 1]);
       std::swap(cost[b], cost[b - 1]);
       std::swap(ntiles[b], ntiles[b - 1]);
       std::swap(tbl.c[b], tbl.c[b - 1]);
     }
-  uint64_t tiles = 0;
+  uint32_t mask = 0;
   for (uint32_t i = 0; i < m; ++i) {
-    tbl.c[i].tile_begin = tiles;
-    tiles += ntiles[i];
+    BatchClass &bc = tbl.hdr.cls[cls[i]];
+    if (!(mask >> cls[i] & 1u)) bc.first = i;
+    mask |= 1u << cls[i];
+    tbl.c[i].tile_begin = bc.total_tiles;
+    bc.total_tiles += ntiles[i];
+    bc.count += 1;
   }
   tbl.hdr.n_calls = m;
-  tbl.hdr.total_tiles = tiles;
   tbl.hdr.comm = reinterpret_cast<unsigned long long *>(comm);
   if (m == 0) return FFSS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -908,11 +985,15 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
   // the table is staged from host memory before this call returns; the queue
   // head must start at zero on every call
   CUDA_TRY(cudaMemcpyAsync(dtab, &tbl, sizeof(tbl), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
-  batch_kernel<<<ctx->sm_count, kGateThreads, gate_smem_bytes(), st>>>(
-      reinterpret_cast<const BatchHdr *>(dtab), reinterpret_cast<const BatchCall *>(dtab + offsetof(Table, c)),
-      counter, ctx->t0_dev);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long) * kShapeClasses, st));
+  for (int c = 0; c < kShapeClasses; ++c) {   // one persistent kernel per shape class, in stream order
+    if (!(mask >> c & 1u)) continue;
+    const int grid = int(std::min<uint64_t>(tbl.hdr.cls[c].total_tiles, uint64_t(ctx->sm_count)));
+    cudaError_t e = launch_batch_class(c, grid, reinterpret_cast<const BatchHdr *>(dtab),
+                                       reinterpret_cast<const BatchCall *>(dtab + offsetof(Table, c)), counter,
+                                       ctx->t0_dev, st);
+    if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+  }
   for (uint32_t i = 0; i < n_calls; ++i)
     if (calls[i].n) { calls[i].k0->used |= 3; calls[i].k1->used |= 3; }
   return FFSS_OK;

@@ -83,6 +83,23 @@ struct AesDcfCall {
   __device__ __forceinline__ uint4 operator()(uint4 in) const { return aes_dcf_call(in, tb.base, tb.lane4); }
 };
 
+// Four AES_K blocks per out-of-line call: the four encryptions interleave,
+// which a one-block call cannot do (the dealer's levels need 4 or 4 + 4V
+// independent blocks each).
+__device__ __noinline__ Blk4 aes4_dcf_call(Blk4 in, const char *base, uint32_t lane4) {
+  const Tab tb{base, lane4};
+  Blk4 o;
+  o.v[0] = aes128v<kAesVariant>(in.v[0], RkDcf(), tb);
+  o.v[1] = aes128v<kAesVariant>(in.v[1], RkDcf(), tb);
+  o.v[2] = aes128v<kAesVariant>(in.v[2], RkDcf(), tb);
+  o.v[3] = aes128v<kAesVariant>(in.v[3], RkDcf(), tb);
+  return o;
+}
+struct AesDcfCall4 {
+  Tab tb;
+  __device__ __forceinline__ Blk4 operator()(const Blk4 &in) const { return aes4_dcf_call(in, tb.base, tb.lane4); }
+};
+
 // Stage the four rotated T-tables, 32 lane copies each, and the spec.
 __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, const uint32_t *t0,
                                              const DevSpec *spec) {
@@ -322,142 +339,6 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   *sent_io += sent;
 }
 
-// The same tile with the output count r, degree d and payload length
-// p = r (d + 1) known only at run time (batch kernel: one CTA meets calls of
-// every shape).  Only the payload block count V (1 for p <= 2, 2 for p <= 4)
-// is compiled in, so the DCF walks, which hold all the work, exist once per
-// V; the reduction and Horner rounds index fixed-size register arrays.
-template <int V>
-__device__ __forceinline__ void gate_tile_rt(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
-                                             uint64_t tile, unsigned long long *sent_io) {
-  constexpr int PM = 2 * V;
-  const DevSpec &S = *G.spec;
-  const KeyLayout &L = A.L;
-  const AesDcfInline aes{tb};
-  ulonglong2 *box = G.box;
-  const uint32_t R = S.r, D = S.d, P = S.p;
-  const uint32_t NS = SC.S, E = SC.E;
-  const uint32_t b = threadIdx.x >> 8;
-  const uint32_t rem = threadIdx.x & 255u;
-  const uint32_t slot = rem / E, le = rem - slot * E;
-  const bool lead = slot == 0;
-  const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
-  const char *kb = b ? A.k1 : A.k0;
-  const uint64_t e = tile * E + le;
-  const bool valid = e < A.n;
-  unsigned long long sent = 0;
-  // (1) shares -> masked opening (App. C); .y keeps the sender's own r_b
-  if (lead) {
-    uint64_t msg = 0, rr = 0;
-    if (valid) {
-      rr = reinterpret_cast<const uint64_t *>(kb + L.off_r)[e];
-      msg = (b ? A.x1 : A.x0)[e] + rr;
-      sent += 8;
-    }
-    box[b * E + le] = make_ulonglong2(msg, rr);
-  }
-  __syncthreads();
-  const uint64_t xhat = box[le].x + box[E + le].x;
-  // (2)(3) this slot's DCF walks
-  uint32_t atoms = 0;
-  uint64_t acc[PM];
-#pragma unroll
-  for (int q = 0; q < PM; ++q) acc[q] = 0;
-  if (valid) {
-    uint32_t it = it0;
-    for (; it < it1 && SC.item[it] < S.T; ++it) {
-      const uint32_t t = SC.item[it];
-      atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
-    }
-    const uint32_t k = S.k;
-    const uint32_t u = view(xhat, k, 0);
-    for (; it < it1; ++it) {
-      const char *l = kb + L.off_l[SC.item[it] - S.T];
-      dcf_vec_eval_acc_rt<V>(b, k, u, reinterpret_cast<const uint4 *>(l) + e,
-                             reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e, L.n, P, acc, aes);
-    }
-  }
-  const uint64_t r_b = lead ? box[b * E + le].y : 0;
-  const uint32_t ri = (b * NS + slot) * E + le;
-  G.red_atoms[ri] = atoms;
-#pragma unroll
-  for (int q = 0; q < PM; ++q) G.red_acc[uint64_t(ri) * kMaxP + q] = acc[q];
-  __syncthreads();
-  uint32_t z = 0;
-  uint64_t pay[PM], y[kMaxP];
-  uint64_t xs = 0;
-  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
-  if (lead) {
-    for (uint32_t s2 = 1; s2 < NS; ++s2) {
-      const uint32_t rj = (b * NS + s2) * E + le;
-      atoms |= G.red_atoms[rj];
-#pragma unroll
-      for (int q = 0; q < PM; ++q) acc[q] += G.red_acc[uint64_t(rj) * kMaxP + q];
-    }
-    const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
-#pragma unroll
-    for (int q = 0; q < PM; ++q)
-      pay[q] = (valid && q < int(P)) ? vl[uint64_t(q) * L.n + e] + (b ? 0ull - acc[q] : acc[q]) : 0ull;
-    if (valid) z = combine_bits(b, S, L, kb, e, atoms);
-    xs = b == 0 ? xhat - r_b : 0ull - r_b;
-    // y_o = c_{o,d}: payload word o (d + 1) + d
-#pragma unroll
-    for (int o = 0; o < kMaxP; ++o) {
-      y[o] = 0;
-#pragma unroll
-      for (int q = 0; q < PM; ++q)
-        if (uint32_t(o) < R && uint32_t(q) == o * (D + 1) + D) y[o] = pay[q];
-    }
-  }
-  // (5) Horner: d Beaver rounds
-  for (int jj = int(D) - 1; jj >= 0; --jj) {
-    uint64_t ta[kMaxP], tbv[kMaxP], tc[kMaxP];
-    if (lead) {
-#pragma unroll
-      for (int o = 0; o < kMaxP; ++o) {
-        if (uint32_t(o) >= R) break;
-        const uint32_t mi = (D - 1 - jj) * R + o;
-        if (valid) {
-          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
-          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
-          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
-          sent += 16;
-        } else {
-          ta[o] = tbv[o] = tc[o] = 0;
-        }
-        box[(b * E + le) * R + o] = make_ulonglong2(y[o] - ta[o], xs - tbv[o]);
-      }
-    }
-    __syncthreads();
-    if (lead) {
-#pragma unroll
-      for (int o = 0; o < kMaxP; ++o) {
-        if (uint32_t(o) >= R) break;
-        const ulonglong2 m0 = box[le * R + o], m1 = box[(E + le) * R + o];
-        const uint64_t Ev = m0.x + m1.x, Fv = m0.y + m1.y;
-        uint64_t zz = Ev * tbv[o] + Fv * ta[o] + tc[o];
-        if (b == 0) zz += Ev * Fv;
-        uint64_t c = 0;
-#pragma unroll
-        for (int q = 0; q < PM; ++q)
-          if (uint32_t(q) == o * (D + 1) + jj) c = pay[q];
-        y[o] = zz + c;
-      }
-    }
-    __syncthreads();
-  }
-  if (lead && valid) {
-#pragma unroll
-    for (int o = 0; o < kMaxP; ++o) {
-      if (uint32_t(o) >= R) break;
-      (b ? A.y1 : A.y0)[e * R + o] = y[o];
-    }
-    (b ? A.z1 : A.z0)[e] = z;
-  }
-  __syncthreads();
-  *sent_io += sent;
-}
-
 __device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned long long sent) {
   if (!comm) return;
 #pragma unroll
@@ -501,13 +382,27 @@ struct BatchCall {
   Sched sched;
 };
 
+// Calls are grouped by shape class (n_out, degree); each class present is
+// drained by its own persistent kernel over calls [first, first + count).
+constexpr int kShapeClasses = 8;
+
+struct BatchClass {
+  uint32_t first, count;
+  uint64_t total_tiles;      // tiles of this class's calls (tile_begin restarts at 0 per class)
+};
+
 struct BatchHdr {
   uint32_t n_calls;
   uint32_t pad;
-  uint64_t total_tiles;
   unsigned long long *comm;   // [2] bytes sent per party, may be null
-  uint64_t pad2;
+  BatchClass cls[kShapeClasses];
 };
+
+// (n_out, degree) -> shape class, or -1
+__host__ __device__ constexpr int shape_class(uint32_t r, uint32_t d) {
+  return r == 1 ? (d <= 3 ? int(d) : -1) : r == 2 ? (d <= 1 ? 4 + int(d) : -1) : r == 3 ? (d == 0 ? 6 : -1)
+       : r == 4 ? (d == 0 ? 7 : -1) : -1;
+}
 
 constexpr uint32_t kBatchMaxCalls = 512;
 
@@ -531,8 +426,10 @@ __device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n)
   return L;
 }
 
-__global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *hdr, const BatchCall *calls,
-                                                                unsigned long long *counter, const uint32_t *t0) {
+template <int R, int D>
+__global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *hdr, const BatchCall *all_calls,
+                                                                unsigned long long *counters, const uint32_t *t0) {
+  constexpr int C = shape_class(R, D);
   extern __shared__ __align__(16) unsigned char smem[];
   const GateSmem G = carve_gate_smem(smem);
   __shared__ GateArgs cur;
@@ -540,18 +437,20 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
   __shared__ int cur_call;
   __shared__ int restage;
   __shared__ unsigned long long next_tile;
+  __shared__ unsigned long long s_begin[kBatchMaxCalls];   // first tile of each call of this class
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
     const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
     const uint32_t v = t0[e];
     tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
   }
-  __shared__ unsigned long long s_begin[kBatchMaxCalls];   // first tile of each call
-  const uint32_t n_calls = hdr->n_calls;
+  const BatchCall *calls = all_calls + hdr->cls[C].first;
+  const uint32_t n_calls = hdr->cls[C].count;
+  const unsigned long long total = hdr->cls[C].total_tiles;
+  unsigned long long *counter = counters + C;
   for (uint32_t i = threadIdx.x; i < n_calls; i += blockDim.x) s_begin[i] = calls[i].tile_begin;
   if (threadIdx.x == 0) cur_call = -1;
   const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
-  const unsigned long long total = hdr->total_tiles;
   unsigned long long sent = 0;
   // thread 0 claims the next tile one tile ahead, so the atomic's round trip
   // overlaps the current tile's work
@@ -597,9 +496,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
       if (threadIdx.x == 0) cur.L = device_layout(*G.spec, cur.n);
       __syncthreads();
     }
-    const uint64_t local = next_tile;
-    if (G.spec->V == 1) gate_tile_rt<1>(cur, cur_sched, G, tb, local, &sent);
-    else gate_tile_rt<2>(cur, cur_sched, G, tb, local, &sent);
+    gate_tile<R, D>(cur, cur_sched, G, tb, next_tile, &sent);
   }
   flush_comm(hdr->comm, sent);
 }
@@ -659,7 +556,7 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
   const DevSpec &S = *sspec;
   const KeyLayout &L = A.L;
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
-  const AesDcfCall rkd{tb};
+  const AesDcfCall4 rkd{tb};
   const uint64_t n = A.n;
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
        e += uint64_t(gridDim.x) * blockDim.x) {
