@@ -371,7 +371,9 @@ static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t 
   int rc = FFSS_OK;
   std::call_once(once, [&] { rc = set_smem(keygen_kernel<P>, smem); });
   if (rc) return rc;
-  keygen_kernel<P><<<grid_for(ctx, A.n, 512), 512, smem, st>>>(A);
+  // one warp per (key, 32 elements) unit; one 512-thread CTA per SM
+  const uint64_t units = (A.n + 31) / 32 * A.n_items;
+  keygen_kernel<P><<<grid_for(ctx, units, 16), 512, smem, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
 }
@@ -394,6 +396,7 @@ extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t s
   A.k0 = k0->buf; A.k1 = k1->buf;
   A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
   A.n = n; A.e0 = 0; A.call_id = call_id;
+  A.n_items = (spec->host.M > 1 ? spec->host.M - 1 : 0) + spec->host.T + 1;
   key_schedule(seed, A.rk.w);
   A.t0 = ctx->t0_dev;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

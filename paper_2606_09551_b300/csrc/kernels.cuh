@@ -1,6 +1,6 @@
 // CUDA kernels of the FuseFSS online path and its dealer (sm_103a).
 //
-//  keygen_kernel<P>      GPU dealer: one thread per element, both parties' keys.
+//  keygen_kernel<P>      GPU dealer: one warp per (key, 32 elements), both parties.
 //  gate_kernel<R,D,E>    the whole two-party gate, both parties of a tile of E
 //                        elements in one CTA, exchanges through shared-memory
 //                        outboxes (the per-party message buffers).
@@ -26,6 +26,7 @@ struct KeygenArgs {
   uint64_t n;
   uint64_t e0;         // element index of this launch's first element within its call
   uint32_t call_id;
+  uint32_t n_items;    // work items per element: M-1 lookup keys + T comparison keys + 1
   RkParam rk;          // AES-128 key schedule of the run seed (dealer PRG)
   const uint32_t *t0;  // global T-table 0
 };
@@ -558,8 +559,20 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
   const AesDcfCall4 rkd{tb};
   const uint64_t n = A.n;
-  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
-       e += uint64_t(gridDim.x) * blockDim.x) {
+  // Work unit = (item, 32 consecutive elements), one warp each.  Items, in
+  // falling cost: the M-1 lookup keys, the T comparison keys, then the rest
+  // of an element's material (mask shares, input shares, carries, last
+  // payload, triples).  Every item recomputes r_in (one block) itself.
+  const uint32_t n_vec = S.M > 1 ? S.M - 1 : 0;
+  const uint32_t n_items = A.n_items;
+  const uint64_t groups = (n + 31) / 32;
+  const uint64_t units = groups * n_items;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint64_t u = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; u < units;
+       u += uint64_t(gridDim.x) * blockDim.x / 32) {
+    const uint32_t item = uint32_t(u / groups);
+    const uint64_t e = (u % groups) * 32 + lane;
+    if (e >= n) continue;
     // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id);
     // the counter uses the element's index within the whole call, so a call
     // dealt in chunks gets the same material as in one launch
@@ -568,26 +581,25 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       return aes_rk_call(make_uint4(dr, uint32_t(ge), uint32_t(ge >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
     };
     const uint64_t r_in = lo64(prg(kDrawRin));
-    const uint64_t r0 = lo64(prg(kDrawRsh));
-    reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;
-    reinterpret_cast<uint64_t *>(A.k1 + L.off_r)[e] = r_in - r0;
-    if (A.x_plain) {
-      const uint64_t xs = lo64(prg(kDrawXsh));
-      A.x0[e] = xs;
-      A.x1[e] = A.x_plain[e] - xs;
-    }
-    // carries of the masked rewrites: w_j = 1[r_f + gamma_j >= 2^f]
-    uint32_t carries = 0;
-    for (uint32_t j = 0; j < S.n_prim; ++j) {
-      const uint32_t f = S.prim_f[j];
-      const uint64_t sum = (r_in & ((uint64_t(1) << f) - 1)) + S.prim_gamma[j];
-      carries |= uint32_t(sum >> f) << j;
-    }
-    const uint32_t cs0 = prg(kDrawCarry).x;
-    reinterpret_cast<uint32_t *>(A.k0 + L.off_carry)[e] = cs0;
-    reinterpret_cast<uint32_t *>(A.k1 + L.off_carry)[e] = cs0 ^ carries;
-    // packed-comparison keys: alpha = r_f for the r-atom, theta_j otherwise
-    for (uint32_t t = 0; t < S.T; ++t) {
+    if (item < n_vec) {
+      // lookup key j = item + 1: boundary B_j, payload step v_{j-1} - v_j
+      uint64_t B[kMaxM + 2];
+      uint32_t ord[kMaxM + 1];
+      lookup_boundaries(S, r_in, B, ord);
+      const uint32_t j = item + 1;
+      uint64_t beta[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) beta[q] = S.coeff[ord[j - 1] * P + q] - S.coeff[ord[j] * P + q];
+      const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
+      const uint4 s0 = prg(di), s1 = prg(di + 1);
+      char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
+      dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
+                     reinterpret_cast<uint4 *>(l1) + e,
+                     reinterpret_cast<uint64_t *>(l0 + 16ull * (S.k + 1) * n) + e,
+                     reinterpret_cast<uint64_t *>(l1 + 16ull * (S.k + 1) * n) + e, n, rkd);
+    } else if (item < n_vec + S.T) {
+      // packed-comparison key t: alpha = r_f for the r-atom, theta_j otherwise
+      const uint32_t t = item - n_vec;
       const uint32_t f = S.q_f[t];
       const uint64_t mask = (uint64_t(1) << f) - 1;
       const int j = S.q_prim[t];
@@ -598,46 +610,53 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
                   reinterpret_cast<uint4 *>(q1) + e,
                   reinterpret_cast<uint64_t *>(q0 + 16ull * (f + 1) * n) + e,
                   reinterpret_cast<uint64_t *>(q1 + 16ull * (f + 1) * n) + e, n, rkd);
-    }
-    // lookup instance and its M-1 vector DCFs
-    uint32_t last = 0;
-    if (S.M > 1) {
-      uint64_t B[kMaxM + 2];
-      uint32_t ord[kMaxM + 1];
-      lookup_boundaries(S, r_in, B, ord);
-      for (uint32_t j = 1; j < S.M; ++j) {
-        uint64_t beta[P];
-#pragma unroll
-        for (int q = 0; q < P; ++q) beta[q] = S.coeff[ord[j - 1] * P + q] - S.coeff[ord[j] * P + q];
-        const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
-        const uint4 s0 = prg(di), s1 = prg(di + 1);
-        char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
-        dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                       reinterpret_cast<uint4 *>(l1) + e,
-                       reinterpret_cast<uint64_t *>(l0 + 16ull * (S.k + 1) * n) + e,
-                       reinterpret_cast<uint64_t *>(l1 + 16ull * (S.k + 1) * n) + e, n, rkd);
+    } else {
+      const uint64_t r0 = lo64(prg(kDrawRsh));
+      reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;
+      reinterpret_cast<uint64_t *>(A.k1 + L.off_r)[e] = r_in - r0;
+      if (A.x_plain) {
+        const uint64_t xs = lo64(prg(kDrawXsh));
+        A.x0[e] = xs;
+        A.x1[e] = A.x_plain[e] - xs;
       }
-      last = ord[S.M - 1];
-    }
+      // carries of the masked rewrites: w_j = 1[r_f + gamma_j >= 2^f]
+      uint32_t carries = 0;
+      for (uint32_t j = 0; j < S.n_prim; ++j) {
+        const uint32_t f = S.prim_f[j];
+        const uint64_t sum = (r_in & ((uint64_t(1) << f) - 1)) + S.prim_gamma[j];
+        carries |= uint32_t(sum >> f) << j;
+      }
+      const uint32_t cs0 = prg(kDrawCarry).x;
+      reinterpret_cast<uint32_t *>(A.k0 + L.off_carry)[e] = cs0;
+      reinterpret_cast<uint32_t *>(A.k1 + L.off_carry)[e] = cs0 ^ carries;
+      // shares of the last lookup payload v_{M-1}
+      uint32_t last = 0;
+      if (S.M > 1) {
+        uint64_t B[kMaxM + 2];
+        uint32_t ord[kMaxM + 1];
+        lookup_boundaries(S, r_in, B, ord);
+        last = ord[S.M - 1];
+      }
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const uint64_t sh = lo64(prg(kDrawVlast + q));
-      reinterpret_cast<uint64_t *>(A.k0 + L.off_vlast)[uint64_t(q) * n + e] = sh;
-      reinterpret_cast<uint64_t *>(A.k1 + L.off_vlast)[uint64_t(q) * n + e] = S.coeff[last * P + q] - sh;
-    }
-    // Beaver triples (a, b, c = a b), fresh per multiplication
-    uint64_t *tr0 = reinterpret_cast<uint64_t *>(A.k0 + L.off_trip);
-    uint64_t *tr1 = reinterpret_cast<uint64_t *>(A.k1 + L.off_trip);
-    for (uint32_t mi = 0; mi < S.d * S.r; ++mi) {
-      const uint32_t di = S.base_triples + 5 * mi;
-      const uint64_t a = lo64(prg(di)), bb = lo64(prg(di + 1));
-      const uint64_t a0 = lo64(prg(di + 2)), b0 = lo64(prg(di + 3)), c0 = lo64(prg(di + 4));
-      tr0[(uint64_t(mi) * 3 + 0) * n + e] = a0;
-      tr1[(uint64_t(mi) * 3 + 0) * n + e] = a - a0;
-      tr0[(uint64_t(mi) * 3 + 1) * n + e] = b0;
-      tr1[(uint64_t(mi) * 3 + 1) * n + e] = bb - b0;
-      tr0[(uint64_t(mi) * 3 + 2) * n + e] = c0;
-      tr1[(uint64_t(mi) * 3 + 2) * n + e] = a * bb - c0;
+      for (int q = 0; q < P; ++q) {
+        const uint64_t sh = lo64(prg(kDrawVlast + q));
+        reinterpret_cast<uint64_t *>(A.k0 + L.off_vlast)[uint64_t(q) * n + e] = sh;
+        reinterpret_cast<uint64_t *>(A.k1 + L.off_vlast)[uint64_t(q) * n + e] = S.coeff[last * P + q] - sh;
+      }
+      // Beaver triples (a, b, c = a b), fresh per multiplication
+      uint64_t *tr0 = reinterpret_cast<uint64_t *>(A.k0 + L.off_trip);
+      uint64_t *tr1 = reinterpret_cast<uint64_t *>(A.k1 + L.off_trip);
+      for (uint32_t mi = 0; mi < S.d * S.r; ++mi) {
+        const uint32_t di = S.base_triples + 5 * mi;
+        const uint64_t a = lo64(prg(di)), bb = lo64(prg(di + 1));
+        const uint64_t a0 = lo64(prg(di + 2)), b0 = lo64(prg(di + 3)), c0 = lo64(prg(di + 4));
+        tr0[(uint64_t(mi) * 3 + 0) * n + e] = a0;
+        tr1[(uint64_t(mi) * 3 + 0) * n + e] = a - a0;
+        tr0[(uint64_t(mi) * 3 + 1) * n + e] = b0;
+        tr1[(uint64_t(mi) * 3 + 1) * n + e] = bb - b0;
+        tr0[(uint64_t(mi) * 3 + 2) * n + e] = c0;
+        tr1[(uint64_t(mi) * 3 + 2) * n + e] = a * bb - c0;
+      }
     }
   }
 }

@@ -294,6 +294,7 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
         A.k0 = k0->buf; A.k1 = k1->buf;
         A.x_plain = o.x + r.elem; A.x0 = x0; A.x1 = x1;
         A.n = n; A.e0 = r.elem; A.call_id = call_id;
+        A.n_items = (o.spec->host.M > 1 ? o.spec->host.M - 1 : 0) + o.spec->host.T + 1;
         key_schedule(sv->cfg.seed, A.rk.w);
         A.t0 = sv->ctx->t0_dev;
         switch (o.spec->host.p) {
