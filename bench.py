@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=8)
     ap.add_argument("--served-layers", type=int, default=2)
     ap.add_argument("--no-large", action="store_true", help="skip the streamed large-layer run")
+    ap.add_argument("--gpt2-layers", type=int, default=1, help="layers per request in the 32-request batch")
+    ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
@@ -362,14 +364,16 @@ def run_ours(args, rank, world, local_rank):
                    "form": "one persistent work-queue launch per layer, CUDA graph replay"}
         bt.close()
 
-    served = large = None
-    if not (args.no_served and args.no_large):
+    served = large = gpt2 = None
+    if not (args.no_served and args.no_large and args.no_gpt2):
         del sets
         torch.cuda.empty_cache()
     if not args.no_served:
         served = run_served(ctx, args, dev)
     if not args.no_large:
         large = run_large_layer(ctx, dev)
+    if not args.no_gpt2:
+        gpt2 = run_gpt2_batch(ctx, args, dev)
 
     # roofline of the dominant kernel (the op with the largest launch time)
     dom = max(calls, key=lambda c: per_op_ms[c.name])
@@ -427,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "served": served,
         "large_layer": large,
+        "gpt2_batch": gpt2,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)
@@ -437,15 +442,57 @@ def run_ours(args, rank, world, local_rank):
 # served form: BERT-large-shaped requests, Poisson arrivals, key streaming
 # ---------------------------------------------------------------------------
 
+def _layer_ops(css, dev, gen, L, heads, mlp, hidden, f, act="gelu", n_ln=1):
+    """Synthetic nonlinear-layer inputs on the device: activation
+    pre-activations ~ N(0,1) on L x mlp, max-subtracted attention scores
+    ~ N(0, 2^2) on heads x L x L, their softmax row sums, and per-token
+    LayerNorm variances of a N(0,1) L x hidden state (+1e-5), quantized at f
+    fractional bits.  Returns the server's op tuples with output buffers."""
+    import torch
+    scale = float(2 ** f)
+
+    def fx(t):
+        return torch.round(t * scale).to(torch.int64).view(torch.uint64)
+
+    g = torch.randn(L, mlp, device=dev, generator=gen, dtype=torch.float64)
+    sc = 2.0 * torch.randn(heads, L, L, device=dev, generator=gen, dtype=torch.float64)
+    sc = sc - sc.amax(dim=-1, keepdim=True)
+    rows = torch.exp(sc).sum(dim=-1)
+    var = torch.randn(n_ln * L, hidden, device=dev, generator=gen, dtype=torch.float64).var(dim=-1) + 1e-5
+    xs = [(act, fx(g.reshape(-1))), ("exp", fx(sc.reshape(-1))), ("recip", fx(rows.reshape(-1))),
+          ("rsqrt", fx(var.reshape(-1)))]
+    del g, sc, rows, var
+    ops = []
+    for name, x in xs:
+        y = torch.empty(x.numel(), dtype=torch.uint64, device=dev)
+        z = torch.empty(x.numel(), dtype=torch.uint32, device=dev)
+        ops.append((css[name], x, y, torch.empty_like(y), z, torch.empty_like(z)))
+    return ops
+
+
+def _server_result(sv, nreq, clk, wall):
+    st = sv.summary()
+    infos = [sv.request_info(i) for i in range(nreq)]
+    queue = sorted(max(0.0, r["admitted_ms"] - r["arrival_ms"]) for r in infos)
+    span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
+    return st, {"value": st["elements"] / span_s, "unit": "elements/s",
+                "eval_only_elements_per_s": st["elements"] / (st["eval_ms"] * 1e-3),
+                "note": "includes the on-device dealer: keys are streamed through the key pool, not preloaded",
+                "requests": nreq, "elements": int(st["elements"]), "steps": int(st["steps"]),
+                "chunks": int(st["chunks"]), "batched_launches": int(st["steps"]),
+                "layer_ms_p50": st["layer_ms_p50"], "layer_ms_p99": st["layer_ms_p99"],
+                "layer_ms_max": st["layer_ms_max"],
+                "queue_ms_p50": queue[len(queue) // 2], "queue_ms_max": queue[-1],
+                "span_s": span_s, "wall_s": wall, "clocks": clk.summary()}
+
+
 def run_served(ctx, args, dev):
     """A finite trace of secure-inference requests through the library's
     continuous-batching server: BERT-large layer shapes (hidden 1024, 16 heads,
     MLP 4096), sequence lengths log-uniform in [16, 2048], Poisson arrivals
     at 20 requests/s, a 64 GB key budget; keys are made on the device chunk by
-    chunk just before use.  Inputs are synthetic activations drawn on the
-    device (GeLU pre-activations ~ N(0,1), max-subtracted scores ~ N(0, 2^2),
-    softmax row sums, LayerNorm variances), reused by every layer of a
-    request; every layer gets fresh masks and keys."""
+    chunk just before use.  Every layer of a request reuses its inputs and gets
+    fresh masks and keys."""
     import numpy as np
     import torch
 
@@ -461,30 +508,11 @@ def run_served(ctx, args, dev):
            "recip": F.CompiledSpec(S.recip16(f=f), ctx), "rsqrt": F.CompiledSpec(S.rsqrt16(f=f), ctx)}
     gen = torch.Generator(device=dev)
     gen.manual_seed(I.MASTER_SEED)
-    scale = float(2 ** f)
-
-    def fx(t):
-        return torch.round(t * scale).to(torch.int64).view(torch.uint64)
-
     total = 0
     pending = []
     for i, L in enumerate(lens):
-        L = int(L)
-        g = torch.randn(L, 4096, device=dev, generator=gen, dtype=torch.float64)
-        sc = 2.0 * torch.randn(16, L, L, device=dev, generator=gen, dtype=torch.float64)
-        sc = sc - sc.amax(dim=-1, keepdim=True)
-        rows = torch.exp(sc).sum(dim=-1)
-        var = torch.randn(L, 1024, device=dev, generator=gen, dtype=torch.float64).var(dim=-1) + 1e-5
-        xs = {"gelu": fx(g.reshape(-1)), "exp": fx(sc.reshape(-1)), "recip": fx(rows.reshape(-1)),
-              "rsqrt": fx(var.reshape(-1))}
-        del g, sc, rows, var
-        ops = []
-        for name in ("gelu", "exp", "recip", "rsqrt"):
-            x = xs[name]
-            y = torch.empty(x.numel(), dtype=torch.uint64, device=dev)
-            z = torch.empty(x.numel(), dtype=torch.uint32, device=dev)
-            ops.append((css[name], x, y, torch.empty_like(y), z, torch.empty_like(z)))
-            total += x.numel() * nlay
+        ops = _layer_ops(css, dev, gen, int(L), 16, 4096, 1024, f)
+        total += sum(o[1].numel() for o in ops) * nlay
         pending.append(([ops] * nlay, float(arrivals[i]), 10000 + 100 * i))
     torch.cuda.synchronize()
     # the server clock starts here: arrivals are offsets from its creation
@@ -495,23 +523,55 @@ def run_served(ctx, args, dev):
     with ClockSampler(int(dev.split(":")[1])) as clk:
         sv.run()
     wall = time.perf_counter() - t0
-    st = sv.summary()
-    infos = [sv.request_info(i) for i in range(nreq)]
-    queue = sorted(max(0.0, r["admitted_ms"] - r["arrival_ms"]) for r in infos)
-    span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
-    res = {"value": st["elements"] / span_s, "unit": "elements/s",
-           "note": "served throughput includes the on-device dealer (keys are streamed, not preloaded)",
-           "requests": nreq, "layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
-           "elements": int(st["elements"]), "steps": int(st["steps"]), "chunks": int(st["chunks"]),
-           "layer_ms_p50": st["layer_ms_p50"], "layer_ms_p99": st["layer_ms_p99"],
-           "layer_ms_max": st["layer_ms_max"],
-           "queue_ms_p50": queue[len(queue) // 2], "queue_ms_max": queue[-1],
-           "offered_requests_per_s": 20.0,
-           "sustainable_requests_per_s": nreq / span_s,
-           "wall_s": wall, "clocks": clk.summary(),
-           "config": "BERT-large shapes (hidden 1024, 16 heads, MLP 4096), L log-uniform [16, 2048], "
-                     "Poisson 20 req/s, 64 GB key budget, max 8 admitted, chunks <= 4M elements"}
+    st, res = _server_result(sv, nreq, clk, wall)
     assert st["elements"] == total
+    res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
+                "offered_requests_per_s": 20.0,
+                "sustainable_requests_per_s": nreq / res["span_s"],
+                "config": "BERT-large shapes (hidden 1024, 16 heads, MLP 4096), L log-uniform [16, 2048], "
+                          "Poisson 20 req/s, 64 GB key budget, max 8 admitted, chunks <= 4M elements"})
+    sv.close()
+    return res
+
+
+def run_gpt2_batch(ctx, args, dev):
+    """Config 3: 32 GPT-2-small-shaped requests (hidden 768, 12 heads, MLP
+    3072), sequence lengths uniform in [32, 1024], all present at once; every
+    step evaluates chunks of all admitted requests' GeLU / exp / reciprocal /
+    rsqrt calls in one batched launch, keys streamed through a 64 GB pool."""
+    import numpy as np
+    import torch
+
+    from paper_2606_09551_b300 import fusefss as F
+    from paper_2606_09551_b300 import inputs as I
+    from paper_2606_09551_b300 import specs as S
+    rng = np.random.default_rng([I.MASTER_SEED, 33])
+    nreq, nlay = 32, args.gpt2_layers
+    lens = rng.integers(32, 1025, nreq)
+    f = 12
+    css = {"gelu": F.CompiledSpec(S.gelu8(f=f), ctx), "exp": F.CompiledSpec(S.nexp16(f=f), ctx),
+           "recip": F.CompiledSpec(S.recip16(f=f), ctx), "rsqrt": F.CompiledSpec(S.rsqrt16(f=f), ctx)}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(I.MASTER_SEED + 3)
+    total = 0
+    pending = []
+    for i, L in enumerate(lens):
+        ops = _layer_ops(css, dev, gen, int(L), 12, 3072, 768, f, n_ln=2)
+        total += sum(o[1].numel() for o in ops) * nlay
+        pending.append(([ops] * nlay, 0.0, 20000 + 100 * i))
+    torch.cuda.synchronize()
+    sv = F.Server(ctx, 64 << 30, 32, 1 << 22, I.KEY_SEED)
+    for layers, arr, cid in pending:
+        sv.submit(layers, arr, call_id_base=cid)
+    t0 = time.perf_counter()
+    with ClockSampler(int(dev.split(":")[1])) as clk:
+        sv.run()
+    wall = time.perf_counter() - t0
+    st, res = _server_result(sv, nreq, clk, wall)
+    assert st["elements"] == total
+    res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
+                "config": "32 GPT-2-small requests (hidden 768, 12 heads, MLP 3072, 2 LayerNorms), "
+                          "L uniform [32, 1024], %d of 12 layers each, 64 GB key budget" % nlay})
     sv.close()
     return res
 
@@ -568,6 +628,7 @@ def run_large_layer(ctx, dev):
     key_tb = sum(2 * css[n].shape.key_bytes_per_elem * xs[n].numel() for n in xs) / 1e12
     sv.close()
     return {"value": total / span_s, "unit": "elements/s", "elements": int(total), "layer_ms": st["layer_ms_max"],
+            "eval_only_elements_per_s": total / (st["eval_ms"] * 1e-3),
             "steps": int(st["steps"]), "chunks": int(st["chunks"]), "keys_tb_streamed": key_tb,
             "wall_s": wall, "clocks": clk.summary(),
             "note": "includes the on-device dealer: keys are streamed through a 64 GB pool, not preloaded",

@@ -294,6 +294,7 @@ typedef struct {
     uint64_t elements, steps, chunks, layers;
     double first_admit_ms, last_done_ms;
     double layer_ms_p50, layer_ms_p99, layer_ms_max;
+    double eval_ms;             /* GPU time of the batched evaluations (dealer excluded) */
 } ffss_server_stats;
 
 /* The served form (no counterpart in the paper, which evaluates one model at

@@ -48,6 +48,7 @@ struct SrvChunk {
 
 struct SrvStep {
   int half;
+  cudaEvent_t start;            // on the eval stream, after the dealer's chunks are ready
   cudaEvent_t done;
   std::vector<SrvChunk> chunks;
 };
@@ -71,6 +72,7 @@ struct ffss_server {
   std::vector<cudaEvent_t> free_events;
   uint64_t elements = 0, steps = 0, chunks = 0;
   double first_admit = -1, last_done = -1;
+  double eval_ms = 0;                 // GPU time of the batched evaluations alone
   std::vector<double> all_layer_ms;
 };
 
@@ -94,6 +96,9 @@ static cudaEvent_t srv_event(ffss_server *sv) {
 // Retire a completed step: advance each chunk's request, close layers.
 static void srv_retire(ffss_server *sv, SrvStep &st) {
   const double t = srv_gpu_ms(sv, st.done);
+  float ev_ms = 0;
+  if (cudaEventElapsedTime(&ev_ms, st.start, st.done) == cudaSuccess) sv->eval_ms += ev_ms;
+  sv->free_events.push_back(st.start);
   for (auto &c : st.chunks) {
     SrvReq &r = sv->reqs[c.req];
     ffss_keys_release(c.k0);
@@ -141,7 +146,10 @@ extern "C" int ffss_server_destroy(ffss_server *sv) {
   for (auto &st : sv->inflight)
     for (auto &c : st.chunks) { ffss_keys_release(c.k0); ffss_keys_release(c.k1); }
   for (auto e : sv->free_events) cudaEventDestroy(e);
-  for (auto &st : sv->inflight) cudaEventDestroy(st.done);
+  for (auto &st : sv->inflight) {
+    cudaEventDestroy(st.done);
+    cudaEventDestroy(st.start);
+  }
   for (int h = 0; h < 2; ++h) {
     if (sv->pool[h]) cudaFree(sv->pool[h]);
     if (sv->half_free[h]) cudaEventDestroy(sv->half_free[h]);
@@ -332,6 +340,8 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
   cudaEvent_t gen_done = srv_event(sv);
   CUDA_TRY(cudaEventRecord(gen_done, sv->s_gen));
   CUDA_TRY(cudaStreamWaitEvent(sv->s_eval, gen_done, 0));
+  st.start = srv_event(sv);
+  CUDA_TRY(cudaEventRecord(st.start, sv->s_eval));
   int rc = ffss_batch_eval(sv->batch, calls.data(), uint32_t(calls.size()), nullptr, sv->s_eval);
   sv->free_events.push_back(gen_done);
   if (rc) return rc;
@@ -378,6 +388,7 @@ extern "C" int ffss_server_summary(ffss_server *sv, ffss_server_stats *out) {
   out->layers = sv->all_layer_ms.size();
   out->first_admit_ms = sv->first_admit;
   out->last_done_ms = sv->last_done;
+  out->eval_ms = sv->eval_ms;
   if (!sv->all_layer_ms.empty()) {
     std::vector<double> v = sv->all_layer_ms;
     std::sort(v.begin(), v.end());

@@ -81,7 +81,7 @@ class RequestStats(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("elements", C.c_uint64), ("steps", C.c_uint64), ("chunks", C.c_uint64), ("layers", C.c_uint64),
                 ("first_admit_ms", C.c_double), ("last_done_ms", C.c_double), ("layer_ms_p50", C.c_double),
-                ("layer_ms_p99", C.c_double), ("layer_ms_max", C.c_double)]
+                ("layer_ms_p99", C.c_double), ("layer_ms_max", C.c_double), ("eval_ms", C.c_double)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
