@@ -49,7 +49,7 @@ def lib():
         L.or_dcf_gen.argtypes = [C.c_int, C.c_uint64, C.c_int, u64p, u8p, u8p, C.c_void_p, C.c_void_p]
         L.or_dcf_eval.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.POINTER(C.c_int), u64p]
         L.or_spec_build.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
-                                    u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p]
+                                    u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32]
         L.or_spec_build.restype = C.c_int
         L.or_spec_shape.argtypes = [C.c_void_p, u32p]
         L.or_spec_query.argtypes = [C.c_void_p, C.c_uint32, u32p, u64p, i32p]
@@ -152,7 +152,7 @@ def dcf_eval(b: int, key: DcfKey, u: int, p: int):
 class Spec:
     """Oracle-side compiled operator specification."""
 
-    def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=()):
+    def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False):
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
         alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64))
         coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.uint64).reshape(-1))
@@ -163,7 +163,7 @@ class Spec:
         pn = np.array([q[3] for q in preds] or [0], np.uint32)
         rc = lib().or_spec_build(self.ptr, k, m, d, r, _p(alpha, u64p), _p(coeff, u64p),
                                  1 if partition_bits else 0, n, _p(pf, u32p), _p(pc, u64p),
-                                 _p(pg, u64p), _p(pn, u32p))
+                                 _p(pg, u64p), _p(pn, u32p), 1 if xhat_basis else 0)
         if rc != 0:
             raise ValueError("oracle rejected the operator specification")
         sh = np.zeros(6, np.uint32)

@@ -424,6 +424,8 @@ typedef struct {
 typedef struct {
     /* descriptor */
     uint32_t k, m, d, r;
+    uint32_t xhat_basis;              /* payload re-expanded around the public x^ */
+    uint32_t n_mults;                 /* Beaver multiplications: d r, or 0 in the x^ basis */
     uint64_t alpha[MAXM + 1];
     uint64_t coeff[MAXM * MAXP];      /* [piece][out][power], low power first */
     uint32_t n_out_bits;              /* number of Boolean outputs */
@@ -454,7 +456,7 @@ static uint64_t pow2(uint32_t f) { return (uint64_t)1 << f; }
 int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
                   const uint64_t *alpha, const uint64_t *coeff, uint32_t partition_bits,
                   uint32_t n_extra, const uint32_t *ef, const uint64_t *ec,
-                  const uint64_t *egamma, const uint32_t *eneg)
+                  const uint64_t *egamma, const uint32_t *eneg, uint32_t xhat_basis)
 {
     memset(sp, 0, sizeof(*sp));
     if (k < 1 || k > MAXK || m < 1 || m > MAXM) return -1;
@@ -466,6 +468,8 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
     memcpy(sp->alpha, alpha, sizeof(uint64_t) * (m + 1));
     memcpy(sp->coeff, coeff, sizeof(uint64_t) * m * r * (d + 1));
     sp->p = r * (d + 1);
+    sp->xhat_basis = xhat_basis ? 1 : 0;
+    sp->n_mults = sp->xhat_basis ? 0 : d * r;
     /* M = min(m+1, 2^k) (App. F); a single-interval spec has an
      * interval-independent payload and omits the lookup call (App. O). */
     if (m == 1) sp->M = 1;
@@ -536,7 +540,7 @@ size_t or_spec_size(void) { return sizeof(or_spec); }
 
 void or_spec_shape(const or_spec *sp, uint32_t *out)
 {
-    out[0] = sp->T; out[1] = sp->M; out[2] = sp->p; out[3] = sp->d * sp->r;
+    out[0] = sp->T; out[1] = sp->M; out[2] = sp->p; out[3] = sp->n_mults;
     out[4] = sp->n_out_bits; out[5] = sp->n_prim;
 }
 
@@ -680,10 +684,34 @@ void or_compile_lookup(const or_spec *sp, uint64_t r_in, uint64_t *B, uint32_t *
     compile_lookup(sp, r_in, B, ord);
 }
 
-/* Payload of piece i: index o*(d+1)+j = coefficient of x^j of output o. */
-static void payload(const or_spec *sp, uint32_t piece, uint64_t *v)
+static uint64_t binom(uint32_t t, uint32_t j)
+{
+    uint64_t v = 1;
+    for (uint32_t i = 1; i <= j; i++) v = v * (t - j + i) / i;
+    return v;
+}
+
+/* Payload of piece i: index o*(d+1)+j = coefficient of x^j of output o.  In
+ * the x^ basis the dealer rewrites P(x) = P(x^ - r) = sum_j c'_j x^^j with
+ * c'_j = sum_{t >= j} c_t binom(t, j) (-r)^(t-j)  (mod 2^64), so the parties
+ * can evaluate on the public x^ without multiplying shares. */
+static void payload(const or_spec *sp, uint32_t piece, uint64_t r_in, uint64_t *v)
 {
     for (uint32_t q = 0; q < sp->p; q++) v[q] = sp->coeff[piece * sp->p + q];
+    if (!sp->xhat_basis) return;
+    uint64_t neg_r = (uint64_t)0 - r_in;
+    for (uint32_t o = 0; o < sp->r; o++) {
+        const uint64_t *c = &sp->coeff[piece * sp->p + o * (sp->d + 1)];
+        for (uint32_t j = 0; j <= sp->d; j++) {
+            uint64_t acc = 0;
+            for (uint32_t t = j; t <= sp->d; t++) {
+                uint64_t pw = 1;
+                for (uint32_t i = 0; i < t - j; i++) pw *= neg_r;
+                acc += c[t] * binom(t, j) * pw;
+            }
+            v[o * (sp->d + 1) + j] = acc;
+        }
+    }
 }
 
 /* Dealer for elements [e0, e0+n): masks, carries, keys, triples, input shares
@@ -751,7 +779,7 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
         if (M == 1) { B[0] = 0; B[1] = pow2(sp->k); ord[0] = 0; }
         else compile_lookup(sp, r_in, B, ord);
         uint64_t v[MAXM + 1][MAXP];
-        for (uint32_t j = 0; j < M; j++) payload(sp, ord[j], v[j]);
+        for (uint32_t j = 0; j < M; j++) payload(sp, ord[j], r_in, v[j]);
         for (uint32_t j = 1; j < M; j++) {
             uint64_t beta[MAXP];
             for (uint32_t q = 0; q < p; q++) beta[q] = v[j - 1][q] - v[j][q];
@@ -768,7 +796,7 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
         }
 
         /* Beaver triples (a, b, c = ab) */
-        for (uint32_t mi = 0; mi < sp->d * sp->r; mi++) {
+        for (uint32_t mi = 0; mi < sp->n_mults; mi++) {
             uint32_t di = base_triples + 5 * mi;
             uint64_t a = prg_u64(&g, di + 0, e);
             uint64_t b = prg_u64(&g, di + 1, e);
@@ -871,9 +899,16 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
             /* Horner starts from the leading coefficient */
             for (uint32_t o = 0; o < r; o++) y[b][o] = pay[b][o * (d + 1) + d];
         }
+        /* x^ basis: Horner on the public x^ with shared coefficients, local */
+        if (sp->xhat_basis) {
+            for (int b = 0; b < 2; b++)
+                for (uint32_t o = 0; o < r; o++)
+                    for (int j = (int)d - 1; j >= 0; j--)
+                        y[b][o] = y[b][o] * xhat + pay[b][o * (d + 1) + (uint32_t)j];
+        }
         /* (5) Horner: y <- y*x + c_j for j = d-1 .. 0; each product is one
          * Beaver multiplication with a fresh triple (open e = y - a, f = x - b). */
-        for (int j = (int)d - 1; j >= 0; j--) {
+        for (int j = (int)d - 1; j >= 0 && !sp->xhat_basis; j--) {
             uint64_t em[2][MAXP], fm[2][MAXP];
             for (int b = 0; b < 2; b++)
                 for (uint32_t o = 0; o < r; o++) {

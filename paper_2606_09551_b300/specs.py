@@ -49,6 +49,9 @@ class OperatorSpec:
     coeff: np.ndarray           # uint64 [m, r, d+1], low power first, Z_{2^64}
     partition_bits: bool = True
     preds: List[PredDesc] = field(default_factory=list)
+    # evaluate on the public x^ with payload coefficients re-expanded by the
+    # dealer (no Beaver multiplications); same function, other protocol variant
+    xhat_basis: bool = False
     real_fn: Callable[[np.ndarray], np.ndarray] | None = None
     domain: Tuple[float, float] | None = None
 
@@ -58,6 +61,12 @@ class OperatorSpec:
 
     def pred_tuples(self):
         return [q.astuple() for q in self.preds]
+
+    def variant(self, xhat_basis: bool) -> "OperatorSpec":
+        """The same specification evaluated in the other protocol variant."""
+        import dataclasses
+        return dataclasses.replace(self, xhat_basis=xhat_basis,
+                                   name=self.name + ("_xhat" if xhat_basis else ""))
 
 
 # --------------------------------------------------------------------------

@@ -14,7 +14,7 @@ M64 = (1 << 64) - 1
 
 def ospec(sp):
     return O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits,
-                  sp.pred_tuples())
+                  sp.pred_tuples(), sp.xhat_basis)
 
 
 def python_plain(sp, xs):
@@ -167,3 +167,38 @@ def test_distinct_calls_draw_distinct_masks():
     ra = [(a0.fields(o, i)["r_share"] + a1.fields(o, i)["r_share"]) & M64 for i in range(64)]
     rb = [(b0.fields(o, i)["r_share"] + b1.fields(o, i)["r_share"]) & M64 for i in range(64)]
     assert len(set(ra) | set(rb)) == 128
+
+
+@pytest.mark.parametrize("k", [2, 4, 5])
+def test_xhat_basis_variant_every_mask_every_input(k):
+    """The x^-basis payload variant: the dealer re-expands each piece as a
+    polynomial in the public x^ (binomial expansion of P(x^ - r) over
+    Z_{2^64}); reconstruction still equals F(x) for all x and r, with no
+    Beaver multiplication and only the 8-byte opening on the wire."""
+    rng = np.random.default_rng(90 + k)
+    N = 2 ** k
+    for trial in range(6):
+        m = int(rng.integers(1, min(N, 16) + 1))
+        d = int(rng.integers(0, 4))
+        r = 1 if d > 1 else int(rng.integers(1, 3))
+        sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 3)))
+        sp = sp.variant(True)
+        hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
+        rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        assert o.n_mults == 0
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all()
+        assert (res["comm"] == xs.size * 8).all()
+
+
+def test_xhat_basis_matches_standard_reconstruction():
+    """Same inputs and masks through both variants: shares differ, the
+    reconstructed outputs agree (the workload specs, full 64-bit masks)."""
+    for sp in (S.gelu8(), S.nexp16()):
+        x = np.random.default_rng(4).integers(0, 2 ** 64, size=200, dtype=np.uint64)
+        _, _, y_std, z_std = run_gate(sp, x, call_id=3)
+        _, _, y_x, z_x = run_gate(sp.variant(True), x, call_id=3)
+        assert np.array_equal(y_std, y_x) and np.array_equal(z_std, z_x)
