@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the streamed large-layer run")
     ap.add_argument("--gpt2-layers", type=int, default=1, help="layers per request in the 32-request batch")
     ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
+    ap.add_argument("--no-xhat", action="store_true", help="skip the x^-basis variant run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
@@ -364,10 +365,53 @@ def run_ours(args, rank, world, local_rank):
                    "form": "one persistent work-queue launch per layer, CUDA graph replay"}
         bt.close()
 
-    served = large = gpt2 = None
-    if not (args.no_served and args.no_large and args.no_gpt2):
-        del sets
+    del sets
+    torch.cuda.empty_cache()
+
+    # x^-basis payload variant: the same layer, local evaluation on the public
+    # x^ (no Beaver rounds, no triples); plain per-operator launches
+    xhat = None
+    if not args.no_xhat:
+        vcss = {c.name: F.CompiledSpec(c.spec.variant(True), ctx) for c in calls}
+        vsets = []
+        for s_ in range(args.steps + 1):
+            ks = {}
+            for c in calls:
+                x0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
+                x1 = torch.empty_like(x0)
+                k0, k1 = F.Keys(vcss[c.name], c.n, 0), F.Keys(vcss[c.name], c.n, 1)
+                F.keygen(ctx, vcss[c.name], I.KEY_SEED, c.call_id + 16 * (400 + s_), c.n, k0, k1, xp[c.name], x0, x1)
+                ks[c.name] = (k0, k1, x0, x1)
+            vsets.append(ks)
+        vcomm = torch.zeros(2, dtype=torch.uint64, device=dev)
+
+        def vstep(ks, cm=None):
+            for c in calls:
+                F.eval_pair(ctx, vcss[c.name], *ks[c.name], *outs[c.name], cm)
+
+        vstep(vsets[-1])                      # warm-up
+        torch.cuda.synchronize()
+        barrier(world)
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for s_ in range(args.steps):
+            vstep(vsets[s_], vcomm)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        vms = max_over_ranks(v0.elapsed_time(v1) / args.steps, world, dev)
+        xhat = {"value": aggregate(total, vms, world), "unit": "elements/s", "ms_per_step": vms,
+                "vs_standard": ms / vms,
+                "comm_bytes_per_party_per_step": int(vcomm.cpu().tolist()[0]) // args.steps,
+                "comm_bytes_per_party_per_step_standard": comm_b[0] // (args.steps + args.warmup),
+                "key_bytes_per_step": sum(2 * vcss[c.name].shape.key_bytes_per_elem * c.n for c in calls),
+                "online_rounds": 1,
+                "form": "dealer re-expands P(x^ - r) in the public x^; lookup returns shares of those "
+                        "coefficients; Horner on x^ is local (no triples, one opening round)"}
+        del vsets
         torch.cuda.empty_cache()
+
+    served = large = gpt2 = None
     if not args.no_served:
         served = run_served(ctx, args, dev)
     if not args.no_large:
@@ -432,6 +476,7 @@ def run_ours(args, rank, world, local_rank):
         "served": served,
         "large_layer": large,
         "gpt2_batch": gpt2,
+        "xhat_variant": xhat,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)

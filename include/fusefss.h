@@ -91,6 +91,12 @@ typedef struct {
     const uint64_t *coeff;
     uint32_t n_pred;
     const ffss_pred_desc *preds;
+    /* 0: the paper's evaluation, Horner on shares of x with d Beaver rounds.
+     * 1: x^-basis variant: the dealer re-expands each piece around the public
+     *    x^ (P(x) = P(x^ - r_in) = sum_j c'_j x^^j over Z_{2^64}) and the lookup
+     *    returns shares of c', so each party evaluates locally; no triples, no
+     *    rounds beyond the opening.  Same outputs F(x). */
+    uint32_t xhat_basis;
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -100,7 +106,7 @@ typedef struct {
     uint32_t T;              /* packed-comparison queries */
     uint32_t M;              /* lookup intervals (1 when m = 1: lookup omitted, App. O) */
     uint32_t p;              /* payload length */
-    uint32_t n_mults;        /* Beaver multiplications per element = degree * n_out */
+    uint32_t n_mults;        /* Beaver multiplications per element: degree * n_out (0 in the x^ basis) */
     uint32_t n_bool;         /* Boolean outputs */
     uint32_t n_views;        /* distinct (f, c) views among the queries */
     uint64_t key_bytes_per_elem;   /* one party, this library's layout */

@@ -358,6 +358,24 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
   }
 }
 
+// Payload word q = o (d + 1) + j of piece `piece`: the coefficient of x^j of
+// output o, or in the x^ basis the coefficient of x^^j of P(x^ - r_in):
+// sum_{t >= j} c_t binom(t, j) (-r_in)^(t-j)  (mod 2^64).
+FFSS_CORE uint64_t payload_word(const DevSpec &S, uint32_t piece, uint32_t q, uint64_t r_in) {
+  if (!S.xhat) return S.coeff[piece * S.p + q];
+  const uint32_t d = S.d, o = q / (d + 1), j = q - o * (d + 1);
+  const uint64_t *c = &S.coeff[piece * S.p + o * (d + 1)];
+  const uint64_t neg_r = 0ull - r_in;
+  uint64_t acc = 0, pw = 1;
+  for (uint32_t t = j; t <= d; ++t) {
+    uint64_t bin = 1;
+    for (uint32_t i = 1; i <= j; ++i) bin = bin * (t - j + i) / i;
+    acc += c[t] * bin * pw;
+    pw *= neg_r;
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------------------
 // Lookup instance of one element (App. F step 1).  The translated starts
 // s_i = (alpha_i + r_k) mod 2^k are a rotation of the sorted alpha: the w

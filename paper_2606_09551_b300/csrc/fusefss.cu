@@ -195,6 +195,9 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   S.k = d->k; S.m = d->m; S.d = d->degree; S.r = d->n_out; S.p = p;
   S.V = (p + 1) / 2;
   S.M = d->m == 1 ? 1 : d->m + 1;
+  if (d->xhat_basis > 1) return fail(FFSS_ERR_INVALID, "xhat_basis must be 0 or 1");
+  S.xhat = d->xhat_basis;
+  S.n_mults = S.xhat ? 0 : d->degree * d->n_out;
   for (uint32_t i = 0; i <= d->m; ++i) S.alpha[i] = d->alpha[i];
   for (uint32_t i = 0; i < d->m * p; ++i) S.coeff[i] = d->coeff[i];
 
@@ -276,10 +279,10 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   }
   ffss_shape &sh = sp->shape;
   sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
-  sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.d * S.r; sh.n_bool = S.n_bool;
+  sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.n_mults; sh.n_bool = S.n_bool;
   sh.n_views = S.n_views;
   sh.key_bytes_per_elem = key_bytes_per_elem(S);
-  sh.comm_bytes_per_elem = 8 + 16ull * S.d * S.r;
+  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults;
   sh.aes_per_elem = aes_per_elem(S);
   *out = sp;
   return FFSS_OK;

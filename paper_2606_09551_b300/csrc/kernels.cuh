@@ -299,9 +299,18 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
 #pragma unroll
     for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
   }
+  // x^-basis variant: the coefficients multiply the public x^, so Horner is
+  // local to each party
+  if (S.xhat && lead) {
+#pragma unroll
+    for (int jj = D - 1; jj >= 0; --jj)
+#pragma unroll
+      for (int o = 0; o < R; ++o) y[o] = y[o] * xhat + pay[o * (D + 1) + jj];
+  }
   // (5) Horner from the leading coefficient, one Beaver product per step
 #pragma unroll
   for (int jj = D - 1; jj >= 0; --jj) {
+    if (S.xhat) break;   // uniform across the CTA: one spec per tile
     uint64_t ta[R], tbv[R], tc[R];
     if (lead) {
 #pragma unroll
@@ -414,7 +423,7 @@ __device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n)
   L.off_r = o; o = align256(o + 8 * n);
   L.off_carry = o; o = align256(o + 4 * n);
   L.off_vlast = o; o = align256(o + 8ull * s.p * n);
-  L.off_trip = o; o = align256(o + 24ull * s.d * s.r * n);
+  L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
     o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
@@ -589,7 +598,7 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       const uint32_t j = item + 1;
       uint64_t beta[P];
 #pragma unroll
-      for (int q = 0; q < P; ++q) beta[q] = S.coeff[ord[j - 1] * P + q] - S.coeff[ord[j] * P + q];
+      for (int q = 0; q < P; ++q) beta[q] = payload_word(S, ord[j - 1], q, r_in) - payload_word(S, ord[j], q, r_in);
       const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
       const uint4 s0 = prg(di), s1 = prg(di + 1);
       char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
@@ -641,12 +650,12 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       for (int q = 0; q < P; ++q) {
         const uint64_t sh = lo64(prg(kDrawVlast + q));
         reinterpret_cast<uint64_t *>(A.k0 + L.off_vlast)[uint64_t(q) * n + e] = sh;
-        reinterpret_cast<uint64_t *>(A.k1 + L.off_vlast)[uint64_t(q) * n + e] = S.coeff[last * P + q] - sh;
+        reinterpret_cast<uint64_t *>(A.k1 + L.off_vlast)[uint64_t(q) * n + e] = payload_word(S, last, q, r_in) - sh;
       }
       // Beaver triples (a, b, c = a b), fresh per multiplication
       uint64_t *tr0 = reinterpret_cast<uint64_t *>(A.k0 + L.off_trip);
       uint64_t *tr1 = reinterpret_cast<uint64_t *>(A.k1 + L.off_trip);
-      for (uint32_t mi = 0; mi < S.d * S.r; ++mi) {
+      for (uint32_t mi = 0; mi < S.n_mults; ++mi) {
         const uint32_t di = S.base_triples + 5 * mi;
         const uint64_t a = lo64(prg(di)), bb = lo64(prg(di + 1));
         const uint64_t a0 = lo64(prg(di + 2)), b0 = lo64(prg(di + 3)), c0 = lo64(prg(di + 4));

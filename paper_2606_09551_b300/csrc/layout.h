@@ -44,6 +44,8 @@ struct DevSpec {
   uint32_t out_neg;            // negations (bit o), applied by party 0 only
   uint32_t base_roots, base_triples;  // dealer draw indices
   uint32_t n_views;
+  uint32_t xhat;               // 1: payload re-expanded around the public x^ (no Beaver rounds)
+  uint32_t n_mults;            // Beaver multiplications per element (d r, or 0 when xhat)
   uint64_t alpha[kMaxM + 1];
   uint64_t coeff[kMaxM * kMaxP];      // [piece][q], q = o*(d+1) + j
 };
@@ -76,7 +78,7 @@ inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_r = o; o = align256(o + 8 * n);
   L.off_carry = o; o = align256(o + 4 * n);
   L.off_vlast = o; o = align256(o + 8ull * s.p * n);
-  L.off_trip = o; o = align256(o + 24ull * s.d * s.r * n);
+  L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
     o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
@@ -91,7 +93,7 @@ inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
-  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.d * s.r;
+  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults;
   for (uint32_t t = 0; t < s.T; ++t) b += 16ull * (s.q_f[t] + 1) + 8;
   if (s.M > 1) b += (s.M - 1) * (16ull * (s.k + 1) + 8ull * (s.k + 1) * s.p);
   return b;

@@ -40,7 +40,7 @@ class SpecDesc(C.Structure):
     _fields_ = [("k", C.c_uint32), ("frac_bits", C.c_uint32), ("m", C.c_uint32), ("degree", C.c_uint32),
                 ("n_out", C.c_uint32), ("partition_bits", C.c_uint32),
                 ("alpha", C.POINTER(C.c_uint64)), ("coeff", C.POINTER(C.c_uint64)),
-                ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc))]
+                ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc)), ("xhat_basis", C.c_uint32)]
 
 
 class Shape(C.Structure):
@@ -190,7 +190,7 @@ class CompiledSpec:
         self._keep = (alpha, coeff, preds)
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
-                     len(spec.preds), preds)
+                     len(spec.preds), preds, 1 if spec.xhat_basis else 0)
         h = vp()
         _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
         self.h = h

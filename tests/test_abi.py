@@ -66,6 +66,9 @@ def test_workload_spec_shapes():
     assert sh.aes_per_elem == 16 * 24 + 16 * (24 * 3 + 2)
     for sp in (S.recip16(), S.rsqrt16(), S.silu16(), S.relu(16), S.relu(4)):
         _shape_vs_oracle(sp)
+    # x^-basis variant: no Beaver multiplications, no triples in the keys, 8 B online
+    sh = _shape_vs_oracle(S.nexp16().variant(True))
+    assert sh.n_mults == 0 and sh.comm_bytes_per_elem == 8
 
 
 def test_random_spec_shapes():
@@ -77,7 +80,7 @@ def test_random_spec_shapes():
         r = 1 if d > 1 else int(rng.integers(1, 3))
         sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(rng.integers(0, 2)),
                            n_extra=int(rng.integers(0, 6)))
-        _shape_vs_oracle(sp)
+        _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)))
 
 
 @pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0"])

@@ -69,6 +69,8 @@ def _specs():
     for k, m, d, r, extra in [(12, 5, 2, 1, 2), (20, 16, 3, 1, 1), (9, 3, 0, 2, 3), (16, 1, 1, 1, 1),
                               (32, 7, 1, 2, 2), (6, 4, 3, 1, 4)]:
         out.append(S.random_spec(rng, k, m, d, r, partition_bits=True, n_extra=extra, name=f"rand_k{k}_m{m}"))
+    # the x^-basis payload variant (no Beaver rounds) on a workload spec and two random ones
+    out += [S.gelu8().variant(True), out[4].variant(True), out[8].variant(True)]
     return out
 
 
@@ -94,7 +96,8 @@ def test_keygen_and_gate_bit_exact(ctx, sp):
         assert np.array_equal(g[key], o[key]), key
     yp, zp = osp.plain_eval(x)
     assert np.array_equal(g["y"], yp) and np.array_equal(g["z"], zp)
-    assert list(g["comm"]) == [n * (8 + 16 * sp.degree * sp.n_out)] * 2
+    mults = 0 if sp.xhat_basis else sp.degree * sp.n_out
+    assert list(g["comm"]) == [n * (8 + 16 * mults)] * 2
 
 
 def test_gpu_eval_of_oracle_keys(ctx):
