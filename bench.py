@@ -515,14 +515,29 @@ def _layer_ops(css, dev, gen, L, heads, mlp, hidden, f, act="gelu", n_ln=1):
     return ops
 
 
-def _server_result(sv, nreq, clk, wall):
+def _stream_aes(pending_ops, nlay):
+    """Algorithmic AES blocks of a streamed run: dealer + both parties online."""
+    tot = 0
+    for ops in pending_ops:
+        for cs, x, *_ in ops:
+            tot += x.numel() * nlay * (cs.shape.keygen_aes_per_elem + 2 * cs.shape.aes_per_elem)
+    return tot
+
+
+def _aes_roofline():
+    return SMS * SM_MAX_MHZ * 1e6 / max(ALU_OPS_PER_AES / 64.0, LDS_PER_AES / 32.0)
+
+
+def _server_result(sv, nreq, clk, wall, aes_blocks):
     st = sv.summary()
     infos = [sv.request_info(i) for i in range(nreq)]
     queue = sorted(max(0.0, r["admitted_ms"] - r["arrival_ms"]) for r in infos)
     span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
     return st, {"value": st["elements"] / span_s, "unit": "elements/s",
-                "eval_only_elements_per_s": st["elements"] / (st["eval_ms"] * 1e-3),
-                "note": "includes the on-device dealer: keys are streamed through the key pool, not preloaded",
+                "aes_blocks": aes_blocks,
+                "aes_roofline_frac": aes_blocks / span_s / _aes_roofline(),
+                "note": "includes the on-device dealer: keys are streamed through the key pool, not preloaded; "
+                        "aes_roofline_frac counts dealer + online AES blocks against the AES roofline",
                 "requests": nreq, "elements": int(st["elements"]), "steps": int(st["steps"]),
                 "chunks": int(st["chunks"]), "batched_launches": int(st["steps"]),
                 "layer_ms_p50": st["layer_ms_p50"], "layer_ms_p99": st["layer_ms_p99"],
@@ -568,7 +583,7 @@ def run_served(ctx, args, dev):
     with ClockSampler(int(dev.split(":")[1])) as clk:
         sv.run()
     wall = time.perf_counter() - t0
-    st, res = _server_result(sv, nreq, clk, wall)
+    st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "offered_requests_per_s": 20.0,
@@ -612,7 +627,7 @@ def run_gpt2_batch(ctx, args, dev):
     with ClockSampler(int(dev.split(":")[1])) as clk:
         sv.run()
     wall = time.perf_counter() - t0
-    st, res = _server_result(sv, nreq, clk, wall)
+    st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "config": "32 GPT-2-small requests (hidden 768, 12 heads, MLP 3072, 2 LayerNorms), "
@@ -672,8 +687,9 @@ def run_large_layer(ctx, dev):
     span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
     key_tb = sum(2 * css[n].shape.key_bytes_per_elem * xs[n].numel() for n in xs) / 1e12
     sv.close()
+    aes_blocks = _stream_aes([ops], 1)
     return {"value": total / span_s, "unit": "elements/s", "elements": int(total), "layer_ms": st["layer_ms_max"],
-            "eval_only_elements_per_s": total / (st["eval_ms"] * 1e-3),
+            "aes_blocks": aes_blocks, "aes_roofline_frac": aes_blocks / span_s / _aes_roofline(),
             "steps": int(st["steps"]), "chunks": int(st["chunks"]), "keys_tb_streamed": key_tb,
             "wall_s": wall, "clocks": clk.summary(),
             "note": "includes the on-device dealer: keys are streamed through a 64 GB pool, not preloaded",

@@ -112,6 +112,9 @@ typedef struct {
     uint64_t key_bytes_per_elem;   /* one party, this library's layout */
     uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults */
     uint64_t aes_per_elem;         /* one party, online AES-128 blocks */
+    uint64_t keygen_aes_per_elem;  /* dealer AES-128 blocks per element (both parties' keys,
+                                      PRG draws included): 4 k_t per comparison key,
+                                      k (4 + 4V) + 2V per lookup key */
 } ffss_shape;
 
 /* ---- context ------------------------------------------------------------ */

@@ -284,6 +284,7 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   sh.key_bytes_per_elem = key_bytes_per_elem(S);
   sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults;
   sh.aes_per_elem = aes_per_elem(S);
+  sh.keygen_aes_per_elem = keygen_aes_per_elem(S);
   *out = sp;
   return FFSS_OK;
 }

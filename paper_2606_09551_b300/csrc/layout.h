@@ -107,4 +107,15 @@ inline uint64_t aes_per_elem(const DevSpec &s) {
   return a;
 }
 
+// Dealer AES-128 blocks per element: the CTR draws, then per DCF level both
+// children of both parties' seeds (4 blocks) and, for a lookup key, both
+// children's payload blocks of both parties (4V); the final lookup
+// correction needs both parties' leaf payloads (2V).
+inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
+  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults;
+  for (uint32_t t = 0; t < s.T; ++t) a += 4ull * s.q_f[t];
+  if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (4 + 4 * s.V) + 2 * s.V);
+  return a;
+}
+
 }  // namespace ffss

@@ -48,7 +48,7 @@ class Shape(C.Structure):
                 ("T", C.c_uint32), ("M", C.c_uint32), ("p", C.c_uint32), ("n_mults", C.c_uint32),
                 ("n_bool", C.c_uint32), ("n_views", C.c_uint32),
                 ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
-                ("aes_per_elem", C.c_uint64)]
+                ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
