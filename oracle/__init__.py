@@ -49,7 +49,8 @@ def lib():
         L.or_dcf_gen.argtypes = [C.c_int, C.c_uint64, C.c_int, u64p, u8p, u8p, C.c_void_p, C.c_void_p]
         L.or_dcf_eval.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.POINTER(C.c_int), u64p]
         L.or_spec_build.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
-                                    u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32]
+                                    u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32,
+                                    C.c_uint32, u32p, u64p, u64p, u32p]
         L.or_spec_build.restype = C.c_int
         L.or_spec_shape.argtypes = [C.c_void_p, u32p]
         L.or_spec_query.argtypes = [C.c_void_p, C.c_uint32, u32p, u64p, i32p]
@@ -64,6 +65,7 @@ def lib():
         L.or_elem_lkey.argtypes = [C.c_void_p, C.c_uint32]
         L.or_elem_lkey.restype = C.c_void_p
         L.or_dcf_key_fields.argtypes = [C.c_void_p, u8p, u8p, u8p, u8p, u8p, u64p]
+        L.or_elem_btriples.argtypes = [C.c_void_p, C.c_uint32, u32p, u32p, u32p]
         L.or_elem_fields.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, u64p, u32p, u64p, u64p, u64p, u64p]
         _lib = L
     return _lib
@@ -152,7 +154,9 @@ def dcf_eval(b: int, key: DcfKey, u: int, p: int):
 class Spec:
     """Oracle-side compiled operator specification."""
 
-    def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False):
+    def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False,
+                 piecewise=()):
+        """piecewise: per output j, m tuples (f, c, gamma, negate), one per interval."""
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
         alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64))
         coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.uint64).reshape(-1))
@@ -161,9 +165,17 @@ class Spec:
         pc = np.array([q[1] for q in preds] or [0], np.uint64)
         pg = np.array([q[2] for q in preds] or [0], np.uint64)
         pn = np.array([q[3] for q in preds] or [0], np.uint32)
+        npw = len(piecewise)
+        flat = [piecewise[j][i] for i in range(m) for j in range(npw)] or [(1, 0, 0, 0)]
+        wf = np.array([q[0] for q in flat], np.uint32)
+        wc = np.array([q[1] for q in flat], np.uint64)
+        wg = np.array([q[2] for q in flat], np.uint64)
+        wn = np.array([q[3] for q in flat], np.uint32)
         rc = lib().or_spec_build(self.ptr, k, m, d, r, _p(alpha, u64p), _p(coeff, u64p),
                                  1 if partition_bits else 0, n, _p(pf, u32p), _p(pc, u64p),
-                                 _p(pg, u64p), _p(pn, u32p), 1 if xhat_basis else 0)
+                                 _p(pg, u64p), _p(pn, u32p), 1 if xhat_basis else 0,
+                                 npw, _p(wf, u32p), _p(wc, u64p), _p(wg, u64p), _p(wn, u32p))
+        self.n_pw = npw
         if rc != 0:
             raise ValueError("oracle rejected the operator specification")
         sh = np.zeros(6, np.uint32)
@@ -219,8 +231,12 @@ class ElemKeys:
         ta, tb, tc = (np.zeros(nm, np.uint64) for _ in range(3))
         lib().or_elem_fields(self.elem_ptr(i), spec.p, spec.n_mults, _p(r_share, u64p),
                              _p(carry, u32p), _p(vlast, u64p), _p(ta, u64p), _p(tb, u64p), _p(tc, u64p))
+        npw = getattr(spec, "n_pw", 0)
+        ba, bb, bc = (np.zeros(max(npw, 1), np.uint32) for _ in range(3))
+        lib().or_elem_btriples(self.elem_ptr(i), npw, _p(ba, u32p), _p(bb, u32p), _p(bc, u32p))
         return dict(r_share=int(r_share[0]), carry=int(carry[0]), vlast=vlast[:spec.p],
-                    ta=ta[:spec.n_mults], tb=tb[:spec.n_mults], tc=tc[:spec.n_mults])
+                    ta=ta[:spec.n_mults], tb=tb[:spec.n_mults], tc=tc[:spec.n_mults],
+                    ba=ba[:npw], bb=bb[:npw], bc=bc[:npw])
 
     def qkey(self, i: int, t: int) -> DcfKey:
         key = DcfKey()

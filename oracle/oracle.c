@@ -413,6 +413,7 @@ size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
 #define MAXM 16     /* intervals m <= 16, so at most 16 lookup keys */
 #define MAXPRED 32  /* Boolean outputs */
 #define MAXQ 32     /* packed-comparison queries (one uint32 of atoms) */
+#define MAXPW 4     /* piecewise Boolean outputs */
 
 typedef struct {
     uint32_t f;        /* view width */
@@ -443,7 +444,27 @@ typedef struct {
     int32_t q_prim[MAXQ];             /* per query: prim index, or -1 for the 1[view < r_f] atom */
     int32_t prim_qtheta[MAXPRED];     /* per prim: its theta query */
     int32_t prim_qr[MAXPRED];         /* per prim: the r-atom query of its view */
+    /* piecewise Boolean outputs (Def. "operator specification" item 3 and
+     * Lemma "boolean normalization"): output j is B_i^(j)(x) on interval i */
+    uint32_t n_pw;
+    or_pred pw_pred[MAXM][MAXPW];     /* B_i^(j), negate used */
+    int32_t pw_prim[MAXM][MAXPW];     /* its prim, or -1 for a sentinel constant */
+    uint32_t pw_const[MAXM][MAXPW];   /* the constant when pw_prim < 0 */
+    int32_t part_prim[MAXM + 1];      /* prim of C_{alpha_i}, i = 1..m-1 (when n_pw > 0) */
 } or_spec;
+
+/* index of primitive predicate (f, c, gamma) in sp->prim, adding it if new;
+ * -1 for the sentinels gamma = 0 and gamma = 2^f */
+static int add_prim(or_spec *sp, uint32_t f, uint64_t c, uint64_t gamma)
+{
+    if (gamma == 0 || gamma == ((uint64_t)1 << f)) return -1;
+    for (uint32_t j = 0; j < sp->n_prim; j++)
+        if (sp->prim[j].f == f && sp->prim[j].c == c && sp->prim[j].gamma == gamma) return (int)j;
+    if (sp->n_prim >= MAXPRED) return -2;
+    sp->prim[sp->n_prim].f = f; sp->prim[sp->n_prim].c = c;
+    sp->prim[sp->n_prim].gamma = gamma; sp->prim[sp->n_prim].negate = 0;
+    return (int)sp->n_prim++;
+}
 
 static uint64_t pow2(uint32_t f) { return (uint64_t)1 << f; }
 
@@ -456,7 +477,9 @@ static uint64_t pow2(uint32_t f) { return (uint64_t)1 << f; }
 int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
                   const uint64_t *alpha, const uint64_t *coeff, uint32_t partition_bits,
                   uint32_t n_extra, const uint32_t *ef, const uint64_t *ec,
-                  const uint64_t *egamma, const uint32_t *eneg, uint32_t xhat_basis)
+                  const uint64_t *egamma, const uint32_t *eneg, uint32_t xhat_basis,
+                  uint32_t n_pw, const uint32_t *pwf, const uint64_t *pwc, const uint64_t *pwg,
+                  const uint32_t *pwn)
 {
     memset(sp, 0, sizeof(*sp));
     if (k < 1 || k > MAXK || m < 1 || m > MAXM) return -1;
@@ -510,6 +533,30 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
         sp->out_prim[o] = found;
     }
 
+    /* piecewise outputs: the partition predicates (for the interval
+     * indicators J_i) join the primitive predicates, then each output's
+     * per-interval predicates, output by output, interval by interval */
+    if (n_pw > MAXPW || nb + n_pw > MAXPRED) return -1;
+    sp->n_pw = n_pw;
+    if (n_pw > 0) {
+        for (uint32_t i = 1; i < m; i++) {
+            sp->part_prim[i] = add_prim(sp, k, 0, alpha[i]);
+            if (sp->part_prim[i] < -1) return -1;
+        }
+        for (uint32_t j = 0; j < n_pw; j++)
+            for (uint32_t i = 0; i < m; i++) {
+                uint32_t idx = i * n_pw + j;
+                if (pwf[idx] < 1 || pwf[idx] > k) return -1;
+                if (pwc[idx] >= pow2(pwf[idx]) || pwg[idx] > pow2(pwf[idx])) return -1;
+                or_pred *q = &sp->pw_pred[i][j];
+                q->f = pwf[idx]; q->c = pwc[idx]; q->gamma = pwg[idx]; q->negate = pwn[idx] & 1;
+                int pr = add_prim(sp, q->f, q->c, q->gamma);
+                if (pr < -1) return -1;
+                sp->pw_prim[i][j] = pr;
+                sp->pw_const[i][j] = q->gamma == 0 ? 0 : 1;
+            }
+    }
+
     /* views in order of first appearance */
     uint32_t nviews = 0, vf[MAXPRED];
     uint64_t vc[MAXPRED];
@@ -541,7 +588,7 @@ size_t or_spec_size(void) { return sizeof(or_spec); }
 void or_spec_shape(const or_spec *sp, uint32_t *out)
 {
     out[0] = sp->T; out[1] = sp->M; out[2] = sp->p; out[3] = sp->n_mults;
-    out[4] = sp->n_out_bits; out[5] = sp->n_prim;
+    out[4] = sp->n_out_bits + sp->n_pw; out[5] = sp->n_prim;
 }
 
 void or_spec_query(const or_spec *sp, uint32_t t, uint32_t *f, uint64_t *c, int32_t *prim)
@@ -580,6 +627,11 @@ void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y
             const or_pred *op = &sp->out_pred[o];
             uint32_t v = view(x[e], op->f, op->c) < op->gamma ? 1u : 0u;
             bits |= (v ^ op->negate) << o;
+        }
+        for (uint32_t j = 0; j < sp->n_pw; j++) {
+            const or_pred *op = &sp->pw_pred[piece][j];
+            uint32_t v = view(x[e], op->f, op->c) < op->gamma ? 1u : 0u;
+            bits |= (v ^ op->negate) << (sp->n_out_bits + j);
         }
         z[e] = bits;
     }
@@ -632,6 +684,7 @@ typedef struct {
     or_bit_key qkey[MAXQ];            /* packed-comparison keys, query order */
     or_dcf_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
     uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
+    uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
 } or_elem_keys;
 
 size_t or_elem_keys_size(void) { return sizeof(or_elem_keys); }
@@ -807,6 +860,21 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             K0->tb[mi] = b0; K1->tb[mi] = b - b0;
             K0->tc[mi] = c0; K1->tc[mi] = a * b - c0;
         }
+
+        /* Boolean AND triples for the piecewise outputs: m packed bits each,
+         * draws (a, b, a_0, b_0, c_0) after the ring triples */
+        uint32_t mbits = sp->m >= 32 ? 0xFFFFFFFFu : ((1u << sp->m) - 1);
+        for (uint32_t j = 0; j < sp->n_pw; j++) {
+            uint32_t di = base_triples + 5 * sp->n_mults + 5 * j;
+            uint32_t a = (uint32_t)prg_u64(&g, di + 0, e) & mbits;
+            uint32_t b = (uint32_t)prg_u64(&g, di + 1, e) & mbits;
+            uint32_t a0 = (uint32_t)prg_u64(&g, di + 2, e) & mbits;
+            uint32_t b0 = (uint32_t)prg_u64(&g, di + 3, e) & mbits;
+            uint32_t c0 = (uint32_t)prg_u64(&g, di + 4, e) & mbits;
+            K0->ba[j] = a0; K1->ba[j] = a ^ a0;
+            K0->bb[j] = b0; K1->bb[j] = b ^ b0;
+            K0->bc[j] = c0; K1->bc[j] = (a & b) ^ c0;
+        }
     }
 }
 
@@ -831,6 +899,43 @@ static uint32_t party_pred_atoms(int b, const or_spec *sp, const or_elem_keys *K
 }
 
 /* Local rewrite: share of C(x) = atom_theta ^ atom_r ^ w, then NOT by party 0. */
+/* Party b's XOR share of C(x) for primitive predicate j (no negation). */
+static uint32_t prim_share(const or_spec *sp, const or_elem_keys *K, uint32_t atoms, int j)
+{
+    return ((atoms >> sp->prim_qtheta[j]) & 1) ^ ((atoms >> sp->prim_qr[j]) & 1) ^ ((K->carry_share >> j) & 1);
+}
+
+/* Shares of the interval indicators J_i = C_{alpha_{i+1}} ^ C_{alpha_i}
+ * (Lemma "interval indicator as XOR"; C_{alpha_0} = 0 and C_{alpha_m} = 1,
+ * the constant held by party 0) and of B_i^(j), as m-bit words (bit i). */
+static void party_pw_words(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms, uint32_t *Jw,
+                           uint32_t *Bw)
+{
+    uint32_t C[MAXM + 1];
+    C[0] = 0;
+    C[sp->m] = b == 0 ? 1u : 0u;
+    for (uint32_t i = 1; i < sp->m; i++) C[i] = prim_share(sp, K, atoms, sp->part_prim[i]);
+    *Jw = 0;
+    for (uint32_t i = 0; i < sp->m; i++) *Jw |= (C[i + 1] ^ C[i]) << i;
+    for (uint32_t j = 0; j < sp->n_pw; j++) {
+        Bw[j] = 0;
+        for (uint32_t i = 0; i < sp->m; i++) {
+            uint32_t bit;
+            if (sp->pw_prim[i][j] < 0) bit = b == 0 ? sp->pw_const[i][j] : 0;
+            else bit = prim_share(sp, K, atoms, sp->pw_prim[i][j]);
+            if (b == 0) bit ^= sp->pw_pred[i][j].negate;
+            Bw[j] |= bit << i;
+        }
+    }
+}
+
+static uint32_t parity32(uint32_t v)
+{
+    uint32_t p = 0;
+    while (v) { p ^= v & 1; v >>= 1; }
+    return p;
+}
+
 static uint32_t party_out_bits(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms)
 {
     uint32_t z = 0;
@@ -884,9 +989,11 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
         if (xhat_out) xhat_out[e] = xhat;
 
         uint64_t pay[2][MAXP], xb[2], y[2][MAXP];
+        uint32_t atoms_b[2];
         for (int b = 0; b < 2; b++) {
             /* (2) packed comparison and local rewrite */
             uint32_t atoms = party_pred_atoms(b, sp, KK[b], xhat);
+            atoms_b[b] = atoms;
             zs[b][e] = party_out_bits(b, sp, KK[b], atoms);
             if (b == 0 && atoms0) atoms0[e] = atoms;
             if (b == 1 && atoms1) atoms1[e] = atoms;
@@ -898,6 +1005,28 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
             xb[b] = b == 0 ? xhat - KK[0]->r_share : (uint64_t)0 - KK[1]->r_share;
             /* Horner starts from the leading coefficient */
             for (uint32_t o = 0; o < r; o++) y[b][o] = pay[b][o * (d + 1) + d];
+        }
+        /* piecewise Boolean outputs (Lemma "boolean normalization"):
+         * z_j = XOR_i (J_i AND B_i^(j)); the m ANDs of an output use one
+         * packed Boolean triple: open e = J ^ a, f = B ^ b (4 + 4 bytes),
+         * then share = [b=0] e&f ^ e&b_b ^ f&a_b ^ c_b, and z_j = its parity */
+        if (sp->n_pw > 0) {
+            uint32_t Jw[2], Bw[2][MAXPW], ew[2][MAXPW], fw[2][MAXPW];
+            for (int b = 0; b < 2; b++) {
+                party_pw_words(b, sp, KK[b], b == 0 ? atoms_b[0] : atoms_b[1], &Jw[b], Bw[b]);
+                for (uint32_t j = 0; j < sp->n_pw; j++) {
+                    ew[b][j] = Jw[b] ^ KK[b]->ba[j];
+                    fw[b][j] = Bw[b][j] ^ KK[b]->bb[j];
+                    sent[b] += 8;
+                }
+            }
+            for (int b = 0; b < 2; b++)
+                for (uint32_t j = 0; j < sp->n_pw; j++) {
+                    uint32_t E = ew[0][j] ^ ew[1][j], F = fw[0][j] ^ fw[1][j];
+                    uint32_t w = (E & KK[b]->bb[j]) ^ (F & KK[b]->ba[j]) ^ KK[b]->bc[j];
+                    if (b == 0) w ^= E & F;
+                    zs[b][e] |= parity32(w) << (sp->n_out_bits + j);
+                }
         }
         /* x^ basis: Horner on the public x^ with shared coefficients, local */
         if (sp->xhat_basis) {
@@ -961,6 +1090,11 @@ void or_dcf_key_fields(const or_dcf_key *key, uint8_t *root, uint8_t *scw, uint8
         vcw_bit[i] = key->vcw_bit[i];
         for (int q = 0; q < p; q++) vcw[i * (p > 0 ? p : 1) + q] = key->vcw[i][q];
     }
+}
+
+void or_elem_btriples(const or_elem_keys *K, uint32_t npw, uint32_t *ba, uint32_t *bb, uint32_t *bc)
+{
+    for (uint32_t j = 0; j < npw; j++) { ba[j] = K->ba[j]; bb[j] = K->bb[j]; bc[j] = K->bc[j]; }
 }
 
 void or_elem_fields(const or_elem_keys *K, uint32_t p, uint32_t nm, uint64_t *r_share,

@@ -52,6 +52,10 @@ class OperatorSpec:
     # evaluate on the public x^ with payload coefficients re-expanded by the
     # dealer (no Beaver multiplications); same function, other protocol variant
     xhat_basis: bool = False
+    # piecewise Boolean outputs: piecewise[j][i] is output j's predicate on
+    # interval i (sentinel gamma 0 / 2^f for constants); they follow the
+    # partition bits and the preds in z
+    piecewise: List[List[PredDesc]] = field(default_factory=list)
     real_fn: Callable[[np.ndarray], np.ndarray] | None = None
     domain: Tuple[float, float] | None = None
 
@@ -61,6 +65,9 @@ class OperatorSpec:
 
     def pred_tuples(self):
         return [q.astuple() for q in self.preds]
+
+    def piecewise_tuples(self):
+        return [[q.astuple() for q in out] for out in self.piecewise]
 
     def variant(self, xhat_basis: bool) -> "OperatorSpec":
         """The same specification evaluated in the other protocol variant."""
@@ -296,6 +303,33 @@ def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,
         preds.append(PredDesc(f, c, g, int(rng.integers(0, 2))))
     return OperatorSpec(name=name, k=k, frac_bits=0, out_frac_bits=0, m=m, degree=d, n_out=r,
                         alpha=alpha, coeff=coeff, partition_bits=partition_bits, preds=preds)
+
+
+def random_piecewise(rng: np.random.Generator, spec: OperatorSpec, n_pw: int) -> OperatorSpec:
+    """Add n_pw random piecewise Boolean outputs to a spec (for tests): per
+    interval a random primitive predicate or a constant."""
+    import dataclasses
+    outs = []
+    for _ in range(n_pw):
+        # a small pool of predicates per output keeps the distinct primitive
+        # predicates (one query and one carry bit each) within 32
+        pool = []
+        for _p in range(2):
+            f = int(rng.integers(1, spec.k + 1))
+            pool.append((f, int(rng.integers(0, 1 << f)), int(rng.integers(0, (1 << f) + 1))))
+        col = []
+        for i in range(spec.m):
+            kind = int(rng.integers(0, 4))
+            neg = int(rng.integers(0, 2))
+            if kind == 0:
+                col.append(PredDesc(1, 0, 2 * int(rng.integers(0, 2)), neg))       # constant
+            elif kind == 1:
+                col.append(PredDesc(spec.k, 0, 1 << (spec.k - 1), 1))             # MSB(x)
+            else:
+                f, c, g = pool[kind - 2]
+                col.append(PredDesc(f, c, g, neg))
+        outs.append(col)
+    return dataclasses.replace(spec, piecewise=outs, name=spec.name + "_pw%d" % n_pw)
 
 
 def approx_error(spec: OperatorSpec, x_fixed: np.ndarray, y_fixed: np.ndarray) -> dict:

@@ -41,7 +41,7 @@ def test_context_without_gpu_fails_cleanly(libpath):
 
 def _shape_vs_oracle(sp):
     cs = F.CompiledSpec(sp)           # host-only compile
-    o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis)
+    o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
     sh = cs.shape
     assert (sh.T, sh.M, sh.p, sh.n_mults, sh.n_bool) == (o.T, o.M, o.p, o.n_mults, o.n_bool)
     assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults

@@ -14,7 +14,7 @@ M64 = (1 << 64) - 1
 
 def ospec(sp):
     return O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits,
-                  sp.pred_tuples(), sp.xhat_basis)
+                  sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
 
 
 def python_plain(sp, xs):
@@ -39,6 +39,10 @@ def python_plain(sp, xs):
         for t, (f, c, g, neg) in enumerate(bits):
             v = (((x % (1 << f)) + c) % (1 << f)) < g
             z |= (int(v) ^ neg) << t
+        for j, out in enumerate(sp.piecewise):          # the active interval's predicate
+            q = out[i]
+            v = (((x % (1 << q.f)) + q.c) % (1 << q.f)) < q.gamma
+            z |= (int(v) ^ q.negate) << (len(bits) + j)
         zs.append(z)
     return np.array(ys, dtype=np.uint64), np.array(zs, dtype=np.uint32)
 
@@ -202,3 +206,42 @@ def test_xhat_basis_matches_standard_reconstruction():
         _, _, y_std, z_std = run_gate(sp, x, call_id=3)
         _, _, y_x, z_x = run_gate(sp.variant(True), x, call_id=3)
         assert np.array_equal(y_std, y_x) and np.array_equal(z_std, z_x)
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_piecewise_boolean_outputs_every_mask_every_input(k):
+    """Lemma "boolean normalization": piecewise Boolean outputs
+    z_j = XOR_i (J_i AND B_i^(j)) with XOR-shared interval indicators and one
+    packed Boolean AND triple per output reconstruct B_{i*}^(j)(x) for all
+    x and r; each output adds 8 bytes per party (one opening of e and f)."""
+    rng = np.random.default_rng(120 + k)
+    N = 2 ** k
+    for trial in range(6):
+        m = int(rng.integers(1, min(N, 16) + 1))
+        d = int(rng.integers(0, 3))
+        sp = S.random_spec(rng, k, m, d, 1, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 3)))
+        sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
+        if trial % 3 == 2:
+            sp = sp.variant(True)
+        hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
+        rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all(), (trial, sp.name)
+        mults = 0 if sp.xhat_basis else d
+        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * len(sp.piecewise))).all()
+
+
+def test_piecewise_relu_sign_select():
+    """A concrete piecewise output: on the non-negative half return
+    1[x mod 2^4 < 8] (a low-bit predicate), on the negative half the constant 1."""
+    k = 8
+    sp = S.relu(k)
+    sp.piecewise = [[S.PredDesc(4, 0, 8, 0), S.PredDesc(k, 0, 1 << k, 0)]]
+    xs = np.arange(-(2 ** (k - 1)), 2 ** (k - 1), dtype=np.int64)
+    o, res, y, z = run_gate(sp, xs.view(np.uint64))
+    want = np.where(xs >= 0, ((xs % 16) < 8).astype(np.uint32), 1)
+    assert np.array_equal((z >> 1) & 1, want)
+    assert np.array_equal(z & 1, (xs < 0).astype(np.uint32))
