@@ -87,15 +87,55 @@ def workload(name):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """Samples the SM clock and the clock-event reasons of one GPU every
+    10 ms while the timed region runs (NVML reads only; nothing is set).
+    Falls back to `nvidia-smi -lms 200` when NVML cannot be loaded."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.thread = None
+        self.rows = []
+        self.nvml_error = None
+
+    def _nvml_handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        try:
+            pr = torch.cuda.get_device_properties(self.gpu)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+
+    def _loop(self, nv, h, first):
+        bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
+                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self.stop.is_set():
+            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+            rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+            self.rows.append((float(sm), float(mx), [n for n, b in zip(self.NAMES, bits) if rs & b]))
+            first.set()
+            self.stop.wait(0.010)
 
     def __enter__(self):
+        import threading
+        try:
+            nv, h = self._nvml_handle()
+            self.stop, first = threading.Event(), threading.Event()
+            self.thread = threading.Thread(target=self._loop, args=(nv, h, first), daemon=True)
+            self.thread.start()
+            first.wait(2.0)
+            return self
+        except Exception as ex:
+            self.nvml_error = "%s: %s" % (type(ex).__name__, ex)
+            self.thread = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -105,32 +145,34 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(2.0)
+            return
+        out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                out, _ = self.proc.communicate(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
-
-    def summary(self):
-        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+                out, _ = self.proc.communicate()
+        for r in csv.reader(io.StringIO(out or "")):
+            if len(r) < 9:
+                continue
             try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
+                self.rows.append((float(r[1]), float(r[2]),
+                                  [n for n, v in zip(self.NAMES, r[5:9]) if v.strip().lower() == "active"]))
             except ValueError:
                 continue
-            for name, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(name)
-        if not sm:
+
+    def summary(self):
+        if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = sorted({n for _, _, rs in self.rows for n in rs})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": self.rows[-1][1],
+                "reasons": reasons, "samples": len(self.rows),
+                "source": "nvml 10 ms" if self.thread is not None else "nvidia-smi 200 ms (nvml: %s)" % self.nvml_error}
 
 
 # ---------------------------------------------------------------------------

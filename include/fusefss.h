@@ -54,6 +54,7 @@ extern "C" {
 #define FFSS_MAX_M 16        /* intervals m */
 #define FFSS_MAX_P 4         /* payload length p = n_out * (degree + 1) */
 #define FFSS_MAX_BOOL 32     /* Boolean outputs, one uint32 per element */
+#define FFSS_MAX_PW 4        /* piecewise Boolean outputs */
 #define FFSS_MAX_T 32        /* packed-comparison queries, one uint32 of atoms */
 
 typedef struct ffss_ctx ffss_ctx;     /* per-device state (tables, autotune cache) */
@@ -97,6 +98,17 @@ typedef struct {
      *    returns shares of c', so each party evaluates locally; no triples, no
      *    rounds beyond the opening.  Same outputs F(x). */
     uint32_t xhat_basis;
+    /* Piecewise Boolean outputs (Sec. 4.1 item 3, Lemma "boolean
+     * normalization"): output j (0 <= j < n_piecewise <= FFSS_MAX_PW) is
+     * B_i^(j)(x) on interval i, B_i^(j) = piecewise[i * n_piecewise + j]
+     * (m * n_piecewise entries, each a predicate like preds[]).  The bits
+     * follow the other Boolean outputs in the output word (bit
+     * n_bool - n_piecewise + j, n_bool from the shape) and take one extra exchange of 8 bytes per
+     * output per party (one packed Boolean AND triple).  Computed by the
+     * fused two-party calls only (ffss_eval_pair, the batch, the server);
+     * ffss_eval_pred returns the other outputs. */
+    uint32_t n_piecewise;
+    const ffss_pred_desc *piecewise;
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -107,14 +119,15 @@ typedef struct {
     uint32_t M;              /* lookup intervals (1 when m = 1: lookup omitted, App. O) */
     uint32_t p;              /* payload length */
     uint32_t n_mults;        /* Beaver multiplications per element: degree * n_out (0 in the x^ basis) */
-    uint32_t n_bool;         /* Boolean outputs */
+    uint32_t n_bool;         /* Boolean outputs, piecewise ones included (bits of the output word) */
     uint32_t n_views;        /* distinct (f, c) views among the queries */
     uint64_t key_bytes_per_elem;   /* one party, this library's layout */
-    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults */
+    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults + 8 * n_piecewise */
     uint64_t aes_per_elem;         /* one party, online AES-128 blocks */
     uint64_t keygen_aes_per_elem;  /* dealer AES-128 blocks per element (both parties' keys,
                                       PRG draws included): 4 k_t per comparison key,
                                       k (4 + 4V) + 2V per lookup key */
+    uint32_t n_piecewise;          /* piecewise Boolean outputs (the last n_piecewise of n_bool) */
 } ffss_shape;
 
 /* ---- context ------------------------------------------------------------ */

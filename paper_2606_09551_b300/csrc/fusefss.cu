@@ -236,6 +236,44 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
     }
     S.out_prim[o] = found;
   }
+  // piecewise outputs: the partition predicates C_{alpha_i} (for the interval
+  // indicators) join the distinct predicates, then each output's
+  // per-interval predicates, output by output, interval by interval
+  auto add_prim = [&](uint32_t f, uint64_t c, uint64_t g) -> int {
+    if (g == 0 || g == (uint64_t(1) << f)) return -1;
+    for (uint32_t j = 0; j < S.n_prim; ++j)
+      if (S.prim_f[j] == f && S.prim_c[j] == c && S.prim_gamma[j] == g) return int(j);
+    if (S.n_prim >= uint32_t(kMaxBool)) return -2;
+    S.prim_f[S.n_prim] = f;
+    S.prim_c[S.n_prim] = c;
+    S.prim_gamma[S.n_prim] = g;
+    return int(S.n_prim++);
+  };
+  if (d->n_piecewise > FFSS_MAX_PW)
+    return fail(FFSS_ERR_UNSUPPORTED, "%u piecewise outputs > %d", d->n_piecewise, FFSS_MAX_PW);
+  if (S.n_bool + d->n_piecewise > FFSS_MAX_BOOL)
+    return fail(FFSS_ERR_UNSUPPORTED, "%u Boolean outputs > %d", S.n_bool + d->n_piecewise, FFSS_MAX_BOOL);
+  S.n_pw = d->n_piecewise;
+  if (S.n_pw > 0) {
+    if (!d->piecewise) return fail(FFSS_ERR_INVALID, "piecewise predicates NULL");
+    for (uint32_t i = 1; i < d->m; ++i) {
+      S.part_prim[i] = add_prim(d->k, 0, d->alpha[i]);
+      if (S.part_prim[i] < -1) return fail(FFSS_ERR_UNSUPPORTED, "more than %d distinct predicates", kMaxBool);
+    }
+    for (uint32_t j = 0; j < S.n_pw; ++j)
+      for (uint32_t i = 0; i < d->m; ++i) {
+        const ffss_pred_desc &q = d->piecewise[i * S.n_pw + j];
+        if (q.f < 1 || q.f > d->k) return fail(FFSS_ERR_INVALID, "piecewise (%u, %u): f=%u outside 1..k", i, j, q.f);
+        const uint64_t Nf = uint64_t(1) << q.f;
+        if (q.c >= Nf || q.gamma > Nf)
+          return fail(FFSS_ERR_INVALID, "piecewise (%u, %u): c or gamma out of range", i, j);
+        const int pr = add_prim(q.f, q.c, q.gamma);
+        if (pr < -1) return fail(FFSS_ERR_UNSUPPORTED, "more than %d distinct predicates", kMaxBool);
+        S.pw_prim[j][i] = pr;
+        const uint32_t cst = (pr < 0 && q.gamma != 0) ? 1u : 0u;
+        S.pw_fix[j] |= (cst ^ (q.negate & 1u)) << i;
+      }
+  }
   // query list: views in order of first appearance; per view the r-atom, then
   // one theta atom per predicate of that view
   std::vector<std::pair<uint32_t, uint64_t>> views;
@@ -279,10 +317,11 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   }
   ffss_shape &sh = sp->shape;
   sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
-  sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.n_mults; sh.n_bool = S.n_bool;
+  sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.n_mults; sh.n_bool = S.n_bool + S.n_pw;
+  sh.n_piecewise = S.n_pw;
   sh.n_views = S.n_views;
   sh.key_bytes_per_elem = key_bytes_per_elem(S);
-  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults;
+  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults + 8ull * S.n_pw;
   sh.aes_per_elem = aes_per_elem(S);
   sh.keygen_aes_per_elem = keygen_aes_per_elem(S);
   *out = sp;

@@ -143,17 +143,77 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
-// share of C(x) = atom_theta ^ atom_r ^ <w>, constants and negations by party 0.
+// a party's share of primitive predicate j is atom_theta ^ atom_r ^ <w_j>.
+__device__ __forceinline__ uint32_t prim_share(const DevSpec &S, uint32_t atoms, uint32_t carry, int j) {
+  return ((atoms >> S.prim_qtheta[j]) ^ (atoms >> S.prim_qr[j]) ^ (carry >> j)) & 1u;
+}
+
+// Shares of the global Boolean outputs; constants and negations by party 0.
 __device__ __forceinline__ uint32_t combine_bits(uint32_t b, const DevSpec &S, const KeyLayout &L,
                                                  const char *kb, uint64_t e, uint32_t atoms) {
   const uint32_t carry = reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e];
   uint32_t z = 0;
   for (uint32_t o = 0; o < S.n_bool; ++o) {
     const int j = S.out_prim[o];
-    if (j >= 0)
-      z |= (((atoms >> S.prim_qtheta[j]) ^ (atoms >> S.prim_qr[j]) ^ (carry >> j)) & 1u) << o;
+    if (j >= 0) z |= prim_share(S, atoms, carry, j) << o;
   }
   if (b == 0) z ^= S.out_const ^ S.out_neg;
+  return z;
+}
+
+// Piecewise Boolean outputs (Lemma "boolean normalization"): output j is
+// XOR_i (J_i AND B_i^(j)), where J_i = C_{alpha_{i+1}} ^ C_{alpha_i} is the
+// interval indicator (Lemma "interval indicator as XOR"; C_{alpha_0} = 0,
+// C_{alpha_m} = 1).  Both are m-bit words of XOR shares (bit i = interval
+// i), so an output's m ANDs take one packed Boolean triple (a, b, c): each
+// party opens e = J ^ a and f = B ^ b (4 + 4 bytes), then holds
+// [party 0] (E & F) ^ (E & b) ^ (F & a) ^ c, whose parity is its share of z_j.
+// First half: write this party's (e | f << 32) words to `out` (kMaxPW slots).
+__device__ __forceinline__ void pw_send(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
+                                        uint64_t e, bool valid, uint32_t atoms, uint64_t *out,
+                                        unsigned long long &sent) {
+  uint32_t jw = 0;
+  const uint32_t *bt = reinterpret_cast<const uint32_t *>(kb + L.off_btrip);
+  const uint32_t carry = valid ? reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e] : 0u;
+  if (valid) {
+    uint32_t c_prev = 0;                       // C_{alpha_0} = 0
+    for (uint32_t i = 0; i < S.m; ++i) {
+      const uint32_t c_next = i + 1 < S.m ? prim_share(S, atoms, carry, S.part_prim[i + 1]) : (b == 0 ? 1u : 0u);
+      jw |= (c_next ^ c_prev) << i;
+      c_prev = c_next;
+    }
+  }
+  for (uint32_t j = 0; j < S.n_pw; ++j) {
+    uint64_t msg = 0;
+    if (valid) {
+      uint32_t bw = b == 0 ? S.pw_fix[j] : 0u;
+      for (uint32_t i = 0; i < S.m; ++i) {
+        const int pr = S.pw_prim[j][i];
+        if (pr >= 0) bw ^= prim_share(S, atoms, carry, pr) << i;
+      }
+      const uint32_t a = bt[(uint64_t(j) * 3 + 0) * L.n + e], bb = bt[(uint64_t(j) * 3 + 1) * L.n + e];
+      msg = uint64_t(jw ^ a) | (uint64_t(bw ^ bb) << 32);
+      sent += 8;
+    }
+    out[j] = msg;
+  }
+}
+
+// Second half: combine both parties' openings into this party's output bits
+// (already shifted to bit n_bool + j).
+__device__ __forceinline__ uint32_t pw_finish(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
+                                              uint64_t e, const uint64_t *m0, const uint64_t *m1) {
+  const uint32_t *bt = reinterpret_cast<const uint32_t *>(kb + L.off_btrip);
+  uint32_t z = 0;
+  for (uint32_t j = 0; j < S.n_pw; ++j) {
+    const uint64_t o = m0[j] ^ m1[j];
+    const uint32_t Ev = uint32_t(o), Fv = uint32_t(o >> 32);
+    const uint32_t a = bt[(uint64_t(j) * 3 + 0) * L.n + e], bb = bt[(uint64_t(j) * 3 + 1) * L.n + e];
+    const uint32_t c = bt[(uint64_t(j) * 3 + 2) * L.n + e];
+    uint32_t w = (Ev & bb) ^ (Fv & a) ^ c;
+    if (b == 0) w ^= Ev & Fv;
+    z |= (uint32_t(__popc(w)) & 1u) << (S.n_bool + j);
+  }
   return z;
 }
 
@@ -201,12 +261,13 @@ struct GateSmem {
   ulonglong2 *box;        // [party][le][R] openings (the first word also carries x_b + r_b)
   uint64_t *red_acc;      // [party][slot][le][P]
   uint32_t *red_atoms;    // [party][slot][le]
+  uint64_t *pwbox;        // [party][le][kMaxPW] piecewise-output openings (e | f << 32)
 };
 
 __host__ __device__ constexpr size_t gate_smem_bytes() {
-  // tables + spec + outbox (R <= 4) + slot partials (P <= 4)
+  // tables + spec + outbox (R <= 4) + slot partials (P <= 4) + piecewise openings
   return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 2ull * 256 * 4 * 16 +
-         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4;
+         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4 + 2ull * 256 * 8 * kMaxPW;
 }
 
 __device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
@@ -219,6 +280,8 @@ __device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
   g.red_acc = reinterpret_cast<uint64_t *>(p);
   p += 2ull * 256 * 8 * kMaxP;
   g.red_atoms = reinterpret_cast<uint32_t *>(p);
+  p += 2ull * 256 * 4;
+  g.pwbox = reinterpret_cast<uint64_t *>(p);
   return g;
 }
 
@@ -298,6 +361,13 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
     xs = b == 0 ? xhat - r_b : 0ull - r_b;
 #pragma unroll
     for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
+    if (S.n_pw) pw_send(b, S, L, kb, e, valid, atoms, G.pwbox + (b * E + le) * kMaxPW, sent);
+  }
+  // piecewise Boolean outputs: one exchange of the packed AND openings
+  // (uniform across the CTA: one spec per tile)
+  if (S.n_pw) {
+    __syncthreads();
+    if (lead && valid) z |= pw_finish(b, S, L, kb, e, G.pwbox + le * kMaxPW, G.pwbox + (E + le) * kMaxPW);
   }
   // x^-basis variant: the coefficients multiply the public x^, so Horner is
   // local to each party
@@ -416,25 +486,7 @@ __host__ __device__ constexpr int shape_class(uint32_t r, uint32_t d) {
 
 constexpr uint32_t kBatchMaxCalls = 512;
 
-__device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n) {
-  KeyLayout L;
-  L.n = n;
-  uint64_t o = 0;
-  L.off_r = o; o = align256(o + 8 * n);
-  L.off_carry = o; o = align256(o + 4 * n);
-  L.off_vlast = o; o = align256(o + 8ull * s.p * n);
-  L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
-  for (uint32_t t = 0; t < s.T; ++t) {
-    L.off_q[t] = o;
-    o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
-  }
-  for (uint32_t j = 0; j + 1 < s.M; ++j) {
-    L.off_l[j] = o;
-    o = align256(o + 16ull * (s.k + 1) * n + 8ull * (s.k + 1) * s.p * n);
-  }
-  L.total = o;
-  return L;
-}
+__device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n) { return make_layout(s, n); }
 
 template <int R, int D>
 __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *hdr, const BatchCall *all_calls,
@@ -665,6 +717,22 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
         tr1[(uint64_t(mi) * 3 + 1) * n + e] = bb - b0;
         tr0[(uint64_t(mi) * 3 + 2) * n + e] = c0;
         tr1[(uint64_t(mi) * 3 + 2) * n + e] = a * bb - c0;
+      }
+      // packed Boolean AND triples of the piecewise outputs: m bits each,
+      // c = a AND b, XOR-shared
+      uint32_t *bt0 = reinterpret_cast<uint32_t *>(A.k0 + L.off_btrip);
+      uint32_t *bt1 = reinterpret_cast<uint32_t *>(A.k1 + L.off_btrip);
+      const uint32_t mbits = S.m >= 32 ? 0xFFFFFFFFu : ((1u << S.m) - 1u);
+      for (uint32_t j = 0; j < S.n_pw; ++j) {
+        const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * j;
+        const uint32_t a = prg(di).x & mbits, bb = prg(di + 1).x & mbits;
+        const uint32_t a0 = prg(di + 2).x & mbits, b0 = prg(di + 3).x & mbits, c0 = prg(di + 4).x & mbits;
+        bt0[(uint64_t(j) * 3 + 0) * n + e] = a0;
+        bt1[(uint64_t(j) * 3 + 0) * n + e] = a ^ a0;
+        bt0[(uint64_t(j) * 3 + 1) * n + e] = b0;
+        bt1[(uint64_t(j) * 3 + 1) * n + e] = bb ^ b0;
+        bt0[(uint64_t(j) * 3 + 2) * n + e] = c0;
+        bt1[(uint64_t(j) * 3 + 2) * n + e] = (a & bb) ^ c0;
       }
     }
   }

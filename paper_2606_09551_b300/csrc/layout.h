@@ -16,11 +16,13 @@ constexpr int kMaxM = 16;
 constexpr int kMaxP = 4;
 constexpr int kMaxT = 32;
 constexpr int kMaxBool = 32;
+constexpr int kMaxPW = 4;      // piecewise Boolean outputs
 
 // Dealer draw indices per element (public, spec-determined): r_in, party-0
 // share of r_in, party-0 share of x, party-0 carry-share word, p party-0
 // shares of v_{M-1}, two root seeds per DCF key (queries, then lookup keys),
-// five draws per Beaver triple (a, b, a_0, b_0, c_0).
+// five draws per Beaver triple (a, b, a_0, b_0, c_0), then five per packed
+// Boolean AND triple of a piecewise output (a, b, a_0, b_0, c_0; m bits each).
 constexpr uint32_t kDrawRin = 0;
 constexpr uint32_t kDrawRsh = 1;
 constexpr uint32_t kDrawXsh = 2;
@@ -48,6 +50,15 @@ struct DevSpec {
   uint32_t n_mults;            // Beaver multiplications per element (d r, or 0 when xhat)
   uint64_t alpha[kMaxM + 1];
   uint64_t coeff[kMaxM * kMaxP];      // [piece][q], q = o*(d+1) + j
+  // Piecewise Boolean outputs (operator specification item 3; Lemma
+  // "boolean normalization"): output j is B_i^(j)(x) on interval i, computed
+  // as XOR_i (J_i AND B_i^(j)) with the interval indicators
+  // J_i = C_{alpha_{i+1}} ^ C_{alpha_i}.  Their bits follow the n_bool
+  // global outputs in the output word.
+  uint32_t n_pw;
+  int32_t part_prim[kMaxM];           // [i], i = 1..m-1: predicate index of C_{alpha_i}
+  int32_t pw_prim[kMaxPW][kMaxM];     // [j][i]: predicate of B_i^(j), or -1 (sentinel constant)
+  uint32_t pw_fix[kMaxPW];            // [j]: bit i = sentinel value ^ negation, applied by party 0
 };
 
 // Byte offsets of one party's key material for n elements.  Every section is
@@ -58,12 +69,13 @@ struct DevSpec {
 //   carry share      u32  [n]
 //   v_{M-1} share    u64  [p][n]
 //   triples          u64  [n_mults][3][n]          (a, b, c)
+//   Boolean triples  u32  [n_pw][3][n]             (a, b, c), m packed bits each
 //   query t          uint4 root[n], uint4 cw[k_t][n] (seed CW | t_L | t_R << 1),
 //                    u64 vcw[n] (bit i = V_CW of level i, bit k_t = final CW)
 //   lookup key j     uint4 root[n], uint4 cw[k][n], u64 vcw[k+1][p][n] (level k = final CW)
 struct KeyLayout {
   uint64_t n;
-  uint64_t off_r, off_carry, off_vlast, off_trip;
+  uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip;
   uint64_t off_q[kMaxT];
   uint64_t off_l[kMaxM];
   uint64_t total;
@@ -71,7 +83,7 @@ struct KeyLayout {
 
 FFSS_HD uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
+FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   KeyLayout L{};
   L.n = n;
   uint64_t o = 0;
@@ -79,6 +91,7 @@ inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_carry = o; o = align256(o + 4 * n);
   L.off_vlast = o; o = align256(o + 8ull * s.p * n);
   L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
+  L.off_btrip = o; o = align256(o + 12ull * s.n_pw * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
     o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
@@ -93,7 +106,7 @@ inline KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
-  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults;
+  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_pw;
   for (uint32_t t = 0; t < s.T; ++t) b += 16ull * (s.q_f[t] + 1) + 8;
   if (s.M > 1) b += (s.M - 1) * (16ull * (s.k + 1) + 8ull * (s.k + 1) * s.p);
   return b;
@@ -112,7 +125,7 @@ inline uint64_t aes_per_elem(const DevSpec &s) {
 // children's payload blocks of both parties (4V); the final lookup
 // correction needs both parties' leaf payloads (2V).
 inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
-  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults;
+  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_pw;
   for (uint32_t t = 0; t < s.T; ++t) a += 4ull * s.q_f[t];
   if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (4 + 4 * s.V) + 2 * s.V);
   return a;

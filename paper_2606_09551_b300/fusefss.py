@@ -40,7 +40,8 @@ class SpecDesc(C.Structure):
     _fields_ = [("k", C.c_uint32), ("frac_bits", C.c_uint32), ("m", C.c_uint32), ("degree", C.c_uint32),
                 ("n_out", C.c_uint32), ("partition_bits", C.c_uint32),
                 ("alpha", C.POINTER(C.c_uint64)), ("coeff", C.POINTER(C.c_uint64)),
-                ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc)), ("xhat_basis", C.c_uint32)]
+                ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc)), ("xhat_basis", C.c_uint32),
+                ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc))]
 
 
 class Shape(C.Structure):
@@ -48,7 +49,8 @@ class Shape(C.Structure):
                 ("T", C.c_uint32), ("M", C.c_uint32), ("p", C.c_uint32), ("n_mults", C.c_uint32),
                 ("n_bool", C.c_uint32), ("n_views", C.c_uint32),
                 ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
-                ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64)]
+                ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64),
+                ("n_piecewise", C.c_uint32)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -187,10 +189,16 @@ class CompiledSpec:
         preds = (PredDesc * max(len(spec.preds), 1))()
         for i, q in enumerate(spec.preds):
             preds[i] = PredDesc(q.f, q.negate, q.c, q.gamma)
-        self._keep = (alpha, coeff, preds)
+        # piecewise outputs: spec.piecewise[j][i] -> flat index i * n_piecewise + j
+        npw = len(spec.piecewise)
+        pw = (PredDesc * max(npw * spec.m, 1))()
+        for j, out in enumerate(spec.piecewise):
+            for i, q in enumerate(out):
+                pw[i * npw + j] = PredDesc(q.f, q.negate, q.c, q.gamma)
+        self._keep = (alpha, coeff, preds, pw)
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
-                     len(spec.preds), preds, 1 if spec.xhat_basis else 0)
+                     len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw)
         h = vp()
         _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
         self.h = h

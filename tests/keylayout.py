@@ -22,6 +22,7 @@ def offsets(ospec: O.Spec, n: int):
     off["carry"] = o; o = _a256(o + 4 * n)
     off["vlast"] = o; o = _a256(o + 8 * ospec.p * n)
     off["trip"] = o; o = _a256(o + 24 * ospec.n_mults * n)
+    off["btrip"] = o; o = _a256(o + 12 * ospec.n_pw * n)
     off["q"] = []
     for (f, c, pr) in q:
         off["q"].append(o)
@@ -59,6 +60,9 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
     out["ta"] = np.array([trip[(mi * 3 + 0) * n + e] for mi in range(nm)], np.uint64)
     out["tb"] = np.array([trip[(mi * 3 + 1) * n + e] for mi in range(nm)], np.uint64)
     out["tc"] = np.array([trip[(mi * 3 + 2) * n + e] for mi in range(nm)], np.uint64)
+    bt = _u32(buf, off["btrip"], 3 * ospec.n_pw * n)
+    for name, w in (("ba", 0), ("bb", 1), ("bc", 2)):
+        out[name] = np.array([bt[(j * 3 + w) * n + e] for j in range(ospec.n_pw)], np.uint32)
     qk = []
     for t, (f, c, pr) in enumerate(ospec.queries()):
         blk = _blocks(buf, off["q"][t], (f + 1) * n)
@@ -84,7 +88,7 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
     the library's way (t_L in bit 0, t_R in bit 1 of the seed correction)."""
     base = keys.fields(ospec, i)
     out = dict(r_share=base["r_share"], carry=base["carry"], vlast=base["vlast"],
-               ta=base["ta"], tb=base["tb"], tc=base["tc"])
+               ta=base["ta"], tb=base["tb"], tc=base["tc"], ba=base["ba"], bb=base["bb"], bc=base["bc"])
     qk = []
     for t, (f, c, pr) in enumerate(ospec.queries()):
         fl = keys.qkey(i, t).fields(f, 0)
@@ -107,7 +111,7 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
 def fields_equal(a, b) -> bool:
     if a["r_share"] != b["r_share"] or a["carry"] != b["carry"]:
         return False
-    for key in ("vlast", "ta", "tb", "tc"):
+    for key in ("vlast", "ta", "tb", "tc", "ba", "bb", "bc"):
         if not np.array_equal(a[key], b[key]):
             return False
     for qa, qb in zip(a["q"], b["q"]):
@@ -130,6 +134,7 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
     cy = _u32(buf, off["carry"], n)
     vl = _u64(buf, off["vlast"], p * n)
     tr = _u64(buf, off["trip"], 3 * nm * n)
+    bt = _u32(buf, off["btrip"], 3 * ospec.n_pw * n)
     qs = ospec.queries()
     for e in range(n):
         fl = oracle_fields(keys, ospec, e)
@@ -141,6 +146,9 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             tr[(mi * 3 + 0) * n + e] = fl["ta"][mi]
             tr[(mi * 3 + 1) * n + e] = fl["tb"][mi]
             tr[(mi * 3 + 2) * n + e] = fl["tc"][mi]
+        for j in range(ospec.n_pw):
+            for w, name in enumerate(("ba", "bb", "bc")):
+                bt[(j * 3 + w) * n + e] = fl[name][j]
         for t, (f, c, pr) in enumerate(qs):
             blk = _blocks(buf, off["q"][t], (f + 1) * n)
             blk[e] = fl["q"][t]["root"]

@@ -39,14 +39,23 @@ def test_context_without_gpu_fails_cleanly(libpath):
     assert rc == -3 and F.lib().ffss_last_error()
 
 
-def _shape_vs_oracle(sp):
+def _shape_vs_oracle(sp, may_reject=False):
+    try:
+        o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(),
+                   sp.xhat_basis, sp.piecewise_tuples())
+    except ValueError:
+        # past the 32-query / 32-predicate limits: the library rejects it too
+        assert may_reject
+        with pytest.raises(F.FfssError):
+            F.CompiledSpec(sp)
+        return None
     cs = F.CompiledSpec(sp)           # host-only compile
-    o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
     sh = cs.shape
     assert (sh.T, sh.M, sh.p, sh.n_mults, sh.n_bool) == (o.T, o.M, o.p, o.n_mults, o.n_bool)
-    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults
+    assert sh.n_piecewise == o.n_pw == len(sp.piecewise)
+    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_pw
     qs = o.queries()
-    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + sum(16 * (f + 1) + 8 for f, _, _ in qs)
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + sum(16 * (f + 1) + 8 for f, _, _ in qs)
     if o.M > 1:
         kb += (o.M - 1) * (16 * (o.k + 1) + 8 * (o.k + 1) * o.p)
     assert sh.key_bytes_per_elem == kb
@@ -80,10 +89,13 @@ def test_random_spec_shapes():
         r = 1 if d > 1 else int(rng.integers(1, 3))
         sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(rng.integers(0, 2)),
                            n_extra=int(rng.integers(0, 6)))
-        _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)))
+        if trial % 2:
+            sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
+        _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)), may_reject=True)
 
 
-@pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0"])
+@pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0",
+                                 "pw_count", "pw_f", "pw_gamma"])
 def test_invalid_specs_rejected(bad):
     sp = S.random_spec(np.random.default_rng(1), 8, 4, 1)
     if bad == "alpha_order":
@@ -100,5 +112,11 @@ def test_invalid_specs_rejected(bad):
         sp.preds = [S.PredDesc(9, 0, 3, 0)]
     elif bad == "k0":
         sp.k = 0
+    elif bad == "pw_count":
+        sp.piecewise = [[S.PredDesc(1, 0, 1, 0)] * sp.m for _ in range(5)]
+    elif bad == "pw_f":
+        sp.piecewise = [[S.PredDesc(9, 0, 1, 0)] * sp.m]
+    elif bad == "pw_gamma":
+        sp.piecewise = [[S.PredDesc(3, 0, 9, 0)] * sp.m]
     with pytest.raises(F.FfssError):
         F.CompiledSpec(sp)

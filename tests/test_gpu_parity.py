@@ -71,10 +71,15 @@ def _specs():
         out.append(S.random_spec(rng, k, m, d, r, partition_bits=True, n_extra=extra, name=f"rand_k{k}_m{m}"))
     # the x^-basis payload variant (no Beaver rounds) on a workload spec and two random ones
     out += [S.gelu8().variant(True), out[4].variant(True), out[8].variant(True)]
-    return out
+    # piecewise Boolean outputs (one packed Boolean AND triple each)
+    pw = [S.random_piecewise(rng, S.gelu4(), 2), S.random_piecewise(rng, out[3], 3),
+          S.random_piecewise(rng, out[4], 4), S.random_piecewise(rng, out[8], 1).variant(True),
+          S.random_piecewise(rng, out[6], 2)]
+    return out + pw
 
 
 SPECS = _specs()
+PW_SPECS = [s for s in SPECS if s.piecewise]
 
 
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
@@ -97,14 +102,14 @@ def test_keygen_and_gate_bit_exact(ctx, sp):
     yp, zp = osp.plain_eval(x)
     assert np.array_equal(g["y"], yp) and np.array_equal(g["z"], zp)
     mults = 0 if sp.xhat_basis else sp.degree * sp.n_out
-    assert list(g["comm"]) == [n * (8 + 16 * mults)] * 2
+    assert list(g["comm"]) == [n * (8 + 16 * mults + 8 * len(sp.piecewise))] * 2
 
 
 def test_gpu_eval_of_oracle_keys(ctx):
     """Keys written by the oracle dealer, packed into the library's layout,
     evaluate on the GPU to the oracle's shares (eval checked apart from keygen)."""
     import torch
-    for sp in (S.gelu4(), SPECS[4]):
+    for sp in (S.gelu4(), SPECS[4], PW_SPECS[1]):
         n = 300
         x = I.uniform_x(n, sp.k, 9)
         o = oracle_gate(sp, x, call_id=3)
@@ -162,6 +167,8 @@ def test_every_input_small_k(ctx, k):
         m = int(rng.integers(1, min(16, N - 1) + 1))
         d = int(rng.integers(0, 4))
         sp = S.random_spec(rng, k, m, d, 1, partition_bits=True, n_extra=int(rng.integers(0, 4)))
+        if trial % 2:
+            sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
         x = np.tile(np.arange(N, dtype=np.uint64), 64) + (rng.integers(0, 2 ** 50, N * 64, dtype=np.uint64) << np.uint64(k))
         g = gpu_gate(ctx, sp, x, call_id=trial)
         yp, zp = ospec(sp).plain_eval(x)

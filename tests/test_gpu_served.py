@@ -43,7 +43,10 @@ def _shares(layers):
 
 def test_alone_equals_mixed_and_plain(ctx):
     import torch
-    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    # GeLU-8 with two piecewise Boolean outputs: their Boolean triples are
+    # dealt per chunk too
+    gelu_pw = S.random_piecewise(np.random.default_rng(8), S.gelu8(), 2)
+    css = [F.CompiledSpec(gelu_pw, ctx), F.CompiledSpec(S.nexp16(), ctx)]
     sizes = [[2500, 900], [700, 1300], [4000, 64], [300, 2000]]
     # alone, roomy budget
     sv = F.Server(ctx, 256 << 20, 4, 1 << 20, I.KEY_SEED)
