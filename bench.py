@@ -192,8 +192,7 @@ def oracle_rates(calls, cpu_seconds, threads=None):
     threads = threads or os.cpu_count() or 1
     out, desc = {}, {}
     for c in calls:
-        o = O.Spec(c.spec.k, c.spec.m, c.spec.degree, c.spec.n_out, c.spec.alpha, c.spec.coeff,
-                   c.spec.partition_bits, c.spec.pred_tuples(), c.spec.xhat_basis, c.spec.piecewise_tuples())
+        o = O.Spec(**c.spec.descriptor())
         # single-core cost estimate: 0.45 us per AES block, both parties
         per_elem = 0.45e-6 * 2 * (sum(f for f, _, _ in o.queries())
                                   + (o.M - 1) * (o.k * (1 + (o.p + 1) // 2) + (o.p + 1) // 2))

@@ -50,8 +50,9 @@ def lib():
         L.or_dcf_eval.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.POINTER(C.c_int), u64p]
         L.or_spec_build.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                     u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32,
-                                    C.c_uint32, u32p, u64p, u64p, u32p]
+                                    C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32, C.c_uint32]
         L.or_spec_build.restype = C.c_int
+        L.or_elem_trunc.argtypes = [C.c_void_p, u64p, u32p, u64p]
         L.or_spec_shape.argtypes = [C.c_void_p, u32p]
         L.or_spec_query.argtypes = [C.c_void_p, C.c_uint32, u32p, u64p, i32p]
         L.or_plain_eval.argtypes = [C.c_void_p, u64p, C.c_uint64, u64p, u32p]
@@ -155,8 +156,10 @@ class Spec:
     """Oracle-side compiled operator specification."""
 
     def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False,
-                 piecewise=()):
-        """piecewise: per output j, m tuples (f, c, gamma, negate), one per interval."""
+                 piecewise=(), trunc_s=0, trunc_signed=False):
+        """piecewise: per output j, m tuples (f, c, gamma, negate), one per interval.
+        trunc_s > 0: output 0 gains the shift of the k-bit view by trunc_s
+        (arithmetic when trunc_signed)."""
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
         alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64))
         coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.uint64).reshape(-1))
@@ -174,8 +177,10 @@ class Spec:
         rc = lib().or_spec_build(self.ptr, k, m, d, r, _p(alpha, u64p), _p(coeff, u64p),
                                  1 if partition_bits else 0, n, _p(pf, u32p), _p(pc, u64p),
                                  _p(pg, u64p), _p(pn, u32p), 1 if xhat_basis else 0,
-                                 npw, _p(wf, u32p), _p(wc, u64p), _p(wg, u64p), _p(wn, u32p))
+                                 npw, _p(wf, u32p), _p(wc, u64p), _p(wg, u64p), _p(wn, u32p),
+                                 trunc_s, 1 if trunc_signed else 0)
         self.n_pw = npw
+        self.trunc_s, self.trunc_signed = trunc_s, bool(trunc_signed)
         if rc != 0:
             raise ValueError("oracle rejected the operator specification")
         sh = np.zeros(6, np.uint32)
@@ -234,9 +239,14 @@ class ElemKeys:
         npw = getattr(spec, "n_pw", 0)
         ba, bb, bc = (np.zeros(max(npw, 1), np.uint32) for _ in range(3))
         lib().or_elem_btriples(self.elem_ptr(i), npw, _p(ba, u32p), _p(bb, u32p), _p(bc, u32p))
-        return dict(r_share=int(r_share[0]), carry=int(carry[0]), vlast=vlast[:spec.p],
-                    ta=ta[:spec.n_mults], tb=tb[:spec.n_mults], tc=tc[:spec.n_mults],
-                    ba=ba[:npw], bb=bb[:npw], bc=bc[:npw])
+        out = dict(r_share=int(r_share[0]), carry=int(carry[0]), vlast=vlast[:spec.p],
+                   ta=ta[:spec.n_mults], tb=tb[:spec.n_mults], tc=tc[:spec.n_mults],
+                   ba=ba[:npw], bb=bb[:npw], bc=bc[:npw])
+        if getattr(spec, "trunc_s", 0):
+            t, rho, rho_a = np.zeros(1, np.uint64), np.zeros(1, np.uint32), np.zeros(2, np.uint64)
+            lib().or_elem_trunc(self.elem_ptr(i), _p(t, u64p), _p(rho, u32p), _p(rho_a, u64p))
+            out.update(tr_t=int(t[0]), tr_rho=int(rho[0]), tr_rho_a=rho_a)
+        return out
 
     def qkey(self, i: int, t: int) -> DcfKey:
         key = DcfKey()

@@ -451,6 +451,14 @@ typedef struct {
     int32_t pw_prim[MAXM][MAXPW];     /* its prim, or -1 for a sentinel constant */
     uint32_t pw_const[MAXM][MAXPW];   /* the constant when pw_prim < 0 */
     int32_t part_prim[MAXM + 1];      /* prim of C_{alpha_i}, i = 1..m-1 (when n_pw > 0) */
+    /* truncation / arithmetic right shift by trunc_s (Def. "specification-
+     * compatible scalar gate"): output 0 gains T_s(x), with T_s the logical
+     * shift of the k-bit view (trunc_signed = 0) or the arithmetic shift of
+     * its sign-extended value (trunc_signed = 1); 0 = none */
+    uint32_t trunc_s, trunc_signed;
+    uint64_t trunc_c;                 /* view shift: 2^{k-1} for the signed form, else 0 */
+    int32_t trunc_q_lo;               /* query of the r-atom 1[x^ mod 2^s < r mod 2^s] */
+    int32_t trunc_q_hi;               /* query of the r-atom 1[view_{k,c}(x^) < r mod 2^k] */
 } or_spec;
 
 /* index of primitive predicate (f, c, gamma) in sp->prim, adding it if new;
@@ -479,7 +487,7 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
                   uint32_t n_extra, const uint32_t *ef, const uint64_t *ec,
                   const uint64_t *egamma, const uint32_t *eneg, uint32_t xhat_basis,
                   uint32_t n_pw, const uint32_t *pwf, const uint64_t *pwc, const uint64_t *pwg,
-                  const uint32_t *pwn)
+                  const uint32_t *pwn, uint32_t trunc_s, uint32_t trunc_signed)
 {
     memset(sp, 0, sizeof(*sp));
     if (k < 1 || k > MAXK || m < 1 || m > MAXM) return -1;
@@ -557,18 +565,34 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
             }
     }
 
-    /* views in order of first appearance */
-    uint32_t nviews = 0, vf[MAXPRED];
-    uint64_t vc[MAXPRED];
+    /* views in order of first appearance; a truncation adds the views
+     * (s, 0) and (k, c_t) after them when no predicate uses them */
+    uint32_t nviews = 0, vf[MAXPRED + 2];
+    uint64_t vc[MAXPRED + 2];
     for (uint32_t j = 0; j < sp->n_prim; j++) {
         int seen = 0;
         for (uint32_t v = 0; v < nviews; v++) if (vf[v] == sp->prim[j].f && vc[v] == sp->prim[j].c) seen = 1;
         if (!seen) { vf[nviews] = sp->prim[j].f; vc[nviews] = sp->prim[j].c; nviews++; }
     }
+    if (trunc_s > 0) {
+        if (trunc_s >= k) return -1;
+        sp->trunc_s = trunc_s;
+        sp->trunc_signed = trunc_signed ? 1 : 0;
+        sp->trunc_c = sp->trunc_signed ? pow2(k - 1) : 0;
+        uint32_t tf[2] = {trunc_s, k};
+        uint64_t tc[2] = {0, sp->trunc_c};
+        for (int u = 0; u < 2; u++) {
+            int seen = 0;
+            for (uint32_t v = 0; v < nviews; v++) if (vf[v] == tf[u] && vc[v] == tc[u]) seen = 1;
+            if (!seen) { vf[nviews] = tf[u]; vc[nviews] = tc[u]; nviews++; }
+        }
+    }
     uint32_t T = 0;
     for (uint32_t v = 0; v < nviews; v++) {
         if (T >= MAXQ) return -1;
         int qr = (int)T;
+        if (sp->trunc_s && vf[v] == sp->trunc_s && vc[v] == 0) sp->trunc_q_lo = qr;
+        if (sp->trunc_s && vf[v] == k && vc[v] == sp->trunc_c) sp->trunc_q_hi = qr;
         sp->q_f[T] = vf[v]; sp->q_c[T] = vc[v]; sp->q_prim[T] = -1; T++;
         for (uint32_t j = 0; j < sp->n_prim; j++) {
             if (sp->prim[j].f != vf[v] || sp->prim[j].c != vc[v]) continue;
@@ -621,6 +645,20 @@ void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y
             uint64_t acc = c[sp->d];
             for (int j = (int)sp->d - 1; j >= 0; j--) acc = acc * x[e] + c[j];
             y[e * sp->r + o] = acc;
+        }
+        if (sp->trunc_s) {
+            /* logical: (x mod 2^k) >> s; signed: floor(v / 2^s) with v the
+             * k-bit two's-complement value of x mod 2^k, sign-extended */
+            uint64_t t;
+            if (sp->trunc_signed) {
+                int64_t v = (int64_t)xk - ((xk >> (sp->k - 1)) ? (int64_t)pow2(sp->k) : 0);
+                int64_t q = v >= 0 ? v / (int64_t)pow2(sp->trunc_s)
+                                   : -(((-v) + (int64_t)pow2(sp->trunc_s) - 1) / (int64_t)pow2(sp->trunc_s));
+                t = (uint64_t)q;
+            } else {
+                t = xk / pow2(sp->trunc_s);
+            }
+            y[e * sp->r] += t;
         }
         uint32_t bits = 0;
         for (uint32_t o = 0; o < sp->n_out_bits; o++) {
@@ -685,6 +723,9 @@ typedef struct {
     or_dcf_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
     uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
     uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
+    uint64_t tr_t;                    /* truncation: share of (r mod 2^k) >> s */
+    uint32_t tr_rho;                  /* daBits: XOR shares of rho_lo (bit 0), rho_hi (bit 1) */
+    uint64_t tr_rho_a[2];             /* daBits: additive shares of rho_lo, rho_hi */
 } or_elem_keys;
 
 size_t or_elem_keys_size(void) { return sizeof(or_elem_keys); }
@@ -875,6 +916,22 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             K0->bb[j] = b0; K1->bb[j] = b ^ b0;
             K0->bc[j] = c0; K1->bc[j] = (a & b) ^ c0;
         }
+
+        /* truncation: shares of (r mod 2^k) >> s and two daBits (a random
+         * bit held both XOR- and additively shared, for the B2A of the
+         * borrow and wrap atoms); draws after the Boolean triples */
+        if (sp->trunc_s) {
+            uint32_t di = base_triples + 5 * sp->n_mults + 5 * sp->n_pw;
+            uint64_t t = (r_in & (pow2(sp->k) - 1)) >> sp->trunc_s;
+            uint64_t t0 = prg_u64(&g, di + 0, e);
+            uint32_t rho = (uint32_t)prg_u64(&g, di + 1, e) & 3u;
+            uint32_t rho0 = (uint32_t)prg_u64(&g, di + 2, e) & 3u;
+            uint64_t a_lo = prg_u64(&g, di + 3, e), a_hi = prg_u64(&g, di + 4, e);
+            K0->tr_t = t0; K1->tr_t = t - t0;
+            K0->tr_rho = rho0; K1->tr_rho = rho ^ rho0;
+            K0->tr_rho_a[0] = a_lo; K1->tr_rho_a[0] = (uint64_t)(rho & 1u) - a_lo;
+            K0->tr_rho_a[1] = a_hi; K1->tr_rho_a[1] = (uint64_t)(rho >> 1) - a_hi;
+        }
     }
 }
 
@@ -1055,6 +1112,33 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
                     y[b][o] = zz + pay[b][o * (d + 1) + (uint32_t)j];
                 }
         }
+        /* truncation (post-processing circuit of the shift gate): with
+         * u = view_{k,c}(x^), the integer identity
+         *   (x + c mod 2^k) >> s = (u >> s) - (r_k >> s) - 1[u mod 2^s < r_s] + 2^{k-s} 1[u < r_k]
+         * takes the borrow and wrap bits, the r-atoms of views (s, 0) and
+         * (k, c), from the packed comparison; each goes from XOR to additive
+         * shares with a daBit: open o = bit ^ rho (both bits in one byte),
+         * then [bit] = [b=0] o + (1 - 2 o) [rho]; finally subtract c >> s */
+        if (sp->trunc_s) {
+            uint32_t o[2];
+            for (int b = 0; b < 2; b++) {
+                uint32_t lo = (atoms_b[b] >> sp->trunc_q_lo) & 1u, hi = (atoms_b[b] >> sp->trunc_q_hi) & 1u;
+                o[b] = (lo | (hi << 1)) ^ KK[b]->tr_rho;
+                sent[b] += 1;
+            }
+            uint32_t delta = o[0] ^ o[1];
+            uint64_t u = view(xhat, sp->k, sp->trunc_c);
+            for (int b = 0; b < 2; b++) {
+                uint64_t bit_a[2];
+                for (int q = 0; q < 2; q++) {
+                    uint64_t dq = (delta >> q) & 1u;
+                    bit_a[q] = (b == 0 ? dq : 0) + (dq ? (uint64_t)0 - KK[b]->tr_rho_a[q] : KK[b]->tr_rho_a[q]);
+                }
+                uint64_t sh = (uint64_t)0 - KK[b]->tr_t - bit_a[0] + (bit_a[1] << (sp->k - sp->trunc_s));
+                if (b == 0) sh += (u >> sp->trunc_s) - (sp->trunc_c >> sp->trunc_s);
+                y[b][0] += sh;
+            }
+        }
         for (int b = 0; b < 2; b++)
             for (uint32_t o = 0; o < r; o++) ys[b][e * r + o] = y[b][o];
     }
@@ -1104,4 +1188,9 @@ void or_elem_fields(const or_elem_keys *K, uint32_t p, uint32_t nm, uint64_t *r_
     *carry = K->carry_share;
     for (uint32_t q = 0; q < p; q++) vlast[q] = K->vlast_share[q];
     for (uint32_t i = 0; i < nm; i++) { ta[i] = K->ta[i]; tb[i] = K->tb[i]; tc[i] = K->tc[i]; }
+}
+
+void or_elem_trunc(const or_elem_keys *K, uint64_t *t, uint32_t *rho, uint64_t *rho_a)
+{
+    *t = K->tr_t; *rho = K->tr_rho; rho_a[0] = K->tr_rho_a[0]; rho_a[1] = K->tr_rho_a[1];
 }

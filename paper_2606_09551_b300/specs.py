@@ -56,6 +56,10 @@ class OperatorSpec:
     # interval i (sentinel gamma 0 / 2^f for constants); they follow the
     # partition bits and the preds in z
     piecewise: List[List[PredDesc]] = field(default_factory=list)
+    # truncation: output 0 gains (x mod 2^k) >> trunc_shift, or the arithmetic
+    # shift of its k-bit two's-complement value when trunc_signed (0 = none)
+    trunc_shift: int = 0
+    trunc_signed: bool = False
     real_fn: Callable[[np.ndarray], np.ndarray] | None = None
     domain: Tuple[float, float] | None = None
 
@@ -68,6 +72,13 @@ class OperatorSpec:
 
     def piecewise_tuples(self):
         return [[q.astuple() for q in out] for out in self.piecewise]
+
+    def descriptor(self) -> dict:
+        """The public descriptor as plain Python values (no method arithmetic):
+        what a compiler of this specification needs, by field name."""
+        return dict(k=self.k, m=self.m, d=self.degree, r=self.n_out, alpha=list(self.alpha), coeff=self.coeff,
+                    partition_bits=self.partition_bits, preds=self.pred_tuples(), xhat_basis=self.xhat_basis,
+                    piecewise=self.piecewise_tuples(), trunc_s=self.trunc_shift, trunc_signed=self.trunc_signed)
 
     def variant(self, xhat_basis: bool) -> "OperatorSpec":
         """The same specification evaluated in the other protocol variant."""
@@ -303,6 +314,15 @@ def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,
         preds.append(PredDesc(f, c, g, int(rng.integers(0, 2))))
     return OperatorSpec(name=name, k=k, frac_bits=0, out_frac_bits=0, m=m, degree=d, n_out=r,
                         alpha=alpha, coeff=coeff, partition_bits=partition_bits, preds=preds)
+
+
+def trunc(k: int, s: int, signed: bool = True, name: str | None = None) -> OperatorSpec:
+    """Truncation (logical shift of the k-bit view by s) or arithmetic right
+    shift (signed k-bit value, floor division by 2^s) as a gate: one
+    interval, a zero polynomial, and the shift added to the output."""
+    return OperatorSpec(name or ("ars" if signed else "trunc") + f"{k}_{s}", k=k, frac_bits=s, out_frac_bits=0,
+                        m=1, degree=0, n_out=1, alpha=[0, 1 << k], coeff=np.zeros((1, 1, 1), np.uint64),
+                        partition_bits=False, trunc_shift=s, trunc_signed=signed)
 
 
 def random_piecewise(rng: np.random.Generator, spec: OperatorSpec, n_pw: int) -> OperatorSpec:

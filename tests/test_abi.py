@@ -41,8 +41,7 @@ def test_context_without_gpu_fails_cleanly(libpath):
 
 def _shape_vs_oracle(sp, may_reject=False):
     try:
-        o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(),
-                   sp.xhat_basis, sp.piecewise_tuples())
+        o = O.Spec(**sp.descriptor())
     except ValueError:
         # past the 32-query / 32-predicate limits: the library rejects it too
         assert may_reject

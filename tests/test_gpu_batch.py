@@ -70,7 +70,7 @@ def test_batch_equals_plain(ctx, slots):
             assert torch.equal(p[i], b[i]), sp.name
         y = (b[5].cpu().numpy() + b[6].cpu().numpy()).reshape(x.size, sp.n_out)
         z = b[7].cpu().numpy() ^ b[8].cpu().numpy()
-        o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
+        o = O.Spec(**sp.descriptor())
         yp, zp = o.plain_eval(x)
         assert np.array_equal(y, yp) and np.array_equal(z, zp), sp.name
     assert torch.equal(cp, cb)
@@ -85,7 +85,7 @@ def test_batch_graph_replay_and_ring(ctx):
     import torch
     bt = F.Batch(ctx, 8)
     sp = S.gelu4()
-    o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
+    o = O.Spec(**sp.descriptor())
     outs = []
     for rep in range(5):
         x = I.uniform_x(3000 + rep * 77, sp.k, 500 + rep)
@@ -98,7 +98,7 @@ def test_batch_graph_replay_and_ring(ctx):
         y = c[5].cpu().numpy() + c[6].cpu().numpy()
         assert np.array_equal(y, o.plain_eval(x)[0][:, 0])
         r = S.relu(16)
-        orl = O.Spec(r.k, r.m, r.degree, r.n_out, r.alpha, r.coeff, r.partition_bits, r.pred_tuples(), r.xhat_basis, r.piecewise_tuples())
+        orl = O.Spec(**r.descriptor())
         y2 = c2[5].cpu().numpy() + c2[6].cpu().numpy()
         assert np.array_equal(y2, orl.plain_eval(x[:999])[0][:, 0])
 

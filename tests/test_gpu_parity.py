@@ -24,7 +24,7 @@ def ctx():
 
 
 def ospec(sp):
-    return O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
+    return O.Spec(**sp.descriptor())
 
 
 def gpu_gate(ctx, sp, x, call_id=0):

@@ -83,7 +83,7 @@ def test_alone_equals_mixed_and_plain(ctx):
             F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
             assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)
             sp = cs.spec
-            o = O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits, sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
+            o = O.Spec(**sp.descriptor())
             yp, zp = o.plain_eval(x.cpu().numpy())
             assert np.array_equal(y0.cpu().numpy() + y1.cpu().numpy(), yp[:, 0])
             assert np.array_equal(z0.cpu().numpy() ^ z1.cpu().numpy(), zp)

@@ -13,8 +13,7 @@ M64 = (1 << 64) - 1
 
 
 def ospec(sp):
-    return O.Spec(sp.k, sp.m, sp.degree, sp.n_out, sp.alpha, sp.coeff, sp.partition_bits,
-                  sp.pred_tuples(), sp.xhat_basis, sp.piecewise_tuples())
+    return O.Spec(**sp.descriptor())
 
 
 def python_plain(sp, xs):
@@ -34,6 +33,9 @@ def python_plain(sp, xs):
             for j in range(sp.degree, -1, -1):
                 acc = (acc * x + c[j]) & M64
             row.append(acc)
+        if sp.trunc_shift:                  # Python's >> floors negative values
+            v = xk - (1 << sp.k) if (sp.trunc_signed and xk >> (sp.k - 1)) else xk
+            row[0] = (row[0] + (v >> sp.trunc_shift)) & M64
         ys.append(row)
         z = 0
         for t, (f, c, g, neg) in enumerate(bits):
@@ -63,6 +65,8 @@ def test_plain_evaluator_matches_independent_python():
         d = int(rng.integers(0, 4))
         r = 1 if d > 1 else int(rng.integers(1, 3))
         sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 4)))
+        if trial % 3 == 0:
+            sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), bool(trial % 2)
         x = rng.integers(0, 2 ** 64, size=300, dtype=np.uint64)
         y, z = ospec(sp).plain_eval(x)
         yp, zp = python_plain(sp, x)
@@ -245,3 +249,63 @@ def test_piecewise_relu_sign_select():
     want = np.where(xs >= 0, ((xs % 16) < 8).astype(np.uint32), 1)
     assert np.array_equal((z >> 1) & 1, want)
     assert np.array_equal(z & 1, (xs < 0).astype(np.uint32))
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 7])
+def test_truncation_every_shift_every_mask_every_input(k):
+    """Shift gate (Def. "specification-compatible scalar gate" with the
+    low-bit rewrite of App. "low-bit predicate rewrite"): for every shift s,
+    both the logical and the arithmetic form, all x and all masks r, the
+    reconstruction is the shift of the k-bit view; one byte per element per
+    party opens the two daBit-masked bits."""
+    N = 2 ** k
+    rng = np.random.default_rng(300 + k)
+    hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+    hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+    xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
+    rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
+    for s_ in range(1, k):
+        for signed in (False, True):
+            sp = S.trunc(k, s_, signed)
+            o, res, y, z = run_gate(sp, xs, r_override=rs)
+            yp, _ = python_plain(sp, xs)
+            assert (y == yp).all(), (s_, signed)
+            assert (res["comm"] == xs.size * (8 + 1)).all()
+
+
+def test_truncation_textbook_shifts():
+    """In-range values: the signed form is numpy's arithmetic right shift of
+    int64, the logical form numpy's right shift of the unsigned k-bit value."""
+    rng = np.random.default_rng(5)
+    k, s_ = 32, 12
+    v = rng.integers(-(2 ** 31), 2 ** 31, size=4000, dtype=np.int64)
+    _, _, y, _ = run_gate(S.trunc(k, s_, True), v.view(np.uint64))
+    assert np.array_equal(y[:, 0].view(np.int64), np.right_shift(v, s_))
+    u = rng.integers(0, 2 ** 32, size=4000, dtype=np.uint64) + (rng.integers(0, 2 ** 31, size=4000, dtype=np.uint64) << np.uint64(33))
+    _, _, y, _ = run_gate(S.trunc(k, s_, False), u)
+    assert np.array_equal(y[:, 0], (u & np.uint64(2 ** 32 - 1)) >> np.uint64(s_))
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_truncation_with_polynomial_and_boolean_outputs(k):
+    """A shift added to a piecewise polynomial's first output, beside
+    predicates, piecewise outputs and the x^-basis variant; all x, all r."""
+    N = 2 ** k
+    rng = np.random.default_rng(400 + k)
+    xs = np.tile(np.arange(N, dtype=np.uint64), N) + (rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k))
+    rs = np.repeat(np.arange(N, dtype=np.uint64), N) + (rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k))
+    for trial in range(6):
+        m = int(rng.integers(1, min(N, 16) + 1))
+        d = int(rng.integers(0, 3))
+        r = 1 if d > 1 else int(rng.integers(1, 3))
+        sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 3)))
+        if trial % 3 == 1:
+            sp = S.random_piecewise(rng, sp, 2)
+        sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), bool(trial % 2)
+        if trial % 3 == 2:
+            sp = sp.variant(True)
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all(), trial
+        mults = 0 if sp.xhat_basis else d * r
+        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * len(sp.piecewise) + 1)).all()
