@@ -109,6 +109,18 @@ typedef struct {
      * ffss_eval_pred returns the other outputs. */
     uint32_t n_piecewise;
     const ffss_pred_desc *piecewise;
+    /* Shift gate (truncation / ARS as a specification-compatible gate,
+     * Def. "specification-compatible scalar gate"; low-bit rewrite lemma,
+     * App. "low-bit predicate rewrite"): if trunc_shift = s > 0 (s < k),
+     * arithmetic output 0 gains T_s(x): (x mod 2^k) >> s when trunc_signed = 0;
+     * floor(v / 2^s) sign-extended to 64 bits, v the k-bit two's-complement
+     * value of x mod 2^k, when trunc_signed = 1.  A pure shift gate is m = 1,
+     * degree 0, n_out 1 with a zero coefficient.  Costs the r-atoms of views
+     * (s, 0) and (k, 2^{k-1} or 0) in the packed comparison and one byte per
+     * element per party (two daBit-masked bits, opened with the other
+     * post-comparison messages). */
+    uint32_t trunc_shift;
+    uint32_t trunc_signed;
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -122,12 +134,14 @@ typedef struct {
     uint32_t n_bool;         /* Boolean outputs, piecewise ones included (bits of the output word) */
     uint32_t n_views;        /* distinct (f, c) views among the queries */
     uint64_t key_bytes_per_elem;   /* one party, this library's layout */
-    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults + 8 * n_piecewise */
+    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults + 8 * n_piecewise
+                                      (+ 1 with a shift) */
     uint64_t aes_per_elem;         /* one party, online AES-128 blocks */
     uint64_t keygen_aes_per_elem;  /* dealer AES-128 blocks per element (both parties' keys,
                                       PRG draws included): 4 k_t per comparison key,
                                       k (4 + 4V) + 2V per lookup key */
     uint32_t n_piecewise;          /* piecewise Boolean outputs (the last n_piecewise of n_bool) */
+    uint32_t trunc_shift;          /* the shift s, 0 = none */
 } ffss_shape;
 
 /* ---- context ------------------------------------------------------------ */

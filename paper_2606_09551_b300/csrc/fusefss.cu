@@ -275,18 +275,31 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
       }
   }
   // query list: views in order of first appearance; per view the r-atom, then
-  // one theta atom per predicate of that view
+  // one theta atom per predicate of that view.  A shift gate appends the
+  // views (s, 0) and (k, c) when no predicate uses them.
   std::vector<std::pair<uint32_t, uint64_t>> views;
-  for (uint32_t j = 0; j < S.n_prim; ++j) {
+  auto add_view = [&](uint32_t f, uint64_t c) {
     bool seen = false;
-    for (auto &v : views) seen |= (v.first == S.prim_f[j] && v.second == S.prim_c[j]);
-    if (!seen) views.push_back({S.prim_f[j], S.prim_c[j]});
+    for (auto &v : views) seen |= (v.first == f && v.second == c);
+    if (!seen) views.push_back({f, c});
+  };
+  for (uint32_t j = 0; j < S.n_prim; ++j) add_view(S.prim_f[j], S.prim_c[j]);
+  if (d->trunc_shift) {
+    if (d->trunc_shift >= d->k) return fail(FFSS_ERR_INVALID, "trunc_shift=%u must be < k", d->trunc_shift);
+    if (d->trunc_signed > 1) return fail(FFSS_ERR_INVALID, "trunc_signed must be 0 or 1");
+    S.trunc_s = d->trunc_shift;
+    S.trunc_signed = d->trunc_signed;
+    S.trunc_c = d->trunc_signed ? (uint64_t(1) << (d->k - 1)) : 0;
+    add_view(S.trunc_s, 0);
+    add_view(d->k, S.trunc_c);
   }
   S.n_views = uint32_t(views.size());
   uint32_t T = 0;
   for (auto &v : views) {
     if (T >= FFSS_MAX_T) return fail(FFSS_ERR_UNSUPPORTED, "more than %d queries", FFSS_MAX_T);
     const uint32_t qr = T;
+    if (S.trunc_s && v.first == S.trunc_s && v.second == 0) S.trunc_q_lo = qr;
+    if (S.trunc_s && v.first == d->k && v.second == S.trunc_c) S.trunc_q_hi = qr;
     S.q_f[T] = v.first; S.q_c[T] = v.second; S.q_prim[T] = -1; ++T;
     for (uint32_t j = 0; j < S.n_prim; ++j) {
       if (S.prim_f[j] != v.first || S.prim_c[j] != v.second) continue;
@@ -321,7 +334,8 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   sh.n_piecewise = S.n_pw;
   sh.n_views = S.n_views;
   sh.key_bytes_per_elem = key_bytes_per_elem(S);
-  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults + 8ull * S.n_pw;
+  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults + 8ull * S.n_pw + (S.trunc_s ? 1 : 0);
+  sh.trunc_shift = S.trunc_s;
   sh.aes_per_elem = aes_per_elem(S);
   sh.keygen_aes_per_elem = keygen_aes_per_elem(S);
   *out = sp;

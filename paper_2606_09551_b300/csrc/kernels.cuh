@@ -217,6 +217,34 @@ __device__ __forceinline__ uint32_t pw_finish(uint32_t b, const DevSpec &S, cons
   return z;
 }
 
+// Shift gate post-processing (truncation / arithmetic right shift by s of the
+// k-bit view; Def. "specification-compatible scalar gate", low-bit rewrite
+// lemma).  With u = view_{k,c}(x^), r_k = r mod 2^k, the integer identity
+//   ((x + c) mod 2^k) >> s = (u >> s) - (r_k >> s) - 1[u mod 2^s < r_k mod 2^s] + 2^{k-s} 1[u < r_k]
+// takes its two bits from the packed comparison (the r-atoms of views (s, 0)
+// and (k, c)); a daBit turns each XOR-shared bit into additive shares:
+// open o = bit ^ rho, then [bit] = [party 0] o + (1 - 2 o) [rho].
+// First half: this party's masked opening of (borrow, wrap), bits 0 and 1.
+__device__ __forceinline__ uint32_t trunc_send(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e,
+                                               uint32_t atoms) {
+  const uint32_t rho = reinterpret_cast<const uint32_t *>(kb + L.off_trunc_rho)[e];
+  return (((atoms >> S.trunc_q_lo) & 1u) | (((atoms >> S.trunc_q_hi) & 1u) << 1)) ^ rho;
+}
+
+// Second half: this party's additive share of T_s(x) from the public
+// delta = o_0 ^ o_1; the arithmetic form subtracts c >> s = 2^{k-1-s}.
+__device__ __forceinline__ uint64_t trunc_finish(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
+                                                 uint64_t e, uint64_t xhat, uint32_t delta) {
+  const uint64_t *tt = reinterpret_cast<const uint64_t *>(kb + L.off_trunc);
+  const uint64_t d_lo = delta & 1u, d_hi = (delta >> 1) & 1u;
+  const uint64_t a_lo = tt[L.n + e], a_hi = tt[2 * L.n + e];
+  const uint64_t borrow = (b == 0 ? d_lo : 0ull) + (d_lo ? 0ull - a_lo : a_lo);
+  const uint64_t wrap = (b == 0 ? d_hi : 0ull) + (d_hi ? 0ull - a_hi : a_hi);
+  uint64_t sh = 0ull - tt[e] - borrow + (wrap << (S.k - S.trunc_s));
+  if (b == 0) sh += (view(xhat, S.k, S.trunc_c) >> S.trunc_s) - (S.trunc_c >> S.trunc_s);
+  return sh;
+}
+
 // Lookup output: share of v_{M-1} plus (-1)^b times the summed DCF terms,
 // LUT(u) = v_{M-1} + sum_{j=1}^{M-1} 1[u < B_j] (v_{j-1} - v_j).
 template <int P>
@@ -255,19 +283,22 @@ struct GateArgsS {
 };
 
 
+constexpr uint32_t kPwSlots = kMaxPW + 1;
+
 // Shared-memory carve-up of a gate CTA (after the T-tables).
 struct GateSmem {
   DevSpec *spec;
   ulonglong2 *box;        // [party][le][R] openings (the first word also carries x_b + r_b)
   uint64_t *red_acc;      // [party][slot][le][P]
   uint32_t *red_atoms;    // [party][slot][le]
-  uint64_t *pwbox;        // [party][le][kMaxPW] piecewise-output openings (e | f << 32)
+  uint64_t *pwbox;        // [party][le][kPwSlots] piecewise-output openings (e | f << 32), then
+                          // the shift gate's masked bits
 };
 
 __host__ __device__ constexpr size_t gate_smem_bytes() {
   // tables + spec + outbox (R <= 4) + slot partials (P <= 4) + piecewise openings
   return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 2ull * 256 * 4 * 16 +
-         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4 + 2ull * 256 * 8 * kMaxPW;
+         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4 + 2ull * 256 * 8 * kPwSlots;
 }
 
 __device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
@@ -361,13 +392,22 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
     xs = b == 0 ? xhat - r_b : 0ull - r_b;
 #pragma unroll
     for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
-    if (S.n_pw) pw_send(b, S, L, kb, e, valid, atoms, G.pwbox + (b * E + le) * kMaxPW, sent);
+    if (S.n_pw) pw_send(b, S, L, kb, e, valid, atoms, G.pwbox + (b * E + le) * kPwSlots, sent);
+    if (S.trunc_s) {
+      G.pwbox[(b * E + le) * kPwSlots + kMaxPW] = valid ? trunc_send(S, L, kb, e, atoms) : 0u;
+      if (valid) sent += 1;
+    }
   }
-  // piecewise Boolean outputs: one exchange of the packed AND openings
-  // (uniform across the CTA: one spec per tile)
-  if (S.n_pw) {
+  // piecewise Boolean outputs and the shift gate's bits: one exchange after
+  // the packed comparison (uniform across the CTA: one spec per tile)
+  uint64_t tsh = 0;
+  if (S.n_pw || S.trunc_s) {
     __syncthreads();
-    if (lead && valid) z |= pw_finish(b, S, L, kb, e, G.pwbox + le * kMaxPW, G.pwbox + (E + le) * kMaxPW);
+    if (lead && valid) {
+      const uint64_t *m0 = G.pwbox + le * kPwSlots, *m1 = G.pwbox + (E + le) * kPwSlots;
+      if (S.n_pw) z |= pw_finish(b, S, L, kb, e, m0, m1);
+      if (S.trunc_s) tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
+    }
   }
   // x^-basis variant: the coefficients multiply the public x^, so Horner is
   // local to each party
@@ -411,6 +451,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
     __syncthreads();
   }
   if (lead && valid) {
+    y[0] += tsh;
 #pragma unroll
     for (int o = 0; o < R; ++o) (b ? A.y1 : A.y0)[e * R + o] = y[o];
     (b ? A.z1 : A.z0)[e] = z;
@@ -733,6 +774,25 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
         bt1[(uint64_t(j) * 3 + 1) * n + e] = bb ^ b0;
         bt0[(uint64_t(j) * 3 + 2) * n + e] = c0;
         bt1[(uint64_t(j) * 3 + 2) * n + e] = (a & bb) ^ c0;
+      }
+      // shift gate: shares of (r mod 2^k) >> s and two daBits (a random bit
+      // held both XOR- and additively shared) for the borrow / wrap B2A
+      if (S.trunc_s) {
+        const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * S.n_pw;
+        const uint64_t t = (r_in & ((uint64_t(1) << S.k) - 1)) >> S.trunc_s;
+        const uint64_t t0 = lo64(prg(di));
+        const uint32_t rho = prg(di + 1).x & 3u, rho0 = prg(di + 2).x & 3u;
+        const uint64_t a_lo = lo64(prg(di + 3)), a_hi = lo64(prg(di + 4));
+        uint64_t *tt0 = reinterpret_cast<uint64_t *>(A.k0 + L.off_trunc);
+        uint64_t *tt1 = reinterpret_cast<uint64_t *>(A.k1 + L.off_trunc);
+        tt0[e] = t0;
+        tt1[e] = t - t0;
+        tt0[n + e] = a_lo;
+        tt1[n + e] = uint64_t(rho & 1u) - a_lo;
+        tt0[2 * n + e] = a_hi;
+        tt1[2 * n + e] = uint64_t(rho >> 1) - a_hi;
+        reinterpret_cast<uint32_t *>(A.k0 + L.off_trunc_rho)[e] = rho0;
+        reinterpret_cast<uint32_t *>(A.k1 + L.off_trunc_rho)[e] = rho ^ rho0;
       }
     }
   }

@@ -22,7 +22,9 @@ constexpr int kMaxPW = 4;      // piecewise Boolean outputs
 // share of r_in, party-0 share of x, party-0 carry-share word, p party-0
 // shares of v_{M-1}, two root seeds per DCF key (queries, then lookup keys),
 // five draws per Beaver triple (a, b, a_0, b_0, c_0), then five per packed
-// Boolean AND triple of a piecewise output (a, b, a_0, b_0, c_0; m bits each).
+// Boolean AND triple of a piecewise output (a, b, a_0, b_0, c_0; m bits each),
+// then five for a shift gate (share of (r mod 2^k) >> s, the two daBit values,
+// their XOR share, their additive shares lo and hi).
 constexpr uint32_t kDrawRin = 0;
 constexpr uint32_t kDrawRsh = 1;
 constexpr uint32_t kDrawXsh = 2;
@@ -59,6 +61,12 @@ struct DevSpec {
   int32_t part_prim[kMaxM];           // [i], i = 1..m-1: predicate index of C_{alpha_i}
   int32_t pw_prim[kMaxPW][kMaxM];     // [j][i]: predicate of B_i^(j), or -1 (sentinel constant)
   uint32_t pw_fix[kMaxPW];            // [j]: bit i = sentinel value ^ negation, applied by party 0
+  // Shift gate (truncation / arithmetic right shift by trunc_s of the k-bit
+  // view, added to output 0; 0 = none).  The borrow and wrap bits are the
+  // r-atoms of views (trunc_s, 0) and (k, trunc_c), queries trunc_q_lo / _hi.
+  uint32_t trunc_s, trunc_signed;
+  uint32_t trunc_q_lo, trunc_q_hi;
+  uint64_t trunc_c;                   // 2^{k-1} for the arithmetic shift, else 0
 };
 
 // Byte offsets of one party's key material for n elements.  Every section is
@@ -70,12 +78,14 @@ struct DevSpec {
 //   v_{M-1} share    u64  [p][n]
 //   triples          u64  [n_mults][3][n]          (a, b, c)
 //   Boolean triples  u32  [n_pw][3][n]             (a, b, c), m packed bits each
+//   shift gate       u64  [3][n] ((r mod 2^k) >> s share, daBit additive shares lo, hi),
+//                    u32  [n] (daBit XOR shares, bits 0 and 1)
 //   query t          uint4 root[n], uint4 cw[k_t][n] (seed CW | t_L | t_R << 1),
 //                    u64 vcw[n] (bit i = V_CW of level i, bit k_t = final CW)
 //   lookup key j     uint4 root[n], uint4 cw[k][n], u64 vcw[k+1][p][n] (level k = final CW)
 struct KeyLayout {
   uint64_t n;
-  uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip;
+  uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip, off_trunc, off_trunc_rho;
   uint64_t off_q[kMaxT];
   uint64_t off_l[kMaxM];
   uint64_t total;
@@ -92,6 +102,9 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_vlast = o; o = align256(o + 8ull * s.p * n);
   L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
   L.off_btrip = o; o = align256(o + 12ull * s.n_pw * n);
+  const uint64_t tr = s.trunc_s ? 1 : 0;
+  L.off_trunc = o; o = align256(o + 24ull * tr * n);
+  L.off_trunc_rho = o; o = align256(o + 4ull * tr * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
     o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
@@ -106,7 +119,7 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
-  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_pw;
+  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_pw + (s.trunc_s ? 28 : 0);
   for (uint32_t t = 0; t < s.T; ++t) b += 16ull * (s.q_f[t] + 1) + 8;
   if (s.M > 1) b += (s.M - 1) * (16ull * (s.k + 1) + 8ull * (s.k + 1) * s.p);
   return b;
@@ -125,7 +138,8 @@ inline uint64_t aes_per_elem(const DevSpec &s) {
 // children's payload blocks of both parties (4V); the final lookup
 // correction needs both parties' leaf payloads (2V).
 inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
-  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_pw;
+  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_pw +
+               (s.trunc_s ? 5 : 0);
   for (uint32_t t = 0; t < s.T; ++t) a += 4ull * s.q_f[t];
   if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (4 + 4 * s.V) + 2 * s.V);
   return a;

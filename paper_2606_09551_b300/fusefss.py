@@ -41,7 +41,8 @@ class SpecDesc(C.Structure):
                 ("n_out", C.c_uint32), ("partition_bits", C.c_uint32),
                 ("alpha", C.POINTER(C.c_uint64)), ("coeff", C.POINTER(C.c_uint64)),
                 ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc)), ("xhat_basis", C.c_uint32),
-                ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc))]
+                ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc)),
+                ("trunc_shift", C.c_uint32), ("trunc_signed", C.c_uint32)]
 
 
 class Shape(C.Structure):
@@ -50,7 +51,7 @@ class Shape(C.Structure):
                 ("n_bool", C.c_uint32), ("n_views", C.c_uint32),
                 ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
                 ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64),
-                ("n_piecewise", C.c_uint32)]
+                ("n_piecewise", C.c_uint32), ("trunc_shift", C.c_uint32)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -198,7 +199,8 @@ class CompiledSpec:
         self._keep = (alpha, coeff, preds, pw)
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
-                     len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw)
+                     len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw,
+                     spec.trunc_shift, int(spec.trunc_signed))
         h = vp()
         _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
         self.h = h

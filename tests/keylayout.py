@@ -23,6 +23,9 @@ def offsets(ospec: O.Spec, n: int):
     off["vlast"] = o; o = _a256(o + 8 * ospec.p * n)
     off["trip"] = o; o = _a256(o + 24 * ospec.n_mults * n)
     off["btrip"] = o; o = _a256(o + 12 * ospec.n_pw * n)
+    tr = 1 if ospec.trunc_s else 0
+    off["trunc"] = o; o = _a256(o + 24 * tr * n)
+    off["trunc_rho"] = o; o = _a256(o + 4 * tr * n)
     off["q"] = []
     for (f, c, pr) in q:
         off["q"].append(o)
@@ -63,6 +66,10 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
     bt = _u32(buf, off["btrip"], 3 * ospec.n_pw * n)
     for name, w in (("ba", 0), ("bb", 1), ("bc", 2)):
         out[name] = np.array([bt[(j * 3 + w) * n + e] for j in range(ospec.n_pw)], np.uint32)
+    if ospec.trunc_s:
+        tt = _u64(buf, off["trunc"], 3 * n)
+        out.update(tr_t=int(tt[e]), tr_rho=int(_u32(buf, off["trunc_rho"], n)[e]),
+                   tr_rho_a=np.array([tt[n + e], tt[2 * n + e]], np.uint64))
     qk = []
     for t, (f, c, pr) in enumerate(ospec.queries()):
         blk = _blocks(buf, off["q"][t], (f + 1) * n)
@@ -89,6 +96,9 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
     base = keys.fields(ospec, i)
     out = dict(r_share=base["r_share"], carry=base["carry"], vlast=base["vlast"],
                ta=base["ta"], tb=base["tb"], tc=base["tc"], ba=base["ba"], bb=base["bb"], bc=base["bc"])
+    for key in ("tr_t", "tr_rho", "tr_rho_a"):
+        if key in base:
+            out[key] = base[key]
     qk = []
     for t, (f, c, pr) in enumerate(ospec.queries()):
         fl = keys.qkey(i, t).fields(f, 0)
@@ -110,6 +120,10 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
 
 def fields_equal(a, b) -> bool:
     if a["r_share"] != b["r_share"] or a["carry"] != b["carry"]:
+        return False
+    if a.get("tr_t") != b.get("tr_t") or a.get("tr_rho") != b.get("tr_rho"):
+        return False
+    if ("tr_rho_a" in a) != ("tr_rho_a" in b) or ("tr_rho_a" in a and not np.array_equal(a["tr_rho_a"], b["tr_rho_a"])):
         return False
     for key in ("vlast", "ta", "tb", "tc", "ba", "bb", "bc"):
         if not np.array_equal(a[key], b[key]):
@@ -149,6 +163,10 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
         for j in range(ospec.n_pw):
             for w, name in enumerate(("ba", "bb", "bc")):
                 bt[(j * 3 + w) * n + e] = fl[name][j]
+        if ospec.trunc_s:
+            tt = _u64(buf, off["trunc"], 3 * n)
+            tt[e], tt[n + e], tt[2 * n + e] = fl["tr_t"], fl["tr_rho_a"][0], fl["tr_rho_a"][1]
+            _u32(buf, off["trunc_rho"], n)[e] = fl["tr_rho"]
         for t, (f, c, pr) in enumerate(qs):
             blk = _blocks(buf, off["q"][t], (f + 1) * n)
             blk[e] = fl["q"][t]["root"]

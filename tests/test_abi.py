@@ -52,9 +52,11 @@ def _shape_vs_oracle(sp, may_reject=False):
     sh = cs.shape
     assert (sh.T, sh.M, sh.p, sh.n_mults, sh.n_bool) == (o.T, o.M, o.p, o.n_mults, o.n_bool)
     assert sh.n_piecewise == o.n_pw == len(sp.piecewise)
-    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_pw
+    tr = 1 if sp.trunc_shift else 0
+    assert sh.trunc_shift == sp.trunc_shift
+    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_pw + tr
     qs = o.queries()
-    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + sum(16 * (f + 1) + 8 for f, _, _ in qs)
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + 28 * tr + sum(16 * (f + 1) + 8 for f, _, _ in qs)
     if o.M > 1:
         kb += (o.M - 1) * (16 * (o.k + 1) + 8 * (o.k + 1) * o.p)
     assert sh.key_bytes_per_elem == kb
@@ -77,6 +79,9 @@ def test_workload_spec_shapes():
     # x^-basis variant: no Beaver multiplications, no triples in the keys, 8 B online
     sh = _shape_vs_oracle(S.nexp16().variant(True))
     assert sh.n_mults == 0 and sh.comm_bytes_per_elem == 8
+    # shift gate: two bit-DCF queries of s and k levels, 9 bytes online
+    sh = _shape_vs_oracle(S.trunc(32, 12, True))
+    assert (sh.T, sh.M, sh.aes_per_elem, sh.comm_bytes_per_elem) == (2, 1, 12 + 32, 9)
 
 
 def test_random_spec_shapes():
@@ -90,11 +95,13 @@ def test_random_spec_shapes():
                            n_extra=int(rng.integers(0, 6)))
         if trial % 2:
             sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
+        if trial % 5 < 2:
+            sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), bool(trial % 5)
         _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)), may_reject=True)
 
 
 @pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0",
-                                 "pw_count", "pw_f", "pw_gamma"])
+                                 "pw_count", "pw_f", "pw_gamma", "trunc_s", "trunc_signed"])
 def test_invalid_specs_rejected(bad):
     sp = S.random_spec(np.random.default_rng(1), 8, 4, 1)
     if bad == "alpha_order":
@@ -117,5 +124,9 @@ def test_invalid_specs_rejected(bad):
         sp.piecewise = [[S.PredDesc(9, 0, 1, 0)] * sp.m]
     elif bad == "pw_gamma":
         sp.piecewise = [[S.PredDesc(3, 0, 9, 0)] * sp.m]
+    elif bad == "trunc_s":
+        sp.trunc_shift = sp.k
+    elif bad == "trunc_signed":
+        sp.trunc_shift, sp.trunc_signed = 3, 2
     with pytest.raises(F.FfssError):
         F.CompiledSpec(sp)

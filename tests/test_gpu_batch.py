@@ -31,8 +31,9 @@ def _mixed_calls():
              S.random_spec(rng, 14, 6, 0, 3, n_extra=0, name="r3d0"),
              S.recip16(), S.gelu8().variant(True),
              S.random_piecewise(rng, S.gelu4(), 3),
-             S.random_piecewise(rng, S.random_spec(rng, 16, 7, 1, 2, n_extra=1, name="r2d1b"), 2)]
-    sizes = [5000, 1777, 1, 300, 64, 999, 33, 257, 1536, 2222, 1111, 700]
+             S.random_piecewise(rng, S.random_spec(rng, 16, 7, 1, 2, n_extra=1, name="r2d1b"), 2),
+             S.trunc(32, 12, True), S.trunc(20, 5, False)]
+    sizes = [5000, 1777, 1, 300, 64, 999, 33, 257, 1536, 2222, 1111, 700, 3333, 129]
     return [(sp, I.uniform_x(n, sp.k, 100 + i), 7 + i) for i, (sp, n) in enumerate(zip(specs, sizes))]
 
 

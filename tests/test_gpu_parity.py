@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on the
 same seeded inputs.  All ring and bit outputs must be bit-exact (integer
 work); reconstructions must equal the plaintext spec evaluation."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -75,11 +77,18 @@ def _specs():
     pw = [S.random_piecewise(rng, S.gelu4(), 2), S.random_piecewise(rng, out[3], 3),
           S.random_piecewise(rng, out[4], 4), S.random_piecewise(rng, out[8], 1).variant(True),
           S.random_piecewise(rng, out[6], 2)]
-    return out + pw
+    # shift gates (truncation / ARS), alone and added to a polynomial output
+    tr = [S.trunc(32, 12, True), S.trunc(24, 16, False), S.trunc(16, 1, True),
+          dataclasses.replace(S.gelu4(), name="gelu4_ars4", trunc_shift=4, trunc_signed=True),
+          dataclasses.replace(pw[1], name=pw[1].name + "_trunc7", trunc_shift=7, trunc_signed=False),
+          dataclasses.replace(out[8], name=out[8].name + "_xhat_ars3", trunc_shift=3, trunc_signed=True,
+                              xhat_basis=True)]
+    return out + pw + tr
 
 
 SPECS = _specs()
 PW_SPECS = [s for s in SPECS if s.piecewise]
+TR_SPECS = [s for s in SPECS if s.trunc_shift]
 
 
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
@@ -102,14 +111,14 @@ def test_keygen_and_gate_bit_exact(ctx, sp):
     yp, zp = osp.plain_eval(x)
     assert np.array_equal(g["y"], yp) and np.array_equal(g["z"], zp)
     mults = 0 if sp.xhat_basis else sp.degree * sp.n_out
-    assert list(g["comm"]) == [n * (8 + 16 * mults + 8 * len(sp.piecewise))] * 2
+    assert list(g["comm"]) == [n * (8 + 16 * mults + 8 * len(sp.piecewise) + (1 if sp.trunc_shift else 0))] * 2
 
 
 def test_gpu_eval_of_oracle_keys(ctx):
     """Keys written by the oracle dealer, packed into the library's layout,
     evaluate on the GPU to the oracle's shares (eval checked apart from keygen)."""
     import torch
-    for sp in (S.gelu4(), SPECS[4], PW_SPECS[1]):
+    for sp in (S.gelu4(), SPECS[4], PW_SPECS[1], TR_SPECS[0], TR_SPECS[4]):
         n = 300
         x = I.uniform_x(n, sp.k, 9)
         o = oracle_gate(sp, x, call_id=3)
@@ -169,6 +178,8 @@ def test_every_input_small_k(ctx, k):
         sp = S.random_spec(rng, k, m, d, 1, partition_bits=True, n_extra=int(rng.integers(0, 4)))
         if trial % 2:
             sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
+        if trial >= 2:
+            sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), trial == 3
         x = np.tile(np.arange(N, dtype=np.uint64), 64) + (rng.integers(0, 2 ** 50, N * 64, dtype=np.uint64) << np.uint64(k))
         g = gpu_gate(ctx, sp, x, call_id=trial)
         yp, zp = ospec(sp).plain_eval(x)
