@@ -37,8 +37,24 @@ sys.path.insert(0, ROOT)
 ALU_OPS_PER_AES = 240
 LDS_PER_AES = 160
 SMS = 148
-SM_MAX_MHZ = 2032.0
-HBM_GBS = 6491.5        # measured copy bandwidth of the B300s
+
+
+def _measured_peaks():
+    """The measured peaks of the B300s (MEASURED_PEAKS.json at
+    the repository root), else the recorded fallback figures."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2032.0)), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, 2032.0, "fallback"
+
+
+HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
+# gate_kernel DRAM bytes (read + write) per element by spec, from ncu
+# captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
+# retaken whenever the kernel changes
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (3.389263e9 + 5.116160e6) / 65536}
 
 
 def parse():
@@ -47,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small"], default="bert_layer")
+    ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small", "bert_rescale"], default="bert_layer")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-served", action="store_true")
@@ -57,6 +73,7 @@ def parse():
     ap.add_argument("--gpt2-layers", type=int, default=1, help="layers per request in the 32-request batch")
     ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
     ap.add_argument("--no-xhat", action="store_true", help="skip the x^-basis variant run")
+    ap.add_argument("--no-rescale", action="store_true", help="skip the layer-rescale (ARS) run")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
@@ -70,6 +87,13 @@ def workload(name):
         c.x = c.x[:65536]
         return [c], {"workload": "nexp16_65536", "spec": "nExp-16 k=24 f=12 d=3", "elements": 65536,
                      "form": "plain"}
+    if name == "bert_rescale":
+        # the shift gates of one BERT-base layer alone (each matrix product's
+        # output shifted right by 12 on a 32-bit signed view)
+        calls = I.bert_layer_rescales()
+        return calls, {"workload": "bert_base_layer_rescales", "spec": "ARS k=32 s=12",
+                       "ops": {c.name: c.n for c in calls}, "elements": sum(c.n for c in calls),
+                       "form": "plain per-product launches"}
     if name == "gelu4":
         return I.single_gelu4(), {"workload": "gelu4_single_op", "spec": "GeLU-4 k=16 f=12 d=2",
                                   "elements": 65536, "form": "plain"}
@@ -89,7 +113,7 @@ def workload(name):
 class ClockSampler:
     """Samples the SM clock and the clock-event reasons of one GPU every
     10 ms while the timed region runs (NVML reads only; nothing is set).
-    Falls back to `nvidia-smi -lms 200` when NVML cannot be loaded."""
+    Falls back to `nvidia-smi -lms 200` when NVML cannot be used."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -103,36 +127,55 @@ class ClockSampler:
         self.nvml_error = None
 
     def _nvml_handle(self):
-        import pynvml
+        """NVML through the driver's libnvidia-ml (read-only queries); the
+        device is matched by PCI bus id, which survives device masking."""
+        import ctypes
         import torch
-        pynvml.nvmlInit()
+        L = ctypes.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        rc = -1
         try:
             pr = torch.cuda.get_device_properties(self.gpu)
             bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
-            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
-        except Exception:
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+            rc = L.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h))
+        except AttributeError:
+            pass
+        if rc != 0 and L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle for GPU %d" % self.gpu)
+        return L, h
 
-    def _loop(self, nv, h, first):
-        bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
-                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+    def _loop(self, L, h, first):
+        import ctypes
+        NVML_CLOCK_SM = 1
+        # clock-event reason bits of the NVML API
+        bits = (0x8, 0x40, 0x20, 0x4)   # hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+        reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx, sm, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        L.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx))
         while not self.stop.is_set():
-            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-            rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-            self.rows.append((float(sm), float(mx), [n for n, b in zip(self.NAMES, bits) if rs & b]))
+            if L.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(sm)) != 0 or \
+                    reasons_fn(h, ctypes.byref(rs)) != 0:
+                return
+            self.rows.append((float(sm.value), float(mx.value),
+                              [n for n, b in zip(self.NAMES, bits) if rs.value & b]))
             first.set()
             self.stop.wait(0.010)
 
     def __enter__(self):
         import threading
         try:
-            nv, h = self._nvml_handle()
+            lib, h = self._nvml_handle()
             self.stop, first = threading.Event(), threading.Event()
-            self.thread = threading.Thread(target=self._loop, args=(nv, h, first), daemon=True)
+            self.thread = threading.Thread(target=self._loop, args=(lib, h, first), daemon=True)
             self.thread.start()
-            first.wait(2.0)
-            return self
+            if first.wait(2.0):
+                return self
+            self.stop.set()
+            self.thread.join(2.0)
+            raise RuntimeError("no NVML sample within 2 s")
         except Exception as ex:
             self.nvml_error = "%s: %s" % (type(ex).__name__, ex)
             self.thread = None
@@ -452,6 +495,10 @@ def run_ours(args, rank, world, local_rank):
         del vsets
         torch.cuda.empty_cache()
 
+    rescale = None
+    if not args.no_rescale:
+        rescale = run_rescales(ctx, args, dev, stream, world)
+
     served = large = gpt2 = None
     if not args.no_served:
         served = run_served(ctx, args, dev)
@@ -491,6 +538,16 @@ def run_ours(args, rank, world, local_rank):
     roof["peak_basis"] = ("derived: 148 SMs x 2032 MHz / max(%d ALU ops / 64 lanes, %d shared lookups / 32 banks) "
                           "per block; ops per block measured by ncu on the AES micro-kernel" % (ALU_OPS_PER_AES, LDS_PER_AES))
     roof["hbm_frac_of_measured"] = roof["hbm_gbs_achieved"] / HBM_GBS
+    roof["hbm_peak_gbs"] = HBM_GBS
+    roof["hbm_peak_basis"] = PEAKS_BASIS
+    # DRAM traffic of this kernel per element, from an ncu capture of a
+    # smaller launch of the same spec, scaled by elements (traffic grows in
+    # proportion: one-time keys are read once, outputs written once)
+    per_elem = GATE_DRAM_BYTES_PER_ELEM.get(dom.spec.name)
+    if per_elem is not None:
+        roof["traffic"] = per_elem * dom.n
+        roof["traffic_basis"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of gate_kernel on %s, "
+                                 "65,536 elements, scaled to %d elements" % (dom.spec.name, dom.n))
 
     res = {
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
@@ -518,6 +575,7 @@ def run_ours(args, rank, world, local_rank):
         "large_layer": large,
         "gpt2_batch": gpt2,
         "xhat_variant": xhat,
+        "rescale": rescale,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)
@@ -563,6 +621,72 @@ def _stream_aes(pending_ops, nlay):
         for cs, x, *_ in ops:
             tot += x.numel() * nlay * (cs.shape.keygen_aes_per_elem + 2 * cs.shape.aes_per_elem)
     return tot
+
+
+def run_rescales(ctx, args, dev, stream, world):
+    """The shift gates of one BERT-base layer (every matrix product's output
+    shifted right by 12 on a 32-bit signed view): K steps of fresh keys dealt
+    before the timed region, one fused launch per product."""
+    import numpy as np
+    import torch
+
+    from paper_2606_09551_b300 import fusefss as F
+    from paper_2606_09551_b300 import inputs as I
+    calls = I.bert_layer_rescales()
+    cs = F.CompiledSpec(calls[0].spec, ctx)
+    total = sum(c.n for c in calls)
+    xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
+    outs = {}
+    for c in calls:
+        y0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
+        z0 = torch.empty(c.n, dtype=torch.uint32, device=dev)
+        outs[c.name] = (y0, torch.empty_like(y0), z0, torch.empty_like(z0))
+    sets = []
+    for s_ in range(args.steps + 1):
+        ks = {}
+        for c in calls:
+            x0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
+            x1 = torch.empty_like(x0)
+            k0, k1 = F.Keys(cs, c.n, 0), F.Keys(cs, c.n, 1)
+            F.keygen(ctx, cs, I.KEY_SEED, c.call_id + 16 * (600 + s_), c.n, k0, k1, xp[c.name], x0, x1)
+            ks[c.name] = (k0, k1, x0, x1)
+        sets.append(ks)
+    comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+
+    def step(ks, cm=None):
+        for c in calls:
+            F.eval_pair(ctx, cs, *ks[c.name], *outs[c.name], cm)
+
+    step(sets[-1])                            # warm-up
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in range(args.steps):
+        step(sets[s_], comm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    # the last step's reconstruction against numpy's arithmetic shift (in-range inputs)
+    ok = True
+    for c in calls:
+        y = (outs[c.name][0].cpu().numpy() + outs[c.name][1].cpu().numpy()).view(np.int64)
+        ok &= bool(np.array_equal(y, np.right_shift(c.x.view(np.int64), 12)))
+    sh = cs.shape
+    aes = 2 * sh.aes_per_elem * total
+    res = {"value": aggregate(total, ms, world), "unit": "elements/s", "ms_per_step": ms,
+           "elements": total, "spec": "ARS k=32 s=12 (signed)",
+           "ops": {c.name: c.n for c in calls},
+           "aes_per_elem_per_party": sh.aes_per_elem,
+           "aes_roofline_frac": aes / (ms * 1e-3) / _aes_roofline(),
+           "key_bytes_per_elem_per_party": sh.key_bytes_per_elem,
+           "comm_bytes_per_party_per_step": int(comm.cpu().tolist()[0]) // args.steps,
+           "reconstruction_equals_numpy_right_shift": ok,
+           "form": "plain per-product launches; keys dealt on the GPU before the timed region"}
+    del sets
+    torch.cuda.empty_cache()
+    return res
 
 
 def _aes_roofline():

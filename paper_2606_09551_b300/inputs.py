@@ -69,6 +69,26 @@ def bert_layer(seq: int = 128, hidden: int = 768, heads: int = 12, mlp: int = 30
     ]
 
 
+def bert_layer_rescales(seq: int = 128, hidden: int = 768, heads: int = 12, mlp: int = 3072,
+                        seed_tag: int = 3, call_base: int = 8, f: int = 12, k: int = 32) -> List[OpCall]:
+    """The fixed-point rescales of one BERT-style encoder layer at batch 1:
+    every matrix product of two f-bit operands carries 2f fractional bits and
+    is shifted right by f (arithmetic shift on the k-bit view): Q, K, V
+    projections (3 x seq x hidden), attention scores (heads x seq x seq),
+    probabilities times V (seq x hidden), output projection (seq x hidden),
+    MLP up (seq x mlp) and down (seq x hidden).  Values are products of two
+    N(0, 1) activations' scale, drawn as N(0, 2^2) at 2f fractional bits."""
+    rng = _rng(seed_tag)
+    sizes = [("qkv", 3 * seq * hidden), ("scores", heads * seq * seq), ("attn_v", seq * hidden),
+             ("out_proj", seq * hidden), ("mlp_up", seq * mlp), ("mlp_down", seq * hidden)]
+    spec = S.trunc(k, f, True, name=f"ars{k}_{f}")
+    out = []
+    for i, (name, n) in enumerate(sizes):
+        v = 2.0 * rng.standard_normal(n)
+        out.append(OpCall("rescale_" + name, spec, S.encode(v, 2 * f), call_base + i))
+    return out
+
+
 def uniform_x(n: int, k: int, seed_tag: int) -> np.ndarray:
     """Uniform 64-bit inputs (exercise every view and wrap case)."""
     rng = _rng(seed_tag)
