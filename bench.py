@@ -513,8 +513,8 @@ def run_ours(args, rank, world, local_rank):
     aes_launch = 2 * sh.aes_per_elem * dom.n
     key_bytes_launch = 2 * sh.key_bytes_per_elem * dom.n
     lop3_rate, _ = F.microbench(ctx, 0, 4096)
-    aes_rates = {f"variant{v}": F.microbench(ctx, v + 1, 2048)[0] for v in range(3)}
-    aes_rate = aes_rates["variant0"]
+    aes_rates = {name: F.microbench(ctx, v + 1, 2048)[0]
+                 for v, name in enumerate(("shift_mask", "permute_mad", "permute_mad_ptx", "permute_interleaved"))}
     dom_s = per_op_ms[dom.name] * 1e-3
     roof = {
         "bound": "alu", "kernel": f"gate_kernel ({dom.name}: {dom.spec.name}, {dom.n} elements)",

@@ -372,10 +372,11 @@ int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint3
 /* Micro-benchmarks behind the roofline figures (no counterpart in the paper,
  * which reports no roofline).  which = 0: 32-bit LOP3 issue rate, result in
  * operations/s (iters x 128 LOP3 per thread, 2 CTAs of 1024 threads per SM);
- * which = 1: AES-128 blocks/s of the shared-memory T-table code the FSS
- * kernels use (iters chained blocks per thread, one 512-thread CTA per SM);
- * which = 2, 3: the same with table addresses formed by byte permute plus
- * multiply-add (C, and PTX mad) instead of shift plus mask.
+ * which = 1..4: AES-128 blocks/s of shared-memory T-table code (iters
+ * chained blocks per thread, one 512-thread CTA per SM), table addresses by
+ * 1: shift plus mask; 2, 3: byte permute plus multiply-add (C, PTX mad);
+ * 4: one byte permute into two tables interleaved per 256-byte entry, the
+ * form the FSS kernels use.
  * Synchronizes the device; *ms (may be NULL) receives the kernel time. */
 int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms);
 

@@ -5,8 +5,12 @@
 // AES-128 (FIPS-197) is written as four 32-bit T-table lookups per output
 // column per round.  The tables live in shared memory as 4 tables x 256
 // entries x 32 copies (128 KB): lane l always reads copy l, which sits in bank
-// l, so a warp's 32 random lookups never conflict.  Lookup address of entry e
-// for lane l: table*32768 + e*128 + 4*l.
+// l, so a warp's 32 random lookups never conflict.  Layout used by the FSS
+// kernels: region r (64 KB) holds tables 2r and 2r+1 interleaved, entry e of
+// table 2r+h for lane l at byte r*65536 + e*256 + h*128 + 4*l, so a lookup
+// address (byte << 8) | (128h + 4l) comes out of one byte permute.  (The
+// AES micro-benchmark's variants 0-2 use the plain layout
+// table*32768 + e*128 + 4*l.)
 #pragma once
 #include <stdint.h>
 #include "layout.h"
@@ -56,8 +60,54 @@ __device__ __forceinline__ uint32_t ixv(uint32_t w, uint32_t l4, int j) {
   }
 }
 
+// Shared word idx of the interleaved layout: table 2*(idx >> 14) + bit 5 of
+// idx, entry bits 6..13; table t holds T0 rotated left by 8t bits.
+__device__ __forceinline__ uint32_t tab_word(const uint32_t *t0, uint32_t idx) {
+  const uint32_t e = (idx >> 6) & 255u, table = ((idx >> 14) << 1) | ((idx >> 5) & 1u);
+  const uint32_t v = t0[e];
+  return table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+}
+
+// Lookup of table T (interleaved layout) at byte j of w: the permute puts
+// byte j of w in bits 8..15 over the lane offset lb (128h + 4l < 256).
+template <int T>
+__device__ __forceinline__ uint32_t tperm(const Tab &tb, uint32_t w, int j, uint32_t la, uint32_t lb) {
+  const uint32_t a = __byte_perm(w, (T & 1) ? lb : la, 0x5504u | (uint32_t(j) << 4));
+  return *reinterpret_cast<const uint32_t *>(tb.base + (T >> 1) * 65536u + a);
+}
+
+// VAR 4: one byte permute per lookup (interleaved layout).
+template <class RK>
+__device__ __forceinline__ uint4 aes128p(uint4 in, const RK &rk, const Tab &tb) {
+  const uint32_t la = tb.lane4, lb = tb.lane4 | 128u;
+  uint32_t s0 = in.x ^ rk[0], s1 = in.y ^ rk[1], s2 = in.z ^ rk[2], s3 = in.w ^ rk[3];
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    uint32_t t0 = tperm<0>(tb, s0, 0, la, lb) ^ tperm<1>(tb, s1, 1, la, lb) ^ tperm<2>(tb, s2, 2, la, lb) ^
+                  tperm<3>(tb, s3, 3, la, lb) ^ rk[4 * r + 0];
+    uint32_t t1 = tperm<0>(tb, s1, 0, la, lb) ^ tperm<1>(tb, s2, 1, la, lb) ^ tperm<2>(tb, s3, 2, la, lb) ^
+                  tperm<3>(tb, s0, 3, la, lb) ^ rk[4 * r + 1];
+    uint32_t t2 = tperm<0>(tb, s2, 0, la, lb) ^ tperm<1>(tb, s3, 1, la, lb) ^ tperm<2>(tb, s0, 2, la, lb) ^
+                  tperm<3>(tb, s1, 3, la, lb) ^ rk[4 * r + 2];
+    uint32_t t3 = tperm<0>(tb, s3, 0, la, lb) ^ tperm<1>(tb, s0, 1, la, lb) ^ tperm<2>(tb, s1, 2, la, lb) ^
+                  tperm<3>(tb, s2, 3, la, lb) ^ rk[4 * r + 3];
+    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+  }
+  uint4 o;
+  o.x = ((tperm<2>(tb, s0, 0, la, lb) & 0xFFu) | (tperm<3>(tb, s1, 1, la, lb) & 0xFF00u) |
+         (tperm<0>(tb, s2, 2, la, lb) & 0xFF0000u) | (tperm<1>(tb, s3, 3, la, lb) & 0xFF000000u)) ^ rk[40];
+  o.y = ((tperm<2>(tb, s1, 0, la, lb) & 0xFFu) | (tperm<3>(tb, s2, 1, la, lb) & 0xFF00u) |
+         (tperm<0>(tb, s3, 2, la, lb) & 0xFF0000u) | (tperm<1>(tb, s0, 3, la, lb) & 0xFF000000u)) ^ rk[41];
+  o.z = ((tperm<2>(tb, s2, 0, la, lb) & 0xFFu) | (tperm<3>(tb, s3, 1, la, lb) & 0xFF00u) |
+         (tperm<0>(tb, s0, 2, la, lb) & 0xFF0000u) | (tperm<1>(tb, s1, 3, la, lb) & 0xFF000000u)) ^ rk[42];
+  o.w = ((tperm<2>(tb, s3, 0, la, lb) & 0xFFu) | (tperm<3>(tb, s0, 1, la, lb) & 0xFF00u) |
+         (tperm<0>(tb, s1, 2, la, lb) & 0xFF0000u) | (tperm<1>(tb, s2, 3, la, lb) & 0xFF000000u)) ^ rk[43];
+  return o;
+}
+
+// VAR 0-2: plain layout, addresses by shift + mask or permute + multiply-add.
 template <int VAR, class RK>
-__device__ __forceinline__ uint4 aes128v(uint4 in, const RK &rk, const Tab &tb) {
+__device__ __forceinline__ uint4 aes128t(uint4 in, const RK &rk, const Tab &tb) {
   const uint32_t l4 = tb.lane4;
   uint32_t s0 = in.x ^ rk[0], s1 = in.y ^ rk[1], s2 = in.z ^ rk[2], s3 = in.w ^ rk[3];
 #pragma unroll
@@ -82,6 +132,14 @@ __device__ __forceinline__ uint4 aes128v(uint4 in, const RK &rk, const Tab &tb) 
   o.w = ((tload(tb, 2, ixv<VAR>(s3, l4, 0)) & 0xFFu) | (tload(tb, 3, ixv<VAR>(s0, l4, 1)) & 0xFF00u) |
          (tload(tb, 0, ixv<VAR>(s1, l4, 2)) & 0xFF0000u) | (tload(tb, 1, ixv<VAR>(s2, l4, 3)) & 0xFF000000u)) ^ rk[43];
   return o;
+}
+template <int VAR, class RK>
+__device__ __forceinline__ uint4 aes128v(uint4 in, const RK &rk, const Tab &tb) {
+  if constexpr (VAR == 4) {
+    return aes128p(in, rk, tb);
+  } else {
+    return aes128t<VAR>(in, rk, tb);
+  }
 }
 #endif
 

@@ -1095,7 +1095,7 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
     mb_lop3_kernel<<<blocks, threads>>>(static_cast<uint32_t *>(out), iters);
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters * 16.0 * 8.0;
-  } else if (which >= 1 && which <= 3) {
+  } else if (which >= 1 && which <= 4) {
     const int blocks = ctx->sm_count, threads = 512;
     const size_t smem = kTabBytes;
     static std::once_flag once;
@@ -1103,9 +1103,11 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
       rc = set_smem(mb_aes_kernel<0>, smem);
       if (!rc) rc = set_smem(mb_aes_kernel<1>, smem);
       if (!rc) rc = set_smem(mb_aes_kernel<2>, smem);
+      if (!rc) rc = set_smem(mb_aes_kernel<4>, smem);
     });
     if (rc) return rc;
-    auto kern = which == 1 ? mb_aes_kernel<0> : which == 2 ? mb_aes_kernel<1> : mb_aes_kernel<2>;
+    auto kern = which == 1 ? mb_aes_kernel<0> : which == 2 ? mb_aes_kernel<1>
+              : which == 3 ? mb_aes_kernel<2> : mb_aes_kernel<4>;
     CUDA_TRY(cudaMalloc(&out, sizeof(uint4) * blocks * threads));
     kern<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), 4);
     CUDA_TRY(cudaEventRecord(a));
@@ -1113,7 +1115,7 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters;
   } else {
-    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1..3 (AES variants)");
+    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1..4 (AES variants)");
   }
   cudaError_t e = cudaEventSynchronize(b);
   float t = 0;

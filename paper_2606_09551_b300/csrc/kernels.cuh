@@ -59,11 +59,12 @@ struct RkDcf {
   __device__ __forceinline__ uint32_t operator[](int i) const { return c_rk_dcf[i]; }
 };
 
-// Table addressing used by every kernel: byte permute + multiply-add, which
-// moves a third of the round's integer work from the ALU pipe to the FMA pipe
-// (240 instead of 360 ALU operations per block; the shared-memory lookups,
-// 160 per block, become the limit).
-constexpr int kAesVariant = 1;
+// Table addressing used by every FSS kernel: one byte permute forms each
+// lookup address in the interleaved layout (variant 4), so a block costs
+// 160 shared-memory lookups, 160 permutes and the XOR combines; the earlier
+// permute + multiply-add form (variant 1) spent one more instruction per
+// lookup and left the bit-DCF walks issue-bound.
+constexpr int kAesVariant = 4;
 
 // AES_K for the DCF PRG, inlined (online path).
 struct AesDcfInline {
@@ -104,11 +105,7 @@ struct AesDcfCall4 {
 // Stage the four rotated T-tables, 32 lane copies each, and the spec.
 __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, const uint32_t *t0,
                                              const DevSpec *spec) {
-  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
-    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
-    const uint32_t v = t0[e];
-    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
-  }
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
   const uint32_t *src = reinterpret_cast<const uint32_t *>(spec);
   uint32_t *dst = reinterpret_cast<uint32_t *>(sspec);
   for (uint32_t i = threadIdx.x; i < sizeof(DevSpec) / 4; i += blockDim.x) dst[i] = src[i];
@@ -542,11 +539,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
   __shared__ unsigned long long next_tile;
   __shared__ unsigned long long s_begin[kBatchMaxCalls];   // first tile of each call of this class
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
-  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
-    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
-    const uint32_t v = t0[e];
-    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
-  }
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
   const BatchCall *calls = all_calls + hdr->cls[C].first;
   const uint32_t n_calls = hdr->cls[C].count;
   const unsigned long long total = hdr->cls[C].total_tiles;
@@ -841,9 +834,13 @@ __global__ void __launch_bounds__(512, 1) mb_aes_kernel(const uint32_t *t0, uint
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) {
-    const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
-    const uint32_t v = t0[e];
-    tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+    if (VAR == 4) {
+      tab[idx] = tab_word(t0, idx);
+    } else {   // plain layout: table*8192 + e*32 + lane words
+      const uint32_t e = (idx >> 5) & 255u, table = idx >> 13;
+      const uint32_t v = t0[e];
+      tab[idx] = table == 0 ? v : __funnelshift_l(v, v, 8 * table);
+    }
   }
   __syncthreads();
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
