@@ -116,6 +116,16 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // party-local steps (party b sees only its own key material kb)
 // ---------------------------------------------------------------------------
 
+// The bit-DCF walk compiled out of line: its own register allocation keeps
+// the walk at the cost of the bare AES chain plus a few operations per level;
+// inlined into the fused gate the compiler emitted about 40 % more
+// instructions per level.  One call per walk.
+__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint32_t u, const uint4 *root, uint64_t n,
+                                          uint64_t vcw, const char *tab, uint32_t lane4) {
+  const AesDcfInline aes{Tab{tab, lane4}};
+  return dcf_bit_eval(b, f, u, root, n, vcw, aes);
+}
+
 // One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
 __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const KeyLayout &L,
                                              const char *kb, uint64_t e, uint64_t xhat, uint32_t t,
@@ -124,7 +134,7 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   const uint32_t f = S.q_f[t];
   const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
   const uint64_t vcw = reinterpret_cast<const uint64_t *>(q + 16ull * (f + 1) * L.n)[e];
-  return dcf_bit_eval(b, f, view(xhat, f, S.q_c[t]), root, L.n, vcw, aes);
+  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, vcw, aes.tb.base, aes.tb.lane4);
 }
 
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
