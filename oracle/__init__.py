@@ -53,6 +53,9 @@ def lib():
                                     C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32, C.c_uint32]
         L.or_spec_build.restype = C.c_int
         L.or_elem_trunc.argtypes = [C.c_void_p, u64p, u32p, u64p]
+        L.or_beaver_dealer.argtypes = [u8p, C.c_uint32, C.c_uint64, C.c_uint64, u64p, u64p]
+        L.or_beaver_mul.argtypes = [u64p, u64p, u64p, u64p, u64p, u64p, C.c_uint64, C.c_uint64,
+                                    u64p, u64p, u64p]
         L.or_spec_shape.argtypes = [C.c_void_p, u32p]
         L.or_spec_query.argtypes = [C.c_void_p, C.c_uint32, u32p, u64p, i32p]
         L.or_plain_eval.argtypes = [C.c_void_p, u64p, C.c_uint64, u64p, u32p]
@@ -63,8 +66,7 @@ def lib():
                                    u64p, u64p, u32p, u32p, u32p, u32p, u64p, u64p, u64p, u64p]
         L.or_reconstruct.argtypes = [u64p, u64p, u32p, u32p, C.c_uint64, C.c_uint32, u64p, u32p]
         L.or_elem_qkey.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
-        L.or_elem_lkey.argtypes = [C.c_void_p, C.c_uint32]
-        L.or_elem_lkey.restype = C.c_void_p
+        L.or_elem_lkey.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
         L.or_dcf_key_fields.argtypes = [C.c_void_p, u8p, u8p, u8p, u8p, u8p, u64p]
         L.or_elem_btriples.argtypes = [C.c_void_p, C.c_uint32, u32p, u32p, u32p]
         L.or_elem_fields.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, u64p, u32p, u64p, u64p, u64p, u64p]
@@ -256,8 +258,7 @@ class ElemKeys:
     def lkey(self, i: int, j: int) -> DcfKey:
         """Lookup key j (1-based boundary index j = 1..M-1)."""
         key = DcfKey()
-        src = lib().or_elem_lkey(self.elem_ptr(i), j - 1)
-        C.memmove(key.ptr, src, key.buf.size)
+        lib().or_elem_lkey(self.elem_ptr(i), j - 1, key.ptr)
         return key
 
 
@@ -314,3 +315,26 @@ def reconstruct(y0, y1, z0, z1, r: int):
     lib().or_reconstruct(_p(y0, u64p), _p(y1, u64p), _p(z0, u32p), _p(z1, u32p), n, r,
                          _p(y, u64p), _p(z, u32p))
     return y.reshape(n, r), z
+
+
+# --------------------------------------------------------------------------
+# Beaver multiplication of shared vectors (composition of gates)
+# --------------------------------------------------------------------------
+
+def beaver_dealer(seed: bytes, call_id: int, e0: int, n: int):
+    """Triple shares of both parties, each uint64 [3, n] (a_b, b_b, c_b)."""
+    sd = np.frombuffer(bytes(seed), np.uint8).copy()
+    t0 = np.zeros(3 * max(n, 1), np.uint64)
+    t1 = np.zeros(3 * max(n, 1), np.uint64)
+    lib().or_beaver_dealer(_p(sd, u8p), call_id, e0, n, _p(t0, u64p), _p(t1, u64p))
+    return t0[:3 * n].reshape(3, n), t1[:3 * n].reshape(3, n)
+
+
+def beaver_mul(t0, t1, x0, x1, y0, y1, group: int = 1):
+    """Shares of x * y[e // group]; returns z0, z1 and the bytes each party sent."""
+    n = x0.size
+    arrs = [np.ascontiguousarray(a, dtype=np.uint64).reshape(-1) for a in (t0, t1, x0, x1, y0, y1)]
+    z0, z1 = np.zeros(n, np.uint64), np.zeros(n, np.uint64)
+    comm = np.zeros(2, np.uint64)
+    lib().or_beaver_mul(*[_p(a, u64p) for a in arrs], n, group, _p(z0, u64p), _p(z1, u64p), _p(comm, u64p))
+    return z0, z1, comm

@@ -1,0 +1,142 @@
+"""Vector blocks composed from oracle gates -- TEST INFRASTRUCTURE ONLY.
+
+Same rules as the rest of ``oracle/``: only ``tests/``, ``__graft_entry__``
+and the CPU-baseline leg of ``bench.py`` may use it; the CUDA product path
+never imports it.
+
+App. G writes softmax as a composition of (i) linear operations on additive
+shares, (ii) a comparison-tree max, (iii) specification-compatible scalar
+gates (nExp, reciprocal) and Beaver multiplications (Sec. 3.4).  This module
+runs that composition on the oracle's gates, party by party, with the linear
+steps as plain numpy arithmetic on the share arrays (uint64, wrapping), and
+gives the plaintext definition of the same pipeline from each gate's
+plaintext evaluator.
+
+Pipeline on an input X of shape [rows, L] (fixed point, f fractional bits);
+the gates come as a dict of oracle specs with the keys below:
+
+1. m = row max by a comparison tree: while a row holds n > 1 values, pair
+   the first half with the second (a_j, b_j = c_j, c_{j+h}, h = n // 2),
+   gate d = a - b through `relu` and keep b + ReLU(d), i.e. max(a, b); an
+   odd last value passes through.  ceil(log2 L) gate rounds.
+2. D = X - m (per row, local).
+3. E = `exp`(D), rescaled by the shift gate `shift_e`.
+4. s = row sum of E (local).
+5. t = `recip`(s), rescaled by `shift_t`.
+6. P = E * t (Beaver multiplication, t broadcast over the row).
+7. Y = `shift_p`(P).
+
+Every rescale rounds to nearest: party 0 adds 2^(s-1) (a public constant,
+local) before the shift gate's floor by 2^s.
+
+Dealer call ids: call_base + j for the j-th step that draws (the tree
+rounds, then exp, shift_e, recip, shift_t, the multiplication, shift_p)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import beaver_dealer, beaver_mul, dealer, eval_pair
+
+
+def tree_rounds(L: int) -> int:
+    """Gate rounds of the comparison-tree max over L values."""
+    r, n = 0, L
+    while n > 1:
+        n = n // 2 + n % 2
+        r += 1
+    return r
+
+
+def _gate(spec, seed, call_id, x0, x1):
+    x0 = np.ascontiguousarray(x0, dtype=np.uint64).reshape(-1)
+    x1 = np.ascontiguousarray(x1, dtype=np.uint64).reshape(-1)
+    k0, k1, _, _ = dealer(spec, seed, call_id, 0, x0.size)
+    res = eval_pair(spec, k0, k1, x0, x1)
+    return res["y0"][:, 0].copy(), res["y1"][:, 0].copy(), res["comm"].astype(np.uint64)
+
+
+def row_max_pair(relu, seed, call_base, x0, x1):
+    """Shares of the row maxima (step 1); returns m0, m1, comm, next call id."""
+    c0, c1 = np.asarray(x0, np.uint64), np.asarray(x1, np.uint64)
+    rows = c0.shape[0]
+    comm = np.zeros(2, np.uint64)
+    cid = call_base
+    while c0.shape[1] > 1:
+        n = c0.shape[1]
+        h = n // 2
+        d0 = c0[:, :h] - c0[:, h:2 * h]
+        d1 = c1[:, :h] - c1[:, h:2 * h]
+        r0, r1, cm = _gate(relu, seed, cid, d0, d1)
+        cid += 1
+        comm += cm
+        n0 = c0[:, h:2 * h] + r0.reshape(rows, h)
+        n1 = c1[:, h:2 * h] + r1.reshape(rows, h)
+        if n % 2:
+            n0 = np.concatenate([n0, c0[:, 2 * h:]], axis=1)
+            n1 = np.concatenate([n1, c1[:, 2 * h:]], axis=1)
+        c0, c1 = n0, n1
+    return c0[:, 0].copy(), c1[:, 0].copy(), comm, cid
+
+
+def softmax_pair(g, seed, call_base, x0, x1):
+    """Both parties' shares of the softmax pipeline on shares x0, x1 [rows, L];
+    g maps relu, exp, shift_e, recip, shift_t, shift_p to oracle specs.
+    Returns (y0, y1, comm, steps) with steps the intermediate shares."""
+    x0 = np.asarray(x0, np.uint64)
+    x1 = np.asarray(x1, np.uint64)
+    rows, L = x0.shape
+    m0, m1, comm, cid = row_max_pair(g["relu"], seed, call_base, x0, x1)
+    steps = dict(m=(m0, m1))
+
+    def gate(name, a0, a1):
+        nonlocal cid, comm
+        if g[name].trunc_s:                   # round to nearest: party 0 adds 2^(s-1)
+            a0 = a0 + np.uint64(1 << (g[name].trunc_s - 1))
+        r0, r1, cm = _gate(g[name], seed, cid, a0, a1)
+        cid += 1
+        comm = comm + cm
+        steps[name] = (r0, r1)
+        return r0, r1
+
+    E0, E1 = gate("exp", x0 - m0[:, None], x1 - m1[:, None])
+    E0, E1 = gate("shift_e", E0, E1)
+    s0 = E0.reshape(rows, L).sum(axis=1, dtype=np.uint64)
+    s1 = E1.reshape(rows, L).sum(axis=1, dtype=np.uint64)
+    t0, t1 = gate("recip", s0, s1)
+    t0, t1 = gate("shift_t", t0, t1)
+    T0, T1 = beaver_dealer(seed, cid, 0, rows * L)
+    cid += 1
+    P0, P1, cm = beaver_mul(T0, T1, E0, E1, t0, t1, group=L)
+    comm = comm + cm
+    steps["mul"] = (P0, P1)
+    Y0, Y1 = gate("shift_p", P0, P1)
+    return Y0.reshape(rows, L), Y1.reshape(rows, L), comm, steps
+
+
+def softmax_plain(g, x):
+    """The same pipeline on plaintext integers: each gate by its plaintext
+    evaluator, the linear steps and the product in Z_{2^64}."""
+    x = np.asarray(x, np.uint64)
+    rows, L = x.shape
+
+    def ev(name, v):
+        v = np.asarray(v, np.uint64).reshape(-1)
+        if g[name].trunc_s:
+            v = v + np.uint64(1 << (g[name].trunc_s - 1))
+        return g[name].plain_eval(v)[0][:, 0]
+
+    c = x
+    while c.shape[1] > 1:
+        n = c.shape[1]
+        h = n // 2
+        nc = c[:, h:2 * h] + ev("relu", c[:, :h] - c[:, h:2 * h]).reshape(rows, h)
+        if n % 2:
+            nc = np.concatenate([nc, c[:, 2 * h:]], axis=1)
+        c = nc
+    m = c[:, 0]
+    E = ev("shift_e", ev("exp", x - m[:, None])).reshape(rows, L)
+    s = E.sum(axis=1, dtype=np.uint64)
+    t = ev("shift_t", ev("recip", s))
+    P = E * t[:, None]
+    Y = ev("shift_p", P).reshape(rows, L)
+    return Y, dict(m=m, E=E, s=s, t=t, P=P)

@@ -196,7 +196,8 @@ static void mmo(const uint8_t s[16], uint32_t j, uint8_t out[16])
 
 void or_mmo(const uint8_t s[16], uint32_t j, uint8_t out[16]) { mmo(s, j, out); }
 
-#define MAXK 32     /* view width k <= 32 */
+#define MAXK 63     /* view width k <= 63 (k + 1 V_CW bits of a bit key fit a uint64) */
+#define MAXKL 32    /* view width of a spec with an interval lookup */
 #define MAXP 4      /* payload length p = r (d + 1) <= 4 */
 
 static int nblocks_for(int p) { return (8 * p + 15) / 16; }   /* V = ceil(8p/16) */
@@ -256,6 +257,36 @@ typedef struct {
     uint8_t tcw_l[MAXK], tcw_r[MAXK];
     uint8_t vcw_bit[MAXK + 1];
 } or_bit_key;
+
+/* Stored lookup keys: at most MAXKL levels. */
+typedef struct {
+    int k, p;
+    uint8_t root[16];
+    uint8_t scw[MAXKL][16];
+    uint8_t tcw_l[MAXKL], tcw_r[MAXKL];
+    uint64_t vcw[MAXKL + 1][MAXP];
+} or_lut_key;
+
+static void lut_key_from(const or_dcf_key *src, or_lut_key *dst)
+{
+    dst->k = src->k; dst->p = src->p;
+    memcpy(dst->root, src->root, 16);
+    memcpy(dst->scw, src->scw, sizeof(dst->scw));
+    memcpy(dst->tcw_l, src->tcw_l, MAXKL);
+    memcpy(dst->tcw_r, src->tcw_r, MAXKL);
+    memcpy(dst->vcw, src->vcw, sizeof(dst->vcw));
+}
+
+static void lut_key_to(const or_lut_key *src, or_dcf_key *dst)
+{
+    memset(dst, 0, sizeof(*dst));
+    dst->k = src->k; dst->p = src->p;
+    memcpy(dst->root, src->root, 16);
+    memcpy(dst->scw, src->scw, sizeof(src->scw));
+    memcpy(dst->tcw_l, src->tcw_l, MAXKL);
+    memcpy(dst->tcw_r, src->tcw_r, MAXKL);
+    memcpy(dst->vcw, src->vcw, sizeof(src->vcw));
+}
 
 static void bit_key_from(const or_dcf_key *src, or_bit_key *dst)
 {
@@ -505,6 +536,7 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
      * interval-independent payload and omits the lookup call (App. O). */
     if (m == 1) sp->M = 1;
     else sp->M = (uint64_t)(m + 1) < pow2(k) ? m + 1 : (uint32_t)pow2(k);
+    if (sp->M > 1 && k > MAXKL) return -1;   /* the lookup keys hold at most MAXKL levels */
 
     uint32_t nb = 0;
     if (partition_bits)
@@ -651,7 +683,8 @@ void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y
              * k-bit two's-complement value of x mod 2^k, sign-extended */
             uint64_t t;
             if (sp->trunc_signed) {
-                int64_t v = (int64_t)xk - ((xk >> (sp->k - 1)) ? (int64_t)pow2(sp->k) : 0);
+                /* two's-complement value of the k-bit view (unsigned wrap, then cast) */
+                int64_t v = (int64_t)((xk >> (sp->k - 1)) ? xk - pow2(sp->k) : xk);
                 int64_t q = v >= 0 ? v / (int64_t)pow2(sp->trunc_s)
                                    : -(((-v) + (int64_t)pow2(sp->trunc_s) - 1) / (int64_t)pow2(sp->trunc_s));
                 t = (uint64_t)q;
@@ -720,7 +753,7 @@ typedef struct {
     uint32_t carry_share;
     uint64_t vlast_share[MAXP];
     or_bit_key qkey[MAXQ];            /* packed-comparison keys, query order */
-    or_dcf_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
+    or_lut_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
     uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
     uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
     uint64_t tr_t;                    /* truncation: share of (r mod 2^k) >> s */
@@ -881,7 +914,10 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             uint32_t di = base_roots + 2 * (T + j - 1);
             prg_block(&g, di, e, s0);
             prg_block(&g, di + 1, e, s1);
-            or_dcf_gen((int)sp->k, B[j], (int)p, beta, s0, s1, &K0->lkey[j - 1], &K1->lkey[j - 1]);
+            or_dcf_key g0, g1;
+            or_dcf_gen((int)sp->k, B[j], (int)p, beta, s0, s1, &g0, &g1);
+            lut_key_from(&g0, &K0->lkey[j - 1]);
+            lut_key_from(&g1, &K1->lkey[j - 1]);
         }
         for (uint32_t q = 0; q < p; q++) {
             uint64_t sh = prg_u64(&g, DRAW_VLAST + q, e);
@@ -1018,7 +1054,9 @@ static void party_lookup(int b, const or_spec *sp, const or_elem_keys *K, uint64
     for (uint32_t q = 0; q < sp->p; q++) pay[q] = K->vlast_share[q];
     for (uint32_t j = 1; j < sp->M; j++) {
         uint64_t sh[MAXP];
-        or_dcf_eval(b, &K->lkey[j - 1], u, NULL, sh);
+        or_dcf_key key;
+        lut_key_to(&K->lkey[j - 1], &key);
+        or_dcf_eval(b, &key, u, NULL, sh);
         for (uint32_t q = 0; q < sp->p; q++) pay[q] += sh[q];
     }
 }
@@ -1158,7 +1196,7 @@ void or_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0, 
 /* ------------------------------------------------------------------------ */
 
 void or_elem_qkey(const or_elem_keys *K, uint32_t t, or_dcf_key *out) { bit_key_to(&K->qkey[t], out); }
-const or_dcf_key *or_elem_lkey(const or_elem_keys *K, uint32_t j) { return &K->lkey[j]; }
+void or_elem_lkey(const or_elem_keys *K, uint32_t j, or_dcf_key *out) { lut_key_to(&K->lkey[j], out); }
 
 void or_dcf_key_fields(const or_dcf_key *key, uint8_t *root, uint8_t *scw, uint8_t *tcw_l,
                        uint8_t *tcw_r, uint8_t *vcw_bit, uint64_t *vcw)
@@ -1193,4 +1231,56 @@ void or_elem_fields(const or_elem_keys *K, uint32_t p, uint32_t nm, uint64_t *r_
 void or_elem_trunc(const or_elem_keys *K, uint64_t *t, uint32_t *rho, uint64_t *rho_a)
 {
     *t = K->tr_t; *rho = K->tr_rho; rho_a[0] = K->tr_rho_a[0]; rho_a[1] = K->tr_rho_a[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Beaver multiplication of shared ring vectors (Sec. 3.4: preprocessing-   */
+/* based multiplication over R with Beaver triples), for composing gates    */
+/* into vector blocks (App. G).                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Dealer: for element e of call call_id, draws (a, b, a_0, b_0, c_0) from
+ * the run seed's AES-CTR (draw indices 0..4); party 0 holds (a_0, b_0, c_0),
+ * party 1 (a - a_0, b - b_0, a b - c_0).  t_b layout: [3][n] = a_b, b_b, c_b. */
+void or_beaver_dealer(const uint8_t seed[16], uint32_t call_id, uint64_t e0, uint64_t n,
+                      uint64_t *t0, uint64_t *t1)
+{
+    or_prg g;
+    aes_expand(seed, &g.ks);
+    g.call_id = call_id;
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t e = e0 + i;
+        uint64_t a = prg_u64(&g, 0, e), b = prg_u64(&g, 1, e);
+        uint64_t a0 = prg_u64(&g, 2, e), b0 = prg_u64(&g, 3, e), c0 = prg_u64(&g, 4, e);
+        t0[i] = a0;         t1[i] = a - a0;
+        t0[n + i] = b0;     t1[n + i] = b - b0;
+        t0[2 * n + i] = c0; t1[2 * n + i] = a * b - c0;
+    }
+}
+
+/* Online: z = x * y[e / group] over Z_{2^64} (group = 1: elementwise; group
+ * = L: one y per row of L).  Each party opens e = x_b - a_b and
+ * f = y_b - b_b (16 bytes), then z_b = [b=0] E F + E b_b + F a_b + c_b. */
+void or_beaver_mul(const uint64_t *t0, const uint64_t *t1, const uint64_t *x0, const uint64_t *x1,
+                   const uint64_t *y0, const uint64_t *y1, uint64_t n, uint64_t group,
+                   uint64_t *z0, uint64_t *z1, uint64_t *comm)
+{
+    const uint64_t *T[2] = {t0, t1}, *X[2] = {x0, x1}, *Y[2] = {y0, y1};
+    uint64_t *Z[2] = {z0, z1};
+    uint64_t sent[2] = {0, 0};
+    for (uint64_t e = 0; e < n; e++) {
+        uint64_t em[2], fm[2];
+        for (int b = 0; b < 2; b++) {
+            em[b] = X[b][e] - T[b][e];
+            fm[b] = Y[b][e / group] - T[b][n + e];
+            sent[b] += 16;
+        }
+        uint64_t E = em[0] + em[1], F = fm[0] + fm[1];
+        for (int b = 0; b < 2; b++) {
+            uint64_t z = E * T[b][n + e] + F * T[b][e] + T[b][2 * n + e];
+            if (b == 0) z += E * F;
+            Z[b][e] = z;
+        }
+    }
+    if (comm) { comm[0] = sent[0]; comm[1] = sent[1]; }
 }

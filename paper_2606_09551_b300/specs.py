@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Callable, List, Sequence, Tuple
+from typing import Callable, Dict, List, Sequence, Tuple
 
 import numpy as np
 
@@ -241,7 +241,7 @@ def silu16(k: int = 24, f: int = 16, d: int = 3) -> OperatorSpec:
     return build_piecewise("silu16", _silu, k, f, d, pieces, domain=(-16, 16))
 
 
-def nexp16(k: int = 24, f: int = 12, d: int = 3) -> OperatorSpec:
+def nexp16(k: int = 24, f: int = 12, d: int = 3, out_frac_bits: int | None = None) -> OperatorSpec:
     """exp(x) for x <= 0 (softmax after max subtraction); 0 below -16, 1 above 0."""
     h = 2 ** (k - 1 - f)
     cuts = [-16, -12, -10, -8, -7, -6, -5, -4, -3.5, -3, -2.5, -2, -1.5, -1, 0]
@@ -249,7 +249,7 @@ def nexp16(k: int = 24, f: int = 12, d: int = 3) -> OperatorSpec:
     for lo, hi in zip(cuts, cuts[1:]):
         pieces.append((lo, hi, "fit"))
     pieces.append((0, h, "const:1"))
-    return build_piecewise("nexp16", np.exp, k, f, d, pieces, domain=(-16, 0))
+    return build_piecewise("nexp16", np.exp, k, f, d, pieces, out_frac_bits=out_frac_bits, domain=(-16, 0))
 
 
 def _octave_pieces(k: int, f: int, fn, first_exp: int, const_below: float):
@@ -263,11 +263,11 @@ def _octave_pieces(k: int, f: int, fn, first_exp: int, const_below: float):
     return pieces
 
 
-def recip16(k: int = 24, f: int = 12, d: int = 3) -> OperatorSpec:
+def recip16(k: int = 24, f: int = 12, d: int = 3, out_frac_bits: int | None = None) -> OperatorSpec:
     """1/x on octaves [2^j, 2^(j+1)); constant below the first octave, zero for x < 0."""
     first = (k - 1 - f) - 14
     pieces = _octave_pieces(k, f, lambda x: 1.0 / x, first, 2.0 ** (-first))
-    return build_piecewise("recip16", lambda x: 1.0 / x, k, f, d, pieces,
+    return build_piecewise("recip16", lambda x: 1.0 / x, k, f, d, pieces, out_frac_bits=out_frac_bits,
                            domain=(2.0 ** first, 2.0 ** (k - 1 - f)))
 
 
@@ -288,6 +288,28 @@ def relu(k: int) -> OperatorSpec:
     return OperatorSpec(name="relu", k=k, frac_bits=0, out_frac_bits=0, m=2, degree=1, n_out=1,
                         alpha=[0, 1 << (k - 1), 1 << k], coeff=coeff, partition_bits=False,
                         preds=[PredDesc(k, 0, 1 << (k - 1), 1)])
+
+
+def softmax_specs(f: int = 12) -> Dict[str, OperatorSpec]:
+    """The gates of a fixed-point softmax over rows (App. G), in pipeline order,
+    for scores at f fractional bits.  Each polynomial gate keeps the output
+    scale its fit needs (Horner over Z_{2^64} stores c_j at scale F - j*f), and
+    shift gates on wide views rescale between the steps:
+
+    relu     ReLU on a 24-bit view: the comparison-tree max, max(a, b) = b + ReLU(a - b)
+    exp      nExp (k 24, f, d 3) at its fitted scale F_e
+    shift_e  ARS by F_e - 16 on a 63-bit view: E at 16 bits
+    recip    1/x for inputs at 16 bits on a 28-bit view (octaves 2^-3 .. 2^11;
+             a row sum of up to 2^11 ones), at its fitted scale F_r
+    shift_t  ARS by F_r - 20 on a 63-bit view: t at 20 bits
+    shift_p  ARS by 24 on a 40-bit view: the product E t (36 bits, below 2^37) at 12 bits"""
+    exp = nexp16(f=f)
+    recip = recip16(k=28, f=16)
+    return {"relu": relu(24), "exp": exp,
+            "shift_e": trunc(63, exp.out_frac_bits - 16, True, name=f"ars63_{exp.out_frac_bits - 16}"),
+            "recip": recip,
+            "shift_t": trunc(63, recip.out_frac_bits - 20, True, name=f"ars63_{recip.out_frac_bits - 20}"),
+            "shift_p": trunc(40, 16 + 20 - f, True, name=f"ars40_{16 + 20 - f}")}
 
 
 def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,

@@ -57,3 +57,17 @@ def test_single_key_shares_look_random():
     a, b = O.dcf_gen(k, 512, 0, None, rng.bytes(16), rng.bytes(16))
     s0 = np.array([O.dcf_eval(0, a, u, 0) for u in range(2 ** k)])
     assert 0.4 < s0[:512].mean() < 0.6 and 0.4 < s0[512:].mean() < 0.6
+
+
+@pytest.mark.parametrize("k", [33, 47, 63])
+def test_bit_dcf_wide_views(k):
+    """Bit DCF on views wider than 32 bits (comparisons up to k = 63): on
+    random alpha and u plus the neighbours of alpha and the ends of the
+    domain, Eval_0 xor Eval_1 = 1[u < alpha]."""
+    rng = np.random.default_rng(k)
+    for trial in range(6):
+        alpha = int(rng.integers(1, 2 ** k - 1, dtype=np.uint64))
+        k0, k1 = O.dcf_gen(k, alpha, 0, None, rng.bytes(16), rng.bytes(16))
+        us = [0, 2 ** k - 1, alpha - 1, alpha, alpha + 1] + [int(v) for v in rng.integers(0, 2 ** k, 10, dtype=np.uint64)]
+        for u in us:
+            assert (O.dcf_eval(0, k0, u, 0) ^ O.dcf_eval(1, k1, u, 0)) == int(u < alpha), (alpha, u)

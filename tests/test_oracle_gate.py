@@ -309,3 +309,42 @@ def test_truncation_with_polynomial_and_boolean_outputs(k):
         assert (y == yp).all() and (z == zp).all(), trial
         mults = 0 if sp.xhat_basis else d * r
         assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * len(sp.piecewise) + 1)).all()
+
+
+@pytest.mark.parametrize("k,s", [(40, 20), (63, 49), (63, 1), (48, 47)])
+def test_truncation_wide_views(k, s):
+    """Shift gates on views wider than 32 bits (single-interval specs may use
+    k up to 63): random 64-bit x against Python's integer shift of the k-bit
+    view; at k = 63 the arithmetic form equals numpy's int64 right shift of
+    values inside the 63-bit signed range."""
+    rng = np.random.default_rng(k * 100 + s)
+    x = rng.integers(0, 2 ** 64, size=3000, dtype=np.uint64)
+    for signed in (False, True):
+        sp = S.trunc(k, s, signed)
+        _, res, y, _ = run_gate(sp, x)
+        yp, _ = python_plain(sp, x)
+        assert np.array_equal(y, yp), signed
+        assert (res["comm"] == x.size * 9).all()
+    if k == 63:
+        v = rng.integers(-(2 ** 62), 2 ** 62, size=3000, dtype=np.int64)
+        _, _, y, _ = run_gate(S.trunc(63, s, True), v.view(np.uint64))
+        assert np.array_equal(y[:, 0].view(np.int64), np.right_shift(v, s))
+
+
+def test_wide_view_predicates_single_interval():
+    """m = 1 specs with predicates on views up to 63 bits (no lookup)."""
+    rng = np.random.default_rng(77)
+    x = rng.integers(0, 2 ** 64, size=2000, dtype=np.uint64)
+    for k in (33, 50, 63):
+        preds = [S.PredDesc(k, 0, 1 << (k - 1), 1),                       # MSB of the k-bit view
+                 S.PredDesc(k, int(rng.integers(0, 2 ** k, dtype=np.uint64)), int(rng.integers(1, 2 ** k, dtype=np.uint64)), 0),
+                 S.PredDesc(min(k, 40), 12345, 2 ** (min(k, 40) - 1) + 7, 1)]
+        coeff = rng.integers(0, 2 ** 64, size=(1, 1, 3), dtype=np.uint64)
+        sp = S.OperatorSpec(f"wide{k}", k=k, frac_bits=0, out_frac_bits=0, m=1, degree=2, n_out=1,
+                            alpha=[0, 1 << k], coeff=coeff, partition_bits=False, preds=preds)
+        _, _, y, z = run_gate(sp, x)
+        yp, zp = python_plain(sp, x)
+        assert np.array_equal(y, yp) and np.array_equal(z, zp), k
+    # a lookup needs k <= 32
+    with pytest.raises(ValueError):
+        ospec(S.random_spec(rng, 33, 3, 1, 1))
