@@ -50,7 +50,8 @@ extern "C" {
 #define FFSS_ERR_UNSUPPORTED (-7) /* shape outside what the kernels are built for */
 
 /* Library limits (checked when a spec is compiled). */
-#define FFSS_MAX_K 32        /* comparison view width k */
+#define FFSS_MAX_K 63        /* comparison view width k (bit-DCF queries, shift gates) */
+#define FFSS_MAX_K_LOOKUP 32 /* k of a spec with an interval lookup (m > 1) */
 #define FFSS_MAX_M 16        /* intervals m */
 #define FFSS_MAX_P 4         /* payload length p = n_out * (degree + 1) */
 #define FFSS_MAX_BOOL 32     /* Boolean outputs, one uint32 per element */
@@ -82,7 +83,8 @@ typedef struct {
  *        C_{alpha_i}(x) = 1[(x mod 2^k) < alpha_i], i = 1..m-1; preds[0..n_pred)
  *        follow. */
 typedef struct {
-    uint32_t k;              /* comparison view width, 1..FFSS_MAX_K */
+    uint32_t k;              /* comparison view width, 1..FFSS_MAX_K; at most
+                                FFSS_MAX_K_LOOKUP when m > 1 (interval lookup) */
     uint32_t frac_bits;      /* fixed-point metadata (not used by the arithmetic) */
     uint32_t m;              /* intervals, 1..FFSS_MAX_M, m < 2^k */
     uint32_t degree;         /* d */
@@ -366,6 +368,51 @@ int ffss_server_summary(ffss_server *server, ffss_server_stats *out);
 int ffss_reconstruct(const uint64_t *y0_dev, const uint64_t *y1_dev, const uint32_t *z0_dev,
                      const uint32_t *z1_dev, uint64_t n, uint32_t n_out, uint64_t *y_dev,
                      uint32_t *z_dev, void *stream);
+
+/* ---- composed vector blocks (App. G) --------------------------------------- */
+
+/* Beaver multiplication of additively shared vectors (Sec. 3.4: one triple
+ * per product).  Triples are caller-owned device buffers of u64 [3][n] per
+ * party (a_b, b_b, c_b; 24 n bytes), one-time: use each for one
+ * ffss_beaver_mul.  ffss_beaver_keygen deals them for call call_id from the
+ * run seed's AES-128-CTR (draws a, b, a_0, b_0, c_0 = indices 0..4 of
+ * element e).  ffss_beaver_mul computes shares of z = x * y[e / group]
+ * (group = 1: elementwise; group = L: one y per row of L) over Z_{2^64};
+ * each party sends 16 bytes per element, counted into comm[party] when comm
+ * is not NULL.  Errors: FFSS_ERR_INVALID, FFSS_ERR_CUDA. */
+int ffss_beaver_keygen(ffss_ctx *ctx, const uint8_t seed[16], uint32_t call_id, uint64_t n,
+                       uint64_t *t0_dev, uint64_t *t1_dev, void *stream);
+int ffss_beaver_mul(ffss_ctx *ctx, const uint64_t *t0_dev, const uint64_t *t1_dev,
+                    const uint64_t *x0, const uint64_t *x1, const uint64_t *y0, const uint64_t *y1,
+                    uint64_t n, uint64_t group, uint64_t *z0, uint64_t *z1, uint64_t *comm,
+                    void *stream);
+
+/* Softmax over rows of shared fixed-point values (App. G, "How Softmax /
+ * Layer Norm are handled"), both parties on this GPU:
+ *   1. m = row max by a comparison tree: per round, d = a - b on the row's
+ *      two halves, gate gates[0] (ReLU), max(a, b) = b + ReLU(d); an odd last
+ *      value passes through; ceil(log2 L) rounds;
+ *   2. D = X - m;  3. E = gates[2](gates[1](D) + h2)   (nExp, then a shift);
+ *   4. s = row sum of E;  5. t = gates[4](gates[3](s) + h4)   (Recip, shift);
+ *   6. P = E * t (Beaver, t broadcast over the row);  7. Y = gates[5](P + h5),
+ * where h_i = 2^(s_i - 1) for the shift s_i of gates[i], added by party 0 so
+ * every rescale rounds to nearest.  gates[0], [1], [3] must have n_out = 1;
+ * gates[2], [4], [5] must be shift gates (m = 1, trunc_shift > 0).  The plan
+ * owns device memory for all steps' one-time keys and scratch.  Keys: step j
+ * (the tree rounds, then gates 1..4, the product, gate 5) is dealer call
+ * call_base + j.  ffss_softmax_eval consumes them (FFSS_ERR_SHAPE on reuse);
+ * x, y are [rows][L] u64 shares; comm[party] accumulates every step's bytes.
+ * ffss_softmax_info: tree rounds, key bytes (both parties) and elements
+ * through gates per evaluation. */
+typedef struct ffss_softmax ffss_softmax;
+int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], uint64_t rows, uint64_t L,
+                        ffss_softmax **out);
+int ffss_softmax_keygen(ffss_softmax *sm, const uint8_t seed[16], uint32_t call_base, void *stream);
+int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                      uint64_t *y1, uint64_t *comm, void *stream);
+int ffss_softmax_info(const ffss_softmax *sm, uint32_t *rounds, uint64_t *key_bytes,
+                      uint64_t *gate_elements);
+int ffss_softmax_destroy(ffss_softmax *sm);
 
 /* ---- measurement support ------------------------------------------------ */
 

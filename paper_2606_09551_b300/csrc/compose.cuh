@@ -1,0 +1,381 @@
+// Vector blocks composed from gates (App. G): Beaver multiplication of
+// shared vectors (Sec. 3.4), the party-local linear steps, and the softmax
+// plan (comparison-tree max, nExp, row sum, Recip, product, rescales).
+// Included by fusefss.cu after the gate and server code it builds on.
+#pragma once
+
+namespace ffss {
+
+// ---------------------------------------------------------------------------
+// device kernels
+// ---------------------------------------------------------------------------
+
+// Beaver triples for z = x * y (Sec. 3.4): element e of call call_id draws
+// (a, b, a_0, b_0, c_0) from the run seed's AES-128-CTR, draw indices 0..4,
+// counter (draw, e low, e high, call id).  Party 0 keeps (a_0, b_0, c_0),
+// party 1 (a - a_0, b - b_0, a b - c_0); layout u64 [3][n] per party.
+__global__ void __launch_bounds__(512, 1) beaver_keygen_kernel(const uint32_t *t0, const RkParam rk,
+                                                                uint32_t call_id, uint64_t n, uint64_t *k0,
+                                                                uint64_t *k1) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  uint32_t *rk_s = reinterpret_cast<uint32_t *>(smem + kTabBytes);
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  if (threadIdx.x < 44) rk_s[threadIdx.x] = rk.w[threadIdx.x];
+  __syncthreads();
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += uint64_t(gridDim.x) * blockDim.x) {
+    auto prg = [&](uint32_t dr) {
+      return lo64(aes_rk_call(make_uint4(dr, uint32_t(e), uint32_t(e >> 32), call_id), rk_s, tb.base, tb.lane4));
+    };
+    const uint64_t a = prg(0), b = prg(1), a0 = prg(2), b0 = prg(3), c0 = prg(4);
+    k0[e] = a0;
+    k1[e] = a - a0;
+    k0[n + e] = b0;
+    k1[n + e] = b - b0;
+    k0[2 * n + e] = c0;
+    k1[2 * n + e] = a * b - c0;
+  }
+}
+
+constexpr uint32_t kMulThreads = 256;   // 128 elements x 2 parties per CTA
+
+// z = x * y[e / group] with one triple per product.  Threads [0, 128) act
+// as party 0 and [128, 256) as party 1 for the same 128 elements; each party
+// reads only its own shares and triple and sends (x_b - a_b, y_b - b_b)
+// (16 bytes) through shared memory; then z_b = [b=0] E F + E b_b + F a_b + c_b.
+__global__ void __launch_bounds__(kMulThreads) beaver_mul_kernel(const uint64_t *t0, const uint64_t *t1,
+                                                                 const uint64_t *x0, const uint64_t *x1,
+                                                                 const uint64_t *y0, const uint64_t *y1,
+                                                                 uint64_t n, uint64_t group, uint64_t *z0,
+                                                                 uint64_t *z1, unsigned long long *comm) {
+  __shared__ ulonglong2 box[2][kMulThreads / 2];
+  const uint32_t b = threadIdx.x / (kMulThreads / 2), le = threadIdx.x % (kMulThreads / 2);
+  const uint64_t *T = b ? t1 : t0, *X = b ? x1 : x0, *Y = b ? y1 : y0;
+  uint64_t *Z = b ? z1 : z0;
+  unsigned long long sent = 0;
+  const uint64_t step = uint64_t(gridDim.x) * (kMulThreads / 2);
+  for (uint64_t base = uint64_t(blockIdx.x) * (kMulThreads / 2); base < n; base += step) {
+    const uint64_t e = base + le;
+    const bool valid = e < n;
+    ulonglong2 msg = make_ulonglong2(0, 0);
+    if (valid) {
+      msg = make_ulonglong2(X[e] - T[e], Y[e / group] - T[n + e]);
+      sent += 16;
+    }
+    box[b][le] = msg;
+    __syncthreads();
+    if (valid) {
+      const uint64_t E = box[0][le].x + box[1][le].x, F = box[0][le].y + box[1][le].y;
+      uint64_t z = E * T[n + e] + F * T[e] + T[2 * n + e];
+      if (b == 0) z += E * F;
+      Z[e] = z;
+    }
+    __syncthreads();
+  }
+  if (comm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sent += __shfl_xor_sync(0xffffffffu, sent, off);
+    if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(comm + b, sent);
+  }
+}
+
+// Party-local linear steps on additive shares: every output share of party b
+// depends only on party b's input shares (and public constants added by
+// party 0).  Each kernel runs both parties' arrays.
+
+// One comparison-tree round on rows of n values (h = n / 2): d = c[:, :h] - c[:, h:2h].
+__global__ void tree_diff_kernel(const uint64_t *c0, const uint64_t *c1, uint64_t rows, uint64_t n,
+                                 uint64_t *d0, uint64_t *d1) {
+  const uint64_t h = n / 2;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * h; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t r = i / h, j = i - r * h;
+    d0[i] = c0[r * n + j] - c0[r * n + h + j];
+    d1[i] = c1[r * n + j] - c1[r * n + h + j];
+  }
+}
+
+// Its merge: o[:, j] = c[:, h + j] + relu[:, j] (= max(c_j, c_{h+j})); an odd
+// last value is carried.  o has rows x (h + n % 2) values.
+__global__ void tree_merge_kernel(const uint64_t *c0, const uint64_t *c1, const uint64_t *r0,
+                                  const uint64_t *r1, uint64_t rows, uint64_t n, uint64_t *o0, uint64_t *o1) {
+  const uint64_t h = n / 2, w = h + n % 2;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * w; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t r = i / w, j = i - r * w;
+    if (j < h) {
+      o0[i] = c0[r * n + h + j] + r0[r * h + j];
+      o1[i] = c1[r * n + h + j] + r1[r * h + j];
+    } else {
+      o0[i] = c0[r * n + 2 * h];
+      o1[i] = c1[r * n + 2 * h];
+    }
+  }
+}
+
+// o = x - m[row] over rows of L values.
+__global__ void row_sub_kernel(const uint64_t *x0, const uint64_t *x1, const uint64_t *m0, const uint64_t *m1,
+                               uint64_t rows, uint64_t L, uint64_t *o0, uint64_t *o1) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * L; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t r = i / L;
+    o0[i] = x0[i] - m0[r];
+    o1[i] = x1[i] - m1[r];
+  }
+}
+
+// s[row] = sum of the row's L values; one warp per row.
+__global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t rows, uint64_t L, uint64_t *s0,
+                               uint64_t *s1) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint64_t r = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; r < rows;
+       r += uint64_t(gridDim.x) * blockDim.x / 32) {
+    uint64_t a = 0, b = 0;
+    for (uint64_t j = lane; j < L; j += 32) {
+      a += e0[r * L + j];
+      b += e1[r * L + j];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, off);
+      b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    if (lane == 0) {
+      s0[r] = a;
+      s1[r] = b;
+    }
+  }
+}
+
+// Party 0 adds the public constant c (rounding offset before a shift gate).
+__global__ void add_const_kernel(uint64_t *x0, uint64_t n, uint64_t c) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    x0[i] += c;
+}
+
+}  // namespace ffss
+
+// ---------------------------------------------------------------------------
+// host: Beaver multiplication
+// ---------------------------------------------------------------------------
+
+static int beaver_keygen_raw(const ffss_ctx *ctx, const uint8_t seed[16], uint32_t call_id, uint64_t n,
+                             uint64_t *t0, uint64_t *t1, cudaStream_t st) {
+  const size_t smem = kTabBytes + 44 * 4;
+  static std::once_flag once;
+  int rc = FFSS_OK;
+  std::call_once(once, [&] { rc = set_smem(beaver_keygen_kernel, smem); });
+  if (rc) return rc;
+  RkParam rk;
+  key_schedule(seed, rk.w);
+  beaver_keygen_kernel<<<grid_for(ctx, n, 512), 512, smem, st>>>(ctx->t0_dev, rk, call_id, n, t0, t1);
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+static int beaver_mul_raw(const ffss_ctx *ctx, const uint64_t *t0, const uint64_t *t1, const uint64_t *x0,
+                          const uint64_t *x1, const uint64_t *y0, const uint64_t *y1, uint64_t n, uint64_t group,
+                          uint64_t *z0, uint64_t *z1, uint64_t *comm, cudaStream_t st) {
+  beaver_mul_kernel<<<grid_for(ctx, n, kMulThreads / 2), kMulThreads, 0, st>>>(
+      t0, t1, x0, x1, y0, y1, n, group, z0, z1, reinterpret_cast<unsigned long long *>(comm));
+  CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_beaver_keygen(ffss_ctx *ctx, const uint8_t seed[16], uint32_t call_id, uint64_t n,
+                                  uint64_t *t0_dev, uint64_t *t1_dev, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !seed || !t0_dev || !t1_dev) return fail(FFSS_ERR_INVALID, "ffss_beaver_keygen: NULL argument");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  return beaver_keygen_raw(ctx, seed, call_id, n, t0_dev, t1_dev, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ffss_beaver_mul(ffss_ctx *ctx, const uint64_t *t0_dev, const uint64_t *t1_dev, const uint64_t *x0,
+                               const uint64_t *x1, const uint64_t *y0, const uint64_t *y1, uint64_t n,
+                               uint64_t group, uint64_t *z0, uint64_t *z1, uint64_t *comm, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !t0_dev || !t1_dev || !x0 || !x1 || !y0 || !y1 || !z0 || !z1)
+    return fail(FFSS_ERR_INVALID, "ffss_beaver_mul: NULL argument");
+  if (group == 0) return fail(FFSS_ERR_INVALID, "ffss_beaver_mul: group must be >= 1");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  return beaver_mul_raw(ctx, t0_dev, t1_dev, x0, x1, y0, y1, n, group, z0, z1, comm,
+                        static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// host: the softmax block
+// ---------------------------------------------------------------------------
+
+enum { kSmRelu, kSmExp, kSmShiftE, kSmRecip, kSmShiftT, kSmShiftP, kSmGates };
+
+struct ffss_softmax {
+  ffss_ctx *ctx;
+  const ffss_spec *g[kSmGates];
+  uint64_t rows, L;
+  std::vector<uint64_t> tn;        // values per row entering each tree round
+  struct Step {
+    const ffss_spec *spec;         // nullptr: the Beaver multiplication
+    uint64_t n, off0, off1;        // elements; key offsets of party 0 and 1 in `keys`
+  };
+  std::vector<Step> steps;         // tree rounds, exp, shift_e, recip, shift_t, product, shift_p
+  char *keys;
+  uint64_t key_bytes;
+  uint64_t *sh;                    // share scratch (see ffss_softmax_create)
+  uint32_t *z;                     // the gates' Boolean outputs (not used by the block)
+  int keyed;
+};
+
+extern "C" int ffss_softmax_destroy(ffss_softmax *sm) {
+  if (!sm) return FFSS_OK;
+  cudaSetDevice(sm->ctx->device);
+  if (sm->keys) cudaFree(sm->keys);
+  if (sm->sh) cudaFree(sm->sh);
+  if (sm->z) cudaFree(sm->z);
+  delete sm;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], uint64_t rows, uint64_t L,
+                                   ffss_softmax **out) {
+  if (!ctx || !gates || !out) return fail(FFSS_ERR_INVALID, "ffss_softmax_create: NULL argument");
+  if (rows == 0 || L == 0) return fail(FFSS_ERR_SHAPE, "ffss_softmax_create: rows and L must be >= 1");
+  for (int i = 0; i < kSmGates; ++i) {
+    if (!gates[i]) return fail(FFSS_ERR_INVALID, "ffss_softmax_create: gate %d is NULL", i);
+    if (int rc = check_device_spec(ctx, gates[i])) return rc;
+    if (gates[i]->host.r != 1) return fail(FFSS_ERR_SHAPE, "ffss_softmax_create: gate %d must have n_out = 1", i);
+  }
+  for (int i : {kSmShiftE, kSmShiftT, kSmShiftP})
+    if (gates[i]->host.trunc_s == 0) return fail(FFSS_ERR_SHAPE, "ffss_softmax_create: gate %d must be a shift gate", i);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  ffss_softmax *sm = new ffss_softmax();
+  sm->ctx = ctx;
+  for (int i = 0; i < kSmGates; ++i) sm->g[i] = gates[i];
+  sm->rows = rows;
+  sm->L = L;
+  for (uint64_t n = L; n > 1; n = n / 2 + n % 2) sm->tn.push_back(n);
+  const uint64_t N = rows * L;
+  uint64_t off = 0;
+  auto add = [&](const ffss_spec *spec, uint64_t n) {
+    const uint64_t b = spec ? make_layout(spec->host, n).total : align256(24 * n);
+    sm->steps.push_back({spec, n, off, off + b});
+    off += 2 * b;
+  };
+  for (uint64_t n : sm->tn) add(gates[kSmRelu], rows * (n / 2));
+  add(gates[kSmExp], N);
+  add(gates[kSmShiftE], N);
+  add(gates[kSmRecip], rows);
+  add(gates[kSmShiftT], rows);
+  add(nullptr, N);
+  add(gates[kSmShiftP], N);
+  sm->key_bytes = off;
+  // share scratch, both parties (the carve-up of ffss_softmax_eval): tree
+  // ping-pong 2 x N, differences and ReLU outputs N / 2 + 1 each (h <= L / 2),
+  // D, E, E' and P N each, s, t, t' rows each
+  const uint64_t words = 2 * (2 * N + 2 * (N / 2 + 1) + 4 * N + 3 * rows);
+  cudaError_t e = cudaMalloc(&sm->keys, sm->key_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&sm->sh, words * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&sm->z, 2 * N * 4);
+  if (e != cudaSuccess) {
+    ffss_softmax_destroy(sm);
+    return fail(FFSS_ERR_CUDA, "ffss_softmax_create: %s", cudaGetErrorString(e));
+  }
+  *out = sm;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_softmax_info(const ffss_softmax *sm, uint32_t *rounds, uint64_t *key_bytes,
+                                 uint64_t *gate_elements) {
+  if (!sm) return fail(FFSS_ERR_INVALID, "ffss_softmax_info: NULL argument");
+  if (rounds) *rounds = uint32_t(sm->tn.size());
+  if (key_bytes) *key_bytes = sm->key_bytes;
+  if (gate_elements) {
+    uint64_t t = 0;
+    for (const auto &s : sm->steps) t += s.spec ? s.n : 0;
+    *gate_elements = t;
+  }
+  return FFSS_OK;
+}
+
+extern "C" int ffss_softmax_keygen(ffss_softmax *sm, const uint8_t seed[16], uint32_t call_base, void *stream) {
+  if (!sm || !seed) return fail(FFSS_ERR_INVALID, "ffss_softmax_keygen: NULL argument");
+  CUDA_TRY(cudaSetDevice(sm->ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (size_t j = 0; j < sm->steps.size(); ++j) {
+    const auto &s = sm->steps[j];
+    int rc;
+    if (s.spec)
+      rc = keygen_raw(sm->ctx, s.spec, seed, call_base + uint32_t(j), s.n, nullptr, sm->keys + s.off0,
+                      sm->keys + s.off1, nullptr, nullptr, st);
+    else
+      rc = beaver_keygen_raw(sm->ctx, seed, call_base + uint32_t(j), s.n,
+                             reinterpret_cast<uint64_t *>(sm->keys + s.off0),
+                             reinterpret_cast<uint64_t *>(sm->keys + s.off1), st);
+    if (rc) return rc;
+  }
+  sm->keyed = 1;
+  return FFSS_OK;
+}
+
+// Scratch layout (u64 words, party 0 then party 1 for each array):
+//   c: two ping-pong tree buffers of N; d, r: N / 2 each (held in one N);
+//   D, E, E', P: N each; s, t, t': rows each.
+extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                                 uint64_t *y1, uint64_t *comm, void *stream) {
+  if (!sm || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_softmax_eval: NULL argument");
+  if (!sm->keyed) return fail(FFSS_ERR_SHAPE, "ffss_softmax_eval: keys not generated (or already used)");
+  const ffss_ctx *ctx = sm->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t rows = sm->rows, L = sm->L, N = rows * L;
+  uint64_t *p = sm->sh;
+  auto take = [&](uint64_t words) { uint64_t *q = p; p += words; return q; };
+  uint64_t *cA0 = take(N), *cA1 = take(N), *cB0 = take(N), *cB1 = take(N);
+  uint64_t *d0 = take(N / 2 + 1), *d1 = take(N / 2 + 1);
+  uint64_t *r0 = take(N / 2 + 1), *r1 = take(N / 2 + 1);
+  uint64_t *D0 = take(N), *D1 = take(N), *E0 = take(N), *E1 = take(N);
+  uint64_t *F0 = take(N), *F1 = take(N), *P0 = take(N), *P1 = take(N);
+  uint64_t *s0 = take(rows), *s1 = take(rows), *t0 = take(rows), *t1 = take(rows);
+  uint64_t *u0 = take(rows), *u1 = take(rows);
+  uint32_t *z0 = sm->z, *z1 = sm->z + N;
+  const int TB = 256;
+  size_t j = 0;
+  auto gate = [&](const uint64_t *a0, const uint64_t *a1, uint64_t *o0, uint64_t *o1) {
+    const auto &s = sm->steps[j++];
+    return eval_pair_raw(ctx, s.spec, sm->keys + s.off0, sm->keys + s.off1, a0, a1, s.n, o0, o1, z0, z1, comm, st);
+  };
+  auto half = [&](int g) { return uint64_t(1) << (sm->g[g]->host.trunc_s - 1); };
+  // (1) row max by the comparison tree: max(a, b) = b + ReLU(a - b)
+  const uint64_t *c0 = x0, *c1 = x1;
+  uint64_t *nx0 = cA0, *nx1 = cA1;
+  for (uint64_t n : sm->tn) {
+    const uint64_t h = n / 2, w = h + n % 2;
+    tree_diff_kernel<<<grid_for(ctx, rows * h, TB), TB, 0, st>>>(c0, c1, rows, n, d0, d1);
+    if (int rc = gate(d0, d1, r0, r1)) return rc;
+    tree_merge_kernel<<<grid_for(ctx, rows * w, TB), TB, 0, st>>>(c0, c1, r0, r1, rows, n, nx0, nx1);
+    c0 = nx0; c1 = nx1;
+    nx0 = (nx0 == cA0) ? cB0 : cA0;
+    nx1 = (nx1 == cA1) ? cB1 : cA1;
+  }
+  // c now holds one value per row: the row maxima
+  // (2) D = X - m; (3) E = shift_e(exp(D) + half)
+  row_sub_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(x0, x1, c0, c1, rows, L, D0, D1);
+  if (int rc = gate(D0, D1, E0, E1)) return rc;
+  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(E0, N, half(kSmShiftE));
+  if (int rc = gate(E0, E1, F0, F1)) return rc;
+  // (4) s = row sums; (5) t = shift_t(recip(s) + half)
+  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(F0, F1, rows, L, s0, s1);
+  if (int rc = gate(s0, s1, t0, t1)) return rc;
+  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(t0, rows, half(kSmShiftT));
+  if (int rc = gate(t0, t1, u0, u1)) return rc;
+  // (6) P = E' * t' (t' broadcast over the row); (7) Y = shift_p(P + half)
+  {
+    const auto &s = sm->steps[j++];
+    if (int rc = beaver_mul_raw(ctx, reinterpret_cast<const uint64_t *>(sm->keys + s.off0),
+                                reinterpret_cast<const uint64_t *>(sm->keys + s.off1), F0, F1, u0, u1, N, L, P0,
+                                P1, comm, st))
+      return rc;
+  }
+  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kSmShiftP));
+  if (int rc = gate(P0, P1, y0, y1)) return rc;
+  CUDA_TRY(cudaGetLastError());
+  sm->keyed = 0;   // one-time keys
+  return FFSS_OK;
+}

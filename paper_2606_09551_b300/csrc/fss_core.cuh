@@ -205,10 +205,10 @@ FFSS_CORE Blk4 mmo4(uint4 s0, uint32_t j0, uint4 s1, uint32_t j1, uint4 s2, uint
   return o;
 }
 
-// Public view_{f,c}(u) = ((u mod 2^f) + c) mod 2^f  (Sec. 3.6), f <= 32.
-FFSS_CORE uint32_t view(uint64_t u, uint32_t f, uint64_t c) {
-  uint64_t mask = (uint64_t(1) << f) - 1;
-  return uint32_t(((u & mask) + c) & mask);
+// Public view_{f,c}(u) = ((u mod 2^f) + c) mod 2^f  (Sec. 3.6), f <= 63.
+FFSS_CORE uint64_t view(uint64_t u, uint32_t f, uint64_t c) {
+  const uint64_t mask = (uint64_t(1) << f) - 1;
+  return ((u & mask) + c) & mask;
 }
 
 // ---------------------------------------------------------------------------
@@ -222,12 +222,12 @@ FFSS_CORE uint32_t view(uint64_t u, uint32_t f, uint64_t c) {
 // Bit payload (Z_2): returns the XOR share of 1[u < alpha].
 // root: uint4 root[n] of this key; cw level i at root[(1+i)*n]; vcw: V_CW bits.
 template <class AES>
-FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, uint64_t n,
+FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 *root, uint64_t n,
                                 uint64_t vcw, const AES &aes) {
   uint4 s = root[0];
   uint32_t t = b, v = 0;
   for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t x = (u >> (k - 1 - i)) & 1u;
+    const uint32_t x = uint32_t(u >> (k - 1 - i)) & 1u;
     const uint4 cw = root[(1 + uint64_t(i)) * n];
     const uint4 blk = mmo(s, x, aes);
     const uint32_t tm = 0u - t;
@@ -295,14 +295,14 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
 // ---------------------------------------------------------------------------
 
 template <class AES4>
-FFSS_CORE void dcf_bit_gen(uint32_t k, uint32_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
+FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
                            uint64_t *vcw0, uint64_t *vcw1, uint64_t n, const AES4 &aes4) {
   q0[0] = s0;
   q1[0] = s1;
   uint32_t t0 = 0, t1 = 1, va = 0;
   uint64_t vbits = 0;
   for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
+    const uint32_t a = uint32_t(alpha >> (k - 1 - i)) & 1u;
     const Blk4 ex = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
     const uint4 L0 = ex.v[0], R0 = ex.v[1], L1 = ex.v[2], R1 = ex.v[3];
     const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;   // Lose side

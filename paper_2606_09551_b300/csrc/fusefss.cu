@@ -195,6 +195,8 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   S.k = d->k; S.m = d->m; S.d = d->degree; S.r = d->n_out; S.p = p;
   S.V = (p + 1) / 2;
   S.M = d->m == 1 ? 1 : d->m + 1;
+  if (S.M > 1 && d->k > FFSS_MAX_K_LOOKUP)
+    return fail(FFSS_ERR_UNSUPPORTED, "k=%u > %d with an interval lookup (m > 1)", d->k, FFSS_MAX_K_LOOKUP);
   if (d->xhat_basis > 1) return fail(FFSS_ERR_INVALID, "xhat_basis must be 0 or 1");
   S.xhat = d->xhat_basis;
   S.n_mults = S.xhat ? 0 : d->degree * d->n_out;
@@ -435,6 +437,29 @@ static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t 
   return FFSS_OK;
 }
 
+// Dealer launch on raw key buffers (n elements of a call, no handle checks).
+static int keygen_raw(const ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                      uint64_t n, const uint64_t *x_plain, char *k0, char *k1, uint64_t *x0, uint64_t *x1,
+                      cudaStream_t st) {
+  KeygenArgs A;
+  memset(&A, 0, sizeof(A));
+  A.spec = spec->dev;
+  A.L = make_layout(spec->host, n);
+  A.k0 = k0; A.k1 = k1;
+  A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
+  A.n = n; A.e0 = 0; A.call_id = call_id;
+  A.n_items = (spec->host.M > 1 ? spec->host.M - 1 : 0) + spec->host.T + 1;
+  key_schedule(seed, A.rk.w);
+  A.t0 = ctx->t0_dev;
+  switch (spec->host.p) {
+    case 1: return launch_keygen<1>(ctx, A, st);
+    case 2: return launch_keygen<2>(ctx, A, st);
+    case 3: return launch_keygen<3>(ctx, A, st);
+    case 4: return launch_keygen<4>(ctx, A, st);
+    default: return fail(FFSS_ERR_UNSUPPORTED, "payload p=%u", spec->host.p);
+  }
+}
+
 extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
                            uint64_t n, const uint64_t *x_plain, ffss_keys *k0, ffss_keys *k1,
                            uint64_t *x0, uint64_t *x1, void *stream) {
@@ -446,25 +471,8 @@ extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t s
   if (x_plain && (!x0 || !x1)) return fail(FFSS_ERR_INVALID, "ffss_keygen: x0/x1 needed with x_plain");
   if (int rc0 = check_device_spec(ctx, spec)) return rc0;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  KeygenArgs A;
-  memset(&A, 0, sizeof(A));
-  A.spec = spec->dev;
-  A.L = make_layout(spec->host, n);
-  A.k0 = k0->buf; A.k1 = k1->buf;
-  A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
-  A.n = n; A.e0 = 0; A.call_id = call_id;
-  A.n_items = (spec->host.M > 1 ? spec->host.M - 1 : 0) + spec->host.T + 1;
-  key_schedule(seed, A.rk.w);
-  A.t0 = ctx->t0_dev;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc;
-  switch (spec->host.p) {
-    case 1: rc = launch_keygen<1>(ctx, A, st); break;
-    case 2: rc = launch_keygen<2>(ctx, A, st); break;
-    case 3: rc = launch_keygen<3>(ctx, A, st); break;
-    case 4: rc = launch_keygen<4>(ctx, A, st); break;
-    default: return fail(FFSS_ERR_UNSUPPORTED, "payload p=%u", spec->host.p);
-  }
+  const int rc = keygen_raw(ctx, spec, seed, call_id, n, x_plain, k0->buf, k1->buf, x0, x1,
+                            static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   k0->generated = k1->generated = 1;
   k0->used = k1->used = 0;
@@ -614,6 +622,31 @@ static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st)
   return FFSS_OK;
 }
 
+// Fused two-party gate launch on raw key buffers (no handle checks).
+static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
+                         const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
+                         uint32_t *z0, uint32_t *z1, uint64_t *comm, cudaStream_t st) {
+  GateArgsS AS;
+  memset(&AS, 0, sizeof(AS));
+  GateArgs &A = AS.g;
+  A.spec = spec->dev; A.L = make_layout(spec->host, n);
+  A.k0 = k0; A.k1 = k1; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
+  A.comm = reinterpret_cast<unsigned long long *>(comm);
+  A.n = n; A.t0 = ctx->t0_dev;
+  AS.sched = ctx->force_slots ? make_sched(spec->host, ctx->force_slots, nullptr)
+                              : choose_sched(ctx, spec->host, n);
+  const uint32_t R = spec->host.r, D = spec->host.d;
+  if (R == 1 && D == 0) return launch_gate<1, 0>(ctx, AS, st);
+  if (R == 1 && D == 1) return launch_gate<1, 1>(ctx, AS, st);
+  if (R == 1 && D == 2) return launch_gate<1, 2>(ctx, AS, st);
+  if (R == 1 && D == 3) return launch_gate<1, 3>(ctx, AS, st);
+  if (R == 2 && D == 0) return launch_gate<2, 0>(ctx, AS, st);
+  if (R == 2 && D == 1) return launch_gate<2, 1>(ctx, AS, st);
+  if (R == 3 && D == 0) return launch_gate<3, 0>(ctx, AS, st);
+  if (R == 4 && D == 0) return launch_gate<4, 0>(ctx, AS, st);
+  return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
+}
+
 extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
                               const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0,
                               uint64_t *y1, uint32_t *z0, uint32_t *z1, uint64_t *comm, void *stream) {
@@ -625,26 +658,7 @@ extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k
   if (!rc) rc = check_keys(spec, k1, 1, n, 3);
   if (rc) return rc;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  GateArgsS AS;
-  memset(&AS, 0, sizeof(AS));
-  GateArgs &A = AS.g;
-  A.spec = spec->dev; A.L = make_layout(spec->host, n);
-  A.k0 = k0->buf; A.k1 = k1->buf; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
-  A.comm = reinterpret_cast<unsigned long long *>(comm);
-  A.n = n; A.t0 = ctx->t0_dev;
-  AS.sched = ctx->force_slots ? make_sched(spec->host, ctx->force_slots, nullptr)
-                              : choose_sched(ctx, spec->host, n);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const uint32_t R = spec->host.r, D = spec->host.d;
-  if (R == 1 && D == 0) rc = launch_gate<1, 0>(ctx, AS, st);
-  else if (R == 1 && D == 1) rc = launch_gate<1, 1>(ctx, AS, st);
-  else if (R == 1 && D == 2) rc = launch_gate<1, 2>(ctx, AS, st);
-  else if (R == 1 && D == 3) rc = launch_gate<1, 3>(ctx, AS, st);
-  else if (R == 2 && D == 0) rc = launch_gate<2, 0>(ctx, AS, st);
-  else if (R == 2 && D == 1) rc = launch_gate<2, 1>(ctx, AS, st);
-  else if (R == 3 && D == 0) rc = launch_gate<3, 0>(ctx, AS, st);
-  else if (R == 4 && D == 0) rc = launch_gate<4, 0>(ctx, AS, st);
-  else return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
+  rc = eval_pair_raw(ctx, spec, k0->buf, k1->buf, x0, x1, n, y0, y1, z0, z1, comm, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   k0->used |= 3;
   k1->used |= 3;
@@ -1060,6 +1074,7 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
 }
 
 #include "server.cuh"
+#include "compose.cuh"
 
 extern "C" int ffss_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0,
                                 const uint32_t *z1, uint64_t n, uint32_t n_out, uint64_t *y, uint32_t *z,

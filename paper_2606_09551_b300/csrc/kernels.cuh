@@ -120,7 +120,7 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // the walk at the cost of the bare AES chain plus a few operations per level;
 // inlined into the fused gate the compiler emitted about 40 % more
 // instructions per level.  One call per walk.
-__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint32_t u, const uint4 *root, uint64_t n,
+__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, uint64_t n,
                                           uint64_t vcw, const char *tab, uint32_t lane4) {
   const AesDcfInline aes{Tab{tab, lane4}};
   return dcf_bit_eval(b, f, u, root, n, vcw, aes);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
   const char *l = kb + L.off_l[j];
   const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
   const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e;
-  dcf_vec_eval_acc<P>(b, k, view(xhat, k, 0), root, vcw, L.n, acc, aes);
+  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, L.n, acc, aes);   // lookups: k <= 32
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       const uint64_t alpha = j < 0 ? (r_in & mask) : (((r_in & mask) + S.prim_gamma[j]) & mask);
       const uint4 s0 = prg(S.base_roots + 2 * t), s1 = prg(S.base_roots + 2 * t + 1);
       char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
-      dcf_bit_gen(f, uint32_t(alpha), s0, s1, reinterpret_cast<uint4 *>(q0) + e,
+      dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
                   reinterpret_cast<uint4 *>(q1) + e,
                   reinterpret_cast<uint64_t *>(q0 + 16ull * (f + 1) * n) + e,
                   reinterpret_cast<uint64_t *>(q1 + 16ull * (f + 1) * n) + e, n, rkd);

@@ -11,7 +11,8 @@
 
 namespace ffss {
 
-constexpr int kMaxK = 32;
+constexpr int kMaxK = 63;         // comparison views; a spec with an interval lookup keeps k <= kMaxKLookup
+constexpr int kMaxKLookup = 32;
 constexpr int kMaxM = 16;
 constexpr int kMaxP = 4;
 constexpr int kMaxT = 32;

@@ -133,6 +133,13 @@ def lib():
         L.ffss_server_summary.argtypes = [vp, C.POINTER(ServerStats)]
         L.ffss_batch_eval_noalloc.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
         L.ffss_microbench.argtypes = [vp, C.c_int, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.ffss_beaver_keygen.argtypes = [vp, C.POINTER(C.c_uint8), C.c_uint32, C.c_uint64, vp, vp, vp]
+        L.ffss_beaver_mul.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_uint64, C.c_uint64, vp, vp, vp, vp]
+        L.ffss_softmax_create.argtypes = [vp, C.POINTER(vp), C.c_uint64, C.c_uint64, C.POINTER(vp)]
+        L.ffss_softmax_keygen.argtypes = [vp, C.POINTER(C.c_uint8), C.c_uint32, vp]
+        L.ffss_softmax_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.ffss_softmax_info.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+        L.ffss_softmax_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -389,6 +396,57 @@ def reconstruct(y0, y1, z0, z1, n_out: int, y, z, stream=None):
     n = z0.numel() if z0 is not None else y0.numel() // n_out
     _check(lib().ffss_reconstruct(_ptr(y0), _ptr(y1), _ptr(z0), _ptr(z1), n, n_out, _ptr(y), _ptr(z),
                                   _stream(stream)))
+
+
+def _seed(seed: bytes):
+    return (C.c_uint8 * 16)(*bytes(seed))
+
+
+def beaver_keygen(ctx: Context, seed: bytes, call_id: int, n: int, t0, t1, stream=None):
+    """Deal Beaver triples for n products into t0, t1 (uint64 device tensors of 3 n)."""
+    _check(lib().ffss_beaver_keygen(ctx.h, _seed(seed), call_id, n, _ptr(t0), _ptr(t1), _stream(stream)))
+
+
+def beaver_mul(ctx: Context, t0, t1, x0, x1, y0, y1, z0, z1, group: int = 1, comm=None, stream=None):
+    """Shares of z = x * y[e // group] (uint64 device tensors)."""
+    _check(lib().ffss_beaver_mul(ctx.h, _ptr(t0), _ptr(t1), _ptr(x0), _ptr(x1), _ptr(y0), _ptr(y1), x0.numel(),
+                                 group, _ptr(z0), _ptr(z1), _ptr(comm), _stream(stream)))
+
+
+class Softmax:
+    """The softmax block over rows of shared values (plan with its own keys
+    and scratch).  gates: CompiledSpecs for relu, exp, shift_e, recip,
+    shift_t, shift_p (in that order)."""
+
+    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, L: int):
+        self.ctx, self.rows, self.L = ctx, rows, L
+        self._gates = list(gates)
+        arr = (vp * 6)(*[g.h for g in self._gates])
+        h = vp()
+        _check(lib().ffss_softmax_create(ctx.h, arr, rows, L, C.byref(h)))
+        self.h = h
+
+    def keygen(self, seed: bytes, call_base: int, stream=None):
+        _check(lib().ffss_softmax_keygen(self.h, _seed(seed), call_base, _stream(stream)))
+
+    def eval(self, x0, x1, y0, y1, comm=None, stream=None):
+        _check(lib().ffss_softmax_eval(self.h, _ptr(x0), _ptr(x1), _ptr(y0), _ptr(y1), _ptr(comm), _stream(stream)))
+
+    def info(self):
+        r, kb, ge = C.c_uint32(), C.c_uint64(), C.c_uint64()
+        _check(lib().ffss_softmax_info(self.h, C.byref(r), C.byref(kb), C.byref(ge)))
+        return {"rounds": r.value, "key_bytes": kb.value, "gate_elements": ge.value}
+
+    def close(self):
+        if self.h:
+            lib().ffss_softmax_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def microbench(ctx: Context, which: int, iters: int):

@@ -83,7 +83,15 @@ def _specs():
           dataclasses.replace(pw[1], name=pw[1].name + "_trunc7", trunc_shift=7, trunc_signed=False),
           dataclasses.replace(out[8], name=out[8].name + "_xhat_ars3", trunc_shift=3, trunc_signed=True,
                               xhat_basis=True)]
-    return out + pw + tr
+    # views wider than 32 bits: shift gates and predicates of single-interval specs
+    rng2 = np.random.default_rng(63)
+    wide = [S.trunc(63, 45, True), S.trunc(48, 20, False), S.trunc(40, 24, True),
+            S.OperatorSpec("wide50", k=50, frac_bits=0, out_frac_bits=0, m=1, degree=2, n_out=1,
+                           alpha=[0, 1 << 50], coeff=rng2.integers(0, 2 ** 64, size=(1, 1, 3), dtype=np.uint64),
+                           partition_bits=False,
+                           preds=[S.PredDesc(50, 0, 1 << 49, 1), S.PredDesc(50, 12345, (1 << 49) + 77, 0),
+                                  S.PredDesc(37, 999, 5 << 30, 1)])]
+    return out + pw + tr + wide
 
 
 SPECS = _specs()
