@@ -140,3 +140,82 @@ def softmax_plain(g, x):
     P = E * t[:, None]
     Y = ev("shift_p", P).reshape(rows, L)
     return Y, dict(m=m, E=E, s=s, t=t, P=P)
+
+
+# --------------------------------------------------------------------------
+# LayerNorm (App. G: mean and variance are linear, 1/sqrt is a scalar gate)
+# --------------------------------------------------------------------------
+#
+# On X [rows, H] at f fractional bits, with c_H = round(2^s_mu / H) public and
+# g mapping shift_mu, shift_var, rsqrt, shift_r, shift_y to oracle specs:
+#   1. mu = shift_mu(rowsum(X) * c_H)               (the mean at f bits)
+#   2. D = X - mu
+#   3. Q = D * D                                     (Beaver, elementwise)
+#   4. var = shift_var(rowsum(Q) * c_H) + eps        (the variance at f bits)
+#   5. r = shift_r(rsqrt(var))
+#   6. Y = shift_y(D * r)                            (Beaver, r broadcast)
+# Products by the public c_H are local (each party scales its share); every
+# shift rounds to nearest as in the softmax block.  Dealer call ids:
+# call_base + j for the j-th drawing step (shift_mu, the square, shift_var,
+# rsqrt, shift_r, the product, shift_y).
+
+def layernorm_pair(g, seed, call_base, x0, x1, c_H: int, eps: int = 0):
+    """Both parties' shares of the LayerNorm pipeline on shares x0, x1 [rows, H]."""
+    x0 = np.asarray(x0, np.uint64)
+    x1 = np.asarray(x1, np.uint64)
+    rows, H = x0.shape
+    cH = np.uint64(c_H)
+    comm = np.zeros(2, np.uint64)
+    cid = call_base
+    steps = {}
+
+    def gate(name, a0, a1):
+        nonlocal cid, comm
+        if g[name].trunc_s:
+            a0 = a0 + np.uint64(1 << (g[name].trunc_s - 1))
+        r0, r1, cm = _gate(g[name], seed, cid, a0, a1)
+        cid += 1
+        comm = comm + cm
+        steps[name] = (r0, r1)
+        return r0, r1
+
+    def mul(a0, a1, b0, b1, group):
+        nonlocal cid, comm
+        T0, T1 = beaver_dealer(seed, cid, 0, a0.size)
+        cid += 1
+        z0, z1, cm = beaver_mul(T0, T1, a0, a1, b0, b1, group)
+        comm = comm + cm
+        return z0, z1
+
+    mu0, mu1 = gate("shift_mu", x0.sum(axis=1, dtype=np.uint64) * cH, x1.sum(axis=1, dtype=np.uint64) * cH)
+    D0, D1 = x0 - mu0[:, None], x1 - mu1[:, None]
+    Q0, Q1 = mul(D0.reshape(-1), D1.reshape(-1), D0.reshape(-1), D1.reshape(-1), 1)
+    v0, v1 = gate("shift_var", Q0.reshape(rows, H).sum(axis=1, dtype=np.uint64) * cH,
+                  Q1.reshape(rows, H).sum(axis=1, dtype=np.uint64) * cH)
+    v0 = v0 + np.uint64(eps)
+    r0, r1 = gate("rsqrt", v0, v1)
+    r0, r1 = gate("shift_r", r0, r1)
+    P0, P1 = mul(D0.reshape(-1), D1.reshape(-1), r0, r1, H)
+    Y0, Y1 = gate("shift_y", P0, P1)
+    steps.update(mu=(mu0, mu1), var=(v0, v1))
+    return Y0.reshape(rows, H), Y1.reshape(rows, H), comm, steps
+
+
+def layernorm_plain(g, x, c_H: int, eps: int = 0):
+    """The same pipeline on plaintext integers."""
+    x = np.asarray(x, np.uint64)
+    rows, H = x.shape
+    cH = np.uint64(c_H)
+
+    def ev(name, v):
+        v = np.asarray(v, np.uint64).reshape(-1)
+        if g[name].trunc_s:
+            v = v + np.uint64(1 << (g[name].trunc_s - 1))
+        return g[name].plain_eval(v)[0][:, 0]
+
+    mu = ev("shift_mu", x.sum(axis=1, dtype=np.uint64) * cH)
+    D = x - mu[:, None]
+    var = ev("shift_var", (D * D).sum(axis=1, dtype=np.uint64) * cH) + np.uint64(eps)
+    r = ev("shift_r", ev("rsqrt", var))
+    Y = ev("shift_y", D * r[:, None]).reshape(rows, H)
+    return Y, dict(mu=mu, var=var, r=r)

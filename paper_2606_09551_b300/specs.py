@@ -312,6 +312,26 @@ def softmax_specs(f: int = 12) -> Dict[str, OperatorSpec]:
             "shift_p": trunc(40, 16 + 20 - f, True, name=f"ars40_{16 + 20 - f}")}
 
 
+def layernorm_specs(H: int, f: int = 12) -> Tuple[Dict[str, OperatorSpec], int]:
+    """The gates of a fixed-point LayerNorm over rows of H values (App. G),
+    with the public constant c_H = round(2^24 / H) that turns a row sum into a
+    mean: shift_mu (ARS by 24, 48-bit view) for the mean; shift_var (ARS by
+    24 + f, 56-bit view) for the variance from a row sum of squares at 2f
+    bits; rsqrt (k 24, f) at its fitted scale F_r; shift_r (ARS by F_r - 20,
+    63-bit view) for 1/sqrt at 20 bits; shift_y (ARS by 20, 48-bit view) for
+    the normalised output at f bits.  The values stay inside the views
+    while |x - mu| < 11 real units (the scaled sum of squares, about
+    max|x - mu|^2 * 2^48, stays below 2^55) and the variance is at least 1/8
+    (the range of the rsqrt fit)."""
+    rs = rsqrt16(f=f)
+    c_H = int(round(2 ** 24 / H))
+    return ({"shift_mu": trunc(48, 24, True, name="ars48_24"),
+             "shift_var": trunc(56, 24 + f, True, name=f"ars56_{24 + f}"),
+             "rsqrt": rs,
+             "shift_r": trunc(63, rs.out_frac_bits - 20, True, name=f"ars63_{rs.out_frac_bits - 20}"),
+             "shift_y": trunc(48, 20, True, name="ars48_20")}, c_H)
+
+
 def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,
                 partition_bits: bool = True, n_extra: int = 0, name: str = "random") -> OperatorSpec:
     """A random well-formed spec: distinct sorted boundaries, uniform Z_{2^64}

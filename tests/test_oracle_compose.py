@@ -80,3 +80,35 @@ def test_softmax_accuracy_against_float():
     ref /= ref.sum(axis=1, keepdims=True)
     assert np.abs(got - ref).max() < 3e-3
     assert np.abs(got.sum(axis=1) - 1.0).max() < 1e-2
+
+
+@pytest.mark.parametrize("rows,H", [(3, 1), (4, 5), (3, 768)])
+def test_layernorm_pair_equals_plain(rows, H):
+    """LayerNorm composition (App. G): shares reconstruct to the plaintext
+    pipeline exactly; the mean is the rounded row mean; bytes = the gates'
+    closed forms plus 16 per Beaver product."""
+    sp, cH = S.layernorm_specs(H)
+    g = {k: O.Spec(**v.descriptor()) for k, v in sp.items()}
+    rng = np.random.default_rng(rows * 7 + H)
+    h = 1.3 * rng.standard_normal((rows, H)) + 0.4
+    x = S.encode(h.reshape(-1), 12).reshape(rows, H)
+    x0 = rng.integers(0, 2 ** 64, size=(rows, H), dtype=np.uint64)
+    y0, y1, comm, st = C.layernorm_pair(g, SEED, 900, x0, x - x0, cH)
+    yp, plain = C.layernorm_plain(g, x, cH)
+    assert np.array_equal(y0 + y1, yp)
+    mu = (st["mu"][0] + st["mu"][1]).view(np.int64)
+    sx = x.view(np.int64).sum(axis=1)
+    assert np.array_equal(mu, np.floor((sx * cH + 2 ** 23) / 2 ** 24).astype(np.int64))
+    want = rows * (9 + 9 + (8 + 48) + 9) + rows * H * (16 + 16 + 9)
+    assert list(comm) == [want] * 2
+
+
+def test_layernorm_accuracy_against_float():
+    sp, cH = S.layernorm_specs(768)
+    g = {k: O.Spec(**v.descriptor()) for k, v in sp.items()}
+    rng = np.random.default_rng(5)
+    h = rng.standard_normal((8, 768)) * np.linspace(0.5, 3, 8)[:, None] + np.linspace(-2, 2, 8)[:, None]
+    x = S.encode(h.reshape(-1), 12).reshape(8, 768)
+    yp, _ = C.layernorm_plain(g, x, cH)
+    ref = (h - h.mean(axis=1, keepdims=True)) / np.sqrt(h.var(axis=1, keepdims=True) + 1e-5)
+    assert np.abs(yp.view(np.int64) / 2.0 ** 12 - ref).max() < 5e-3
