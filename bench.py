@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
     ap.add_argument("--no-xhat", action="store_true", help="skip the x^-basis variant run")
     ap.add_argument("--no-rescale", action="store_true", help="skip the layer-rescale (ARS) run")
+    ap.add_argument("--no-blocks", action="store_true", help="skip the softmax / LayerNorm block runs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
@@ -498,6 +499,9 @@ def run_ours(args, rank, world, local_rank):
     rescale = None
     if not args.no_rescale:
         rescale = run_rescales(ctx, args, dev, stream, world)
+    blocks = None
+    if not args.no_blocks:
+        blocks = run_blocks(ctx, args, dev, stream, world)
 
     served = large = gpt2 = None
     if not args.no_served:
@@ -576,6 +580,7 @@ def run_ours(args, rank, world, local_rank):
         "gpt2_batch": gpt2,
         "xhat_variant": xhat,
         "rescale": rescale,
+        "blocks": blocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(calls, args.cpu_seconds)
@@ -687,6 +692,95 @@ def run_rescales(ctx, args, dev, stream, world):
     del sets
     torch.cuda.empty_cache()
     return res
+
+
+def run_blocks(ctx, args, dev, stream, world):
+    """The composed blocks of one BERT-base layer at seq 128: attention
+    softmax over 12 x 128 rows of 128 scores, and one LayerNorm over 128
+    rows of 768.  Fresh keys are dealt (untimed) before each evaluation;
+    CUDA events bracket the evaluations only."""
+    import numpy as np
+    import torch
+
+    from paper_2606_09551_b300 import fusefss as F
+    from paper_2606_09551_b300 import inputs as I
+    from paper_2606_09551_b300 import specs as S
+    rng = np.random.default_rng(I.MASTER_SEED + 7)
+    out = {}
+
+    def timed(plan, x, n, call_base):
+        x0 = rng.integers(0, 2 ** 64, size=x.size, dtype=np.uint64)
+        X0 = torch.from_numpy(x0).to(dev)
+        X1 = torch.from_numpy(x.reshape(-1) - x0).to(dev)
+        Y0 = torch.empty(n, dtype=torch.uint64, device=dev)
+        Y1 = torch.empty_like(Y0)
+        comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+        plan.keygen(I.KEY_SEED, call_base)
+        plan.eval(X0, X1, Y0, Y1)                       # warm-up
+        total = 0.0
+        for s_ in range(args.steps):
+            plan.keygen(I.KEY_SEED, call_base + 64 * (s_ + 1))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            plan.eval(X0, X1, Y0, Y1, comm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        ms = max_over_ranks(total / args.steps, world, dev)
+        y = (Y0.cpu().numpy() + Y1.cpu().numpy()).view(np.int64) / 2.0 ** 12
+        return ms, y, int(comm.cpu().tolist()[0]) // args.steps
+
+    def aes_of(gates, counts):
+        return sum(2 * g.shape.aes_per_elem * c for g, c in zip(gates, counts))
+
+    # softmax
+    rows, L = 12 * 128, 128
+    sp = S.softmax_specs()
+    names = ["relu", "exp", "shift_e", "recip", "shift_t", "shift_p"]
+    gates = [F.CompiledSpec(sp[k], ctx) for k in names]
+    sm = F.Softmax(ctx, gates, rows, L)
+    scores = 2.0 * rng.standard_normal((rows, L))
+    ms, y, cb = timed(sm, S.encode(scores.reshape(-1), 12), rows * L, 2000)
+    ref = np.exp(scores - scores.max(axis=1, keepdims=True))
+    ref /= ref.sum(axis=1, keepdims=True)
+    tree = 0
+    n = L
+    while n > 1:
+        tree += rows * (n // 2)
+        n = n // 2 + n % 2
+    aes = aes_of(gates, [tree, rows * L, rows * L, rows, rows, rows * L])
+    info = sm.info()
+    out["softmax"] = {"value": aggregate(rows * L, ms, world), "unit": "elements/s", "ms_per_block": ms,
+                      "shape": [rows, L], "tree_rounds": info["rounds"], "gate_elements": info["gate_elements"],
+                      "key_bytes": info["key_bytes"], "comm_bytes_per_party": cb,
+                      "comm_bytes_per_elem_per_party": cb / (rows * L),
+                      "aes_blocks": aes, "aes_roofline_frac": aes / (ms * 1e-3) / _aes_roofline(),
+                      "max_abs_err_vs_float64": float(np.abs(y.reshape(rows, L) - ref).max()),
+                      "form": "comparison-tree max (ReLU gates), nExp, row sums, Recip, Beaver product, "
+                              "rounding shift gates; one plan, keys dealt before each evaluation"}
+    sm.close()
+    # LayerNorm
+    rows, H = 128, 768
+    lsp, cH = S.layernorm_specs(H)
+    names = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
+    gates = [F.CompiledSpec(lsp[k], ctx) for k in names]
+    ln = F.LayerNorm(ctx, gates, rows, H, cH)
+    hid = rng.standard_normal((rows, H)) * 1.2 + 0.3
+    ms, y, cb = timed(ln, S.encode(hid.reshape(-1), 12), rows * H, 3000)
+    ref = (hid - hid.mean(axis=1, keepdims=True)) / np.sqrt(hid.var(axis=1, keepdims=True) + 1e-5)
+    aes = aes_of(gates, [rows, rows, rows, rows, rows * H])
+    info = ln.info()
+    out["layernorm"] = {"value": aggregate(rows * H, ms, world), "unit": "elements/s", "ms_per_block": ms,
+                        "shape": [rows, H], "gate_elements": info["gate_elements"], "key_bytes": info["key_bytes"],
+                        "comm_bytes_per_party": cb, "comm_bytes_per_elem_per_party": cb / (rows * H),
+                        "aes_blocks": aes, "aes_roofline_frac": aes / (ms * 1e-3) / _aes_roofline(),
+                        "max_abs_err_vs_float64": float(np.abs(y.reshape(rows, H) - ref).max()),
+                        "form": "row mean and variance by local sums, Beaver square, Rsqrt, Beaver product, "
+                                "rounding shift gates (no affine weights)"}
+    ln.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _aes_roofline():

@@ -414,6 +414,28 @@ int ffss_softmax_info(const ffss_softmax *sm, uint32_t *rounds, uint64_t *key_by
                       uint64_t *gate_elements);
 int ffss_softmax_destroy(ffss_softmax *sm);
 
+/* LayerNorm over rows of H shared fixed-point values (App. G: mean and
+ * variance are linear, 1/sqrt is a scalar gate), without the affine
+ * weights; c_H is the public constant round(2^s / H) that turns a row sum
+ * into a mean at the shift s of gates[0]:
+ *   1. mu = gates[0](rowsum(X) c_H + h0);  2. D = X - mu;
+ *   3. Q = D * D (Beaver);  4. var = gates[1](rowsum(Q) c_H + h1) + eps;
+ *   5. r = gates[3](gates[2](var) + h3)   (Rsqrt, then a shift);
+ *   6. Y = gates[4](D * r + h4)   (Beaver, r broadcast over the row),
+ * with h_i = 2^(s_i - 1) added by party 0 (round to nearest) and eps a
+ * public constant added by party 0.  gates[2] must have n_out = 1; the
+ * others must be shift gates.  Keys: step j (gates[0], the square, gates[1],
+ * gates[2], gates[3], the product, gates[4]) is dealer call call_base + j;
+ * one-time as for the softmax plan. */
+typedef struct ffss_layernorm ffss_layernorm;
+int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], uint64_t rows, uint64_t H,
+                          uint64_t c_H, uint64_t eps, ffss_layernorm **out);
+int ffss_layernorm_keygen(ffss_layernorm *ln, const uint8_t seed[16], uint32_t call_base, void *stream);
+int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                        uint64_t *y1, uint64_t *comm, void *stream);
+int ffss_layernorm_info(const ffss_layernorm *ln, uint64_t *key_bytes, uint64_t *gate_elements);
+int ffss_layernorm_destroy(ffss_layernorm *ln);
+
 /* ---- measurement support ------------------------------------------------ */
 
 /* Micro-benchmarks behind the roofline figures (no counterpart in the paper,

@@ -122,9 +122,10 @@ __global__ void row_sub_kernel(const uint64_t *x0, const uint64_t *x1, const uin
   }
 }
 
-// s[row] = sum of the row's L values; one warp per row.
-__global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t rows, uint64_t L, uint64_t *s0,
-                               uint64_t *s1) {
+// s[row] = scale * (sum of the row's L values), scale a public constant
+// (each party scales its own share); one warp per row.
+__global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t rows, uint64_t L, uint64_t scale,
+                               uint64_t *s0, uint64_t *s1) {
   const uint32_t lane = threadIdx.x & 31u;
   for (uint64_t r = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; r < rows;
        r += uint64_t(gridDim.x) * blockDim.x / 32) {
@@ -139,8 +140,8 @@ __global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t 
       b += __shfl_xor_sync(0xffffffffu, b, off);
     }
     if (lane == 0) {
-      s0[r] = a;
-      s1[r] = b;
+      s0[r] = a * scale;
+      s1[r] = b * scale;
     }
   }
 }
@@ -361,7 +362,7 @@ extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uin
   add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(E0, N, half(kSmShiftE));
   if (int rc = gate(E0, E1, F0, F1)) return rc;
   // (4) s = row sums; (5) t = shift_t(recip(s) + half)
-  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(F0, F1, rows, L, s0, s1);
+  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(F0, F1, rows, L, 1, s0, s1);
   if (int rc = gate(s0, s1, t0, t1)) return rc;
   add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(t0, rows, half(kSmShiftT));
   if (int rc = gate(t0, t1, u0, u1)) return rc;
@@ -377,5 +378,167 @@ extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uin
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
   sm->keyed = 0;   // one-time keys
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host: the LayerNorm block
+// ---------------------------------------------------------------------------
+
+enum { kLnShiftMu, kLnShiftVar, kLnRsqrt, kLnShiftR, kLnShiftY, kLnGates };
+
+struct ffss_layernorm {
+  ffss_ctx *ctx;
+  const ffss_spec *g[kLnGates];
+  uint64_t rows, H, c_H, eps;
+  struct Step {
+    const ffss_spec *spec;           // nullptr: a Beaver multiplication
+    uint64_t n, off0, off1;
+  };
+  std::vector<Step> steps;           // shift_mu, square, shift_var, rsqrt, shift_r, product, shift_y
+  char *keys;
+  uint64_t key_bytes;
+  uint64_t *sh;
+  uint32_t *z;
+  int keyed;
+};
+
+extern "C" int ffss_layernorm_destroy(ffss_layernorm *ln) {
+  if (!ln) return FFSS_OK;
+  cudaSetDevice(ln->ctx->device);
+  if (ln->keys) cudaFree(ln->keys);
+  if (ln->sh) cudaFree(ln->sh);
+  if (ln->z) cudaFree(ln->z);
+  delete ln;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], uint64_t rows, uint64_t H,
+                                     uint64_t c_H, uint64_t eps, ffss_layernorm **out) {
+  if (!ctx || !gates || !out) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create: NULL argument");
+  if (rows == 0 || H == 0) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_create: rows and H must be >= 1");
+  for (int i = 0; i < kLnGates; ++i) {
+    if (!gates[i]) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create: gate %d is NULL", i);
+    if (int rc = check_device_spec(ctx, gates[i])) return rc;
+    if (gates[i]->host.r != 1) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_create: gate %d must have n_out = 1", i);
+    if (i != kLnRsqrt && gates[i]->host.trunc_s == 0)
+      return fail(FFSS_ERR_SHAPE, "ffss_layernorm_create: gate %d must be a shift gate", i);
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  ffss_layernorm *ln = new ffss_layernorm();
+  ln->ctx = ctx;
+  for (int i = 0; i < kLnGates; ++i) ln->g[i] = gates[i];
+  ln->rows = rows; ln->H = H; ln->c_H = c_H; ln->eps = eps;
+  const uint64_t N = rows * H;
+  uint64_t off = 0;
+  auto add = [&](const ffss_spec *spec, uint64_t n) {
+    const uint64_t b = spec ? make_layout(spec->host, n).total : align256(24 * n);
+    ln->steps.push_back({spec, n, off, off + b});
+    off += 2 * b;
+  };
+  add(gates[kLnShiftMu], rows);
+  add(nullptr, N);
+  add(gates[kLnShiftVar], rows);
+  add(gates[kLnRsqrt], rows);
+  add(gates[kLnShiftR], rows);
+  add(nullptr, N);
+  add(gates[kLnShiftY], N);
+  ln->key_bytes = off;
+  // scratch, both parties (the carve-up of ffss_layernorm_eval): D, Q, P N each;
+  // sums and the per-row chain 6 x rows
+  const uint64_t words = 2 * (3 * N + 6 * rows);
+  cudaError_t e = cudaMalloc(&ln->keys, ln->key_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&ln->sh, words * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&ln->z, 2 * N * 4);
+  if (e != cudaSuccess) {
+    ffss_layernorm_destroy(ln);
+    return fail(FFSS_ERR_CUDA, "ffss_layernorm_create: %s", cudaGetErrorString(e));
+  }
+  *out = ln;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_info(const ffss_layernorm *ln, uint64_t *key_bytes, uint64_t *gate_elements) {
+  if (!ln) return fail(FFSS_ERR_INVALID, "ffss_layernorm_info: NULL argument");
+  if (key_bytes) *key_bytes = ln->key_bytes;
+  if (gate_elements) {
+    uint64_t t = 0;
+    for (const auto &s : ln->steps) t += s.spec ? s.n : 0;
+    *gate_elements = t;
+  }
+  return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_keygen(ffss_layernorm *ln, const uint8_t seed[16], uint32_t call_base, void *stream) {
+  if (!ln || !seed) return fail(FFSS_ERR_INVALID, "ffss_layernorm_keygen: NULL argument");
+  CUDA_TRY(cudaSetDevice(ln->ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (size_t j = 0; j < ln->steps.size(); ++j) {
+    const auto &s = ln->steps[j];
+    int rc;
+    if (s.spec)
+      rc = keygen_raw(ln->ctx, s.spec, seed, call_base + uint32_t(j), s.n, nullptr, ln->keys + s.off0,
+                      ln->keys + s.off1, nullptr, nullptr, st);
+    else
+      rc = beaver_keygen_raw(ln->ctx, seed, call_base + uint32_t(j), s.n,
+                             reinterpret_cast<uint64_t *>(ln->keys + s.off0),
+                             reinterpret_cast<uint64_t *>(ln->keys + s.off1), st);
+    if (rc) return rc;
+  }
+  ln->keyed = 1;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                                   uint64_t *y1, uint64_t *comm, void *stream) {
+  if (!ln || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_layernorm_eval: NULL argument");
+  if (!ln->keyed) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_eval: keys not generated (or already used)");
+  const ffss_ctx *ctx = ln->ctx;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t rows = ln->rows, H = ln->H, N = rows * H;
+  uint64_t *p = ln->sh;
+  auto take = [&](uint64_t words) { uint64_t *q = p; p += words; return q; };
+  uint64_t *D0 = take(N), *D1 = take(N), *Q0 = take(N), *Q1 = take(N), *P0 = take(N), *P1 = take(N);
+  uint64_t *a0 = take(rows), *a1 = take(rows), *m0 = take(rows), *m1 = take(rows);
+  uint64_t *v0 = take(rows), *v1 = take(rows), *w0 = take(rows), *w1 = take(rows);
+  uint64_t *q0 = take(rows), *q1 = take(rows), *r0 = take(rows), *r1 = take(rows);
+  uint32_t *z0 = ln->z, *z1 = ln->z + N;
+  const int TB = 256;
+  size_t j = 0;
+  auto half = [&](int g) { return uint64_t(1) << (ln->g[g]->host.trunc_s - 1); };
+  auto gate = [&](const uint64_t *b0, const uint64_t *b1, uint64_t *o0, uint64_t *o1) {
+    const auto &s = ln->steps[j++];
+    return eval_pair_raw(ctx, s.spec, ln->keys + s.off0, ln->keys + s.off1, b0, b1, s.n, o0, o1, z0, z1, comm, st);
+  };
+  auto mul = [&](const uint64_t *b0, const uint64_t *b1, const uint64_t *c0, const uint64_t *c1, uint64_t group,
+                 uint64_t *o0, uint64_t *o1) {
+    const auto &s = ln->steps[j++];
+    return beaver_mul_raw(ctx, reinterpret_cast<const uint64_t *>(ln->keys + s.off0),
+                          reinterpret_cast<const uint64_t *>(ln->keys + s.off1), b0, b1, c0, c1, s.n, group, o0, o1,
+                          comm, st);
+  };
+  // (1) mu = shift_mu(rowsum(X) c_H + half)
+  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(x0, x1, rows, H, ln->c_H, a0, a1);
+  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(a0, rows, half(kLnShiftMu));
+  if (int rc = gate(a0, a1, m0, m1)) return rc;
+  // (2) D = X - mu; (3) Q = D * D
+  row_sub_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(x0, x1, m0, m1, rows, H, D0, D1);
+  if (int rc = mul(D0, D1, D0, D1, 1, Q0, Q1)) return rc;
+  // (4) var = shift_var(rowsum(Q) c_H + half) + eps
+  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(Q0, Q1, rows, H, ln->c_H, v0, v1);
+  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(v0, rows, half(kLnShiftVar));
+  if (int rc = gate(v0, v1, w0, w1)) return rc;
+  if (ln->eps) add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(w0, rows, ln->eps);
+  // (5) r = shift_r(rsqrt(var) + half)
+  if (int rc = gate(w0, w1, q0, q1)) return rc;
+  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(q0, rows, half(kLnShiftR));
+  if (int rc = gate(q0, q1, r0, r1)) return rc;
+  // (6) Y = shift_y(D * r + half), r broadcast over the row
+  if (int rc = mul(D0, D1, r0, r1, H, P0, P1)) return rc;
+  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kLnShiftY));
+  if (int rc = gate(P0, P1, y0, y1)) return rc;
+  CUDA_TRY(cudaGetLastError());
+  ln->keyed = 0;
   return FFSS_OK;
 }

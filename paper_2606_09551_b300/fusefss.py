@@ -140,6 +140,12 @@ def lib():
         L.ffss_softmax_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.ffss_softmax_info.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
         L.ffss_softmax_destroy.argtypes = [vp]
+        L.ffss_layernorm_create.argtypes = [vp, C.POINTER(vp), C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                            C.POINTER(vp)]
+        L.ffss_layernorm_keygen.argtypes = [vp, C.POINTER(C.c_uint8), C.c_uint32, vp]
+        L.ffss_layernorm_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.ffss_layernorm_info.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+        L.ffss_layernorm_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -440,6 +446,43 @@ class Softmax:
     def close(self):
         if self.h:
             lib().ffss_softmax_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LayerNorm:
+    """The LayerNorm block over rows of H shared values (plan with its own
+    keys and scratch).  gates: CompiledSpecs for shift_mu, shift_var, rsqrt,
+    shift_r, shift_y (in that order); c_H = round(2^s_mu / H)."""
+
+    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, H: int, c_H: int, eps: int = 0):
+        self.ctx, self.rows, self.H = ctx, rows, H
+        self._gates = list(gates)
+        arr = (vp * 5)(*[g.h for g in self._gates])
+        h = vp()
+        _check(lib().ffss_layernorm_create(ctx.h, arr, rows, H, c_H, eps, C.byref(h)))
+        self.h = h
+
+    def keygen(self, seed: bytes, call_base: int, stream=None):
+        _check(lib().ffss_layernorm_keygen(self.h, _seed(seed), call_base, _stream(stream)))
+
+    def eval(self, x0, x1, y0, y1, comm=None, stream=None):
+        _check(lib().ffss_layernorm_eval(self.h, _ptr(x0), _ptr(x1), _ptr(y0), _ptr(y1), _ptr(comm),
+                                         _stream(stream)))
+
+    def info(self):
+        kb, ge = C.c_uint64(), C.c_uint64()
+        _check(lib().ffss_layernorm_info(self.h, C.byref(kb), C.byref(ge)))
+        return {"key_bytes": kb.value, "gate_elements": ge.value}
+
+    def close(self):
+        if self.h:
+            lib().ffss_layernorm_destroy(self.h)
             self.h = None
 
     def __del__(self):

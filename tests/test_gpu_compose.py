@@ -95,3 +95,35 @@ def test_softmax_rejects_non_shift_gates(ctx):
     bad[2] = gates[1]           # the nExp gate where a shift gate belongs
     with pytest.raises(F.FfssError):
         F.Softmax(ctx, bad, 2, 8)
+
+
+@pytest.mark.parametrize("rows,H", [(3, 1), (4, 5), (16, 768)])
+def test_layernorm_matches_oracle(ctx, rows, H):
+    import torch
+    sp, cH = S.layernorm_specs(H)
+    order = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
+    gates = [F.CompiledSpec(sp[k], ctx) for k in order]
+    og = {k: O.Spec(**sp[k].descriptor()) for k in order}
+    rng = np.random.default_rng(rows * 31 + H)
+    h = 1.3 * rng.standard_normal((rows, H)) + 0.4
+    x = S.encode(h.reshape(-1), 12).reshape(rows, H)
+    x0 = rng.integers(0, 2 ** 64, size=(rows, H), dtype=np.uint64)
+    x1 = x - x0
+    ln = F.LayerNorm(ctx, gates, rows, H, cH)
+    ln.keygen(SEED, 800)
+    dev = "cuda:0"
+    X0, X1 = torch.from_numpy(x0.reshape(-1)).to(dev), torch.from_numpy(x1.reshape(-1)).to(dev)
+    Y0 = torch.empty(rows * H, dtype=torch.uint64, device=dev)
+    Y1 = torch.empty_like(Y0)
+    comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+    ln.eval(X0, X1, Y0, Y1, comm)
+    torch.cuda.synchronize()
+    r0, r1, rcomm, _ = OC.layernorm_pair(og, SEED, 800, x0, x1, cH)
+    assert np.array_equal(Y0.cpu().numpy(), r0.reshape(-1))
+    assert np.array_equal(Y1.cpu().numpy(), r1.reshape(-1))
+    assert list(comm.cpu().numpy()) == list(rcomm)
+    yp, _ = OC.layernorm_plain(og, x, cH)
+    assert np.array_equal(Y0.cpu().numpy() + Y1.cpu().numpy(), yp.reshape(-1))
+    with pytest.raises(F.FfssError):
+        ln.eval(X0, X1, Y0, Y1)
+    ln.close()
