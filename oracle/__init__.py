@@ -46,7 +46,8 @@ def lib():
         L.or_dcf_key_size.restype = C.c_size_t
         L.or_spec_size.restype = C.c_size_t
         L.or_elem_keys_size.restype = C.c_size_t
-        L.or_dcf_gen.argtypes = [C.c_int, C.c_uint64, C.c_int, u64p, u8p, u8p, C.c_void_p, C.c_void_p]
+        L.or_dcf_gen.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_int, u64p, u8p, u8p, u8p, C.c_void_p, C.c_void_p]
+        L.or_elem_keys_size.argtypes = [C.c_void_p]
         L.or_dcf_eval.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.POINTER(C.c_int), u64p]
         L.or_spec_build.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                     u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32,
@@ -65,9 +66,9 @@ def lib():
         L.or_eval_pair.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, u64p, u64p, C.c_uint64,
                                    u64p, u64p, u32p, u32p, u32p, u32p, u64p, u64p, u64p, u64p]
         L.or_reconstruct.argtypes = [u64p, u64p, u32p, u32p, C.c_uint64, C.c_uint32, u64p, u32p]
-        L.or_elem_qkey.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
-        L.or_elem_lkey.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
-        L.or_dcf_key_fields.argtypes = [C.c_void_p, u8p, u8p, u8p, u8p, u8p, u64p]
+        L.or_elem_qkey.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p]
+        L.or_elem_lkey.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p]
+        L.or_dcf_key_fields.argtypes = [C.c_void_p, u32p, u8p, u8p, u64p, u8p, u64p]
         L.or_elem_btriples.argtypes = [C.c_void_p, C.c_uint32, u32p, u32p, u32p]
         L.or_elem_fields.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, u64p, u32p, u64p, u64p, u64p, u64p]
         _lib = L
@@ -116,27 +117,40 @@ class DcfKey:
     def ptr(self):
         return self.buf.ctypes.data
 
-    def fields(self, k: int, p: int):
+    def fields(self):
+        """root [16], cw [nlev, A, 16] (t CW in bit 0, bit-payload value CW in
+        bit 1), vcw [nlev, A, p], leaf_bit, leaf [p]; A = 2^r."""
+        dims = np.zeros(4, np.uint32)
+        lib().or_dcf_key_fields(self.ptr, _p(dims, u32p), None, None, None, None, None)
+        k, r, nlev, p = (int(v) for v in dims)
+        A = 1 << r
         root = np.zeros(16, np.uint8)
-        scw = np.zeros((max(k, 1), 16), np.uint8)
-        tl = np.zeros(max(k, 1), np.uint8)
-        tr = np.zeros(max(k, 1), np.uint8)
-        vb = np.zeros(k + 1, np.uint8)
-        vcw = np.zeros((k + 1) * max(p, 1), np.uint64)
-        lib().or_dcf_key_fields(self.ptr, _p(root, u8p), _p(scw, u8p), _p(tl, u8p), _p(tr, u8p),
-                                _p(vb, u8p), _p(vcw, u64p))
-        return dict(root=root, scw=scw[:k], tcw_l=tl[:k], tcw_r=tr[:k], vcw_bit=vb,
-                    vcw=vcw.reshape(k + 1, max(p, 1))[:, :p])
+        cw = np.zeros((max(nlev, 1), A, 16), np.uint8)
+        vcw = np.zeros((max(nlev, 1), A, max(p, 1)), np.uint64)
+        lb = np.zeros(1, np.uint8)
+        leaf = np.zeros(max(p, 1), np.uint64)
+        lib().or_dcf_key_fields(self.ptr, _p(dims, u32p), _p(root, u8p), _p(cw, u8p), _p(vcw, u64p), _p(lb, u8p),
+                                _p(leaf, u64p))
+        return dict(k=k, r=r, nlev=nlev, p=p, root=root, cw=cw[:nlev], vcw=vcw[:nlev, :, :p],
+                    leaf_bit=int(lb[0]), leaf=leaf[:p])
 
 
-def dcf_gen(k: int, alpha: int, p: int, beta, root0: bytes, root1: bytes):
-    """BCG+21 comparison DCF for beta * 1[u < alpha] on k-bit u.  p == 0: bit payload."""
+def dcf_gen(k: int, alpha: int, p: int, beta, root0: bytes, root1: bytes, r: int = 2, rnd: bytes = None):
+    """DCF of arity 2^r for beta * 1[u < alpha] on k-bit u (p == 0: bit
+    payload).  rnd: the path children's random correction words, ceil(k/r) x
+    (1 + V) blocks of 16 bytes (drawn from a seeded generator when None)."""
     k0, k1 = DcfKey(), DcfKey()
     b = None
     if p > 0:
         b = np.ascontiguousarray(np.asarray(beta, dtype=np.uint64).reshape(p))
-    lib().or_dcf_gen(k, alpha, p, _p(b, u64p), _p(_bytes16(root0), u8p), _p(_bytes16(root1), u8p),
-                     k0.ptr, k1.ptr)
+    nlev = -(-k // r)
+    nb = 1 + ((8 * p + 15) // 16 if p else 0)
+    if rnd is None:
+        rnd = np.random.default_rng(int.from_bytes(bytes(root0)[:8], "little")).bytes(16 * nlev * nb)
+    rb = np.frombuffer(bytes(rnd), np.uint8).copy()
+    assert rb.size >= 16 * nlev * nb
+    lib().or_dcf_gen(k, r, alpha, p, _p(b, u64p), _p(_bytes16(root0), u8p), _p(_bytes16(root1), u8p),
+                     _p(rb, u8p), k0.ptr, k1.ptr)
     return k0, k1
 
 
@@ -219,9 +233,10 @@ class Spec:
 class ElemKeys:
     """Per-element preprocessing material of one party for n elements."""
 
-    def __init__(self, n: int):
+    def __init__(self, n: int, spec: "Spec"):
         self.n = n
-        self.size = lib().or_elem_keys_size()
+        self.size = lib().or_elem_keys_size(spec.ptr)
+        self.spec = spec
         self.buf = np.zeros(max(n, 1) * self.size, np.uint8)
 
     @property
@@ -252,20 +267,20 @@ class ElemKeys:
 
     def qkey(self, i: int, t: int) -> DcfKey:
         key = DcfKey()
-        lib().or_elem_qkey(self.elem_ptr(i), t, key.ptr)
+        lib().or_elem_qkey(self.spec.ptr, self.elem_ptr(i), t, key.ptr)
         return key
 
     def lkey(self, i: int, j: int) -> DcfKey:
         """Lookup key j (1-based boundary index j = 1..M-1)."""
         key = DcfKey()
-        lib().or_elem_lkey(self.elem_ptr(i), j - 1, key.ptr)
+        lib().or_elem_lkey(self.spec.ptr, self.elem_ptr(i), j - 1, key.ptr)
         return key
 
 
 def dealer(spec: Spec, seed: bytes, call_id: int, e0: int, n: int, x_plain=None, r_override=None):
     """Preprocessing for elements [e0, e0+n).  Returns (keys0, keys1, x0, x1).
     r_override (tests only) forces the input masks r_in."""
-    k0, k1 = ElemKeys(n), ElemKeys(n)
+    k0, k1 = ElemKeys(n, spec), ElemKeys(n, spec)
     x0 = x1 = None
     xp = None
     if x_plain is not None:

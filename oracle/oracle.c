@@ -196,194 +196,178 @@ static void mmo(const uint8_t s[16], uint32_t j, uint8_t out[16])
 
 void or_mmo(const uint8_t s[16], uint32_t j, uint8_t out[16]) { mmo(s, j, out); }
 
-#define MAXK 63     /* view width k <= 63 (k + 1 V_CW bits of a bit key fit a uint64) */
+#define MAXK 63     /* view width k <= 63 */
 #define MAXKL 32    /* view width of a spec with an interval lookup */
 #define MAXP 4      /* payload length p = r (d + 1) <= 4 */
+#define MAXR 3      /* DCF input bits per tree level: arity 2^r <= 8 */
+#define MAXC 8      /* children per level */
+#define MAXLV 63    /* tree levels (r = 1, k = 63) */
 
 static int nblocks_for(int p) { return (8 * p + 15) / 16; }   /* V = ceil(8p/16) */
 
-/* Expansion of one child sigma of seed s: the next seed (low two bits
- * cleared), its control bit t (bit 0) and, for the bit payload, v (bit 1). */
-static void expand_child(const uint8_t s[16], int sigma, uint8_t seed[16], int *t, int *vbit)
-{
-    uint8_t blk[16];
-    mmo(s, (uint32_t)sigma, blk);
-    *t = blk[0] & 1;
-    *vbit = (blk[0] >> 1) & 1;
-    memcpy(seed, blk, 16);
-    seed[0] &= (uint8_t)~3u;
-}
-
-/* Vector payload of child sigma: V blocks H(s, 2 + sigma*V + q), q < V, read
- * as p little-endian uint64 values. */
-static void convert_child(const uint8_t s[16], int sigma, int p, uint64_t *v)
-{
-    int V = nblocks_for(p);
-    uint8_t buf[16 * 4];
-    for (int q = 0; q < V; q++) mmo(s, (uint32_t)(2 + sigma * V + q), buf + 16 * q);
-    for (int i = 0; i < p; i++) v[i] = le64(buf + 8 * i);
-}
-
-/* Conversion of a leaf seed: H(s, 2 + q), q < V, read as p uint64. */
-static void convert_leaf(const uint8_t s[16], int p, uint64_t *v)
-{
-    int V = nblocks_for(p);
-    uint8_t buf[16 * 4];
-    for (int q = 0; q < V; q++) mmo(s, (uint32_t)(2 + q), buf + 16 * q);
-    for (int i = 0; i < p; i++) v[i] = le64(buf + 8 * i);
-}
-
 /* ------------------------------------------------------------------------ */
-/* DCF (BCG+21), f(u) = beta * 1[u < alpha] on k-bit u, MSB first.          */
-/* p == 0 selects the bit payload over Z_2 (beta = 1); p >= 1 selects the    */
-/* vector payload over Z_{2^64}^p.                                            */
+/* DCF with arity 2^r (a generalisation of BCG+21, written out below):      */
+/* f(u) = beta * 1[u < alpha] on k-bit u, read as nlev = ceil(k/r) digits   */
+/* MSB first (the first digit takes the k - r(nlev-1) top bits).            */
+/* p == 0 selects the bit payload over Z_2 (beta = 1); p >= 1 the vector    */
+/* payload over Z_{2^64}^p.                                                  */
+/*                                                                          */
+/* Expansion of seed s, child c (arity A = 2^r): blk = H(s, c); control bit */
+/* t = bit 0; bit payload = bit 1; child seed = blk with bits 0, 1 cleared. */
+/* Vector payload of child c: V blocks H(s, A + cV + q), q < V.  Leaf:      */
+/* bit 2 of the seed, or V blocks H(s, A + q).                              */
+/*                                                                          */
+/* Gen keeps both parties' seeds and t_0 ^ t_1 = 1 on the path of alpha.     */
+/* At a level with alpha's digit a, every other child c gets the seed CW    */
+/* s_0^c ^ s_1^c, the t CW t_0^c ^ t_1^c and the value CW                   */
+/*   (-1)^{t_1} (beta 1[c < a] - W - v_0^c + v_1^c)                         */
+/* (W = the path's running sum of party 0's minus party 1's contributions), */
+/* so leaving the path through c sums to beta 1[c < a] and both parties    */
+/* continue with equal seeds and control bits (their later terms cancel).  */
+/* The path child a gets a fresh random seed CW and value CW (they hide a), */
+/* t CW t_0^a ^ t_1^a ^ 1, and W grows by v_0^a - v_1^a + (-1)^{t_1} CW.    */
+/* The leaf CW (-1)^{t_1} (Conv(s_1) - Conv(s_0) - W) makes u = alpha sum   */
+/* to 0.  Eval_b adds (-1)^b (v^c + t CW_value[c]) per level, then          */
+/* s <- s^c ^ t CW_seed[c], t <- t^c ^ t CW_t[c], and the leaf term.        */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    int k, p;
+    int k, p, r, nlev;
     uint8_t root[16];
-    uint8_t scw[MAXK][16];
-    uint8_t tcw_l[MAXK], tcw_r[MAXK];
-    uint8_t vcw_bit[MAXK + 1];            /* bit payload: per level, [k] = leaf */
-    uint64_t vcw[MAXK + 1][MAXP];         /* vector payload: per level, [k] = leaf */
+    uint8_t cw[MAXLV][MAXC][16];          /* seed CW; bit 0 = t CW; bit 1 = value CW (bit payload) */
+    uint64_t vcw[MAXLV][MAXC][MAXP];      /* value CWs (vector payload) */
+    uint8_t leaf_bit;                     /* leaf CW (bit payload) */
+    uint64_t leaf[MAXP];                  /* leaf CW (vector payload) */
 } or_dcf_key;
 
-/* The packed-comparison keys carry only bit payloads; a smaller record keeps
- * the per-element material small. */
-typedef struct {
-    int k;
-    uint8_t root[16];
-    uint8_t scw[MAXK][16];
-    uint8_t tcw_l[MAXK], tcw_r[MAXK];
-    uint8_t vcw_bit[MAXK + 1];
-} or_bit_key;
+static int dcf_levels(int k, int r) { return (k + r - 1) / r; }
 
-/* Stored lookup keys: at most MAXKL levels. */
-typedef struct {
-    int k, p;
-    uint8_t root[16];
-    uint8_t scw[MAXKL][16];
-    uint8_t tcw_l[MAXKL], tcw_r[MAXKL];
-    uint64_t vcw[MAXKL + 1][MAXP];
-} or_lut_key;
-
-static void lut_key_from(const or_dcf_key *src, or_lut_key *dst)
+/* width in bits and shift of level i's digit */
+static void dcf_digit(int k, int r, int i, int *w, int *sh)
 {
-    dst->k = src->k; dst->p = src->p;
-    memcpy(dst->root, src->root, 16);
-    memcpy(dst->scw, src->scw, sizeof(dst->scw));
-    memcpy(dst->tcw_l, src->tcw_l, MAXKL);
-    memcpy(dst->tcw_r, src->tcw_r, MAXKL);
-    memcpy(dst->vcw, src->vcw, sizeof(dst->vcw));
+    int nlev = dcf_levels(k, r);
+    *sh = r * (nlev - 1 - i);
+    *w = i == 0 ? k - r * (nlev - 1) : r;
 }
 
-static void lut_key_to(const or_lut_key *src, or_dcf_key *dst)
+/* payload of child c of seed s: V blocks H(s, 2^r + cV + q) as p uint64 */
+static void dcf_child_payload(const uint8_t s[16], int r, int c, int p, uint64_t *v)
 {
-    memset(dst, 0, sizeof(*dst));
-    dst->k = src->k; dst->p = src->p;
-    memcpy(dst->root, src->root, 16);
-    memcpy(dst->scw, src->scw, sizeof(src->scw));
-    memcpy(dst->tcw_l, src->tcw_l, MAXKL);
-    memcpy(dst->tcw_r, src->tcw_r, MAXKL);
-    memcpy(dst->vcw, src->vcw, sizeof(src->vcw));
+    int V = nblocks_for(p);
+    uint8_t buf[16 * 4];
+    for (int q = 0; q < V; q++) mmo(s, (uint32_t)((1 << r) + c * V + q), buf + 16 * q);
+    for (int i = 0; i < p; i++) v[i] = le64(buf + 8 * i);
 }
 
-static void bit_key_from(const or_dcf_key *src, or_bit_key *dst)
+static void dcf_leaf_payload(const uint8_t s[16], int r, int p, uint64_t *v)
 {
-    dst->k = src->k;
-    memcpy(dst->root, src->root, 16);
-    memcpy(dst->scw, src->scw, sizeof(dst->scw));
-    memcpy(dst->tcw_l, src->tcw_l, MAXK);
-    memcpy(dst->tcw_r, src->tcw_r, MAXK);
-    memcpy(dst->vcw_bit, src->vcw_bit, MAXK + 1);
+    dcf_child_payload(s, r, 0, p, v);     /* tweaks 2^r + q */
 }
 
-static void bit_key_to(const or_bit_key *src, or_dcf_key *dst)
-{
-    memset(dst, 0, sizeof(*dst));
-    dst->k = src->k;
-    dst->p = 0;
-    memcpy(dst->root, src->root, 16);
-    memcpy(dst->scw, src->scw, sizeof(src->scw));
-    memcpy(dst->tcw_l, src->tcw_l, MAXK);
-    memcpy(dst->tcw_r, src->tcw_r, MAXK);
-    memcpy(dst->vcw_bit, src->vcw_bit, MAXK + 1);
-}
-
-void or_dcf_gen(int k, uint64_t alpha, int p, const uint64_t *beta,
-                const uint8_t root0[16], const uint8_t root1[16],
+/* rnd: nlev x (1 + V) random 16-byte blocks (level major) for the path
+ * child's seed CW (block 0; its bit 1 is the bit-payload value CW) and
+ * value CWs (blocks 1..V, read as p uint64). */
+void or_dcf_gen(int k, int r, uint64_t alpha, int p, const uint64_t *beta,
+                const uint8_t root0[16], const uint8_t root1[16], const uint8_t *rnd,
                 or_dcf_key *k0, or_dcf_key *k1)
 {
     uint8_t s[2][16];
     int t[2] = {0, 1};
-    uint64_t va[MAXP] = {0};
-    int va_bit = 0;
-    memset(k0, 0, sizeof(*k0));
-    memset(k1, 0, sizeof(*k1));
+    uint64_t W[MAXP] = {0};
+    int Wb = 0;
+    int V = nblocks_for(p);
+    int nlev = dcf_levels(k, r);
     k0->k = k1->k = k;
     k0->p = k1->p = p;
+    k0->r = k1->r = r;
+    k0->nlev = k1->nlev = nlev;
+    k0->leaf_bit = k1->leaf_bit = 0;
     memcpy(s[0], root0, 16);
     memcpy(s[1], root1, 16);
     memcpy(k0->root, root0, 16);
     memcpy(k1->root, root1, 16);
 
-    for (int i = 0; i < k; i++) {
-        int a = (int)((alpha >> (k - 1 - i)) & 1);
-        uint8_t cs[2][2][16];       /* [party][child] seed */
-        int ct[2][2], cvb[2][2];    /* control bit, bit payload */
-        uint64_t cv[2][2][MAXP];    /* vector payload */
+    for (int i = 0; i < nlev; i++) {
+        int w, sh;
+        dcf_digit(k, r, i, &w, &sh);
+        int nc = 1 << w;
+        int a = (int)((alpha >> sh) & (uint64_t)(nc - 1));
+        uint8_t cs[2][MAXC][16];
+        int ct[2][MAXC], cvb[2][MAXC];
+        uint64_t cv[2][MAXC][MAXP];
         for (int b = 0; b < 2; b++)
-            for (int sg = 0; sg < 2; sg++) {
-                expand_child(s[b], sg, cs[b][sg], &ct[b][sg], &cvb[b][sg]);
-                if (p > 0) convert_child(s[b], sg, p, cv[b][sg]);
+            for (int c = 0; c < nc; c++) {
+                uint8_t blk[16];
+                mmo(s[b], (uint32_t)c, blk);
+                ct[b][c] = blk[0] & 1;
+                cvb[b][c] = (blk[0] >> 1) & 1;
+                memcpy(cs[b][c], blk, 16);
+                cs[b][c][0] &= (uint8_t)~3u;
+                if (p > 0) dcf_child_payload(s[b], r, c, p, cv[b][c]);
             }
-        int keep = a, lose = 1 - a;
-        uint8_t scw[16];
-        for (int j = 0; j < 16; j++) scw[j] = cs[0][lose][j] ^ cs[1][lose][j];
-        int tcw_l = ct[0][0] ^ ct[1][0] ^ a ^ 1;
-        int tcw_r = ct[0][1] ^ ct[1][1] ^ a;
-
+        int sign = t[1];                      /* (-1)^{t_1}: negate when t_1 = 1 */
+        const uint8_t *R = rnd + (size_t)i * (1 + V) * 16;
+        for (int c = nc; c < (1 << r); c++) {  /* children a narrow first digit cannot take */
+            memset(k0->cw[i][c], 0, 16);
+            memset(k1->cw[i][c], 0, 16);
+            for (int q = 0; q < p; q++) k0->vcw[i][c][q] = k1->vcw[i][c][q] = 0;
+        }
+        for (int c = 0; c < nc; c++) {
+            uint8_t cw[16];
+            int tcw, vb = 0;
+            if (c != a) {
+                for (int j = 0; j < 16; j++) cw[j] = cs[0][c][j] ^ cs[1][c][j];
+                tcw = ct[0][c] ^ ct[1][c];
+                if (p == 0) {
+                    vb = cvb[0][c] ^ cvb[1][c] ^ Wb ^ (c < a ? 1 : 0);
+                } else {
+                    for (int q = 0; q < p; q++) {
+                        uint64_t d = (c < a ? beta[q] : 0) - W[q] - cv[0][c][q] + cv[1][c][q];
+                        k0->vcw[i][c][q] = k1->vcw[i][c][q] = sign ? (uint64_t)0 - d : d;
+                    }
+                }
+            } else {
+                memcpy(cw, R, 16);
+                cw[0] &= (uint8_t)~3u;
+                tcw = ct[0][c] ^ ct[1][c] ^ 1;
+                if (p == 0) vb = (R[0] >> 1) & 1;
+                else
+                    for (int q = 0; q < p; q++) k0->vcw[i][c][q] = k1->vcw[i][c][q] = le64(R + 16 + 8 * q);
+            }
+            cw[0] |= (uint8_t)(tcw | (vb << 1));
+            memcpy(k0->cw[i][c], cw, 16);
+            memcpy(k1->cw[i][c], cw, 16);
+        }
+        /* the path continues through child a */
+        const uint8_t *ca = k0->cw[i][a];
         if (p == 0) {
-            /* over Z_2 every sign is +1 and subtraction is XOR */
-            int vcw = cvb[1][lose] ^ cvb[0][lose] ^ va_bit;
-            if (lose == 0) vcw ^= 1;          /* beta = 1 */
-            va_bit = va_bit ^ cvb[1][keep] ^ cvb[0][keep] ^ vcw;
-            k0->vcw_bit[i] = k1->vcw_bit[i] = (uint8_t)vcw;
+            Wb ^= cvb[0][a] ^ cvb[1][a] ^ ((ca[0] >> 1) & 1);
         } else {
-            int neg = t[1];                   /* (-1)^{t_1} */
             for (int q = 0; q < p; q++) {
-                uint64_t d = cv[1][lose][q] - cv[0][lose][q] - va[q];
-                if (lose == 0) d += beta[q];
-                uint64_t vcw = neg ? (uint64_t)0 - d : d;
-                va[q] = va[q] - cv[1][keep][q] + cv[0][keep][q] + (neg ? (uint64_t)0 - vcw : vcw);
-                k0->vcw[i][q] = k1->vcw[i][q] = vcw;
+                uint64_t vc = k0->vcw[i][a][q];
+                W[q] = W[q] + cv[0][a][q] - cv[1][a][q] + (sign ? (uint64_t)0 - vc : vc);
             }
         }
-        memcpy(k0->scw[i], scw, 16);
-        memcpy(k1->scw[i], scw, 16);
-        k0->tcw_l[i] = k1->tcw_l[i] = (uint8_t)tcw_l;
-        k0->tcw_r[i] = k1->tcw_r[i] = (uint8_t)tcw_r;
-
-        int tcw_keep = keep ? tcw_r : tcw_l;
         for (int b = 0; b < 2; b++) {
             int t_old = t[b];
-            for (int j = 0; j < 16; j++) s[b][j] = cs[b][keep][j] ^ (t_old ? scw[j] : 0);
-            t[b] = ct[b][keep] ^ (t_old & tcw_keep);
+            for (int j = 0; j < 16; j++) {
+                uint8_t m = j == 0 ? (uint8_t)~3u : 0xFF;
+                s[b][j] = cs[b][a][j] ^ (t_old ? (uint8_t)(ca[j] & m) : 0);
+            }
+            t[b] = ct[b][a] ^ (t_old & (ca[0] & 1));
         }
     }
-    /* final correction word CW_{k+1} */
+    /* leaf correction word */
     if (p == 0) {
         int c0 = (s[0][0] >> 2) & 1, c1 = (s[1][0] >> 2) & 1;
-        int cw = c1 ^ c0 ^ va_bit;
-        k0->vcw_bit[k] = k1->vcw_bit[k] = (uint8_t)cw;
+        k0->leaf_bit = k1->leaf_bit = (uint8_t)(c1 ^ c0 ^ Wb);
     } else {
         uint64_t l0[MAXP], l1[MAXP];
-        convert_leaf(s[0], p, l0);
-        convert_leaf(s[1], p, l1);
+        dcf_leaf_payload(s[0], r, p, l0);
+        dcf_leaf_payload(s[1], r, p, l1);
         for (int q = 0; q < p; q++) {
-            uint64_t d = l1[q] - l0[q] - va[q];
-            uint64_t cw = t[1] ? (uint64_t)0 - d : d;
-            k0->vcw[k][q] = k1->vcw[k][q] = cw;
+            uint64_t d = l1[q] - l0[q] - W[q];
+            k0->leaf[q] = k1->leaf[q] = t[1] ? (uint64_t)0 - d : d;
         }
     }
 }
@@ -392,43 +376,46 @@ void or_dcf_gen(int k, uint64_t alpha, int p, const uint64_t *beta,
  * *out_bit.  Vector payload: writes p uint64 shares to out. */
 void or_dcf_eval(int b, const or_dcf_key *key, uint64_t u, int *out_bit, uint64_t *out)
 {
-    int k = key->k, p = key->p;
+    int k = key->k, p = key->p, r = key->r;
     uint8_t s[16];
     int t = b;
     int vb = 0;
     uint64_t v[MAXP] = {0};
     memcpy(s, key->root, 16);
-    for (int i = 0; i < k; i++) {
-        int x = (int)((u >> (k - 1 - i)) & 1);
-        uint8_t seed[16];
-        int tc, vbit;
-        uint64_t cv[MAXP];
-        expand_child(s, x, seed, &tc, &vbit);
-        if (p > 0) convert_child(s, x, p, cv);
-        int t_old = t;
-        if (t_old) {
-            for (int j = 0; j < 16; j++) seed[j] ^= key->scw[i][j];
-            tc ^= x ? key->tcw_r[i] : key->tcw_l[i];
-        }
+    for (int i = 0; i < key->nlev; i++) {
+        int w, sh;
+        dcf_digit(k, r, i, &w, &sh);
+        int c = (int)((u >> sh) & (uint64_t)((1 << w) - 1));
+        uint8_t blk[16];
+        mmo(s, (uint32_t)c, blk);
+        const uint8_t *cw = key->cw[i][c];
+        int tc = blk[0] & 1, vbit = (blk[0] >> 1) & 1;
         if (p == 0) {
-            vb ^= vbit ^ (t_old & key->vcw_bit[i]);
+            vb ^= vbit ^ (t & ((cw[0] >> 1) & 1));
         } else {
+            uint64_t cv[MAXP];
+            dcf_child_payload(s, r, c, p, cv);
             for (int q = 0; q < p; q++) {
-                uint64_t add = cv[q] + (t_old ? key->vcw[i][q] : 0);
+                uint64_t add = cv[q] + (t ? key->vcw[i][c][q] : 0);
                 v[q] += b ? (uint64_t)0 - add : add;
             }
         }
-        memcpy(s, seed, 16);
+        blk[0] &= (uint8_t)~3u;
+        if (t) {
+            for (int j = 0; j < 16; j++) blk[j] ^= j == 0 ? (uint8_t)(cw[0] & ~3u) : cw[j];
+            tc ^= cw[0] & 1;
+        }
+        memcpy(s, blk, 16);
         t = tc;
     }
     if (p == 0) {
-        vb ^= ((s[0] >> 2) & 1) ^ (t & key->vcw_bit[k]);
+        vb ^= ((s[0] >> 2) & 1) ^ (t & key->leaf_bit);
         *out_bit = vb;
     } else {
         uint64_t leaf[MAXP];
-        convert_leaf(s, p, leaf);
+        dcf_leaf_payload(s, r, p, leaf);
         for (int q = 0; q < p; q++) {
-            uint64_t add = leaf[q] + (t ? key->vcw[k][q] : 0);
+            uint64_t add = leaf[q] + (t ? key->leaf[q] : 0);
             v[q] += b ? (uint64_t)0 - add : add;
         }
         for (int q = 0; q < p; q++) out[q] = v[q];
@@ -436,6 +423,10 @@ void or_dcf_eval(int b, const or_dcf_key *key, uint64_t u, int *out_bit, uint64_
 }
 
 size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
+
+/* The gate's DCF keys: arity 4 (two input bits per level). */
+#define GATE_R 2
+
 
 /* ------------------------------------------------------------------------ */
 /* Operator specification (Def. "operator specification", Sec. 4.1)        */
@@ -445,6 +436,19 @@ size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
 #define MAXPRED 32  /* Boolean outputs */
 #define MAXQ 32     /* packed-comparison queries (one uint32 of atoms) */
 #define MAXPW 4     /* piecewise Boolean outputs */
+
+typedef struct {
+    uint64_t r_share;
+    uint32_t carry_share;
+    uint64_t vlast_share[MAXP];
+    uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
+    uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
+    uint64_t tr_t;                    /* truncation: share of (r mod 2^k) >> s */
+    uint32_t tr_rho;                  /* daBits: XOR shares of rho_lo (bit 0), rho_hi (bit 1) */
+    uint64_t tr_rho_a[2];             /* daBits: additive shares of rho_lo, rho_hi */
+} or_elem_keys;   /* the header of an element's record; its packed DCF keys follow */
+
+static size_t packed_key_bytes(int k, int p);
 
 typedef struct {
     uint32_t f;        /* view width */
@@ -490,6 +494,8 @@ typedef struct {
     uint64_t trunc_c;                 /* view shift: 2^{k-1} for the signed form, else 0 */
     int32_t trunc_q_lo;               /* query of the r-atom 1[x^ mod 2^s < r mod 2^s] */
     int32_t trunc_q_hi;               /* query of the r-atom 1[view_{k,c}(x^) < r mod 2^k] */
+    /* per-element record layout (bytes): header, query keys, lookup keys */
+    uint32_t rec_size, q_off[MAXQ], l_off, l_size;
 } or_spec;
 
 /* index of primitive predicate (f, c, gamma) in sp->prim, adding it if new;
@@ -636,6 +642,16 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
         }
     }
     sp->T = T;
+    /* record layout */
+    uint32_t off = (uint32_t)((sizeof(or_elem_keys) + 15) & ~(size_t)15);
+    for (uint32_t t = 0; t < T; t++) {
+        sp->q_off[t] = off;
+        off += (uint32_t)packed_key_bytes((int)sp->q_f[t], 0);
+    }
+    sp->l_off = off;
+    sp->l_size = (uint32_t)packed_key_bytes((int)k, (int)sp->p);
+    off += (sp->M > 1 ? sp->M - 1 : 0) * sp->l_size;
+    sp->rec_size = (off + 15) & ~15u;
     return 0;
 }
 
@@ -743,25 +759,70 @@ static uint64_t prg_u64(const or_prg *g, uint32_t draw, uint64_t elem)
 #define DRAW_XSH 2
 #define DRAW_CARRY 3
 #define DRAW_VLAST 4
+/* path-child randomness of the DCF keys: key kappa (queries in order, then
+ * lookup keys), level i, block q at draw DRAW_KEEP + (32 kappa + i) 4 + q */
+#define DRAW_KEEP 0x100000u
 
 /* ------------------------------------------------------------------------ */
 /* Per-element preprocessing material (one party)                           */
 /* ------------------------------------------------------------------------ */
 
-typedef struct {
-    uint64_t r_share;
-    uint32_t carry_share;
-    uint64_t vlast_share[MAXP];
-    or_bit_key qkey[MAXQ];            /* packed-comparison keys, query order */
-    or_lut_key lkey[MAXM];            /* lookup keys j = 1..M-1 at index j-1 */
-    uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
-    uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
-    uint64_t tr_t;                    /* truncation: share of (r mod 2^k) >> s */
-    uint32_t tr_rho;                  /* daBits: XOR shares of rho_lo (bit 0), rho_hi (bit 1) */
-    uint64_t tr_rho_a[2];             /* daBits: additive shares of rho_lo, rho_hi */
-} or_elem_keys;
 
-size_t or_elem_keys_size(void) { return sizeof(or_elem_keys); }
+/* One element's record: the header above (padded to 16 bytes), then the T
+ * packed-comparison keys in query order, then the M-1 lookup keys; sizes
+ * and offsets depend on the spec (sp->rec_size, sp->q_off, sp->l_off). */
+size_t or_elem_keys_size(const or_spec *sp) { return sp->rec_size; }
+
+static or_elem_keys *elem_at(or_elem_keys *base, const or_spec *sp, uint64_t i)
+{
+    return (or_elem_keys *)((uint8_t *)base + i * sp->rec_size);
+}
+
+static const or_elem_keys *celem_at(const or_elem_keys *base, const or_spec *sp, uint64_t i)
+{
+    return (const or_elem_keys *)((const uint8_t *)base + i * sp->rec_size);
+}
+
+/* Packed gate key (arity 2^GATE_R): root[16], cw[nlev][A][16], then for a
+ * vector payload vcw[nlev][A][p] uint64 and the leaf CW p uint64, for a bit
+ * payload the leaf CW bit in one uint64. */
+static size_t packed_key_bytes(int k, int p)
+{
+    size_t nlev = (size_t)dcf_levels(k, GATE_R), A = (size_t)1 << GATE_R;
+    return 16 + nlev * A * 16 + (p ? nlev * A * (size_t)p * 8 + 8 * (size_t)p : 8);
+}
+
+static void pack_key(const or_dcf_key *K, uint8_t *dst)
+{
+    int A = 1 << GATE_R;
+    memcpy(dst, K->root, 16);
+    dst += 16;
+    for (int i = 0; i < K->nlev; i++)
+        for (int c = 0; c < A; c++, dst += 16) memcpy(dst, K->cw[i][c], 16);
+    uint64_t *w = (uint64_t *)dst;
+    if (K->p == 0) { w[0] = K->leaf_bit; return; }
+    for (int i = 0; i < K->nlev; i++)
+        for (int c = 0; c < A; c++)
+            for (int q = 0; q < K->p; q++) *w++ = K->vcw[i][c][q];
+    for (int q = 0; q < K->p; q++) *w++ = K->leaf[q];
+}
+
+static void unpack_key(const uint8_t *src, int k, int p, or_dcf_key *K)
+{
+    int A = 1 << GATE_R;
+    K->k = k; K->p = p; K->r = GATE_R; K->nlev = dcf_levels(k, GATE_R);
+    K->leaf_bit = 0;
+    memcpy(K->root, src, 16);
+    src += 16;
+    for (int i = 0; i < K->nlev; i++)
+        for (int c = 0; c < A; c++, src += 16) memcpy(K->cw[i][c], src, 16);
+    const uint64_t *w = (const uint64_t *)src;
+    if (p == 0) { K->leaf_bit = (uint8_t)(w[0] & 1); return; }
+    for (int i = 0; i < K->nlev; i++)
+        for (int c = 0; c < A; c++)
+            for (int q = 0; q < p; q++) K->vcw[i][c][q] = *w++;
+    for (int q = 0; q < p; q++) K->leaf[q] = *w++;
+}
 
 /* Lookup instance for one element: App. F step (1).  Writes B[0..M], ord[0..M-1]. */
 static void compile_lookup(const or_spec *sp, uint64_t r_in, uint64_t *B, uint32_t *ord)
@@ -843,6 +904,15 @@ static void payload(const or_spec *sp, uint32_t piece, uint64_t r_in, uint64_t *
 
 /* Dealer for elements [e0, e0+n): masks, carries, keys, triples, input shares
  * (Sec. 5.2).  x_plain may be NULL (then x shares are not written). */
+/* nlev levels x (1 + V) blocks of path-child randomness for DCF key kappa */
+static void keep_rand(const or_prg *g, uint32_t kappa, int nlev, int p, uint64_t e, uint8_t *out)
+{
+    int nb = 1 + (p ? nblocks_for(p) : 0);
+    for (int i = 0; i < nlev; i++)
+        for (int q = 0; q < nb; q++)
+            prg_block(g, DRAW_KEEP + (32u * kappa + (uint32_t)i) * 4u + (uint32_t)q, e, out + (size_t)(i * nb + q) * 16);
+}
+
 void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
                uint64_t e0, uint64_t n, const uint64_t *x_plain,
                or_elem_keys *k0, or_elem_keys *k1, uint64_t *x0, uint64_t *x1,
@@ -854,12 +924,15 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
     uint32_t p = sp->p, T = sp->T, M = sp->M;
     uint32_t base_roots = DRAW_VLAST + p;
     uint32_t base_triples = base_roots + 2 * (T + M - 1);
+    or_dcf_key *G = (or_dcf_key *)malloc(2 * sizeof(or_dcf_key));   /* working keys of both parties */
+    uint8_t rnd[32 * 3 * 16];                                           /* path-child randomness */
+    if (!G) return;
 
     for (uint64_t i = 0; i < n; i++) {
         uint64_t e = e0 + i;
-        or_elem_keys *K0 = &k0[i], *K1 = &k1[i];
-        memset(K0, 0, sizeof(*K0));
-        memset(K1, 0, sizeof(*K1));
+        or_elem_keys *K0 = elem_at(k0, sp, i), *K1 = elem_at(k1, sp, i);
+        memset(K0, 0, sp->rec_size);
+        memset(K1, 0, sp->rec_size);
         /* r_override (tests only) replaces the drawn mask to cover every r */
         uint64_t r_in = r_override ? r_override[i] : prg_u64(&g, DRAW_RIN, e);
         uint64_t r0 = prg_u64(&g, DRAW_RSH, e);
@@ -891,12 +964,12 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             uint64_t Nf = pow2(sp->q_f[t]);
             uint64_t a = sp->q_prim[t] < 0 ? (r_in & (Nf - 1)) : theta[sp->q_prim[t]];
             uint8_t s0[16], s1[16];
-            or_dcf_key g0, g1;
             prg_block(&g, base_roots + 2 * t, e, s0);
             prg_block(&g, base_roots + 2 * t + 1, e, s1);
-            or_dcf_gen((int)sp->q_f[t], a, 0, NULL, s0, s1, &g0, &g1);
-            bit_key_from(&g0, &K0->qkey[t]);
-            bit_key_from(&g1, &K1->qkey[t]);
+            keep_rand(&g, t, dcf_levels((int)sp->q_f[t], GATE_R), 0, e, rnd);
+            or_dcf_gen((int)sp->q_f[t], GATE_R, a, 0, NULL, s0, s1, rnd, &G[0], &G[1]);
+            pack_key(&G[0], (uint8_t *)K0 + sp->q_off[t]);
+            pack_key(&G[1], (uint8_t *)K1 + sp->q_off[t]);
         }
 
         /* lookup: M-1 vector DCFs, telescoped:
@@ -914,10 +987,10 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             uint32_t di = base_roots + 2 * (T + j - 1);
             prg_block(&g, di, e, s0);
             prg_block(&g, di + 1, e, s1);
-            or_dcf_key g0, g1;
-            or_dcf_gen((int)sp->k, B[j], (int)p, beta, s0, s1, &g0, &g1);
-            lut_key_from(&g0, &K0->lkey[j - 1]);
-            lut_key_from(&g1, &K1->lkey[j - 1]);
+            keep_rand(&g, T + j - 1, dcf_levels((int)sp->k, GATE_R), (int)p, e, rnd);
+            or_dcf_gen((int)sp->k, GATE_R, B[j], (int)p, beta, s0, s1, rnd, &G[0], &G[1]);
+            pack_key(&G[0], (uint8_t *)K0 + sp->l_off + (size_t)(j - 1) * sp->l_size);
+            pack_key(&G[1], (uint8_t *)K1 + sp->l_off + (size_t)(j - 1) * sp->l_size);
         }
         for (uint32_t q = 0; q < p; q++) {
             uint64_t sh = prg_u64(&g, DRAW_VLAST + q, e);
@@ -969,6 +1042,7 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             K0->tr_rho_a[1] = a_hi; K1->tr_rho_a[1] = (uint64_t)(rho >> 1) - a_hi;
         }
     }
+    free(G);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -984,7 +1058,7 @@ static uint32_t party_pred_atoms(int b, const or_spec *sp, const or_elem_keys *K
         uint64_t u = view(xhat, sp->q_f[t], sp->q_c[t]);
         int bit;
         or_dcf_key key;
-        bit_key_to(&K->qkey[t], &key);
+        unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, &key);
         or_dcf_eval(b, &key, u, &bit, NULL);
         atoms |= (uint32_t)bit << t;
     }
@@ -1055,7 +1129,7 @@ static void party_lookup(int b, const or_spec *sp, const or_elem_keys *K, uint64
     for (uint32_t j = 1; j < sp->M; j++) {
         uint64_t sh[MAXP];
         or_dcf_key key;
-        lut_key_to(&K->lkey[j - 1], &key);
+        unpack_key((const uint8_t *)K + sp->l_off + (size_t)(j - 1) * sp->l_size, (int)sp->k, (int)sp->p, &key);
         or_dcf_eval(b, &key, u, NULL, sh);
         for (uint32_t q = 0; q < sp->p; q++) pay[q] += sh[q];
     }
@@ -1076,7 +1150,7 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
     uint32_t p = sp->p, d = sp->d, r = sp->r;
     uint64_t sent[2] = {0, 0};
     for (uint64_t e = 0; e < n; e++) {
-        KK[0] = &k0[e]; KK[1] = &k1[e];
+        KK[0] = celem_at(k0, sp, e); KK[1] = celem_at(k1, sp, e);
         /* (1) shares -> masked opening (App. C): each party sends x_b + r_b */
         uint64_t msg[2];
         for (int b = 0; b < 2; b++) { msg[b] = xs[b][e] + KK[b]->r_share; sent[b] += 8; }
@@ -1195,23 +1269,32 @@ void or_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0, 
 /* Accessors used by tests to read key material                              */
 /* ------------------------------------------------------------------------ */
 
-void or_elem_qkey(const or_elem_keys *K, uint32_t t, or_dcf_key *out) { bit_key_to(&K->qkey[t], out); }
-void or_elem_lkey(const or_elem_keys *K, uint32_t j, or_dcf_key *out) { lut_key_to(&K->lkey[j], out); }
-
-void or_dcf_key_fields(const or_dcf_key *key, uint8_t *root, uint8_t *scw, uint8_t *tcw_l,
-                       uint8_t *tcw_r, uint8_t *vcw_bit, uint64_t *vcw)
+void or_elem_qkey(const or_spec *sp, const or_elem_keys *K, uint32_t t, or_dcf_key *out)
 {
-    int k = key->k, p = key->p;
+    unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, out);
+}
+
+void or_elem_lkey(const or_spec *sp, const or_elem_keys *K, uint32_t j, or_dcf_key *out)
+{
+    unpack_key((const uint8_t *)K + sp->l_off + (size_t)j * sp->l_size, (int)sp->k, (int)sp->p, out);
+}
+
+/* key material as arrays: root[16], cw[nlev][A][16], vcw[nlev][A][p],
+ * leaf_bit, leaf[p] (A = 2^r) */
+void or_dcf_key_fields(const or_dcf_key *key, uint32_t *dims, uint8_t *root, uint8_t *cw, uint64_t *vcw,
+                       uint8_t *leaf_bit, uint64_t *leaf)
+{
+    int A = 1 << key->r, p = key->p;
+    dims[0] = (uint32_t)key->k; dims[1] = (uint32_t)key->r; dims[2] = (uint32_t)key->nlev; dims[3] = (uint32_t)p;
+    if (!root) return;
     memcpy(root, key->root, 16);
-    for (int i = 0; i < k; i++) {
-        memcpy(scw + 16 * i, key->scw[i], 16);
-        tcw_l[i] = key->tcw_l[i];
-        tcw_r[i] = key->tcw_r[i];
-    }
-    for (int i = 0; i <= k; i++) {
-        vcw_bit[i] = key->vcw_bit[i];
-        for (int q = 0; q < p; q++) vcw[i * (p > 0 ? p : 1) + q] = key->vcw[i][q];
-    }
+    for (int i = 0; i < key->nlev; i++)
+        for (int c = 0; c < A; c++) {
+            memcpy(cw + (size_t)(i * A + c) * 16, key->cw[i][c], 16);
+            for (int q = 0; q < p; q++) vcw[(size_t)(i * A + c) * p + q] = key->vcw[i][c][q];
+        }
+    *leaf_bit = key->leaf_bit;
+    for (int q = 0; q < p; q++) leaf[q] = key->leaf[q];
 }
 
 void or_elem_btriples(const or_elem_keys *K, uint32_t npw, uint32_t *ba, uint32_t *bb, uint32_t *bc)

@@ -1,16 +1,19 @@
-"""Pins for the oracle's DCF (Boyle et al., EUROCRYPT 2021) by brute force:
-Eval_0 (+) Eval_1 = beta * 1[u < alpha] for every alpha and every u at small k."""
+"""Pins for the oracle's DCF (a generalisation of Boyle et al., EUROCRYPT
+2021, to arity 2^r: r input bits per tree level) by brute force:
+Eval_0 (+) Eval_1 = beta * 1[u < alpha] for every alpha and every u at small
+k, for r = 1, 2 (the gates' keys) and 3, including k not a multiple of r."""
 import numpy as np
 import pytest
 
 import oracle as O
 
 
-@pytest.mark.parametrize("k", [1, 2, 4, 6])
-def test_bit_dcf_all_alpha_all_u(k):
-    rng = np.random.default_rng(100 + k)
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_bit_dcf_all_alpha_all_u(k, r):
+    rng = np.random.default_rng(100 + k + 10 * r)
     for alpha in range(2 ** k):
-        a, b = O.dcf_gen(k, alpha, 0, None, rng.bytes(16), rng.bytes(16))
+        a, b = O.dcf_gen(k, alpha, 0, None, rng.bytes(16), rng.bytes(16), r=r)
         for u in range(2 ** k):
             assert O.dcf_eval(0, a, u, 0) ^ O.dcf_eval(1, b, u, 0) == (1 if u < alpha else 0)
 
@@ -24,16 +27,37 @@ def test_bit_dcf_k10_sampled_alpha_all_u():
             assert O.dcf_eval(0, a, u, 0) ^ O.dcf_eval(1, b, u, 0) == (1 if u < alpha else 0)
 
 
-@pytest.mark.parametrize("k,p", [(1, 1), (3, 2), (5, 3), (5, 4)])
-def test_vector_dcf_all_alpha_all_u(k, p):
-    rng = np.random.default_rng(200 + 10 * k + p)
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("k,p", [(1, 1), (3, 2), (5, 3), (5, 4), (6, 1)])
+def test_vector_dcf_all_alpha_all_u(k, p, r):
+    rng = np.random.default_rng(200 + 10 * k + p + 100 * r)
     for alpha in range(2 ** k):
         beta = rng.integers(0, 2 ** 64, size=p, dtype=np.uint64)
-        a, b = O.dcf_gen(k, alpha, p, beta, rng.bytes(16), rng.bytes(16))
+        a, b = O.dcf_gen(k, alpha, p, beta, rng.bytes(16), rng.bytes(16), r=r)
         for u in range(2 ** k):
             got = O.dcf_eval(0, a, u, p) + O.dcf_eval(1, b, u, p)
             want = beta if u < alpha else np.zeros(p, np.uint64)
             assert (got == want).all()
+
+
+def test_path_child_randomness_hides_alpha():
+    """The correction words at a level do not single out alpha's digit: over
+    many keys, the t-CW bits of every child are unbiased, and for each child
+    the value-CW bit is unbiased too (the path child's are drawn fresh, the
+    others are masked by pseudorandom expansion bits)."""
+    rng = np.random.default_rng(12)
+    k, r = 8, 2
+    counts = np.zeros((4, 4, 2))
+    for trial in range(800):
+        alpha = int(rng.integers(0, 2 ** k))
+        a, _ = O.dcf_gen(k, alpha, 0, None, rng.bytes(16), rng.bytes(16), r=r)
+        f = a.fields()
+        d0 = (alpha >> 6) & 3                     # digit of the first level
+        for c in range(4):
+            counts[d0, c, 0] += f["cw"][0, c, 0] & 1
+            counts[d0, c, 1] += (f["cw"][0, c, 0] >> 1) & 1
+    per = counts / (counts.sum(axis=(1, 2), keepdims=True) / 8 + 1e-9)
+    assert np.abs(per - 1.0).max() < 0.35
 
 
 def test_vector_dcf_k10_sampled():
