@@ -212,65 +212,74 @@ FFSS_CORE uint64_t view(uint64_t u, uint32_t f, uint64_t c) {
 }
 
 // ---------------------------------------------------------------------------
-// DCF Eval_b (Boyle et al. 2021 comparison DCF, MSB first).
-// Expansion of child x of seed s: blk = H(s, x); control bit t = blk bit 0;
-// bit payload v = blk bit 1; next seed = blk with bits 0,1 cleared.  A
-// party with t = 1 XORs the level's correction word into the seed and
-// t_CW^x into t.  Correction words store t_CW^L, t_CW^R in bits 0, 1.
+// DCF of arity 4 (two input bits per tree level; a generalisation of Boyle et
+// al. 2021's comparison DCF): the k-bit input is read as ceil(k/2) digits MSB
+// first, the first digit taking one bit when k is odd.  Expansion of child c
+// of seed s: blk = H(s, c); control bit t = bit 0; bit payload = bit 1; next
+// seed = blk with bits 0, 1 cleared; vector payload V blocks H(s, 4 + cV + q).
+// Each level stores a correction word per child, row (level * 4 + c): the
+// seed CW with the t CW in bit 0 and, for the bit payload, the value CW in
+// bit 1.  A party with t = 1 XORs child c's CWs in.  Leaf: bit 2 of the seed
+// (bit payload) or H(s, 4 + q), plus t times the leaf CW.
 // ---------------------------------------------------------------------------
 
-// Bit payload (Z_2): returns the XOR share of 1[u < alpha].
-// root: uint4 root[n] of this key; cw level i at root[(1+i)*n]; vcw: V_CW bits.
+FFSS_CORE uint32_t dcf_levels(uint32_t k) { return (k + 1) / 2; }
+
+// Bit payload: returns the XOR share of 1[u < alpha].
+// root: uint4 root[n]; child CW of level i at root[(1 + 4 i + c) n]; leaf: the leaf CW bit.
 template <class AES>
 FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 *root, uint64_t n,
-                                uint64_t vcw, const AES &aes) {
+                                uint64_t leaf, const AES &aes) {
+  const uint32_t nlev = dcf_levels(k);
   uint4 s = root[0];
   uint32_t t = b, v = 0;
-  for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t x = uint32_t(u >> (k - 1 - i)) & 1u;
-    const uint4 cw = root[(1 + uint64_t(i)) * n];
-    const uint4 blk = mmo(s, x, aes);
+  for (uint32_t i = 0; i < nlev; ++i) {
+    const uint32_t c = uint32_t(u >> (2 * (nlev - 1 - i))) & 3u;
+    const uint4 cw = root[(1 + 4 * uint64_t(i) + c) * n];
+    const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
-    v ^= (blk.x >> 1) ^ (t & uint32_t(vcw >> i));
-    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
+    v ^= (blk.x >> 1) ^ (tm & (cw.x >> 1));
+    const uint32_t tn = (blk.x ^ (tm & cw.x)) & 1u;
     s.x = (blk.x ^ (tm & cw.x)) & ~3u;
     s.y = blk.y ^ (tm & cw.y);
     s.z = blk.z ^ (tm & cw.z);
     s.w = blk.w ^ (tm & cw.w);
     t = tn;
   }
-  v ^= (s.x >> 2) ^ (t & uint32_t(vcw >> k));
+  v ^= (s.x >> 2) ^ (t & uint32_t(leaf));
   return v & 1u;
 }
 
-// Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^x) + t*V_CW) + leaf
+// Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^c) + t VCW[c]) + leaf
 // term into acc (the caller applies the party sign (-1)^b once).
-// root: uint4 root[n]; cw level i at root[(1+i)*n]; vcw: u64 [(k+1)][P][n].
+// vcw: u64 [levels][4][P][n]; leaf: u64 [P][n].
 template <int P, class AES>
-FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root,
-                                const uint64_t *vcw, uint64_t n, uint64_t *acc, const AES &aes) {
+FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint64_t *vcw,
+                                const uint64_t *leaf, uint64_t n, uint64_t *acc, const AES &aes) {
   constexpr int V = (P + 1) / 2;
+  const uint32_t nlev = dcf_levels(k);
   uint4 s = root[0];
   uint32_t t = b;
-  for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t x = (u >> (k - 1 - i)) & 1u;
-    const uint4 cw = root[(1 + uint64_t(i)) * n];
+  for (uint32_t i = 0; i < nlev; ++i) {
+    const uint32_t c = (u >> (2 * (nlev - 1 - i))) & 3u;
+    const uint64_t row = 4 * uint64_t(i) + c;
+    const uint4 cw = root[(1 + row) * n];
     uint64_t vc[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) vc[q] = vcw[(uint64_t(i) * P + q) * n];
-    const uint4 blk = mmo(s, x, aes);
+    for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
+    const uint4 blk = mmo(s, c, aes);
     uint64_t conv[2 * V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-      const uint4 c = mmo(s, 2u + x * V + q, aes);
-      conv[2 * q] = lo64(c);
-      conv[2 * q + 1] = hi64(c);
+      const uint4 cb = mmo(s, 4u + c * V + q, aes);
+      conv[2 * q] = lo64(cb);
+      conv[2 * q + 1] = hi64(cb);
     }
     const uint64_t tm64 = 0ull - uint64_t(t);
 #pragma unroll
     for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vc[q] & tm64);
     const uint32_t tm = 0u - t;
-    const uint32_t tn = (blk.x ^ (tm & (cw.x >> x))) & 1u;
+    const uint32_t tn = (blk.x ^ (tm & cw.x)) & 1u;
     s.x = (blk.x ^ (tm & cw.x)) & ~3u;
     s.y = blk.y ^ (tm & cw.y);
     s.z = blk.z ^ (tm & cw.z);
@@ -280,13 +289,13 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
   uint64_t conv[2 * V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
-    const uint4 c = mmo(s, 2u + q, aes);
-    conv[2 * q] = lo64(c);
-    conv[2 * q + 1] = hi64(c);
+    const uint4 cb = mmo(s, 4u + q, aes);
+    conv[2 * q] = lo64(cb);
+    conv[2 * q + 1] = hi64(cb);
   }
   const uint64_t tm64 = 0ull - uint64_t(t);
 #pragma unroll
-  for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vcw[(uint64_t(k) * P + q) * n] & tm64);
+  for (int q = 0; q < P; ++q) acc[q] += conv[q] + (leaf[uint64_t(q) * n] & tm64);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,44 +303,72 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
 // (identical for both parties) and the V_CW words into both key sections.
 // ---------------------------------------------------------------------------
 
+// The four children of both parties' seeds: ch[b][c] = H(s_b, c), c < nc
+// (nc = 2 for a one-bit first digit; the other two stay zero).
 template <class AES4>
+FFSS_CORE void expand_children(uint4 s0, uint4 s1, uint32_t nc, uint4 (&ch)[2][4], const AES4 &aes4) {
+  const Blk4 e0 = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
+  ch[0][0] = e0.v[0]; ch[0][1] = e0.v[1]; ch[1][0] = e0.v[2]; ch[1][1] = e0.v[3];
+  if (nc == 4) {
+    const Blk4 e1 = mmo4(s0, 2, s0, 3, s1, 2, s1, 3, aes4);
+    ch[0][2] = e1.v[0]; ch[0][3] = e1.v[1]; ch[1][2] = e1.v[2]; ch[1][3] = e1.v[3];
+  } else {
+    ch[0][2] = ch[0][3] = ch[1][2] = ch[1][3] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Bit-payload DCF Gen of arity 4 for 1[u < alpha] on k-bit u, both parties.
+// keep(i, q) returns the q-th random block of level i for the path child
+// (block 0: its seed CW, and bit 1 its value CW).  Writes root and child CWs
+// (rows 1 + 4 i + c) and the leaf CW bit into both keys.
+template <class AES4, class KEEP>
 FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
-                           uint64_t *vcw0, uint64_t *vcw1, uint64_t n, const AES4 &aes4) {
+                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP &keep) {
   q0[0] = s0;
   q1[0] = s1;
-  uint32_t t0 = 0, t1 = 1, va = 0;
-  uint64_t vbits = 0;
-  for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t a = uint32_t(alpha >> (k - 1 - i)) & 1u;
-    const Blk4 ex = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
-    const uint4 L0 = ex.v[0], R0 = ex.v[1], L1 = ex.v[2], R1 = ex.v[3];
-    const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;   // Lose side
-    const uint4 ke0 = a ? R0 : L0, ke1 = a ? R1 : L1;   // Keep side
-    uint4 scw = xor4(lo0, lo1);
-    scw.x &= ~3u;
-    const uint32_t tl = (L0.x ^ L1.x ^ a ^ 1u) & 1u;
-    const uint32_t tr = (R0.x ^ R1.x ^ a) & 1u;
-    // Lose = L exactly when a = 1; then beta = 1 enters the correction.
-    const uint32_t vc = ((lo1.x >> 1) ^ (lo0.x >> 1) ^ va ^ a) & 1u;
-    va = (va ^ (ke1.x >> 1) ^ (ke0.x >> 1) ^ vc) & 1u;
-    uint4 cw = scw;
-    cw.x |= tl | (tr << 1);
-    q0[(1 + uint64_t(i)) * n] = cw;
-    q1[(1 + uint64_t(i)) * n] = cw;
-    vbits |= uint64_t(vc) << i;
-    const uint32_t tk = a ? tr : tl;
-    const uint32_t m0 = 0u - t0, m1 = 0u - t1;
-    uint4 ns0 = xor4(ke0, and4(scw, m0));
-    uint4 ns1 = xor4(ke1, and4(scw, m1));
-    const uint32_t nt0 = (ke0.x ^ (t0 & tk)) & 1u;
-    const uint32_t nt1 = (ke1.x ^ (t1 & tk)) & 1u;
+  const uint32_t nlev = dcf_levels(k);
+  uint32_t t0 = 0, t1 = 1, wb = 0;
+  for (uint32_t i = 0; i < nlev; ++i) {
+    const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
+    const uint32_t a = uint32_t(alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
+    uint4 ch[2][4];
+    expand_children(s0, s1, nc, ch, aes4);
+    const uint4 R = keep(i, 0u);
+    uint4 ck = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (uint32_t c = 0; c < 4; ++c) {
+      uint4 cw = make_uint4(0, 0, 0, 0);
+      if (c < nc) {
+        if (c != a) {
+          cw = xor4(ch[0][c], ch[1][c]);
+          const uint32_t tcw = cw.x & 1u;
+          const uint32_t vb = ((cw.x >> 1) ^ wb ^ (c < a ? 1u : 0u)) & 1u;
+          cw.x = (cw.x & ~3u) | tcw | (vb << 1);
+        } else {
+          cw = R;
+          cw.x = (cw.x & ~3u) | ((ch[0][c].x ^ ch[1][c].x ^ 1u) & 1u) | (R.x & 2u);
+          ck = cw;
+        }
+      }
+      q0[(1 + 4 * uint64_t(i) + c) * n] = cw;
+      q1[(1 + 4 * uint64_t(i) + c) * n] = cw;
+    }
+    // the path continues through child a
+    const uint4 ka0 = ch[0][a], ka1 = ch[1][a];
+    wb = (wb ^ (ka0.x >> 1) ^ (ka1.x >> 1) ^ (ck.x >> 1)) & 1u;
+    uint4 sk = ck;
+    sk.x &= ~3u;
+    const uint32_t tk = ck.x & 1u;
+    uint4 ns0 = xor4(ka0, and4(sk, 0u - t0));
+    uint4 ns1 = xor4(ka1, and4(sk, 0u - t1));
     ns0.x &= ~3u;
     ns1.x &= ~3u;
+    const uint32_t nt0 = (ka0.x ^ (t0 & tk)) & 1u, nt1 = (ka1.x ^ (t1 & tk)) & 1u;
     s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
   }
-  vbits |= uint64_t(((s1.x >> 2) ^ (s0.x >> 2) ^ va) & 1u) << k;
-  vcw0[0] = vbits;
-  vcw1[0] = vbits;
+  const uint64_t lf = ((s1.x >> 2) ^ (s0.x >> 2) ^ wb) & 1u;
+  leaf0[0] = lf;
+  leaf1[0] = lf;
 }
 
 // Payload words of V consecutive MMO blocks starting at tweak j0, for the
@@ -350,69 +387,115 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
   }
 }
 
-template <int P, class AES4>
+// Vector-payload DCF Gen of arity 4 for beta * 1[u < alpha] on k-bit u
+// (k <= 32), both parties.  keep(i, q): block 0 the path child's seed CW,
+// blocks 1..V its value CWs (p little-endian uint64).  Writes root and
+// child CWs (rows 1 + 4 i + c), value CWs vcw [levels][4][P][n] and the
+// leaf CWs [P][n].
+template <int P, class AES4, class KEEP>
 FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
-                           uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t n,
-                           const AES4 &aes4) {
+                           uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t *leaf0,
+                           uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP &keep) {
   constexpr uint32_t V = (P + 1) / 2;
   l0[0] = s0;
   l1[0] = s1;
+  const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1;
-  uint64_t va[P];
+  uint64_t W[P];
 #pragma unroll
-  for (int q = 0; q < P; ++q) va[q] = 0;
-  for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t a = (alpha >> (k - 1 - i)) & 1u;
-    const uint32_t keep = a, lose = 1u - a;
-    const Blk4 ex = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
-    const uint4 L0 = ex.v[0], R0 = ex.v[1], L1 = ex.v[2], R1 = ex.v[3];
-    // payloads: [0] party 0 lose side, [1] party 1 lose, [2] party 0 keep, [3] party 1 keep
-    const uint4 sd[4] = {s0, s1, s0, s1};
-    const uint32_t j0[4] = {2u + lose * V, 2u + lose * V, 2u + keep * V, 2u + keep * V};
-    uint64_t cv[4][P + 1];
-    conv4<P>(sd, j0, cv, aes4);
-    const bool neg = t1 != 0;
+  for (int q = 0; q < P; ++q) W[q] = 0;
+  for (uint32_t i = 0; i < nlev; ++i) {
+    const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
+    const uint32_t a = (alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
+    uint4 ch[2][4];
+    expand_children(s0, s1, nc, ch, aes4);
+    // payloads cv[b * 4 + c] of the children, four (seed, tweak) pairs per call
+    uint64_t cv[8][P + 1];
+    {
+      const uint4 sd[4] = {s0, s0, s1, s1};
+      const uint32_t j0[4] = {4u, 4u + V, 4u, 4u + V};
+      uint64_t o[4][P + 1];
+      conv4<P>(sd, j0, o, aes4);
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      uint64_t d = cv[1][q] - cv[0][q] - va[q];
-      if (lose == 0) d += beta[q];
-      const uint64_t vc = neg ? 0ull - d : d;
-      va[q] = va[q] - cv[3][q] + cv[2][q] + (neg ? 0ull - vc : vc);
-      vcw0[(uint64_t(i) * P + q) * n] = vc;
-      vcw1[(uint64_t(i) * P + q) * n] = vc;
+      for (int q = 0; q <= P; ++q) { cv[0][q] = o[0][q]; cv[1][q] = o[1][q]; cv[4][q] = o[2][q]; cv[5][q] = o[3][q]; }
+      if (nc == 4) {
+        const uint32_t j1[4] = {4u + 2 * V, 4u + 3 * V, 4u + 2 * V, 4u + 3 * V};
+        conv4<P>(sd, j1, o, aes4);
+#pragma unroll
+        for (int q = 0; q <= P; ++q) { cv[2][q] = o[0][q]; cv[3][q] = o[1][q]; cv[6][q] = o[2][q]; cv[7][q] = o[3][q]; }
+      }
     }
-    const uint4 lo0 = a ? L0 : R0, lo1 = a ? L1 : R1;
-    const uint4 ke0 = a ? R0 : L0, ke1 = a ? R1 : L1;
-    uint4 scw = xor4(lo0, lo1);
-    scw.x &= ~3u;
-    const uint32_t tl = (L0.x ^ L1.x ^ a ^ 1u) & 1u;
-    const uint32_t tr = (R0.x ^ R1.x ^ a) & 1u;
-    uint4 cw = scw;
-    cw.x |= tl | (tr << 1);
-    l0[(1 + uint64_t(i)) * n] = cw;
-    l1[(1 + uint64_t(i)) * n] = cw;
-    const uint32_t tk = a ? tr : tl;
-    const uint32_t m0 = 0u - t0, m1 = 0u - t1;
-    uint4 ns0 = xor4(ke0, and4(scw, m0));
-    uint4 ns1 = xor4(ke1, and4(scw, m1));
-    const uint32_t nt0 = (ke0.x ^ (t0 & tk)) & 1u;
-    const uint32_t nt1 = (ke1.x ^ (t1 & tk)) & 1u;
+    const bool neg = t1 != 0;
+    const uint4 R = keep(i, 0u);
+    uint64_t rv[2 * V];
+#pragma unroll
+    for (uint32_t q = 0; q < V; ++q) {
+      const uint4 rb = keep(i, 1u + q);
+      rv[2 * q] = lo64(rb);
+      rv[2 * q + 1] = hi64(rb);
+    }
+    uint4 ck = make_uint4(0, 0, 0, 0);
+    uint64_t vk[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) vk[q] = 0;
+#pragma unroll
+    for (uint32_t c = 0; c < 4; ++c) {
+      uint4 cw = make_uint4(0, 0, 0, 0);
+      uint64_t vc[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) vc[q] = 0;
+      if (c < nc) {
+        if (c != a) {
+          cw = xor4(ch[0][c], ch[1][c]);
+          cw.x = (cw.x & ~3u) | (cw.x & 1u);
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const uint64_t d = (c < a ? beta[q] : 0ull) - W[q] - cv[c][q] + cv[4 + c][q];
+            vc[q] = neg ? 0ull - d : d;
+          }
+        } else {
+          cw = R;
+          cw.x = (cw.x & ~3u) | ((ch[0][c].x ^ ch[1][c].x ^ 1u) & 1u);
+#pragma unroll
+          for (int q = 0; q < P; ++q) vc[q] = vk[q] = rv[q];
+          ck = cw;
+        }
+      }
+      const uint64_t row = 4 * uint64_t(i) + c;
+      l0[(1 + row) * n] = cw;
+      l1[(1 + row) * n] = cw;
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        vcw0[(row * P + q) * n] = vc[q];
+        vcw1[(row * P + q) * n] = vc[q];
+      }
+    }
+    // the path continues through child a
+#pragma unroll
+    for (int q = 0; q < P; ++q) W[q] = W[q] + cv[a][q] - cv[4 + a][q] + (neg ? 0ull - vk[q] : vk[q]);
+    const uint4 ka0 = ch[0][a], ka1 = ch[1][a];
+    uint4 sk = ck;
+    sk.x &= ~3u;
+    const uint32_t tk = ck.x & 1u;
+    uint4 ns0 = xor4(ka0, and4(sk, 0u - t0));
+    uint4 ns1 = xor4(ka1, and4(sk, 0u - t1));
     ns0.x &= ~3u;
     ns1.x &= ~3u;
+    const uint32_t nt0 = (ka0.x ^ (t0 & tk)) & 1u, nt1 = (ka1.x ^ (t1 & tk)) & 1u;
     s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
   }
-  // final correction word from the leaf conversions H(s, 2 + q) of both parties
+  // leaf CW from both parties' leaf conversions H(s, 4 + q)
   const uint4 sd[4] = {s0, s1, s0, s1};
-  const uint32_t j0[4] = {2u, 2u, 2u, 2u};
+  const uint32_t j0[4] = {4u, 4u, 4u, 4u};
   uint64_t f[4][P + 1];
   conv4<P>(sd, j0, f, aes4);
   const bool neg = t1 != 0;
 #pragma unroll
   for (int q = 0; q < P; ++q) {
-    const uint64_t d = f[1][q] - f[0][q] - va[q];
+    const uint64_t d = f[1][q] - f[0][q] - W[q];
     const uint64_t cw = neg ? 0ull - d : d;
-    vcw0[(uint64_t(k) * P + q) * n] = cw;
-    vcw1[(uint64_t(k) * P + q) * n] = cw;
+    leaf0[uint64_t(q) * n] = cw;
+    leaf1[uint64_t(q) * n] = cw;
   }
 }
 

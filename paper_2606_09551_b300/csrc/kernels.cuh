@@ -121,9 +121,9 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // inlined into the fused gate the compiler emitted about 40 % more
 // instructions per level.  One call per walk.
 __device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, uint64_t n,
-                                          uint64_t vcw, const char *tab, uint32_t lane4) {
+                                          uint64_t leaf, const char *tab, uint32_t lane4) {
   const AesDcfInline aes{Tab{tab, lane4}};
-  return dcf_bit_eval(b, f, u, root, n, vcw, aes);
+  return dcf_bit_eval(b, f, u, root, n, leaf, aes);
 }
 
 // One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
@@ -133,8 +133,8 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   const char *q = kb + L.off_q[t];
   const uint32_t f = S.q_f[t];
   const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
-  const uint64_t vcw = reinterpret_cast<const uint64_t *>(q + 16ull * (f + 1) * L.n)[e];
-  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, vcw, aes.tb.base, aes.tb.lane4);
+  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + 16ull * (1 + 4ull * key_levels(f)) * L.n)[e];
+  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
 }
 
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
@@ -144,9 +144,11 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
                                          const AesDcfInline &aes) {
   const uint32_t k = S.k;
   const char *l = kb + L.off_l[j];
+  const uint64_t lv = key_levels(k);
   const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
-  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (k + 1) * L.n) + e;
-  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, L.n, acc, aes);   // lookups: k <= 32
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + 4 * lv) * L.n) + e;
+  const uint64_t *leaf = vcw + 4 * lv * P * L.n;
+  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -697,11 +699,15 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       for (int q = 0; q < P; ++q) beta[q] = payload_word(S, ord[j - 1], q, r_in) - payload_word(S, ord[j], q, r_in);
       const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
       const uint4 s0 = prg(di), s1 = prg(di + 1);
+      const uint32_t kappa = S.T + j - 1;
+      auto keep = [&](uint32_t lvl, uint32_t q) { return prg(kDrawKeep + (32u * kappa + lvl) * 4u + q); };
       char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
+      const uint64_t lv = key_levels(S.k);
+      uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
+      uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
       dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                     reinterpret_cast<uint4 *>(l1) + e,
-                     reinterpret_cast<uint64_t *>(l0 + 16ull * (S.k + 1) * n) + e,
-                     reinterpret_cast<uint64_t *>(l1 + 16ull * (S.k + 1) * n) + e, n, rkd);
+                     reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
+                     keep);
     } else if (item < n_vec + S.T) {
       // packed-comparison key t: alpha = r_f for the r-atom, theta_j otherwise
       const uint32_t t = item - n_vec;
@@ -710,11 +716,13 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
       const int j = S.q_prim[t];
       const uint64_t alpha = j < 0 ? (r_in & mask) : (((r_in & mask) + S.prim_gamma[j]) & mask);
       const uint4 s0 = prg(S.base_roots + 2 * t), s1 = prg(S.base_roots + 2 * t + 1);
+      auto keep = [&](uint32_t lvl, uint32_t q) { return prg(kDrawKeep + (32u * t + lvl) * 4u + q); };
       char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
+      const uint64_t lv = key_levels(f);
       dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
                   reinterpret_cast<uint4 *>(q1) + e,
-                  reinterpret_cast<uint64_t *>(q0 + 16ull * (f + 1) * n) + e,
-                  reinterpret_cast<uint64_t *>(q1 + 16ull * (f + 1) * n) + e, n, rkd);
+                  reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
+                  reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep);
     } else {
       const uint64_t r0 = lo64(prg(kDrawRsh));
       reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;

@@ -31,6 +31,9 @@ constexpr uint32_t kDrawRsh = 1;
 constexpr uint32_t kDrawXsh = 2;
 constexpr uint32_t kDrawCarry = 3;
 constexpr uint32_t kDrawVlast = 4;
+// Path-child randomness of the DCF keys: key kappa (queries in order, then
+// lookup keys), level i, block q at draw kDrawKeep + (32 kappa + i) 4 + q.
+constexpr uint32_t kDrawKeep = 0x100000u;
 
 // Compiled operator specification (public).  Sec. 4.1 descriptor plus the
 // query list of App. F step (4) in its fixed descriptor order.
@@ -81,9 +84,10 @@ struct DevSpec {
 //   Boolean triples  u32  [n_pw][3][n]             (a, b, c), m packed bits each
 //   shift gate       u64  [3][n] ((r mod 2^k) >> s share, daBit additive shares lo, hi),
 //                    u32  [n] (daBit XOR shares, bits 0 and 1)
-//   query t          uint4 root[n], uint4 cw[k_t][n] (seed CW | t_L | t_R << 1),
-//                    u64 vcw[n] (bit i = V_CW of level i, bit k_t = final CW)
-//   lookup key j     uint4 root[n], uint4 cw[k][n], u64 vcw[k+1][p][n] (level k = final CW)
+//   query t          uint4 root[n], uint4 cw[L_t][4][n] (per child: seed CW | t CW |
+//                    value CW << 1), u64 leaf[n] (bit 0); L_t = ceil(k_t / 2) levels
+//   lookup key j     uint4 root[n], uint4 cw[L][4][n], u64 vcw[L][4][p][n],
+//                    u64 leaf[p][n]; L = ceil(k / 2)
 struct KeyLayout {
   uint64_t n;
   uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip, off_trunc, off_trunc_rho;
@@ -93,6 +97,15 @@ struct KeyLayout {
 };
 
 FFSS_HD uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
+
+// Tree levels of a k-bit DCF with two input bits per level (arity 4).
+FFSS_HD uint32_t key_levels(uint32_t k) { return (k + 1) / 2; }
+
+// Bytes per element of one comparison key (view width f) and one lookup key.
+FFSS_HD uint64_t query_key_bytes(uint32_t f) { return 16 + 64ull * key_levels(f) + 8; }
+FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p) {
+  return 16 + 64ull * key_levels(k) + 32ull * key_levels(k) * p + 8ull * p;
+}
 
 FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   KeyLayout L{};
@@ -108,11 +121,11 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_trunc_rho = o; o = align256(o + 4ull * tr * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
-    o = align256(o + 16ull * (s.q_f[t] + 1) * n + 8ull * n);
+    o = align256(o + query_key_bytes(s.q_f[t]) * n);
   }
   for (uint32_t j = 0; j + 1 < s.M; ++j) {
     L.off_l[j] = o;
-    o = align256(o + 16ull * (s.k + 1) * n + 8ull * (s.k + 1) * s.p * n);
+    o = align256(o + lookup_key_bytes(s.k, s.p) * n);
   }
   L.total = o < 256 ? 256 : o;
   return L;
@@ -121,28 +134,38 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
   uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_pw + (s.trunc_s ? 28 : 0);
-  for (uint32_t t = 0; t < s.T; ++t) b += 16ull * (s.q_f[t] + 1) + 8;
-  if (s.M > 1) b += (s.M - 1) * (16ull * (s.k + 1) + 8ull * (s.k + 1) * s.p);
+  for (uint32_t t = 0; t < s.T; ++t) b += query_key_bytes(s.q_f[t]);
+  if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p);
   return b;
 }
 
-// Online AES-128 blocks per element per party: k_t per query, k(1+V)+V per lookup key.
+// Online AES-128 blocks per element per party: one per level of a
+// comparison key, (1 + V) per level plus V at the leaf of a lookup key.
 inline uint64_t aes_per_elem(const DevSpec &s) {
   uint64_t a = 0;
-  for (uint32_t t = 0; t < s.T; ++t) a += s.q_f[t];
-  if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (1 + s.V) + s.V);
+  for (uint32_t t = 0; t < s.T; ++t) a += key_levels(s.q_f[t]);
+  if (s.M > 1) a += (s.M - 1) * (uint64_t(key_levels(s.k)) * (1 + s.V) + s.V);
   return a;
 }
 
-// Dealer AES-128 blocks per element: the CTR draws, then per DCF level both
-// children of both parties' seeds (4 blocks) and, for a lookup key, both
-// children's payload blocks of both parties (4V); the final lookup
-// correction needs both parties' leaf payloads (2V).
+// Dealer AES-128 blocks per element: the CTR draws (including the path
+// children's random correction words: one block per level of a comparison
+// key, 1 + V per level of a lookup key), then per level both parties'
+// children (2 x arity blocks) and, for a lookup key, their payload blocks
+// (2 x arity x V); the leaf needs both parties' conversions (2V).  A one-bit
+// first digit has arity 2.
 inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
   uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_pw +
                (s.trunc_s ? 5 : 0);
-  for (uint32_t t = 0; t < s.T; ++t) a += 4ull * s.q_f[t];
-  if (s.M > 1) a += (s.M - 1) * (uint64_t(s.k) * (4 + 4 * s.V) + 2 * s.V);
+  for (uint32_t t = 0; t < s.T; ++t) {
+    const uint32_t lv = key_levels(s.q_f[t]);
+    a += lv + 8ull * lv - ((s.q_f[t] & 1u) ? 4 : 0);
+  }
+  if (s.M > 1) {
+    const uint32_t lv = key_levels(s.k);
+    const uint64_t per = uint64_t(lv) * (1 + s.V) + (8ull * lv - ((s.k & 1u) ? 4 : 0)) * (1 + s.V) + 2ull * s.V;
+    a += (s.M - 1) * per;
+  }
   return a;
 }
 

@@ -1,7 +1,13 @@
 """Test-only mapping between the CUDA library's per-party key layout and the
 oracle's per-element key records.  The layout is the library's own choice
 (element-minor sections, each 256-byte aligned); the oracle compares shares
-and, through this transform, key material."""
+and, through this transform, key material.
+
+DCF keys have arity 4 (two input bits per tree level).  Per comparison key
+of view width f (L = ceil(f/2) levels): root uint4[n], child correction
+words uint4[L][4][n] (seed CW with the t CW in bit 0 and the value CW in bit
+1), the leaf CW u64[n].  Per lookup key (k bits, payload p): root, child
+CWs uint4[L][4][n], value CWs u64[L][4][p][n], leaf CWs u64[p][n]."""
 from __future__ import annotations
 
 import numpy as np
@@ -13,9 +19,12 @@ def _a256(v):
     return (v + 255) & ~255
 
 
+def _lv(f):
+    return (f + 1) // 2
+
+
 def offsets(ospec: O.Spec, n: int):
     """Section offsets for n elements (the library's layout, restated)."""
-    q = ospec.queries()
     o = 0
     off = {}
     off["r"] = o; o = _a256(o + 8 * n)
@@ -27,13 +36,14 @@ def offsets(ospec: O.Spec, n: int):
     off["trunc"] = o; o = _a256(o + 24 * tr * n)
     off["trunc_rho"] = o; o = _a256(o + 4 * tr * n)
     off["q"] = []
-    for (f, c, pr) in q:
+    for (f, c, pr) in ospec.queries():
         off["q"].append(o)
-        o = _a256(o + 16 * (f + 1) * n + 8 * n)
+        o = _a256(o + (16 + 64 * _lv(f) + 8) * n)
     off["l"] = []
     for j in range(ospec.M - 1):
         off["l"].append(o)
-        o = _a256(o + 16 * (ospec.k + 1) * n + 8 * (ospec.k + 1) * ospec.p * n)
+        lv = _lv(ospec.k)
+        o = _a256(o + (16 + 64 * lv + 32 * lv * ospec.p + 8 * ospec.p) * n)
     off["total"] = max(o, 256)
     return off
 
@@ -48,6 +58,22 @@ def _u32(buf, off, count):
 
 def _blocks(buf, off, count):
     return buf[off: off + 16 * count].reshape(count, 16)
+
+
+def _gpu_key(buf, base, n, e, k, p):
+    lv = _lv(k)
+    blk = _blocks(buf, base, (1 + 4 * lv) * n)
+    root = blk[e].copy()
+    cw = np.stack([blk[(1 + row) * n + e] for row in range(4 * lv)]).reshape(lv, 4, 16)
+    tail = base + 16 * (1 + 4 * lv) * n
+    if p == 0:
+        return dict(root=root, cw=cw, leaf_bit=int(_u64(buf, tail, n)[e]) & 1)
+    v = _u64(buf, tail, 4 * lv * p * n)
+    vcw = np.array([[[v[((i * 4 + c) * p + q) * n + e] for q in range(p)] for c in range(4)] for i in range(lv)],
+                   np.uint64)
+    lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
+    leaf = np.array([lf[q * n + e] for q in range(p)], np.uint64)
+    return dict(root=root, cw=cw, vcw=vcw, leaf=leaf)
 
 
 def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
@@ -70,29 +96,13 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
         tt = _u64(buf, off["trunc"], 3 * n)
         out.update(tr_t=int(tt[e]), tr_rho=int(_u32(buf, off["trunc_rho"], n)[e]),
                    tr_rho_a=np.array([tt[n + e], tt[2 * n + e]], np.uint64))
-    qk = []
-    for t, (f, c, pr) in enumerate(ospec.queries()):
-        blk = _blocks(buf, off["q"][t], (f + 1) * n)
-        root = blk[e].copy()
-        cws = np.stack([blk[(1 + i) * n + e] for i in range(f)]) if f else np.zeros((0, 16), np.uint8)
-        vcw = int(_u64(buf, off["q"][t] + 16 * (f + 1) * n, n)[e])
-        qk.append(dict(root=root, cw=cws, vcw=vcw, k=f))
-    out["q"] = qk
-    lk = []
-    for j in range(ospec.M - 1):
-        blk = _blocks(buf, off["l"][j], (k + 1) * n)
-        root = blk[e].copy()
-        cws = np.stack([blk[(1 + i) * n + e] for i in range(k)])
-        v = _u64(buf, off["l"][j] + 16 * (k + 1) * n, (k + 1) * p * n)
-        vcw = np.array([[v[(i * p + q) * n + e] for q in range(p)] for i in range(k + 1)], np.uint64)
-        lk.append(dict(root=root, cw=cws, vcw=vcw))
-    out["l"] = lk
+    out["q"] = [_gpu_key(buf, off["q"][t], n, e, f, 0) for t, (f, c, pr) in enumerate(ospec.queries())]
+    out["l"] = [_gpu_key(buf, off["l"][j], n, e, k, p) for j in range(ospec.M - 1)]
     return out
 
 
 def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
-    """The same fields from an oracle key record, correction words packed
-    the library's way (t_L in bit 0, t_R in bit 1 of the seed correction)."""
+    """The same fields from an oracle key record."""
     base = keys.fields(ospec, i)
     out = dict(r_share=base["r_share"], carry=base["carry"], vlast=base["vlast"],
                ta=base["ta"], tb=base["tb"], tc=base["tc"], ba=base["ba"], bb=base["bb"], bc=base["bc"])
@@ -100,20 +110,15 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
         if key in base:
             out[key] = base[key]
     qk = []
-    for t, (f, c, pr) in enumerate(ospec.queries()):
-        fl = keys.qkey(i, t).fields(f, 0)
-        cws = fl["scw"].copy()
-        if f:
-            cws[:, 0] |= fl["tcw_l"] | (fl["tcw_r"] << 1)
-        vcw = sum(int(fl["vcw_bit"][lv]) << lv for lv in range(f + 1))
-        qk.append(dict(root=fl["root"], cw=cws, vcw=vcw, k=f))
+    for t in range(ospec.T):
+        fl = keys.qkey(i, t).fields()
+        assert fl["r"] == 2
+        qk.append(dict(root=fl["root"], cw=fl["cw"], leaf_bit=fl["leaf_bit"]))
     out["q"] = qk
     lk = []
     for j in range(1, ospec.M):
-        fl = keys.lkey(i, j).fields(ospec.k, ospec.p)
-        cws = fl["scw"].copy()
-        cws[:, 0] |= fl["tcw_l"] | (fl["tcw_r"] << 1)
-        lk.append(dict(root=fl["root"], cw=cws, vcw=fl["vcw"].astype(np.uint64)))
+        fl = keys.lkey(i, j).fields()
+        lk.append(dict(root=fl["root"], cw=fl["cw"], vcw=fl["vcw"].astype(np.uint64), leaf=fl["leaf"]))
     out["l"] = lk
     return out
 
@@ -128,15 +133,17 @@ def fields_equal(a, b) -> bool:
     for key in ("vlast", "ta", "tb", "tc", "ba", "bb", "bc"):
         if not np.array_equal(a[key], b[key]):
             return False
+    if len(a["q"]) != len(b["q"]) or len(a["l"]) != len(b["l"]):
+        return False
     for qa, qb in zip(a["q"], b["q"]):
         if not (np.array_equal(qa["root"], qb["root"]) and np.array_equal(qa["cw"], qb["cw"])
-                and qa["vcw"] == qb["vcw"]):
+                and qa["leaf_bit"] == qb["leaf_bit"]):
             return False
     for la, lb in zip(a["l"], b["l"]):
         if not (np.array_equal(la["root"], lb["root"]) and np.array_equal(la["cw"], lb["cw"])
-                and np.array_equal(la["vcw"], lb["vcw"])):
+                and np.array_equal(la["vcw"], lb["vcw"]) and np.array_equal(la["leaf"], lb["leaf"])):
             return False
-    return len(a["q"]) == len(b["q"]) and len(a["l"]) == len(b["l"])
+    return True
 
 
 def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
@@ -168,18 +175,25 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             tt[e], tt[n + e], tt[2 * n + e] = fl["tr_t"], fl["tr_rho_a"][0], fl["tr_rho_a"][1]
             _u32(buf, off["trunc_rho"], n)[e] = fl["tr_rho"]
         for t, (f, c, pr) in enumerate(qs):
-            blk = _blocks(buf, off["q"][t], (f + 1) * n)
+            lv = _lv(f)
+            blk = _blocks(buf, off["q"][t], (1 + 4 * lv) * n)
             blk[e] = fl["q"][t]["root"]
-            for i in range(f):
-                blk[(1 + i) * n + e] = fl["q"][t]["cw"][i]
-            _u64(buf, off["q"][t] + 16 * (f + 1) * n, n)[e] = fl["q"][t]["vcw"]
+            for row in range(4 * lv):
+                blk[(1 + row) * n + e] = fl["q"][t]["cw"][row // 4, row % 4]
+            _u64(buf, off["q"][t] + 16 * (1 + 4 * lv) * n, n)[e] = fl["q"][t]["leaf_bit"]
         for j in range(ospec.M - 1):
-            blk = _blocks(buf, off["l"][j], (k + 1) * n)
+            lv = _lv(k)
+            blk = _blocks(buf, off["l"][j], (1 + 4 * lv) * n)
             blk[e] = fl["l"][j]["root"]
-            for i in range(k):
-                blk[(1 + i) * n + e] = fl["l"][j]["cw"][i]
-            v = _u64(buf, off["l"][j] + 16 * (k + 1) * n, (k + 1) * p * n)
-            for i in range(k + 1):
-                for q in range(p):
-                    v[(i * p + q) * n + e] = fl["l"][j]["vcw"][i][q]
+            for row in range(4 * lv):
+                blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // 4, row % 4]
+            tail = off["l"][j] + 16 * (1 + 4 * lv) * n
+            v = _u64(buf, tail, 4 * lv * p * n)
+            for i in range(lv):
+                for c in range(4):
+                    for q in range(p):
+                        v[((i * 4 + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
+            lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
+            for q in range(p):
+                lf[q * n + e] = fl["l"][j]["leaf"][q]
     return buf

@@ -56,12 +56,14 @@ def _shape_vs_oracle(sp, may_reject=False):
     assert sh.trunc_shift == sp.trunc_shift
     assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_pw + tr
     qs = o.queries()
-    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + 28 * tr + sum(16 * (f + 1) + 8 for f, _, _ in qs)
-    if o.M > 1:
-        kb += (o.M - 1) * (16 * (o.k + 1) + 8 * (o.k + 1) * o.p)
+    lv = lambda f: (f + 1) // 2          # tree levels: two input bits per level (arity 4)
+    # a comparison key: root, 4 child CWs per level, the leaf CW word
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + 28 * tr + sum(16 + 64 * lv(f) + 8 for f, _, _ in qs)
+    if o.M > 1:   # a lookup key: root, 4 child CWs and 4 x p value CWs per level, p leaf CWs
+        kb += (o.M - 1) * (16 + 64 * lv(o.k) + 32 * lv(o.k) * o.p + 8 * o.p)
     assert sh.key_bytes_per_elem == kb
     V = (o.p + 1) // 2
-    aes = sum(f for f, _, _ in qs) + ((o.M - 1) * (o.k * (1 + V) + V) if o.M > 1 else 0)
+    aes = sum(lv(f) for f, _, _ in qs) + ((o.M - 1) * (lv(o.k) * (1 + V) + V) if o.M > 1 else 0)
     assert sh.aes_per_elem == aes
     return sh
 
@@ -69,11 +71,11 @@ def _shape_vs_oracle(sp, may_reject=False):
 def test_workload_spec_shapes():
     # per-element key bytes and AES blocks of the workload specs
     sh = _shape_vs_oracle(S.gelu4())
-    assert (sh.T, sh.M, sh.p) == (4, 5, 3) and sh.aes_per_elem == 64 + 4 * (16 * 3 + 2)
+    assert (sh.T, sh.M, sh.p) == (4, 5, 3) and sh.aes_per_elem == 4 * 8 + 4 * (8 * 3 + 2)
     sh = _shape_vs_oracle(S.gelu8())
-    assert sh.aes_per_elem == 528
+    assert sh.aes_per_elem == 8 * 8 + 8 * (8 * 3 + 2)
     sh = _shape_vs_oracle(S.nexp16())
-    assert sh.aes_per_elem == 16 * 24 + 16 * (24 * 3 + 2)
+    assert sh.aes_per_elem == 16 * 12 + 16 * (12 * 3 + 2)
     for sp in (S.recip16(), S.rsqrt16(), S.silu16(), S.relu(16), S.relu(4)):
         _shape_vs_oracle(sp)
     # x^-basis variant: no Beaver multiplications, no triples in the keys, 8 B online
@@ -81,7 +83,7 @@ def test_workload_spec_shapes():
     assert sh.n_mults == 0 and sh.comm_bytes_per_elem == 8
     # shift gate: two bit-DCF queries of s and k levels, 9 bytes online
     sh = _shape_vs_oracle(S.trunc(32, 12, True))
-    assert (sh.T, sh.M, sh.aes_per_elem, sh.comm_bytes_per_elem) == (2, 1, 12 + 32, 9)
+    assert (sh.T, sh.M, sh.aes_per_elem, sh.comm_bytes_per_elem) == (2, 1, 6 + 16, 9)
 
 
 def test_random_spec_shapes():
