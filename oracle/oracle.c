@@ -759,8 +759,9 @@ static uint64_t prg_u64(const or_prg *g, uint32_t draw, uint64_t elem)
 #define DRAW_XSH 2
 #define DRAW_CARRY 3
 #define DRAW_VLAST 4
-/* path-child randomness of the DCF keys: key kappa (queries in order, then
- * lookup keys), level i, block q at draw DRAW_KEEP + (32 kappa + i) 4 + q */
+/* path-child randomness of the DCF keys: one fresh secret block per key
+ * kappa (queries in order, then lookup keys) at draw DRAW_KEEP + kappa,
+ * expanded by the DCF's own PRG: block q of level i is H(base, 4 i + q) */
 #define DRAW_KEEP 0x100000u
 
 /* ------------------------------------------------------------------------ */
@@ -908,9 +909,10 @@ static void payload(const or_spec *sp, uint32_t piece, uint64_t r_in, uint64_t *
 static void keep_rand(const or_prg *g, uint32_t kappa, int nlev, int p, uint64_t e, uint8_t *out)
 {
     int nb = 1 + (p ? nblocks_for(p) : 0);
+    uint8_t base[16];
+    prg_block(g, DRAW_KEEP + kappa, e, base);
     for (int i = 0; i < nlev; i++)
-        for (int q = 0; q < nb; q++)
-            prg_block(g, DRAW_KEEP + (32u * kappa + (uint32_t)i) * 4u + (uint32_t)q, e, out + (size_t)(i * nb + q) * 16);
+        for (int q = 0; q < nb; q++) mmo(base, (uint32_t)(4 * i + q), out + (size_t)(i * nb + q) * 16);
 }
 
 void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,

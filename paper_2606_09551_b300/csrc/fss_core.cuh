@@ -318,23 +318,26 @@ FFSS_CORE void expand_children(uint4 s0, uint4 s1, uint32_t nc, uint4 (&ch)[2][4
 }
 
 // Bit-payload DCF Gen of arity 4 for 1[u < alpha] on k-bit u, both parties.
-// keep(i, q) returns the q-th random block of level i for the path child
-// (block 0: its seed CW, and bit 1 its value CW).  Writes root and child CWs
-// (rows 1 + 4 i + c) and the leaf CW bit into both keys.
-template <class AES4, class KEEP>
+// keep4(i0) returns the path child's random block 0 of levels i0 .. i0 + 3
+// (its seed CW, and bit 1 its value CW).  Writes root and child CWs (rows
+// 1 + 4 i + c) and the leaf CW bit into both keys.
+template <class AES4, class KEEP4>
 FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
-                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP &keep) {
+                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   q0[0] = s0;
   q1[0] = s1;
   const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1, wb = 0;
+  Blk4 R4;
   for (uint32_t i = 0; i < nlev; ++i) {
     const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
     const uint32_t a = uint32_t(alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
     uint4 ch[2][4];
     expand_children(s0, s1, nc, ch, aes4);
-    const uint4 R = keep(i, 0u);
-    uint4 ck = make_uint4(0, 0, 0, 0);
+    if ((i & 3u) == 0) R4 = keep4(i);
+    const uint32_t ri = i & 3u;
+    const uint4 R = ri == 0 ? R4.v[0] : ri == 1 ? R4.v[1] : ri == 2 ? R4.v[2] : R4.v[3];
+    uint4 ck = make_uint4(0, 0, 0, 0), ka0 = ck, ka1 = ck;
 #pragma unroll
     for (uint32_t c = 0; c < 4; ++c) {
       uint4 cw = make_uint4(0, 0, 0, 0);
@@ -348,13 +351,14 @@ FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4
           cw = R;
           cw.x = (cw.x & ~3u) | ((ch[0][c].x ^ ch[1][c].x ^ 1u) & 1u) | (R.x & 2u);
           ck = cw;
+          ka0 = ch[0][c];
+          ka1 = ch[1][c];
         }
       }
       q0[(1 + 4 * uint64_t(i) + c) * n] = cw;
       q1[(1 + 4 * uint64_t(i) + c) * n] = cw;
     }
     // the path continues through child a
-    const uint4 ka0 = ch[0][a], ka1 = ch[1][a];
     wb = (wb ^ (ka0.x >> 1) ^ (ka1.x >> 1) ^ (ck.x >> 1)) & 1u;
     uint4 sk = ck;
     sk.x &= ~3u;
@@ -388,14 +392,15 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
 }
 
 // Vector-payload DCF Gen of arity 4 for beta * 1[u < alpha] on k-bit u
-// (k <= 32), both parties.  keep(i, q): block 0 the path child's seed CW,
-// blocks 1..V its value CWs (p little-endian uint64).  Writes root and
+// (k <= 32), both parties.  keep4(i): the path child's random blocks of
+// level i; block 0 its seed CW, blocks 1..V its value CWs (p little-endian
+// uint64).  Writes root and
 // child CWs (rows 1 + 4 i + c), value CWs vcw [levels][4][P][n] and the
 // leaf CWs [P][n].
-template <int P, class AES4, class KEEP>
+template <int P, class AES4, class KEEP4>
 FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
                            uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t *leaf0,
-                           uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP &keep) {
+                           uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   constexpr uint32_t V = (P + 1) / 2;
   l0[0] = s0;
   l1[0] = s1;
@@ -407,73 +412,86 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
   for (uint32_t i = 0; i < nlev; ++i) {
     const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
     const uint32_t a = (alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
-    uint4 ch[2][4];
-    expand_children(s0, s1, nc, ch, aes4);
-    // payloads cv[b * 4 + c] of the children, four (seed, tweak) pairs per call
-    uint64_t cv[8][P + 1];
-    {
-      const uint4 sd[4] = {s0, s0, s1, s1};
-      const uint32_t j0[4] = {4u, 4u + V, 4u, 4u + V};
-      uint64_t o[4][P + 1];
-      conv4<P>(sd, j0, o, aes4);
-#pragma unroll
-      for (int q = 0; q <= P; ++q) { cv[0][q] = o[0][q]; cv[1][q] = o[1][q]; cv[4][q] = o[2][q]; cv[5][q] = o[3][q]; }
-      if (nc == 4) {
-        const uint32_t j1[4] = {4u + 2 * V, 4u + 3 * V, 4u + 2 * V, 4u + 3 * V};
-        conv4<P>(sd, j1, o, aes4);
-#pragma unroll
-        for (int q = 0; q <= P; ++q) { cv[2][q] = o[0][q]; cv[3][q] = o[1][q]; cv[6][q] = o[2][q]; cv[7][q] = o[3][q]; }
-      }
-    }
     const bool neg = t1 != 0;
-    const uint4 R = keep(i, 0u);
-    uint64_t rv[2 * V];
+    const Blk4 K4 = keep4(i);
+    uint4 ck = make_uint4(0, 0, 0, 0), ka0 = ck, ka1 = ck;
+    uint64_t vk[P], ca0[P], ca1[P];
 #pragma unroll
-    for (uint32_t q = 0; q < V; ++q) {
-      const uint4 rb = keep(i, 1u + q);
-      rv[2 * q] = lo64(rb);
-      rv[2 * q + 1] = hi64(rb);
-    }
-    uint4 ck = make_uint4(0, 0, 0, 0);
-    uint64_t vk[P];
+    for (int q = 0; q < P; ++q) vk[q] = ca0[q] = ca1[q] = 0;
+    // children in pairs (cp, cp + 1): seeds of both parties in one 4-block call
 #pragma unroll
-    for (int q = 0; q < P; ++q) vk[q] = 0;
+    for (uint32_t cp = 0; cp < 4; cp += 2) {
+      uint4 e[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      uint64_t pv[2][2][P + 1];     // [child - cp][party][word]
+      if (cp < nc) {
+        const Blk4 sb = mmo4(s0, cp, s1, cp, s0, cp + 1, s1, cp + 1, aes4);
+        e[0] = sb.v[0]; e[1] = sb.v[1]; e[2] = sb.v[2]; e[3] = sb.v[3];
+        if (V == 1) {
+          const Blk4 pb = mmo4(s0, 4u + cp, s1, 4u + cp, s0, 4u + cp + 1, s1, 4u + cp + 1, aes4);
 #pragma unroll
-    for (uint32_t c = 0; c < 4; ++c) {
-      uint4 cw = make_uint4(0, 0, 0, 0);
-      uint64_t vc[P];
-#pragma unroll
-      for (int q = 0; q < P; ++q) vc[q] = 0;
-      if (c < nc) {
-        if (c != a) {
-          cw = xor4(ch[0][c], ch[1][c]);
-          cw.x = (cw.x & ~3u) | (cw.x & 1u);
-#pragma unroll
-          for (int q = 0; q < P; ++q) {
-            const uint64_t d = (c < a ? beta[q] : 0ull) - W[q] - cv[c][q] + cv[4 + c][q];
-            vc[q] = neg ? 0ull - d : d;
+          for (int w = 0; w < 4; ++w) {
+            pv[w >> 1][w & 1][0] = lo64(pb.v[w]);
+            pv[w >> 1][w & 1][1] = hi64(pb.v[w]);
           }
         } else {
-          cw = R;
-          cw.x = (cw.x & ~3u) | ((ch[0][c].x ^ ch[1][c].x ^ 1u) & 1u);
 #pragma unroll
-          for (int q = 0; q < P; ++q) vc[q] = vk[q] = rv[q];
-          ck = cw;
+          for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t j = 4u + (cp + h) * V;
+            const Blk4 pb = mmo4(s0, j, s0, j + 1, s1, j, s1, j + 1, aes4);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+              pv[h][b][0] = lo64(pb.v[2 * b]);
+              pv[h][b][1] = hi64(pb.v[2 * b]);
+              pv[h][b][2] = lo64(pb.v[2 * b + 1]);
+              if (P > 3) pv[h][b][3] = hi64(pb.v[2 * b + 1]);
+            }
+          }
         }
       }
-      const uint64_t row = 4 * uint64_t(i) + c;
-      l0[(1 + row) * n] = cw;
-      l1[(1 + row) * n] = cw;
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        vcw0[(row * P + q) * n] = vc[q];
-        vcw1[(row * P + q) * n] = vc[q];
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t c = cp + h;
+        const uint4 c0 = e[h * 2], c1 = e[h * 2 + 1];   // party 0 / party 1 child c
+        uint4 cw = make_uint4(0, 0, 0, 0);
+        uint64_t vc[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) vc[q] = 0;
+        if (c < nc) {
+          if (c != a) {
+            cw = xor4(c0, c1);
+            cw.x = (cw.x & ~3u) | (cw.x & 1u);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              const uint64_t d = (c < a ? beta[q] : 0ull) - W[q] - pv[h][0][q] + pv[h][1][q];
+              vc[q] = neg ? 0ull - d : d;
+            }
+          } else {
+            cw = K4.v[0];
+            cw.x = (cw.x & ~3u) | ((c0.x ^ c1.x ^ 1u) & 1u);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              vc[q] = vk[q] = (q & 1) ? hi64(K4.v[1 + q / 2]) : lo64(K4.v[1 + q / 2]);
+              ca0[q] = pv[h][0][q];
+              ca1[q] = pv[h][1][q];
+            }
+            ck = cw;
+            ka0 = c0;
+            ka1 = c1;
+          }
+        }
+        const uint64_t row = 4 * uint64_t(i) + c;
+        l0[(1 + row) * n] = cw;
+        l1[(1 + row) * n] = cw;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          vcw0[(row * P + q) * n] = vc[q];
+          vcw1[(row * P + q) * n] = vc[q];
+        }
       }
     }
     // the path continues through child a
 #pragma unroll
-    for (int q = 0; q < P; ++q) W[q] = W[q] + cv[a][q] - cv[4 + a][q] + (neg ? 0ull - vk[q] : vk[q]);
-    const uint4 ka0 = ch[0][a], ka1 = ch[1][a];
+    for (int q = 0; q < P; ++q) W[q] = W[q] + ca0[q] - ca1[q] + (neg ? 0ull - vk[q] : vk[q]);
     uint4 sk = ck;
     sk.x &= ~3u;
     const uint32_t tk = ck.x & 1u;

@@ -653,6 +653,66 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
 // GPU dealer
 // ---------------------------------------------------------------------------
 
+// Dealer work items, each compiled out of line (its own register
+// allocation): one lookup key or one comparison key of 32 elements.
+template <int P>
+__device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
+                                            uint64_t e, uint64_t ge, uint64_t r_in, uint32_t item) {
+  const KeyLayout &L = A.L;
+  const uint64_t n = A.n;
+  const AesDcfCall4 rkd{tb};
+  auto prg = [&](uint32_t dr) {
+    return aes_rk_call(make_uint4(dr, uint32_t(ge), uint32_t(ge >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
+  };
+  // lookup key j = item + 1: boundary B_j, payload step v_{j-1} - v_j
+  uint64_t B[kMaxM + 2];
+  uint32_t ord[kMaxM + 1];
+  lookup_boundaries(S, r_in, B, ord);
+  const uint32_t j = item + 1;
+  uint64_t beta[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) beta[q] = payload_word(S, ord[j - 1], q, r_in) - payload_word(S, ord[j], q, r_in);
+  const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
+  const uint4 s0 = prg(di), s1 = prg(di + 1);
+  const uint4 base = prg(kDrawKeep + S.T + j - 1);
+  auto keep4 = [&](uint32_t lvl) {   // the 4 blocks of level lvl: H(base, 4 lvl + w)
+    return mmo4(base, 4u * lvl, base, 4u * lvl + 1, base, 4u * lvl + 2, base, 4u * lvl + 3, rkd);
+  };
+  char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
+  const uint64_t lv = key_levels(S.k);
+  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
+  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
+  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
+                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
+                 keep4);
+}
+
+__device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
+                                           uint64_t e, uint64_t ge, uint64_t r_in, uint32_t t) {
+  const KeyLayout &L = A.L;
+  const uint64_t n = A.n;
+  const AesDcfCall4 rkd{tb};
+  auto prg = [&](uint32_t dr) {
+    return aes_rk_call(make_uint4(dr, uint32_t(ge), uint32_t(ge >> 32), A.call_id), rk_prg, tb.base, tb.lane4);
+  };
+  // packed-comparison key t: alpha = r_f for the r-atom, theta_j otherwise
+  const uint32_t f = S.q_f[t];
+  const uint64_t mask = (uint64_t(1) << f) - 1;
+  const int j = S.q_prim[t];
+  const uint64_t alpha = j < 0 ? (r_in & mask) : (((r_in & mask) + S.prim_gamma[j]) & mask);
+  const uint4 s0 = prg(S.base_roots + 2 * t), s1 = prg(S.base_roots + 2 * t + 1);
+  const uint4 base = prg(kDrawKeep + t);
+  auto keep4 = [&](uint32_t lvl0) {   // block 0 of levels lvl0 .. lvl0 + 3: H(base, 4 (lvl0 + w))
+    return mmo4(base, 4u * lvl0, base, 4u * (lvl0 + 1), base, 4u * (lvl0 + 2), base, 4u * (lvl0 + 3), rkd);
+  };
+  char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
+  const uint64_t lv = key_levels(f);
+  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
+              reinterpret_cast<uint4 *>(q1) + e,
+              reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
+              reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
+}
+
 template <int P>
 __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ KeygenArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -689,40 +749,9 @@ __global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ 
     };
     const uint64_t r_in = lo64(prg(kDrawRin));
     if (item < n_vec) {
-      // lookup key j = item + 1: boundary B_j, payload step v_{j-1} - v_j
-      uint64_t B[kMaxM + 2];
-      uint32_t ord[kMaxM + 1];
-      lookup_boundaries(S, r_in, B, ord);
-      const uint32_t j = item + 1;
-      uint64_t beta[P];
-#pragma unroll
-      for (int q = 0; q < P; ++q) beta[q] = payload_word(S, ord[j - 1], q, r_in) - payload_word(S, ord[j], q, r_in);
-      const uint32_t di = S.base_roots + 2 * (S.T + j - 1);
-      const uint4 s0 = prg(di), s1 = prg(di + 1);
-      const uint32_t kappa = S.T + j - 1;
-      auto keep = [&](uint32_t lvl, uint32_t q) { return prg(kDrawKeep + (32u * kappa + lvl) * 4u + q); };
-      char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
-      const uint64_t lv = key_levels(S.k);
-      uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
-      uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
-      dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                     reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
-                     keep);
+      gen_lookup_key<P>(A, S, rk_prg, tb, e, ge, r_in, item);
     } else if (item < n_vec + S.T) {
-      // packed-comparison key t: alpha = r_f for the r-atom, theta_j otherwise
-      const uint32_t t = item - n_vec;
-      const uint32_t f = S.q_f[t];
-      const uint64_t mask = (uint64_t(1) << f) - 1;
-      const int j = S.q_prim[t];
-      const uint64_t alpha = j < 0 ? (r_in & mask) : (((r_in & mask) + S.prim_gamma[j]) & mask);
-      const uint4 s0 = prg(S.base_roots + 2 * t), s1 = prg(S.base_roots + 2 * t + 1);
-      auto keep = [&](uint32_t lvl, uint32_t q) { return prg(kDrawKeep + (32u * t + lvl) * 4u + q); };
-      char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
-      const uint64_t lv = key_levels(f);
-      dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
-                  reinterpret_cast<uint4 *>(q1) + e,
-                  reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
-                  reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep);
+      gen_query_key(A, S, rk_prg, tb, e, ge, r_in, item - n_vec);
     } else {
       const uint64_t r0 = lo64(prg(kDrawRsh));
       reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;

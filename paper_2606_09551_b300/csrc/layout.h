@@ -31,8 +31,9 @@ constexpr uint32_t kDrawRsh = 1;
 constexpr uint32_t kDrawXsh = 2;
 constexpr uint32_t kDrawCarry = 3;
 constexpr uint32_t kDrawVlast = 4;
-// Path-child randomness of the DCF keys: key kappa (queries in order, then
-// lookup keys), level i, block q at draw kDrawKeep + (32 kappa + i) 4 + q.
+// Path-child randomness of the DCF keys: one fresh secret block per key
+// kappa (queries in order, then lookup keys) at draw kDrawKeep + kappa,
+// expanded by the DCF's own PRG: block q of level i is H(base, 4 i + q).
 constexpr uint32_t kDrawKeep = 0x100000u;
 
 // Compiled operator specification (public).  Sec. 4.1 descriptor plus the
