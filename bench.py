@@ -54,7 +54,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (3.388992e9 + 4.675840e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.254390e9 + 5.161984e6) / 65536}
 
 
 def parse():
@@ -332,30 +332,43 @@ def run_ours(args, rank, world, local_rank):
         step(warm)
     torch.cuda.synchronize()
     del warm
-    # dealer: K key sets, timed separately
-    sets = [KeySet() for _ in range(args.steps)]
+    # dealer: as many key sets as HBM holds (one-time keys: one set per step),
+    # timed separately
+    set_bytes = sum(2 * css[c.name].key_bytes(c.n) for c in calls)
+    G = sets_that_fit(set_bytes, args.steps)
+    sets = [KeySet() for _ in range(G)]
     kg0, kg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kg0.record(stream)
     for s, ks in enumerate(sets):
         ks.generate(s)
     kg1.record(stream)
     torch.cuda.synchronize()
-    keygen_ms = kg0.elapsed_time(kg1) / args.steps
+    keygen_ms = kg0.elapsed_time(kg1) / G
 
-    # timed region: K steps, inputs resident in HBM (keys > L2 every step)
+    # timed region: K steps on fresh keys, inputs resident in HBM (keys > L2
+    # every step); when K sets do not fit, the K steps run in groups of G
+    # sets, the dealer refilling them between groups outside the timing
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             for _ in calls] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
+    total_ms = 0.0
     with ClockSampler(local_rank) as clk:
-        t0.record(stream)
-        for s in range(args.steps):
-            step(sets[s], evs[s])
-        t1.record(stream)
-        torch.cuda.synchronize()
-    barrier(world)
-    ms = t0.elapsed_time(t1) / args.steps
+        for g0 in range(0, args.steps, G):
+            gs = min(G, args.steps - g0)
+            if g0 > 0:
+                for s in range(gs):
+                    sets[s].generate(g0 + s)
+            torch.cuda.synchronize()
+            barrier(world)
+            torch.cuda.synchronize()
+            t0.record(stream)
+            for s in range(gs):
+                step(sets[s], evs[g0 + s])
+            t1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            total_ms += t0.elapsed_time(t1)
+    ms = total_ms / args.steps
     ms = max_over_ranks(ms, world, dev)
     per_op_ms = {c.name: statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
                  for i, c in enumerate(calls)}
@@ -364,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public API: host (pinned) input shares in, shares out
     e2e = None
     if not args.no_e2e:
+        ne = len(sets)                         # steps on resident fresh key sets
         for s, ks in enumerate(sets):
             ks.generate(100 + s)
         host_in, host_out = {}, {}
@@ -376,9 +390,9 @@ def run_ours(args, rank, world, local_rank):
         d2h = sum(2 * 8 * c.n * c.spec.n_out + 2 * 4 * c.n for c in calls)
         copy = torch.cuda.Stream(device=dev)
         ev = lambda: torch.cuda.Event()
-        in_ready = [[ev() for _ in calls] for _ in range(args.steps)]
-        done = [[ev() for _ in calls] for _ in range(args.steps)]
-        out_free = [[ev() for _ in calls] for _ in range(args.steps)]
+        in_ready = [[ev() for _ in calls] for _ in range(ne)]
+        done = [[ev() for _ in calls] for _ in range(ne)]
+        out_free = [[ev() for _ in calls] for _ in range(ne)]
         torch.cuda.synchronize()
         barrier(world)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -389,13 +403,13 @@ def run_ours(args, rank, world, local_rank):
         # as it is evaluated; outputs are reused across steps, so an
         # evaluation waits for the previous step's copy-out of its buffers
         with torch.cuda.stream(copy):
-            for s in range(args.steps):
+            for s in range(ne):
                 for i, c in enumerate(calls):
                     k0, k1, x0, x1 = sets[s].k[c.name]
                     x0.copy_(host_in[c.name][0], non_blocking=True)
                     x1.copy_(host_in[c.name][1], non_blocking=True)
                     in_ready[s][i].record(copy)
-        for s in range(args.steps):
+        for s in range(ne):
             for i, c in enumerate(calls):
                 k0, k1, x0, x1 = sets[s].k[c.name]
                 y0, y1, z0, z1 = outs[c.name]
@@ -413,9 +427,9 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        ems = max_over_ranks(e0.elapsed_time(e1) / ne, world, dev)
         e2e = {"value": total * world / (ems * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems, "steps": ne}
 
     # batched form: the same layer as ONE persistent launch per step (graph replay)
     batched = None
@@ -433,10 +447,10 @@ def run_ours(args, rank, world, local_rank):
         for s, ks in enumerate(sets):
             ks.generate(300 + s)
         torch.cuda.synchronize()
-        bev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(args.steps)]
+        bev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(len(sets))]
         barrier(world)
         torch.cuda.synchronize()
-        for s in range(args.steps):
+        for s in range(len(sets)):
             bev[s][0].record(stream)
             batch_step(sets[s])
             bev[s][1].record(stream)
@@ -459,7 +473,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_xhat:
         vcss = {c.name: F.CompiledSpec(c.spec.variant(True), ctx) for c in calls}
         vsets = []
-        for s_ in range(args.steps + 1):
+        nx = sets_that_fit(sum(2 * vcss[c.name].key_bytes(c.n) for c in calls), args.steps + 1) - 1
+        for s_ in range(nx + 1):
             ks = {}
             for c in calls:
                 x0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
@@ -479,15 +494,15 @@ def run_ours(args, rank, world, local_rank):
         barrier(world)
         v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         v0.record(stream)
-        for s_ in range(args.steps):
+        for s_ in range(nx):
             vstep(vsets[s_], vcomm)
         v1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-        vms = max_over_ranks(v0.elapsed_time(v1) / args.steps, world, dev)
+        vms = max_over_ranks(v0.elapsed_time(v1) / nx, world, dev)
         xhat = {"value": aggregate(total, vms, world), "unit": "elements/s", "ms_per_step": vms,
                 "vs_standard": ms / vms,
-                "comm_bytes_per_party_per_step": int(vcomm.cpu().tolist()[0]) // args.steps,
+                "comm_bytes_per_party_per_step": int(vcomm.cpu().tolist()[0]) // nx, "steps": nx,
                 "comm_bytes_per_party_per_step_standard": comm_b[0] // (args.steps + args.warmup),
                 "key_bytes_per_step": sum(2 * vcss[c.name].shape.key_bytes_per_elem * c.n for c in calls),
                 "online_rounds": 1,
@@ -566,7 +581,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded activations; random masks, keys and triples from the GPU dealer)",
         "config": dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" %
                        (sum(2 * css[c.name].shape.key_bytes_per_elem * c.n for c in calls) / 1e9),
-                       parallelism="replicas" if world > 1 else "single GPU, both parties on it"),
+                       parallelism="replicas" if world > 1 else "single GPU, both parties on it",
+                       key_sets_resident=G, timed_groups=-(-args.steps // G)),
         "per_op_ms": per_op_ms,
         "keygen": {"ms_per_step": keygen_ms, "elements_per_s": total / (keygen_ms * 1e-3)},
         "comm_bytes_per_party": comm_b,
@@ -781,6 +797,13 @@ def run_blocks(ctx, args, dev, stream, world):
     ln.close()
     torch.cuda.empty_cache()
     return out
+
+
+def sets_that_fit(set_bytes: int, want: int, margin: float = 12e9) -> int:
+    """How many key sets of set_bytes fit in free HBM (at least 1, at most want)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return max(1, min(want, int((free - margin) // max(set_bytes, 1))))
 
 
 def _aes_roofline():

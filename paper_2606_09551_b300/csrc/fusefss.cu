@@ -430,9 +430,9 @@ static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t 
   int rc = FFSS_OK;
   std::call_once(once, [&] { rc = set_smem(keygen_kernel<P>, smem); });
   if (rc) return rc;
-  // one warp per (key, 32 elements) unit; one 512-thread CTA per SM
+  // one warp per (key, 32 elements) unit; one CTA of kKeygenThreads per SM
   const uint64_t units = (A.n + 31) / 32 * A.n_items;
-  keygen_kernel<P><<<grid_for(ctx, units, 16), 512, smem, st>>>(A);
+  keygen_kernel<P><<<grid_for(ctx, units, kKeygenThreads / 32), kKeygenThreads, smem, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
 }

@@ -713,8 +713,12 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
               reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
 }
 
+// 384 threads per CTA: 168 registers per thread keep a key's running state
+// out of local memory around the out-of-line AES calls.
+constexpr uint32_t kKeygenThreads = 384;
+
 template <int P>
-__global__ void __launch_bounds__(512, 1) keygen_kernel(const __grid_constant__ KeygenArgs A) {
+__global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_constant__ KeygenArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
