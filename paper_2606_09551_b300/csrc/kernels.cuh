@@ -120,10 +120,10 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // the walk at the cost of the bare AES chain plus a few operations per level;
 // inlined into the fused gate the compiler emitted about 40 % more
 // instructions per level.  One call per walk.
-__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, uint64_t n,
-                                          uint64_t leaf, const char *tab, uint32_t lane4) {
+__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, const uint4 *cw,
+                                          uint64_t cs, uint64_t leaf, const char *tab, uint32_t lane4) {
   const AesDcfInline aes{Tab{tab, lane4}};
-  return dcf_bit_eval(b, f, u, root, n, leaf, aes);
+  return dcf_bit_eval(b, f, u, root, cw, cs, leaf, aes);
 }
 
 // One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
@@ -133,8 +133,9 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   const char *q = kb + L.off_q[t];
   const uint32_t f = S.q_f[t];
   const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
-  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + 16ull * (1 + 4ull * key_levels(f)) * L.n)[e];
-  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
+  const uint4 *cw = reinterpret_cast<const uint4 *>(q + qkey_cw_off(L.n)) + 4 * e;
+  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + qkey_leaf_off(f, L.n))[e];
+  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, cw, 4 * L.n, leaf, aes.tb.base, aes.tb.lane4);
 }
 
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
@@ -144,11 +145,13 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
                                          const AesDcfInline &aes) {
   const uint32_t k = S.k;
   const char *l = kb + L.off_l[j];
-  const uint64_t lv = key_levels(k);
-  const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
-  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + 4 * lv) * L.n) + e;
-  const uint64_t *leaf = vcw + 4 * lv * P * L.n;
-  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
+  const uint64_t n = L.n;
+  const uint4 *root = reinterpret_cast<const uint4 *>(l + lkey_root_off(k, P, n)) + e;
+  const uint4 *cw = reinterpret_cast<const uint4 *>(l + lkey_cw_off(k, P, n)) + 4 * e;
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l) + 4 * P * e;
+  const uint64_t *leaf = reinterpret_cast<const uint64_t *>(l + lkey_leaf_off(k, P, n)) + e;
+  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, cw, 4 * n, vcw, 4 * P * n, leaf, n, acc,
+                      aes);   // lookups: k <= 32
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -679,12 +682,13 @@ __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &
     return mmo4(base, 4u * lvl, base, 4u * lvl + 1, base, 4u * lvl + 2, base, 4u * lvl + 3, rkd);
   };
   char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
-  const uint64_t lv = key_levels(S.k);
-  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
-  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
-  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
-                 keep4);
+  const uint64_t ro = lkey_root_off(S.k, P, n), co = lkey_cw_off(S.k, P, n), lo = lkey_leaf_off(S.k, P, n);
+  reinterpret_cast<uint4 *>(l0 + ro)[e] = s0;
+  reinterpret_cast<uint4 *>(l1 + ro)[e] = s1;
+  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0 + co) + 4 * e,
+                 reinterpret_cast<uint4 *>(l1 + co) + 4 * e, 4 * n, reinterpret_cast<uint64_t *>(l0) + 4 * P * e,
+                 reinterpret_cast<uint64_t *>(l1) + 4 * P * e, 4 * P * n, reinterpret_cast<uint64_t *>(l0 + lo) + e,
+                 reinterpret_cast<uint64_t *>(l1 + lo) + e, n, rkd, keep4);
 }
 
 __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
@@ -706,11 +710,12 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
     return mmo4(base, 4u * lvl0, base, 4u * (lvl0 + 1), base, 4u * (lvl0 + 2), base, 4u * (lvl0 + 3), rkd);
   };
   char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
-  const uint64_t lv = key_levels(f);
-  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
-              reinterpret_cast<uint4 *>(q1) + e,
-              reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
-              reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
+  const uint64_t co = qkey_cw_off(n), lo = qkey_leaf_off(f, n);
+  reinterpret_cast<uint4 *>(q0)[e] = s0;
+  reinterpret_cast<uint4 *>(q1)[e] = s1;
+  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0 + co) + 4 * e,
+              reinterpret_cast<uint4 *>(q1 + co) + 4 * e, 4 * n, reinterpret_cast<uint64_t *>(q0 + lo) + e,
+              reinterpret_cast<uint64_t *>(q1 + lo) + e, rkd, keep4);
 }
 
 // 384 threads per CTA: 168 registers per thread keep a key's running state
