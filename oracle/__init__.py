@@ -51,8 +51,10 @@ def lib():
         L.or_dcf_eval.argtypes = [C.c_int, C.c_void_p, C.c_uint64, C.POINTER(C.c_int), u64p]
         L.or_spec_build.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                     u64p, u64p, C.c_uint32, C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32,
-                                    C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32, C.c_uint32]
+                                    C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32, u32p, u32p, u32p, u32p,
+                                    C.c_uint32, C.c_uint32]
         L.or_spec_build.restype = C.c_int
+        L.or_spec_bx_shape.argtypes = [C.c_void_p, u32p]
         L.or_elem_trunc.argtypes = [C.c_void_p, u64p, u32p, u64p]
         L.or_beaver_dealer.argtypes = [u8p, C.c_uint32, C.c_uint64, C.c_uint64, u64p, u64p]
         L.or_beaver_mul.argtypes = [u64p, u64p, u64p, u64p, u64p, u64p, C.c_uint64, C.c_uint64,
@@ -172,8 +174,13 @@ class Spec:
     """Oracle-side compiled operator specification."""
 
     def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False,
-                 piecewise=(), trunc_s=0, trunc_signed=False):
-        """piecewise: per output j, m tuples (f, c, gamma, negate), one per interval.
+                 piecewise=(), trunc_s=0, trunc_signed=False, bx_nodes=None):
+        """piecewise: per output j, m entries, one per interval: the tuple
+        (f, c, gamma, negate) of a single predicate when bx_nodes is None,
+        else the index in bx_nodes of the root of the formula B_i^(j).
+        bx_nodes: formula nodes ("pred", (f, c, gamma, negate)), ("const",
+        bit), ("not", a), ("xor", a, b), ("and", a, b), ("or", a, b); the
+        children a, b are indices of earlier nodes.
         trunc_s > 0: output 0 gains the shift of the k-bit view by trunc_s
         (arithmetic when trunc_signed)."""
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
@@ -185,7 +192,19 @@ class Spec:
         pg = np.array([q[2] for q in preds] or [0], np.uint64)
         pn = np.array([q[3] for q in preds] or [0], np.uint32)
         npw = len(piecewise)
-        flat = [piecewise[j][i] for i in range(m) for j in range(npw)] or [(1, 0, 0, 0)]
+        codes = {"pred": 0, "const": 1, "not": 2, "xor": 3, "and": 4, "or": 5}
+        if bx_nodes is None:
+            flat = [piecewise[j][i] for i in range(m) for j in range(npw)] or [(1, 0, 0, 0)]
+            nbx = 0
+            bop = ba = bb = roots = np.zeros(1, np.uint32)
+        else:
+            nbx = len(bx_nodes)
+            flat = [nd[1] if nd[0] == "pred" else (1, 0, 0, 0) for nd in bx_nodes] or [(1, 0, 0, 0)]
+            bop = np.array([codes[nd[0]] for nd in bx_nodes] or [0], np.uint32)
+            ba = np.array([(nd[1] if nd[0] in ("const", "not", "xor", "and", "or") else 0) for nd in bx_nodes]
+                          or [0], np.uint32)
+            bb = np.array([(nd[2] if nd[0] in ("xor", "and", "or") else 0) for nd in bx_nodes] or [0], np.uint32)
+            roots = np.array([piecewise[j][i] for i in range(m) for j in range(npw)] or [0], np.uint32)
         wf = np.array([q[0] for q in flat], np.uint32)
         wc = np.array([q[1] for q in flat], np.uint64)
         wg = np.array([q[2] for q in flat], np.uint64)
@@ -194,6 +213,7 @@ class Spec:
                                  1 if partition_bits else 0, n, _p(pf, u32p), _p(pc, u64p),
                                  _p(pg, u64p), _p(pn, u32p), 1 if xhat_basis else 0,
                                  npw, _p(wf, u32p), _p(wc, u64p), _p(wg, u64p), _p(wn, u32p),
+                                 nbx, _p(bop, u32p), _p(ba, u32p), _p(bb, u32p), _p(roots, u32p),
                                  trunc_s, 1 if trunc_signed else 0)
         self.n_pw = npw
         self.trunc_s, self.trunc_signed = trunc_s, bool(trunc_signed)
@@ -203,6 +223,9 @@ class Spec:
         lib().or_spec_shape(self.ptr, _p(sh, u32p))
         self.k, self.m, self.d, self.r = k, m, d, r
         self.T, self.M, self.p, self.n_mults, self.n_bool, self.n_prim = (int(v) for v in sh)
+        bx = np.zeros(2, np.uint32)
+        lib().or_spec_bx_shape(self.ptr, _p(bx, u32p))
+        self.n_bx_rounds, self.n_bw = int(bx[0]), int(bx[1])
 
     @property
     def ptr(self):
@@ -253,12 +276,12 @@ class ElemKeys:
         ta, tb, tc = (np.zeros(nm, np.uint64) for _ in range(3))
         lib().or_elem_fields(self.elem_ptr(i), spec.p, spec.n_mults, _p(r_share, u64p),
                              _p(carry, u32p), _p(vlast, u64p), _p(ta, u64p), _p(tb, u64p), _p(tc, u64p))
-        npw = getattr(spec, "n_pw", 0)
-        ba, bb, bc = (np.zeros(max(npw, 1), np.uint32) for _ in range(3))
-        lib().or_elem_btriples(self.elem_ptr(i), npw, _p(ba, u32p), _p(bb, u32p), _p(bc, u32p))
+        nbw = spec.n_bw
+        ba, bb, bc = (np.zeros(max(nbw, 1), np.uint32) for _ in range(3))
+        lib().or_elem_btriples(self.elem_ptr(i), nbw, _p(ba, u32p), _p(bb, u32p), _p(bc, u32p))
         out = dict(r_share=int(r_share[0]), carry=int(carry[0]), vlast=vlast[:spec.p],
                    ta=ta[:spec.n_mults], tb=tb[:spec.n_mults], tc=tc[:spec.n_mults],
-                   ba=ba[:npw], bb=bb[:npw], bc=bc[:npw])
+                   ba=ba[:nbw], bb=bb[:nbw], bc=bc[:nbw])
         if getattr(spec, "trunc_s", 0):
             t, rho, rho_a = np.zeros(1, np.uint64), np.zeros(1, np.uint32), np.zeros(2, np.uint64)
             lib().or_elem_trunc(self.elem_ptr(i), _p(t, u64p), _p(rho, u32p), _p(rho_a, u64p))

@@ -28,11 +28,19 @@
  *     packed comparison, vector interval lookup, masked-to-shares, Horner with
  *     one Beaver multiplication per step (Sec. 3.4), with explicit message
  *     buffers per party and byte counters.
+ *   - Piecewise Boolean outputs whose per-interval entries are formulas of
+ *     the bit-expression grammar, normalised by interval indicators (Lemmas
+ *     "interval indicator as XOR" and "boolean normalization", App. D) and
+ *     evaluated on XOR shares round by round with Boolean AND triples.
+ *   - The shift gate (truncation / arithmetic right shift, low-bit rewrite
+ *     lemma) with daBit B2A, Beaver products of shared vectors, and the
+ *     softmax / LayerNorm compositions of gates (compose.py).
  *   - The plaintext operator evaluator (Def. "operator specification", Sec. 4.1).
  *
  * Parity pins live in tests/ (FIPS-197 known answers, brute-force DCF
  * correctness, brute-force lemma checks, the App. N ReLU closed form, the
- * plaintext evaluator against an independent numpy evaluation).
+ * plaintext evaluator against an independent numpy evaluation, the Boolean
+ * formulas against the grammar's semantics for every input and mask).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -436,13 +444,19 @@ size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
 #define MAXPRED 32  /* Boolean outputs */
 #define MAXQ 32     /* packed-comparison queries (one uint32 of atoms) */
 #define MAXPW 4     /* piecewise Boolean outputs */
+#define MAXBX 64    /* nodes of the piecewise outputs' Boolean formulas */
+#define MAXBXD 4    /* AND depth of a formula (so at most MAXBXD + 1 rounds) */
+#define MAXBW 8     /* packed Boolean AND triples (32 gates each) per element */
+
+/* node kinds of a Boolean formula */
+enum { OR_BX_PRED = 0, OR_BX_CONST = 1, OR_BX_NOT = 2, OR_BX_XOR = 3, OR_BX_AND = 4, OR_BX_OR = 5 };
 
 typedef struct {
     uint64_t r_share;
     uint32_t carry_share;
     uint64_t vlast_share[MAXP];
     uint64_t ta[MAXP], tb[MAXP], tc[MAXP];   /* Beaver triple shares, d*r of them */
-    uint32_t ba[MAXPW], bb[MAXPW], bc[MAXPW]; /* Boolean AND triples, m bits per output */
+    uint32_t ba[MAXBW], bb[MAXBW], bc[MAXBW]; /* Boolean AND triples, one bit per AND gate */
     uint64_t tr_t;                    /* truncation: share of (r mod 2^k) >> s */
     uint32_t tr_rho;                  /* daBits: XOR shares of rho_lo (bit 0), rho_hi (bit 1) */
     uint64_t tr_rho_a[2];             /* daBits: additive shares of rho_lo, rho_hi */
@@ -480,12 +494,29 @@ typedef struct {
     int32_t prim_qtheta[MAXPRED];     /* per prim: its theta query */
     int32_t prim_qr[MAXPRED];         /* per prim: the r-atom query of its view */
     /* piecewise Boolean outputs (Def. "operator specification" item 3 and
-     * Lemma "boolean normalization"): output j is B_i^(j)(x) on interval i */
+     * Lemma "boolean normalization"): output j is B_i^(j)(x) on interval i,
+     * a formula of the bit-expression grammar (App. "a minimal typed
+     * expression language"): node v is a primitive predicate, a constant,
+     * NOT, XOR, AND or OR of nodes below v; pw_root[i][j] is B_i^(j)'s node */
     uint32_t n_pw;
-    or_pred pw_pred[MAXM][MAXPW];     /* B_i^(j), negate used */
-    int32_t pw_prim[MAXM][MAXPW];     /* its prim, or -1 for a sentinel constant */
-    uint32_t pw_const[MAXM][MAXPW];   /* the constant when pw_prim < 0 */
+    uint32_t n_bx;
+    uint32_t bx_op[MAXBX];            /* OR_BX_* */
+    uint32_t bx_a[MAXBX], bx_b[MAXBX];
+    or_pred bx_pred[MAXBX];           /* OR_BX_PRED: the predicate, negate used */
+    int32_t bx_prim[MAXBX];           /* OR_BX_PRED: its prim, or -1 for a sentinel constant */
+    uint32_t bx_const[MAXBX];         /* OR_BX_CONST, sentinel OR_BX_PRED: the constant */
+    uint32_t bx_depth[MAXBX];         /* AND depth */
+    uint32_t pw_root[MAXM][MAXPW];
     int32_t part_prim[MAXM + 1];      /* prim of C_{alpha_i}, i = 1..m-1 (when n_pw > 0) */
+    /* AND gates by round: round l (1-based) evaluates the AND/OR nodes of
+     * depth l (node order), then the normalisation gates J_i AND B_i^(j)
+     * with depth(B_i^(j)) + 1 = l (output-major, interval-minor); gate g of
+     * round l is bit g % 32 of packed triple word bw_base[l] + g / 32 */
+    uint32_t n_bxr;                   /* rounds */
+    uint32_t n_bw;                    /* packed triple words */
+    uint32_t gate_off[MAXBXD + 3];    /* round l's gates: gate[gate_off[l] .. gate_off[l + 1]) */
+    uint32_t gate[MAXBX + MAXM * MAXPW];   /* node v, or 256 + 16 j + i for a normalisation gate */
+    uint32_t bw_base[MAXBXD + 3];
     /* truncation / arithmetic right shift by trunc_s (Def. "specification-
      * compatible scalar gate"): output 0 gains T_s(x), with T_s the logical
      * shift of the k-bit view (trunc_signed = 0) or the arithmetic shift of
@@ -524,7 +555,8 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
                   uint32_t n_extra, const uint32_t *ef, const uint64_t *ec,
                   const uint64_t *egamma, const uint32_t *eneg, uint32_t xhat_basis,
                   uint32_t n_pw, const uint32_t *pwf, const uint64_t *pwc, const uint64_t *pwg,
-                  const uint32_t *pwn, uint32_t trunc_s, uint32_t trunc_signed)
+                  const uint32_t *pwn, uint32_t n_bx, const uint32_t *bxop, const uint32_t *bxa,
+                  const uint32_t *bxb, const uint32_t *pwroot, uint32_t trunc_s, uint32_t trunc_signed)
 {
     memset(sp, 0, sizeof(*sp));
     if (k < 1 || k > MAXK || m < 1 || m > MAXM) return -1;
@@ -580,8 +612,10 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
     }
 
     /* piecewise outputs: the partition predicates (for the interval
-     * indicators J_i) join the primitive predicates, then each output's
-     * per-interval predicates, output by output, interval by interval */
+     * indicators J_i) join the primitive predicates, then the formulas'
+     * predicate nodes in node order.  Without formula nodes (n_bx = 0) each
+     * B_i^(j) is the single predicate at flat index i n_pw + j, taken as node
+     * j m + i (output by output, interval by interval). */
     if (n_pw > MAXPW || nb + n_pw > MAXPRED) return -1;
     sp->n_pw = n_pw;
     if (n_pw > 0) {
@@ -589,18 +623,68 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
             sp->part_prim[i] = add_prim(sp, k, 0, alpha[i]);
             if (sp->part_prim[i] < -1) return -1;
         }
-        for (uint32_t j = 0; j < n_pw; j++)
-            for (uint32_t i = 0; i < m; i++) {
-                uint32_t idx = i * n_pw + j;
+        uint32_t nn = n_bx ? n_bx : m * n_pw;
+        if (nn > MAXBX) return -1;
+        sp->n_bx = nn;
+        for (uint32_t v = 0; v < nn; v++) {
+            uint32_t op = n_bx ? bxop[v] : OR_BX_PRED;
+            uint32_t idx = n_bx ? v : (v % m) * n_pw + v / m;
+            sp->bx_op[v] = op;
+            sp->bx_prim[v] = -1;
+            if (op == OR_BX_PRED) {
                 if (pwf[idx] < 1 || pwf[idx] > k) return -1;
                 if (pwc[idx] >= pow2(pwf[idx]) || pwg[idx] > pow2(pwf[idx])) return -1;
-                or_pred *q = &sp->pw_pred[i][j];
+                or_pred *q = &sp->bx_pred[v];
                 q->f = pwf[idx]; q->c = pwc[idx]; q->gamma = pwg[idx]; q->negate = pwn[idx] & 1;
                 int pr = add_prim(sp, q->f, q->c, q->gamma);
                 if (pr < -1) return -1;
-                sp->pw_prim[i][j] = pr;
-                sp->pw_const[i][j] = q->gamma == 0 ? 0 : 1;
+                sp->bx_prim[v] = pr;
+                sp->bx_const[v] = q->gamma == 0 ? 0 : 1;
+                sp->bx_depth[v] = 0;
+            } else if (op == OR_BX_CONST) {
+                if (bxa[v] > 1) return -1;
+                sp->bx_const[v] = bxa[v];
+                sp->bx_depth[v] = 0;
+            } else if (op == OR_BX_NOT) {
+                if (bxa[v] >= v) return -1;
+                sp->bx_a[v] = bxa[v];
+                sp->bx_depth[v] = sp->bx_depth[bxa[v]];
+            } else if (op == OR_BX_XOR || op == OR_BX_AND || op == OR_BX_OR) {
+                if (bxa[v] >= v || bxb[v] >= v) return -1;
+                sp->bx_a[v] = bxa[v]; sp->bx_b[v] = bxb[v];
+                uint32_t da = sp->bx_depth[bxa[v]], db = sp->bx_depth[bxb[v]];
+                sp->bx_depth[v] = (da > db ? da : db) + (op == OR_BX_XOR ? 0 : 1);
+                if (sp->bx_depth[v] > MAXBXD) return -1;
+            } else {
+                return -1;
             }
+        }
+        uint32_t R = 1;
+        for (uint32_t v = 0; v < nn; v++) if (sp->bx_depth[v] > R) R = sp->bx_depth[v];
+        for (uint32_t i = 0; i < m; i++)
+            for (uint32_t j = 0; j < n_pw; j++) {
+                uint32_t root = n_bx ? pwroot[i * n_pw + j] : j * m + i;
+                if (root >= nn) return -1;
+                sp->pw_root[i][j] = root;
+                if (sp->bx_depth[root] + 1 > R) R = sp->bx_depth[root] + 1;
+            }
+        /* the AND gates of each round and their packed triple words */
+        sp->n_bxr = R;
+        uint32_t ng = 0, nw = 0;
+        for (uint32_t l = 1; l <= R; l++) {
+            sp->gate_off[l] = ng;
+            sp->bw_base[l] = nw;
+            for (uint32_t v = 0; v < nn; v++)
+                if ((sp->bx_op[v] == OR_BX_AND || sp->bx_op[v] == OR_BX_OR) && sp->bx_depth[v] == l)
+                    sp->gate[ng++] = v;
+            for (uint32_t j = 0; j < n_pw; j++)
+                for (uint32_t i = 0; i < m; i++)
+                    if (sp->bx_depth[sp->pw_root[i][j]] + 1 == l) sp->gate[ng++] = 256 + 16 * j + i;
+            nw += (ng - sp->gate_off[l] + 31) / 32;
+        }
+        sp->gate_off[R + 1] = ng;
+        if (nw > MAXBW) return -1;
+        sp->n_bw = nw;
     }
 
     /* views in order of first appearance; a truncation adds the views
@@ -663,6 +747,12 @@ void or_spec_shape(const or_spec *sp, uint32_t *out)
     out[4] = sp->n_out_bits + sp->n_pw; out[5] = sp->n_prim;
 }
 
+/* Boolean-formula shape: rounds of AND gates and packed triple words */
+void or_spec_bx_shape(const or_spec *sp, uint32_t *out)
+{
+    out[0] = sp->n_pw ? sp->n_bxr : 0; out[1] = sp->n_bw;
+}
+
 void or_spec_query(const or_spec *sp, uint32_t t, uint32_t *f, uint64_t *c, int32_t *prim)
 {
     *f = sp->q_f[t]; *c = sp->q_c[t]; *prim = sp->q_prim[t];
@@ -680,6 +770,23 @@ static uint64_t view(uint64_t u, uint32_t f, uint64_t c)
 /* (x mod 2^k) in [alpha_i, alpha_{i+1}); Horner over Z_{2^64} on the full   */
 /* 64-bit x.                                                                 */
 /* ------------------------------------------------------------------------ */
+
+/* plaintext value of formula node v at x: the grammar's semantics, with
+ * 1[view_{f,c}(x) < gamma] XOR negate at a predicate leaf */
+static uint32_t bx_plain(const or_spec *sp, uint32_t v, uint64_t x)
+{
+    switch (sp->bx_op[v]) {
+    case OR_BX_PRED: {
+        const or_pred *q = &sp->bx_pred[v];
+        return (view(x, q->f, q->c) < q->gamma ? 1u : 0u) ^ q->negate;
+    }
+    case OR_BX_CONST: return sp->bx_const[v];
+    case OR_BX_NOT: return 1u ^ bx_plain(sp, sp->bx_a[v], x);
+    case OR_BX_XOR: return bx_plain(sp, sp->bx_a[v], x) ^ bx_plain(sp, sp->bx_b[v], x);
+    case OR_BX_AND: return bx_plain(sp, sp->bx_a[v], x) & bx_plain(sp, sp->bx_b[v], x);
+    default: return bx_plain(sp, sp->bx_a[v], x) | bx_plain(sp, sp->bx_b[v], x);
+    }
+}
 
 void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y, uint32_t *z)
 {
@@ -715,11 +822,8 @@ void or_plain_eval(const or_spec *sp, const uint64_t *x, uint64_t n, uint64_t *y
             uint32_t v = view(x[e], op->f, op->c) < op->gamma ? 1u : 0u;
             bits |= (v ^ op->negate) << o;
         }
-        for (uint32_t j = 0; j < sp->n_pw; j++) {
-            const or_pred *op = &sp->pw_pred[piece][j];
-            uint32_t v = view(x[e], op->f, op->c) < op->gamma ? 1u : 0u;
-            bits |= (v ^ op->negate) << (sp->n_out_bits + j);
-        }
+        for (uint32_t j = 0; j < sp->n_pw; j++)
+            bits |= bx_plain(sp, sp->pw_root[piece][j], x[e]) << (sp->n_out_bits + j);
         z[e] = bits;
     }
 }
@@ -1013,26 +1117,33 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             K0->tc[mi] = c0; K1->tc[mi] = a * b - c0;
         }
 
-        /* Boolean AND triples for the piecewise outputs: m packed bits each,
-         * draws (a, b, a_0, b_0, c_0) after the ring triples */
-        uint32_t mbits = sp->m >= 32 ? 0xFFFFFFFFu : ((1u << sp->m) - 1);
-        for (uint32_t j = 0; j < sp->n_pw; j++) {
-            uint32_t di = base_triples + 5 * sp->n_mults + 5 * j;
-            uint32_t a = (uint32_t)prg_u64(&g, di + 0, e) & mbits;
-            uint32_t b = (uint32_t)prg_u64(&g, di + 1, e) & mbits;
-            uint32_t a0 = (uint32_t)prg_u64(&g, di + 2, e) & mbits;
-            uint32_t b0 = (uint32_t)prg_u64(&g, di + 3, e) & mbits;
-            uint32_t c0 = (uint32_t)prg_u64(&g, di + 4, e) & mbits;
-            K0->ba[j] = a0; K1->ba[j] = a ^ a0;
-            K0->bb[j] = b0; K1->bb[j] = b ^ b0;
-            K0->bc[j] = c0; K1->bc[j] = (a & b) ^ c0;
+        /* Boolean AND triples for the piecewise outputs' AND gates: one
+         * packed word per 32 gates of a round, one bit per gate (the word's
+         * gate count of low bits), draws (a, b, a_0, b_0, c_0) after the
+         * ring triples */
+        for (uint32_t l = 1; l <= sp->n_bxr && sp->n_pw; l++) {
+            uint32_t ng = sp->gate_off[l + 1] - sp->gate_off[l];
+            for (uint32_t w = 0; 32 * w < ng; w++) {
+                uint32_t gw = ng - 32 * w >= 32 ? 32 : ng - 32 * w;
+                uint32_t mbits = gw >= 32 ? 0xFFFFFFFFu : ((1u << gw) - 1);
+                uint32_t wi = sp->bw_base[l] + w;
+                uint32_t di = base_triples + 5 * sp->n_mults + 5 * wi;
+                uint32_t a = (uint32_t)prg_u64(&g, di + 0, e) & mbits;
+                uint32_t b = (uint32_t)prg_u64(&g, di + 1, e) & mbits;
+                uint32_t a0 = (uint32_t)prg_u64(&g, di + 2, e) & mbits;
+                uint32_t b0 = (uint32_t)prg_u64(&g, di + 3, e) & mbits;
+                uint32_t c0 = (uint32_t)prg_u64(&g, di + 4, e) & mbits;
+                K0->ba[wi] = a0; K1->ba[wi] = a ^ a0;
+                K0->bb[wi] = b0; K1->bb[wi] = b ^ b0;
+                K0->bc[wi] = c0; K1->bc[wi] = (a & b) ^ c0;
+            }
         }
 
         /* truncation: shares of (r mod 2^k) >> s and two daBits (a random
          * bit held both XOR- and additively shared, for the B2A of the
          * borrow and wrap atoms); draws after the Boolean triples */
         if (sp->trunc_s) {
-            uint32_t di = base_triples + 5 * sp->n_mults + 5 * sp->n_pw;
+            uint32_t di = base_triples + 5 * sp->n_mults + 5 * sp->n_bw;
             uint64_t t = (r_in & (pow2(sp->k) - 1)) >> sp->trunc_s;
             uint64_t t0 = prg_u64(&g, di + 0, e);
             uint32_t rho = (uint32_t)prg_u64(&g, di + 1, e) & 3u;
@@ -1074,35 +1185,55 @@ static uint32_t prim_share(const or_spec *sp, const or_elem_keys *K, uint32_t at
     return ((atoms >> sp->prim_qtheta[j]) & 1) ^ ((atoms >> sp->prim_qr[j]) & 1) ^ ((K->carry_share >> j) & 1);
 }
 
-/* Shares of the interval indicators J_i = C_{alpha_{i+1}} ^ C_{alpha_i}
- * (Lemma "interval indicator as XOR"; C_{alpha_0} = 0 and C_{alpha_m} = 1,
- * the constant held by party 0) and of B_i^(j), as m-bit words (bit i). */
-static void party_pw_words(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms, uint32_t *Jw,
-                           uint32_t *Bw)
+/* This party's shares of the interval indicators J_i = C_{alpha_{i+1}} ^
+ * C_{alpha_i} (Lemma "interval indicator as XOR"; C_{alpha_0} = 0 and
+ * C_{alpha_m} = 1, the constant held by party 0), bit i. */
+static uint32_t party_J(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms)
 {
     uint32_t C[MAXM + 1];
     C[0] = 0;
     C[sp->m] = b == 0 ? 1u : 0u;
     for (uint32_t i = 1; i < sp->m; i++) C[i] = prim_share(sp, K, atoms, sp->part_prim[i]);
-    *Jw = 0;
-    for (uint32_t i = 0; i < sp->m; i++) *Jw |= (C[i + 1] ^ C[i]) << i;
-    for (uint32_t j = 0; j < sp->n_pw; j++) {
-        Bw[j] = 0;
-        for (uint32_t i = 0; i < sp->m; i++) {
-            uint32_t bit;
-            if (sp->pw_prim[i][j] < 0) bit = b == 0 ? sp->pw_const[i][j] : 0;
-            else bit = prim_share(sp, K, atoms, sp->pw_prim[i][j]);
-            if (b == 0) bit ^= sp->pw_pred[i][j].negate;
-            Bw[j] |= bit << i;
+    uint32_t J = 0;
+    for (uint32_t i = 0; i < sp->m; i++) J |= (C[i + 1] ^ C[i]) << i;
+    return J;
+}
+
+/* The formula nodes of AND depth l that need no exchange, in node order:
+ * predicates and constants (depth 0), NOT and XOR of nodes already held.
+ * Constants, negations and NOT are applied by party 0 only.  Bit v of *nv is
+ * this party's XOR share of node v. */
+static void bx_local(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms, uint32_t l, uint64_t *nv)
+{
+    for (uint32_t v = 0; v < sp->n_bx; v++) {
+        if (sp->bx_depth[v] != l) continue;
+        uint32_t bit;
+        switch (sp->bx_op[v]) {
+        case OR_BX_PRED:
+            bit = sp->bx_prim[v] < 0 ? (b == 0 ? sp->bx_const[v] : 0u) : prim_share(sp, K, atoms, sp->bx_prim[v]);
+            if (b == 0) bit ^= sp->bx_pred[v].negate;
+            break;
+        case OR_BX_CONST: bit = b == 0 ? sp->bx_const[v] : 0u; break;
+        case OR_BX_NOT: bit = (uint32_t)(*nv >> sp->bx_a[v]) & 1u; if (b == 0) bit ^= 1u; break;
+        case OR_BX_XOR: bit = (uint32_t)((*nv >> sp->bx_a[v]) ^ (*nv >> sp->bx_b[v])) & 1u; break;
+        default: continue;   /* AND / OR: evaluated in round l */
         }
+        *nv |= (uint64_t)bit << v;
     }
 }
 
-static uint32_t parity32(uint32_t v)
+/* The two input shares of AND gate g: the children of an AND/OR node, or
+ * (J_i, B_i^(j)) for the normalisation gate of output j, interval i. */
+static void gate_inputs(const or_spec *sp, uint32_t g, uint64_t nv, uint32_t J, uint32_t *x, uint32_t *y)
 {
-    uint32_t p = 0;
-    while (v) { p ^= v & 1; v >>= 1; }
-    return p;
+    if (g < 256) {
+        *x = (uint32_t)(nv >> sp->bx_a[g]) & 1u;
+        *y = (uint32_t)(nv >> sp->bx_b[g]) & 1u;
+    } else {
+        uint32_t j = (g - 256) / 16, i = (g - 256) % 16;
+        *x = (J >> i) & 1u;
+        *y = (uint32_t)(nv >> sp->pw_root[i][j]) & 1u;
+    }
 }
 
 static uint32_t party_out_bits(int b, const or_spec *sp, const or_elem_keys *K, uint32_t atoms)
@@ -1178,26 +1309,60 @@ void or_eval_pair(const or_spec *sp, const or_elem_keys *k0, const or_elem_keys 
             for (uint32_t o = 0; o < r; o++) y[b][o] = pay[b][o * (d + 1) + d];
         }
         /* piecewise Boolean outputs (Lemma "boolean normalization"):
-         * z_j = XOR_i (J_i AND B_i^(j)); the m ANDs of an output use one
-         * packed Boolean triple: open e = J ^ a, f = B ^ b (4 + 4 bytes),
-         * then share = [b=0] e&f ^ e&b_b ^ f&a_b ^ c_b, and z_j = its parity */
+         * z_j = XOR_i (J_i AND B_i^(j)), each B_i^(j) a formula over the
+         * primitive predicates' shares.  Round l evaluates the AND gates of
+         * depth l, 32 per packed Boolean triple (a, b, c): each party opens
+         * e = X ^ a and f = Y ^ b (4 + 4 bytes per word), then holds
+         * [b = 0] E&F ^ E&b_b ^ F&a_b ^ c_b, bit g = its share of gate g's
+         * AND (an OR adds its input shares: x | y = x ^ y ^ (x & y)). */
         if (sp->n_pw > 0) {
-            uint32_t Jw[2], Bw[2][MAXPW], ew[2][MAXPW], fw[2][MAXPW];
+            uint64_t nv[2] = {0, 0};
+            uint32_t J[2], zp[2] = {0, 0};
             for (int b = 0; b < 2; b++) {
-                party_pw_words(b, sp, KK[b], b == 0 ? atoms_b[0] : atoms_b[1], &Jw[b], Bw[b]);
-                for (uint32_t j = 0; j < sp->n_pw; j++) {
-                    ew[b][j] = Jw[b] ^ KK[b]->ba[j];
-                    fw[b][j] = Bw[b][j] ^ KK[b]->bb[j];
-                    sent[b] += 8;
-                }
+                uint32_t at = b == 0 ? atoms_b[0] : atoms_b[1];
+                J[b] = party_J(b, sp, KK[b], at);
+                bx_local(b, sp, KK[b], at, 0, &nv[b]);
             }
-            for (int b = 0; b < 2; b++)
-                for (uint32_t j = 0; j < sp->n_pw; j++) {
-                    uint32_t E = ew[0][j] ^ ew[1][j], F = fw[0][j] ^ fw[1][j];
-                    uint32_t w = (E & KK[b]->bb[j]) ^ (F & KK[b]->ba[j]) ^ KK[b]->bc[j];
-                    if (b == 0) w ^= E & F;
-                    zs[b][e] |= parity32(w) << (sp->n_out_bits + j);
+            for (uint32_t l = 1; l <= sp->n_bxr; l++) {
+                uint32_t g0 = sp->gate_off[l], ng = sp->gate_off[l + 1] - g0;
+                for (uint32_t w = 0; 32 * w < ng; w++) {
+                    uint32_t wi = sp->bw_base[l] + w, ew[2], fw[2];
+                    uint32_t gw = ng - 32 * w >= 32 ? 32 : ng - 32 * w;
+                    for (int b = 0; b < 2; b++) {
+                        uint32_t X = 0, Y = 0;
+                        for (uint32_t t = 0; t < gw; t++) {
+                            uint32_t x, y;
+                            gate_inputs(sp, sp->gate[g0 + 32 * w + t], nv[b], J[b], &x, &y);
+                            X |= x << t;
+                            Y |= y << t;
+                        }
+                        ew[b] = X ^ KK[b]->ba[wi];
+                        fw[b] = Y ^ KK[b]->bb[wi];
+                        sent[b] += 8;
+                    }
+                    uint32_t E = ew[0] ^ ew[1], F = fw[0] ^ fw[1];
+                    for (int b = 0; b < 2; b++) {
+                        uint32_t and_w = (E & KK[b]->bb[wi]) ^ (F & KK[b]->ba[wi]) ^ KK[b]->bc[wi];
+                        if (b == 0) and_w ^= E & F;
+                        for (uint32_t t = 0; t < gw; t++) {
+                            uint32_t g = sp->gate[g0 + 32 * w + t], bit = (and_w >> t) & 1u;
+                            if (g < 256) {
+                                if (sp->bx_op[g] == OR_BX_OR) {
+                                    uint32_t x, y;
+                                    gate_inputs(sp, g, nv[b], J[b], &x, &y);
+                                    bit ^= x ^ y;
+                                }
+                                nv[b] |= (uint64_t)bit << g;
+                            } else {
+                                zp[b] ^= bit << ((g - 256) / 16);
+                            }
+                        }
+                    }
                 }
+                for (int b = 0; b < 2; b++)
+                    bx_local(b, sp, KK[b], b == 0 ? atoms_b[0] : atoms_b[1], l, &nv[b]);
+            }
+            for (int b = 0; b < 2; b++) zs[b][e] |= zp[b] << sp->n_out_bits;
         }
         /* x^ basis: Horner on the public x^ with shared coefficients, local */
         if (sp->xhat_basis) {

@@ -37,6 +37,24 @@ class PredDesc:
 
 
 @dataclass
+class BxNode:
+    """One node of a piecewise Boolean formula (the operator specification's
+    bit-expression grammar): op "pred" (pred), "const" (a = the bit), "not"
+    (a), "xor" / "and" / "or" (a, b); children are indices of earlier nodes."""
+    op: str
+    a: int = 0
+    b: int = 0
+    pred: PredDesc | None = None
+
+    def astuple(self):
+        if self.op == "pred":
+            return ("pred", self.pred.astuple())
+        if self.op in ("const", "not"):
+            return (self.op, self.a)
+        return (self.op, self.a, self.b)
+
+
+@dataclass
 class OperatorSpec:
     name: str
     k: int                      # comparison view width (bits)
@@ -53,9 +71,11 @@ class OperatorSpec:
     # dealer (no Beaver multiplications); same function, other protocol variant
     xhat_basis: bool = False
     # piecewise Boolean outputs: piecewise[j][i] is output j's predicate on
-    # interval i (sentinel gamma 0 / 2^f for constants); they follow the
-    # partition bits and the preds in z
-    piecewise: List[List[PredDesc]] = field(default_factory=list)
+    # interval i (sentinel gamma 0 / 2^f for constants), or, with formula
+    # nodes, the index in bx_nodes of the root of its formula; they follow
+    # the partition bits and the preds in z
+    piecewise: List[List[PredDesc | int]] = field(default_factory=list)
+    bx_nodes: List[BxNode] = field(default_factory=list)
     # truncation: output 0 gains (x mod 2^k) >> trunc_shift, or the arithmetic
     # shift of its k-bit two's-complement value when trunc_signed (0 = none)
     trunc_shift: int = 0
@@ -71,6 +91,8 @@ class OperatorSpec:
         return [q.astuple() for q in self.preds]
 
     def piecewise_tuples(self):
+        if self.bx_nodes:
+            return [[int(q) for q in out] for out in self.piecewise]
         return [[q.astuple() for q in out] for out in self.piecewise]
 
     def descriptor(self) -> dict:
@@ -78,7 +100,8 @@ class OperatorSpec:
         what a compiler of this specification needs, by field name."""
         return dict(k=self.k, m=self.m, d=self.degree, r=self.n_out, alpha=list(self.alpha), coeff=self.coeff,
                     partition_bits=self.partition_bits, preds=self.pred_tuples(), xhat_basis=self.xhat_basis,
-                    piecewise=self.piecewise_tuples(), trunc_s=self.trunc_shift, trunc_signed=self.trunc_signed)
+                    piecewise=self.piecewise_tuples(), trunc_s=self.trunc_shift, trunc_signed=self.trunc_signed,
+                    bx_nodes=[nd.astuple() for nd in self.bx_nodes] or None)
 
     def variant(self, xhat_basis: bool) -> "OperatorSpec":
         """The same specification evaluated in the other protocol variant."""
@@ -392,6 +415,61 @@ def random_piecewise(rng: np.random.Generator, spec: OperatorSpec, n_pw: int) ->
                 col.append(PredDesc(f, c, g, neg))
         outs.append(col)
     return dataclasses.replace(spec, piecewise=outs, name=spec.name + "_pw%d" % n_pw)
+
+
+def random_formulas(rng: np.random.Generator, spec: OperatorSpec, n_pw: int, n_nodes: int = 24,
+                    max_depth: int = 4) -> OperatorSpec:
+    """Add n_pw piecewise Boolean outputs whose per-interval entries are
+    random formulas (for tests): a random node DAG over a small predicate
+    pool (low-bit D_{gamma,f}, C_beta, MSB(x + c), sentinel constants) with
+    NOT / XOR / AND / OR of AND depth at most max_depth; each (interval,
+    output) takes a random node as its root."""
+    import dataclasses
+    k = spec.k
+    pool = [PredDesc(k, 0, 1 << (k - 1), 1)]                                   # MSB(x)
+    for _p in range(3):
+        f = int(rng.integers(1, k + 1))
+        pool.append(PredDesc(f, int(rng.integers(0, 1 << f)), int(rng.integers(0, (1 << f) + 1)),
+                             int(rng.integers(0, 2))))
+    nodes: List[BxNode] = []
+    depth: List[int] = []
+    n_leaf = max(2, n_nodes // 3)
+    for v in range(n_nodes):
+        if v < n_leaf:
+            if rng.integers(0, 6) == 0:
+                nodes.append(BxNode("const", int(rng.integers(0, 2))))
+            else:
+                nodes.append(BxNode("pred", pred=pool[int(rng.integers(0, len(pool)))]))
+            depth.append(0)
+            continue
+        while True:
+            op = ("not", "xor", "and", "or")[int(rng.integers(0, 4))]
+            a, b = int(rng.integers(0, v)), int(rng.integers(0, v))
+            dd = max(depth[a], depth[b]) + (1 if op in ("and", "or") else 0)
+            if op == "not":
+                dd = depth[a]
+            if dd <= max_depth - 1 or (dd <= max_depth and rng.integers(0, 3) == 0):
+                break
+        nodes.append(BxNode(op, a, b))
+        depth.append(dd)
+    outs = [[int(rng.integers(0, n_nodes)) for _ in range(spec.m)] for _ in range(n_pw)]
+    return dataclasses.replace(spec, piecewise=outs, bx_nodes=nodes, name=spec.name + "_bx%d" % n_pw)
+
+
+def deep_formula(spec: OperatorSpec) -> OperatorSpec:
+    """One piecewise output whose formulas reach the AND-depth bound (for
+    tests): on every interval an alternating AND / OR chain of depth 4 over
+    three predicates (a low-bit D_{gamma,f}, C_beta and MSB(x + c)), negated
+    on odd intervals, so the normalisation ANDs take a fifth round."""
+    import dataclasses
+    k = spec.k
+    P = [PredDesc(min(3, k), 1, 3, 0), PredDesc(k, 0, (1 << k) // 3 + 1, 1),
+         PredDesc(k, (1 << k) // 5, 1 << (k - 1), 1)]
+    nodes = [BxNode("pred", pred=q) for q in P]
+    nodes += [BxNode("and", 0, 1), BxNode("or", 3, 2), BxNode("and", 4, 0), BxNode("or", 5, 1),
+              BxNode("not", 6)]
+    outs = [[6 if i % 2 == 0 else 7 for i in range(spec.m)]]
+    return dataclasses.replace(spec, piecewise=outs, bx_nodes=nodes, name=spec.name + "_deep")
 
 
 def approx_error(spec: OperatorSpec, x_fixed: np.ndarray, y_fixed: np.ndarray) -> dict:

@@ -16,6 +16,20 @@ def ospec(sp):
     return O.Spec(**sp.descriptor())
 
 
+def _formula_value(nodes, v, x):
+    """The bit-expression grammar's semantics with Python booleans."""
+    nd = nodes[v]
+    if nd.op == "pred":
+        q = nd.pred
+        return int((((x % (1 << q.f)) + q.c) % (1 << q.f)) < q.gamma) ^ q.negate
+    if nd.op == "const":
+        return nd.a
+    if nd.op == "not":
+        return 1 - _formula_value(nodes, nd.a, x)
+    a, b = _formula_value(nodes, nd.a, x), _formula_value(nodes, nd.b, x)
+    return {"xor": a ^ b, "and": a & b, "or": a | b}[nd.op]
+
+
 def python_plain(sp, xs):
     """Independent plaintext evaluation with Python integers."""
     ys, zs = [], []
@@ -41,7 +55,10 @@ def python_plain(sp, xs):
         for t, (f, c, g, neg) in enumerate(bits):
             v = (((x % (1 << f)) + c) % (1 << f)) < g
             z |= (int(v) ^ neg) << t
-        for j, out in enumerate(sp.piecewise):          # the active interval's predicate
+        for j, out in enumerate(sp.piecewise):          # the active interval's predicate / formula
+            if sp.bx_nodes:
+                z |= _formula_value(sp.bx_nodes, out[i], x) << (len(bits) + j)
+                continue
             q = out[i]
             v = (((x % (1 << q.f)) + q.c) % (1 << q.f)) < q.gamma
             z |= (int(v) ^ q.negate) << (len(bits) + j)
@@ -216,8 +233,9 @@ def test_xhat_basis_matches_standard_reconstruction():
 def test_piecewise_boolean_outputs_every_mask_every_input(k):
     """Lemma "boolean normalization": piecewise Boolean outputs
     z_j = XOR_i (J_i AND B_i^(j)) with XOR-shared interval indicators and one
-    packed Boolean AND triple per output reconstruct B_{i*}^(j)(x) for all
-    x and r; each output adds 8 bytes per party (one opening of e and f)."""
+    packed Boolean AND triple per 32 gates reconstruct B_{i*}^(j)(x) for all
+    x and r; the n_pw * m normalisation ANDs take one round and 8 bytes per
+    party per 32 of them (one opening of e and f)."""
     rng = np.random.default_rng(120 + k)
     N = 2 ** k
     for trial in range(6):
@@ -235,7 +253,98 @@ def test_piecewise_boolean_outputs_every_mask_every_input(k):
         yp, zp = python_plain(sp, xs)
         assert (y == yp).all() and (z == zp).all(), (trial, sp.name)
         mults = 0 if sp.xhat_basis else d
-        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * len(sp.piecewise))).all()
+        words = -(-len(sp.piecewise) * m // 32)
+        assert o.n_bw == words
+        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * words)).all()
+
+
+def _and_rounds(nodes, roots):
+    """Rounds and packed words of the formulas' AND gates, from the AND
+    depths: AND / OR add one, NOT / XOR keep their inputs' depth."""
+    dep = []
+    for nd in nodes:
+        if nd.op in ("pred", "const"):
+            dep.append(0)
+        elif nd.op == "not":
+            dep.append(dep[nd.a])
+        else:
+            dep.append(max(dep[nd.a], dep[nd.b]) + (0 if nd.op == "xor" else 1))
+    gates = {}
+    for v, nd in enumerate(nodes):
+        if nd.op in ("and", "or"):
+            gates[dep[v]] = gates.get(dep[v], 0) + 1
+    for out in roots:
+        for r in out:
+            gates[dep[r] + 1] = gates.get(dep[r] + 1, 0) + 1
+    return max(gates), sum(-(-g // 32) for g in gates.values())
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_formula_outputs_every_mask_every_input(k):
+    """Boolean formulas per interval (NOT / XOR / AND / OR over predicates
+    and constants, AND depth up to 4): the round-by-round evaluation on XOR
+    shares with packed Boolean AND triples reconstructs B_{i*}^(j)(x) for
+    every x and every mask r; each AND round sends 8 bytes per party per 32
+    gates."""
+    rng = np.random.default_rng(310 + k)
+    N = 2 ** k
+    for trial in range(5):
+        m = int(rng.integers(1, min(N - 1, 8) + 1))
+        d = int(rng.integers(0, 3))
+        sp = S.random_spec(rng, k, m, d, 1, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 2)))
+        sp = S.random_formulas(rng, sp, int(rng.integers(1, 4)), n_nodes=int(rng.integers(3, 30)))
+        if trial % 3 == 2:
+            sp = sp.variant(True)
+        hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
+        xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
+        rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all(), (trial, sp.name)
+        rounds, words = _and_rounds(sp.bx_nodes, sp.piecewise)
+        assert (o.n_bx_rounds, o.n_bw) == (rounds, words)
+        mults = 0 if sp.xhat_basis else d
+        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * words)).all()
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_formula_depth_bound_every_mask_every_input(k):
+    """Formulas at the AND-depth bound (4), so five exchange rounds, for
+    every x and r."""
+    rng = np.random.default_rng(400 + k)
+    N = 2 ** k
+    sp = S.deep_formula(S.random_spec(rng, k, 3, 1, 1, partition_bits=True))
+    xs = np.tile(np.arange(N, dtype=np.uint64), N)
+    rs = np.repeat(np.arange(N, dtype=np.uint64), N) + (rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64)
+                                                         << np.uint64(k))
+    o, res, y, z = run_gate(sp, xs, r_override=rs)
+    assert (o.n_bx_rounds, o.n_bw) == (5, 5)
+    yp, zp = python_plain(sp, xs)
+    assert (y == yp).all() and (z == zp).all()
+
+
+def test_formula_closed_form_example():
+    """A hand-written formula with a closed form: on the negative half
+    (x >= 2^(k-1)) output (x mod 16 < 8) AND NOT(x mod 4 < 1), on the
+    non-negative half (x < 100) OR MSB(x + 2^(k-1)), i.e. x < 100 OR x < 2^(k-1)."""
+    k = 8
+    sp = S.random_spec(np.random.default_rng(2), k, 2, 1)
+    sp.alpha = [0, 1 << (k - 1), 1 << k]
+    sp.partition_bits = False
+    sp.preds = []
+    nodes = [S.BxNode("pred", pred=S.PredDesc(4, 0, 8, 0)),            # 0: x mod 16 < 8
+             S.BxNode("pred", pred=S.PredDesc(2, 0, 1, 0)),            # 1: x mod 4 < 1
+             S.BxNode("not", 1),                                       # 2
+             S.BxNode("and", 0, 2),                                    # 3
+             S.BxNode("pred", pred=S.PredDesc(k, 0, 100, 0)),          # 4: x < 100
+             S.BxNode("pred", pred=S.PredDesc(k, 1 << (k - 1), 1 << (k - 1), 1)),   # 5: MSB(x + 2^(k-1))
+             S.BxNode("or", 4, 5)]                                     # 6
+    sp.bx_nodes, sp.piecewise = nodes, [[6, 3]]
+    xs = np.arange(1 << k, dtype=np.uint64)
+    _, res, _, z = run_gate(sp, xs + (np.uint64(7) << np.uint64(40)))
+    want = [(int(x < 100 or x < 128) if x < 128 else int(x % 16 < 8 and x % 4 != 0)) for x in range(1 << k)]
+    assert list(z) == want
 
 
 def test_piecewise_relu_sign_select():
@@ -308,7 +417,7 @@ def test_truncation_with_polynomial_and_boolean_outputs(k):
         yp, zp = python_plain(sp, xs)
         assert (y == yp).all() and (z == zp).all(), trial
         mults = 0 if sp.xhat_basis else d * r
-        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * len(sp.piecewise) + 1)).all()
+        assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * -(-len(sp.piecewise) * sp.m // 32) + 1)).all()
 
 
 @pytest.mark.parametrize("k,s", [(40, 20), (63, 49), (63, 1), (48, 47)])
