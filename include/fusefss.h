@@ -56,6 +56,9 @@ extern "C" {
 #define FFSS_MAX_P 4         /* payload length p = n_out * (degree + 1) */
 #define FFSS_MAX_BOOL 32     /* Boolean outputs, one uint32 per element */
 #define FFSS_MAX_PW 4        /* piecewise Boolean outputs */
+#define FFSS_MAX_BX_NODES 64 /* nodes of the piecewise outputs' Boolean formulas */
+#define FFSS_MAX_BX_DEPTH 4  /* AND depth of one formula (AND and OR nodes on a path) */
+#define FFSS_MAX_BX_WORDS 8  /* packed Boolean AND triples per element (32 AND gates each) */
 #define FFSS_MAX_T 32        /* packed-comparison queries, one uint32 of atoms */
 
 typedef struct ffss_ctx ffss_ctx;     /* per-device state (tables, autotune cache) */
@@ -72,6 +75,27 @@ typedef struct {
     uint64_t c;          /* public shift, c < 2^f */
     uint64_t gamma;      /* threshold, 0 <= gamma <= 2^f (0 and 2^f are constants) */
 } ffss_pred_desc;
+
+/* One node of a piecewise Boolean formula, the bit-expression grammar of the
+ * operator specification (Sec. 4.1 item 3; App. "a minimal typed expression
+ * language": 0 | 1 | C_beta | D_{gamma,f} | MSB(x+c) | NOT | XOR | AND | OR).
+ *   FFSS_BX_PRED   pred (a predicate as in ffss_pred_desc; negate applies)
+ *   FFSS_BX_CONST  the constant bit a (0 or 1)
+ *   FFSS_BX_NOT    NOT node a
+ *   FFSS_BX_XOR / FFSS_BX_AND / FFSS_BX_OR   node a op node b
+ * Children are indices of earlier nodes (a, b < this node's index), so a node
+ * array is a DAG in topological order; subformulas may be shared. */
+#define FFSS_BX_PRED 0
+#define FFSS_BX_CONST 1
+#define FFSS_BX_NOT 2
+#define FFSS_BX_XOR 3
+#define FFSS_BX_AND 4
+#define FFSS_BX_OR 5
+typedef struct {
+    uint32_t op;
+    uint32_t a, b;
+    ffss_pred_desc pred;
+} ffss_bx_node;
 
 /* Operator specification (Sec. 4.1).  Caller-owned; copied by ffss_spec_compile.
  * alpha: m+1 entries with alpha[0] = 0 < alpha[1] < ... < alpha[m] = 2^k
@@ -102,13 +126,20 @@ typedef struct {
     uint32_t xhat_basis;
     /* Piecewise Boolean outputs (Sec. 4.1 item 3, Lemma "boolean
      * normalization"): output j (0 <= j < n_piecewise <= FFSS_MAX_PW) is
-     * B_i^(j)(x) on interval i, B_i^(j) = piecewise[i * n_piecewise + j]
-     * (m * n_piecewise entries, each a predicate like preds[]).  The bits
-     * follow the other Boolean outputs in the output word (bit
-     * n_bool - n_piecewise + j, n_bool from the shape) and take one extra exchange of 8 bytes per
-     * output per party (one packed Boolean AND triple).  Computed by the
-     * fused two-party calls only (ffss_eval_pair, the batch, the server);
-     * ffss_eval_pred returns the other outputs. */
+     * B_i^(j)(x) on interval i.  The bits follow the other Boolean outputs
+     * in the output word (bit n_bool - n_piecewise + j, n_bool from the
+     * shape).  Computed by the fused two-party calls only (ffss_eval_pair,
+     * the batch, the server); ffss_eval_pred returns the other outputs.
+     * With formula nodes (n_bx_nodes > 0) B_i^(j) is the formula rooted at
+     * bx_nodes[piecewise_root[i * n_piecewise + j]] and piecewise is unused.
+     * Without them each B_i^(j) is the single predicate
+     * piecewise[i * n_piecewise + j], taken as node j * m + i.
+     * Evaluation (Lemma "boolean normalization"): z_j = XOR_i (J_i AND
+     * B_i^(j)).  Round l = 1, 2, ... evaluates the AND gates of depth l: the
+     * AND and OR nodes of AND depth l (node order), then the normalisation
+     * gates J_i AND B_i^(j) with depth(B_i^(j)) + 1 = l (output-major,
+     * interval-minor); 32 gates per packed Boolean triple, one exchange of
+     * 4 + 4 bytes per triple word per party. */
     uint32_t n_piecewise;
     const ffss_pred_desc *piecewise;
     /* Shift gate (truncation / ARS as a specification-compatible gate,
@@ -123,6 +154,10 @@ typedef struct {
      * post-comparison messages). */
     uint32_t trunc_shift;
     uint32_t trunc_signed;
+    /* Formulas of the piecewise outputs (see piecewise above); 0 / NULL: none. */
+    uint32_t n_bx_nodes;                 /* <= FFSS_MAX_BX_NODES */
+    const ffss_bx_node *bx_nodes;
+    const uint32_t *piecewise_root;      /* m * n_piecewise node indices */
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -136,7 +171,7 @@ typedef struct {
     uint32_t n_bool;         /* Boolean outputs, piecewise ones included (bits of the output word) */
     uint32_t n_views;        /* distinct (f, c) views among the queries */
     uint64_t key_bytes_per_elem;   /* one party, this library's layout */
-    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults + 8 * n_piecewise
+    uint64_t comm_bytes_per_elem;  /* one party, online: 8 + 16 * n_mults + 8 * bx_words
                                       (+ 1 with a shift) */
     uint64_t aes_per_elem;         /* one party, online AES-128 blocks */
     uint64_t keygen_aes_per_elem;  /* dealer AES-128 blocks per element (both parties' keys,
@@ -144,6 +179,8 @@ typedef struct {
                                       k (4 + 4V) + 2V per lookup key */
     uint32_t n_piecewise;          /* piecewise Boolean outputs (the last n_piecewise of n_bool) */
     uint32_t trunc_shift;          /* the shift s, 0 = none */
+    uint32_t bx_rounds;            /* exchange rounds of the piecewise outputs' AND gates */
+    uint32_t bx_words;             /* packed Boolean AND triples per element */
 } ffss_shape;
 
 /* ---- context ------------------------------------------------------------ */

@@ -349,12 +349,13 @@ FFSS_CORE void expand_children(uint4 s0, uint4 s1, uint32_t nc, uint4 (&ch)[2][4
 
 // Bit-payload DCF Gen of arity 4 for 1[u < alpha] on k-bit u, both parties.
 // keep4(i0) returns the path child's random block 0 of levels i0 .. i0 + 3
-// (its seed CW, and bit 1 its value CW).  Writes the child CWs (level i,
-// child c at cw + i * cs + c) and the leaf CW bit into both keys; the caller
+// (its seed CW, and bit 1 its value CW).  Hands each child CW to
+// sink.put(c, cw) and closes level i with sink.level_done(i) (the CWs are the
+// same in both keys); writes the leaf CW bit into both keys.  The caller
 // stores the roots s0, s1.
-template <class AES4, class KEEP4>
-FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *cw0, uint4 *cw1, uint64_t cs,
-                           uint64_t *leaf0, uint64_t *leaf1, const AES4 &aes4, const KEEP4 &keep4) {
+template <class AES4, class KEEP4, class SINK>
+FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, const SINK &sink, uint64_t *leaf0,
+                           uint64_t *leaf1, const AES4 &aes4, const KEEP4 &keep4) {
   const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1, wb = 0;
   Blk4 R4;
@@ -384,9 +385,9 @@ FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4
           ka1 = ch[1][c];
         }
       }
-      cw0[i * cs + c] = cw;
-      cw1[i * cs + c] = cw;
+      sink.put(c, cw);
     }
+    sink.level_done(i);
     // the path continues through child a
     wb = (wb ^ (ka0.x >> 1) ^ (ka1.x >> 1) ^ (ck.x >> 1)) & 1u;
     uint4 sk = ck;
@@ -423,13 +424,12 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
 // Vector-payload DCF Gen of arity 4 for beta * 1[u < alpha] on k-bit u
 // (k <= 32), both parties.  keep4(i): the path child's random blocks of
 // level i; block 0 its seed CW, blocks 1..V its value CWs (p little-endian
-// uint64).  Writes the child CWs (level i, child c at cw + i * cs + c), the
-// value CWs (word q at vcw + i * vs + c * P + q) and the leaf CWs (word q at
-// leaf + q * n); the caller stores the roots s0, s1.
-template <int P, class AES4, class KEEP4>
-FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1, uint4 *cw0,
-                           uint4 *cw1, uint64_t cs, uint64_t *vcw0, uint64_t *vcw1, uint64_t vs, uint64_t *leaf0,
-                           uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
+// uint64).  Hands each child's seed CW and value CWs to sink.put(c, cw, vc)
+// and closes level i with sink.level_done(i); writes the leaf CWs (word q at
+// leaf + q * n) into both keys.  The caller stores the roots s0, s1.
+template <int P, class AES4, class KEEP4, class SINK>
+FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1, const SINK &sink,
+                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   constexpr uint32_t V = (P + 1) / 2;
   const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1;
@@ -506,12 +506,10 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
             ka1 = c1;
           }
         }
-        cw0[i * cs + c] = cw;
-        cw1[i * cs + c] = cw;
-        store_words<P>(vcw0 + i * vs + c * P, vc);
-        store_words<P>(vcw1 + i * vs + c * P, vc);
+        sink.put(c, cw, vc);
       }
     }
+    sink.level_done(i);
     // the path continues through child a
 #pragma unroll
     for (int q = 0; q < P; ++q) W[q] = W[q] + ca0[q] - ca1[q] + (neg ? 0ull - vk[q] : vk[q]);

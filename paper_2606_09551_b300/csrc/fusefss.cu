@@ -239,8 +239,9 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
     S.out_prim[o] = found;
   }
   // piecewise outputs: the partition predicates C_{alpha_i} (for the interval
-  // indicators) join the distinct predicates, then each output's
-  // per-interval predicates, output by output, interval by interval
+  // indicators) join the distinct predicates, then the formulas' predicate
+  // nodes in node order.  Without formula nodes each B_i^(j) is the single
+  // predicate piecewise[i * n_pw + j], taken as node j * m + i.
   auto add_prim = [&](uint32_t f, uint64_t c, uint64_t g) -> int {
     if (g == 0 || g == (uint64_t(1) << f)) return -1;
     for (uint32_t j = 0; j < S.n_prim; ++j)
@@ -257,24 +258,80 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
     return fail(FFSS_ERR_UNSUPPORTED, "%u Boolean outputs > %d", S.n_bool + d->n_piecewise, FFSS_MAX_BOOL);
   S.n_pw = d->n_piecewise;
   if (S.n_pw > 0) {
-    if (!d->piecewise) return fail(FFSS_ERR_INVALID, "piecewise predicates NULL");
+    const bool formulas = d->n_bx_nodes > 0;
+    if (!formulas && !d->piecewise) return fail(FFSS_ERR_INVALID, "piecewise predicates NULL");
+    if (formulas && (!d->bx_nodes || !d->piecewise_root)) return fail(FFSS_ERR_INVALID, "formula nodes or roots NULL");
+    const uint32_t nn = formulas ? d->n_bx_nodes : d->m * S.n_pw;
+    if (nn > uint32_t(FFSS_MAX_BX_NODES))
+      return fail(FFSS_ERR_UNSUPPORTED, "%u formula nodes > %d", nn, FFSS_MAX_BX_NODES);
     for (uint32_t i = 1; i < d->m; ++i) {
       S.part_prim[i] = add_prim(d->k, 0, d->alpha[i]);
       if (S.part_prim[i] < -1) return fail(FFSS_ERR_UNSUPPORTED, "more than %d distinct predicates", kMaxBool);
     }
-    for (uint32_t j = 0; j < S.n_pw; ++j)
-      for (uint32_t i = 0; i < d->m; ++i) {
-        const ffss_pred_desc &q = d->piecewise[i * S.n_pw + j];
-        if (q.f < 1 || q.f > d->k) return fail(FFSS_ERR_INVALID, "piecewise (%u, %u): f=%u outside 1..k", i, j, q.f);
+    S.n_bx = nn;
+    for (uint32_t v = 0; v < nn; ++v) {
+      const uint32_t op = formulas ? d->bx_nodes[v].op : kBxPred;
+      const uint32_t a = formulas ? d->bx_nodes[v].a : 0, bb = formulas ? d->bx_nodes[v].b : 0;
+      S.bx_op[v] = uint8_t(op);
+      S.bx_prim[v] = -1;
+      if (op == kBxPred) {
+        const ffss_pred_desc &q = formulas ? d->bx_nodes[v].pred : d->piecewise[(v % d->m) * S.n_pw + v / d->m];
+        if (q.f < 1 || q.f > d->k) return fail(FFSS_ERR_INVALID, "formula node %u: f=%u outside 1..k", v, q.f);
         const uint64_t Nf = uint64_t(1) << q.f;
-        if (q.c >= Nf || q.gamma > Nf)
-          return fail(FFSS_ERR_INVALID, "piecewise (%u, %u): c or gamma out of range", i, j);
+        if (q.c >= Nf || q.gamma > Nf) return fail(FFSS_ERR_INVALID, "formula node %u: c or gamma out of range", v);
         const int pr = add_prim(q.f, q.c, q.gamma);
         if (pr < -1) return fail(FFSS_ERR_UNSUPPORTED, "more than %d distinct predicates", kMaxBool);
-        S.pw_prim[j][i] = pr;
-        const uint32_t cst = (pr < 0 && q.gamma != 0) ? 1u : 0u;
-        S.pw_fix[j] |= (cst ^ (q.negate & 1u)) << i;
+        S.bx_prim[v] = int8_t(pr);
+        const uint64_t cst = (pr < 0 && q.gamma != 0) ? 1u : 0u;
+        S.bx_fix |= (cst ^ (q.negate & 1u)) << v;
+        S.bx_depth[v] = 0;
+      } else if (op == kBxConst) {
+        if (a > 1) return fail(FFSS_ERR_INVALID, "formula node %u: constant %u not a bit", v, a);
+        S.bx_fix |= uint64_t(a) << v;
+        S.bx_depth[v] = 0;
+      } else if (op == kBxNot) {
+        if (a >= v) return fail(FFSS_ERR_INVALID, "formula node %u: child %u not an earlier node", v, a);
+        S.bx_a[v] = uint8_t(a);
+        S.bx_fix |= uint64_t(1) << v;
+        S.bx_depth[v] = S.bx_depth[a];
+      } else if (op == kBxXor || op == kBxAnd || op == kBxOr) {
+        if (a >= v || bb >= v) return fail(FFSS_ERR_INVALID, "formula node %u: children not earlier nodes", v);
+        S.bx_a[v] = uint8_t(a);
+        S.bx_b[v] = uint8_t(bb);
+        const uint32_t dep = std::max(S.bx_depth[a], S.bx_depth[bb]) + (op == kBxXor ? 0u : 1u);
+        if (dep > uint32_t(FFSS_MAX_BX_DEPTH))
+          return fail(FFSS_ERR_UNSUPPORTED, "formula node %u: AND depth %u > %d", v, dep, FFSS_MAX_BX_DEPTH);
+        S.bx_depth[v] = uint8_t(dep);
+      } else {
+        return fail(FFSS_ERR_INVALID, "formula node %u: unknown op %u", v, op);
       }
+    }
+    uint32_t R = 1;
+    for (uint32_t v = 0; v < nn; ++v) R = std::max(R, uint32_t(S.bx_depth[v]));
+    for (uint32_t i = 0; i < d->m; ++i)
+      for (uint32_t j = 0; j < S.n_pw; ++j) {
+        const uint32_t root = formulas ? d->piecewise_root[i * S.n_pw + j] : j * d->m + i;
+        if (root >= nn) return fail(FFSS_ERR_INVALID, "piecewise root (%u, %u) = %u not a node", i, j, root);
+        S.pw_root[j][i] = uint8_t(root);
+        R = std::max(R, uint32_t(S.bx_depth[root]) + 1);
+      }
+    // AND gates by round and their packed triple words
+    S.n_bxr = R;
+    uint32_t ng = 0, nw = 0;
+    for (uint32_t l = 1; l <= R; ++l) {
+      S.gate_off[l] = uint8_t(ng);
+      S.bw_base[l] = uint8_t(nw);
+      for (uint32_t v = 0; v < nn; ++v)
+        if ((S.bx_op[v] == kBxAnd || S.bx_op[v] == kBxOr) && S.bx_depth[v] == l) S.gate[ng++] = uint8_t(v);
+      for (uint32_t j = 0; j < S.n_pw; ++j)
+        for (uint32_t i = 0; i < d->m; ++i)
+          if (S.bx_depth[S.pw_root[j][i]] + 1u == l) S.gate[ng++] = uint8_t(kMaxBx + 16 * j + i);
+      nw += (ng - S.gate_off[l] + 31) / 32;
+    }
+    S.gate_off[R + 1] = uint8_t(ng);
+    if (nw > uint32_t(FFSS_MAX_BX_WORDS))
+      return fail(FFSS_ERR_UNSUPPORTED, "%u packed AND triples > %d", nw, FFSS_MAX_BX_WORDS);
+    S.n_bw = nw;
   }
   // query list: views in order of first appearance; per view the r-atom, then
   // one theta atom per predicate of that view.  A shift gate appends the
@@ -334,9 +391,11 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
   sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.n_mults; sh.n_bool = S.n_bool + S.n_pw;
   sh.n_piecewise = S.n_pw;
+  sh.bx_rounds = S.n_pw ? S.n_bxr : 0;
+  sh.bx_words = S.n_bw;
   sh.n_views = S.n_views;
   sh.key_bytes_per_elem = key_bytes_per_elem(S);
-  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults + 8ull * S.n_pw + (S.trunc_s ? 1 : 0);
+  sh.comm_bytes_per_elem = 8 + 16ull * S.n_mults + 8ull * S.n_bw + (S.trunc_s ? 1 : 0);
   sh.trunc_shift = S.trunc_s;
   sh.aes_per_elem = aes_per_elem(S);
   sh.keygen_aes_per_elem = keygen_aes_per_elem(S);
@@ -425,7 +484,8 @@ static size_t spec_smem() { return (sizeof(DevSpec) + 15) & ~size_t(15); }
 
 template <int P>
 static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t st) {
-  const size_t smem = kTabBytes + spec_smem() + 44 * 4;
+  const size_t smem = keygen_stage_off() + size_t(kKeygenThreads / 32) * kStageBytes;
+  static_assert(44 * 4 <= 256, "PRG round keys fit their slot");
   static std::once_flag once;
   int rc = FFSS_OK;
   std::call_once(once, [&] { rc = set_smem(keygen_kernel<P>, smem); });

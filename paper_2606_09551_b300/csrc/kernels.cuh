@@ -176,57 +176,117 @@ __device__ __forceinline__ uint32_t combine_bits(uint32_t b, const DevSpec &S, c
 // Piecewise Boolean outputs (Lemma "boolean normalization"): output j is
 // XOR_i (J_i AND B_i^(j)), where J_i = C_{alpha_{i+1}} ^ C_{alpha_i} is the
 // interval indicator (Lemma "interval indicator as XOR"; C_{alpha_0} = 0,
-// C_{alpha_m} = 1).  Both are m-bit words of XOR shares (bit i = interval
-// i), so an output's m ANDs take one packed Boolean triple (a, b, c): each
-// party opens e = J ^ a and f = B ^ b (4 + 4 bytes), then holds
-// [party 0] (E & F) ^ (E & b) ^ (F & a) ^ c, whose parity is its share of z_j.
-// First half: write this party's (e | f << 32) words to `out` (kMaxPW slots).
-__device__ __forceinline__ void pw_send(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
-                                        uint64_t e, bool valid, uint32_t atoms, uint64_t *out,
-                                        unsigned long long &sent) {
-  uint32_t jw = 0;
-  const uint32_t *bt = reinterpret_cast<const uint32_t *>(kb + L.off_btrip);
-  const uint32_t carry = valid ? reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e] : 0u;
-  if (valid) {
-    uint32_t c_prev = 0;                       // C_{alpha_0} = 0
-    for (uint32_t i = 0; i < S.m; ++i) {
-      const uint32_t c_next = i + 1 < S.m ? prim_share(S, atoms, carry, S.part_prim[i + 1]) : (b == 0 ? 1u : 0u);
-      jw |= (c_next ^ c_prev) << i;
-      c_prev = c_next;
-    }
+// C_{alpha_m} = 1) and B_i^(j) a formula over the primitive predicates.  A
+// party holds XOR shares of the formula nodes as bits of a word nv; NOT and
+// XOR are local (constants by party 0), each AND / OR node and each
+// normalisation AND is a gate of the exchange round given by its AND depth,
+// 32 gates to a packed Boolean triple (a, b, c): each party opens
+// e = X ^ a and f = Y ^ b (4 + 4 bytes), then holds
+// [party 0] (E & F) ^ (E & b) ^ (F & a) ^ c, bit g = its share of gate g's
+// AND (an OR adds its input shares: x | y = x ^ y ^ (x & y)).  These steps
+// run once per element and round; compiled out of line, they leave the
+// gate's register allocation for the DCF walks alone.
+
+// This party's interval indicators (bit i = share of J_i).
+__device__ __noinline__ uint32_t pw_J(uint32_t b, const DevSpec &S, uint32_t atoms, uint32_t carry) {
+  uint32_t jw = 0, c_prev = 0;                       // C_{alpha_0} = 0
+  for (uint32_t i = 0; i < S.m; ++i) {
+    const uint32_t c_next = i + 1 < S.m ? prim_share(S, atoms, carry, S.part_prim[i + 1]) : (b == 0 ? 1u : 0u);
+    jw |= (c_next ^ c_prev) << i;
+    c_prev = c_next;
   }
-  for (uint32_t j = 0; j < S.n_pw; ++j) {
-    uint64_t msg = 0;
-    if (valid) {
-      uint32_t bw = b == 0 ? S.pw_fix[j] : 0u;
-      for (uint32_t i = 0; i < S.m; ++i) {
-        const int pr = S.pw_prim[j][i];
-        if (pr >= 0) bw ^= prim_share(S, atoms, carry, pr) << i;
-      }
-      const uint32_t a = bt[(uint64_t(j) * 3 + 0) * L.n + e], bb = bt[(uint64_t(j) * 3 + 1) * L.n + e];
-      msg = uint64_t(jw ^ a) | (uint64_t(bw ^ bb) << 32);
-      sent += 8;
-    }
-    out[j] = msg;
+  return jw;
+}
+
+// The formula nodes of AND depth l that need no exchange, in node order:
+// predicates and constants (depth 0), NOT and XOR of nodes already held.
+__device__ __noinline__ uint64_t bx_local(uint32_t b, const DevSpec &S, uint32_t atoms, uint32_t carry,
+                                             uint32_t l, uint64_t nv) {
+  for (uint32_t v = 0; v < S.n_bx; ++v) {
+    if (S.bx_depth[v] != l) continue;
+    const uint32_t op = S.bx_op[v];
+    uint32_t bit;
+    if (op == kBxPred) bit = S.bx_prim[v] >= 0 ? prim_share(S, atoms, carry, S.bx_prim[v]) : 0u;
+    else if (op == kBxConst) bit = 0;
+    else if (op == kBxNot) bit = uint32_t(nv >> S.bx_a[v]) & 1u;
+    else if (op == kBxXor) bit = uint32_t((nv >> S.bx_a[v]) ^ (nv >> S.bx_b[v])) & 1u;
+    else continue;   // AND / OR: a gate of round l
+    if (b == 0) bit ^= uint32_t(S.bx_fix >> v) & 1u;
+    nv |= uint64_t(bit) << v;
+  }
+  return nv;
+}
+
+// The two input shares of gate g: an AND / OR node's children, or (J_i, B_i^(j)).
+__device__ __forceinline__ void gate_in(const DevSpec &S, uint32_t g, uint64_t nv, uint32_t J, uint32_t &x,
+                                        uint32_t &y) {
+  if (g < uint32_t(kMaxBx)) {
+    x = uint32_t(nv >> S.bx_a[g]) & 1u;
+    y = uint32_t(nv >> S.bx_b[g]) & 1u;
+  } else {
+    const uint32_t j = (g - kMaxBx) >> 4, i = (g - kMaxBx) & 15u;
+    x = (J >> i) & 1u;
+    y = uint32_t(nv >> S.pw_root[j][i]) & 1u;
   }
 }
 
-// Second half: combine both parties' openings into this party's output bits
-// (already shifted to bit n_bool + j).
-__device__ __forceinline__ uint32_t pw_finish(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
-                                              uint64_t e, const uint64_t *m0, const uint64_t *m1) {
+// Round l, first half: this party's (e | f << 32) words to out[0 ..).
+__device__ __noinline__ void bx_send(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e,
+                                        bool valid, uint64_t nv, uint32_t J, uint32_t l, uint64_t *out,
+                                        unsigned long long &sent) {
   const uint32_t *bt = reinterpret_cast<const uint32_t *>(kb + L.off_btrip);
-  uint32_t z = 0;
-  for (uint32_t j = 0; j < S.n_pw; ++j) {
-    const uint64_t o = m0[j] ^ m1[j];
-    const uint32_t Ev = uint32_t(o), Fv = uint32_t(o >> 32);
-    const uint32_t a = bt[(uint64_t(j) * 3 + 0) * L.n + e], bb = bt[(uint64_t(j) * 3 + 1) * L.n + e];
-    const uint32_t c = bt[(uint64_t(j) * 3 + 2) * L.n + e];
-    uint32_t w = (Ev & bb) ^ (Fv & a) ^ c;
-    if (b == 0) w ^= Ev & Fv;
-    z |= (uint32_t(__popc(w)) & 1u) << (S.n_bool + j);
+  const uint32_t g0 = S.gate_off[l], ng = uint32_t(S.gate_off[l + 1]) - g0;
+  for (uint32_t w = 0; 32 * w < ng; ++w) {
+    uint64_t msg = 0;
+    if (valid) {
+      const uint32_t gw = min(32u, ng - 32 * w), wi = S.bw_base[l] + w;
+      uint32_t X = 0, Y = 0;
+      for (uint32_t t = 0; t < gw; ++t) {
+        uint32_t x, y;
+        gate_in(S, S.gate[g0 + 32 * w + t], nv, J, x, y);
+        X |= x << t;
+        Y |= y << t;
+      }
+      const uint32_t a = bt[(uint64_t(wi) * 3 + 0) * L.n + e], bb = bt[(uint64_t(wi) * 3 + 1) * L.n + e];
+      msg = uint64_t(X ^ a) | (uint64_t(Y ^ bb) << 32);
+      sent += 8;
+    }
+    out[w] = msg;
   }
-  return z;
+}
+
+// Round l, second half: both parties' openings -> this party's gate shares
+// (AND / OR nodes into nv, normalisation gates into output bit j of zp).
+__device__ __noinline__ void bx_finish(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
+                                          uint64_t e, uint32_t J, uint32_t l, const uint64_t *m0,
+                                          const uint64_t *m1, uint64_t &nv, uint32_t &zp) {
+  const uint32_t *bt = reinterpret_cast<const uint32_t *>(kb + L.off_btrip);
+  const uint32_t g0 = S.gate_off[l], ng = uint32_t(S.gate_off[l + 1]) - g0;
+  uint64_t nn = nv;
+  for (uint32_t w = 0; 32 * w < ng; ++w) {
+    const uint32_t gw = min(32u, ng - 32 * w), wi = S.bw_base[l] + w;
+    const uint64_t o = m0[w] ^ m1[w];
+    const uint32_t Ev = uint32_t(o), Fv = uint32_t(o >> 32);
+    const uint32_t a = bt[(uint64_t(wi) * 3 + 0) * L.n + e], bb = bt[(uint64_t(wi) * 3 + 1) * L.n + e];
+    const uint32_t c = bt[(uint64_t(wi) * 3 + 2) * L.n + e];
+    uint32_t andw = (Ev & bb) ^ (Fv & a) ^ c;
+    if (b == 0) andw ^= Ev & Fv;
+    for (uint32_t t = 0; t < gw; ++t) {
+      const uint32_t g = S.gate[g0 + 32 * w + t];
+      uint32_t bit = (andw >> t) & 1u;
+      if (g < uint32_t(kMaxBx)) {
+        if (S.bx_op[g] == kBxOr) {
+          uint32_t x, y;
+          gate_in(S, g, nv, J, x, y);
+          bit ^= x ^ y;
+        }
+        nn |= uint64_t(bit) << g;
+      } else {
+        zp ^= bit << ((g - kMaxBx) >> 4);
+      }
+    }
+  }
+  nv = nn;
 }
 
 // Shift gate post-processing (truncation / arithmetic right shift by s of the
@@ -296,6 +356,8 @@ struct GateArgsS {
 
 
 constexpr uint32_t kPwSlots = kMaxPW + 1;
+// A round's AND gates (at most kMaxGates) fill at most kMaxPW opening words.
+static_assert((kMaxGates + 31) / 32 <= kMaxPW, "opening slots per round");
 
 // Shared-memory carve-up of a gate CTA (after the T-tables).
 struct GateSmem {
@@ -404,21 +466,41 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
     xs = b == 0 ? xhat - r_b : 0ull - r_b;
 #pragma unroll
     for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
-    if (S.n_pw) pw_send(b, S, L, kb, e, valid, atoms, G.pwbox + (b * E + le) * kPwSlots, sent);
     if (S.trunc_s) {
       G.pwbox[(b * E + le) * kPwSlots + kMaxPW] = valid ? trunc_send(S, L, kb, e, atoms) : 0u;
       if (valid) sent += 1;
     }
   }
-  // piecewise Boolean outputs and the shift gate's bits: one exchange after
-  // the packed comparison (uniform across the CTA: one spec per tile)
+  // the shift gate's bits and the piecewise Boolean outputs, after the packed
+  // comparison: the shift bits travel with the first (or only) exchange, the
+  // formulas take one exchange per AND round (the round count is uniform
+  // across the CTA: one spec per tile)
   uint64_t tsh = 0;
-  if (S.n_pw || S.trunc_s) {
+  if (S.n_pw) {
+    const uint32_t carry = (lead && valid) ? reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e] : 0u;
+    uint64_t nv = 0;
+    uint32_t J = 0, zp = 0;
+    if (lead && valid) {
+      J = pw_J(b, S, atoms, carry);
+      nv = bx_local(b, S, atoms, carry, 0, 0);
+    }
+    for (uint32_t l = 1; l <= S.n_bxr; ++l) {
+      if (l > 1) __syncthreads();   // the previous round's openings have been read
+      if (lead) bx_send(S, L, kb, e, valid, nv, J, l, G.pwbox + (b * E + le) * kPwSlots, sent);
+      __syncthreads();
+      if (lead && valid) {
+        const uint64_t *m0 = G.pwbox + le * kPwSlots, *m1 = G.pwbox + (E + le) * kPwSlots;
+        bx_finish(b, S, L, kb, e, J, l, m0, m1, nv, zp);
+        nv = bx_local(b, S, atoms, carry, l, nv);
+        if (l == 1 && S.trunc_s) tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
+      }
+    }
+    if (lead && valid) z |= zp << S.n_bool;
+  } else if (S.trunc_s) {
     __syncthreads();
     if (lead && valid) {
       const uint64_t *m0 = G.pwbox + le * kPwSlots, *m1 = G.pwbox + (E + le) * kPwSlots;
-      if (S.n_pw) z |= pw_finish(b, S, L, kb, e, m0, m1);
-      if (S.trunc_s) tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
+      tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
     }
   }
   // x^-basis variant: the coefficients multiply the public x^, so Horner is
@@ -656,11 +738,85 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
 // GPU dealer
 // ---------------------------------------------------------------------------
 
+// Per-warp shared-memory staging of one tree level's child records (the
+// four children of each of the warp's 32 consecutive elements).  In the
+// element-major key layout a lane's records lie 64 (seed CWs) or 32p (value
+// CWs) bytes apart, so a store from each lane would scatter one instruction
+// over 16 lines; the staged copy writes both keys in contiguous 512-byte
+// runs instead.  All 32 lanes take part (in a ragged last group the spare
+// lanes redo the last element); lanes 0 .. nact - 1 hold real elements.
+constexpr uint32_t kStageBytes = 32 * 4 * 16 + 32 * 4 * kMaxP * 8;   // per warp
+
+template <int P>
+struct LevelStage {
+  static constexpr int PP = P > 0 ? P : 1;
+  uint4 *scw;            // [32 lanes][4 children]
+  uint64_t *svc;         // [32][4][P]
+  uint4 *cw0, *cw1;      // level-0 child CWs of the warp's first element, both keys
+  uint64_t *vc0, *vc1;   // level-0 value CWs of the warp's first element, both keys
+  uint64_t cs, vs;       // per-level strides (uint4, u64)
+  uint32_t lane, nact;
+  __device__ __forceinline__ void put(uint32_t c, uint4 cw) const { scw[lane * 4 + c] = cw; }
+  __device__ __forceinline__ void put(uint32_t c, uint4 cw, const uint64_t (&vc)[PP]) const {
+    scw[lane * 4 + c] = cw;
+    store_words<P>(svc + (lane * 4 + c) * P, vc);
+  }
+  __device__ __forceinline__ void level_done(uint32_t i) const {
+    __syncwarp();
+#pragma unroll
+    for (uint32_t r = 0; r < 4; ++r) {
+      const uint32_t j = 32 * r + lane;          // element j / 4, child j % 4
+      if (j < 4 * nact) {
+        const uint4 v = scw[j];
+        cw0[i * cs + j] = v;
+        cw1[i * cs + j] = v;
+      }
+    }
+    if constexpr (P > 0) {
+      if constexpr (P % 2 == 0) {               // 16-byte words: 64 P per level
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(svc);
+        ulonglong2 *d0 = reinterpret_cast<ulonglong2 *>(vc0 + i * vs);
+        ulonglong2 *d1 = reinterpret_cast<ulonglong2 *>(vc1 + i * vs);
+#pragma unroll
+        for (uint32_t r = 0; r < 2 * P; ++r) {
+          const uint32_t j = 32 * r + lane;
+          if (j < 2 * P * nact) {
+            const ulonglong2 v = src[j];
+            d0[j] = v;
+            d1[j] = v;
+          }
+        }
+      } else {                                  // 8-byte words: 128 P per level
+#pragma unroll
+        for (uint32_t r = 0; r < 4 * P; ++r) {
+          const uint32_t j = 32 * r + lane;
+          if (j < 4 * P * nact) {
+            const uint64_t v = svc[j];
+            vc0[i * vs + j] = v;
+            vc1[i * vs + j] = v;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+};
+
+// The dealer's dynamic shared memory: T-tables | spec | PRG round keys (256
+// bytes) | one staging area per warp.
+extern __shared__ __align__(16) unsigned char stage_smem[];
+__host__ __device__ constexpr size_t keygen_stage_off() {
+  return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 256;
+}
+__device__ __forceinline__ unsigned char *warp_stage(unsigned char *smem) {
+  return smem + keygen_stage_off() + (threadIdx.x >> 5) * kStageBytes;
+}
+
 // Dealer work items, each compiled out of line (its own register
 // allocation): one lookup key or one comparison key of 32 elements.
 template <int P>
 __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
-                                            uint64_t e, uint64_t ge, uint64_t r_in, uint32_t item) {
+                                            uint64_t e, uint64_t e0, uint64_t ge, uint64_t r_in, uint32_t item) {
   const KeyLayout &L = A.L;
   const uint64_t n = A.n;
   const AesDcfCall4 rkd{tb};
@@ -685,14 +841,18 @@ __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &
   const uint64_t ro = lkey_root_off(S.k, P, n), co = lkey_cw_off(S.k, P, n), lo = lkey_leaf_off(S.k, P, n);
   reinterpret_cast<uint4 *>(l0 + ro)[e] = s0;
   reinterpret_cast<uint4 *>(l1 + ro)[e] = s1;
-  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0 + co) + 4 * e,
-                 reinterpret_cast<uint4 *>(l1 + co) + 4 * e, 4 * n, reinterpret_cast<uint64_t *>(l0) + 4 * P * e,
-                 reinterpret_cast<uint64_t *>(l1) + 4 * P * e, 4 * P * n, reinterpret_cast<uint64_t *>(l0 + lo) + e,
+  const uint32_t lane = threadIdx.x & 31u;
+  unsigned char *st = warp_stage(stage_smem);
+  const LevelStage<P> sink{reinterpret_cast<uint4 *>(st), reinterpret_cast<uint64_t *>(st + 32 * 4 * 16),
+                           reinterpret_cast<uint4 *>(l0 + co) + 4 * e0, reinterpret_cast<uint4 *>(l1 + co) + 4 * e0,
+                           reinterpret_cast<uint64_t *>(l0) + 4 * P * e0, reinterpret_cast<uint64_t *>(l1) + 4 * P * e0,
+                           4 * n, 4 * P * n, lane, uint32_t(min(uint64_t(32), n - e0))};
+  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, sink, reinterpret_cast<uint64_t *>(l0 + lo) + e,
                  reinterpret_cast<uint64_t *>(l1 + lo) + e, n, rkd, keep4);
 }
 
 __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
-                                           uint64_t e, uint64_t ge, uint64_t r_in, uint32_t t) {
+                                           uint64_t e, uint64_t e0, uint64_t ge, uint64_t r_in, uint32_t t) {
   const KeyLayout &L = A.L;
   const uint64_t n = A.n;
   const AesDcfCall4 rkd{tb};
@@ -713,8 +873,12 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
   const uint64_t co = qkey_cw_off(n), lo = qkey_leaf_off(f, n);
   reinterpret_cast<uint4 *>(q0)[e] = s0;
   reinterpret_cast<uint4 *>(q1)[e] = s1;
-  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0 + co) + 4 * e,
-              reinterpret_cast<uint4 *>(q1 + co) + 4 * e, 4 * n, reinterpret_cast<uint64_t *>(q0 + lo) + e,
+  const uint32_t lane = threadIdx.x & 31u;
+  unsigned char *st = warp_stage(stage_smem);
+  const LevelStage<0> sink{reinterpret_cast<uint4 *>(st), nullptr, reinterpret_cast<uint4 *>(q0 + co) + 4 * e0,
+                           reinterpret_cast<uint4 *>(q1 + co) + 4 * e0, nullptr, nullptr, 4 * n, 0, lane,
+                           uint32_t(min(uint64_t(32), n - e0))};
+  dcf_bit_gen(f, alpha, s0, s1, sink, reinterpret_cast<uint64_t *>(q0 + lo) + e,
               reinterpret_cast<uint64_t *>(q1 + lo) + e, rkd, keep4);
 }
 
@@ -747,8 +911,11 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
   for (uint64_t u = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; u < units;
        u += uint64_t(gridDim.x) * blockDim.x / 32) {
     const uint32_t item = uint32_t(u / groups);
-    const uint64_t e = (u % groups) * 32 + lane;
-    if (e >= n) continue;
+    // the whole warp stays on one unit (the key items stage their stores per
+    // warp): in a ragged last group the spare lanes redo element n - 1 and
+    // write the same values as its own lane
+    const uint64_t e0 = (u % groups) * 32;
+    const uint64_t e = min(e0 + lane, n - 1);
     // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id);
     // the counter uses the element's index within the whole call, so a call
     // dealt in chunks gets the same material as in one launch
@@ -758,9 +925,9 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
     };
     const uint64_t r_in = lo64(prg(kDrawRin));
     if (item < n_vec) {
-      gen_lookup_key<P>(A, S, rk_prg, tb, e, ge, r_in, item);
+      gen_lookup_key<P>(A, S, rk_prg, tb, e, e0, ge, r_in, item);
     } else if (item < n_vec + S.T) {
-      gen_query_key(A, S, rk_prg, tb, e, ge, r_in, item - n_vec);
+      gen_query_key(A, S, rk_prg, tb, e, e0, ge, r_in, item - n_vec);
     } else {
       const uint64_t r0 = lo64(prg(kDrawRsh));
       reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;
@@ -808,26 +975,31 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
         tr0[(uint64_t(mi) * 3 + 2) * n + e] = c0;
         tr1[(uint64_t(mi) * 3 + 2) * n + e] = a * bb - c0;
       }
-      // packed Boolean AND triples of the piecewise outputs: m bits each,
-      // c = a AND b, XOR-shared
+      // packed Boolean AND triples of the piecewise outputs' AND gates: one
+      // word per 32 gates of a round, one bit per gate, c = a AND b, XOR-shared
       uint32_t *bt0 = reinterpret_cast<uint32_t *>(A.k0 + L.off_btrip);
       uint32_t *bt1 = reinterpret_cast<uint32_t *>(A.k1 + L.off_btrip);
-      const uint32_t mbits = S.m >= 32 ? 0xFFFFFFFFu : ((1u << S.m) - 1u);
-      for (uint32_t j = 0; j < S.n_pw; ++j) {
-        const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * j;
-        const uint32_t a = prg(di).x & mbits, bb = prg(di + 1).x & mbits;
-        const uint32_t a0 = prg(di + 2).x & mbits, b0 = prg(di + 3).x & mbits, c0 = prg(di + 4).x & mbits;
-        bt0[(uint64_t(j) * 3 + 0) * n + e] = a0;
-        bt1[(uint64_t(j) * 3 + 0) * n + e] = a ^ a0;
-        bt0[(uint64_t(j) * 3 + 1) * n + e] = b0;
-        bt1[(uint64_t(j) * 3 + 1) * n + e] = bb ^ b0;
-        bt0[(uint64_t(j) * 3 + 2) * n + e] = c0;
-        bt1[(uint64_t(j) * 3 + 2) * n + e] = (a & bb) ^ c0;
+      for (uint32_t l = 1; S.n_pw && l <= S.n_bxr; ++l) {
+        const uint32_t ng = uint32_t(S.gate_off[l + 1]) - S.gate_off[l];
+        for (uint32_t w = 0; 32 * w < ng; ++w) {
+          const uint32_t gw = ng - 32 * w >= 32 ? 32u : ng - 32 * w;
+          const uint32_t mbits = gw >= 32 ? 0xFFFFFFFFu : ((1u << gw) - 1u);
+          const uint32_t wi = S.bw_base[l] + w;
+          const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * wi;
+          const uint32_t a = prg(di).x & mbits, bb = prg(di + 1).x & mbits;
+          const uint32_t a0 = prg(di + 2).x & mbits, b0 = prg(di + 3).x & mbits, c0 = prg(di + 4).x & mbits;
+          bt0[(uint64_t(wi) * 3 + 0) * n + e] = a0;
+          bt1[(uint64_t(wi) * 3 + 0) * n + e] = a ^ a0;
+          bt0[(uint64_t(wi) * 3 + 1) * n + e] = b0;
+          bt1[(uint64_t(wi) * 3 + 1) * n + e] = bb ^ b0;
+          bt0[(uint64_t(wi) * 3 + 2) * n + e] = c0;
+          bt1[(uint64_t(wi) * 3 + 2) * n + e] = (a & bb) ^ c0;
+        }
       }
       // shift gate: shares of (r mod 2^k) >> s and two daBits (a random bit
       // held both XOR- and additively shared) for the borrow / wrap B2A
       if (S.trunc_s) {
-        const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * S.n_pw;
+        const uint32_t di = S.base_triples + 5 * S.n_mults + 5 * S.n_bw;
         const uint64_t t = (r_in & ((uint64_t(1) << S.k) - 1)) >> S.trunc_s;
         const uint64_t t0 = lo64(prg(di));
         const uint32_t rho = prg(di + 1).x & 3u, rho0 = prg(di + 2).x & 3u;

@@ -18,12 +18,18 @@ constexpr int kMaxP = 4;
 constexpr int kMaxT = 32;
 constexpr int kMaxBool = 32;
 constexpr int kMaxPW = 4;      // piecewise Boolean outputs
+constexpr int kMaxBx = 64;     // nodes of the piecewise outputs' formulas
+constexpr int kMaxBxDepth = 4; // AND depth of a formula
+constexpr int kMaxBw = 8;      // packed Boolean AND triples per element
+constexpr int kMaxGates = kMaxBx + kMaxM * kMaxPW;   // AND gates of all rounds
+// Formula node kinds (the C ABI's FFSS_BX_* values)
+constexpr uint32_t kBxPred = 0, kBxConst = 1, kBxNot = 2, kBxXor = 3, kBxAnd = 4, kBxOr = 5;
 
 // Dealer draw indices per element (public, spec-determined): r_in, party-0
 // share of r_in, party-0 share of x, party-0 carry-share word, p party-0
 // shares of v_{M-1}, two root seeds per DCF key (queries, then lookup keys),
 // five draws per Beaver triple (a, b, a_0, b_0, c_0), then five per packed
-// Boolean AND triple of a piecewise output (a, b, a_0, b_0, c_0; m bits each),
+// Boolean AND triple word (a, b, a_0, b_0, c_0; one bit per AND gate),
 // then five for a shift gate (share of (r mod 2^k) >> s, the two daBit values,
 // their XOR share, their additive shares lo and hi).
 constexpr uint32_t kDrawRin = 0;
@@ -58,14 +64,27 @@ struct DevSpec {
   uint64_t alpha[kMaxM + 1];
   uint64_t coeff[kMaxM * kMaxP];      // [piece][q], q = o*(d+1) + j
   // Piecewise Boolean outputs (operator specification item 3; Lemma
-  // "boolean normalization"): output j is B_i^(j)(x) on interval i, computed
-  // as XOR_i (J_i AND B_i^(j)) with the interval indicators
-  // J_i = C_{alpha_{i+1}} ^ C_{alpha_i}.  Their bits follow the n_bool
-  // global outputs in the output word.
+  // "boolean normalization"): output j is B_i^(j)(x) on interval i, a
+  // formula over the primitive predicates, computed as XOR_i (J_i AND
+  // B_i^(j)) with the interval indicators J_i = C_{alpha_{i+1}} ^ C_{alpha_i}.
+  // Their bits follow the n_bool global outputs in the output word.
   uint32_t n_pw;
   int32_t part_prim[kMaxM];           // [i], i = 1..m-1: predicate index of C_{alpha_i}
-  int32_t pw_prim[kMaxPW][kMaxM];     // [j][i]: predicate of B_i^(j), or -1 (sentinel constant)
-  uint32_t pw_fix[kMaxPW];            // [j]: bit i = sentinel value ^ negation, applied by party 0
+  uint32_t n_bx, n_bxr, n_bw;         // formula nodes, AND rounds, packed triple words
+  uint8_t bx_op[kMaxBx];              // kBx*
+  uint8_t bx_a[kMaxBx], bx_b[kMaxBx]; // children
+  uint8_t bx_depth[kMaxBx];           // AND depth
+  int8_t bx_prim[kMaxBx];             // kBxPred: predicate index, or -1 (sentinel constant)
+  uint64_t bx_fix;                    // bit v: constant XORed in by party 0 (sentinel ^ negation,
+                                      // the constant, or 1 for NOT)
+  uint8_t pw_root[kMaxPW][kMaxM];     // [j][i]: root node of B_i^(j)
+  // AND gates in round order: a node v < kMaxBx, or kMaxBx + 16 j + i for
+  // the normalisation gate J_i AND B_i^(j).  Round l (1-based) holds gates
+  // [gate_off[l], gate_off[l + 1]); its gate g sits in bit g % 32 of packed
+  // triple word bw_base[l] + g / 32.
+  uint8_t gate[kMaxGates];
+  uint8_t gate_off[kMaxBxDepth + 3];
+  uint8_t bw_base[kMaxBxDepth + 3];
   // Shift gate (truncation / arithmetic right shift by trunc_s of the k-bit
   // view, added to output 0; 0 = none).  The borrow and wrap bits are the
   // r-atoms of views (trunc_s, 0) and (k, trunc_c), queries trunc_q_lo / _hi.
@@ -84,7 +103,7 @@ struct DevSpec {
 //   carry share      u32  [n]
 //   v_{M-1} share    u64  [p][n]
 //   triples          u64  [n_mults][3][n]          (a, b, c)
-//   Boolean triples  u32  [n_pw][3][n]             (a, b, c), m packed bits each
+//   Boolean triples  u32  [n_bw][3][n]             (a, b, c), one bit per AND gate
 //   shift gate       u64  [3][n] ((r mod 2^k) >> s share, daBit additive shares lo, hi),
 //                    u32  [n] (daBit XOR shares, bits 0 and 1)
 //   query t          uint4 root[n], uint4 cw[L_t][n][4] (per child: seed CW | t CW |
@@ -135,7 +154,7 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_carry = o; o = align256(o + 4 * n);
   L.off_vlast = o; o = align256(o + 8ull * s.p * n);
   L.off_trip = o; o = align256(o + 24ull * s.n_mults * n);
-  L.off_btrip = o; o = align256(o + 12ull * s.n_pw * n);
+  L.off_btrip = o; o = align256(o + 12ull * s.n_bw * n);
   const uint64_t tr = s.trunc_s ? 1 : 0;
   L.off_trunc = o; o = align256(o + 24ull * tr * n);
   L.off_trunc_rho = o; o = align256(o + 4ull * tr * n);
@@ -153,7 +172,7 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
-  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_pw + (s.trunc_s ? 28 : 0);
+  uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_bw + (s.trunc_s ? 28 : 0);
   for (uint32_t t = 0; t < s.T; ++t) b += query_key_bytes(s.q_f[t]);
   if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p);
   return b;
@@ -175,7 +194,7 @@ inline uint64_t aes_per_elem(const DevSpec &s) {
 // (2 x arity x V); the leaf needs both parties' conversions (2V).  A one-bit
 // first digit has arity 2.
 inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
-  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_pw +
+  uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_bw +
                (s.trunc_s ? 5 : 0);
   for (uint32_t t = 0; t < s.T; ++t) {
     const uint32_t lv = key_levels(s.q_f[t]);

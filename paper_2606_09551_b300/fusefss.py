@@ -36,13 +36,22 @@ class PredDesc(C.Structure):
     _fields_ = [("f", C.c_uint32), ("negate", C.c_uint32), ("c", C.c_uint64), ("gamma", C.c_uint64)]
 
 
+class BxNode(C.Structure):
+    _fields_ = [("op", C.c_uint32), ("a", C.c_uint32), ("b", C.c_uint32), ("pred", PredDesc)]
+
+
+_BX_OPS = {"pred": 0, "const": 1, "not": 2, "xor": 3, "and": 4, "or": 5}
+
+
 class SpecDesc(C.Structure):
     _fields_ = [("k", C.c_uint32), ("frac_bits", C.c_uint32), ("m", C.c_uint32), ("degree", C.c_uint32),
                 ("n_out", C.c_uint32), ("partition_bits", C.c_uint32),
                 ("alpha", C.POINTER(C.c_uint64)), ("coeff", C.POINTER(C.c_uint64)),
                 ("n_pred", C.c_uint32), ("preds", C.POINTER(PredDesc)), ("xhat_basis", C.c_uint32),
                 ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc)),
-                ("trunc_shift", C.c_uint32), ("trunc_signed", C.c_uint32)]
+                ("trunc_shift", C.c_uint32), ("trunc_signed", C.c_uint32),
+                ("n_bx_nodes", C.c_uint32), ("bx_nodes", C.POINTER(BxNode)),
+                ("piecewise_root", C.POINTER(C.c_uint32))]
 
 
 class Shape(C.Structure):
@@ -51,7 +60,8 @@ class Shape(C.Structure):
                 ("n_bool", C.c_uint32), ("n_views", C.c_uint32),
                 ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
                 ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64),
-                ("n_piecewise", C.c_uint32), ("trunc_shift", C.c_uint32)]
+                ("n_piecewise", C.c_uint32), ("trunc_shift", C.c_uint32),
+                ("bx_rounds", C.c_uint32), ("bx_words", C.c_uint32)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -204,16 +214,28 @@ class CompiledSpec:
         for i, q in enumerate(spec.preds):
             preds[i] = PredDesc(q.f, q.negate, q.c, q.gamma)
         # piecewise outputs: spec.piecewise[j][i] -> flat index i * n_piecewise + j
+        # (a predicate, or with formula nodes the root node index)
         npw = len(spec.piecewise)
+        nbx = len(spec.bx_nodes)
         pw = (PredDesc * max(npw * spec.m, 1))()
+        roots = (C.c_uint32 * max(npw * spec.m, 1))()
+        nodes = (BxNode * max(nbx, 1))()
         for j, out in enumerate(spec.piecewise):
             for i, q in enumerate(out):
-                pw[i * npw + j] = PredDesc(q.f, q.negate, q.c, q.gamma)
-        self._keep = (alpha, coeff, preds, pw)
+                if nbx:
+                    roots[i * npw + j] = int(q)
+                else:
+                    pw[i * npw + j] = PredDesc(q.f, q.negate, q.c, q.gamma)
+        for v, nd in enumerate(spec.bx_nodes):
+            q = nd.pred
+            op = _BX_OPS[nd.op] if isinstance(nd.op, str) else int(nd.op)   # ints pass through
+            nodes[v] = BxNode(op, nd.a, nd.b,
+                              PredDesc(q.f, q.negate, q.c, q.gamma) if q is not None else PredDesc(0, 0, 0, 0))
+        self._keep = (alpha, coeff, preds, pw, roots, nodes)
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
                      len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw,
-                     spec.trunc_shift, int(spec.trunc_signed))
+                     spec.trunc_shift, int(spec.trunc_signed), nbx, nodes, roots)
         h = vp()
         _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
         self.h = h

@@ -32,7 +32,7 @@ def offsets(ospec: O.Spec, n: int):
     off["carry"] = o; o = _a256(o + 4 * n)
     off["vlast"] = o; o = _a256(o + 8 * ospec.p * n)
     off["trip"] = o; o = _a256(o + 24 * ospec.n_mults * n)
-    off["btrip"] = o; o = _a256(o + 12 * ospec.n_pw * n)
+    off["btrip"] = o; o = _a256(o + 12 * ospec.n_bw * n)
     tr = 1 if ospec.trunc_s else 0
     off["trunc"] = o; o = _a256(o + 24 * tr * n)
     off["trunc_rho"] = o; o = _a256(o + 4 * tr * n)
@@ -99,9 +99,9 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
     out["ta"] = np.array([trip[(mi * 3 + 0) * n + e] for mi in range(nm)], np.uint64)
     out["tb"] = np.array([trip[(mi * 3 + 1) * n + e] for mi in range(nm)], np.uint64)
     out["tc"] = np.array([trip[(mi * 3 + 2) * n + e] for mi in range(nm)], np.uint64)
-    bt = _u32(buf, off["btrip"], 3 * ospec.n_pw * n)
+    bt = _u32(buf, off["btrip"], 3 * ospec.n_bw * n)
     for name, w in (("ba", 0), ("bb", 1), ("bc", 2)):
-        out[name] = np.array([bt[(j * 3 + w) * n + e] for j in range(ospec.n_pw)], np.uint32)
+        out[name] = np.array([bt[(j * 3 + w) * n + e] for j in range(ospec.n_bw)], np.uint32)
     if ospec.trunc_s:
         tt = _u64(buf, off["trunc"], 3 * n)
         out.update(tr_t=int(tt[e]), tr_rho=int(_u32(buf, off["trunc_rho"], n)[e]),
@@ -165,7 +165,7 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
     cy = _u32(buf, off["carry"], n)
     vl = _u64(buf, off["vlast"], p * n)
     tr = _u64(buf, off["trip"], 3 * nm * n)
-    bt = _u32(buf, off["btrip"], 3 * ospec.n_pw * n)
+    bt = _u32(buf, off["btrip"], 3 * ospec.n_bw * n)
     qs = ospec.queries()
     for e in range(n):
         fl = oracle_fields(keys, ospec, e)
@@ -177,7 +177,7 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             tr[(mi * 3 + 0) * n + e] = fl["ta"][mi]
             tr[(mi * 3 + 1) * n + e] = fl["tb"][mi]
             tr[(mi * 3 + 2) * n + e] = fl["tc"][mi]
-        for j in range(ospec.n_pw):
+        for j in range(ospec.n_bw):
             for w, name in enumerate(("ba", "bb", "bc")):
                 bt[(j * 3 + w) * n + e] = fl[name][j]
         if ospec.trunc_s:

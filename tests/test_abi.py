@@ -52,13 +52,17 @@ def _shape_vs_oracle(sp, may_reject=False):
     sh = cs.shape
     assert (sh.T, sh.M, sh.p, sh.n_mults, sh.n_bool) == (o.T, o.M, o.p, o.n_mults, o.n_bool)
     assert sh.n_piecewise == o.n_pw == len(sp.piecewise)
+    assert (sh.bx_rounds, sh.bx_words) == (o.n_bx_rounds, o.n_bw)
+    if sp.piecewise and not sp.bx_nodes:
+        # single predicates: one round of m normalisation ANDs per output, 32 per word
+        assert (sh.bx_rounds, sh.bx_words) == (1, -(-len(sp.piecewise) * sp.m // 32))
     tr = 1 if sp.trunc_shift else 0
     assert sh.trunc_shift == sp.trunc_shift
-    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_pw + tr
+    assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_bw + tr
     qs = o.queries()
     lv = lambda f: (f + 1) // 2          # tree levels: two input bits per level (arity 4)
     # a comparison key: root, 4 child CWs per level, the leaf CW word
-    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_pw + 28 * tr + sum(16 + 64 * lv(f) + 8 for f, _, _ in qs)
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_bw + 28 * tr + sum(16 + 64 * lv(f) + 8 for f, _, _ in qs)
     if o.M > 1:   # a lookup key: root, 4 child CWs and 4 x p value CWs per level, p leaf CWs
         kb += (o.M - 1) * (16 + 64 * lv(o.k) + 32 * lv(o.k) * o.p + 8 * o.p)
     assert sh.key_bytes_per_elem == kb
@@ -95,8 +99,10 @@ def test_random_spec_shapes():
         r = 1 if d > 1 else int(rng.integers(1, 3))
         sp = S.random_spec(rng, k, m, d, r, partition_bits=bool(rng.integers(0, 2)),
                            n_extra=int(rng.integers(0, 6)))
-        if trial % 2:
+        if trial % 4 == 1:
             sp = S.random_piecewise(rng, sp, int(rng.integers(1, 5)))
+        elif trial % 4 == 3:
+            sp = S.random_formulas(rng, sp, int(rng.integers(1, 5)), n_nodes=int(rng.integers(4, 40)))
         if trial % 5 < 2:
             sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), bool(trial % 5)
         _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)), may_reject=True)
@@ -132,3 +138,59 @@ def test_invalid_specs_rejected(bad):
         sp.trunc_shift, sp.trunc_signed = 3, 2
     with pytest.raises(F.FfssError):
         F.CompiledSpec(sp)
+
+
+def _formula_spec(nodes, roots):
+    sp = S.random_spec(np.random.default_rng(1), 8, 2, 1)
+    sp.bx_nodes = nodes
+    sp.piecewise = [roots]
+    return sp
+
+
+@pytest.mark.parametrize("bad", ["child_forward", "child_self", "op", "const_bit", "root", "depth",
+                                 "node_count", "pred_f"])
+def test_invalid_formulas_rejected(bad):
+    """Malformed formula nodes fail to compile (library and oracle alike)."""
+    P = S.PredDesc(8, 0, 100, 0)
+    leaf = S.BxNode("pred", pred=P)
+    nodes, roots = [leaf, S.BxNode("const", 1), S.BxNode("and", 0, 1)], [2, 0]
+    if bad == "child_forward":
+        nodes[2] = S.BxNode("and", 0, 2)
+    elif bad == "child_self":
+        nodes[1] = S.BxNode("not", 1)
+    elif bad == "op":
+        nodes[1] = S.BxNode(9, 0, 0)         # no such node kind
+    elif bad == "const_bit":
+        nodes[1] = S.BxNode("const", 2)
+    elif bad == "root":
+        roots = [3, 0]
+    elif bad == "depth":          # a chain of five ANDs: AND depth 5 > 4
+        nodes = [leaf, S.BxNode("pred", pred=S.PredDesc(4, 1, 3, 1))]
+        for _ in range(5):
+            nodes.append(S.BxNode("and", len(nodes) - 1, 0))
+        roots = [0, len(nodes) - 1]
+    elif bad == "node_count":
+        nodes = [leaf] + [S.BxNode("not", v) for v in range(64)]
+        roots = [0, 1]
+    elif bad == "pred_f":
+        nodes[0] = S.BxNode("pred", pred=S.PredDesc(9, 0, 1, 0))
+    sp = _formula_spec(nodes, roots)
+    if bad != "op":
+        with pytest.raises(ValueError):
+            O.Spec(**sp.descriptor())
+    with pytest.raises(F.FfssError):
+        F.CompiledSpec(sp)
+
+
+def test_formula_shape_rounds_and_words():
+    """Rounds and triple words follow the AND depths: a root of depth 2 takes
+    two rounds of inner gates and a third of normalisation gates."""
+    P0, P1 = S.PredDesc(8, 0, 100, 0), S.PredDesc(3, 1, 5, 1)
+    nodes = [S.BxNode("pred", pred=P0), S.BxNode("pred", pred=P1), S.BxNode("or", 0, 1),
+             S.BxNode("not", 2), S.BxNode("and", 3, 0), S.BxNode("xor", 4, 1)]
+    sp = _formula_spec(nodes, [5, 1])
+    sh = _shape_vs_oracle(sp)
+    # round 1: node 2 (OR) + the normalisation of interval 1 (root 1, depth 0);
+    # round 2: node 4 (AND); round 3: the normalisation of interval 0 (root 5, depth 2)
+    assert (sh.bx_rounds, sh.bx_words) == (3, 3)
+    assert sh.comm_bytes_per_elem == 8 + 16 * 1 + 8 * 3

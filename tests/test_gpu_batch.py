@@ -32,8 +32,10 @@ def _mixed_calls():
              S.recip16(), S.gelu8().variant(True),
              S.random_piecewise(rng, S.gelu4(), 3),
              S.random_piecewise(rng, S.random_spec(rng, 16, 7, 1, 2, n_extra=1, name="r2d1b"), 2),
-             S.trunc(32, 12, True), S.trunc(20, 5, False)]
-    sizes = [5000, 1777, 1, 300, 64, 999, 33, 257, 1536, 2222, 1111, 700, 3333, 129]
+             S.trunc(32, 12, True), S.trunc(20, 5, False),
+             S.random_formulas(rng, S.gelu4(), 2),
+             S.deep_formula(S.random_spec(rng, 16, 5, 1, 1, n_extra=0, name="deep"))]
+    sizes = [5000, 1777, 1, 300, 64, 999, 33, 257, 1536, 2222, 1111, 700, 3333, 129, 1500, 801]
     return [(sp, I.uniform_x(n, sp.k, 100 + i), 7 + i) for i, (sp, n) in enumerate(zip(specs, sizes))]
 
 

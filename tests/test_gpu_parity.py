@@ -77,6 +77,12 @@ def _specs():
     pw = [S.random_piecewise(rng, S.gelu4(), 2), S.random_piecewise(rng, out[3], 3),
           S.random_piecewise(rng, out[4], 4), S.random_piecewise(rng, out[8], 1).variant(True),
           S.random_piecewise(rng, out[6], 2)]
+    # piecewise Boolean formulas (NOT / XOR / AND / OR over predicates, AND
+    # depth up to 4: up to five exchange rounds)
+    bx = [S.random_formulas(rng, S.gelu4(), 2), S.random_formulas(rng, out[3], 3, n_nodes=40),
+          S.random_formulas(rng, out[4], 4, n_nodes=30), S.random_formulas(rng, out[8], 1).variant(True)]
+    bx.append(dataclasses.replace(bx[1], name=bx[1].name + "_ars5", trunc_shift=5, trunc_signed=True))
+    bx.append(S.deep_formula(out[3]))
     # shift gates (truncation / ARS), alone and added to a polynomial output
     tr = [S.trunc(32, 12, True), S.trunc(24, 16, False), S.trunc(16, 1, True),
           dataclasses.replace(S.gelu4(), name="gelu4_ars4", trunc_shift=4, trunc_signed=True),
@@ -91,7 +97,7 @@ def _specs():
                            partition_bits=False,
                            preds=[S.PredDesc(50, 0, 1 << 49, 1), S.PredDesc(50, 12345, (1 << 49) + 77, 0),
                                   S.PredDesc(37, 999, 5 << 30, 1)])]
-    return out + pw + tr + wide
+    return out + pw + bx + tr + wide
 
 
 SPECS = _specs()
@@ -119,7 +125,7 @@ def test_keygen_and_gate_bit_exact(ctx, sp):
     yp, zp = osp.plain_eval(x)
     assert np.array_equal(g["y"], yp) and np.array_equal(g["z"], zp)
     mults = 0 if sp.xhat_basis else sp.degree * sp.n_out
-    assert list(g["comm"]) == [n * (8 + 16 * mults + 8 * len(sp.piecewise) + (1 if sp.trunc_shift else 0))] * 2
+    assert list(g["comm"]) == [n * (8 + 16 * mults + 8 * osp.n_bw + (1 if sp.trunc_shift else 0))] * 2
 
 
 def test_gpu_eval_of_oracle_keys(ctx):
