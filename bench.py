@@ -54,7 +54,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.609785088e9 + 4.653056e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.254390e9 + 5.161984e6) / 65536}
 
 
 def parse():
@@ -533,7 +533,8 @@ def run_ours(args, rank, world, local_rank):
     key_bytes_launch = 2 * sh.key_bytes_per_elem * dom.n
     lop3_rate, _ = F.microbench(ctx, 0, 4096)
     aes_rates = {name: F.microbench(ctx, v + 1, 2048)[0]
-                 for v, name in enumerate(("shift_mask", "permute_mad", "permute_mad_ptx", "permute_interleaved"))}
+                 for v, name in enumerate(("shift_mask", "permute_mad", "permute_mad_ptx", "permute_interleaved",
+                                           "dealer_4block_calls"))}
     dom_s = per_op_ms[dom.name] * 1e-3
     roof = {
         "bound": "alu", "kernel": f"gate_kernel ({dom.name}: {dom.spec.name}, {dom.n} elements)",

@@ -482,7 +482,9 @@ int ffss_layernorm_destroy(ffss_layernorm *ln);
  * chained blocks per thread, one 512-thread CTA per SM), table addresses by
  * 1: shift plus mask; 2, 3: byte permute plus multiply-add (C, PTX mad);
  * 4: one byte permute into two tables interleaved per 256-byte entry, the
- * form the FSS kernels use.
+ * form the FSS kernels use.  which = 5: the dealer's shape, four independent
+ * chains per thread through the 4-block call (form 4), one CTA of the
+ * dealer's size per SM; blocks/s.
  * Synchronizes the device; *ms (may be NULL) receives the kernel time. */
 int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms);
 

@@ -217,65 +217,33 @@ FFSS_CORE uint64_t view(uint64_t u, uint32_t f, uint64_t c) {
 // first, the first digit taking one bit when k is odd.  Expansion of child c
 // of seed s: blk = H(s, c); control bit t = bit 0; bit payload = bit 1; next
 // seed = blk with bits 0, 1 cleared; vector payload V blocks H(s, 4 + cV + q).
-// Each level stores a correction word per child: the seed CW with the t CW
-// in bit 0 and, for the bit payload, the value CW in bit 1.  A party with
-// t = 1 XORs child c's CWs in.  Leaf: bit 2 of the seed (bit payload) or
-// H(s, 4 + q), plus t times the leaf CW.
-//
-// A key is addressed per element: root = its root seed; cw = its four child
-// CWs of level 0, level i at cw + i * cs; vcw = its value CWs of level 0
-// (child c, word q at c * P + q), level i at vcw + i * vs; leaf = its leaf
-// CW(s), word q at leaf + q * n.
+// Each level stores a correction word per child, row (level * 4 + c): the
+// seed CW with the t CW in bit 0 and, for the bit payload, the value CW in
+// bit 1.  A party with t = 1 XORs child c's CWs in.  Leaf: bit 2 of the seed
+// (bit payload) or H(s, 4 + q), plus t times the leaf CW.
 // ---------------------------------------------------------------------------
 
 FFSS_CORE uint32_t dcf_levels(uint32_t k) { return (k + 1) / 2; }
 
-// The P value CWs of one child: 16-byte loads when P is even (the run then
-// starts on a 16-byte boundary).
-template <int P>
-FFSS_CORE void load_words(const uint64_t *p, uint64_t (&v)[P]) {
-  if constexpr (P % 2 == 0) {
-#pragma unroll
-    for (int h = 0; h < P / 2; ++h) {
-      const ulonglong2 w = reinterpret_cast<const ulonglong2 *>(p)[h];
-      v[2 * h] = w.x;
-      v[2 * h + 1] = w.y;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = p[q];
-  }
-}
-
-template <int P>
-FFSS_CORE void store_words(uint64_t *p, const uint64_t (&v)[P]) {
-  if constexpr (P % 2 == 0) {
-#pragma unroll
-    for (int h = 0; h < P / 2; ++h) reinterpret_cast<ulonglong2 *>(p)[h] = make_ulonglong2(v[2 * h], v[2 * h + 1]);
-  } else {
-#pragma unroll
-    for (int q = 0; q < P; ++q) p[q] = v[q];
-  }
-}
-
 // Bit payload: returns the XOR share of 1[u < alpha].
+// root: uint4 root[n]; child CW of level i at root[(1 + 4 i + c) n]; leaf: the leaf CW bit.
 template <class AES>
-FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 *root, const uint4 *cw,
-                                uint64_t cs, uint64_t leaf, const AES &aes) {
+FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 *root, uint64_t n,
+                                uint64_t leaf, const AES &aes) {
   const uint32_t nlev = dcf_levels(k);
   uint4 s = root[0];
   uint32_t t = b, v = 0;
   for (uint32_t i = 0; i < nlev; ++i) {
     const uint32_t c = uint32_t(u >> (2 * (nlev - 1 - i))) & 3u;
-    const uint4 w = cw[i * cs + c];
+    const uint4 cw = root[(1 + 4 * uint64_t(i) + c) * n];
     const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
-    v ^= (blk.x >> 1) ^ (tm & (w.x >> 1));
-    const uint32_t tn = (blk.x ^ (tm & w.x)) & 1u;
-    s.x = (blk.x ^ (tm & w.x)) & ~3u;
-    s.y = blk.y ^ (tm & w.y);
-    s.z = blk.z ^ (tm & w.z);
-    s.w = blk.w ^ (tm & w.w);
+    v ^= (blk.x >> 1) ^ (tm & (cw.x >> 1));
+    const uint32_t tn = (blk.x ^ (tm & cw.x)) & 1u;
+    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
+    s.y = blk.y ^ (tm & cw.y);
+    s.z = blk.z ^ (tm & cw.z);
+    s.w = blk.w ^ (tm & cw.w);
     t = tn;
   }
   v ^= (s.x >> 2) ^ (t & uint32_t(leaf));
@@ -284,19 +252,21 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 
 
 // Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^c) + t VCW[c]) + leaf
 // term into acc (the caller applies the party sign (-1)^b once).
+// vcw: u64 [levels][4][P][n]; leaf: u64 [P][n].
 template <int P, class AES>
-FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint4 *cw,
-                                uint64_t cs, const uint64_t *vcw, uint64_t vs, const uint64_t *leaf,
-                                uint64_t n, uint64_t *acc, const AES &aes) {
+FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint64_t *vcw,
+                                const uint64_t *leaf, uint64_t n, uint64_t *acc, const AES &aes) {
   constexpr int V = (P + 1) / 2;
   const uint32_t nlev = dcf_levels(k);
   uint4 s = root[0];
   uint32_t t = b;
   for (uint32_t i = 0; i < nlev; ++i) {
     const uint32_t c = (u >> (2 * (nlev - 1 - i))) & 3u;
-    const uint4 w = cw[i * cs + c];
+    const uint64_t row = 4 * uint64_t(i) + c;
+    const uint4 cw = root[(1 + row) * n];
     uint64_t vc[P];
-    load_words<P>(vcw + i * vs + c * P, vc);
+#pragma unroll
+    for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
     const uint4 blk = mmo(s, c, aes);
     uint64_t conv[2 * V];
 #pragma unroll
@@ -309,11 +279,11 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
 #pragma unroll
     for (int q = 0; q < P; ++q) acc[q] += conv[q] + (vc[q] & tm64);
     const uint32_t tm = 0u - t;
-    const uint32_t tn = (blk.x ^ (tm & w.x)) & 1u;
-    s.x = (blk.x ^ (tm & w.x)) & ~3u;
-    s.y = blk.y ^ (tm & w.y);
-    s.z = blk.z ^ (tm & w.z);
-    s.w = blk.w ^ (tm & w.w);
+    const uint32_t tn = (blk.x ^ (tm & cw.x)) & 1u;
+    s.x = (blk.x ^ (tm & cw.x)) & ~3u;
+    s.y = blk.y ^ (tm & cw.y);
+    s.z = blk.z ^ (tm & cw.z);
+    s.w = blk.w ^ (tm & cw.w);
     t = tn;
   }
   uint64_t conv[2 * V];
@@ -349,13 +319,13 @@ FFSS_CORE void expand_children(uint4 s0, uint4 s1, uint32_t nc, uint4 (&ch)[2][4
 
 // Bit-payload DCF Gen of arity 4 for 1[u < alpha] on k-bit u, both parties.
 // keep4(i0) returns the path child's random block 0 of levels i0 .. i0 + 3
-// (its seed CW, and bit 1 its value CW).  Hands each child CW to
-// sink.put(c, cw) and closes level i with sink.level_done(i) (the CWs are the
-// same in both keys); writes the leaf CW bit into both keys.  The caller
-// stores the roots s0, s1.
-template <class AES4, class KEEP4, class SINK>
-FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, const SINK &sink, uint64_t *leaf0,
-                           uint64_t *leaf1, const AES4 &aes4, const KEEP4 &keep4) {
+// (its seed CW, and bit 1 its value CW).  Writes root and child CWs (rows
+// 1 + 4 i + c) and the leaf CW bit into both keys.
+template <class AES4, class KEEP4>
+FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
+                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
+  q0[0] = s0;
+  q1[0] = s1;
   const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1, wb = 0;
   Blk4 R4;
@@ -385,9 +355,9 @@ FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, const
           ka1 = ch[1][c];
         }
       }
-      sink.put(c, cw);
+      q0[(1 + 4 * uint64_t(i) + c) * n] = cw;
+      q1[(1 + 4 * uint64_t(i) + c) * n] = cw;
     }
-    sink.level_done(i);
     // the path continues through child a
     wb = (wb ^ (ka0.x >> 1) ^ (ka1.x >> 1) ^ (ck.x >> 1)) & 1u;
     uint4 sk = ck;
@@ -424,13 +394,16 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
 // Vector-payload DCF Gen of arity 4 for beta * 1[u < alpha] on k-bit u
 // (k <= 32), both parties.  keep4(i): the path child's random blocks of
 // level i; block 0 its seed CW, blocks 1..V its value CWs (p little-endian
-// uint64).  Hands each child's seed CW and value CWs to sink.put(c, cw, vc)
-// and closes level i with sink.level_done(i); writes the leaf CWs (word q at
-// leaf + q * n) into both keys.  The caller stores the roots s0, s1.
-template <int P, class AES4, class KEEP4, class SINK>
-FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1, const SINK &sink,
-                           uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
+// uint64).  Writes root and
+// child CWs (rows 1 + 4 i + c), value CWs vcw [levels][4][P][n] and the
+// leaf CWs [P][n].
+template <int P, class AES4, class KEEP4>
+FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
+                           uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t *leaf0,
+                           uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   constexpr uint32_t V = (P + 1) / 2;
+  l0[0] = s0;
+  l1[0] = s1;
   const uint32_t nlev = dcf_levels(k);
   uint32_t t0 = 0, t1 = 1;
   uint64_t W[P];
@@ -506,10 +479,16 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
             ka1 = c1;
           }
         }
-        sink.put(c, cw, vc);
+        const uint64_t row = 4 * uint64_t(i) + c;
+        l0[(1 + row) * n] = cw;
+        l1[(1 + row) * n] = cw;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          vcw0[(row * P + q) * n] = vc[q];
+          vcw1[(row * P + q) * n] = vc[q];
+        }
       }
     }
-    sink.level_done(i);
     // the path continues through child a
 #pragma unroll
     for (int q = 0; q < P; ++q) W[q] = W[q] + ca0[q] - ca1[q] + (neg ? 0ull - vk[q] : vk[q]);

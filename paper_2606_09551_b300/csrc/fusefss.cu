@@ -484,8 +484,7 @@ static size_t spec_smem() { return (sizeof(DevSpec) + 15) & ~size_t(15); }
 
 template <int P>
 static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t st) {
-  const size_t smem = keygen_stage_off() + size_t(kKeygenThreads / 32) * kStageBytes;
-  static_assert(44 * 4 <= 256, "PRG round keys fit their slot");
+  const size_t smem = kTabBytes + spec_smem() + 44 * 4;
   static std::once_flag once;
   int rc = FFSS_OK;
   std::call_once(once, [&] { rc = set_smem(keygen_kernel<P>, smem); });
@@ -616,8 +615,8 @@ static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
   memset(&sc, 0, sizeof(sc));
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
   std::vector<std::pair<uint64_t, uint32_t>> items;
-  for (uint32_t t = 0; t < S.T; ++t) items.push_back({S.q_f[t], t});
-  for (uint32_t j = 0; j + 1 < S.M; ++j) items.push_back({uint64_t(S.k) * (1 + S.V) + S.V, S.T + j});
+  for (uint32_t t = 0; t < S.T; ++t) items.push_back({key_levels(S.q_f[t]), t});
+  for (uint32_t j = 0; j + 1 < S.M; ++j) items.push_back({uint64_t(key_levels(S.k)) * (1 + S.V) + S.V, S.T + j});
   std::stable_sort(items.begin(), items.end(), [](auto &a, auto &b) { return a.first > b.first; });
   std::vector<uint64_t> load(slots, 0);
   std::vector<std::vector<uint32_t>> own(slots);
@@ -1014,8 +1013,12 @@ static Sched noalloc_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load)
   uint32_t id[kMaxItems];
   uint64_t cost[kMaxItems];
   uint32_t n = 0;
-  for (uint32_t t = 0; t < S.T; ++t) { id[n] = t; cost[n] = S.q_f[t]; ++n; }
-  for (uint32_t j = 0; j + 1 < S.M; ++j) { id[n] = S.T + j; cost[n] = uint64_t(S.k) * (1 + S.V) + S.V; ++n; }
+  for (uint32_t t = 0; t < S.T; ++t) { id[n] = t; cost[n] = key_levels(S.q_f[t]); ++n; }
+  for (uint32_t j = 0; j + 1 < S.M; ++j) {
+    id[n] = S.T + j;
+    cost[n] = uint64_t(key_levels(S.k)) * (1 + S.V) + S.V;
+    ++n;
+  }
   for (uint32_t a = 1; a < n; ++a)   // stable insertion sort, costliest first
     for (uint32_t b = a; b > 0 && cost[b] > cost[b - 1]; --b) {
       std::swap(cost[b], cost[b - 1]);
@@ -1189,8 +1192,20 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
     kern<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters;
+  } else if (which == 5) {
+    const int blocks = ctx->sm_count, threads = int(kKeygenThreads);
+    const size_t smem = kTabBytes;
+    static std::once_flag once5;
+    std::call_once(once5, [&] { rc = set_smem(mb_aes4_kernel, smem); });
+    if (rc) return rc;
+    CUDA_TRY(cudaMalloc(&out, sizeof(uint4) * blocks * threads));
+    mb_aes4_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), 4);
+    CUDA_TRY(cudaEventRecord(a));
+    mb_aes4_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
+    CUDA_TRY(cudaEventRecord(b));
+    work = double(blocks) * threads * iters * 4.0;
   } else {
-    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3) or 1..4 (AES variants)");
+    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3), 1..4 (AES variants) or 5 (4-block calls)");
   }
   cudaError_t e = cudaEventSynchronize(b);
   float t = 0;

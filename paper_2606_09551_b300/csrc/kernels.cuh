@@ -120,10 +120,10 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // the walk at the cost of the bare AES chain plus a few operations per level;
 // inlined into the fused gate the compiler emitted about 40 % more
 // instructions per level.  One call per walk.
-__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, const uint4 *cw,
-                                          uint64_t cs, uint64_t leaf, const char *tab, uint32_t lane4) {
+__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, uint64_t n,
+                                          uint64_t leaf, const char *tab, uint32_t lane4) {
   const AesDcfInline aes{Tab{tab, lane4}};
-  return dcf_bit_eval(b, f, u, root, cw, cs, leaf, aes);
+  return dcf_bit_eval(b, f, u, root, n, leaf, aes);
 }
 
 // One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
@@ -133,9 +133,8 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   const char *q = kb + L.off_q[t];
   const uint32_t f = S.q_f[t];
   const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
-  const uint4 *cw = reinterpret_cast<const uint4 *>(q + qkey_cw_off(L.n)) + 4 * e;
-  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + qkey_leaf_off(f, L.n))[e];
-  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, cw, 4 * L.n, leaf, aes.tb.base, aes.tb.lane4);
+  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + 16ull * (1 + 4ull * key_levels(f)) * L.n)[e];
+  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
 }
 
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
@@ -145,13 +144,11 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
                                          const AesDcfInline &aes) {
   const uint32_t k = S.k;
   const char *l = kb + L.off_l[j];
-  const uint64_t n = L.n;
-  const uint4 *root = reinterpret_cast<const uint4 *>(l + lkey_root_off(k, P, n)) + e;
-  const uint4 *cw = reinterpret_cast<const uint4 *>(l + lkey_cw_off(k, P, n)) + 4 * e;
-  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l) + 4 * P * e;
-  const uint64_t *leaf = reinterpret_cast<const uint64_t *>(l + lkey_leaf_off(k, P, n)) + e;
-  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, cw, 4 * n, vcw, 4 * P * n, leaf, n, acc,
-                      aes);   // lookups: k <= 32
+  const uint64_t lv = key_levels(k);
+  const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + 4 * lv) * L.n) + e;
+  const uint64_t *leaf = vcw + 4 * lv * P * L.n;
+  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -738,85 +735,11 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
 // GPU dealer
 // ---------------------------------------------------------------------------
 
-// Per-warp shared-memory staging of one tree level's child records (the
-// four children of each of the warp's 32 consecutive elements).  In the
-// element-major key layout a lane's records lie 64 (seed CWs) or 32p (value
-// CWs) bytes apart, so a store from each lane would scatter one instruction
-// over 16 lines; the staged copy writes both keys in contiguous 512-byte
-// runs instead.  All 32 lanes take part (in a ragged last group the spare
-// lanes redo the last element); lanes 0 .. nact - 1 hold real elements.
-constexpr uint32_t kStageBytes = 32 * 4 * 16 + 32 * 4 * kMaxP * 8;   // per warp
-
-template <int P>
-struct LevelStage {
-  static constexpr int PP = P > 0 ? P : 1;
-  uint4 *scw;            // [32 lanes][4 children]
-  uint64_t *svc;         // [32][4][P]
-  uint4 *cw0, *cw1;      // level-0 child CWs of the warp's first element, both keys
-  uint64_t *vc0, *vc1;   // level-0 value CWs of the warp's first element, both keys
-  uint64_t cs, vs;       // per-level strides (uint4, u64)
-  uint32_t lane, nact;
-  __device__ __forceinline__ void put(uint32_t c, uint4 cw) const { scw[lane * 4 + c] = cw; }
-  __device__ __forceinline__ void put(uint32_t c, uint4 cw, const uint64_t (&vc)[PP]) const {
-    scw[lane * 4 + c] = cw;
-    store_words<P>(svc + (lane * 4 + c) * P, vc);
-  }
-  __device__ __forceinline__ void level_done(uint32_t i) const {
-    __syncwarp();
-#pragma unroll
-    for (uint32_t r = 0; r < 4; ++r) {
-      const uint32_t j = 32 * r + lane;          // element j / 4, child j % 4
-      if (j < 4 * nact) {
-        const uint4 v = scw[j];
-        cw0[i * cs + j] = v;
-        cw1[i * cs + j] = v;
-      }
-    }
-    if constexpr (P > 0) {
-      if constexpr (P % 2 == 0) {               // 16-byte words: 64 P per level
-        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(svc);
-        ulonglong2 *d0 = reinterpret_cast<ulonglong2 *>(vc0 + i * vs);
-        ulonglong2 *d1 = reinterpret_cast<ulonglong2 *>(vc1 + i * vs);
-#pragma unroll
-        for (uint32_t r = 0; r < 2 * P; ++r) {
-          const uint32_t j = 32 * r + lane;
-          if (j < 2 * P * nact) {
-            const ulonglong2 v = src[j];
-            d0[j] = v;
-            d1[j] = v;
-          }
-        }
-      } else {                                  // 8-byte words: 128 P per level
-#pragma unroll
-        for (uint32_t r = 0; r < 4 * P; ++r) {
-          const uint32_t j = 32 * r + lane;
-          if (j < 4 * P * nact) {
-            const uint64_t v = svc[j];
-            vc0[i * vs + j] = v;
-            vc1[i * vs + j] = v;
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
-};
-
-// The dealer's dynamic shared memory: T-tables | spec | PRG round keys (256
-// bytes) | one staging area per warp.
-extern __shared__ __align__(16) unsigned char stage_smem[];
-__host__ __device__ constexpr size_t keygen_stage_off() {
-  return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 256;
-}
-__device__ __forceinline__ unsigned char *warp_stage(unsigned char *smem) {
-  return smem + keygen_stage_off() + (threadIdx.x >> 5) * kStageBytes;
-}
-
 // Dealer work items, each compiled out of line (its own register
 // allocation): one lookup key or one comparison key of 32 elements.
 template <int P>
 __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
-                                            uint64_t e, uint64_t e0, uint64_t ge, uint64_t r_in, uint32_t item) {
+                                            uint64_t e, uint64_t ge, uint64_t r_in, uint32_t item) {
   const KeyLayout &L = A.L;
   const uint64_t n = A.n;
   const AesDcfCall4 rkd{tb};
@@ -838,21 +761,16 @@ __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &
     return mmo4(base, 4u * lvl, base, 4u * lvl + 1, base, 4u * lvl + 2, base, 4u * lvl + 3, rkd);
   };
   char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
-  const uint64_t ro = lkey_root_off(S.k, P, n), co = lkey_cw_off(S.k, P, n), lo = lkey_leaf_off(S.k, P, n);
-  reinterpret_cast<uint4 *>(l0 + ro)[e] = s0;
-  reinterpret_cast<uint4 *>(l1 + ro)[e] = s1;
-  const uint32_t lane = threadIdx.x & 31u;
-  unsigned char *st = warp_stage(stage_smem);
-  const LevelStage<P> sink{reinterpret_cast<uint4 *>(st), reinterpret_cast<uint64_t *>(st + 32 * 4 * 16),
-                           reinterpret_cast<uint4 *>(l0 + co) + 4 * e0, reinterpret_cast<uint4 *>(l1 + co) + 4 * e0,
-                           reinterpret_cast<uint64_t *>(l0) + 4 * P * e0, reinterpret_cast<uint64_t *>(l1) + 4 * P * e0,
-                           4 * n, 4 * P * n, lane, uint32_t(min(uint64_t(32), n - e0))};
-  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, sink, reinterpret_cast<uint64_t *>(l0 + lo) + e,
-                 reinterpret_cast<uint64_t *>(l1 + lo) + e, n, rkd, keep4);
+  const uint64_t lv = key_levels(S.k);
+  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
+  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
+  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
+                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
+                 keep4);
 }
 
 __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
-                                           uint64_t e, uint64_t e0, uint64_t ge, uint64_t r_in, uint32_t t) {
+                                           uint64_t e, uint64_t ge, uint64_t r_in, uint32_t t) {
   const KeyLayout &L = A.L;
   const uint64_t n = A.n;
   const AesDcfCall4 rkd{tb};
@@ -870,16 +788,11 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
     return mmo4(base, 4u * lvl0, base, 4u * (lvl0 + 1), base, 4u * (lvl0 + 2), base, 4u * (lvl0 + 3), rkd);
   };
   char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
-  const uint64_t co = qkey_cw_off(n), lo = qkey_leaf_off(f, n);
-  reinterpret_cast<uint4 *>(q0)[e] = s0;
-  reinterpret_cast<uint4 *>(q1)[e] = s1;
-  const uint32_t lane = threadIdx.x & 31u;
-  unsigned char *st = warp_stage(stage_smem);
-  const LevelStage<0> sink{reinterpret_cast<uint4 *>(st), nullptr, reinterpret_cast<uint4 *>(q0 + co) + 4 * e0,
-                           reinterpret_cast<uint4 *>(q1 + co) + 4 * e0, nullptr, nullptr, 4 * n, 0, lane,
-                           uint32_t(min(uint64_t(32), n - e0))};
-  dcf_bit_gen(f, alpha, s0, s1, sink, reinterpret_cast<uint64_t *>(q0 + lo) + e,
-              reinterpret_cast<uint64_t *>(q1 + lo) + e, rkd, keep4);
+  const uint64_t lv = key_levels(f);
+  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
+              reinterpret_cast<uint4 *>(q1) + e,
+              reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
+              reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
 }
 
 // 384 threads per CTA: 168 registers per thread keep a key's running state
@@ -911,11 +824,8 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
   for (uint64_t u = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; u < units;
        u += uint64_t(gridDim.x) * blockDim.x / 32) {
     const uint32_t item = uint32_t(u / groups);
-    // the whole warp stays on one unit (the key items stage their stores per
-    // warp): in a ragged last group the spare lanes redo element n - 1 and
-    // write the same values as its own lane
-    const uint64_t e0 = (u % groups) * 32;
-    const uint64_t e = min(e0 + lane, n - 1);
+    const uint64_t e = (u % groups) * 32 + lane;
+    if (e >= n) continue;
     // AES-128-CTR block of draw `dr`: (draw, element lo, element hi, call id);
     // the counter uses the element's index within the whole call, so a call
     // dealt in chunks gets the same material as in one launch
@@ -925,9 +835,9 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
     };
     const uint64_t r_in = lo64(prg(kDrawRin));
     if (item < n_vec) {
-      gen_lookup_key<P>(A, S, rk_prg, tb, e, e0, ge, r_in, item);
+      gen_lookup_key<P>(A, S, rk_prg, tb, e, ge, r_in, item);
     } else if (item < n_vec + S.T) {
-      gen_query_key(A, S, rk_prg, tb, e, e0, ge, r_in, item - n_vec);
+      gen_query_key(A, S, rk_prg, tb, e, ge, r_in, item - n_vec);
     } else {
       const uint64_t r0 = lo64(prg(kDrawRsh));
       reinterpret_cast<uint64_t *>(A.k0 + L.off_r)[e] = r0;
@@ -1075,6 +985,20 @@ __global__ void __launch_bounds__(512, 1) mb_aes_kernel(const uint32_t *t0, uint
   uint4 s = make_uint4(threadIdx.x, blockIdx.x, 7u, 9u);
   for (uint32_t i = 0; i < iters; ++i) s = aes128v<VAR>(s, RkDcf(), tb);
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// The dealer's AES shape: each thread runs four independent chains through
+// the out-of-line 4-block call, at the dealer's CTA size.
+__global__ void __launch_bounds__(kKeygenThreads, 1) mb_aes4_kernel(const uint32_t *t0, uint4 *out, uint32_t iters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  __syncthreads();
+  const AesDcfCall4 aes4{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
+  Blk4 s{{make_uint4(threadIdx.x, blockIdx.x, 1u, 2u), make_uint4(threadIdx.x, blockIdx.x, 3u, 4u),
+          make_uint4(threadIdx.x, blockIdx.x, 5u, 6u), make_uint4(threadIdx.x, blockIdx.x, 7u, 8u)}};
+  for (uint32_t i = 0; i < iters; ++i) s = aes4(s);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = xor4(xor4(s.v[0], s.v[1]), xor4(s.v[2], s.v[3]));
 }
 
 }  // namespace ffss

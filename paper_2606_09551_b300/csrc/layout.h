@@ -94,11 +94,9 @@ struct DevSpec {
 };
 
 // Byte offsets of one party's key material for n elements.  Every section is
-// 256-byte aligned.  Per-element values are element-minor, so a warp's 32
-// consecutive elements read contiguous 16-byte (roots) or 8-byte (ring
-// values) records; the DCF child records of a level are element-major (the
-// four children of one element side by side), since a walk reads one child
-// of four, chosen by its input.
+// 256-byte aligned; arrays are element-minor so a warp's 32 consecutive
+// elements read contiguous 16-byte (seeds, correction words) or 8-byte (ring
+// values) records, and the dealer writes them in contiguous runs.
 //   r share          u64  [n]
 //   carry share      u32  [n]
 //   v_{M-1} share    u64  [p][n]
@@ -106,9 +104,9 @@ struct DevSpec {
 //   Boolean triples  u32  [n_bw][3][n]             (a, b, c), one bit per AND gate
 //   shift gate       u64  [3][n] ((r mod 2^k) >> s share, daBit additive shares lo, hi),
 //                    u32  [n] (daBit XOR shares, bits 0 and 1)
-//   query t          uint4 root[n], uint4 cw[L_t][n][4] (per child: seed CW | t CW |
+//   query t          uint4 root[n], uint4 cw[L_t][4][n] (per child: seed CW | t CW |
 //                    value CW << 1), u64 leaf[n] (bit 0); L_t = ceil(k_t / 2) levels
-//   lookup key j     u64 vcw[L][n][4][p], uint4 root[n], uint4 cw[L][n][4],
+//   lookup key j     uint4 root[n], uint4 cw[L][4][n], u64 vcw[L][4][p][n],
 //                    u64 leaf[p][n]; L = ceil(k / 2)
 struct KeyLayout {
   uint64_t n;
@@ -127,23 +125,6 @@ FFSS_HD uint32_t key_levels(uint32_t k) { return (k + 1) / 2; }
 FFSS_HD uint64_t query_key_bytes(uint32_t f) { return 16 + 64ull * key_levels(f) + 8; }
 FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p) {
   return 16 + 64ull * key_levels(k) + 32ull * key_levels(k) * p + 8ull * p;
-}
-
-// Sub-arrays of one key section of n elements (byte offsets from the
-// section's 256-aligned start).  Child records are element-major within a
-// level, so a walk that takes child c reads one 16-byte seed CW (one DRAM
-// sector) and one contiguous run of p value CWs, not four rows' sectors.
-//   comparison key: root uint4[n] | seed CWs uint4[L][n][4] | leaf u64[n]
-//   lookup key:     value CWs u64[L][n][4][p] | root uint4[n] |
-//                   seed CWs uint4[L][n][4] | leaf u64[p][n]
-// The value CWs come first so that a level's record (32p bytes) starts on
-// a 32-byte boundary: for p = 4 a child's run is exactly one sector.
-FFSS_HD uint64_t qkey_cw_off(uint64_t n) { return 16 * n; }
-FFSS_HD uint64_t qkey_leaf_off(uint32_t f, uint64_t n) { return 16 * n + 64ull * key_levels(f) * n; }
-FFSS_HD uint64_t lkey_root_off(uint32_t k, uint32_t p, uint64_t n) { return 32ull * key_levels(k) * p * n; }
-FFSS_HD uint64_t lkey_cw_off(uint32_t k, uint32_t p, uint64_t n) { return lkey_root_off(k, p, n) + 16 * n; }
-FFSS_HD uint64_t lkey_leaf_off(uint32_t k, uint32_t p, uint64_t n) {
-  return lkey_cw_off(k, p, n) + 64ull * key_levels(k) * n;
 }
 
 FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {

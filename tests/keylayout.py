@@ -5,10 +5,9 @@ and, through this transform, key material.
 
 DCF keys have arity 4 (two input bits per tree level).  Per comparison key
 of view width f (L = ceil(f/2) levels): root uint4[n], child correction
-words uint4[L][n][4] (seed CW with the t CW in bit 0 and the value CW in bit
-1), the leaf CW u64[n].  Per lookup key (k bits, payload p): value CWs
-u64[L][n][4][p], root uint4[n], child CWs uint4[L][n][4], leaf CWs
-u64[p][n]."""
+words uint4[L][4][n] (seed CW with the t CW in bit 0 and the value CW in bit
+1), the leaf CW u64[n].  Per lookup key (k bits, payload p): root, child
+CWs uint4[L][4][n], value CWs u64[L][4][p][n], leaf CWs u64[p][n]."""
 from __future__ import annotations
 
 import numpy as np
@@ -61,27 +60,18 @@ def _blocks(buf, off, count):
     return buf[off: off + 16 * count].reshape(count, 16)
 
 
-def _sub(n, k, p):
-    """Byte offsets of root, child CWs, value CWs and leaf within a key section."""
-    lv = _lv(k)
-    if p == 0:
-        return dict(root=0, cw=16 * n, vcw=None, leaf=16 * n + 64 * lv * n)
-    ro = 32 * lv * p * n
-    return dict(root=ro, cw=ro + 16 * n, vcw=0, leaf=ro + 16 * n + 64 * lv * n)
-
-
 def _gpu_key(buf, base, n, e, k, p):
     lv = _lv(k)
-    so = _sub(n, k, p)
-    root = _blocks(buf, base + so["root"], n)[e].copy()
-    cwb = _blocks(buf, base + so["cw"], 4 * lv * n)
-    cw = np.stack([cwb[(i * n + e) * 4 + c] for i in range(lv) for c in range(4)]).reshape(lv, 4, 16)
+    blk = _blocks(buf, base, (1 + 4 * lv) * n)
+    root = blk[e].copy()
+    cw = np.stack([blk[(1 + row) * n + e] for row in range(4 * lv)]).reshape(lv, 4, 16)
+    tail = base + 16 * (1 + 4 * lv) * n
     if p == 0:
-        return dict(root=root, cw=cw, leaf_bit=int(_u64(buf, base + so["leaf"], n)[e]) & 1)
-    v = _u64(buf, base + so["vcw"], 4 * lv * p * n)
-    vcw = np.array([[[v[((i * n + e) * 4 + c) * p + q] for q in range(p)] for c in range(4)] for i in range(lv)],
+        return dict(root=root, cw=cw, leaf_bit=int(_u64(buf, tail, n)[e]) & 1)
+    v = _u64(buf, tail, 4 * lv * p * n)
+    vcw = np.array([[[v[((i * 4 + c) * p + q) * n + e] for q in range(p)] for c in range(4)] for i in range(lv)],
                    np.uint64)
-    lf = _u64(buf, base + so["leaf"], p * n)
+    lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
     leaf = np.array([lf[q * n + e] for q in range(p)], np.uint64)
     return dict(root=root, cw=cw, vcw=vcw, leaf=leaf)
 
@@ -186,27 +176,24 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             _u32(buf, off["trunc_rho"], n)[e] = fl["tr_rho"]
         for t, (f, c, pr) in enumerate(qs):
             lv = _lv(f)
-            so = _sub(n, f, 0)
-            base = off["q"][t]
-            _blocks(buf, base + so["root"], n)[e] = fl["q"][t]["root"]
-            cwb = _blocks(buf, base + so["cw"], 4 * lv * n)
-            for i in range(lv):
-                for c in range(4):
-                    cwb[(i * n + e) * 4 + c] = fl["q"][t]["cw"][i, c]
-            _u64(buf, base + so["leaf"], n)[e] = fl["q"][t]["leaf_bit"]
+            blk = _blocks(buf, off["q"][t], (1 + 4 * lv) * n)
+            blk[e] = fl["q"][t]["root"]
+            for row in range(4 * lv):
+                blk[(1 + row) * n + e] = fl["q"][t]["cw"][row // 4, row % 4]
+            _u64(buf, off["q"][t] + 16 * (1 + 4 * lv) * n, n)[e] = fl["q"][t]["leaf_bit"]
         for j in range(ospec.M - 1):
             lv = _lv(k)
-            so = _sub(n, k, p)
-            base = off["l"][j]
-            _blocks(buf, base + so["root"], n)[e] = fl["l"][j]["root"]
-            cwb = _blocks(buf, base + so["cw"], 4 * lv * n)
-            v = _u64(buf, base + so["vcw"], 4 * lv * p * n)
+            blk = _blocks(buf, off["l"][j], (1 + 4 * lv) * n)
+            blk[e] = fl["l"][j]["root"]
+            for row in range(4 * lv):
+                blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // 4, row % 4]
+            tail = off["l"][j] + 16 * (1 + 4 * lv) * n
+            v = _u64(buf, tail, 4 * lv * p * n)
             for i in range(lv):
                 for c in range(4):
-                    cwb[(i * n + e) * 4 + c] = fl["l"][j]["cw"][i, c]
                     for q in range(p):
-                        v[((i * n + e) * 4 + c) * p + q] = fl["l"][j]["vcw"][i, c, q]
-            lf = _u64(buf, base + so["leaf"], p * n)
+                        v[((i * 4 + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
+            lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
             for q in range(p):
                 lf[q * n + e] = fl["l"][j]["leaf"][q]
     return buf
