@@ -158,9 +158,7 @@ __device__ __forceinline__ uint32_t prim_share(const DevSpec &S, uint32_t atoms,
 }
 
 // Shares of the global Boolean outputs; constants and negations by party 0.
-__device__ __forceinline__ uint32_t combine_bits(uint32_t b, const DevSpec &S, const KeyLayout &L,
-                                                 const char *kb, uint64_t e, uint32_t atoms) {
-  const uint32_t carry = reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e];
+__device__ __forceinline__ uint32_t combine_bits(uint32_t b, const DevSpec &S, uint32_t atoms, uint32_t carry) {
   uint32_t z = 0;
   for (uint32_t o = 0; o < S.n_bool; ++o) {
     const int j = S.out_prim[o];
@@ -294,34 +292,33 @@ __device__ __noinline__ void bx_finish(uint32_t b, const DevSpec &S, const KeyLa
 // and (k, c)); a daBit turns each XOR-shared bit into additive shares:
 // open o = bit ^ rho, then [bit] = [party 0] o + (1 - 2 o) [rho].
 // First half: this party's masked opening of (borrow, wrap), bits 0 and 1.
-__device__ __forceinline__ uint32_t trunc_send(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e,
-                                               uint32_t atoms) {
-  const uint32_t rho = reinterpret_cast<const uint32_t *>(kb + L.off_trunc_rho)[e];
+__device__ __forceinline__ uint32_t trunc_send(const DevSpec &S, uint32_t atoms, uint32_t rho) {
   return (((atoms >> S.trunc_q_lo) & 1u) | (((atoms >> S.trunc_q_hi) & 1u) << 1)) ^ rho;
 }
 
 // Second half: this party's additive share of T_s(x) from the public
 // delta = o_0 ^ o_1; the arithmetic form subtracts c >> s = 2^{k-1-s}.
-__device__ __forceinline__ uint64_t trunc_finish(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
-                                                 uint64_t e, uint64_t xhat, uint32_t delta) {
-  const uint64_t *tt = reinterpret_cast<const uint64_t *>(kb + L.off_trunc);
+// tt: this element's share of (r mod 2^k) >> s at tt[0], the daBit additive
+// shares at tt[ts], tt[2 ts].
+__device__ __forceinline__ uint64_t trunc_finish(uint32_t b, const DevSpec &S, uint64_t xhat, uint32_t delta,
+                                                 const uint64_t *tt, uint64_t ts) {
   const uint64_t d_lo = delta & 1u, d_hi = (delta >> 1) & 1u;
-  const uint64_t a_lo = tt[L.n + e], a_hi = tt[2 * L.n + e];
+  const uint64_t a_lo = tt[ts], a_hi = tt[2 * ts];
   const uint64_t borrow = (b == 0 ? d_lo : 0ull) + (d_lo ? 0ull - a_lo : a_lo);
   const uint64_t wrap = (b == 0 ? d_hi : 0ull) + (d_hi ? 0ull - a_hi : a_hi);
-  uint64_t sh = 0ull - tt[e] - borrow + (wrap << (S.k - S.trunc_s));
+  uint64_t sh = 0ull - tt[0] - borrow + (wrap << (S.k - S.trunc_s));
   if (b == 0) sh += (view(xhat, S.k, S.trunc_c) >> S.trunc_s) - (S.trunc_c >> S.trunc_s);
   return sh;
 }
 
 // Lookup output: share of v_{M-1} plus (-1)^b times the summed DCF terms,
 // LUT(u) = v_{M-1} + sum_{j=1}^{M-1} 1[u < B_j] (v_{j-1} - v_j).
+// vl: this element's share of v_{M-1}, word q at vl[q vs].
 template <int P>
-__device__ __forceinline__ void finish_lut(uint32_t b, const KeyLayout &L, const char *kb, uint64_t e,
-                                           const uint64_t *acc, uint64_t *pay) {
-  const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
+__device__ __forceinline__ void finish_lut(uint32_t b, const uint64_t *vl, uint64_t vs, const uint64_t *acc,
+                                           uint64_t *pay) {
 #pragma unroll
-  for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * L.n + e] + (b ? 0ull - acc[q] : acc[q]);
+  for (int q = 0; q < P; ++q) pay[q] = vl[uint64_t(q) * vs] + (b ? 0ull - acc[q] : acc[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,12 +361,16 @@ struct GateSmem {
   uint32_t *red_atoms;    // [party][slot][le]
   uint64_t *pwbox;        // [party][le][kPwSlots] piecewise-output openings (e | f << 32), then
                           // the shift gate's masked bits
+  unsigned char *post;    // [party][le] post-walk material records (post_rec_bytes each)
 };
+
+// Shared memory for the post-walk records of one tile (both parties).
+constexpr uint32_t kPostBytes = 20480;
 
 __host__ __device__ constexpr size_t gate_smem_bytes() {
   // tables + spec + outbox (R <= 4) + slot partials (P <= 4) + piecewise openings
   return size_t(kTabBytes) + ((sizeof(DevSpec) + 15) & ~size_t(15)) + 2ull * 256 * 4 * 16 +
-         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4 + 2ull * 256 * 8 * kPwSlots;
+         2ull * 256 * 8 * kMaxP + 2ull * 256 * 4 + 2ull * 256 * 8 * kPwSlots + kPostBytes;
 }
 
 __device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
@@ -384,7 +385,82 @@ __device__ __forceinline__ GateSmem carve_gate_smem(unsigned char *smem) {
   g.red_atoms = reinterpret_cast<uint32_t *>(p);
   p += 2ull * 256 * 4;
   g.pwbox = reinterpret_cast<uint64_t *>(p);
+  p += 2ull * 256 * 8 * kPwSlots;
+  g.post = p;
   return g;
+}
+
+// ---------------------------------------------------------------------------
+// post-walk key material
+//
+// After its walks the lead thread of a (party, element) needs the Beaver
+// triples, the share of v_{M-1}, the carry word and the shift-gate shares.
+// Loaded then, each Horner round and the lookup finish would wait on DRAM
+// with the SM's lookups idle; instead the thread copies them into a
+// shared-memory record (cp.async) before the walks start:
+//   u64 trip[n_mults][3] | u64 vlast[p] | u32 carry, rho | u64 tt[3] (shift gate)
+// ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ uint32_t post_rec_bytes(const DevSpec &S) {
+  return 24 * S.n_mults + 8 * S.p + 8 + (S.trunc_s ? 24 : 0);
+}
+
+struct PostSrc {
+  const uint64_t *trip;   // triple word w of multiplication mi at trip[(3 mi + w) stride]
+  const uint64_t *vl;     // share of v_{M-1}, word q at vl[q stride]
+  const uint64_t *tt;     // shift-gate shares at tt[0], tt[stride], tt[2 stride]
+  uint64_t stride;
+  uint32_t carry, rho;
+};
+
+__device__ __forceinline__ void cp_async8(unsigned char *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(uint32_t(__cvta_generic_to_shared(dst))), "l"(src));
+}
+__device__ __forceinline__ void cp_async4(unsigned char *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(uint32_t(__cvta_generic_to_shared(dst))), "l"(src));
+}
+
+__device__ __forceinline__ void post_fetch(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e,
+                                           unsigned char *rec) {
+  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  for (uint32_t w = 0; w < 3 * S.n_mults; ++w) cp_async8(rec + 8 * w, trip + uint64_t(w) * L.n + e);
+  unsigned char *p = rec + 24 * S.n_mults;
+  const uint64_t *vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast);
+  for (uint32_t q = 0; q < S.p; ++q) cp_async8(p + 8 * q, vl + uint64_t(q) * L.n + e);
+  p += 8 * S.p;
+  cp_async4(p, reinterpret_cast<const uint32_t *>(kb + L.off_carry) + e);
+  if (S.trunc_s) {
+    cp_async4(p + 4, reinterpret_cast<const uint32_t *>(kb + L.off_trunc_rho) + e);
+    const uint64_t *tt = reinterpret_cast<const uint64_t *>(kb + L.off_trunc);
+    for (uint32_t w = 0; w < 3; ++w) cp_async8(p + 8 + 8 * w, tt + uint64_t(w) * L.n + e);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The record after this thread's copies have landed.
+__device__ __forceinline__ PostSrc post_src_smem(const DevSpec &S, const unsigned char *rec) {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  PostSrc m;
+  m.trip = reinterpret_cast<const uint64_t *>(rec);
+  m.vl = m.trip + 3 * S.n_mults;
+  const uint32_t *c = reinterpret_cast<const uint32_t *>(m.vl + S.p);
+  m.carry = c[0];
+  m.rho = S.trunc_s ? c[1] : 0u;
+  m.tt = m.vl + S.p + 1;
+  m.stride = 1;
+  return m;
+}
+
+// The same material read from the key in HBM (records that do not fit).
+__device__ __forceinline__ PostSrc post_src_key(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e) {
+  PostSrc m;
+  m.trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip) + e;
+  m.vl = reinterpret_cast<const uint64_t *>(kb + L.off_vlast) + e;
+  m.tt = reinterpret_cast<const uint64_t *>(kb + L.off_trunc) + e;
+  m.stride = L.n;
+  m.carry = reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e];
+  m.rho = S.trunc_s ? reinterpret_cast<const uint32_t *>(kb + L.off_trunc_rho)[e] : 0u;
+  return m;
 }
 
 // One tile of one call: E = 256 / S elements, both parties.  All 512 threads
@@ -420,6 +496,13 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   }
   __syncthreads();
   const uint64_t xhat = box[le].x + box[E + le].x;
+  // the material the lead thread needs after the walks (triples, last
+  // payload shares, carries, shift-gate shares) is copied to its shared-memory
+  // record while the walks run, when the tile's records fit
+  const uint32_t rec = post_rec_bytes(S);
+  const bool prefetched = 2u * E * rec <= kPostBytes;      // uniform across the CTA
+  unsigned char *prec = G.post + (b * E + le) * rec;
+  if (prefetched && lead && valid) post_fetch(S, L, kb, e, prec);
   // (2)(3) this slot's share of the two FSS calls on the public x^
   uint32_t atoms = 0;
   uint64_t acc[P];
@@ -444,7 +527,9 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   uint64_t pay[P];
   uint64_t y[R];
   uint64_t xs = 0;
-  const uint64_t *trip = reinterpret_cast<const uint64_t *>(kb + L.off_trip);
+  // where this (party, element)'s post-walk material is read from
+  PostSrc pm;
+  if (lead && valid) pm = prefetched ? post_src_smem(S, prec) : post_src_key(S, L, kb, e);
   if (lead) {
     for (uint32_t s2 = 1; s2 < NS; ++s2) {
       const uint32_t rj = (b * NS + s2) * E + le;
@@ -453,8 +538,8 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
       for (int q = 0; q < P; ++q) acc[q] += G.red_acc[uint64_t(rj) * P + q];
     }
     if (valid) {
-      z = combine_bits(b, S, L, kb, e, atoms);
-      finish_lut<P>(b, L, kb, e, acc, pay);
+      z = combine_bits(b, S, atoms, pm.carry);
+      finish_lut<P>(b, pm.vl, pm.stride, acc, pay);
     } else {
 #pragma unroll
       for (int q = 0; q < P; ++q) pay[q] = 0;
@@ -464,7 +549,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
 #pragma unroll
     for (int o = 0; o < R; ++o) y[o] = pay[o * (D + 1) + D];
     if (S.trunc_s) {
-      G.pwbox[(b * E + le) * kPwSlots + kMaxPW] = valid ? trunc_send(S, L, kb, e, atoms) : 0u;
+      G.pwbox[(b * E + le) * kPwSlots + kMaxPW] = valid ? trunc_send(S, atoms, pm.rho) : 0u;
       if (valid) sent += 1;
     }
   }
@@ -474,7 +559,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   // across the CTA: one spec per tile)
   uint64_t tsh = 0;
   if (S.n_pw) {
-    const uint32_t carry = (lead && valid) ? reinterpret_cast<const uint32_t *>(kb + L.off_carry)[e] : 0u;
+    const uint32_t carry = (lead && valid) ? pm.carry : 0u;
     uint64_t nv = 0;
     uint32_t J = 0, zp = 0;
     if (lead && valid) {
@@ -489,7 +574,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
         const uint64_t *m0 = G.pwbox + le * kPwSlots, *m1 = G.pwbox + (E + le) * kPwSlots;
         bx_finish(b, S, L, kb, e, J, l, m0, m1, nv, zp);
         nv = bx_local(b, S, atoms, carry, l, nv);
-        if (l == 1 && S.trunc_s) tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
+        if (l == 1 && S.trunc_s) tsh = trunc_finish(b, S, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]), pm.tt, pm.stride);
       }
     }
     if (lead && valid) z |= zp << S.n_bool;
@@ -497,7 +582,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
     __syncthreads();
     if (lead && valid) {
       const uint64_t *m0 = G.pwbox + le * kPwSlots, *m1 = G.pwbox + (E + le) * kPwSlots;
-      tsh = trunc_finish(b, S, L, kb, e, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]));
+      tsh = trunc_finish(b, S, xhat, uint32_t(m0[kMaxPW] ^ m1[kMaxPW]), pm.tt, pm.stride);
     }
   }
   // x^-basis variant: the coefficients multiply the public x^, so Horner is
@@ -518,9 +603,9 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
       for (int o = 0; o < R; ++o) {
         const uint32_t mi = (D - 1 - jj) * R + o;
         if (valid) {
-          ta[o] = trip[(uint64_t(mi) * 3 + 0) * L.n + e];
-          tbv[o] = trip[(uint64_t(mi) * 3 + 1) * L.n + e];
-          tc[o] = trip[(uint64_t(mi) * 3 + 2) * L.n + e];
+          ta[o] = pm.trip[(uint64_t(mi) * 3 + 0) * pm.stride];
+          tbv[o] = pm.trip[(uint64_t(mi) * 3 + 1) * pm.stride];
+          tc[o] = pm.trip[(uint64_t(mi) * 3 + 2) * pm.stride];
           sent += 16;
         } else {
           ta[o] = tbv[o] = tc[o] = 0;
@@ -707,7 +792,7 @@ __global__ void __launch_bounds__(512, 1) pred_kernel(const __grid_constant__ Pa
     uint32_t atoms = 0;
     for (uint32_t t = 0; t < sspec->T; ++t) atoms |= bit_item(A.party, *sspec, A.L, A.kb, e, xhat, t, aes) << t;
     if (A.atoms) A.atoms[e] = atoms;
-    if (A.bits) A.bits[e] = combine_bits(A.party, *sspec, A.L, A.kb, e, atoms);
+    if (A.bits) A.bits[e] = combine_bits(A.party, *sspec, atoms, reinterpret_cast<const uint32_t *>(A.kb + A.L.off_carry)[e]);
   }
 }
 
@@ -725,7 +810,7 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
 #pragma unroll
     for (int q = 0; q < P; ++q) acc[q] = 0;
     for (uint32_t j = 0; j + 1 < sspec->M; ++j) vec_item<P>(A.party, *sspec, A.L, A.kb, e, xhat, j, acc, aes);
-    finish_lut<P>(A.party, A.L, A.kb, e, acc, pay);
+    finish_lut<P>(A.party, reinterpret_cast<const uint64_t *>(A.kb + A.L.off_vlast) + e, A.L.n, acc, pay);
 #pragma unroll
     for (int q = 0; q < P; ++q) A.payload[e * P + q] = pay[q];
   }
