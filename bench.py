@@ -54,7 +54,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.270674688e9 + 21.855488e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.271577e9 + 21.771776e6) / 65536}
 
 
 def parse():
