@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-rescale", action="store_true", help="skip the layer-rescale (ARS) run")
     ap.add_argument("--no-blocks", action="store_true", help="skip the softmax / LayerNorm block runs")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the cost model's work split (no measured tuning before the timed region)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
 
@@ -291,6 +293,18 @@ def run_ours(args, rank, world, local_rank):
     ctx = F.Context(local_rank)
     calls, config = workload(args.workload)
     css = {c.name: F.CompiledSpec(c.spec, ctx) for c in calls}
+    # measured launch shape per spec, before any timing: the library times the
+    # gate under every work split on throw-away samples and keeps the model
+    tuning = None
+    if not args.no_autotune:
+        tuning = {}
+        for c in calls:
+            cs = css[c.name]
+            model = cs.gate_slots(c.n)
+            t0 = time.perf_counter()
+            tune = cs.autotune()
+            tuning[c.name] = dict(tune, elements=c.n, slots_cost_model=model, slots_tuned=cs.gate_slots(c.n),
+                                  tune_s=time.perf_counter() - t0)
     xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
     total = sum(c.n for c in calls)
     stream = torch.cuda.current_stream()
@@ -522,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_served:
         served = run_served(ctx, args, dev)
     if not args.no_large:
-        large = run_large_layer(ctx, dev)
+        large = run_large_layer(ctx, dev, tune=not args.no_autotune)
     if not args.no_gpt2:
         gpt2 = run_gpt2_batch(ctx, args, dev)
 
@@ -585,6 +599,7 @@ def run_ours(args, rank, world, local_rank):
                        parallelism="replicas" if world > 1 else "single GPU, both parties on it",
                        key_sets_resident=G, timed_groups=-(-args.steps // G)),
         "per_op_ms": per_op_ms,
+        "autotune": tuning,
         "keygen": {"ms_per_step": keygen_ms, "elements_per_s": total / (keygen_ms * 1e-3)},
         "comm_bytes_per_party": comm_b,
         "gpu_launches": args.steps * len(calls),
@@ -849,6 +864,9 @@ def run_served(ctx, args, dev):
     f = 12
     css = {"gelu": F.CompiledSpec(S.gelu8(f=f), ctx), "exp": F.CompiledSpec(S.nexp16(f=f), ctx),
            "recip": F.CompiledSpec(S.recip16(f=f), ctx), "rsqrt": F.CompiledSpec(S.rsqrt16(f=f), ctx)}
+    if not args.no_autotune:
+        for cs in css.values():
+            cs.autotune()
     gen = torch.Generator(device=dev)
     gen.manual_seed(I.MASTER_SEED)
     total = 0
@@ -894,6 +912,9 @@ def run_gpt2_batch(ctx, args, dev):
     f = 12
     css = {"gelu": F.CompiledSpec(S.gelu8(f=f), ctx), "exp": F.CompiledSpec(S.nexp16(f=f), ctx),
            "recip": F.CompiledSpec(S.recip16(f=f), ctx), "rsqrt": F.CompiledSpec(S.rsqrt16(f=f), ctx)}
+    if not args.no_autotune:
+        for cs in css.values():
+            cs.autotune()
     gen = torch.Generator(device=dev)
     gen.manual_seed(I.MASTER_SEED + 3)
     total = 0
@@ -919,7 +940,7 @@ def run_gpt2_batch(ctx, args, dev):
     return res
 
 
-def run_large_layer(ctx, dev):
+def run_large_layer(ctx, dev, tune=True):
     """One GPT-style 2.7B layer (hidden 2560, 32 heads, MLP 10240 with SiLU,
     seq 1024): SiLU on 1024 x 10240, softmax nExp on 32 x 1024 x 1024, the
     reciprocal of the 32 x 1024 row sums and rsqrt for two LayerNorms (2 x
@@ -935,6 +956,9 @@ def run_large_layer(ctx, dev):
     f = 16
     css = {"silu": F.CompiledSpec(S.silu16(f=f), ctx), "exp": F.CompiledSpec(S.nexp16(f=f), ctx),
            "recip": F.CompiledSpec(S.recip16(f=f), ctx), "rsqrt": F.CompiledSpec(S.rsqrt16(f=f), ctx)}
+    if tune:
+        for cs in css.values():
+            cs.autotune()
     gen = torch.Generator(device=dev)
     gen.manual_seed(I.MASTER_SEED + 5)
     scale = float(2 ** f)

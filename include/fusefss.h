@@ -268,6 +268,37 @@ int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_key
                    uint64_t *y0_dev, uint64_t *y1_dev, uint32_t *z0_dev, uint32_t *z1_dev,
                    uint64_t *comm_dev, void *stream);
 
+/* ---- launch-shape autotuner (library tuning, no counterpart in the paper) */
+
+/* Measured per-spec timing of the fused gate for each work split: slots[i]
+ * threads per element (tiles of 256 / slots[i] elements), tile_us[i] the
+ * time one CTA takes for one tile, fixed_us[i] the per-launch cost (table
+ * staging, launch).  A launch of n elements is predicted to take
+ * fixed_us + ceil(ceil(n / tile) / SMs) * tile_us. */
+typedef struct {
+    uint32_t n_tried;        /* entries used below (splits with slots <= walks per element) */
+    uint32_t slots[5];
+    double tile_us[5];
+    double fixed_us[5];
+    uint32_t sample_elems;   /* the larger sample: 2 x SMs x 256 elements */
+    double dealer_ms;        /* time spent generating the samples' throw-away keys */
+} ffss_tune;
+
+/* Time the fused gate of `spec` on two throw-away samples of SMs x 256 and
+ * 2 x SMs x 256 elements under every work split, each with its own keys from
+ * a fixed tuning seed (never used for real calls), and keep the measured
+ * model in the spec: from then on ffss_eval_pair and the batched form pick,
+ * per call, the split with the least predicted time for its n (ties to more
+ * slots).  ffss_ctx_set_slots and ffss_batch_set_slots still override it.
+ * Allocates (cudaMalloc) and frees the sample buffers, and synchronizes the
+ * stream.  Results never depend on the split.  out may be NULL.
+ * Errors: FFSS_ERR_INVALID, FFSS_ERR_CUDA. */
+int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
+
+/* The work split (slots per element) the fused gate of `spec` uses for a call
+ * of n elements: forced, tuned, or the cost model's.  Errors: FFSS_ERR_INVALID. */
+int ffss_gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, uint32_t *slots);
+
 /* ---- online: batched form ----------------------------------------------- */
 
 /* One operator call of a batch: the arguments of ffss_eval_pair. */

@@ -126,6 +126,8 @@ struct ffss_spec {
   DevSpec host;
   DevSpec *dev;
   ffss_shape shape;
+  bool tuned;       // ffss_autotune has measured the work splits below
+  ffss_tune tune;
 };
 
 struct ffss_keys {
@@ -667,6 +669,33 @@ static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
   return best;
 }
 
+// Tiles of `slots`-way split elements that a launch of n elements runs per SM.
+static uint64_t gate_waves(const ffss_ctx *ctx, uint64_t n, uint32_t slots) {
+  const uint64_t tiles = (n + 256 / slots - 1) / (256 / slots);
+  return (tiles + ctx->sm_count - 1) / ctx->sm_count;
+}
+
+// The split a plain gate call of n elements uses: forced by the context, else
+// the measured model of ffss_autotune (least fixed + waves x tile time; ties
+// to more slots), else the AES-count cost model.
+static uint32_t gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n) {
+  if (ctx->force_slots) return ctx->force_slots;
+  if (spec->tuned) {
+    const ffss_tune &t = spec->tune;
+    uint32_t best = t.slots[0];
+    double best_us = 0;
+    for (uint32_t i = 0; i < t.n_tried; ++i) {
+      const double us = t.fixed_us[i] + double(gate_waves(ctx, n, t.slots[i])) * t.tile_us[i];
+      if (i == 0 || us <= best_us) {
+        best = t.slots[i];
+        best_us = us;
+      }
+    }
+    return best;
+  }
+  return choose_sched(ctx, spec->host, n).S;
+}
+
 template <int R, int D>
 static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st) {
   const size_t smem = gate_smem_bytes();
@@ -681,10 +710,11 @@ static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st)
   return FFSS_OK;
 }
 
-// Fused two-party gate launch on raw key buffers (no handle checks).
-static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
-                         const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
-                         uint32_t *z0, uint32_t *z1, uint64_t *comm, cudaStream_t st) {
+// Fused two-party gate launch on raw key buffers (no handle checks), with
+// the given work split.
+static int eval_pair_split(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
+                           const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
+                           uint32_t *z0, uint32_t *z1, uint64_t *comm, uint32_t slots, cudaStream_t st) {
   GateArgsS AS;
   memset(&AS, 0, sizeof(AS));
   GateArgs &A = AS.g;
@@ -692,8 +722,7 @@ static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char 
   A.k0 = k0; A.k1 = k1; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
   A.comm = reinterpret_cast<unsigned long long *>(comm);
   A.n = n; A.t0 = ctx->t0_dev;
-  AS.sched = ctx->force_slots ? make_sched(spec->host, ctx->force_slots, nullptr)
-                              : choose_sched(ctx, spec->host, n);
+  AS.sched = make_sched(spec->host, slots, nullptr);
   const uint32_t R = spec->host.r, D = spec->host.d;
   if (R == 1 && D == 0) return launch_gate<1, 0>(ctx, AS, st);
   if (R == 1 && D == 1) return launch_gate<1, 1>(ctx, AS, st);
@@ -704,6 +733,12 @@ static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char 
   if (R == 3 && D == 0) return launch_gate<3, 0>(ctx, AS, st);
   if (R == 4 && D == 0) return launch_gate<4, 0>(ctx, AS, st);
   return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
+}
+
+static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
+                         const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
+                         uint32_t *z0, uint32_t *z1, uint64_t *comm, cudaStream_t st) {
+  return eval_pair_split(ctx, spec, k0, k1, x0, x1, n, y0, y1, z0, z1, comm, gate_slots(ctx, spec, n), st);
 }
 
 extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
@@ -721,6 +756,130 @@ extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k
   if (rc) return rc;
   k0->used |= 3;
   k1->used |= 3;
+  return FFSS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch-shape autotuner
+// ---------------------------------------------------------------------------
+
+// Device buffers of one tuning sample; freed by the destructor.
+struct TuneSample {
+  uint64_t n = 0;
+  char *k0 = nullptr, *k1 = nullptr;
+  uint64_t *x = nullptr, *x0 = nullptr, *x1 = nullptr, *y0 = nullptr, *y1 = nullptr, *comm = nullptr;
+  uint32_t *z0 = nullptr, *z1 = nullptr;
+  ~TuneSample() {
+    for (void *p : {(void *)k0, (void *)k1, (void *)x, (void *)x0, (void *)x1, (void *)y0, (void *)y1,
+                    (void *)comm, (void *)z0, (void *)z1})
+      if (p) cudaFree(p);
+  }
+  cudaError_t alloc(const ffss_spec *spec, uint64_t elems) {
+    n = elems;
+    const uint64_t kb = make_layout(spec->host, n).total, r = spec->host.r;
+    cudaError_t e = cudaMalloc(&k0, kb);
+    if (e == cudaSuccess) e = cudaMalloc(&k1, kb);
+    if (e == cudaSuccess) e = cudaMalloc(&x, 8 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&x0, 8 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&x1, 8 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&y0, 8 * n * r);
+    if (e == cudaSuccess) e = cudaMalloc(&y1, 8 * n * r);
+    if (e == cudaSuccess) e = cudaMalloc(&z0, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&z1, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&comm, 16);
+    if (e == cudaSuccess) e = cudaMemset(x, 0, 8 * n);
+    return e;
+  }
+};
+
+// Events of one timing; destroyed with it.
+struct TuneEvents {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~TuneEvents() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// Least of `reps` timed launches (after one untimed one) of the gate with the
+// given split on one sample, in microseconds.
+static int time_split(const ffss_ctx *ctx, const ffss_spec *spec, const TuneSample &T, uint32_t slots,
+                      cudaStream_t st, double *us) {
+  TuneEvents ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  const int reps = 3;
+  double best = 0;
+  for (int i = 0; i <= reps; ++i) {
+    CUDA_TRY(cudaEventRecord(ev.a, st));
+    int rc = eval_pair_split(ctx, spec, T.k0, T.k1, T.x0, T.x1, T.n, T.y0, T.y1, T.z0, T.z1, T.comm, slots, st);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(ev.b, st));
+    CUDA_TRY(cudaEventSynchronize(ev.b));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    if (i == 1 || (i > 1 && 1e3 * ms < best)) best = 1e3 * ms;
+  }
+  *us = best;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream) {
+  if (!ctx || !spec) return fail(FFSS_ERR_INVALID, "ffss_autotune: NULL argument");
+  if (int rc = check_device_spec(ctx, spec)) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const DevSpec &S = spec->host;
+  const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  // Two samples of SMs x 256 and 2 x SMs x 256 elements: every split runs
+  // whole waves on both (slots and 2 x slots tiles per SM), so the
+  // difference of the two times is slots tiles of one CTA and the rest is
+  // the launch's fixed cost.
+  TuneSample A, B;
+  const uint64_t na = uint64_t(ctx->sm_count) * 256;
+  CUDA_TRY(A.alloc(spec, na));
+  CUDA_TRY(B.alloc(spec, 2 * na));
+  // Throw-away keys: a fixed tuning seed and call ids no real call uses.
+  static const uint8_t kTuneSeed[16] = {'F', 'F', 'S', 'S', '-', 'a', 'u', 't', 'o', 't', 'u', 'n', 'e', 0, 0, 0};
+  TuneEvents ev;
+  CUDA_TRY(cudaEventCreate(&ev.a));
+  CUDA_TRY(cudaEventCreate(&ev.b));
+  CUDA_TRY(cudaEventRecord(ev.a, st));
+  int rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF0u, A.n, A.x, A.k0, A.k1, A.x0, A.x1, st);
+  if (!rc) rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF1u, B.n, B.x, B.k0, B.k1, B.x0, B.x1, st);
+  if (rc) return rc;
+  CUDA_TRY(cudaEventRecord(ev.b, st));
+  CUDA_TRY(cudaEventSynchronize(ev.b));
+  float dealer_ms = 0;
+  CUDA_TRY(cudaEventElapsedTime(&dealer_ms, ev.a, ev.b));
+  ffss_tune t;
+  memset(&t, 0, sizeof(t));
+  t.sample_elems = uint32_t(B.n);
+  t.dealer_ms = dealer_ms;
+  for (uint32_t slots = 1; slots <= 16; slots *= 2) {
+    if (slots > 1 && slots > nitems) break;
+    double ua = 0, ub = 0;
+    rc = time_split(ctx, spec, A, slots, st, &ua);
+    if (!rc) rc = time_split(ctx, spec, B, slots, st, &ub);
+    if (rc) return rc;
+    double tile = (ub - ua) / slots;
+    if (tile <= 0) tile = ub / (2.0 * slots);   // noise on a tiny spec: no fixed part
+    double fixed = ua - tile * slots;
+    if (fixed < 0) fixed = 0;
+    t.slots[t.n_tried] = slots;
+    t.tile_us[t.n_tried] = tile;
+    t.fixed_us[t.n_tried] = fixed;
+    ++t.n_tried;
+  }
+  spec->tune = t;
+  spec->tuned = true;
+  if (out) *out = t;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, uint32_t *slots) {
+  if (!ctx || !spec || !slots) return fail(FFSS_ERR_INVALID, "ffss_gate_slots: NULL argument");
+  *slots = gate_slots(ctx, spec, n);
   return FFSS_OK;
 }
 
@@ -849,8 +1008,14 @@ extern "C" int ffss_batch_set_slots(ffss_batch *bt, uint32_t slots) {
   return FFSS_OK;
 }
 
-static uint32_t batch_slots(const ffss_batch *bt, const DevSpec &S) {
+// The split of a batched call of n elements: forced by the plan, else the
+// split the plain gate would take for the call (the tuned waves model: a
+// split with the least time per element but tiles of a millisecond leaves
+// the persistent CTAs a long tail), else 8.
+static uint32_t batch_slots(const ffss_batch *bt, const ffss_spec *spec, uint64_t n) {
+  const DevSpec &S = spec->host;
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  if (!bt->force_slots && spec->tuned) return gate_slots(bt->ctx, spec, n);
   uint32_t want = bt->force_slots ? bt->force_slots : 8;
   uint32_t s = 1;
   while (s * 2 <= want && s * 2 <= (nitems ? nitems : 1)) s *= 2;
@@ -888,7 +1053,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
     it.cls = shape_class(S.r, S.d);
     if (it.cls < 0) return fail(FFSS_ERR_UNSUPPORTED, "call %u: n_out=%u degree=%u", i, S.r, S.d);
     uint64_t mx = 0;
-    it.c.sched = make_sched(S, batch_slots(bt, S), &mx);
+    it.c.sched = make_sched(S, batch_slots(bt, c.spec, c.n), &mx);
     it.tile_cost = mx;
     it.tiles = (c.n + it.c.sched.E - 1) / it.c.sched.E;
     items.push_back(it);

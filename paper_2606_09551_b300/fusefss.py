@@ -100,6 +100,17 @@ class ServerStats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Tune(C.Structure):
+    _fields_ = [("n_tried", C.c_uint32), ("slots", C.c_uint32 * 5), ("tile_us", C.c_double * 5),
+                ("fixed_us", C.c_double * 5), ("sample_elems", C.c_uint32), ("dealer_ms", C.c_double)]
+
+    def as_dict(self):
+        n = self.n_tried
+        return {"slots": list(self.slots[:n]), "tile_us": list(self.tile_us[:n]),
+                "fixed_us": list(self.fixed_us[:n]), "sample_elems": self.sample_elems,
+                "dealer_ms": self.dealer_ms}
+
+
 class CallDesc(C.Structure):
     _fields_ = [("spec", vp), ("k0", vp), ("k1", vp), ("x0", vp), ("x1", vp), ("n", C.c_uint64),
                 ("y0", vp), ("y1", vp), ("z0", vp), ("z1", vp)]
@@ -128,6 +139,8 @@ def lib():
         L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
         L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
+        L.ffss_autotune.argtypes = [vp, vp, C.POINTER(Tune), vp]
+        L.ffss_gate_slots.argtypes = [vp, vp, C.c_uint64, C.POINTER(C.c_uint32)]
         L.ffss_batch_create.argtypes = [vp, C.c_uint32, C.POINTER(vp)]
         L.ffss_batch_destroy.argtypes = [vp]
         L.ffss_batch_eval.argtypes = [vp, C.POINTER(CallDesc), C.c_uint32, vp, vp]
@@ -242,6 +255,19 @@ class CompiledSpec:
         sh = Shape()
         _check(lib().ffss_spec_shape(self.h, C.byref(sh)))
         self.shape = sh
+
+    def autotune(self, stream=None) -> dict:
+        """Measure the fused gate under every work split on throw-away samples
+        (library-side); later calls on this spec use the measured model."""
+        t = Tune()
+        _check(lib().ffss_autotune(self.ctx.h, self.h, C.byref(t), _stream(stream)))
+        return t.as_dict()
+
+    def gate_slots(self, n: int) -> int:
+        """Slots per element the fused gate uses for a call of n elements."""
+        v = C.c_uint32()
+        _check(lib().ffss_gate_slots(self.ctx.h, self.h, n, C.byref(v)))
+        return v.value
 
     def key_bytes(self, n: int) -> int:
         b = C.c_uint64()

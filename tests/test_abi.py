@@ -39,6 +39,18 @@ def test_context_without_gpu_fails_cleanly(libpath):
     assert rc == -3 and F.lib().ffss_last_error()
 
 
+def test_autotune_rejects_null_arguments(libpath):
+    L = F.lib()
+    t = F.Tune()
+    assert L.ffss_autotune(None, None, C.byref(t), None) == -1
+    assert b"NULL" in L.ffss_last_error()
+    v = C.c_uint32()
+    assert L.ffss_gate_slots(None, None, 1, C.byref(v)) == -1
+    # a host-only spec (no context) cannot be tuned or launched
+    cs = F.CompiledSpec(S.gelu4())
+    assert L.ffss_autotune(None, cs.h, None, None) == -1
+
+
 def _shape_vs_oracle(sp, may_reject=False):
     try:
         o = O.Spec(**sp.descriptor())

@@ -1,0 +1,95 @@
+"""Launch-shape autotuner: ffss_autotune times the fused gate under every
+work split on throw-away samples, the spec keeps the measured model, and the
+plain and batched forms then pick their split from it.  The split never
+changes a share: tuned calls stay bit-exact to the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_09551_b300 import fusefss as F
+from paper_2606_09551_b300 import inputs as I
+from paper_2606_09551_b300 import specs as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2606_09551_b300 import build
+    build.build()
+    return F.Context(0)
+
+
+def _walks(sp):
+    o = O.Spec(**sp.descriptor())
+    return o.T + (o.M - 1 if o.M > 1 else 0)
+
+
+def _predicted_slots(tune, n, sms):
+    """The plain gate's rule restated: least fixed + waves x tile time, ties to more slots."""
+    best, best_us = None, None
+    for s, tile, fixed in zip(tune["slots"], tune["tile_us"], tune["fixed_us"]):
+        e = 256 // s
+        waves = -(-(-(-n // e)) // sms)
+        us = fixed + waves * tile
+        if best is None or us <= best_us:
+            best, best_us = s, us
+    return best
+
+
+def _gate(ctx, cs, sp, x, call_id, batch=None):
+    import torch
+    n = x.size
+    k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
+    xp = torch.from_numpy(x).cuda()
+    x0, x1 = torch.empty_like(xp), torch.empty_like(xp)
+    F.keygen(ctx, cs, I.KEY_SEED, call_id, n, k0, k1, xp, x0, x1)
+    y0 = torch.empty(n * sp.n_out, dtype=torch.uint64, device="cuda:0")
+    y1 = torch.empty_like(y0)
+    z0 = torch.empty(n, dtype=torch.uint32, device="cuda:0")
+    z1 = torch.empty_like(z0)
+    if batch is None:
+        F.eval_pair(ctx, cs, k0, k1, x0, x1, y0, y1, z0, z1)
+    else:
+        batch.eval([(cs, k0, k1, x0, x1, y0, y1, z0, z1)])
+    torch.cuda.synchronize()
+    return {"y0": y0.cpu().numpy().reshape(n, sp.n_out), "y1": y1.cpu().numpy().reshape(n, sp.n_out),
+            "z0": z0.cpu().numpy(), "z1": z1.cpu().numpy()}
+
+
+@pytest.mark.parametrize("sp", [S.gelu4(), S.nexp16(), S.trunc(32, 12, True)], ids=["gelu4", "nexp16", "ars32"])
+def test_autotune_model_and_parity(ctx, sp):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cs = F.CompiledSpec(sp, ctx)
+    walks = _walks(sp)
+    tune = cs.autotune()
+    want = [s for s in (1, 2, 4, 8, 16) if s == 1 or s <= walks]
+    assert tune["slots"] == want
+    assert tune["sample_elems"] == 2 * sms * 256
+    assert all(t > 0 for t in tune["tile_us"]) and all(f >= 0 for f in tune["fixed_us"])
+    for n in (1, 100, 4097, sms * 32 + 5, 196608, 1 << 22):
+        assert cs.gate_slots(n) == _predicted_slots(tune, n, sms)
+    # tuned calls, plain and batched, on ragged sizes: bit-exact to the oracle
+    o = O.Spec(**sp.descriptor())
+    bt = F.Batch(ctx, 4)
+    for i, n in enumerate((1, 2999)):
+        x = I.uniform_x(n, sp.k, 500 + i)
+        k0, k1, x0, x1 = O.dealer(o, I.KEY_SEED, 40 + i, 0, n, x)
+        ref = O.eval_pair(o, k0, k1, x0, x1)
+        for got in (_gate(ctx, cs, sp, x, 40 + i), _gate(ctx, cs, sp, x, 40 + i, batch=bt)):
+            for name in ("y0", "y1", "z0", "z1"):
+                assert np.array_equal(got[name].reshape(ref[name].shape), ref[name]), name
+
+
+def test_forced_split_overrides_tuning(ctx):
+    cs = F.CompiledSpec(S.gelu8(), ctx)
+    cs.autotune()
+    try:
+        ctx.set_slots(2)
+        assert cs.gate_slots(393216) == 2
+    finally:
+        ctx.set_slots(0)
+    assert cs.gate_slots(393216) in (1, 2, 4, 8, 16)
