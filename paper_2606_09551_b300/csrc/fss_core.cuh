@@ -193,6 +193,7 @@ FFSS_CORE uint4 mmo(uint4 s, uint32_t j, const AES &aes) {
 // Four independent MMO blocks through a 4-block AES functor
 // (aes4(in[4]) -> AES_K of each), so one call carries four encryptions.
 struct Blk4 { uint4 v[4]; };
+struct Blk8 { uint4 v[8]; };
 
 template <class AES4>
 FFSS_CORE Blk4 mmo4(uint4 s0, uint32_t j0, uint4 s1, uint32_t j1, uint4 s2, uint32_t j2, uint4 s3, uint32_t j3,
@@ -434,16 +435,27 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
             pv[w >> 1][w & 1][1] = hi64(pb.v[w]);
           }
         } else {
+          // both children's payload blocks, both parties: one 8-block call
+          Blk8 in;
 #pragma unroll
           for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t j = 4u + (cp + h) * V;
-            const Blk4 pb = mmo4(s0, j, s0, j + 1, s1, j, s1, j + 1, aes4);
+            in.v[4 * h + 0] = s0; in.v[4 * h + 0].x ^= j;
+            in.v[4 * h + 1] = s0; in.v[4 * h + 1].x ^= j + 1;
+            in.v[4 * h + 2] = s1; in.v[4 * h + 2].x ^= j;
+            in.v[4 * h + 3] = s1; in.v[4 * h + 3].x ^= j + 1;
+          }
+          Blk8 pb = aes4.eight(in);
+#pragma unroll
+          for (int w = 0; w < 8; ++w) pb.v[w] = xor4(pb.v[w], in.v[w]);
+#pragma unroll
+          for (uint32_t h = 0; h < 2; ++h) {
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-              pv[h][b][0] = lo64(pb.v[2 * b]);
-              pv[h][b][1] = hi64(pb.v[2 * b]);
-              pv[h][b][2] = lo64(pb.v[2 * b + 1]);
-              if (P > 3) pv[h][b][3] = hi64(pb.v[2 * b + 1]);
+              pv[h][b][0] = lo64(pb.v[4 * h + 2 * b]);
+              pv[h][b][1] = hi64(pb.v[4 * h + 2 * b]);
+              pv[h][b][2] = lo64(pb.v[4 * h + 2 * b + 1]);
+              if (P > 3) pv[h][b][3] = hi64(pb.v[4 * h + 2 * b + 1]);
             }
           }
         }

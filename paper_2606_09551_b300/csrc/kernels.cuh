@@ -97,9 +97,19 @@ __device__ __noinline__ Blk4 aes4_dcf_call(Blk4 in, const char *base, uint32_t l
   o.v[3] = aes128v<kAesVariant>(in.v[3], RkDcf(), tb);
   return o;
 }
+// Eight AES_K blocks per out-of-line call (the payload expansions of a pair
+// of children, both parties, V = 2): twice the independent lookups per round.
+__device__ __noinline__ Blk8 aes8_dcf_call(Blk8 in, const char *base, uint32_t lane4) {
+  const Tab tb{base, lane4};
+  Blk8 o;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) o.v[i] = aes128v<kAesVariant>(in.v[i], RkDcf(), tb);
+  return o;
+}
 struct AesDcfCall4 {
   Tab tb;
   __device__ __forceinline__ Blk4 operator()(const Blk4 &in) const { return aes4_dcf_call(in, tb.base, tb.lane4); }
+  __device__ __forceinline__ Blk8 eight(const Blk8 &in) const { return aes8_dcf_call(in, tb.base, tb.lane4); }
 };
 
 // Stage the four rotated T-tables, 32 lane copies each, and the spec.
