@@ -67,8 +67,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--served-requests", type=int, default=8)
-    ap.add_argument("--served-layers", type=int, default=2)
+    ap.add_argument("--served-requests", type=int, default=16)
+    ap.add_argument("--served-layers", type=int, default=1)
+    ap.add_argument("--no-served-plain", action="store_true",
+                    help="skip the plain per-operator run of the served trace")
     ap.add_argument("--no-large", action="store_true", help="skip the streamed large-layer run")
     ap.add_argument("--gpt2-layers", type=int, default=1, help="layers per request in the 32-request batch")
     ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
@@ -826,10 +828,82 @@ def _aes_roofline():
     return SMS * SM_MAX_MHZ * 1e6 / max(ALU_OPS_PER_AES / 64.0, LDS_PER_AES / 32.0)
 
 
+def _pct(sorted_vals, q):
+    """Nearest-rank percentile of an ascending list."""
+    i = max(0, min(len(sorted_vals) - 1, -(-q * len(sorted_vals) // 100) - 1))
+    return sorted_vals[i]
+
+
+def run_plain_fifo(ctx, dev, trace, pool_bytes, seed):
+    """The plain per-operator form on a served trace: requests one at a time
+    in arrival order, and within a request every layer's operator calls one
+    after another; each call's keys are dealt into a key pool of pool_bytes
+    (both parties) chunk by chunk, each chunk by its own dealer launch and
+    then its own fused-gate launch.  Returns elements/s and per-request
+    latency (arrival to last share written) on the GPU event timeline."""
+    import torch
+
+    from paper_2606_09551_b300 import fusefss as F
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device=dev)
+    cap = 1 << 22
+    xs0 = torch.empty(cap, dtype=torch.uint64, device=dev)
+    xs1 = torch.empty_like(xs0)
+    order = sorted(range(len(trace)), key=lambda i: trace[i][1])
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    host0 = time.perf_counter()
+    done, layer_ev, elements, launches, call_id = {}, [], 0, 0, 3_000_000
+    for i in order:
+        layers, arrival_s, _ = trace[i]
+        # a request cannot start before it arrives
+        wait = arrival_s - (time.perf_counter() - host0)
+        if wait > 0:
+            time.sleep(wait)
+        for ops in layers:
+            a = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for cs, x, y0, y1, z0, z1 in ops:
+                n = x.numel()
+                per = 2 * cs.shape.key_bytes_per_elem
+                chunk = max(1, min(cap, (pool_bytes - 4096) // per))
+                for s0 in range(0, n, chunk):
+                    c = min(chunk, n - s0)
+                    nb = cs.key_bytes(c)
+                    off = -(-nb // 256) * 256
+                    k0 = F.Keys(cs, c, 0, buf=pool[:nb])
+                    k1 = F.Keys(cs, c, 1, buf=pool[off:off + nb])
+                    F.keygen(ctx, cs, seed, call_id, c, k0, k1, x[s0:s0 + c], xs0[:c], xs1[:c])
+                    F.eval_pair(ctx, cs, k0, k1, xs0[:c], xs1[:c], y0[s0:s0 + c], y1[s0:s0 + c],
+                                z0[s0:s0 + c], z1[s0:s0 + c])
+                    k0.close()
+                    k1.close()
+                    call_id += 1
+                    launches += 2
+                elements += n
+            b = torch.cuda.Event(enable_timing=True)
+            b.record()
+            layer_ev.append((a, b))
+        done[i] = layer_ev[-1][1]
+    torch.cuda.synchronize()
+    # trace clock: 0 at t0, request i arrives at arrival_s; the first request
+    # starts on an idle GPU at its arrival
+    req = sorted(t0.elapsed_time(done[i]) - 1e3 * trace[i][1] for i in order)
+    span_s = t0.elapsed_time(layer_ev[-1][1]) * 1e-3 - trace[order[0]][1]
+    lay = sorted(a.elapsed_time(b) for a, b in layer_ev)
+    del pool
+    return {"value": elements / span_s, "unit": "elements/s", "elements": elements, "launches": launches,
+            "span_s": span_s, "request_ms_p50": _pct(req, 50), "request_ms_p99": _pct(req, 99),
+            "layer_service_ms_p50": _pct(lay, 50), "layer_service_ms_p99": _pct(lay, 99),
+            "form": "plain per-operator launches, requests first-come first-served, keys dealt per chunk "
+                    "into a %d GB pool just before each chunk's gate launch" % (pool_bytes >> 30)}
+
+
 def _server_result(sv, nreq, clk, wall, aes_blocks):
     st = sv.summary()
     infos = [sv.request_info(i) for i in range(nreq)]
     queue = sorted(max(0.0, r["admitted_ms"] - r["arrival_ms"]) for r in infos)
+    req = sorted(r["done_ms"] - r["arrival_ms"] for r in infos)
     span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
     return st, {"value": st["elements"] / span_s, "unit": "elements/s",
                 "aes_blocks": aes_blocks,
@@ -841,6 +915,7 @@ def _server_result(sv, nreq, clk, wall, aes_blocks):
                 "layer_ms_p50": st["layer_ms_p50"], "layer_ms_p99": st["layer_ms_p99"],
                 "layer_ms_max": st["layer_ms_max"],
                 "queue_ms_p50": queue[len(queue) // 2], "queue_ms_max": queue[-1],
+                "request_ms_p50": _pct(req, 50), "request_ms_p99": _pct(req, 99),
                 "span_s": span_s, "wall_s": wall, "clocks": clk.summary()}
 
 
@@ -892,6 +967,16 @@ def run_served(ctx, args, dev):
                 "config": "BERT-large shapes (hidden 1024, 16 heads, MLP 4096), L log-uniform [16, 2048], "
                           "Poisson 20 req/s, 64 GB key budget, max 8 admitted, chunks <= 4M elements"})
     sv.close()
+    if not args.no_served_plain:
+        # the same trace in the plain per-operator form; the server keeps half
+        # of its 64 GB key pool for the chunks it evaluates (the other half is
+        # filled meanwhile), so the plain form gets the same 32 GB per chunk set
+        trace = [(layers, arr, cid) for layers, arr, cid in pending]
+        plain = run_plain_fifo(ctx, dev, trace, 32 << 30, I.KEY_SEED)
+        plain["vs_served"] = {"elements_per_s": res["value"] / plain["value"],
+                              "request_ms_p50": plain["request_ms_p50"] / res["request_ms_p50"],
+                              "request_ms_p99": plain["request_ms_p99"] / res["request_ms_p99"]}
+        res["plain_fifo"] = plain
     return res
 
 

@@ -2,9 +2,12 @@
 //
 // Requests arrive with a list of layers; each layer is a list of operator
 // calls (spec, n, plaintext input on the device, output share buffers).  The
-// loop keeps up to max_active requests admitted.  Every step it gathers, in
-// round-robin order over the admitted requests, chunks of each request's
-// ready layer until half of the key pool is spoken for, has the GPU dealer
+// loop keeps up to max_active requests admitted.  Every step it gathers,
+// requests with the fewest key bytes left in their ready layer first, chunks
+// of each request's ready layer until half of the key pool is spoken for
+// (short layers go whole into one step; the longest layer takes the room
+// that is left, but no more than the others hold or a quarter of the half,
+// whichever is larger), has the GPU dealer
 // generate those chunks' keys into that half (keys are produced on the
 // device just before use, so no request's keys need to be resident whole),
 // and evaluates all chunks in ONE batched launch.  Dealer work for step t+1
@@ -263,26 +266,48 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
   // dealer work into this pool half is ordered (on the GPU) after the
   // evaluation that last read it; see the wait recorded at the end of a step
   const int h = sv->next_half;
-  // gather chunks round-robin over admitted requests with a ready layer
+  // gather chunks: admitted requests with a ready layer, least key bytes
+  // left in that layer first, each issuing its layer's ops in order while
+  // the pool half has room.  A short layer is issued whole in one step; a
+  // long one takes the room that is left and goes on in the next steps.
   SrvStep st;
   st.half = h;
   std::vector<ffss_call> calls;
   uint64_t used = 0;
-  bool progress = true;
-  while (progress && calls.size() < kBatchMaxCalls) {
-    progress = false;
-    for (uint32_t ri = 0; ri < sv->reqs.size() && calls.size() < kBatchMaxCalls; ++ri) {
-      SrvReq &r = sv->reqs[ri];
-      // a layer whose chunks are all issued waits until they are written;
-      // only then does the next layer become ready
-      if (r.state != 1 || r.layer_issued) continue;
+  std::vector<std::pair<uint64_t, uint32_t>> order;
+  for (uint32_t ri = 0; ri < sv->reqs.size(); ++ri) {
+    const SrvReq &r = sv->reqs[ri];
+    // a layer whose chunks are all issued waits until they are written;
+    // only then does the next layer become ready
+    if (r.state != 1 || r.layer_issued) continue;
+    uint64_t left_bytes = 0;
+    for (uint32_t oi = r.op; oi < r.per_layer; ++oi) {
+      const SrvOp &o = r.ops[r.layer * r.per_layer + oi];
+      left_bytes += (o.n - (oi == r.op ? r.elem : 0)) * o.spec->shape.key_bytes_per_elem;
+    }
+    order.push_back({left_bytes, ri});
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<uint64_t, uint32_t> &x, const std::pair<uint64_t, uint32_t> &y) {
+                     return x.first < y.first;
+                   });
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const uint32_t ri = order[oi].second;
+    SrvReq &r = sv->reqs[ri];
+    // the longest ready layer, when others share the step, gets at most the
+    // bytes the others already hold (and at least a quarter of the half), so
+    // the step does not last much longer than the short layers need
+    const uint64_t limit = oi + 1 == order.size() && oi > 0
+                               ? std::min(sv->half_bytes, used + std::max(used, sv->half_bytes / 4))
+                               : sv->half_bytes;
+    while (!r.layer_issued && calls.size() < kBatchMaxCalls) {
       const SrvOp &o = r.ops[r.layer * r.per_layer + r.op];
       const uint64_t left = o.n - r.elem;
       uint64_t n = 0;
       {
-        const uint64_t room = sv->half_bytes - used;
+        const uint64_t room = used < limit ? limit - used : 0;
         n = srv_fit(o.spec, room, std::min<uint64_t>(left, sv->cfg.chunk_elems));
-        if (n == 0) continue;
+        if (n == 0) break;
         const uint64_t kb = align256(make_layout(o.spec->host, n).total);
         char *base = sv->pool[h] + used;
         ffss_keys *k0 = nullptr, *k1 = nullptr;
@@ -320,7 +345,6 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
         r.outstanding += 1;
         r.elem += n;
         sv->elements += n;
-        progress = true;
       }
       if (r.elem == o.n) {   // next op of the layer, or the layer is fully issued
         r.elem = 0;

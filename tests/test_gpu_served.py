@@ -109,3 +109,23 @@ def test_admission_limits(ctx):
     tiny.submit([[(big, x, y, y.clone(), z, z.clone())]] * 1, 0.0)   # 51.7 KB per element fits 1 MiB halves
     with pytest.raises(F.FfssError):
         F.Server(ctx, 1 << 20, 1, 16, I.KEY_SEED)
+
+
+def test_short_layers_go_first(ctx):
+    """A step takes the ready layers with the fewest key bytes left first:
+    short requests submitted behind a long one finish before the long
+    request's first layer does, and the long request still completes."""
+    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    sv = F.Server(ctx, 48 << 20, 3, 1 << 20, I.KEY_SEED)   # 24 MB per step: the long layer needs many steps
+    long_req = _request(ctx, css, [20000, 3000], 70)
+    short = [_request(ctx, css, [100, 30], 71 + i) for i in range(2)]
+    lid = sv.submit(long_req, 0.0, call_id_base=700)
+    sids = [sv.submit(r, 0.0, call_id_base=800 + 10 * i) for i, r in enumerate(short)]
+    sv.run()
+    li = sv.request_info(lid)
+    assert li["state"] == 2 and len(li["layer_ms"]) == 2
+    long_first_layer_done = li["admitted_ms"] + li["layer_ms"][0]
+    for s in sids:
+        si = sv.request_info(s)
+        assert si["state"] == 2 and si["done_ms"] < long_first_layer_done
+    sv.close()
