@@ -54,7 +54,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.271577e9 + 21.771776e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.259368e9 + 8.76928e6) / 65536}
 
 
 def parse():
@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the cost model's work split (no measured tuning before the timed region)")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="force the gate's work split (slots per element) for every call (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     return ap.parse_args()
 
@@ -307,6 +309,9 @@ def run_ours(args, rank, world, local_rank):
             tune = cs.autotune()
             tuning[c.name] = dict(tune, elements=c.n, slots_cost_model=model, slots_tuned=cs.gate_slots(c.n),
                                   tune_s=time.perf_counter() - t0)
+    if args.slots:
+        ctx.set_slots(args.slots)
+        config = dict(config, forced_slots=args.slots)
     xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
     total = sum(c.n for c in calls)
     stream = torch.cuda.current_stream()
