@@ -493,6 +493,9 @@ def run_ours(args, rank, world, local_rank):
     xhat = None
     if not args.no_xhat:
         vcss = {c.name: F.CompiledSpec(c.spec.variant(True), ctx) for c in calls}
+        if not args.no_autotune:
+            for cs in vcss.values():
+                cs.autotune()
         vsets = []
         nx = sets_that_fit(sum(2 * vcss[c.name].key_bytes(c.n) for c in calls), args.steps + 1) - 1
         for s_ in range(nx + 1):
@@ -678,6 +681,8 @@ def run_rescales(ctx, args, dev, stream, world):
     from paper_2606_09551_b300 import inputs as I
     calls = I.bert_layer_rescales()
     cs = F.CompiledSpec(calls[0].spec, ctx)
+    if not args.no_autotune:
+        cs.autotune()
     total = sum(c.n for c in calls)
     xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
     outs = {}
@@ -778,6 +783,9 @@ def run_blocks(ctx, args, dev, stream, world):
     sp = S.softmax_specs()
     names = ["relu", "exp", "shift_e", "recip", "shift_t", "shift_p"]
     gates = [F.CompiledSpec(sp[k], ctx) for k in names]
+    if not args.no_autotune:
+        for g in gates:
+            g.autotune()
     sm = F.Softmax(ctx, gates, rows, L)
     scores = 2.0 * rng.standard_normal((rows, L))
     ms, y, cb = timed(sm, S.encode(scores.reshape(-1), 12), rows * L, 2000)
@@ -804,6 +812,9 @@ def run_blocks(ctx, args, dev, stream, world):
     lsp, cH = S.layernorm_specs(H)
     names = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
     gates = [F.CompiledSpec(lsp[k], ctx) for k in names]
+    if not args.no_autotune:
+        for g in gates:
+            g.autotune()
     ln = F.LayerNorm(ctx, gates, rows, H, cH)
     hid = rng.standard_normal((rows, H)) * 1.2 + 0.3
     ms, y, cb = timed(ln, S.encode(hid.reshape(-1), 12), rows * H, 3000)
