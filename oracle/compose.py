@@ -23,6 +23,13 @@ the gates come as a dict of oracle specs with the keys below:
 3. E = `exp`(D), rescaled by the shift gate `shift_e`.
 4. s = row sum of E (local).
 5. t = `recip`(s), rescaled by `shift_t`.
+5a. `newton` times, the reciprocal's refinement as a fixed post-processing
+   circuit (Def. "specification-compatible scalar gate": a constant number of
+   refinement steps, each Beaver products plus shift gates): with s at 16 and
+   t at 20 fractional bits, u = `shift_n1`(s * t) is s t at 20 bits,
+   v = 2 - u (party 0 adds the public 2^21, both negate), and
+   t = `shift_n2`(t * v) at 20 bits: Newton's iteration t (2 - s t) for 1/s,
+   which squares the relative error of t.
 6. P = E * t (Beaver multiplication, t broadcast over the row).
 7. Y = `shift_p`(P).
 
@@ -30,7 +37,9 @@ Every rescale rounds to nearest: party 0 adds 2^(s-1) (a public constant,
 local) before the shift gate's floor by 2^s.
 
 Dealer call ids: call_base + j for the j-th step that draws (the tree
-rounds, then exp, shift_e, recip, shift_t, the multiplication, shift_p)."""
+rounds, then exp, shift_e, recip, shift_t, per Newton step the product
+s t, shift_n1, the product t v and shift_n2, then the multiplication and
+shift_p)."""
 from __future__ import annotations
 
 import numpy as np
@@ -78,10 +87,11 @@ def row_max_pair(relu, seed, call_base, x0, x1):
     return c0[:, 0].copy(), c1[:, 0].copy(), comm, cid
 
 
-def softmax_pair(g, seed, call_base, x0, x1):
+def softmax_pair(g, seed, call_base, x0, x1, newton: int = 0):
     """Both parties' shares of the softmax pipeline on shares x0, x1 [rows, L];
-    g maps relu, exp, shift_e, recip, shift_t, shift_p to oracle specs.
-    Returns (y0, y1, comm, steps) with steps the intermediate shares."""
+    g maps relu, exp, shift_e, recip, shift_t, shift_p (and shift_n1,
+    shift_n2 when newton > 0) to oracle specs.  Returns (y0, y1, comm, steps)
+    with steps the intermediate shares."""
     x0 = np.asarray(x0, np.uint64)
     x1 = np.asarray(x1, np.uint64)
     rows, L = x0.shape
@@ -98,12 +108,28 @@ def softmax_pair(g, seed, call_base, x0, x1):
         steps[name] = (r0, r1)
         return r0, r1
 
+    def mul(a0, a1, b0, b1):
+        nonlocal cid, comm
+        T0, T1 = beaver_dealer(seed, cid, 0, a0.size)
+        cid += 1
+        z0, z1, cm = beaver_mul(T0, T1, a0, a1, b0, b1, 1)
+        comm = comm + cm
+        return z0, z1
+
     E0, E1 = gate("exp", x0 - m0[:, None], x1 - m1[:, None])
     E0, E1 = gate("shift_e", E0, E1)
     s0 = E0.reshape(rows, L).sum(axis=1, dtype=np.uint64)
     s1 = E1.reshape(rows, L).sum(axis=1, dtype=np.uint64)
     t0, t1 = gate("recip", s0, s1)
     t0, t1 = gate("shift_t", t0, t1)
+    steps["t_gate"] = (t0, t1)
+    for _ in range(newton):
+        u0, u1 = mul(s0, s1, t0, t1)
+        u0, u1 = gate("shift_n1", u0, u1)
+        v0, v1 = np.uint64(1 << 21) - u0, np.uint64(0) - u1
+        w0, w1 = mul(t0, t1, v0, v1)
+        t0, t1 = gate("shift_n2", w0, w1)
+    steps["t"] = (t0, t1)
     T0, T1 = beaver_dealer(seed, cid, 0, rows * L)
     cid += 1
     P0, P1, cm = beaver_mul(T0, T1, E0, E1, t0, t1, group=L)
@@ -113,7 +139,7 @@ def softmax_pair(g, seed, call_base, x0, x1):
     return Y0.reshape(rows, L), Y1.reshape(rows, L), comm, steps
 
 
-def softmax_plain(g, x):
+def softmax_plain(g, x, newton: int = 0):
     """The same pipeline on plaintext integers: each gate by its plaintext
     evaluator, the linear steps and the product in Z_{2^64}."""
     x = np.asarray(x, np.uint64)
@@ -137,9 +163,13 @@ def softmax_plain(g, x):
     E = ev("shift_e", ev("exp", x - m[:, None])).reshape(rows, L)
     s = E.sum(axis=1, dtype=np.uint64)
     t = ev("shift_t", ev("recip", s))
+    t_gate = t
+    for _ in range(newton):
+        u = ev("shift_n1", s * t)
+        t = ev("shift_n2", t * (np.uint64(1 << 21) - u))
     P = E * t[:, None]
     Y = ev("shift_p", P).reshape(rows, L)
-    return Y, dict(m=m, E=E, s=s, t=t, P=P)
+    return Y, dict(m=m, E=E, s=s, t=t, t_gate=t_gate, P=P)
 
 
 # --------------------------------------------------------------------------
@@ -153,13 +183,20 @@ def softmax_plain(g, x):
 #   3. Q = D * D                                     (Beaver, elementwise)
 #   4. var = shift_var(rowsum(Q) * c_H) + eps        (the variance at f bits)
 #   5. r = shift_r(rsqrt(var))
+#  5a. `newton` times, Newton's iteration r (3 - var r^2) / 2 for 1/sqrt(var)
+#      as a fixed post-processing circuit (Beaver products and shift gates;
+#      r at 20 bits, var at f): q = shift_n1(r * r) (r^2 at 20 bits),
+#      w = shift_n2(var * q) (var r^2 at 20 bits, ARS by f), z = 3 - w
+#      (party 0 adds the public 3 * 2^20, both negate), r = shift_n3(r * z)
+#      (ARS by 21: the product's 20 extra bits and the halving)
 #   6. Y = shift_y(D * r)                            (Beaver, r broadcast)
 # Products by the public c_H are local (each party scales its share); every
 # shift rounds to nearest as in the softmax block.  Dealer call ids:
 # call_base + j for the j-th drawing step (shift_mu, the square, shift_var,
-# rsqrt, shift_r, the product, shift_y).
+# rsqrt, shift_r, per Newton step r r, shift_n1, var q, shift_n2, r z,
+# shift_n3, then the product and shift_y).
 
-def layernorm_pair(g, seed, call_base, x0, x1, c_H: int, eps: int = 0):
+def layernorm_pair(g, seed, call_base, x0, x1, c_H: int, eps: int = 0, newton: int = 0):
     """Both parties' shares of the LayerNorm pipeline on shares x0, x1 [rows, H]."""
     x0 = np.asarray(x0, np.uint64)
     x1 = np.asarray(x1, np.uint64)
@@ -195,13 +232,20 @@ def layernorm_pair(g, seed, call_base, x0, x1, c_H: int, eps: int = 0):
     v0 = v0 + np.uint64(eps)
     r0, r1 = gate("rsqrt", v0, v1)
     r0, r1 = gate("shift_r", r0, r1)
+    steps["r_gate"] = (r0, r1)
+    for _ in range(newton):
+        q0, q1 = gate("shift_n1", *mul(r0, r1, r0, r1, 1))
+        w0, w1 = gate("shift_n2", *mul(v0, v1, q0, q1, 1))
+        z0, z1 = np.uint64(3 << 20) - w0, np.uint64(0) - w1
+        r0, r1 = gate("shift_n3", *mul(r0, r1, z0, z1, 1))
+    steps["r"] = (r0, r1)
     P0, P1 = mul(D0.reshape(-1), D1.reshape(-1), r0, r1, H)
     Y0, Y1 = gate("shift_y", P0, P1)
     steps.update(mu=(mu0, mu1), var=(v0, v1))
     return Y0.reshape(rows, H), Y1.reshape(rows, H), comm, steps
 
 
-def layernorm_plain(g, x, c_H: int, eps: int = 0):
+def layernorm_plain(g, x, c_H: int, eps: int = 0, newton: int = 0):
     """The same pipeline on plaintext integers."""
     x = np.asarray(x, np.uint64)
     rows, H = x.shape
@@ -217,5 +261,10 @@ def layernorm_plain(g, x, c_H: int, eps: int = 0):
     D = x - mu[:, None]
     var = ev("shift_var", (D * D).sum(axis=1, dtype=np.uint64) * cH) + np.uint64(eps)
     r = ev("shift_r", ev("rsqrt", var))
+    r_gate = r
+    for _ in range(newton):
+        q = ev("shift_n1", r * r)
+        w = ev("shift_n2", var * q)
+        r = ev("shift_n3", r * (np.uint64(3 << 20) - w))
     Y = ev("shift_y", D * r[:, None]).reshape(rows, H)
-    return Y, dict(mu=mu, var=var, r=r)
+    return Y, dict(mu=mu, var=var, r=r, r_gate=r_gate)

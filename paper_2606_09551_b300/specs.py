@@ -325,14 +325,19 @@ def softmax_specs(f: int = 12) -> Dict[str, OperatorSpec]:
     recip    1/x for inputs at 16 bits on a 28-bit view (octaves 2^-3 .. 2^11;
              a row sum of up to 2^11 ones), at its fitted scale F_r
     shift_t  ARS by F_r - 20 on a 63-bit view: t at 20 bits
-    shift_p  ARS by 24 on a 40-bit view: the product E t (36 bits, below 2^37) at 12 bits"""
+    shift_p  ARS by 24 on a 40-bit view: the product E t (36 bits, below 2^37) at 12 bits
+    shift_n1 ARS by 16 on a 40-bit view: s t (36 bits, about 2^36) at 20 bits
+    shift_n2 ARS by 20 on a 48-bit view: t (2 - s t) (40 bits, below 2^42) at 20 bits
+    (the last two only for the reciprocal's Newton refinement)"""
     exp = nexp16(f=f)
     recip = recip16(k=28, f=16)
     return {"relu": relu(24), "exp": exp,
             "shift_e": trunc(63, exp.out_frac_bits - 16, True, name=f"ars63_{exp.out_frac_bits - 16}"),
             "recip": recip,
             "shift_t": trunc(63, recip.out_frac_bits - 20, True, name=f"ars63_{recip.out_frac_bits - 20}"),
-            "shift_p": trunc(40, 16 + 20 - f, True, name=f"ars40_{16 + 20 - f}")}
+            "shift_p": trunc(40, 16 + 20 - f, True, name=f"ars40_{16 + 20 - f}"),
+            "shift_n1": trunc(40, 16, True, name="ars40_16"),
+            "shift_n2": trunc(48, 20, True, name="ars48_20")}
 
 
 def layernorm_specs(H: int, f: int = 12) -> Tuple[Dict[str, OperatorSpec], int]:
@@ -345,14 +350,21 @@ def layernorm_specs(H: int, f: int = 12) -> Tuple[Dict[str, OperatorSpec], int]:
     the normalised output at f bits.  The values stay inside the views
     while |x - mu| < 11 real units (the scaled sum of squares, about
     max|x - mu|^2 * 2^48, stays below 2^55) and the variance is at least 1/8
-    (the range of the rsqrt fit)."""
+    (the range of the rsqrt fit).  For the Newton refinement of 1/sqrt:
+    shift_n1 (ARS by 20, 48-bit view) for r^2 at 20 bits (r below 2^21.6,
+    r^2 below 2^44), shift_n2 (ARS by f, 48-bit view) for var r^2 at 20
+    bits (about 2^(20 + f)), shift_n3 (ARS by 21, 48-bit view) for
+    r (3 - var r^2) / 2 at 20 bits (below 2^43)."""
     rs = rsqrt16(f=f)
     c_H = int(round(2 ** 24 / H))
     return ({"shift_mu": trunc(48, 24, True, name="ars48_24"),
              "shift_var": trunc(56, 24 + f, True, name=f"ars56_{24 + f}"),
              "rsqrt": rs,
              "shift_r": trunc(63, rs.out_frac_bits - 20, True, name=f"ars63_{rs.out_frac_bits - 20}"),
-             "shift_y": trunc(48, 20, True, name="ars48_20")}, c_H)
+             "shift_y": trunc(48, 20, True, name="ars48_20"),
+             "shift_n1": trunc(48, 20, True, name="ars48_20"),
+             "shift_n2": trunc(48, f, True, name=f"ars48_{f}"),
+             "shift_n3": trunc(48, 21, True, name="ars48_21")}, c_H)
 
 
 def random_spec(rng: np.random.Generator, k: int, m: int, d: int, r: int = 1,
