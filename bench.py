@@ -807,6 +807,19 @@ def run_blocks(ctx, args, dev, stream, world):
                       "form": "comparison-tree max (ReLU gates), nExp, row sums, Recip, Beaver product, "
                               "rounding shift gates; one plan, keys dealt before each evaluation"}
     sm.close()
+    # the same block with one Newton step refining the reciprocal
+    ngates = [F.CompiledSpec(sp[k], ctx) for k in ("shift_n1", "shift_n2")]
+    if not args.no_autotune:
+        for g in ngates:
+            g.autotune()
+    smn = F.Softmax(ctx, gates, rows, L, newton_gates=ngates, newton=1)
+    ms_n, y_n, cb_n = timed(smn, S.encode(scores.reshape(-1), 12), rows * L, 2500)
+    aes_n = aes + aes_of(ngates, [rows, rows])
+    out["softmax_newton"] = {"value": aggregate(rows * L, ms_n, world), "unit": "elements/s", "ms_per_block": ms_n,
+                             "newton_steps": 1, "comm_bytes_per_party": cb_n,
+                             "aes_blocks": aes_n, "aes_roofline_frac": aes_n / (ms_n * 1e-3) / _aes_roofline(),
+                             "max_abs_err_vs_float64": float(np.abs(y_n.reshape(rows, L) - ref).max())}
+    smn.close()
     # LayerNorm
     rows, H = 128, 768
     lsp, cH = S.layernorm_specs(H)
@@ -829,6 +842,19 @@ def run_blocks(ctx, args, dev, stream, world):
                         "form": "row mean and variance by local sums, Beaver square, Rsqrt, Beaver product, "
                                 "rounding shift gates (no affine weights)"}
     ln.close()
+    # the same block with one Newton step refining 1/sqrt
+    ngates = [F.CompiledSpec(lsp[k], ctx) for k in ("shift_n1", "shift_n2", "shift_n3")]
+    if not args.no_autotune:
+        for g in ngates:
+            g.autotune()
+    lnn = F.LayerNorm(ctx, gates, rows, H, cH, newton_gates=ngates, newton=1)
+    ms_n, y_n, cb_n = timed(lnn, S.encode(hid.reshape(-1), 12), rows * H, 3500)
+    aes_n = aes + aes_of(ngates, [rows, rows, rows])
+    out["layernorm_newton"] = {"value": aggregate(rows * H, ms_n, world), "unit": "elements/s",
+                               "ms_per_block": ms_n, "newton_steps": 1, "comm_bytes_per_party": cb_n,
+                               "aes_blocks": aes_n, "aes_roofline_frac": aes_n / (ms_n * 1e-3) / _aes_roofline(),
+                               "max_abs_err_vs_float64": float(np.abs(y_n.reshape(rows, H) - ref).max())}
+    lnn.close()
     torch.cuda.empty_cache()
     return out
 

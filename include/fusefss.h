@@ -481,6 +481,20 @@ int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, 
 int ffss_softmax_info(const ffss_softmax *sm, uint32_t *rounds, uint64_t *key_bytes,
                       uint64_t *gate_elements);
 int ffss_softmax_destroy(ffss_softmax *sm);
+/* The same plan with `newton` (0..4) Newton steps refining the reciprocal
+ * after step 5, the fixed post-processing circuit of a specification-
+ * compatible Recip gate (Def. "specification-compatible scalar gate": a
+ * constant number of refinement steps of Beaver products and shifts).  With
+ * s at 16 and t at 20 fractional bits, each step computes
+ *   A = s * t (Beaver);  B = newton_gates[0](A + h);   (s t at 20 bits)
+ *   C = 2^21 - B (party 0 holds the constant);
+ *   A = t * C (Beaver);  t = newton_gates[1](A + h),   (t (2 - s t))
+ * which squares t's relative error.  Keys: the step's four draws follow
+ * gates 1..4 in order (product, gate, product, gate per step), then the
+ * final product and gate 5.  Both newton_gates must be shift gates. */
+int ffss_softmax_create_newton(ffss_ctx *ctx, const ffss_spec *const gates[6],
+                               const ffss_spec *const newton_gates[2], uint32_t newton, uint64_t rows,
+                               uint64_t L, ffss_softmax **out);
 
 /* LayerNorm over rows of H shared fixed-point values (App. G: mean and
  * variance are linear, 1/sqrt is a scalar gate), without the affine
@@ -503,6 +517,20 @@ int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *
                         uint64_t *y1, uint64_t *comm, void *stream);
 int ffss_layernorm_info(const ffss_layernorm *ln, uint64_t *key_bytes, uint64_t *gate_elements);
 int ffss_layernorm_destroy(ffss_layernorm *ln);
+/* The same plan with `newton` (0..4) Newton steps refining 1/sqrt(var)
+ * after step 5 (the fixed post-processing circuit of a specification-
+ * compatible Rsqrt gate).  With var at the input's f and r at 20
+ * fractional bits, each step computes
+ *   B = newton_gates[0](r * r + h)        (r^2 at 20 bits);
+ *   B = newton_gates[1](var * B + h)      (var r^2 at 20 bits);
+ *   C = 3 * 2^20 - B (party 0 holds the constant);
+ *   r = newton_gates[2](r * C + h)        (r (3 - var r^2) / 2: a shift by 21),
+ * three Beaver products and three shift gates.  Keys: per step (product,
+ * gate) x 3 after gates[3], then the final product and gates[4].  All three
+ * newton_gates must be shift gates. */
+int ffss_layernorm_create_newton(ffss_ctx *ctx, const ffss_spec *const gates[5],
+                                 const ffss_spec *const newton_gates[3], uint32_t newton, uint64_t rows,
+                                 uint64_t H, uint64_t c_H, uint64_t eps, ffss_layernorm **out);
 
 /* ---- measurement support ------------------------------------------------ */
 

@@ -152,6 +152,16 @@ __global__ void add_const_kernel(uint64_t *x0, uint64_t n, uint64_t c) {
     x0[i] += c;
 }
 
+// o = c - x: party 0 holds c - x_0, party 1 -x_1 (the constant term of a
+// Newton step, 2 - s t or 3 - v r^2).
+__global__ void const_sub_kernel(const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t c, uint64_t *o0,
+                                 uint64_t *o1) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    o0[i] = c - x0[i];
+    o1[i] = 0 - x1[i];
+  }
+}
+
 }  // namespace ffss
 
 // ---------------------------------------------------------------------------
@@ -210,13 +220,16 @@ enum { kSmRelu, kSmExp, kSmShiftE, kSmRecip, kSmShiftT, kSmShiftP, kSmGates };
 struct ffss_softmax {
   ffss_ctx *ctx;
   const ffss_spec *g[kSmGates];
+  const ffss_spec *gn[2];          // Newton refinement's shift gates (s t, then t (2 - s t))
+  uint32_t newton;                 // refinement steps of the reciprocal
   uint64_t rows, L;
   std::vector<uint64_t> tn;        // values per row entering each tree round
   struct Step {
     const ffss_spec *spec;         // nullptr: the Beaver multiplication
     uint64_t n, off0, off1;        // elements; key offsets of party 0 and 1 in `keys`
   };
-  std::vector<Step> steps;         // tree rounds, exp, shift_e, recip, shift_t, product, shift_p
+  std::vector<Step> steps;         // tree rounds, exp, shift_e, recip, shift_t, per Newton step
+                                   // (product s t, shift_n1, product t v, shift_n2), product, shift_p
   char *keys;
   uint64_t key_bytes;
   uint64_t *sh;                    // share scratch (see ffss_softmax_create)
@@ -234,9 +247,16 @@ extern "C" int ffss_softmax_destroy(ffss_softmax *sm) {
   return FFSS_OK;
 }
 
-extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], uint64_t rows, uint64_t L,
-                                   ffss_softmax **out) {
+static int softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], const ffss_spec *const newton_gates[2],
+                          uint32_t newton, uint64_t rows, uint64_t L, ffss_softmax **out) {
   if (!ctx || !gates || !out) return fail(FFSS_ERR_INVALID, "ffss_softmax_create: NULL argument");
+  if (newton > 4) return fail(FFSS_ERR_INVALID, "ffss_softmax_create_newton: at most 4 refinement steps");
+  for (int i = 0; i < 2 && newton; ++i) {
+    if (!newton_gates || !newton_gates[i]) return fail(FFSS_ERR_INVALID, "ffss_softmax_create_newton: NULL gate");
+    if (int rc = check_device_spec(ctx, newton_gates[i])) return rc;
+    if (newton_gates[i]->host.r != 1 || newton_gates[i]->host.trunc_s == 0)
+      return fail(FFSS_ERR_SHAPE, "ffss_softmax_create_newton: Newton gate %d must be a shift gate", i);
+  }
   if (rows == 0 || L == 0) return fail(FFSS_ERR_SHAPE, "ffss_softmax_create: rows and L must be >= 1");
   for (int i = 0; i < kSmGates; ++i) {
     if (!gates[i]) return fail(FFSS_ERR_INVALID, "ffss_softmax_create: gate %d is NULL", i);
@@ -249,6 +269,8 @@ extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6
   ffss_softmax *sm = new ffss_softmax();
   sm->ctx = ctx;
   for (int i = 0; i < kSmGates; ++i) sm->g[i] = gates[i];
+  sm->newton = newton;
+  for (int i = 0; i < 2; ++i) sm->gn[i] = newton ? newton_gates[i] : nullptr;
   sm->rows = rows;
   sm->L = L;
   for (uint64_t n = L; n > 1; n = n / 2 + n % 2) sm->tn.push_back(n);
@@ -264,13 +286,19 @@ extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6
   add(gates[kSmShiftE], N);
   add(gates[kSmRecip], rows);
   add(gates[kSmShiftT], rows);
+  for (uint32_t it = 0; it < newton; ++it) {
+    add(nullptr, rows);
+    add(newton_gates[0], rows);
+    add(nullptr, rows);
+    add(newton_gates[1], rows);
+  }
   add(nullptr, N);
   add(gates[kSmShiftP], N);
   sm->key_bytes = off;
   // share scratch, both parties (the carve-up of ffss_softmax_eval): tree
   // ping-pong 2 x N, differences and ReLU outputs N / 2 + 1 each (h <= L / 2),
-  // D, E, E' and P N each, s, t, t' rows each
-  const uint64_t words = 2 * (2 * N + 2 * (N / 2 + 1) + 4 * N + 3 * rows);
+  // D, E, E' and P N each, s, t, t' and three Newton temporaries rows each
+  const uint64_t words = 2 * (2 * N + 2 * (N / 2 + 1) + 4 * N + 6 * rows);
   cudaError_t e = cudaMalloc(&sm->keys, sm->key_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&sm->sh, words * 8);
   if (e == cudaSuccess) e = cudaMalloc(&sm->z, 2 * N * 4);
@@ -280,6 +308,17 @@ extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6
   }
   *out = sm;
   return FFSS_OK;
+}
+
+extern "C" int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], uint64_t rows, uint64_t L,
+                                   ffss_softmax **out) {
+  return softmax_create(ctx, gates, nullptr, 0, rows, L, out);
+}
+
+extern "C" int ffss_softmax_create_newton(ffss_ctx *ctx, const ffss_spec *const gates[6],
+                                          const ffss_spec *const newton_gates[2], uint32_t newton, uint64_t rows,
+                                          uint64_t L, ffss_softmax **out) {
+  return softmax_create(ctx, gates, newton_gates, newton, rows, L, out);
 }
 
 extern "C" int ffss_softmax_info(const ffss_softmax *sm, uint32_t *rounds, uint64_t *key_bytes,
@@ -335,6 +374,8 @@ extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uin
   uint64_t *F0 = take(N), *F1 = take(N), *P0 = take(N), *P1 = take(N);
   uint64_t *s0 = take(rows), *s1 = take(rows), *t0 = take(rows), *t1 = take(rows);
   uint64_t *u0 = take(rows), *u1 = take(rows);
+  uint64_t *nA0 = take(rows), *nA1 = take(rows), *nB0 = take(rows), *nB1 = take(rows);
+  uint64_t *nC0 = take(rows), *nC1 = take(rows);
   uint32_t *z0 = sm->z, *z1 = sm->z + N;
   const int TB = 256;
   size_t j = 0;
@@ -366,14 +407,28 @@ extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uin
   if (int rc = gate(s0, s1, t0, t1)) return rc;
   add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(t0, rows, half(kSmShiftT));
   if (int rc = gate(t0, t1, u0, u1)) return rc;
-  // (6) P = E' * t' (t' broadcast over the row); (7) Y = shift_p(P + half)
-  {
+  // (5a) Newton steps t' <- t' (2 - s t') (s at 16, t' at 20 bits):
+  // A = s t'; B = shift_n1(A + half) (s t' at 20 bits); C = 2^21 - B;
+  // A = t' C; t' = shift_n2(A + half)
+  auto nhalf = [&](int g) { return uint64_t(1) << (sm->gn[g]->host.trunc_s - 1); };
+  auto mul = [&](const uint64_t *a0, const uint64_t *a1, const uint64_t *b0, const uint64_t *b1, uint64_t n,
+                 uint64_t group, uint64_t *o0, uint64_t *o1) {
     const auto &s = sm->steps[j++];
-    if (int rc = beaver_mul_raw(ctx, reinterpret_cast<const uint64_t *>(sm->keys + s.off0),
-                                reinterpret_cast<const uint64_t *>(sm->keys + s.off1), F0, F1, u0, u1, N, L, P0,
-                                P1, comm, st))
-      return rc;
+    return beaver_mul_raw(ctx, reinterpret_cast<const uint64_t *>(sm->keys + s.off0),
+                          reinterpret_cast<const uint64_t *>(sm->keys + s.off1), a0, a1, b0, b1, n, group, o0, o1,
+                          comm, st);
+  };
+  for (uint32_t it = 0; it < sm->newton; ++it) {
+    if (int rc = mul(s0, s1, u0, u1, rows, 1, nA0, nA1)) return rc;
+    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(0));
+    if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
+    const_sub_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nB0, nB1, rows, uint64_t(1) << 21, nC0, nC1);
+    if (int rc = mul(u0, u1, nC0, nC1, rows, 1, nA0, nA1)) return rc;
+    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(1));
+    if (int rc = gate(nA0, nA1, u0, u1)) return rc;
   }
+  // (6) P = E' * t' (t' broadcast over the row); (7) Y = shift_p(P + half)
+  if (int rc = mul(F0, F1, u0, u1, N, L, P0, P1)) return rc;
   add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kSmShiftP));
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
@@ -390,12 +445,15 @@ enum { kLnShiftMu, kLnShiftVar, kLnRsqrt, kLnShiftR, kLnShiftY, kLnGates };
 struct ffss_layernorm {
   ffss_ctx *ctx;
   const ffss_spec *g[kLnGates];
+  const ffss_spec *gn[3];            // Newton refinement's shift gates (r^2, v r^2, r (3 - v r^2) / 2)
+  uint32_t newton;                   // refinement steps of 1/sqrt
   uint64_t rows, H, c_H, eps;
   struct Step {
     const ffss_spec *spec;           // nullptr: a Beaver multiplication
     uint64_t n, off0, off1;
   };
-  std::vector<Step> steps;           // shift_mu, square, shift_var, rsqrt, shift_r, product, shift_y
+  std::vector<Step> steps;           // shift_mu, square, shift_var, rsqrt, shift_r, per Newton step
+                                     // (r r, shift_n1, v q, shift_n2, r z, shift_n3), product, shift_y
   char *keys;
   uint64_t key_bytes;
   uint64_t *sh;
@@ -413,9 +471,17 @@ extern "C" int ffss_layernorm_destroy(ffss_layernorm *ln) {
   return FFSS_OK;
 }
 
-extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], uint64_t rows, uint64_t H,
-                                     uint64_t c_H, uint64_t eps, ffss_layernorm **out) {
+static int layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], const ffss_spec *const newton_gates[3],
+                            uint32_t newton, uint64_t rows, uint64_t H, uint64_t c_H, uint64_t eps,
+                            ffss_layernorm **out) {
   if (!ctx || !gates || !out) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create: NULL argument");
+  if (newton > 4) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create_newton: at most 4 refinement steps");
+  for (int i = 0; i < 3 && newton; ++i) {
+    if (!newton_gates || !newton_gates[i]) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create_newton: NULL gate");
+    if (int rc = check_device_spec(ctx, newton_gates[i])) return rc;
+    if (newton_gates[i]->host.r != 1 || newton_gates[i]->host.trunc_s == 0)
+      return fail(FFSS_ERR_SHAPE, "ffss_layernorm_create_newton: Newton gate %d must be a shift gate", i);
+  }
   if (rows == 0 || H == 0) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_create: rows and H must be >= 1");
   for (int i = 0; i < kLnGates; ++i) {
     if (!gates[i]) return fail(FFSS_ERR_INVALID, "ffss_layernorm_create: gate %d is NULL", i);
@@ -428,6 +494,8 @@ extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates
   ffss_layernorm *ln = new ffss_layernorm();
   ln->ctx = ctx;
   for (int i = 0; i < kLnGates; ++i) ln->g[i] = gates[i];
+  ln->newton = newton;
+  for (int i = 0; i < 3; ++i) ln->gn[i] = newton ? newton_gates[i] : nullptr;
   ln->rows = rows; ln->H = H; ln->c_H = c_H; ln->eps = eps;
   const uint64_t N = rows * H;
   uint64_t off = 0;
@@ -441,12 +509,17 @@ extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates
   add(gates[kLnShiftVar], rows);
   add(gates[kLnRsqrt], rows);
   add(gates[kLnShiftR], rows);
+  for (uint32_t it = 0; it < newton; ++it)
+    for (int i = 0; i < 3; ++i) {
+      add(nullptr, rows);
+      add(newton_gates[i], rows);
+    }
   add(nullptr, N);
   add(gates[kLnShiftY], N);
   ln->key_bytes = off;
   // scratch, both parties (the carve-up of ffss_layernorm_eval): D, Q, P N each;
-  // sums and the per-row chain 6 x rows
-  const uint64_t words = 2 * (3 * N + 6 * rows);
+  // sums and the per-row chain 6 x rows, three Newton temporaries rows each
+  const uint64_t words = 2 * (3 * N + 9 * rows);
   cudaError_t e = cudaMalloc(&ln->keys, ln->key_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&ln->sh, words * 8);
   if (e == cudaSuccess) e = cudaMalloc(&ln->z, 2 * N * 4);
@@ -456,6 +529,17 @@ extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates
   }
   *out = ln;
   return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], uint64_t rows, uint64_t H,
+                                     uint64_t c_H, uint64_t eps, ffss_layernorm **out) {
+  return layernorm_create(ctx, gates, nullptr, 0, rows, H, c_H, eps, out);
+}
+
+extern "C" int ffss_layernorm_create_newton(ffss_ctx *ctx, const ffss_spec *const gates[5],
+                                            const ffss_spec *const newton_gates[3], uint32_t newton, uint64_t rows,
+                                            uint64_t H, uint64_t c_H, uint64_t eps, ffss_layernorm **out) {
+  return layernorm_create(ctx, gates, newton_gates, newton, rows, H, c_H, eps, out);
 }
 
 extern "C" int ffss_layernorm_info(const ffss_layernorm *ln, uint64_t *key_bytes, uint64_t *gate_elements) {
@@ -503,6 +587,8 @@ extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const
   uint64_t *a0 = take(rows), *a1 = take(rows), *m0 = take(rows), *m1 = take(rows);
   uint64_t *v0 = take(rows), *v1 = take(rows), *w0 = take(rows), *w1 = take(rows);
   uint64_t *q0 = take(rows), *q1 = take(rows), *r0 = take(rows), *r1 = take(rows);
+  uint64_t *nA0 = take(rows), *nA1 = take(rows), *nB0 = take(rows), *nB1 = take(rows);
+  uint64_t *nC0 = take(rows), *nC1 = take(rows);
   uint32_t *z0 = ln->z, *z1 = ln->z + N;
   const int TB = 256;
   size_t j = 0;
@@ -534,6 +620,22 @@ extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const
   if (int rc = gate(w0, w1, q0, q1)) return rc;
   add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(q0, rows, half(kLnShiftR));
   if (int rc = gate(q0, q1, r0, r1)) return rc;
+  // (5a) Newton steps r <- r (3 - v r^2) / 2 (v = w at f bits, r at 20):
+  // B = shift_n1(r r + half) (r^2 at 20 bits); B = shift_n2(v B + half)
+  // (v r^2 at 20 bits); C = 3 * 2^20 - B; r = shift_n3(r C + half)
+  auto nhalf = [&](int g) { return uint64_t(1) << (ln->gn[g]->host.trunc_s - 1); };
+  for (uint32_t it = 0; it < ln->newton; ++it) {
+    if (int rc = mul(r0, r1, r0, r1, 1, nA0, nA1)) return rc;
+    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(0));
+    if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
+    if (int rc = mul(w0, w1, nB0, nB1, 1, nA0, nA1)) return rc;
+    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(1));
+    if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
+    const_sub_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nB0, nB1, rows, uint64_t(3) << 20, nC0, nC1);
+    if (int rc = mul(r0, r1, nC0, nC1, 1, nA0, nA1)) return rc;
+    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(2));
+    if (int rc = gate(nA0, nA1, r0, r1)) return rc;
+  }
   // (6) Y = shift_y(D * r + half), r broadcast over the row
   if (int rc = mul(D0, D1, r0, r1, H, P0, P1)) return rc;
   add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kLnShiftY));

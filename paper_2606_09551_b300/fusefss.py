@@ -159,6 +159,10 @@ def lib():
         L.ffss_beaver_keygen.argtypes = [vp, C.POINTER(C.c_uint8), C.c_uint32, C.c_uint64, vp, vp, vp]
         L.ffss_beaver_mul.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_uint64, C.c_uint64, vp, vp, vp, vp]
         L.ffss_softmax_create.argtypes = [vp, C.POINTER(vp), C.c_uint64, C.c_uint64, C.POINTER(vp)]
+        L.ffss_softmax_create_newton.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_uint32, C.c_uint64,
+                                                 C.c_uint64, C.POINTER(vp)]
+        L.ffss_layernorm_create_newton.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_uint32, C.c_uint64,
+                                                   C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(vp)]
         L.ffss_softmax_keygen.argtypes = [vp, C.POINTER(C.c_uint8), C.c_uint32, vp]
         L.ffss_softmax_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.ffss_softmax_info.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
@@ -470,14 +474,21 @@ def beaver_mul(ctx: Context, t0, t1, x0, x1, y0, y1, z0, z1, group: int = 1, com
 class Softmax:
     """The softmax block over rows of shared values (plan with its own keys
     and scratch).  gates: CompiledSpecs for relu, exp, shift_e, recip,
-    shift_t, shift_p (in that order)."""
+    shift_t, shift_p (in that order); with newton > 0, newton_gates are the
+    two shift gates of each Newton step of the reciprocal."""
 
-    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, L: int):
+    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, L: int,
+                 newton_gates: Sequence["CompiledSpec"] = (), newton: int = 0):
         self.ctx, self.rows, self.L = ctx, rows, L
         self._gates = list(gates)
         arr = (vp * 6)(*[g.h for g in self._gates])
         h = vp()
-        _check(lib().ffss_softmax_create(ctx.h, arr, rows, L, C.byref(h)))
+        if newton:
+            self._ngates = list(newton_gates)
+            narr = (vp * 2)(*[g.h for g in self._ngates])
+            _check(lib().ffss_softmax_create_newton(ctx.h, arr, narr, newton, rows, L, C.byref(h)))
+        else:
+            _check(lib().ffss_softmax_create(ctx.h, arr, rows, L, C.byref(h)))
         self.h = h
 
     def keygen(self, seed: bytes, call_base: int, stream=None):
@@ -506,14 +517,22 @@ class Softmax:
 class LayerNorm:
     """The LayerNorm block over rows of H shared values (plan with its own
     keys and scratch).  gates: CompiledSpecs for shift_mu, shift_var, rsqrt,
-    shift_r, shift_y (in that order); c_H = round(2^s_mu / H)."""
+    shift_r, shift_y (in that order); c_H = round(2^s_mu / H); with
+    newton > 0, newton_gates are the three shift gates of each Newton step
+    of 1/sqrt."""
 
-    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, H: int, c_H: int, eps: int = 0):
+    def __init__(self, ctx: Context, gates: Sequence["CompiledSpec"], rows: int, H: int, c_H: int, eps: int = 0,
+                 newton_gates: Sequence["CompiledSpec"] = (), newton: int = 0):
         self.ctx, self.rows, self.H = ctx, rows, H
         self._gates = list(gates)
         arr = (vp * 5)(*[g.h for g in self._gates])
         h = vp()
-        _check(lib().ffss_layernorm_create(ctx.h, arr, rows, H, c_H, eps, C.byref(h)))
+        if newton:
+            self._ngates = list(newton_gates)
+            narr = (vp * 3)(*[g.h for g in self._ngates])
+            _check(lib().ffss_layernorm_create_newton(ctx.h, arr, narr, newton, rows, H, c_H, eps, C.byref(h)))
+        else:
+            _check(lib().ffss_layernorm_create(ctx.h, arr, rows, H, c_H, eps, C.byref(h)))
         self.h = h
 
     def keygen(self, seed: bytes, call_base: int, stream=None):

@@ -127,3 +127,69 @@ def test_layernorm_matches_oracle(ctx, rows, H):
     with pytest.raises(F.FfssError):
         ln.eval(X0, X1, Y0, Y1)
     ln.close()
+
+
+@pytest.mark.parametrize("rows,L,newton", [(5, 7, 1), (12, 128, 2)])
+def test_softmax_newton_matches_oracle(ctx, rows, L, newton):
+    """With Newton steps refining the reciprocal: shares bit-exact to the
+    oracle's composition with the same steps, bytes equal, reconstruction
+    equal to the plaintext pipeline."""
+    import torch
+    gates, og = _softmax_gates(ctx)
+    sp = S.softmax_specs()
+    ngates = [F.CompiledSpec(sp[k], ctx) for k in ("shift_n1", "shift_n2")]
+    og.update({k: O.Spec(**sp[k].descriptor()) for k in ("shift_n1", "shift_n2")})
+    rng = np.random.default_rng(rows * 77 + L)
+    g = 2.0 * rng.standard_normal((rows, L))
+    x = S.encode(g.reshape(-1), 12).reshape(rows, L)
+    x0 = rng.integers(0, 2 ** 64, size=(rows, L), dtype=np.uint64)
+    sm = F.Softmax(ctx, gates, rows, L, newton_gates=ngates, newton=newton)
+    sm.keygen(SEED, 1700)
+    dev = "cuda:0"
+    X0, X1 = torch.from_numpy(x0.reshape(-1)).to(dev), torch.from_numpy((x - x0).reshape(-1)).to(dev)
+    Y0 = torch.empty(rows * L, dtype=torch.uint64, device=dev)
+    Y1 = torch.empty_like(Y0)
+    comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+    sm.eval(X0, X1, Y0, Y1, comm)
+    torch.cuda.synchronize()
+    r0, r1, rcomm, _ = OC.softmax_pair(og, SEED, 1700, x0, x - x0, newton=newton)
+    assert np.array_equal(Y0.cpu().numpy(), r0.reshape(-1))
+    assert np.array_equal(Y1.cpu().numpy(), r1.reshape(-1))
+    assert list(comm.cpu().numpy()) == list(rcomm)
+    yp, _ = OC.softmax_plain(og, x, newton=newton)
+    assert np.array_equal(Y0.cpu().numpy() + Y1.cpu().numpy(), yp.reshape(-1))
+    sm.close()
+    with pytest.raises(F.FfssError):      # a Newton gate must be a shift gate
+        F.Softmax(ctx, gates, rows, L, newton_gates=[gates[1], ngates[1]], newton=1)
+
+
+@pytest.mark.parametrize("rows,H,newton", [(4, 5, 1), (16, 768, 1)])
+def test_layernorm_newton_matches_oracle(ctx, rows, H, newton):
+    import torch
+    sp, cH = S.layernorm_specs(H)
+    order = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
+    norder = ["shift_n1", "shift_n2", "shift_n3"]
+    gates = [F.CompiledSpec(sp[k], ctx) for k in order]
+    ngates = [F.CompiledSpec(sp[k], ctx) for k in norder]
+    og = {k: O.Spec(**sp[k].descriptor()) for k in order + norder}
+    rng = np.random.default_rng(rows * 37 + H)
+    h = 1.3 * rng.standard_normal((rows, H)) + 0.4
+    x = S.encode(h.reshape(-1), 12).reshape(rows, H)
+    x0 = rng.integers(0, 2 ** 64, size=(rows, H), dtype=np.uint64)
+    eps = 41
+    ln = F.LayerNorm(ctx, gates, rows, H, cH, eps, newton_gates=ngates, newton=newton)
+    ln.keygen(SEED, 1800)
+    dev = "cuda:0"
+    X0, X1 = torch.from_numpy(x0.reshape(-1)).to(dev), torch.from_numpy((x - x0).reshape(-1)).to(dev)
+    Y0 = torch.empty(rows * H, dtype=torch.uint64, device=dev)
+    Y1 = torch.empty_like(Y0)
+    comm = torch.zeros(2, dtype=torch.uint64, device=dev)
+    ln.eval(X0, X1, Y0, Y1, comm)
+    torch.cuda.synchronize()
+    r0, r1, rcomm, _ = OC.layernorm_pair(og, SEED, 1800, x0, x - x0, cH, eps, newton=newton)
+    assert np.array_equal(Y0.cpu().numpy(), r0.reshape(-1))
+    assert np.array_equal(Y1.cpu().numpy(), r1.reshape(-1))
+    assert list(comm.cpu().numpy()) == list(rcomm)
+    yp, _ = OC.layernorm_plain(og, x, cH, eps, newton=newton)
+    assert np.array_equal(Y0.cpu().numpy() + Y1.cpu().numpy(), yp.reshape(-1))
+    ln.close()
