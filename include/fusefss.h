@@ -292,7 +292,10 @@ typedef struct {
  * slots).  ffss_ctx_set_slots and ffss_batch_set_slots still override it.
  * Allocates (cudaMalloc) and frees the sample buffers, and synchronizes the
  * stream.  Results never depend on the split.  out may be NULL.
- * Errors: FFSS_ERR_INVALID, FFSS_ERR_CUDA. */
+ * Errors: FFSS_ERR_INVALID, FFSS_ERR_CUDA, FFSS_ERR_BUDGET (the samples'
+ * keys, about 3 x SMs x 256 x key_bytes_per_elem x 2 bytes, would take more
+ * than half of the free device memory; nothing is allocated and the spec
+ * keeps the cost model). */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 
 /* The work split (slots per element) the fused gate of `spec` uses for a call

@@ -837,6 +837,14 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
   // the launch's fixed cost.
   TuneSample A, B;
   const uint64_t na = uint64_t(ctx->sm_count) * 256;
+  // both samples' keys (both parties) and share buffers must fit in half of
+  // the free device memory, or the tuner declines before allocating
+  const uint64_t need = 2 * (make_layout(S, na).total + make_layout(S, 2 * na).total) + 3 * na * (40 + 16ull * S.r);
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (need > free_b / 2)
+    return fail(FFSS_ERR_BUDGET, "ffss_autotune: the tuning samples need %llu MB, more than half of the %llu MB free",
+                (unsigned long long)(need >> 20), (unsigned long long)(free_b >> 20));
   CUDA_TRY(A.alloc(spec, na));
   CUDA_TRY(B.alloc(spec, 2 * na));
   // Throw-away keys: a fixed tuning seed and call ids no real call uses.
