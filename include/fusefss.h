@@ -193,9 +193,11 @@ const char *ffss_last_error(void);
 
 /* Work split of the fused gate (library tuning knob, no counterpart in the
  * paper): each element's T + M - 1 DCF walks are spread over `slots` threads
- * (1, 2, 4, 8 or 16; tiles hold 256 / slots elements).  0 (the default) lets
- * the library choose per call from a waves x slowest-slot cost model.
- * Results do not depend on it.  Errors: FFSS_ERR_INVALID. */
+ * (1, 2, 4, 8 or 16; tiles hold 256 / slots elements), in the plain and the
+ * batched form (a batch plan's own ffss_batch_set_slots takes precedence).
+ * 0 (the default) lets the library choose per call: the measured model of
+ * ffss_autotune once the spec is tuned, else a waves x slowest-slot cost
+ * model.  Results do not depend on it.  Errors: FFSS_ERR_INVALID. */
 int ffss_ctx_set_slots(ffss_ctx *ctx, uint32_t slots);
 
 /* ---- specifications ------------------------------------------------------ */

@@ -1016,14 +1016,14 @@ extern "C" int ffss_batch_set_slots(ffss_batch *bt, uint32_t slots) {
   return FFSS_OK;
 }
 
-// The split of a batched call of n elements: forced by the plan, else the
-// split the plain gate would take for the call (the tuned waves model: a
-// split with the least time per element but tiles of a millisecond leaves
-// the persistent CTAs a long tail), else 8.
+// The split of a batched call of n elements: forced by the plan, else by the
+// context, else the split the plain gate would take for the call (the tuned
+// waves model: a split with the least time per element but tiles of a
+// millisecond leaves the persistent CTAs a long tail), else 8.
 static uint32_t batch_slots(const ffss_batch *bt, const ffss_spec *spec, uint64_t n) {
   const DevSpec &S = spec->host;
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
-  if (!bt->force_slots && spec->tuned) return gate_slots(bt->ctx, spec, n);
+  if (!bt->force_slots && (bt->ctx->force_slots || spec->tuned)) return gate_slots(bt->ctx, spec, n);
   uint32_t want = bt->force_slots ? bt->force_slots : 8;
   uint32_t s = 1;
   while (s * 2 <= want && s * 2 <= (nitems ? nitems : 1)) s *= 2;
