@@ -297,7 +297,8 @@ typedef struct {
  * Errors: FFSS_ERR_INVALID, FFSS_ERR_CUDA, FFSS_ERR_BUDGET (the samples'
  * keys, about 3 x SMs x 256 x key_bytes_per_elem x 2 bytes, would take more
  * than half of the free device memory; nothing is allocated and the spec
- * keeps the cost model). */
+ * keeps the cost model).  The call writes the spec's tuning record: it must
+ * not run concurrently with another host thread's call on the same spec. */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 
 /* The work split (slots per element) the fused gate of `spec` uses for a call
