@@ -59,7 +59,11 @@ def _gate(ctx, cs, sp, x, call_id, batch=None):
             "z0": z0.cpu().numpy(), "z1": z1.cpu().numpy()}
 
 
-@pytest.mark.parametrize("sp", [S.gelu4(), S.nexp16(), S.trunc(32, 12, True)], ids=["gelu4", "nexp16", "ars32"])
+_TUNE_SPECS = [S.gelu4(), S.nexp16(), S.trunc(32, 12, True), S.gelu8().variant(True),
+               S.random_formulas(np.random.default_rng(12), S.gelu4(), 2)]
+
+
+@pytest.mark.parametrize("sp", _TUNE_SPECS, ids=["gelu4", "nexp16", "ars32", "gelu8_xhat", "gelu4_formulas"])
 def test_autotune_model_and_parity(ctx, sp):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count

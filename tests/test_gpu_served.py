@@ -129,3 +129,30 @@ def test_short_layers_go_first(ctx):
         si = sv.request_info(s)
         assert si["state"] == 2 and si["done_ms"] < long_first_layer_done
     sv.close()
+
+
+def test_tuned_specs_same_shares(ctx):
+    """With tuned specs the server's batched launches take the measured
+    splits; a request's shares still equal the plain launch's with the same
+    dealer call ids (the split never changes a share)."""
+    import torch
+    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    for cs in css:
+        cs.autotune()
+    sv = F.Server(ctx, 64 << 20, 2, 1500, I.KEY_SEED)
+    reqs = [_request(ctx, css, sz, 90 + i) for i, sz in enumerate([[3000, 700], [128, 2100]])]
+    for i, r in enumerate(reqs):
+        sv.submit(r, 0.0, call_id_base=900 + 50 * i)
+    sv.run()
+    sv.close()
+    for i, r in enumerate(reqs):
+        for li, layer in enumerate(r):
+            for j, (cs, x, y0, y1, z0, z1) in enumerate(layer):
+                n = x.numel()
+                k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
+                x0, x1 = torch.empty_like(x), torch.empty_like(x)
+                F.keygen(ctx, cs, I.KEY_SEED, 900 + 50 * i + li * 2 + j, n, k0, k1, x, x0, x1)
+                p0, p1 = torch.empty_like(y0), torch.empty_like(y1)
+                q0, q1 = torch.empty_like(z0), torch.empty_like(z1)
+                F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
+                assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)
