@@ -890,9 +890,12 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
               reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
 }
 
-// 384 threads per CTA: 168 registers per thread keep a key's running state
-// out of local memory around the out-of-line AES calls.
-constexpr uint32_t kKeygenThreads = 384;
+// 256 threads per CTA: up to 255 registers per thread keep a key's running
+// state out of local memory around the out-of-line AES calls (no spills).
+// Measured on the BERT-base layer's dealer: 47.8 ms against 48.4-49.5 ms at
+// 384 threads (168 registers, small spills for p = 4), 60.4 ms at 320 and
+// 52-58 ms at 448 / 512 (128 registers).
+constexpr uint32_t kKeygenThreads = 256;
 
 template <int P>
 __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_constant__ KeygenArgs A) {
