@@ -894,7 +894,7 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
 // state out of local memory around the out-of-line AES calls (no spills).
 // Measured on the BERT-base layer's dealer: 47.8 ms against 48.4-49.5 ms at
 // 384 threads (168 registers, small spills for p = 4), 60.4 ms at 320 and
-// 52-58 ms at 448 / 512 (128 registers).
+// 58-59 ms at 448 / 512 (128 registers).
 constexpr uint32_t kKeygenThreads = 256;
 
 template <int P>
