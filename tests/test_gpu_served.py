@@ -156,3 +156,53 @@ def test_tuned_specs_same_shares(ctx):
                 q0, q1 = torch.empty_like(z0), torch.empty_like(z1)
                 F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
                 assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)
+
+
+def test_full_size_streamed_large_layer(ctx):
+    """The GPT-style 2.7B layer (SiLU 1024 x 10240, nExp 32 x 1024 x 1024,
+    recip 32 x 1024, rsqrt 2 x 1024; k = 24, f = 16) at full size, in the
+    launch configuration the benchmark times: tuned specs, the server with a
+    64 GB key pool and chunks of at most 4 M elements, keys dealt on the
+    device per chunk.  Shares of sampled elements equal the oracle's for that
+    element of the call (its dealer counter uses the element's index in the
+    call); reconstructions of a large sample equal the plaintext spec."""
+    import torch
+    f = 16
+    specs = {"silu": S.silu16(f=f), "exp": S.nexp16(f=f), "recip": S.recip16(f=f), "rsqrt": S.rsqrt16(f=f)}
+    sizes = {"silu": 1024 * 10240, "exp": 32 * 1024 * 1024, "recip": 32 * 1024, "rsqrt": 2 * 1024}
+    rng = np.random.default_rng(2027)
+    ops, xs = [], {}
+    for name in ("silu", "exp", "recip", "rsqrt"):
+        cs = F.CompiledSpec(specs[name], ctx)
+        cs.autotune()
+        x = I.uniform_x(sizes[name], specs[name].k, 4000 + len(ops))
+        xs[name] = x
+        xd = torch.from_numpy(x).cuda()
+        y = torch.empty(x.size, dtype=torch.uint64, device="cuda:0")
+        z = torch.empty(x.size, dtype=torch.uint32, device="cuda:0")
+        ops.append((cs, xd, y, torch.empty_like(y), z, torch.empty_like(z)))
+    sv = F.Server(ctx, 64 << 30, 1, 1 << 22, I.KEY_SEED)
+    sv.submit([ops], 0.0, call_id_base=50000)
+    sv.run()
+    st = sv.summary()
+    sv.close()
+    assert st["elements"] == sum(sizes.values()) and st["chunks"] > st["steps"] > 1
+    for i, (name, (cs, xd, y0, y1, z0, z1)) in enumerate(zip(xs, ops)):
+        x = xs[name]
+        o = O.Spec(**specs[name].descriptor())
+        pick = np.unique(np.concatenate([[0, x.size - 1], rng.integers(0, x.size, 20000)]))
+        at = torch.from_numpy(pick.astype(np.int64)).cuda()
+        g = {k: t.view(torch.int32 if t.dtype == torch.uint32 else torch.int64)[at].cpu().numpy()
+             for k, t in (("y0", y0), ("y1", y1), ("z0", z0), ("z1", z1))}
+        g["y0"], g["y1"] = g["y0"].view(np.uint64), g["y1"].view(np.uint64)
+        g["z0"], g["z1"] = g["z0"].view(np.uint32), g["z1"].view(np.uint32)
+        yp, zp = o.plain_eval(x[pick])
+        assert np.array_equal(g["y0"] + g["y1"], yp[:, 0]) and np.array_equal(g["z0"] ^ g["z1"], zp), name
+        for j in list(range(0, pick.size, max(1, pick.size // 6)))[:6] + [pick.size - 1]:
+            e = int(pick[j])
+            k0, k1, x0, x1 = O.dealer(o, I.KEY_SEED, 50000 + i, e, 1, x[e:e + 1])
+            ref = O.eval_pair(o, k0, k1, x0, x1)
+            for key in ("y0", "y1"):
+                assert g[key][j] == ref[key][0, 0], (name, e, key)
+            for key in ("z0", "z1"):
+                assert g[key][j] == ref[key][0], (name, e, key)
