@@ -612,6 +612,7 @@ def run_ours(args, rank, world, local_rank):
         "autotune": tuning,
         "keygen": {"ms_per_step": keygen_ms, "elements_per_s": total / (keygen_ms * 1e-3)},
         "comm_bytes_per_party": comm_b,
+        "network_projection": network_projection(calls, css, ms, comm_b, args.steps + args.warmup),
         "gpu_launches": args.steps * len(calls),
         "clocks": clk.summary(),
         "roofline": roof,
@@ -856,6 +857,35 @@ def run_blocks(ctx, args, dev, stream, world):
                                "max_abs_err_vs_float64": float(np.abs(y_n.reshape(rows, H) - ref).max())}
     lnn.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def op_rounds(shape) -> int:
+    """Interactive rounds of one fused gate call: the masked opening, then the
+    Horner steps' Beaver openings (none in the x^ basis), then the piecewise
+    outputs' AND rounds; a shift gate's byte travels with the first of those,
+    or takes a round of its own when there is none."""
+    r = 1 + (shape.degree if shape.n_mults else 0) + (shape.bx_rounds if shape.n_piecewise else 0)
+    if shape.trunc_shift and r == 1:
+        r += 1
+    return r
+
+
+def network_projection(calls, css, ms, comm_b, counted_steps):
+    """Projected online time of one layer step with one party per machine
+    (the paper's Eq. for T_proj): T_comp + 2 B_comm / BW + R RTT, on its LAN
+    (1 GB/s, 0.5 ms) and WAN (400 MB/s, 4 ms) models.  B_comm is one party's
+    bytes per step (the closed form per element, checked against the counted
+    bytes), R the rounds of the operator calls run one after another, and
+    T_comp the measured step time with both parties on this one GPU."""
+    b = sum(c.n * css[c.name].shape.comm_bytes_per_elem for c in calls)
+    rounds = sum(op_rounds(css[c.name].shape) for c in calls)
+    out = {"t_comp_ms": ms, "comm_bytes_per_party": b, "rounds": rounds,
+           "counted_bytes_match": all(v == b * counted_steps for v in comm_b),
+           "note": "T_comp is both parties' time on one GPU; one party per GPU would halve it at most"}
+    for name, bw, rtt in (("lan", 1e9, 0.5), ("wan", 400e6, 4.0)):
+        out[name] = {"bw_bytes_per_s": bw, "rtt_ms": rtt,
+                     "t_proj_ms": ms + 2e3 * b / bw + rounds * rtt}
     return out
 
 
