@@ -40,8 +40,9 @@ SMS = 148
 
 
 def _measured_peaks():
-    """The measured peaks of the B300s (MEASURED_PEAKS.json at
-    the repository root), else the recorded fallback figures."""
+    """The measured peaks of the B300s this runs on (MEASURED_PEAKS.json at
+    the repository root: STREAM-style copy bandwidth and the maximum SM
+    clock), else the recorded fallback figures."""
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
             d = json.load(fh)
