@@ -193,7 +193,7 @@ const char *ffss_last_error(void);
 
 /* Work split of the fused gate (library tuning knob, no counterpart in the
  * paper): each element's T + M - 1 DCF walks are spread over `slots` threads
- * (1, 2, 4, 8 or 16; tiles hold 256 / slots elements), in the plain and the
+ * (1, 2, 4, 8, 16 or 32; tiles hold 256 / slots elements), in the plain and the
  * batched form (a batch plan's own ffss_batch_set_slots takes precedence).
  * 0 (the default) lets the library choose per call: the measured model of
  * ffss_autotune once the spec is tuned, else a waves x slowest-slot cost
@@ -279,9 +279,9 @@ int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_key
  * fixed_us + ceil(ceil(n / tile) / SMs) * tile_us. */
 typedef struct {
     uint32_t n_tried;        /* entries used below (splits with slots <= walks per element) */
-    uint32_t slots[5];
-    double tile_us[5];
-    double fixed_us[5];
+    uint32_t slots[6];
+    double tile_us[6];
+    double fixed_us[6];
     uint32_t sample_elems;   /* the larger sample: 2 x SMs x 256 elements */
     double dealer_ms;        /* time spent generating the samples' throw-away keys */
 } ffss_tune;

@@ -635,7 +635,7 @@ static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
     std::sort(own[q].begin(), own[q].end());
     for (uint32_t v : own[q]) sc.item[pos++] = uint8_t(v);
   }
-  for (uint32_t q = slots; q <= 16; ++q) sc.off[q] = uint8_t(pos);
+  for (uint32_t q = slots; q <= kMaxSlots; ++q) sc.off[q] = uint8_t(pos);
   (void)nitems;
   sc.S = slots;
   sc.E = 256 / slots;
@@ -653,7 +653,7 @@ static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
   Sched best{};
   double best_cost = 0;
   bool have = false;
-  for (uint32_t slots = 1; slots <= 16; slots *= 2) {
+  for (uint32_t slots = 1; slots <= kMaxSlots; slots *= 2) {
     if (slots > 1 && slots > nitems) break;
     uint64_t mx = 0;
     Sched sc = make_sched(S, slots, &mx);
@@ -864,7 +864,7 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
   memset(&t, 0, sizeof(t));
   t.sample_elems = uint32_t(B.n);
   t.dealer_ms = dealer_ms;
-  for (uint32_t slots = 1; slots <= 16; slots *= 2) {
+  for (uint32_t slots = 1; slots <= kMaxSlots; slots *= 2) {
     if (slots > 1 && slots > nitems) break;
     double ua = 0, ub = 0;
     rc = time_split(ctx, spec, A, slots, st, &ua);
@@ -1010,8 +1010,8 @@ extern "C" int ffss_batch_create(ffss_ctx *ctx, uint32_t max_calls, ffss_batch *
 
 extern "C" int ffss_batch_set_slots(ffss_batch *bt, uint32_t slots) {
   if (!bt) return fail(FFSS_ERR_INVALID, "ffss_batch_set_slots: NULL batch");
-  if (slots != 0 && (slots > 16 || (slots & (slots - 1)) != 0))
-    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 16");
+  if (slots != 0 && (slots > kMaxSlots || (slots & (slots - 1)) != 0))
+    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 32");
   bt->force_slots = slots;
   return FFSS_OK;
 }
@@ -1213,7 +1213,7 @@ static Sched noalloc_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load)
       for (uint32_t i = 0; i < n; ++i)
         if (owner[i] == q && id[i] == v) sc.item[pos++] = uint8_t(v);
   }
-  for (uint32_t q = slots; q <= 16; ++q) sc.off[q] = uint8_t(pos);
+  for (uint32_t q = slots; q <= kMaxSlots; ++q) sc.off[q] = uint8_t(pos);
   sc.S = slots;
   sc.E = 256 / slots;
   uint64_t mx = 0;
@@ -1394,8 +1394,8 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
 
 extern "C" int ffss_ctx_set_slots(ffss_ctx *ctx, uint32_t slots) {
   if (!ctx) return fail(FFSS_ERR_INVALID, "ffss_ctx_set_slots: NULL context");
-  if (slots != 0 && (slots > 16 || (slots & (slots - 1)) != 0))
-    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 16");
+  if (slots != 0 && (slots > kMaxSlots || (slots & (slots - 1)) != 0))
+    return fail(FFSS_ERR_INVALID, "slots must be 0 or a power of two <= 32");
   ctx->force_slots = slots;
   return FFSS_OK;
 }

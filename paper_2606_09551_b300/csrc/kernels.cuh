@@ -347,9 +347,11 @@ __device__ __forceinline__ void finish_lut(uint32_t b, const uint64_t *vl, uint6
 constexpr uint32_t kGateThreads = 512;
 constexpr uint32_t kMaxItems = kMaxT + kMaxM;
 
+constexpr uint32_t kMaxSlots = 32;   // threads per element: one walk each for 32-walk specs
+
 struct Sched {
   uint32_t S, E;                 // slots per element, elements per tile (S * E = 256)
-  uint8_t off[17];               // slot s owns items [off[s], off[s+1])
+  uint8_t off[kMaxSlots + 1];    // slot s owns items [off[s], off[s+1])
   uint8_t item[kMaxItems];       // < T: comparison key; >= T: lookup key item - T
 };
 

@@ -101,8 +101,8 @@ class ServerStats(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("n_tried", C.c_uint32), ("slots", C.c_uint32 * 5), ("tile_us", C.c_double * 5),
-                ("fixed_us", C.c_double * 5), ("sample_elems", C.c_uint32), ("dealer_ms", C.c_double)]
+    _fields_ = [("n_tried", C.c_uint32), ("slots", C.c_uint32 * 6), ("tile_us", C.c_double * 6),
+                ("fixed_us", C.c_double * 6), ("sample_elems", C.c_uint32), ("dealer_ms", C.c_double)]
 
     def as_dict(self):
         n = self.n_tried

@@ -70,7 +70,7 @@ def test_autotune_model_and_parity(ctx, sp):
     cs = F.CompiledSpec(sp, ctx)
     walks = _walks(sp)
     tune = cs.autotune()
-    want = [s for s in (1, 2, 4, 8, 16) if s == 1 or s <= walks]
+    want = [s for s in (1, 2, 4, 8, 16, 32) if s == 1 or s <= walks]
     assert tune["slots"] == want
     assert tune["sample_elems"] == 2 * sms * 256
     assert all(t > 0 for t in tune["tile_us"]) and all(f >= 0 for f in tune["fixed_us"])
@@ -96,4 +96,25 @@ def test_forced_split_overrides_tuning(ctx):
         assert cs.gate_slots(393216) == 2
     finally:
         ctx.set_slots(0)
-    assert cs.gate_slots(393216) in (1, 2, 4, 8, 16)
+    assert cs.gate_slots(393216) in (1, 2, 4, 8, 16, 32)
+
+
+@pytest.mark.parametrize("sp", [S.nexp16(), S.gelu4()], ids=["nexp16", "gelu4"])
+def test_forced_32_slots_parity(ctx, sp):
+    """The widest split (32 threads per element, tiles of 8): every thread
+    walks at most one key for nExp (32 walks), several threads walk none for
+    GeLU-4 (8 walks); shares bit-exact to the oracle on ragged sizes."""
+    cs = F.CompiledSpec(sp, ctx)
+    o = O.Spec(**sp.descriptor())
+    try:
+        ctx.set_slots(32)
+        assert cs.gate_slots(1000) == 32
+        for i, n in enumerate((1, 7, 1203)):
+            x = I.uniform_x(n, sp.k, 700 + i)
+            k0, k1, x0, x1 = O.dealer(o, I.KEY_SEED, 70 + i, 0, n, x)
+            ref = O.eval_pair(o, k0, k1, x0, x1)
+            got = _gate(ctx, cs, sp, x, 70 + i)
+            for name in ("y0", "y1", "z0", "z1"):
+                assert np.array_equal(got[name].reshape(ref[name].shape), ref[name]), (n, name)
+    finally:
+        ctx.set_slots(0)

@@ -54,7 +54,7 @@ def _prepare(ctx, sp, x, call_id):
     return (cs, k0, k1, x0, x1, y0, y1, z0, z1)
 
 
-@pytest.mark.parametrize("slots", [0, 1, 4, 16])
+@pytest.mark.parametrize("slots", [0, 1, 4, 16, 32])
 def test_batch_equals_plain(ctx, slots):
     import torch
     work = _mixed_calls()
