@@ -88,6 +88,22 @@ def test_autotune_model_and_parity(ctx, sp):
                 assert np.array_equal(got[name].reshape(ref[name].shape), ref[name]), name
 
 
+def test_split_limits(ctx):
+    """Splits are powers of two up to 32 slots per element; others are refused."""
+    bt = F.Batch(ctx, 2)
+    try:
+        for bad in (3, 64, 48):
+            with pytest.raises(F.FfssError):
+                ctx.set_slots(bad)
+            with pytest.raises(F.FfssError):
+                bt.set_slots(bad)
+        ctx.set_slots(32)
+        bt.set_slots(32)
+    finally:
+        ctx.set_slots(0)
+        bt.set_slots(0)
+
+
 def test_forced_split_overrides_tuning(ctx):
     cs = F.CompiledSpec(S.gelu8(), ctx)
     cs.autotune()
