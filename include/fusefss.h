@@ -226,7 +226,33 @@ int ffss_keys_size(const ffss_spec *spec, uint64_t n, uint64_t *bytes);
  * FFSS_ERR_PARTY. */
 int ffss_keys_bind(const ffss_spec *spec, uint64_t n, int party, void *buf_dev,
                    uint64_t buf_bytes, int state, ffss_keys **out);
+/* Release a key handle.  For a handle from ffss_keys_alloc this is
+ * ffss_keys_free(keys, NULL); a bound buffer stays the caller's. */
 int ffss_keys_release(ffss_keys *keys);
+
+/* Budgeted key pool of a context (the dealer's one-time preprocessing
+ * material of Sec. 5.2 held in a reserved device arena).
+ * ffss_key_pool_reserve reserves `budget_bytes` (rounded up to 256) of device
+ * memory as the pool (0 releases it); keys are then allocated from it with
+ * ffss_keys_alloc, with no device allocation per call.  Errors:
+ * FFSS_ERR_BUDGET (key handles still hold pool memory: nothing changes; or
+ * the device cannot hold an arena of that size: the context is left without
+ * a pool), FFSS_ERR_CUDA (another CUDA failure).  Destroy the context only after
+ * every pooled handle has been freed. */
+int ffss_key_pool_reserve(ffss_ctx *ctx, uint64_t budget_bytes);
+/* Both parties' keys for n elements of `spec`, one 256-byte aligned range
+ * each, from the pool; the handles start empty (fill with ffss_keygen).
+ * FFSS_ERR_BUDGET when the pool has no free range of 2 x ffss_keys_size
+ * bytes, or no pool is reserved; nothing is allocated then. */
+int ffss_keys_alloc(ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, ffss_keys **k0, ffss_keys **k1);
+/* Free a key handle.  A pooled range goes back to the pool once the work
+ * queued on `stream` before this call has completed (an event is recorded
+ * there), so free keys on the stream that last used them.  A bound handle
+ * is released and its buffer stays the caller's. */
+int ffss_keys_free(ffss_keys *keys, void *stream);
+/* Pool size, bytes in use, the peak of bytes in use, and live handles. */
+int ffss_key_pool_stats(const ffss_ctx *ctx, uint64_t *reserved, uint64_t *in_use, uint64_t *peak,
+                        uint32_t *live);
 
 /* GPU dealer (Sec. 5.2, App. F): for elements [0, n) of call `call_id`, draw
  * r_in and its shares, carries and thresholds, translated/padded lookup
@@ -238,6 +264,18 @@ int ffss_keys_release(ffss_keys *keys);
 int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
                 uint64_t n, const uint64_t *x_plain_dev, ffss_keys *k0, ffss_keys *k1,
                 uint64_t *x0_dev, uint64_t *x1_dev, void *stream);
+
+/* The same dealer for elements [e0, e0 + n) of call `call_id`: the keys (bound
+ * for n elements), x_plain_dev, x0_dev and x1_dev hold those n elements, and
+ * element i of the launch gets exactly the material element e0 + i gets in
+ * one ffss_keygen over the whole call (the AES-CTR counter carries the
+ * element's index within the call).  This is how keys are streamed in chunks
+ * (the paper's host key streaming for large models, Sec. 6 / App. B).
+ * ffss_keygen is this call with e0 = 0.  Errors: as ffss_keygen, plus
+ * FFSS_ERR_INVALID when e0 + n overflows. */
+int ffss_keygen_range(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                      uint64_t e0, uint64_t n, const uint64_t *x_plain_dev, ffss_keys *k0, ffss_keys *k1,
+                      uint64_t *x0_dev, uint64_t *x1_dev, void *stream);
 
 /* ---- online: single-party FSS calls (local, non-interactive) ------------ */
 
@@ -353,8 +391,12 @@ int ffss_batch_set_slots(ffss_batch *batch, uint32_t slots);
  * nothing: its scratch (work-queue head and call table) is a fixed array in
  * device memory that every GPU loading this library holds until the process
  * exits, sized for at most 32 calls per batch (more is rejected with
- * FFSS_ERR_SHAPE).  The call table is staged from host memory before the
- * call returns; the queue head is cleared on every call.  All calls on a
+ * FFSS_ERR_SHAPE).  The call table goes to the GPU as the parameter of a
+ * small staging kernel queued on `stream`, so the call neither copies from
+ * host memory nor waits for the stream; that kernel also clears the queue
+ * heads, on every call.  Work splits are chosen as ffss_batch_eval chooses
+ * them without a plan override (the context's forced split, else the
+ * autotuner's, else the default).  All calls on a
  * device share that one array: calls whose work overlaps on the GPU (on
  * different streams, or from different threads without ordering) race and
  * must not be issued.  The first call on a device resolves the array's device
@@ -397,7 +439,8 @@ typedef struct {
 } ffss_request;
 
 typedef struct {
-    uint32_t state;             /* 0 queued, 1 admitted, 2 done */
+    uint32_t state;             /* 0 queued, 1 admitted, 2 done, 3 cancelled with chunks
+                                   still in flight, 4 cancelled (nothing in flight) */
     uint32_t layers_done;
     double arrival_ms, admitted_ms, done_ms;   /* server clock */
 } ffss_request_stats;
@@ -418,7 +461,9 @@ typedef struct {
  * ONE batched launch while the dealer fills the other half for the next
  * step.  A chunk's keys depend only on (request, layer, op, element), so a
  * request's shares are the same whether it runs alone or among others.
- * Errors: FFSS_ERR_INVALID, FFSS_ERR_BUDGET (pool), FFSS_ERR_CUDA. */
+ * Errors: FFSS_ERR_INVALID, FFSS_ERR_BUDGET (the key pool or the batch plan
+ * cannot be allocated, or at submit: one element's keys exceed half the
+ * pool), FFSS_ERR_CUDA. */
 int ffss_server_create(ffss_ctx *ctx, const ffss_server_cfg *cfg, ffss_server **out);
 int ffss_server_destroy(ffss_server *server);
 /* Queue a request arriving at arrival_s seconds on the server clock (0 =
@@ -431,6 +476,14 @@ int ffss_server_submit(ffss_server *server, const ffss_request *req, double arri
 int ffss_server_step(ffss_server *server, int *idle);
 /* Wait for all issued work and retire it. */
 int ffss_server_drain(ffss_server *server);
+/* Cancel a queued or admitted request between steps: no further chunk of it
+ * is dealt or issued and its slot is free for the next admission at once.
+ * Chunks already issued finish on the GPU and are retired by later steps
+ * (their key memory returns to the pool then); until the request's state is
+ * 4 those chunks may still write its output buffers, which must stay valid.
+ * Its outputs are incomplete.  The other requests' shares do not change.
+ * Errors: FFSS_ERR_INVALID (unknown id, or the request already finished). */
+int ffss_server_cancel(ffss_server *server, uint32_t id);
 /* Milliseconds since the server was created (the clock arrivals use). */
 int ffss_server_clock(ffss_server *server, double *ms);
 int ffss_server_request_info(ffss_server *server, uint32_t id, ffss_request_stats *out, double *layer_ms,
@@ -549,7 +602,11 @@ int ffss_layernorm_create_newton(ffss_ctx *ctx, const ffss_spec *const gates[5],
  * 4: one byte permute into two tables interleaved per 256-byte entry, the
  * form the FSS kernels use.  which = 5: the dealer's shape, four independent
  * chains per thread through the 4-block call (form 4), one CTA of the
- * dealer's size per SM; blocks/s.
+ * dealer's size per SM; blocks/s.  which = 6: bitsliced AES-128 (Boyar-Peralta
+ * S-box circuit, integer-ALU logic only, no table lookups), 32 chained
+ * blocks per thread in sliced form, one CTA of 256 threads per SM; blocks/s;
+ * the call then checks 8,192 sliced chains against the T-table AES and fails
+ * with FFSS_ERR_CUDA if any block differs.
  * Synchronizes the device; *ms (may be NULL) receives the kernel time. */
 int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms);
 

@@ -342,7 +342,7 @@ extern "C" int ffss_softmax_keygen(ffss_softmax *sm, const uint8_t seed[16], uin
     const auto &s = sm->steps[j];
     int rc;
     if (s.spec)
-      rc = keygen_raw(sm->ctx, s.spec, seed, call_base + uint32_t(j), s.n, nullptr, sm->keys + s.off0,
+      rc = keygen_raw(sm->ctx, s.spec, seed, call_base + uint32_t(j), 0, s.n, nullptr, sm->keys + s.off0,
                       sm->keys + s.off1, nullptr, nullptr, st);
     else
       rc = beaver_keygen_raw(sm->ctx, seed, call_base + uint32_t(j), s.n,
@@ -561,7 +561,7 @@ extern "C" int ffss_layernorm_keygen(ffss_layernorm *ln, const uint8_t seed[16],
     const auto &s = ln->steps[j];
     int rc;
     if (s.spec)
-      rc = keygen_raw(ln->ctx, s.spec, seed, call_base + uint32_t(j), s.n, nullptr, ln->keys + s.off0,
+      rc = keygen_raw(ln->ctx, s.spec, seed, call_base + uint32_t(j), 0, s.n, nullptr, ln->keys + s.off0,
                       ln->keys + s.off1, nullptr, nullptr, st);
     else
       rc = beaver_keygen_raw(ln->ctx, seed, call_base + uint32_t(j), s.n,

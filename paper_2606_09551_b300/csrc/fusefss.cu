@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -114,11 +115,28 @@ const uint8_t kDcfKey[16] = {'F', 'u', 's', 'e', 'F', 'S', 'S', '-', 'D', 'C', '
 // handles
 // ---------------------------------------------------------------------------
 
+// The context's budgeted key pool: one device arena of the budget's size,
+// sub-allocated first fit in 256-byte aligned ranges; free ranges are kept
+// coalesced.  A range freed on a stream becomes reusable once an event
+// recorded there completes, so key memory is never handed out while work
+// queued before its release may still read it.
+struct KeyPool {
+  std::mutex mu;
+  char *base = nullptr;
+  uint64_t bytes = 0;
+  std::map<uint64_t, uint64_t> free_;   // offset -> length
+  struct Pending { uint64_t off, len; cudaEvent_t ev; };
+  std::vector<Pending> pending;
+  uint64_t in_use = 0, peak = 0;
+  uint32_t live = 0;                    // key handles holding a range
+};
+
 struct ffss_ctx {
   int device;
   int sm_count;
   uint32_t *t0_dev;
-  uint32_t force_slots;   // 0: the cost model picks; else slots per element (1..16, power of two)
+  uint32_t force_slots;   // 0: the cost model picks; else slots per element (1..32, power of two)
+  KeyPool pool;
 };
 
 struct ffss_spec {
@@ -138,6 +156,8 @@ struct ffss_keys {
   uint64_t bytes;
   int generated;
   int used;        // bit 0: comparison keys consumed, bit 1: lookup keys consumed
+  KeyPool *pool;   // non-null: buf is a range of this pool (ffss_keys_alloc)
+  uint64_t pool_off;
 };
 
 template <class K>
@@ -169,6 +189,11 @@ extern "C" int ffss_ctx_create(int device, ffss_ctx **out) {
 extern "C" int ffss_ctx_destroy(ffss_ctx *ctx) {
   if (!ctx) return FFSS_OK;
   cudaSetDevice(ctx->device);
+  for (auto &pd : ctx->pool.pending) {
+    cudaEventSynchronize(pd.ev);
+    cudaEventDestroy(pd.ev);
+  }
+  if (ctx->pool.base) cudaFree(ctx->pool.base);
   cudaFree(ctx->t0_dev);
   delete ctx;
   return FFSS_OK;
@@ -446,14 +471,157 @@ extern "C" int ffss_keys_bind(const ffss_spec *spec, uint64_t n, int party, void
   k->spec = spec; k->n = n; k->party = party; k->buf = static_cast<char *>(buf); k->bytes = bytes;
   k->generated = state == FFSS_KEYS_FILLED;
   k->used = 0;
+  k->pool = nullptr;
+  k->pool_off = 0;
   *out = k;
   return FFSS_OK;
 }
 
-extern "C" int ffss_keys_release(ffss_keys *k) {
+// ---- budgeted key pool -----------------------------------------------------
+
+static int check_device_spec(const ffss_ctx *ctx, const ffss_spec *spec);
+
+static void pool_put(KeyPool &P, uint64_t off, uint64_t len) {
+  auto it = P.free_.emplace(off, len).first;
+  auto nx = std::next(it);
+  if (nx != P.free_.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    P.free_.erase(nx);
+  }
+  if (it != P.free_.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      P.free_.erase(it);
+    }
+  }
+}
+
+// Move freed ranges whose stream work has completed back to the free list
+// (waiting for all of them when `wait`).
+static void pool_reclaim(KeyPool &P, bool wait) {
+  std::vector<KeyPool::Pending> keep;
+  for (auto &pd : P.pending) {
+    if (wait) cudaEventSynchronize(pd.ev);
+    if (cudaEventQuery(pd.ev) == cudaSuccess) {
+      cudaEventDestroy(pd.ev);
+      pool_put(P, pd.off, pd.len);
+    } else {
+      keep.push_back(pd);
+    }
+  }
+  P.pending.swap(keep);
+}
+
+static bool pool_take(KeyPool &P, uint64_t len, uint64_t *off) {
+  for (auto it = P.free_.begin(); it != P.free_.end(); ++it) {
+    if (it->second < len) continue;
+    *off = it->first;
+    const uint64_t rest = it->second - len, roff = it->first + len;
+    P.free_.erase(it);
+    if (rest) P.free_.emplace(roff, rest);
+    return true;
+  }
+  return false;
+}
+
+extern "C" int ffss_key_pool_reserve(ffss_ctx *ctx, uint64_t budget_bytes) {
+  if (!ctx) return fail(FFSS_ERR_INVALID, "ffss_key_pool_reserve: NULL context");
+  KeyPool &P = ctx->pool;
+  std::lock_guard<std::mutex> lock(P.mu);
+  if (P.live) return fail(FFSS_ERR_BUDGET, "ffss_key_pool_reserve: %u key handles still hold pool memory", P.live);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  pool_reclaim(P, true);
+  if (P.base) CUDA_TRY(cudaFree(P.base));
+  P.base = nullptr;
+  P.bytes = P.in_use = P.peak = 0;
+  P.free_.clear();
+  if (budget_bytes == 0) return FFSS_OK;
+  const uint64_t b = align256(budget_bytes);
+  cudaError_t e = cudaMalloc(&P.base, b);
+  if (e != cudaSuccess) {
+    P.base = nullptr;
+    cudaGetLastError();   // a refused allocation must not surface at a later launch check
+    return fail(e == cudaErrorMemoryAllocation ? FFSS_ERR_BUDGET : FFSS_ERR_CUDA,
+                "ffss_key_pool_reserve(%llu B): %s", (unsigned long long)b, cudaGetErrorString(e));
+  }
+  P.bytes = b;
+  P.free_.emplace(0, b);
+  return FFSS_OK;
+}
+
+extern "C" int ffss_key_pool_stats(const ffss_ctx *ctx, uint64_t *reserved, uint64_t *in_use, uint64_t *peak,
+                                   uint32_t *live) {
+  if (!ctx) return fail(FFSS_ERR_INVALID, "ffss_key_pool_stats: NULL context");
+  KeyPool &P = const_cast<KeyPool &>(ctx->pool);
+  std::lock_guard<std::mutex> lock(P.mu);
+  if (reserved) *reserved = P.bytes;
+  if (in_use) *in_use = P.in_use;
+  if (peak) *peak = P.peak;
+  if (live) *live = P.live;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_keys_alloc(ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, ffss_keys **k0, ffss_keys **k1) {
+  if (!ctx || !spec || !k0 || !k1) return fail(FFSS_ERR_INVALID, "ffss_keys_alloc: NULL argument");
+  if (n == 0) return fail(FFSS_ERR_SHAPE, "n must be >= 1");
+  if (int rc = check_device_spec(ctx, spec)) return rc;
+  KeyPool &P = ctx->pool;
+  const uint64_t len = align256(make_layout(spec->host, n).total);
+  std::lock_guard<std::mutex> lock(P.mu);
+  if (!P.base) return fail(FFSS_ERR_BUDGET, "ffss_keys_alloc: no key pool reserved (ffss_key_pool_reserve)");
+  uint64_t off = 0;
+  pool_reclaim(P, false);
+  if (!pool_take(P, 2 * len, &off)) {
+    pool_reclaim(P, true);
+    if (!pool_take(P, 2 * len, &off)) {
+      uint64_t largest = 0;
+      for (auto &f : P.free_) largest = std::max(largest, f.second);
+      return fail(FFSS_ERR_BUDGET, "ffss_keys_alloc: %llu B of keys do not fit the pool (%llu B in use of %llu B, "
+                  "largest free range %llu B)", (unsigned long long)(2 * len), (unsigned long long)P.in_use,
+                  (unsigned long long)P.bytes, (unsigned long long)largest);
+    }
+  }
+  ffss_keys *h[2];
+  for (int b = 0; b < 2; ++b) {
+    h[b] = new ffss_keys();
+    h[b]->spec = spec; h[b]->n = n; h[b]->party = b;
+    h[b]->buf = P.base + off + b * len; h[b]->bytes = len;
+    h[b]->generated = 0; h[b]->used = 0;
+    h[b]->pool = &P; h[b]->pool_off = off + b * len;
+  }
+  P.in_use += 2 * len;
+  P.peak = std::max(P.peak, P.in_use);
+  P.live += 2;
+  *k0 = h[0];
+  *k1 = h[1];
+  return FFSS_OK;
+}
+
+extern "C" int ffss_keys_free(ffss_keys *k, void *stream) {
+  if (!k) return FFSS_OK;
+  if (k->pool) {
+    KeyPool &P = *k->pool;
+    std::lock_guard<std::mutex> lock(P.mu);
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+      // without an event the range can only be returned once the device is idle
+      if (ev) cudaEventDestroy(ev);
+      cudaDeviceSynchronize();
+      pool_put(P, k->pool_off, k->bytes);
+    } else {
+      P.pending.push_back({k->pool_off, k->bytes, ev});
+    }
+    P.in_use -= k->bytes;
+    P.live -= 1;
+  }
   delete k;
   return FFSS_OK;
 }
+
+extern "C" int ffss_keys_release(ffss_keys *k) { return ffss_keys_free(k, nullptr); }
 
 static int check_device_spec(const ffss_ctx *ctx, const ffss_spec *spec) {
   if (!spec->dev || spec->ctx != ctx)
@@ -499,16 +667,18 @@ static int launch_keygen(const ffss_ctx *ctx, const KeygenArgs &A, cudaStream_t 
 }
 
 // Dealer launch on raw key buffers (n elements of a call, no handle checks).
+// Elements [e0, e0 + n) of the call; x_plain, x0, x1 and the key buffers
+// hold those n elements.
 static int keygen_raw(const ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
-                      uint64_t n, const uint64_t *x_plain, char *k0, char *k1, uint64_t *x0, uint64_t *x1,
-                      cudaStream_t st) {
+                      uint64_t e0, uint64_t n, const uint64_t *x_plain, char *k0, char *k1, uint64_t *x0,
+                      uint64_t *x1, cudaStream_t st) {
   KeygenArgs A;
   memset(&A, 0, sizeof(A));
   A.spec = spec->dev;
   A.L = make_layout(spec->host, n);
   A.k0 = k0; A.k1 = k1;
   A.x_plain = x_plain; A.x0 = x0; A.x1 = x1;
-  A.n = n; A.e0 = 0; A.call_id = call_id;
+  A.n = n; A.e0 = e0; A.call_id = call_id;
   A.n_items = (spec->host.M > 1 ? spec->host.M - 1 : 0) + spec->host.T + 1;
   key_schedule(seed, A.rk.w);
   A.t0 = ctx->t0_dev;
@@ -521,23 +691,30 @@ static int keygen_raw(const ffss_ctx *ctx, const ffss_spec *spec, const uint8_t 
   }
 }
 
-extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
-                           uint64_t n, const uint64_t *x_plain, ffss_keys *k0, ffss_keys *k1,
-                           uint64_t *x0, uint64_t *x1, void *stream) {
+extern "C" int ffss_keygen_range(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                                 uint64_t e0, uint64_t n, const uint64_t *x_plain, ffss_keys *k0, ffss_keys *k1,
+                                 uint64_t *x0, uint64_t *x1, void *stream) {
   if (n == 0) return FFSS_OK;
   if (!ctx || !spec || !seed || !k0 || !k1) return fail(FFSS_ERR_INVALID, "ffss_keygen: NULL argument");
+  if (e0 + n < e0) return fail(FFSS_ERR_INVALID, "ffss_keygen_range: element range overflows");
   if (k0->party != 0 || k1->party != 1) return fail(FFSS_ERR_PARTY, "ffss_keygen: k0 must be party 0, k1 party 1");
   if (k0->spec != spec || k1->spec != spec || k0->n != n || k1->n != n)
     return fail(FFSS_ERR_SHAPE, "ffss_keygen: key handles do not match spec / n");
   if (x_plain && (!x0 || !x1)) return fail(FFSS_ERR_INVALID, "ffss_keygen: x0/x1 needed with x_plain");
   if (int rc0 = check_device_spec(ctx, spec)) return rc0;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  const int rc = keygen_raw(ctx, spec, seed, call_id, n, x_plain, k0->buf, k1->buf, x0, x1,
+  const int rc = keygen_raw(ctx, spec, seed, call_id, e0, n, x_plain, k0->buf, k1->buf, x0, x1,
                             static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   k0->generated = k1->generated = 1;
   k0->used = k1->used = 0;
   return FFSS_OK;
+}
+
+extern "C" int ffss_keygen(ffss_ctx *ctx, const ffss_spec *spec, const uint8_t seed[16], uint32_t call_id,
+                           uint64_t n, const uint64_t *x_plain, ffss_keys *k0, ffss_keys *k1,
+                           uint64_t *x0, uint64_t *x1, void *stream) {
+  return ffss_keygen_range(ctx, spec, seed, call_id, 0, n, x_plain, k0, k1, x0, x1, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -853,8 +1030,8 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
   CUDA_TRY(cudaEventCreate(&ev.a));
   CUDA_TRY(cudaEventCreate(&ev.b));
   CUDA_TRY(cudaEventRecord(ev.a, st));
-  int rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF0u, A.n, A.x, A.k0, A.k1, A.x0, A.x1, st);
-  if (!rc) rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF1u, B.n, B.x, B.k0, B.k1, B.x0, B.x1, st);
+  int rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF0u, 0, A.n, A.x, A.k0, A.k1, A.x0, A.x1, st);
+  if (!rc) rc = keygen_raw(ctx, spec, kTuneSeed, 0xFFFFFFF1u, 0, B.n, B.x, B.k0, B.k1, B.x0, B.x1, st);
   if (rc) return rc;
   CUDA_TRY(cudaEventRecord(ev.b, st));
   CUDA_TRY(cudaEventSynchronize(ev.b));
@@ -1016,15 +1193,16 @@ extern "C" int ffss_batch_set_slots(ffss_batch *bt, uint32_t slots) {
   return FFSS_OK;
 }
 
-// The split of a batched call of n elements: forced by the plan, else by the
-// context, else the split the plain gate would take for the call (the tuned
-// waves model: a split with the least time per element but tiles of a
-// millisecond leaves the persistent CTAs a long tail), else 8.
-static uint32_t batch_slots(const ffss_batch *bt, const ffss_spec *spec, uint64_t n) {
+// The split of a batched call of n elements: forced by the plan (plan_force,
+// 0 = none), else by the context, else the split the plain gate would take for
+// the call (the tuned waves model: a split with the least time per element
+// but tiles of a millisecond leaves the persistent CTAs a long tail), else 8.
+// Both batched entry points (with and without a plan) use it.
+static uint32_t batch_split(const ffss_ctx *ctx, uint32_t plan_force, const ffss_spec *spec, uint64_t n) {
   const DevSpec &S = spec->host;
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
-  if (!bt->force_slots && (bt->ctx->force_slots || spec->tuned)) return gate_slots(bt->ctx, spec, n);
-  uint32_t want = bt->force_slots ? bt->force_slots : 8;
+  if (!plan_force && (ctx->force_slots || spec->tuned)) return gate_slots(ctx, spec, n);
+  uint32_t want = plan_force ? plan_force : 8;
   uint32_t s = 1;
   while (s * 2 <= want && s * 2 <= (nitems ? nitems : 1)) s *= 2;
   return s;
@@ -1061,7 +1239,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
     it.cls = shape_class(S.r, S.d);
     if (it.cls < 0) return fail(FFSS_ERR_UNSUPPORTED, "call %u: n_out=%u degree=%u", i, S.r, S.d);
     uint64_t mx = 0;
-    it.c.sched = make_sched(S, batch_slots(bt, c.spec, c.n), &mx);
+    it.c.sched = make_sched(S, batch_split(ctx, bt->force_slots, c.spec, c.n), &mx);
     it.tile_cost = mx;
     it.tiles = (c.n + it.c.sched.E - 1) / it.c.sched.E;
     items.push_back(it);
@@ -1178,48 +1356,26 @@ static int noalloc_setup(int device, unsigned char **out) {
   return FFSS_OK;
 }
 
-// Longest-first split of one element's DCF walks over `slots` threads, with
-// fixed-size arrays only.
-static Sched noalloc_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
-  Sched sc;
-  memset(&sc, 0, sizeof(sc));
-  uint32_t id[kMaxItems];
-  uint64_t cost[kMaxItems];
-  uint32_t n = 0;
-  for (uint32_t t = 0; t < S.T; ++t) { id[n] = t; cost[n] = key_levels(S.q_f[t]); ++n; }
-  for (uint32_t j = 0; j + 1 < S.M; ++j) {
-    id[n] = S.T + j;
-    cost[n] = uint64_t(key_levels(S.k)) * (1 + S.V) + S.V;
-    ++n;
-  }
-  for (uint32_t a = 1; a < n; ++a)   // stable insertion sort, costliest first
-    for (uint32_t b = a; b > 0 && cost[b] > cost[b - 1]; --b) {
-      std::swap(cost[b], cost[b - 1]);
-      std::swap(id[b], id[b - 1]);
-    }
-  uint64_t load[16] = {0};
-  uint32_t owner[kMaxItems];
-  for (uint32_t i = 0; i < n; ++i) {
-    uint32_t best = 0;
-    for (uint32_t q = 1; q < slots; ++q)
-      if (load[q] < load[best]) best = q;
-    load[best] += cost[i];
-    owner[i] = best;
-  }
-  uint32_t pos = 0;
-  for (uint32_t q = 0; q < slots; ++q) {
-    sc.off[q] = uint8_t(pos);
-    for (uint32_t v = 0; v < S.T + S.M; ++v)   // items of slot q in ascending order
-      for (uint32_t i = 0; i < n; ++i)
-        if (owner[i] == q && id[i] == v) sc.item[pos++] = uint8_t(v);
-  }
-  for (uint32_t q = slots; q <= kMaxSlots; ++q) sc.off[q] = uint8_t(pos);
-  sc.S = slots;
-  sc.E = 256 / slots;
-  uint64_t mx = 0;
-  for (uint32_t q = 0; q < slots; ++q) mx = load[q] > mx ? load[q] : mx;
-  *max_load = mx;
-  return sc;
+// The call table of one allocation-free batch.  It travels to the GPU as the
+// parameter of a one-CTA staging kernel (kernel parameters are copied when the
+// launch is enqueued), so the host neither keeps the struct alive nor waits
+// for the stream.
+struct NoAllocTable {
+  BatchHdr hdr;
+  unsigned char pad[(sizeof(BatchHdr) + 255) / 256 * 256 - sizeof(BatchHdr)];
+  BatchCall c[kNoAllocMaxCalls];
+};
+static_assert(sizeof(NoAllocTable) <= kNoAllocTableBytes, "table fits the scratch");
+static_assert(sizeof(NoAllocTable) <= 31 * 1024, "table fits the kernel-parameter limit");
+
+// Copy the table into the scratch array (at dst) and clear the work-queue
+// heads (at counter), which must start at zero on every call.
+__global__ void noalloc_stage_kernel(const __grid_constant__ NoAllocTable tbl, unsigned char *dst,
+                                     unsigned long long *counter) {
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(&tbl);
+  uint32_t *out = reinterpret_cast<uint32_t *>(dst);
+  for (uint32_t i = threadIdx.x; i < sizeof(NoAllocTable) / 4; i += blockDim.x) out[i] = src[i];
+  if (threadIdx.x < kShapeClasses) counter[threadIdx.x] = 0;
 }
 
 extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, uint32_t n_calls, uint64_t *comm,
@@ -1231,12 +1387,7 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
   unsigned char *scratch = nullptr;
   int rc = noalloc_setup(ctx->device, &scratch);
   if (rc) return rc;
-  struct Table {
-    BatchHdr hdr;
-    unsigned char pad[(sizeof(BatchHdr) + 255) / 256 * 256 - sizeof(BatchHdr)];
-    BatchCall c[kNoAllocMaxCalls];
-  } tbl;
-  static_assert(sizeof(Table) <= kNoAllocTableBytes, "table fits the scratch");
+  NoAllocTable tbl;
   memset(&tbl, 0, sizeof(tbl));
   uint64_t cost[kNoAllocMaxCalls], ntiles[kNoAllocMaxCalls];
   int cls[kNoAllocMaxCalls];
@@ -1253,9 +1404,6 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
     for (uint32_t j = 0; j < i; ++j)
       if (calls[j].k0 == c.k0 || calls[j].k1 == c.k1) return fail(FFSS_ERR_SHAPE, "call %u reuses keys of call %u", i, j);
     const DevSpec &S = c.spec->host;
-    const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
-    uint32_t slots = 1;
-    while (slots * 2 <= 8 && slots * 2 <= (nitems ? nitems : 1)) slots *= 2;
     BatchCall &b = tbl.c[m];
     b.spec = c.spec->dev;
     b.k0 = c.k0->buf; b.k1 = c.k1->buf;
@@ -1264,7 +1412,7 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
     b.rd = S.r * 16 + S.d;
     cls[m] = shape_class(S.r, S.d);
     if (cls[m] < 0) return fail(FFSS_ERR_UNSUPPORTED, "call %u: n_out=%u degree=%u", i, S.r, S.d);
-    b.sched = noalloc_sched(S, slots, &cost[m]);
+    b.sched = make_sched(S, batch_split(ctx, 0, c.spec, c.n), &cost[m]);
     ntiles[m] = (c.n + b.sched.E - 1) / b.sched.E;
     ++m;
   }
@@ -1292,15 +1440,15 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
   unsigned long long *counter = reinterpret_cast<unsigned long long *>(scratch);
   unsigned char *dtab = scratch + kNoAllocCounterBytes;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  // the table is staged from host memory before this call returns; the queue
-  // head must start at zero on every call
-  CUDA_TRY(cudaMemcpyAsync(dtab, &tbl, sizeof(tbl), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long) * kShapeClasses, st));
+  // the table travels as the staging kernel's parameter; the queue heads
+  // start at zero on every call
+  noalloc_stage_kernel<<<1, 256, 0, st>>>(tbl, dtab, counter);
+  CUDA_TRY(cudaGetLastError());
   for (int c = 0; c < kShapeClasses; ++c) {   // one persistent kernel per shape class, in stream order
     if (!(mask >> c & 1u)) continue;
     const int grid = int(std::min<uint64_t>(tbl.hdr.cls[c].total_tiles, uint64_t(ctx->sm_count)));
     cudaError_t e = launch_batch_class(c, grid, reinterpret_cast<const BatchHdr *>(dtab),
-                                       reinterpret_cast<const BatchCall *>(dtab + offsetof(Table, c)), counter,
+                                       reinterpret_cast<const BatchCall *>(dtab + offsetof(NoAllocTable, c)), counter,
                                        ctx->t0_dev, st);
     if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
   }
@@ -1328,6 +1476,29 @@ extern "C" int ffss_reconstruct(const uint64_t *y0, const uint64_t *y1, const ui
 // ---------------------------------------------------------------------------
 // micro-benchmarks (measurement support for the roofline; synchronizing)
 // ---------------------------------------------------------------------------
+
+// Self-check of the bitsliced AES: 8,192 chains of three encryptions, sliced
+// (one CTA) and through the T-tables, must agree block for block.
+static int check_bitsliced(const ffss_ctx *ctx) {
+  const uint32_t chains = kBsThreads * 32, iters = 3, seed = 0x5EEDu;
+  uint4 *d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, 2 * sizeof(uint4) * chains));
+  static std::once_flag once;
+  int rc = FFSS_OK;
+  std::call_once(once, [&] { rc = set_smem(mb_aes_bs_ref_kernel, kTabBytes); });
+  if (rc) { cudaFree(d); return rc; }
+  mb_aes_bs_kernel<<<1, kBsThreads>>>(d, iters, seed);
+  mb_aes_bs_ref_kernel<<<(chains + 511) / 512, 512, kTabBytes>>>(ctx->t0_dev, d + chains, iters, seed, chains);
+  std::vector<uint4> h(2 * chains);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), d, 2 * sizeof(uint4) * chains, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "bitsliced AES check: %s", cudaGetErrorString(e));
+  for (uint32_t c = 0; c < chains; ++c)
+    if (memcmp(&h[c], &h[chains + c], sizeof(uint4)) != 0)
+      return fail(FFSS_ERR_CUDA, "bitsliced AES differs from the T-table AES at chain %u", c);
+  return FFSS_OK;
+}
 
 extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double *rate, double *ms) {
   if (!ctx || !rate) return fail(FFSS_ERR_INVALID, "ffss_microbench: NULL argument");
@@ -1377,8 +1548,19 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
     mb_aes4_kernel<<<blocks, threads, smem>>>(ctx->t0_dev, static_cast<uint4 *>(out), iters);
     CUDA_TRY(cudaEventRecord(b));
     work = double(blocks) * threads * iters * 4.0;
+  } else if (which == 6) {
+    // bitsliced AES: 32 sliced chains per thread, one CTA of kBsThreads per SM
+    const int blocks = ctx->sm_count, threads = int(kBsThreads);
+    const uint32_t chains = uint32_t(blocks) * threads * 32;
+    CUDA_TRY(cudaMalloc(&out, sizeof(uint4) * chains));
+    mb_aes_bs_kernel<<<blocks, threads>>>(static_cast<uint4 *>(out), 2, 1u);   // warm-up
+    CUDA_TRY(cudaEventRecord(a));
+    mb_aes_bs_kernel<<<blocks, threads>>>(static_cast<uint4 *>(out), iters, 1u);
+    CUDA_TRY(cudaEventRecord(b));
+    work = double(chains) * iters;
   } else {
-    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3), 1..4 (AES variants) or 5 (4-block calls)");
+    return fail(FFSS_ERR_INVALID, "ffss_microbench: which must be 0 (LOP3), 1..4 (AES variants), 5 (4-block calls) "
+                                  "or 6 (bitsliced)");
   }
   cudaError_t e = cudaEventSynchronize(b);
   float t = 0;
@@ -1387,6 +1569,7 @@ extern "C" int ffss_microbench(ffss_ctx *ctx, int which, uint32_t iters, double 
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "ffss_microbench: %s", cudaGetErrorString(e));
+  if (which == 6 && (rc = check_bitsliced(ctx)) != FFSS_OK) return rc;
   *rate = work / (double(t) * 1e-3);
   if (ms) *ms = t;
   return FFSS_OK;

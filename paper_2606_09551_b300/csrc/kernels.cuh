@@ -12,6 +12,7 @@
 // memory once.  No kernel waits on another CTA or on a flag.
 #pragma once
 #include "fss_core.cuh"
+#include "aes_bitsliced.cuh"
 
 namespace ffss {
 
@@ -1099,6 +1100,53 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) mb_aes4_kernel(const uint32
           make_uint4(threadIdx.x, blockIdx.x, 5u, 6u), make_uint4(threadIdx.x, blockIdx.x, 7u, 8u)}};
   for (uint32_t i = 0; i < iters; ++i) s = aes4(s);
   out[blockIdx.x * blockDim.x + threadIdx.x] = xor4(xor4(s.v[0], s.v[1]), xor4(s.v[2], s.v[3]));
+}
+
+// Bitsliced AES (aes_bitsliced.cuh): each thread runs 32 chains in the sliced
+// form.  Block j of thread t starts as (t, j, 0x9E3779B9 (j + 1), seed) and
+// is encrypted iters times in a row; out[32 t + j] receives its last value.
+constexpr uint32_t kBsThreads = 256;
+
+__device__ __forceinline__ uint4 bs_start(uint32_t t, uint32_t j, uint32_t seed) {
+  return make_uint4(t, j, 0x9E3779B9u * (j + 1u), seed);
+}
+
+__global__ void __launch_bounds__(kBsThreads, 1) mb_aes_bs_kernel(uint4 *out, uint32_t iters, uint32_t seed) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t s[16][8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t w[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const uint4 b = bs_start(t, uint32_t(j), seed);
+      w[j] = q == 0 ? b.x : q == 1 ? b.y : q == 2 ? b.z : b.w;
+    }
+    bs::slice_in(w, s, q);
+  }
+  for (uint32_t i = 0; i < iters; ++i) bs::encrypt(s);
+  uint32_t o[4][32];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bs::slice_out(s, o[q], q);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) out[uint64_t(t) * 32 + j] = make_uint4(o[0][j], o[1][j], o[2][j], o[3][j]);
+}
+
+// The same chains through the T-table AES the FSS kernels use, one chain per
+// thread (chain c is block c % 32 of thread c / 32): the bitsliced kernel's
+// self-check.
+__global__ void __launch_bounds__(512, 1) mb_aes_bs_ref_kernel(const uint32_t *t0, uint4 *out, uint32_t iters,
+                                                               uint32_t seed, uint32_t n_chains) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
+  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  __syncthreads();
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
+  uint4 s = bs_start(c / 32, c % 32, seed);
+  for (uint32_t i = 0; i < iters; ++i) s = aes128p(s, RkDcf(), tb);
+  out[c] = s;
 }
 
 }  // namespace ffss

@@ -34,7 +34,7 @@ struct SrvReq {
   std::vector<SrvOp> ops;       // n_layers * ops_per_layer
   uint32_t n_layers = 0, per_layer = 0, call_base = 0;
   double arrival = 0, admitted = -1, done = -1;   // ms on the server clock
-  int state = 0;                // 0 queued, 1 active, 2 done
+  int state = 0;                // 0 queued, 1 active, 2 done, 3 cancelled (chunks in flight), 4 cancelled
   uint32_t layer = 0, op = 0;   // issue cursor within the current layer
   uint64_t elem = 0;
   uint32_t outstanding = 0;     // chunks of the current layer not yet complete
@@ -107,6 +107,10 @@ static void srv_retire(ffss_server *sv, SrvStep &st) {
     ffss_keys_release(c.k0);
     ffss_keys_release(c.k1);
     r.outstanding -= 1;
+    if (r.state == 3) {           // cancelled: its last chunks in flight are done
+      if (r.outstanding == 0) r.state = 4;
+      continue;
+    }
     if (r.outstanding == 0 && r.layer_issued) {   // the layer's shares are all written
       const double lat = t - r.layer_ready;
       r.layer_ms.push_back(lat);
@@ -187,8 +191,10 @@ extern "C" int ffss_server_create(ffss_ctx *ctx, const ffss_server_cfg *cfg, ffs
   if (e == cudaSuccess) e = cudaEventSynchronize(sv->t0);
   if (e != cudaSuccess) {
     ffss_server_destroy(sv);
-    return fail(rc ? FFSS_ERR_BUDGET : FFSS_ERR_CUDA, "ffss_server_create: %s",
-                rc ? "key pool or batch plan allocation failed" : cudaGetErrorString(e));
+    cudaGetLastError();   // a refused allocation must not surface at a later launch check
+    const bool oom = rc || e == cudaErrorMemoryAllocation;
+    return fail(oom ? FFSS_ERR_BUDGET : FFSS_ERR_CUDA, "ffss_server_create: %s",
+                oom ? "the key pool (or the batch plan) cannot be allocated" : cudaGetErrorString(e));
   }
   sv->host_t0 = std::chrono::steady_clock::now();
   *out = sv;
@@ -320,22 +326,8 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
         // dealer for this chunk: the call id names (request, layer, op); the
         // element offset keeps the masks independent of the chunking
         const uint32_t call_id = r.call_base + r.layer * r.per_layer + r.op;
-        KeygenArgs A;
-        memset(&A, 0, sizeof(A));
-        A.spec = o.spec->dev;
-        A.L = make_layout(o.spec->host, n);
-        A.k0 = k0->buf; A.k1 = k1->buf;
-        A.x_plain = o.x + r.elem; A.x0 = x0; A.x1 = x1;
-        A.n = n; A.e0 = r.elem; A.call_id = call_id;
-        A.n_items = (o.spec->host.M > 1 ? o.spec->host.M - 1 : 0) + o.spec->host.T + 1;
-        key_schedule(sv->cfg.seed, A.rk.w);
-        A.t0 = sv->ctx->t0_dev;
-        switch (o.spec->host.p) {
-          case 1: rc = launch_keygen<1>(sv->ctx, A, sv->s_gen); break;
-          case 2: rc = launch_keygen<2>(sv->ctx, A, sv->s_gen); break;
-          case 3: rc = launch_keygen<3>(sv->ctx, A, sv->s_gen); break;
-          default: rc = launch_keygen<4>(sv->ctx, A, sv->s_gen); break;
-        }
+        rc = keygen_raw(sv->ctx, o.spec, sv->cfg.seed, call_id, r.elem, n, o.x + r.elem, k0->buf, k1->buf, x0, x1,
+                        sv->s_gen);
         if (rc) return rc;
         k0->generated = k1->generated = 1;
         const uint32_t ro = o.spec->host.r;
@@ -355,7 +347,7 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
   }
   if (calls.empty()) {
     bool waiting = false;
-    for (auto &r : sv->reqs) waiting |= r.state != 2;
+    for (auto &r : sv->reqs) waiting |= r.state == 0 || r.state == 1;
     *idle = (sv->inflight.empty() && !waiting) ? 1 : 0;
     if (!sv->inflight.empty()) srv_poll(sv, true);   // nothing new to issue: wait for the oldest step
     return FFSS_OK;
@@ -379,6 +371,18 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
   sv->inflight.push_back(std::move(st));
   sv->steps += 1;
   sv->chunks += calls.size();
+  return FFSS_OK;
+}
+
+extern "C" int ffss_server_cancel(ffss_server *sv, uint32_t id) {
+  if (!sv || id >= sv->reqs.size()) return fail(FFSS_ERR_INVALID, "ffss_server_cancel: bad argument");
+  SrvReq &r = sv->reqs[id];
+  if (r.state >= 2) return fail(FFSS_ERR_INVALID, "ffss_server_cancel: request %u is already finished", id);
+  // no further chunk is issued; chunks already queued finish and are retired
+  // (their keys released) by the normal step loop, and the slot is free for
+  // the next admission now
+  r.state = r.outstanding ? 3 : 4;
+  r.done = srv_now_ms(sv);
   return FFSS_OK;
 }
 

@@ -133,7 +133,14 @@ def lib():
         L.ffss_keys_size.argtypes = [vp, C.c_uint64, C.POINTER(C.c_uint64)]
         L.ffss_keys_bind.argtypes = [vp, C.c_uint64, C.c_int, vp, C.c_uint64, C.c_int, C.POINTER(vp)]
         L.ffss_keys_release.argtypes = [vp]
+        L.ffss_key_pool_reserve.argtypes = [vp, C.c_uint64]
+        L.ffss_key_pool_stats.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                          C.POINTER(C.c_uint32)]
+        L.ffss_keys_alloc.argtypes = [vp, vp, C.c_uint64, C.POINTER(vp), C.POINTER(vp)]
+        L.ffss_keys_free.argtypes = [vp, vp]
         L.ffss_keygen.argtypes = [vp, vp, C.POINTER(C.c_uint8), C.c_uint32, C.c_uint64, vp, vp, vp, vp, vp, vp]
+        L.ffss_keygen_range.argtypes = [vp, vp, C.POINTER(C.c_uint8), C.c_uint32, C.c_uint64, C.c_uint64, vp, vp,
+                                         vp, vp, vp, vp]
         L.ffss_eval_pred.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp, vp]
         L.ffss_eval_lut.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp]
         L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
@@ -150,6 +157,7 @@ def lib():
         L.ffss_server_submit.argtypes = [vp, C.POINTER(RequestDesc), C.c_double, C.POINTER(C.c_uint32)]
         L.ffss_server_step.argtypes = [vp, C.POINTER(C.c_int)]
         L.ffss_server_drain.argtypes = [vp]
+        L.ffss_server_cancel.argtypes = [vp, C.c_uint32]
         L.ffss_server_clock.argtypes = [vp, C.POINTER(C.c_double)]
         L.ffss_server_request_info.argtypes = [vp, C.c_uint32, C.POINTER(RequestStats), C.POINTER(C.c_double),
                                                C.c_uint32]
@@ -206,6 +214,15 @@ class Context:
     def set_slots(self, slots: int):
         """Force the gate's DCF walks per element onto `slots` threads (0: automatic)."""
         _check(lib().ffss_ctx_set_slots(self.h, slots))
+
+    def reserve_key_pool(self, budget_bytes: int):
+        """Reserve the context's key pool (0 releases it)."""
+        _check(lib().ffss_key_pool_reserve(self.h, budget_bytes))
+
+    def key_pool_stats(self) -> dict:
+        r, u, p, n = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint32()
+        _check(lib().ffss_key_pool_stats(self.h, C.byref(r), C.byref(u), C.byref(p), C.byref(n)))
+        return {"reserved": r.value, "in_use": u.value, "peak": p.value, "live": n.value}
 
     def close(self):
         if self.h:
@@ -305,9 +322,26 @@ class Keys:
         _check(lib().ffss_keys_bind(cs.h, n, party, buf.data_ptr(), buf.numel(), state, C.byref(h)))
         self.h = h
 
-    def close(self):
+    @classmethod
+    def alloc_pair(cls, cs: CompiledSpec, n: int):
+        """Both parties' keys for n elements from the context's key pool."""
+        h0, h1 = vp(), vp()
+        _check(lib().ffss_keys_alloc(cs.ctx.h, cs.h, n, C.byref(h0), C.byref(h1)))
+        out = []
+        for party, h in ((0, h0), (1, h1)):
+            k = cls.__new__(cls)
+            k.cs, k.n, k.party, k.buf, k.h = cs, n, party, None, h
+            out.append(k)
+        return out[0], out[1]
+
+    def close(self, stream=None):
+        """Release the handle; pooled memory returns to the pool after the
+        work queued on `stream` completes."""
         if self.h:
-            lib().ffss_keys_release(self.h)
+            if self.buf is not None:
+                lib().ffss_keys_release(self.h)
+            else:
+                lib().ffss_keys_free(self.h, _stream(stream))
             self.h = None
 
     def __del__(self):
@@ -322,6 +356,14 @@ def keygen(ctx: Context, cs: CompiledSpec, seed: bytes, call_id: int, n: int, k0
     sb = (C.c_uint8 * 16).from_buffer_copy(bytes(seed))
     _check(lib().ffss_keygen(ctx.h, cs.h, sb, call_id, n, _ptr(x_plain), k0.h, k1.h, _ptr(x0), _ptr(x1),
                              _stream(stream)))
+
+
+def keygen_range(ctx: Context, cs: CompiledSpec, seed: bytes, call_id: int, e0: int, n: int, k0: Keys, k1: Keys,
+                 x_plain=None, x0=None, x1=None, stream=None):
+    """Dealer for elements [e0, e0 + n) of call call_id (keys bound for n elements)."""
+    sb = (C.c_uint8 * 16).from_buffer_copy(bytes(seed))
+    _check(lib().ffss_keygen_range(ctx.h, cs.h, sb, call_id, e0, n, _ptr(x_plain), k0.h, k1.h, _ptr(x0), _ptr(x1),
+                                   _stream(stream)))
 
 
 def eval_pred(ctx: Context, cs: CompiledSpec, party: int, keys: Keys, xhat, atoms=None, bits=None, stream=None):
@@ -410,6 +452,10 @@ class Server:
         while not self.step():
             pass
         _check(lib().ffss_server_drain(self.h))
+
+    def cancel(self, rid: int):
+        """Stop a queued or admitted request between steps (its outputs are incomplete)."""
+        _check(lib().ffss_server_cancel(self.h, rid))
 
     def clock_ms(self) -> float:
         v = C.c_double()

@@ -206,3 +206,22 @@ def test_formula_shape_rounds_and_words():
     # round 2: node 4 (AND); round 3: the normalisation of interval 0 (root 5, depth 2)
     assert (sh.bx_rounds, sh.bx_words) == (3, 3)
     assert sh.comm_bytes_per_elem == 8 + 16 * 1 + 8 * 3
+
+
+def test_undersized_or_misaligned_key_buffer_refused(libpath):
+    """Binding a key buffer smaller than the layout needs is FFSS_ERR_SHAPE,
+    a misaligned one FFSS_ERR_INVALID; both are refused on the host before
+    anything is queued (the buffer address is never dereferenced)."""
+    cs = F.CompiledSpec(S.nexp16())          # host-only compile: no context, no GPU
+    n = 1000
+    need = cs.key_bytes(n)
+    h = C.c_void_p()
+    fake = 1 << 20                            # an aligned address that is never touched
+    assert F.lib().ffss_keys_bind(cs.h, n, 0, fake, need - 1, 0, C.byref(h)) == -2
+    assert b"needed" in F.lib().ffss_last_error()
+    assert F.lib().ffss_keys_bind(cs.h, n, 0, fake + 16, need, 0, C.byref(h)) == -1
+    assert F.lib().ffss_keys_bind(cs.h, n, 2, fake, need, 0, C.byref(h)) == -6
+    assert F.lib().ffss_keys_bind(cs.h, n, 1, fake, need, 0, C.byref(h)) == 0
+    assert F.lib().ffss_keys_free(h, None) == 0
+    # keys are one-time: a pool request without a context or pool is refused
+    assert F.lib().ffss_keys_alloc(None, cs.h, n, C.byref(h), C.byref(h)) == -1

@@ -206,3 +206,50 @@ def test_full_size_streamed_large_layer(ctx):
                 assert g[key][j] == ref[key][0, 0], (name, e, key)
             for key in ("z0", "z1"):
                 assert g[key][j] == ref[key][0], (name, e, key)
+
+
+def test_staggered_arrivals(ctx):
+    """Requests that arrive while another is on the GPU are admitted after
+    their arrival and before the long request finishes, their work shares
+    the steps with it, and every request's shares equal its alone run and
+    the plain launch with the same dealer call ids."""
+    import torch
+    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    sizes = [[20000, 40000], [800, 300], [1500, 900], [300, 100]]
+    arrivals = [0.0, 0.002, 0.008, 0.020]
+    alone = []
+    for i, sz in enumerate(sizes):
+        sv = F.Server(ctx, 256 << 20, 4, 1 << 20, I.KEY_SEED)
+        rq = _request(ctx, css, sz, 200 + i)
+        sv.submit(rq, 0.0, call_id_base=1000 + 50 * i)
+        sv.run()
+        alone.append(_shares(rq))
+        sv.close()
+    sv = F.Server(ctx, 48 << 20, 4, 1 << 20, I.KEY_SEED)
+    reqs = [_request(ctx, css, sz, 200 + i) for i, sz in enumerate(sizes)]
+    ids = [sv.submit(r, a, call_id_base=1000 + 50 * i) for i, (r, a) in enumerate(zip(reqs, arrivals))]
+    sv.run()
+    infos = [sv.request_info(i) for i in ids]
+    sv.close()
+    for info, a in zip(infos, arrivals):
+        assert info["state"] == 2 and info["layers_done"] == 2
+        assert info["admitted_ms"] >= a * 1e3
+    for info in infos[1:]:
+        assert info["admitted_ms"] < infos[0]["done_ms"] and info["done_ms"] < infos[0]["done_ms"]
+    for i, r in enumerate(reqs):
+        mixed = _shares(r)
+        for la, lb in zip(alone[i], mixed):
+            for oa, ob in zip(la, lb):
+                for a, b in zip(oa, ob):
+                    assert np.array_equal(a, b), i
+    # one late request against the plain launch
+    for li, layer in enumerate(reqs[2]):
+        for j, (cs, x, y0, y1, z0, z1) in enumerate(layer):
+            n = x.numel()
+            k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
+            x0, x1 = torch.empty_like(x), torch.empty_like(x)
+            F.keygen(ctx, cs, I.KEY_SEED, 1000 + 50 * 2 + li * 2 + j, n, k0, k1, x, x0, x1)
+            p0, p1 = torch.empty_like(y0), torch.empty_like(y1)
+            q0, q1 = torch.empty_like(z0), torch.empty_like(z1)
+            F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
+            assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)

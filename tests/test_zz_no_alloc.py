@@ -16,9 +16,9 @@ from paper_2606_09551_b300 import specs as S
 pytestmark = pytest.mark.gpu
 
 
-def _prepare(ctx, sp, x, call_id):
+def _prepare(ctx, sp, x, call_id, cs=None):
     import torch
-    cs = F.CompiledSpec(sp, ctx)
+    cs = cs or F.CompiledSpec(sp, ctx)
     n = x.size
     k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
     xp = torch.from_numpy(x).cuda()
@@ -58,3 +58,24 @@ def test_noalloc_matches_batch_twice_in_a_row():
     with pytest.raises(F.FfssError) as ei:
         F.batch_eval_noalloc(ctx, many)
     assert "32" in str(ei.value)
+
+
+def test_noalloc_takes_the_tuned_split():
+    """With a tuned spec both batched entry points choose the autotuner's work
+    split for the call and give the same shares."""
+    import torch
+    from paper_2606_09551_b300 import build
+    build.build()
+    ctx = F.Context(0)
+    sp = S.gelu8()
+    cs = F.CompiledSpec(sp, ctx)
+    cs.autotune()
+    bt = F.Batch(ctx, 4)
+    x = I.uniform_x(20000, sp.k, 4242)
+    ref = _prepare(ctx, sp, x, 4300, cs)
+    got = _prepare(ctx, sp, x, 4300, cs)
+    bt.eval([ref])
+    F.batch_eval_noalloc(ctx, [got])
+    torch.cuda.synchronize()
+    for i in (5, 6, 7, 8):
+        assert torch.equal(ref[i], got[i]), i
