@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "liboracle.so")
 def build(force: bool = False) -> str:
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
         return OUT
-    cmd = ["gcc", "-O2", "-std=c99", "-Wall", "-Wextra", "-fPIC", "-shared", "-o", OUT + ".tmp", SRC]
+    cmd = ["gcc", "-O3", "-std=c99", "-Wall", "-Wextra", "-fPIC", "-shared", "-o", OUT + ".tmp", SRC]
     subprocess.run(cmd, check=True)
     os.replace(OUT + ".tmp", OUT)
     return OUT
