@@ -188,6 +188,11 @@ typedef struct {
 /* Create a context on CUDA device `device` (makes it current on the calling
  * thread) and upload the AES tables.  Errors: FFSS_ERR_CUDA. */
 int ffss_ctx_create(int device, ffss_ctx **out);
+/* Release the caller's context handle.  Device specs, batch plans, servers,
+ * softmax / LayerNorm plans and pooled keys made from the context each hold
+ * a reference to it, so its device memory is freed when the last of them is
+ * freed; they may be freed before or after this call, in any order.  The
+ * handle must not be used for new work after this call. */
 int ffss_ctx_destroy(ffss_ctx *ctx);
 const char *ffss_last_error(void);
 
@@ -237,8 +242,7 @@ int ffss_keys_release(ffss_keys *keys);
  * ffss_keys_alloc, with no device allocation per call.  Errors:
  * FFSS_ERR_BUDGET (key handles still hold pool memory: nothing changes; or
  * the device cannot hold an arena of that size: the context is left without
- * a pool), FFSS_ERR_CUDA (another CUDA failure).  Destroy the context only after
- * every pooled handle has been freed. */
+ * a pool), FFSS_ERR_CUDA (another CUDA failure). */
 int ffss_key_pool_reserve(ffss_ctx *ctx, uint64_t budget_bytes);
 /* Both parties' keys for n elements of `spec`, one 256-byte aligned range
  * each, from the pool; the handles start empty (fill with ffss_keygen).
@@ -307,6 +311,23 @@ int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_key
                    const uint64_t *x0_dev, const uint64_t *x1_dev, uint64_t n,
                    uint64_t *y0_dev, uint64_t *y1_dev, uint32_t *z0_dev, uint32_t *z1_dev,
                    uint64_t *comm_dev, void *stream);
+
+/* The same gate with HOST input and output buffers (the end-to-end form):
+ * queues on `stream` the copies of x0, x1 (n uint64 each) into device
+ * staging owned by the context, the fused gate, and the copies of the
+ * shares back into y0, y1 (n * n_out uint64) and z0, z1 (n uint32), then
+ * returns without waiting.  The host buffers should be page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to run asynchronously,
+ * and must stay valid and untouched until the stream's work has completed;
+ * synchronize the stream before reading the outputs.  The context keeps two
+ * staging slots, used in turn and reused in stream order, so calls issued
+ * alternately on two streams overlap one call's copies with the other's
+ * gate.  A slot grows (cudaMalloc, after waiting for its previous call) when
+ * a call needs more than it holds.  comm_dev: as ffss_eval_pair.  Consumes
+ * both handles.  Errors: as ffss_eval_pair. */
+int ffss_eval_pair_host(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
+                        const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
+                        uint32_t *z0, uint32_t *z1, uint64_t *comm_dev, void *stream);
 
 /* ---- launch-shape autotuner (library tuning, no counterpart in the paper) */
 

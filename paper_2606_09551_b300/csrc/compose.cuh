@@ -243,7 +243,9 @@ extern "C" int ffss_softmax_destroy(ffss_softmax *sm) {
   if (sm->keys) cudaFree(sm->keys);
   if (sm->sh) cudaFree(sm->sh);
   if (sm->z) cudaFree(sm->z);
+  ffss_ctx *ctx = sm->ctx;
   delete sm;
+  ctx_unref(ctx);
   return FFSS_OK;
 }
 
@@ -268,6 +270,7 @@ static int softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], const 
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_softmax *sm = new ffss_softmax();
   sm->ctx = ctx;
+  ctx_ref(ctx);
   for (int i = 0; i < kSmGates; ++i) sm->g[i] = gates[i];
   sm->newton = newton;
   for (int i = 0; i < 2; ++i) sm->gn[i] = newton ? newton_gates[i] : nullptr;
@@ -467,7 +470,9 @@ extern "C" int ffss_layernorm_destroy(ffss_layernorm *ln) {
   if (ln->keys) cudaFree(ln->keys);
   if (ln->sh) cudaFree(ln->sh);
   if (ln->z) cudaFree(ln->z);
+  ffss_ctx *ctx = ln->ctx;
   delete ln;
+  ctx_unref(ctx);
   return FFSS_OK;
 }
 
@@ -493,6 +498,7 @@ static int layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], cons
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_layernorm *ln = new ffss_layernorm();
   ln->ctx = ctx;
+  ctx_ref(ctx);
   for (int i = 0; i < kLnGates; ++i) ln->g[i] = gates[i];
   ln->newton = newton;
   for (int i = 0; i < 3; ++i) ln->gn[i] = newton ? newton_gates[i] : nullptr;

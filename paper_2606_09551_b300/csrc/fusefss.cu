@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstring>
 #include <map>
@@ -131,13 +132,50 @@ struct KeyPool {
   uint32_t live = 0;                    // key handles holding a range
 };
 
+// Device staging of the host-buffer entry point: a ring of slots, each
+// reusable once the copy-out of its last call has completed.
+struct StageSlot {
+  char *dev = nullptr;
+  uint64_t bytes = 0;
+  cudaEvent_t free_ev = nullptr;
+  bool used = false;
+};
+
 struct ffss_ctx {
   int device;
   int sm_count;
   uint32_t *t0_dev;
   uint32_t force_slots;   // 0: the cost model picks; else slots per element (1..32, power of two)
   KeyPool pool;
+  std::mutex stage_mu;
+  StageSlot stage[2];
+  int stage_next = 0;
+  // Objects that keep this context (device specs, batch plans, servers,
+  // block plans, pooled keys) hold a reference; ffss_ctx_destroy frees the
+  // context when the last of them is released, whatever the order.
+  int refs = 0;
+  bool dying = false;
 };
+
+static std::mutex g_ctx_mu;   // guards refs / dying of every context
+
+static void ctx_free(ffss_ctx *ctx);
+
+static void ctx_ref(ffss_ctx *ctx) {
+  if (!ctx) return;
+  std::lock_guard<std::mutex> lock(g_ctx_mu);
+  ++ctx->refs;
+}
+
+static void ctx_unref(ffss_ctx *ctx) {
+  if (!ctx) return;
+  bool last = false;
+  {
+    std::lock_guard<std::mutex> lock(g_ctx_mu);
+    last = --ctx->refs == 0 && ctx->dying;
+  }
+  if (last) ctx_free(ctx);
+}
 
 struct ffss_spec {
   ffss_ctx *ctx;
@@ -158,6 +196,7 @@ struct ffss_keys {
   int used;        // bit 0: comparison keys consumed, bit 1: lookup keys consumed
   KeyPool *pool;   // non-null: buf is a range of this pool (ffss_keys_alloc)
   uint64_t pool_off;
+  ffss_ctx *pool_ctx;   // the pool's context (held by a reference)
 };
 
 template <class K>
@@ -188,15 +227,32 @@ extern "C" int ffss_ctx_create(int device, ffss_ctx **out) {
 
 extern "C" int ffss_ctx_destroy(ffss_ctx *ctx) {
   if (!ctx) return FFSS_OK;
+  bool now = false;
+  {
+    std::lock_guard<std::mutex> lock(g_ctx_mu);
+    ctx->dying = true;
+    now = ctx->refs == 0;
+  }
+  if (now) ctx_free(ctx);
+  return FFSS_OK;
+}
+
+static void ctx_free(ffss_ctx *ctx) {
   cudaSetDevice(ctx->device);
   for (auto &pd : ctx->pool.pending) {
     cudaEventSynchronize(pd.ev);
     cudaEventDestroy(pd.ev);
   }
   if (ctx->pool.base) cudaFree(ctx->pool.base);
+  for (auto &sl : ctx->stage) {
+    if (sl.free_ev) {
+      cudaEventSynchronize(sl.free_ev);
+      cudaEventDestroy(sl.free_ev);
+    }
+    if (sl.dev) cudaFree(sl.dev);
+  }
   cudaFree(ctx->t0_dev);
   delete ctx;
-  return FFSS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -413,6 +469,7 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
       delete sp;
       return fail(FFSS_ERR_CUDA, "ffss_spec_compile: %s", cudaGetErrorString(e));
     }
+    ctx_ref(ctx);
   }
   ffss_shape &sh = sp->shape;
   sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
@@ -438,11 +495,13 @@ extern "C" int ffss_spec_shape(const ffss_spec *spec, ffss_shape *out) {
 
 extern "C" int ffss_spec_free(ffss_spec *spec) {
   if (!spec) return FFSS_OK;
-  if (spec->ctx && spec->dev) {
-    cudaSetDevice(spec->ctx->device);
+  ffss_ctx *ctx = spec->dev ? spec->ctx : nullptr;
+  if (ctx) {
+    cudaSetDevice(ctx->device);
     cudaFree(spec->dev);
   }
   delete spec;
+  ctx_unref(ctx);
   return FFSS_OK;
 }
 
@@ -473,6 +532,7 @@ extern "C" int ffss_keys_bind(const ffss_spec *spec, uint64_t n, int party, void
   k->used = 0;
   k->pool = nullptr;
   k->pool_off = 0;
+  k->pool_ctx = nullptr;
   *out = k;
   return FFSS_OK;
 }
@@ -589,6 +649,8 @@ extern "C" int ffss_keys_alloc(ffss_ctx *ctx, const ffss_spec *spec, uint64_t n,
     h[b]->buf = P.base + off + b * len; h[b]->bytes = len;
     h[b]->generated = 0; h[b]->used = 0;
     h[b]->pool = &P; h[b]->pool_off = off + b * len;
+    h[b]->pool_ctx = ctx;
+    ctx_ref(ctx);
   }
   P.in_use += 2 * len;
   P.peak = std::max(P.peak, P.in_use);
@@ -600,6 +662,7 @@ extern "C" int ffss_keys_alloc(ffss_ctx *ctx, const ffss_spec *spec, uint64_t n,
 
 extern "C" int ffss_keys_free(ffss_keys *k, void *stream) {
   if (!k) return FFSS_OK;
+  ffss_ctx *owner = k->pool ? k->pool_ctx : nullptr;
   if (k->pool) {
     KeyPool &P = *k->pool;
     std::lock_guard<std::mutex> lock(P.mu);
@@ -618,6 +681,7 @@ extern "C" int ffss_keys_free(ffss_keys *k, void *stream) {
     P.live -= 1;
   }
   delete k;
+  ctx_unref(owner);
   return FFSS_OK;
 }
 
@@ -936,6 +1000,63 @@ extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k
   return FFSS_OK;
 }
 
+extern "C" int ffss_eval_pair_host(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
+                                   const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
+                                   uint32_t *z0, uint32_t *z1, uint64_t *comm, void *stream) {
+  if (n == 0) return FFSS_OK;
+  if (!ctx || !spec || !x0 || !x1 || !y0 || !y1 || !z0 || !z1)
+    return fail(FFSS_ERR_INVALID, "ffss_eval_pair_host: NULL argument");
+  int rc = check_device_spec(ctx, spec);
+  if (!rc) rc = check_keys(spec, k0, 0, n, 3);
+  if (!rc) rc = check_keys(spec, k1, 1, n, 3);
+  if (rc) return rc;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t r = spec->host.r;
+  const uint64_t bx = align256(8 * n), by = align256(8 * n * r), bz = align256(4 * n);
+  const uint64_t need = 2 * (bx + by + bz);
+  std::lock_guard<std::mutex> lock(ctx->stage_mu);
+  StageSlot &sl = ctx->stage[ctx->stage_next];
+  ctx->stage_next ^= 1;
+  if (!sl.free_ev) CUDA_TRY(cudaEventCreateWithFlags(&sl.free_ev, cudaEventDisableTiming));
+  if (sl.bytes < need) {
+    // grow: the slot's previous call must be done with it first
+    if (sl.used) CUDA_TRY(cudaEventSynchronize(sl.free_ev));
+    if (sl.dev) CUDA_TRY(cudaFree(sl.dev));
+    sl.dev = nullptr;
+    sl.bytes = 0;
+    sl.used = false;
+    cudaError_t e = cudaMalloc(&sl.dev, need);
+    if (e != cudaSuccess) {
+      sl.dev = nullptr;
+      cudaGetLastError();
+      return fail(FFSS_ERR_CUDA, "ffss_eval_pair_host: staging of %llu B: %s", (unsigned long long)need,
+                  cudaGetErrorString(e));
+    }
+    sl.bytes = need;
+  } else if (sl.used) {
+    CUDA_TRY(cudaStreamWaitEvent(st, sl.free_ev, 0));   // on the GPU: the slot's last copy-out is done
+  }
+  uint64_t *dx0 = reinterpret_cast<uint64_t *>(sl.dev), *dx1 = reinterpret_cast<uint64_t *>(sl.dev + bx);
+  uint64_t *dy0 = reinterpret_cast<uint64_t *>(sl.dev + 2 * bx);
+  uint64_t *dy1 = reinterpret_cast<uint64_t *>(sl.dev + 2 * bx + by);
+  uint32_t *dz0 = reinterpret_cast<uint32_t *>(sl.dev + 2 * bx + 2 * by);
+  uint32_t *dz1 = reinterpret_cast<uint32_t *>(sl.dev + 2 * bx + 2 * by + bz);
+  CUDA_TRY(cudaMemcpyAsync(dx0, x0, 8 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(dx1, x1, 8 * n, cudaMemcpyHostToDevice, st));
+  rc = eval_pair_raw(ctx, spec, k0->buf, k1->buf, dx0, dx1, n, dy0, dy1, dz0, dz1, comm, st);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(y0, dy0, 8 * n * r, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(y1, dy1, 8 * n * r, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(z0, dz0, 4 * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(z1, dz1, 4 * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaEventRecord(sl.free_ev, st));
+  sl.used = true;
+  k0->used |= 3;
+  k1->used |= 3;
+  return FFSS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // launch-shape autotuner
 // ---------------------------------------------------------------------------
@@ -1124,8 +1245,24 @@ static cudaError_t set_batch_smem() {
   return e;
 }
 
+// Room for cap calls plus one re-split tail entry per shape class.
 static size_t batch_table_bytes(uint32_t cap) {
-  return align256(sizeof(BatchHdr)) + size_t(cap) * sizeof(BatchCall);
+  return align256(sizeof(BatchHdr)) + size_t(cap + kShapeClasses) * sizeof(BatchCall);
+}
+
+// Estimated time of one tile of `spec` under a work split: the autotuner's
+// measured tile time when the spec is tuned (0 if that split was not
+// measured), else the slowest slot's AES blocks.  Only ratios between splits
+// of one spec are used.
+static double tile_time(const ffss_spec *spec, uint32_t slots) {
+  if (spec->tuned) {
+    for (uint32_t i = 0; i < spec->tune.n_tried; ++i)
+      if (spec->tune.slots[i] == slots) return spec->tune.tile_us[i];
+    return 0.0;
+  }
+  uint64_t mx = 0;
+  make_sched(spec->host, slots, &mx);
+  return double(mx);
 }
 
 extern "C" int ffss_batch_destroy(ffss_batch *bt) {
@@ -1147,7 +1284,9 @@ extern "C" int ffss_batch_destroy(ffss_batch *bt) {
     if (bt->branch[c]) cudaStreamDestroy(bt->branch[c]);
   }
   if (bt->own) cudaStreamDestroy(bt->own);
+  ffss_ctx *ctx = bt->ctx;
   delete bt;
+  ctx_unref(ctx);
   return FFSS_OK;
 }
 
@@ -1158,6 +1297,7 @@ extern "C" int ffss_batch_create(ffss_ctx *ctx, uint32_t max_calls, ffss_batch *
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_batch *bt = new ffss_batch();
   bt->ctx = ctx;
+  ctx_ref(ctx);
   bt->cap = max_calls;
   bt->table_bytes = batch_table_bytes(max_calls);
   bt->next = 0;
@@ -1214,7 +1354,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
   if (n_calls > bt->cap) return fail(FFSS_ERR_SHAPE, "%u calls > batch capacity %u", n_calls, bt->cap);
   ffss_ctx *ctx = bt->ctx;
   // validate every call before touching any state
-  struct Item { BatchCall c; int cls; uint64_t tile_cost; uint64_t tiles; };
+  struct Item { BatchCall c; int cls; uint64_t tile_cost; uint64_t tiles; const ffss_spec *sp; };
   std::vector<Item> items;
   for (uint32_t i = 0; i < n_calls; ++i) {
     const ffss_call &c = calls[i];
@@ -1242,12 +1382,61 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
     it.c.sched = make_sched(S, batch_split(ctx, bt->force_slots, c.spec, c.n), &mx);
     it.tile_cost = mx;
     it.tiles = (c.n + it.c.sched.E - 1) / it.c.sched.E;
+    it.sp = c.spec;
     items.push_back(it);
   }
   // group by shape class; within a class the costliest tiles go first
   std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
     return a.cls != b.cls ? a.cls < b.cls : a.tile_cost > b.tile_cost;
   });
+  // The last wave of a class: the persistent CTAs take tiles in queue order,
+  // so when a class's tiles are not a multiple of the CTA count the final
+  // partial wave leaves SMs idle for up to one tile's time.  The class's last
+  // call runs its final r = (class tiles mod CTAs) tiles with a finer work
+  // split instead (more threads per element, fewer elements per tile), spread
+  // over more CTAs, when the estimated time of that tail,
+  // ceil(tiles' / CTAs) x tile time', is under 0.9 of one tile time.  The
+  // split never changes a share.  A forced split (plan or context) is kept.
+  if (!bt->force_slots && !ctx->force_slots) {
+    const uint64_t P = uint64_t(ctx->sm_count);
+    for (size_t i = 0; i < items.size(); ++i) {
+      if (i + 1 < items.size() && items[i + 1].cls == items[i].cls) continue;   // not the class's last call
+      uint64_t total = 0, count = 0;
+      for (size_t j = 0; j <= i; ++j)
+        if (items[j].cls == items[i].cls) { total += items[j].tiles; ++count; }
+      Item &it = items[i];
+      const uint64_t r = std::min<uint64_t>(total % P, it.tiles);
+      if (r == 0 || count + 1 > kBatchMaxCalls) continue;
+      const DevSpec &S = it.sp->host;
+      const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+      const uint32_t S0 = it.c.sched.S;
+      const uint64_t tail_first = (it.tiles - r) * it.c.sched.E, tail_n = it.c.n - tail_first;
+      const double t0 = tile_time(it.sp, S0);
+      double best = 0.9 * t0;
+      uint32_t best_s = 0;
+      for (uint32_t s1 = 2 * S0; t0 > 0 && s1 <= kMaxSlots && s1 <= nitems; s1 *= 2) {
+        const double t1 = tile_time(it.sp, s1);
+        const uint64_t e1 = 256 / s1, tiles1 = (tail_n + e1 - 1) / e1;
+        const double tt = double((tiles1 + P - 1) / P) * t1;
+        if (t1 > 0 && tt < best) {
+          best = tt;
+          best_s = s1;
+        }
+      }
+      if (!best_s) continue;
+      Item tail = it;
+      tail.c.e_first = tail_first;
+      tail.c.sched = make_sched(S, best_s, &tail.tile_cost);
+      tail.tiles = (tail_n + tail.c.sched.E - 1) / tail.c.sched.E;
+      if (it.tiles == r) {
+        it = tail;                      // the whole call is the tail
+      } else {
+        it.tiles -= r;
+        items.insert(items.begin() + i + 1, tail);
+        ++i;
+      }
+    }
+  }
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_batch::Slot &sl = bt->slot[bt->next];
   bt->next ^= 1;

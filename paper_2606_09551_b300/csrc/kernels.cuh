@@ -41,6 +41,7 @@ struct GateArgs {
   uint32_t *z0, *z1;
   unsigned long long *comm;   // [2] bytes sent by party 0 / 1, may be null
   uint64_t n;
+  uint64_t e_first;           // element of tile 0 (a batch may run a call's last tiles with another split)
   const uint32_t *t0;
 };
 
@@ -493,7 +494,7 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   const bool lead = slot == 0;
   const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
   const char *kb = b ? A.k1 : A.k0;
-  const uint64_t e = tile * E + le;
+  const uint64_t e = A.e_first + tile * E + le;
   const bool valid = e < A.n;
   unsigned long long sent = 0;
   // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's.
@@ -686,7 +687,8 @@ struct BatchCall {
   uint64_t *y0, *y1;
   uint32_t *z0, *z1;
   uint64_t n;
-  uint64_t tile_begin;     // first global tile of this call
+  uint64_t e_first;        // element of this entry's tile 0 (0, or where a call's re-split tail starts)
+  uint64_t tile_begin;     // first global tile of this entry
   uint32_t rd;             // n_out * 16 + degree
   uint32_t pad;
   Sched sched;
@@ -764,6 +766,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
           cur.k0 = c.k0; cur.k1 = c.k1; cur.x0 = c.x0; cur.x1 = c.x1;
           cur.y0 = c.y0; cur.y1 = c.y1; cur.z0 = c.z0; cur.z1 = c.z1;
           cur.n = c.n;
+          cur.e_first = c.e_first;
           cur.comm = nullptr;
           cur.t0 = t0;
           cur_sched = c.sched;

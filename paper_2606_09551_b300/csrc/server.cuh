@@ -165,7 +165,9 @@ extern "C" int ffss_server_destroy(ffss_server *sv) {
   if (sv->s_gen) cudaStreamDestroy(sv->s_gen);
   if (sv->s_eval) cudaStreamDestroy(sv->s_eval);
   if (sv->batch) ffss_batch_destroy(sv->batch);
+  ffss_ctx *ctx = sv->ctx;
   delete sv;
+  ctx_unref(ctx);
   return FFSS_OK;
 }
 
@@ -176,6 +178,7 @@ extern "C" int ffss_server_create(ffss_ctx *ctx, const ffss_server_cfg *cfg, ffs
   CUDA_TRY(cudaSetDevice(ctx->device));
   ffss_server *sv = new ffss_server();
   sv->ctx = ctx;
+  ctx_ref(ctx);
   sv->cfg = *cfg;
   sv->half_bytes = (cfg->key_budget_bytes / 2) & ~uint64_t(255);
   int rc = ffss_batch_create(ctx, kBatchMaxCalls, &sv->batch);

@@ -144,6 +144,7 @@ def lib():
         L.ffss_eval_pred.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp, vp]
         L.ffss_eval_lut.argtypes = [vp, vp, C.c_int, vp, vp, C.c_uint64, vp, vp]
         L.ffss_eval_pair.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
+        L.ffss_eval_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
         L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
         L.ffss_autotune.argtypes = [vp, vp, C.POINTER(Tune), vp]
@@ -380,6 +381,14 @@ def eval_pair(ctx: Context, cs: CompiledSpec, k0: Keys, k1: Keys, x0, x1, y0, y1
               stream=None):
     _check(lib().ffss_eval_pair(ctx.h, cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
                                 _ptr(z0), _ptr(z1), _ptr(comm), _stream(stream)))
+
+
+def eval_pair_host(ctx: Context, cs: CompiledSpec, k0: Keys, k1: Keys, x0, x1, y0, y1, z0, z1, comm=None,
+                   stream=None):
+    """The gate on HOST (CPU, ideally pinned) tensors: copies in, gate, copies
+    out, queued on `stream`; synchronize it before reading y*, z*."""
+    _check(lib().ffss_eval_pair_host(ctx.h, cs.h, k0.h, k1.h, _ptr(x0), _ptr(x1), x0.numel(), _ptr(y0), _ptr(y1),
+                                     _ptr(z0), _ptr(z1), _ptr(comm), _stream(stream)))
 
 
 class Batch:

@@ -158,3 +158,35 @@ def test_cancel_mid_flight(ctx):
     assert ei.value.code == INVALID
     sv.close()
     torch.cuda.synchronize()
+
+
+def test_context_freed_after_its_last_user():
+    """Objects made from a context keep it alive: destroying the context
+    first and freeing a spec, pooled keys and a batch plan afterwards (the
+    order a garbage collector may pick) leaves CUDA's error state clean, and
+    a later context works."""
+    import ctypes as C
+    import torch
+    L = F.lib()
+    h = C.c_void_p()
+    assert L.ffss_ctx_create(0, C.byref(h)) == 0
+    sp = S.gelu4()
+    ctx = F.Context.__new__(F.Context)
+    ctx.device, ctx.h = 0, h
+    dev_cs = F.CompiledSpec(sp, ctx)
+    ctx.reserve_key_pool(64 << 20)
+    k0, k1 = F.Keys.alloc_pair(dev_cs, 1000)
+    bt = F.Batch(ctx, 4)
+    assert L.ffss_ctx_destroy(h) == 0          # the context goes first
+    ctx.h = None
+    k0.close()
+    k1.close()
+    bt.close()
+    dev_cs.close()
+    other = F.Context(0)
+    cs2 = F.CompiledSpec(S.gelu4(), other)
+    x = I.uniform_x(300, 16, 63)
+    y0, y1, z0, z1 = _eval(other, cs2, F.Keys(cs2, 300, 0), F.Keys(cs2, 300, 1), x, 702)
+    yp, zp = O.Spec(**sp.descriptor()).plain_eval(x)
+    assert np.array_equal(y0 + y1, yp[:, 0]) and np.array_equal(z0 ^ z1, zp)
+    torch.cuda.synchronize()
