@@ -55,7 +55,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.259368e9 + 8.76928e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.258199e9 + 8.687104e6) / 65536}
 
 
 def parse():
@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--gpt2-layers", type=int, default=1, help="layers per request in the 32-request batch")
     ap.add_argument("--no-gpt2", action="store_true", help="skip the 32-request GPT-2 batch run")
     ap.add_argument("--no-xhat", action="store_true", help="skip the x^-basis variant run")
+    ap.add_argument("--no-serial", action="store_true",
+                    help="skip the streamed forms' second pass that times the dealer and the evaluation apart")
     ap.add_argument("--no-rescale", action="store_true", help="skip the layer-rescale (ARS) run")
     ap.add_argument("--no-blocks", action="store_true", help="skip the softmax / LayerNorm block runs")
     ap.add_argument("--no-cpu", action="store_true")
@@ -532,7 +534,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_served:
         served = run_served(ctx, args, dev)
     if not args.no_large:
-        large = run_large_layer(ctx, dev, tune=not args.no_autotune)
+        large = run_large_layer(ctx, dev, tune=not args.no_autotune, no_serial=args.no_serial)
     if not args.no_gpt2:
         gpt2 = run_gpt2_batch(ctx, args, dev)
 
@@ -604,10 +606,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic (seeded activations; random masks, keys and triples from the GPU dealer)",
-        "config": dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" %
-                       (sum(2 * css[c.name].shape.key_bytes_per_elem * c.n for c in calls) / 1e9),
-                       parallelism="replicas" if world > 1 else "single GPU, both parties on it",
-                       key_sets_resident=G, timed_groups=-(-args.steps // G)),
+        "config": full_config(config, calls, world),
+        "timing": {"key_sets_resident": G, "timed_groups": -(-args.steps // G)},
         "per_op_ms": per_op_ms,
         "autotune": tuning,
         "keygen": {"ms_per_step": keygen_ms, "elements_per_s": total / (keygen_ms * 1e-3)},
@@ -967,19 +967,36 @@ def run_plain_fifo(ctx, dev, trace, pool_bytes, seed):
                     "into a %d GB pool just before each chunk's gate launch" % (pool_bytes >> 30)}
 
 
+def _serial_rates(ctx, pending, max_active, aes_blocks):
+    """The same requests once more through a server that never overlaps the
+    dealer with an evaluation (FFSS_SERVER_SERIAL): the evaluation launches'
+    GPU time alone gives the online (keygen-excluded) rate, the dealer
+    launches' the dealer rate.  Same call ids, so the same keys and shares."""
+    from paper_2606_09551_b300 import fusefss as F
+    from paper_2606_09551_b300 import inputs as I
+    sv = F.Server(ctx, 64 << 30, max_active, 1 << 22, I.KEY_SEED, serial=True)
+    for layers, _, cid in pending:
+        sv.submit(layers, 0.0, call_id_base=cid)
+    sv.run()
+    st = sv.summary()
+    sv.close()
+    ev_s, gen_s = st["eval_ms"] * 1e-3, st["gen_ms"] * 1e-3
+    return {"elements_per_s": st["elements"] / ev_s, "eval_s": ev_s,
+            "aes_roofline_frac": aes_blocks[1] / ev_s / _aes_roofline(),
+            "dealer_elements_per_s": st["elements"] / gen_s, "dealer_s": gen_s,
+            "dealer_aes_roofline_frac": aes_blocks[0] / gen_s / _aes_roofline(),
+            "serial_span_s": (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3,
+            "basis": "keygen excluded: GPU time of the batched evaluation launches of a second pass in "
+                     "which the dealer never overlaps an evaluation (same keys and shares)"}
+
+
 def _server_result(sv, nreq, clk, wall, aes_blocks):
     st = sv.summary()
     infos = [sv.request_info(i) for i in range(nreq)]
     queue = sorted(max(0.0, r["admitted_ms"] - r["arrival_ms"]) for r in infos)
     req = sorted(r["done_ms"] - r["arrival_ms"] for r in infos)
     span_s = (st["last_done_ms"] - st["first_admit_ms"]) * 1e-3
-    eval_s = st["eval_ms"] * 1e-3
     return st, {"value": st["elements"] / span_s, "unit": "elements/s",
-                "online": {"elements_per_s": st["elements"] / eval_s, "eval_s": eval_s,
-                           "aes_roofline_frac": aes_blocks[1] / eval_s / _aes_roofline(),
-                           "basis": "keygen excluded: GPU time of the batched evaluation launches alone "
-                                    "(events on the evaluation stream; the dealer of the next step runs "
-                                    "meanwhile on its own stream)"},
                 "aes_blocks": aes_blocks[0] + aes_blocks[1],
                 "aes_roofline_frac": (aes_blocks[0] + aes_blocks[1]) / span_s / _aes_roofline(),
                 "note": "includes the on-device dealer: keys are streamed through the key pool, not preloaded; "
@@ -1032,6 +1049,8 @@ def run_served(ctx, args, dev):
                 "config": "BERT-large shapes (hidden 1024, 16 heads, MLP 4096), L log-uniform [16, 2048], "
                           "Poisson 20 req/s, 64 GB key budget, max 8 admitted, chunks <= 4M elements"})
     sv.close()
+    if not args.no_serial:
+        res["online"] = _serial_rates(ctx, pending, 8, _stream_aes([p_[0][0] for p_ in pending], nlay))
     if not args.no_served_plain:
         # the same trace in the plain per-operator form; the server keeps half
         # of its 64 GB key pool for the chunks it evaluates (the other half is
@@ -1079,10 +1098,12 @@ def run_gpt2_batch(ctx, args, dev):
                 "config": "32 GPT-2-small requests (hidden 768, 12 heads, MLP 3072, 2 LayerNorms), "
                           "L uniform [32, 1024], %d of 12 layers each, 64 GB key budget" % nlay})
     sv.close()
+    if not args.no_serial:
+        res["online"] = _serial_rates(ctx, pending, 32, _stream_aes([p_[0][0] for p_ in pending], nlay))
     return res
 
 
-def run_large_layer(ctx, dev, tune=True):
+def run_large_layer(ctx, dev, tune=True, no_serial=False):
     """One GPT-style 2.7B layer (hidden 2560, 32 heads, MLP 10240 with SiLU,
     seq 1024): SiLU on 1024 x 10240, softmax nExp on 32 x 1024 x 1024, the
     reciprocal of the 32 x 1024 row sums and rsqrt for two LayerNorms (2 x
@@ -1114,11 +1135,8 @@ def run_large_layer(ctx, dev, tune=True):
     key_tb = sum(2 * css[n].shape.key_bytes_per_elem * xs[n].numel() for n in xs) / 1e12
     sv.close()
     deal, online = _stream_aes([ops], 1)
-    eval_s = st["eval_ms"] * 1e-3
     return {"value": total / span_s, "unit": "elements/s", "elements": int(total), "layer_ms": st["layer_ms_max"],
-            "online": {"elements_per_s": total / eval_s, "eval_s": eval_s,
-                       "aes_roofline_frac": online / eval_s / _aes_roofline(),
-                       "basis": "keygen excluded: GPU time of the batched evaluation launches alone"},
+            "online": None if no_serial else _serial_rates(ctx, [([ops], 0.0, call_base)], 1, (deal, online)),
             "aes_blocks": deal + online, "aes_roofline_frac": (deal + online) / span_s / _aes_roofline(),
             "steps": int(st["steps"]), "chunks": int(st["chunks"]), "keys_tb_streamed": key_tb,
             "wall_s": wall, "clocks": clk.summary(),
@@ -1131,28 +1149,78 @@ def run_large_layer(ctx, dev, tune=True):
 # reference arm: the oracle (the paper ships no code), on the host cores
 # ---------------------------------------------------------------------------
 
-def run_reference(args):
+def full_config(config, calls, world):
+    """The workload's config as both arms print it: the workload, how L2 is
+    kept out of the measurement, and the process layout."""
+    from paper_2606_09551_b300 import fusefss as F
+    key_gb = sum(2 * F.CompiledSpec(c.spec).shape.key_bytes_per_elem * c.n for c in calls) / 1e9
+    return dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" % key_gb,
+                parallelism="replicas x %d" % world if world > 1 else "one process; both parties in it")
+
+
+def run_reference(args, world):
+    """The oracle on the host cores.  A step evaluates (both parties, online
+    phase) a fixed sample of every operator of the workload, the same
+    fraction of each, sized so that all warm-up and timed steps take about
+    two minutes; ms_per_step is that step's measured wall time.  The sample's
+    keys are dealt once by the oracle dealer before timing (the evaluation's
+    cost does not depend on the key values)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    from paper_2606_09551_b300 import inputs as I
     calls, config = workload(args.workload)
-    budget = args.cpu_seconds / 4.0
-    for _ in range(args.warmup):
-        oracle_rates(calls, budget / 4.0)
+    threads = os.cpu_count() or 1
+    step_s = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
+    # per-element oracle time estimate: 0.2 us per AES block per core, both parties
+    per_elem = {}
+    ospec = {}
+    for c in calls:
+        o = O.Spec(**c.spec.descriptor())
+        ospec[c.name] = o
+        per_elem[c.name] = 0.2e-6 * 2 * (sum(f for f, _, _ in o.queries())
+                                        + (o.M - 1) * (o.k * (1 + (o.p + 1) // 2) + (o.p + 1) // 2))
+    est = sum(c.n * per_elem[c.name] for c in calls) / threads
+    frac = min(1.0, step_s / est)
+    sample = {c.name: max(1, int(round(c.n * frac))) for c in calls}
+    work = []
+    for c in calls:
+        ns = sample[c.name]
+        for i in range(threads):
+            a, b = i * ns // threads, (i + 1) * ns // threads
+            if b > a:
+                work.append((c, a, b))
+
+    def deal(w):
+        c, a, b = w
+        return O.dealer(ospec[c.name], I.KEY_SEED, c.call_id, a, b - a, c.x[a:b])
+
+    with ThreadPoolExecutor(threads) as ex:
+        dealt = list(ex.map(deal, work))
+
+    def ev(i):
+        c = work[i][0]
+        k0, k1, x0, x1 = dealt[i]
+        O.eval_pair(ospec[c.name], k0, k1, x0, x1)
+
     times = []
-    threads = None
-    samples = None
-    for _ in range(args.steps):
-        rates, samples, threads = oracle_rates(calls, budget)
-        times.append(sum(c.n * rates[c.name] for c in calls))
-    total = sum(c.n for c in calls)
+    with ThreadPoolExecutor(threads) as ex:
+        for s_ in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            list(ex.map(ev, range(len(work))))
+            if s_ >= args.warmup:
+                times.append(time.perf_counter() - t0)
     per_step_s = statistics.mean(times)
+    total = sum(sample.values())
     value = total / per_step_s
-    desc = ("oracle eval_pair (both parties) per step on the first " +
-            ", ".join(f"{samples[k]} {k}" for k in samples) + " elements; per-op s/element scaled to the layer")
+    desc = ("oracle eval_pair (both parties) per step on %s elements (%.4f of each operator: %s), "
+            "%d threads" % (total, frac, ", ".join(f"{sample[k]} {k}" for k in sample), threads))
     return {
         "impl": "reference",
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
-        "value": value, "unit": "elements/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic", "config": config,
+        "dtype": "u64", "data": "synthetic", "config": full_config(config, calls, world),
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1191,7 +1259,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args)), flush=True)
+            print(json.dumps(run_reference(args, world)), flush=True)
         return
     if world > 1:
         import torch

@@ -431,10 +431,13 @@ int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, uint32_t n_ca
 
 typedef struct ffss_server ffss_server;
 
+#define FFSS_SERVER_SERIAL 1u   /* flags: the dealer never overlaps an evaluation (measurement) */
+
 typedef struct {
     uint64_t key_budget_bytes;  /* device key pool, split in two halves (double buffering) */
     uint32_t max_active;        /* requests admitted at once */
-    uint32_t pad;
+    uint32_t flags;             /* 0, or FFSS_SERVER_SERIAL: each step's dealer work waits for the
+                                   previous evaluation, so eval_ms and gen_ms time each alone */
     uint64_t chunk_elems;       /* largest piece of one operator call per step */
     uint8_t seed[16];           /* dealer AES-128 seed */
 } ffss_server_cfg;
@@ -470,7 +473,10 @@ typedef struct {
     uint64_t elements, steps, chunks, layers;
     double first_admit_ms, last_done_ms;
     double layer_ms_p50, layer_ms_p99, layer_ms_max;
-    double eval_ms;             /* GPU time of the batched evaluations (dealer excluded) */
+    double eval_ms;             /* GPU time of the batched evaluation launches (dealer excluded;
+                                   without FFSS_SERVER_SERIAL the next step's dealer runs
+                                   meanwhile on the same SMs) */
+    double gen_ms;              /* GPU time of the dealer launches */
 } ffss_server_stats;
 
 /* The served form (no counterpart in the paper, which evaluates one model at
@@ -551,7 +557,10 @@ int ffss_beaver_mul(ffss_ctx *ctx, const uint64_t *t0_dev, const uint64_t *t1_de
  * call_base + j.  ffss_softmax_eval consumes them (FFSS_ERR_SHAPE on reuse);
  * x, y are [rows][L] u64 shares; comm[party] accumulates every step's bytes.
  * ffss_softmax_info: tree rounds, key bytes (both parties) and elements
- * through gates per evaluation. */
+ * through gates per evaluation.  An evaluation runs as one CUDA graph on a
+ * stream the plan owns (captured at the first call and again when x, y or
+ * comm change), ordered after the work queued on `stream`; later work on
+ * `stream` waits for it.  The same holds for the LayerNorm plan below. */
 typedef struct ffss_softmax ffss_softmax;
 int ffss_softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], uint64_t rows, uint64_t L,
                         ffss_softmax **out);

@@ -217,6 +217,62 @@ extern "C" int ffss_beaver_mul(ffss_ctx *ctx, const uint64_t *t0_dev, const uint
 
 enum { kSmRelu, kSmExp, kSmShiftE, kSmRecip, kSmShiftT, kSmShiftP, kSmGates };
 
+// A block plan's evaluation as one CUDA graph on the plan's own stream:
+// captured on first use and again whenever the caller's buffers change,
+// replayed otherwise, so the plan's chain of small dependent launches runs
+// without the host's per-launch gaps.  Each run is ordered after the work
+// queued on the caller's stream, and later work on that stream waits for it.
+struct PlanGraph {
+  cudaStream_t own = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void *key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+  void release() {
+    if (own) cudaStreamSynchronize(own);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (in) cudaEventDestroy(in);
+    if (out) cudaEventDestroy(out);
+    if (own) cudaStreamDestroy(own);
+    exec = nullptr; in = out = nullptr; own = nullptr;
+  }
+
+  template <class Issue>
+  int run(const void *const k[5], cudaStream_t st, Issue issue) {
+    if (!own) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&in, cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&out, cudaEventDisableTiming));
+    }
+    if (!exec || memcmp(key, k, sizeof(key)) != 0) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(own, cudaStreamCaptureModeThreadLocal));
+      const int rc = issue(own);
+      const cudaError_t e = cudaStreamEndCapture(own, &g);
+      if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : fail(FFSS_ERR_CUDA, "plan capture: %s", cudaGetErrorString(e));
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        exec = nullptr;
+        return fail(FFSS_ERR_CUDA, "plan graph: %s", cudaGetErrorString(ei));
+      }
+      memcpy(key, k, sizeof(key));
+    }
+    CUDA_TRY(cudaEventRecord(in, st));
+    CUDA_TRY(cudaStreamWaitEvent(own, in, 0));
+    CUDA_TRY(cudaGraphLaunch(exec, own));
+    CUDA_TRY(cudaEventRecord(out, own));
+    CUDA_TRY(cudaStreamWaitEvent(st, out, 0));
+    return FFSS_OK;
+  }
+};
+
 struct ffss_softmax {
   ffss_ctx *ctx;
   const ffss_spec *g[kSmGates];
@@ -235,11 +291,13 @@ struct ffss_softmax {
   uint64_t *sh;                    // share scratch (see ffss_softmax_create)
   uint32_t *z;                     // the gates' Boolean outputs (not used by the block)
   int keyed;
+  PlanGraph graph;
 };
 
 extern "C" int ffss_softmax_destroy(ffss_softmax *sm) {
   if (!sm) return FFSS_OK;
   cudaSetDevice(sm->ctx->device);
+  sm->graph.release();
   if (sm->keys) cudaFree(sm->keys);
   if (sm->sh) cudaFree(sm->sh);
   if (sm->z) cudaFree(sm->z);
@@ -271,6 +329,10 @@ static int softmax_create(ffss_ctx *ctx, const ffss_spec *const gates[6], const 
   ffss_softmax *sm = new ffss_softmax();
   sm->ctx = ctx;
   ctx_ref(ctx);
+  if (int rc = gate_attrs_all()) {
+    ffss_softmax_destroy(sm);
+    return rc;
+  }
   for (int i = 0; i < kSmGates; ++i) sm->g[i] = gates[i];
   sm->newton = newton;
   for (int i = 0; i < 2; ++i) sm->gn[i] = newton ? newton_gates[i] : nullptr;
@@ -360,13 +422,10 @@ extern "C" int ffss_softmax_keygen(ffss_softmax *sm, const uint8_t seed[16], uin
 // Scratch layout (u64 words, party 0 then party 1 for each array):
 //   c: two ping-pong tree buffers of N; d, r: N / 2 each (held in one N);
 //   D, E, E', P: N each; s, t, t': rows each.
-extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
-                                 uint64_t *y1, uint64_t *comm, void *stream) {
-  if (!sm || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_softmax_eval: NULL argument");
-  if (!sm->keyed) return fail(FFSS_ERR_SHAPE, "ffss_softmax_eval: keys not generated (or already used)");
+// Queue every step of the softmax on st (one gate launch per step).
+static int softmax_issue(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, uint64_t *y0, uint64_t *y1,
+                         uint64_t *comm, cudaStream_t st) {
   const ffss_ctx *ctx = sm->ctx;
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t rows = sm->rows, L = sm->L, N = rows * L;
   uint64_t *p = sm->sh;
   auto take = [&](uint64_t words) { uint64_t *q = p; p += words; return q; };
@@ -435,6 +494,18 @@ extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uin
   add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kSmShiftP));
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_softmax_eval(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                                 uint64_t *y1, uint64_t *comm, void *stream) {
+  if (!sm || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_softmax_eval: NULL argument");
+  if (!sm->keyed) return fail(FFSS_ERR_SHAPE, "ffss_softmax_eval: keys not generated (or already used)");
+  CUDA_TRY(cudaSetDevice(sm->ctx->device));
+  const void *key[5] = {x0, x1, y0, y1, comm};
+  const int rc = sm->graph.run(key, static_cast<cudaStream_t>(stream),
+                               [&](cudaStream_t s) { return softmax_issue(sm, x0, x1, y0, y1, comm, s); });
+  if (rc) return rc;
   sm->keyed = 0;   // one-time keys
   return FFSS_OK;
 }
@@ -462,11 +533,13 @@ struct ffss_layernorm {
   uint64_t *sh;
   uint32_t *z;
   int keyed;
+  PlanGraph graph;
 };
 
 extern "C" int ffss_layernorm_destroy(ffss_layernorm *ln) {
   if (!ln) return FFSS_OK;
   cudaSetDevice(ln->ctx->device);
+  ln->graph.release();
   if (ln->keys) cudaFree(ln->keys);
   if (ln->sh) cudaFree(ln->sh);
   if (ln->z) cudaFree(ln->z);
@@ -499,6 +572,10 @@ static int layernorm_create(ffss_ctx *ctx, const ffss_spec *const gates[5], cons
   ffss_layernorm *ln = new ffss_layernorm();
   ln->ctx = ctx;
   ctx_ref(ctx);
+  if (int rc = gate_attrs_all()) {
+    ffss_layernorm_destroy(ln);
+    return rc;
+  }
   for (int i = 0; i < kLnGates; ++i) ln->g[i] = gates[i];
   ln->newton = newton;
   for (int i = 0; i < 3; ++i) ln->gn[i] = newton ? newton_gates[i] : nullptr;
@@ -579,13 +656,10 @@ extern "C" int ffss_layernorm_keygen(ffss_layernorm *ln, const uint8_t seed[16],
   return FFSS_OK;
 }
 
-extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
-                                   uint64_t *y1, uint64_t *comm, void *stream) {
-  if (!ln || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_layernorm_eval: NULL argument");
-  if (!ln->keyed) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_eval: keys not generated (or already used)");
+// Queue every step of the LayerNorm on st.
+static int layernorm_issue(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *x1, uint64_t *y0, uint64_t *y1,
+                           uint64_t *comm, cudaStream_t st) {
   const ffss_ctx *ctx = ln->ctx;
-  CUDA_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const uint64_t rows = ln->rows, H = ln->H, N = rows * H;
   uint64_t *p = ln->sh;
   auto take = [&](uint64_t words) { uint64_t *q = p; p += words; return q; };
@@ -647,6 +721,18 @@ extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const
   add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kLnShiftY));
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
+  return FFSS_OK;
+}
+
+extern "C" int ffss_layernorm_eval(ffss_layernorm *ln, const uint64_t *x0, const uint64_t *x1, uint64_t *y0,
+                                   uint64_t *y1, uint64_t *comm, void *stream) {
+  if (!ln || !x0 || !x1 || !y0 || !y1) return fail(FFSS_ERR_INVALID, "ffss_layernorm_eval: NULL argument");
+  if (!ln->keyed) return fail(FFSS_ERR_SHAPE, "ffss_layernorm_eval: keys not generated (or already used)");
+  CUDA_TRY(cudaSetDevice(ln->ctx->device));
+  const void *key[5] = {x0, x1, y0, y1, comm};
+  const int rc = ln->graph.run(key, static_cast<cudaStream_t>(stream),
+                               [&](cudaStream_t s) { return layernorm_issue(ln, x0, x1, y0, y1, comm, s); });
+  if (rc) return rc;
   ln->keyed = 0;
   return FFSS_OK;
 }

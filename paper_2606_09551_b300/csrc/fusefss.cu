@@ -937,13 +937,33 @@ static uint32_t gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t 
   return choose_sched(ctx, spec->host, n).S;
 }
 
+// The gate kernel's shared-memory limit, raised once per process.
+template <int R, int D>
+static int gate_attr() {
+  static std::once_flag once;
+  static int rc = FFSS_OK;
+  std::call_once(once, [] { rc = set_smem(gate_kernel<R, D>, gate_smem_bytes()); });
+  return rc;
+}
+
+// Every gate kernel's attribute, so that later launches set none (a stream
+// capture of them then records launches only).
+static int gate_attrs_all() {
+  int rc = gate_attr<1, 0>();
+  if (!rc) rc = gate_attr<1, 1>();
+  if (!rc) rc = gate_attr<1, 2>();
+  if (!rc) rc = gate_attr<1, 3>();
+  if (!rc) rc = gate_attr<2, 0>();
+  if (!rc) rc = gate_attr<2, 1>();
+  if (!rc) rc = gate_attr<3, 0>();
+  if (!rc) rc = gate_attr<4, 0>();
+  return rc;
+}
+
 template <int R, int D>
 static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st) {
   const size_t smem = gate_smem_bytes();
-  static std::once_flag once;
-  int rc = FFSS_OK;
-  std::call_once(once, [&] { rc = set_smem(gate_kernel<R, D>, smem); });
-  if (rc) return rc;
+  if (int rc = gate_attr<R, D>()) return rc;
   const uint64_t tiles = (A.g.n + A.sched.E - 1) / A.sched.E;
   const int grid = int(tiles < uint64_t(ctx->sm_count) ? tiles : uint64_t(ctx->sm_count));
   gate_kernel<R, D><<<grid, kGateThreads, smem, st>>>(A);
@@ -1405,10 +1425,49 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
       for (size_t j = 0; j <= i; ++j)
         if (items[j].cls == items[i].cls) { total += items[j].tiles; ++count; }
       Item &it = items[i];
-      const uint64_t r = std::min<uint64_t>(total % P, it.tiles);
-      if (r == 0 || count + 1 > kBatchMaxCalls) continue;
       const DevSpec &S = it.sp->host;
       const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+      if (count == 1 && it.sp->tuned) {
+        // a call alone in its class: choose its head split and its tail's
+        // split together from the tuner's tile times, minimising
+        // (full waves x head tile time) + (re-split tail waves x tail tile time)
+        const ffss_tune &tn = it.sp->tune;
+        double best_t = -1;
+        uint32_t best_h = it.c.sched.S, best_t_s = it.c.sched.S;
+        for (uint32_t a = 0; a < tn.n_tried; ++a) {
+          const uint32_t sh = tn.slots[a];
+          const uint64_t eh = 256 / sh, th = (it.c.n + eh - 1) / eh, rr = th % P;
+          for (uint32_t b = 0; b < tn.n_tried; ++b) {
+            const uint32_t st = tn.slots[b];
+            if (st < sh) continue;
+            const uint64_t et = 256 / st, tt = (rr * eh + et - 1) / et;
+            const double t = double(th / P) * tn.tile_us[a] + double((tt + P - 1) / P) * tn.tile_us[b];
+            if (best_t < 0 || t < best_t) {
+              best_t = t;
+              best_h = sh;
+              best_t_s = st;
+            }
+          }
+        }
+        it.c.sched = make_sched(S, best_h, &it.tile_cost);
+        it.tiles = (it.c.n + it.c.sched.E - 1) / it.c.sched.E;
+        const uint64_t rr = it.tiles % P;
+        if (best_t_s == best_h || rr == 0) continue;
+        Item tail = it;
+        tail.c.e_first = (it.tiles - rr) * it.c.sched.E;
+        tail.c.sched = make_sched(S, best_t_s, &tail.tile_cost);
+        tail.tiles = (it.c.n - tail.c.e_first + tail.c.sched.E - 1) / tail.c.sched.E;
+        if (it.tiles == rr) {
+          it = tail;
+        } else {
+          it.tiles -= rr;
+          items.insert(items.begin() + i + 1, tail);
+          ++i;
+        }
+        continue;
+      }
+      const uint64_t r = std::min<uint64_t>(total % P, it.tiles);
+      if (r == 0 || count + 1 > kBatchMaxCalls) continue;
       const uint32_t S0 = it.c.sched.S;
       const uint64_t tail_first = (it.tiles - r) * it.c.sched.E, tail_n = it.c.n - tail_first;
       const double t0 = tile_time(it.sp, S0);

@@ -51,6 +51,8 @@ struct SrvChunk {
 
 struct SrvStep {
   int half;
+  cudaEvent_t gen_start;        // on the dealer stream, before the step's dealer launches
+  cudaEvent_t gen_done;         // on the dealer stream, after them
   cudaEvent_t start;            // on the eval stream, after the dealer's chunks are ready
   cudaEvent_t done;
   std::vector<SrvChunk> chunks;
@@ -76,6 +78,7 @@ struct ffss_server {
   uint64_t elements = 0, steps = 0, chunks = 0;
   double first_admit = -1, last_done = -1;
   double eval_ms = 0;                 // GPU time of the batched evaluations alone
+  double gen_ms = 0;                  // GPU time of the dealer launches alone
   std::vector<double> all_layer_ms;
 };
 
@@ -99,9 +102,12 @@ static cudaEvent_t srv_event(ffss_server *sv) {
 // Retire a completed step: advance each chunk's request, close layers.
 static void srv_retire(ffss_server *sv, SrvStep &st) {
   const double t = srv_gpu_ms(sv, st.done);
-  float ev_ms = 0;
+  float ev_ms = 0, gen_ms = 0;
   if (cudaEventElapsedTime(&ev_ms, st.start, st.done) == cudaSuccess) sv->eval_ms += ev_ms;
+  if (cudaEventElapsedTime(&gen_ms, st.gen_start, st.gen_done) == cudaSuccess) sv->gen_ms += gen_ms;
   sv->free_events.push_back(st.start);
+  sv->free_events.push_back(st.gen_start);
+  sv->free_events.push_back(st.gen_done);
   for (auto &c : st.chunks) {
     SrvReq &r = sv->reqs[c.req];
     ffss_keys_release(c.k0);
@@ -156,6 +162,8 @@ extern "C" int ffss_server_destroy(ffss_server *sv) {
   for (auto &st : sv->inflight) {
     cudaEventDestroy(st.done);
     cudaEventDestroy(st.start);
+    cudaEventDestroy(st.gen_start);
+    cudaEventDestroy(st.gen_done);
   }
   for (int h = 0; h < 2; ++h) {
     if (sv->pool[h]) cudaFree(sv->pool[h]);
@@ -281,6 +289,8 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
   // long one takes the room that is left and goes on in the next steps.
   SrvStep st;
   st.half = h;
+  st.gen_start = srv_event(sv);
+  CUDA_TRY(cudaEventRecord(st.gen_start, sv->s_gen));
   std::vector<ffss_call> calls;
   uint64_t used = 0;
   std::vector<std::pair<uint64_t, uint32_t>> order;
@@ -349,6 +359,7 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
     }
   }
   if (calls.empty()) {
+    sv->free_events.push_back(st.gen_start);
     bool waiting = false;
     for (auto &r : sv->reqs) waiting |= r.state == 0 || r.state == 1;
     *idle = (sv->inflight.empty() && !waiting) ? 1 : 0;
@@ -356,16 +367,17 @@ extern "C" int ffss_server_step(ffss_server *sv, int *idle) {
     return FFSS_OK;
   }
   *idle = 0;
-  cudaEvent_t gen_done = srv_event(sv);
-  CUDA_TRY(cudaEventRecord(gen_done, sv->s_gen));
-  CUDA_TRY(cudaStreamWaitEvent(sv->s_eval, gen_done, 0));
+  st.gen_done = srv_event(sv);
+  CUDA_TRY(cudaEventRecord(st.gen_done, sv->s_gen));
+  CUDA_TRY(cudaStreamWaitEvent(sv->s_eval, st.gen_done, 0));
   st.start = srv_event(sv);
   CUDA_TRY(cudaEventRecord(st.start, sv->s_eval));
   int rc = ffss_batch_eval(sv->batch, calls.data(), uint32_t(calls.size()), nullptr, sv->s_eval);
-  sv->free_events.push_back(gen_done);
   if (rc) return rc;
   st.done = srv_event(sv);
   CUDA_TRY(cudaEventRecord(st.done, sv->s_eval));
+  // serial mode: the next step's dealer starts after this evaluation
+  if (sv->cfg.flags & FFSS_SERVER_SERIAL) CUDA_TRY(cudaStreamWaitEvent(sv->s_gen, st.done, 0));
   CUDA_TRY(cudaEventRecord(sv->half_free[h], sv->s_eval));
   // the next dealer pass into this half must wait for this evaluation
   sv->half_used[h] = true;
@@ -420,6 +432,7 @@ extern "C" int ffss_server_summary(ffss_server *sv, ffss_server_stats *out) {
   out->first_admit_ms = sv->first_admit;
   out->last_done_ms = sv->last_done;
   out->eval_ms = sv->eval_ms;
+  out->gen_ms = sv->gen_ms;
   if (!sv->all_layer_ms.empty()) {
     std::vector<double> v = sv->all_layer_ms;
     std::sort(v.begin(), v.end());

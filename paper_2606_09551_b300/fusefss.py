@@ -72,7 +72,7 @@ vp = C.c_void_p
 
 
 class ServerCfg(C.Structure):
-    _fields_ = [("key_budget_bytes", C.c_uint64), ("max_active", C.c_uint32), ("pad", C.c_uint32),
+    _fields_ = [("key_budget_bytes", C.c_uint64), ("max_active", C.c_uint32), ("flags", C.c_uint32),
                 ("chunk_elems", C.c_uint64), ("seed", C.c_uint8 * 16)]
 
 
@@ -94,7 +94,8 @@ class RequestStats(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("elements", C.c_uint64), ("steps", C.c_uint64), ("chunks", C.c_uint64), ("layers", C.c_uint64),
                 ("first_admit_ms", C.c_double), ("last_done_ms", C.c_double), ("layer_ms_p50", C.c_double),
-                ("layer_ms_p99", C.c_double), ("layer_ms_max", C.c_double), ("eval_ms", C.c_double)]
+                ("layer_ms_p99", C.c_double), ("layer_ms_max", C.c_double), ("eval_ms", C.c_double),
+                ("gen_ms", C.c_double)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -427,9 +428,9 @@ class Server:
     """Continuous-batching request loop (native scheduler in the library)."""
 
     def __init__(self, ctx: Context, key_budget_bytes: int, max_active: int, chunk_elems: int,
-                 seed: bytes):
+                 seed: bytes, serial: bool = False):
         self.ctx = ctx
-        cfg = ServerCfg(key_budget_bytes, max_active, 0, chunk_elems,
+        cfg = ServerCfg(key_budget_bytes, max_active, 1 if serial else 0, chunk_elems,
                         (C.c_uint8 * 16).from_buffer_copy(bytes(seed)))
         h = vp()
         _check(lib().ffss_server_create(ctx.h, C.byref(cfg), C.byref(h)))

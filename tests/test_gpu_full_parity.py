@@ -6,11 +6,11 @@ per-operator launches (and the layer once more as one batched launch), the
 GPT-2 batch, the BERT-large trace and the 2.7B-scale layer through the
 continuous-batching server with on-device key streaming (64 GB pool, 4 M
 element chunks), all with autotuned work splits.  The GPU shares of every
-planned chunk (every element of the first two workloads; at least 10^6
-elements per operator of the others) are hashed and compared with the
-digests the oracle wrote for the same seeded inputs
-(tests/golden/share_digests/, written by make_share_digests.py from the
-oracle alone).  On a mismatch the oracle is run live on the chunk to name
+planned chunk (every element of the first two workloads, in the plain and
+the batched form; at least 10^6 elements per operator of the others) are
+hashed and compared with the digests the oracle wrote for the same seeded
+inputs (tests/golden/share_digests/, written by make_share_digests.py from
+the oracle alone).  On a mismatch the oracle is run live on the chunk to name
 the first differing element and share."""
 import numpy as np
 import pytest
@@ -164,10 +164,13 @@ def _served(ctx, reqs, css, max_active, arrivals=True):
 
 
 def test_single_gelu4_every_element(ctx):
+    """Plain launch, and the batched form (whose single call may run its
+    head and its last wave with different work splits)."""
     reqs = D.build("gelu4")
     css = _compile(ctx, reqs)
     checked = _check("gelu4", reqs, _plain(ctx, reqs, css))
     assert checked["gelu4"] == 65536
+    _check("gelu4", reqs, _batched(ctx, reqs, css))
 
 
 def test_bert_layer_every_element_plain_and_batched(ctx):

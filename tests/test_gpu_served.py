@@ -253,3 +253,26 @@ def test_staggered_arrivals(ctx):
             q0, q1 = torch.empty_like(z0), torch.empty_like(z1)
             F.eval_pair(ctx, cs, k0, k1, x0, x1, p0, p1, q0, q1)
             assert torch.equal(p0, y0) and torch.equal(p1, y1) and torch.equal(q0, z0) and torch.equal(q1, z1)
+
+
+def test_serial_mode_same_shares(ctx):
+    """FFSS_SERVER_SERIAL keeps the dealer and the evaluation apart (for
+    timing each alone): the shares are those of the default mode, and both
+    GPU times are recorded."""
+    css = [F.CompiledSpec(S.gelu8(), ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    out = []
+    for serial in (False, True):
+        sv = F.Server(ctx, 48 << 20, 2, 1 << 20, I.KEY_SEED, serial=serial)
+        reqs = [_request(ctx, css, sz, 300 + i) for i, sz in enumerate([[3000, 900], [500, 2000]])]
+        for i, r in enumerate(reqs):
+            sv.submit(r, 0.0, call_id_base=1300 + 50 * i)
+        sv.run()
+        st = sv.summary()
+        sv.close()
+        assert st["eval_ms"] > 0 and st["gen_ms"] > 0 and st["steps"] > 2
+        out.append([_shares(r) for r in reqs])
+    for ra, rb in zip(*out):
+        for la, lb in zip(ra, rb):
+            for oa, ob in zip(la, lb):
+                for a, b in zip(oa, ob):
+                    assert np.array_equal(a, b)
