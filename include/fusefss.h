@@ -360,8 +360,12 @@ typedef struct {
  * not run concurrently with another host thread's call on the same spec. */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 
-/* The work split (slots per element) the fused gate of `spec` uses for a call
- * of n elements: forced, tuned, or the cost model's.  Errors: FFSS_ERR_INVALID. */
+/* The work split (slots per element) a plain launch of the fused gate of
+ * `spec` uses for a call of n elements: forced; else 32 for a call that fits
+ * one wave of tiles at 32 threads per element (n <= SMs x 8, a latency-bound
+ * launch, which also takes tiles of 1 to 8 elements and 32 to 256 threads
+ * per party so that its elements spread over as many SMs as possible); else
+ * the tuned model's or the cost model's.  Errors: FFSS_ERR_INVALID. */
 int ffss_gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, uint32_t *slots);
 
 /* ---- online: batched form ----------------------------------------------- */

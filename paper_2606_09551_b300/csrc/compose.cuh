@@ -14,13 +14,13 @@ namespace ffss {
 // (a, b, a_0, b_0, c_0) from the run seed's AES-128-CTR, draw indices 0..4,
 // counter (draw, e low, e high, call id).  Party 0 keeps (a_0, b_0, c_0),
 // party 1 (a - a_0, b - b_0, a b - c_0); layout u64 [3][n] per party.
-__global__ void __launch_bounds__(512, 1) beaver_keygen_kernel(const uint32_t *t0, const RkParam rk,
+__global__ void __launch_bounds__(512, 1) beaver_keygen_kernel(const uint32_t *tabs, const RkParam rk,
                                                                 uint32_t call_id, uint64_t n, uint64_t *k0,
                                                                 uint64_t *k1) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   uint32_t *rk_s = reinterpret_cast<uint32_t *>(smem + kTabBytes);
-  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  stage_tables(tab, tabs);
   if (threadIdx.x < 44) rk_s[threadIdx.x] = rk.w[threadIdx.x];
   __syncthreads();
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};
@@ -177,7 +177,7 @@ static int beaver_keygen_raw(const ffss_ctx *ctx, const uint8_t seed[16], uint32
   if (rc) return rc;
   RkParam rk;
   key_schedule(seed, rk.w);
-  beaver_keygen_kernel<<<grid_for(ctx, n, 512), 512, smem, st>>>(ctx->t0_dev, rk, call_id, n, t0, t1);
+  beaver_keygen_kernel<<<grid_for(ctx, n, 512), 512, smem, st>>>(ctx->tabs_dev, rk, call_id, n, t0, t1);
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
 }

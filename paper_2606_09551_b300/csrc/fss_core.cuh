@@ -68,6 +68,25 @@ __device__ __forceinline__ uint32_t tab_word(const uint32_t *t0, uint32_t idx) {
   return table == 0 ? v : __funnelshift_l(v, v, 8 * table);
 }
 
+// Stage the interleaved tables (all kTabBytes) into shared memory from their
+// copy in global memory (same layout; the context expands it once): each
+// thread queues 16-byte asynchronous copies and waits for its own, so the
+// staging is bound by the L2-to-SM bandwidth rather than by the load latency
+// of a CTA's few threads.  The caller's barrier makes them visible to all.
+__device__ __forceinline__ void stage_tables(uint32_t *tab, const uint32_t *tabs) {
+  const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(tab));
+  for (uint32_t i = threadIdx.x; i < kTabBytes / 16; i += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + 16 * i), "l"(tabs + 4 * i) : "memory");
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+}
+
+// Expansion of T0 into the interleaved layout, word by word (run once per
+// context into the global copy).
+__global__ void expand_tables_kernel(const uint32_t *t0, uint32_t *tabs) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < kTabBytes / 4; idx += gridDim.x * blockDim.x)
+    tabs[idx] = tab_word(t0, idx);
+}
+
 // Lookup of table T (interleaved layout) at byte j of w: the permute puts
 // byte j of w in bits 8..15 over the lane offset lb (128h + 4l < 256).
 template <int T>

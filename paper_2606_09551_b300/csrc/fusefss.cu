@@ -144,7 +144,8 @@ struct StageSlot {
 struct ffss_ctx {
   int device;
   int sm_count;
-  uint32_t *t0_dev;
+  uint32_t *t0_dev;       // AES T-table 0 (256 words)
+  uint32_t *tabs_dev;     // the T-tables expanded into the kernels' shared-memory layout (kTabBytes)
   uint32_t force_slots;   // 0: the cost model picks; else slots per element (1..32, power of two)
   KeyPool pool;
   std::mutex stage_mu;
@@ -214,6 +215,12 @@ extern "C" int ffss_ctx_create(int device, ffss_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->t0_dev, sizeof(uint32_t) * 256);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->t0_dev, tables().t0, sizeof(uint32_t) * 256, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tabs_dev, kTabBytes);
+  if (e == cudaSuccess) {
+    expand_tables_kernel<<<64, 512>>>(c->t0_dev, c->tabs_dev);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   uint32_t rk[44];
   key_schedule(kDcfKey, rk);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rk_dcf, rk, sizeof(rk));
@@ -252,6 +259,7 @@ static void ctx_free(ffss_ctx *ctx) {
     if (sl.dev) cudaFree(sl.dev);
   }
   cudaFree(ctx->t0_dev);
+  cudaFree(ctx->tabs_dev);
   delete ctx;
 }
 
@@ -745,7 +753,7 @@ static int keygen_raw(const ffss_ctx *ctx, const ffss_spec *spec, const uint8_t 
   A.n = n; A.e0 = e0; A.call_id = call_id;
   A.n_items = (spec->host.M > 1 ? spec->host.M - 1 : 0) + spec->host.T + 1;
   key_schedule(seed, A.rk.w);
-  A.t0 = ctx->t0_dev;
+  A.tabs = ctx->tabs_dev;
   switch (spec->host.p) {
     case 1: return launch_keygen<1>(ctx, A, st);
     case 2: return launch_keygen<2>(ctx, A, st);
@@ -798,7 +806,7 @@ extern "C" int ffss_eval_pred(ffss_ctx *ctx, const ffss_spec *spec, int party, f
   PartyArgs A;
   memset(&A, 0, sizeof(A));
   A.spec = spec->dev; A.L = make_layout(spec->host, n); A.kb = keys->buf; A.party = uint32_t(party);
-  A.xhat = xhat; A.atoms = atoms; A.bits = bits; A.n = n; A.t0 = ctx->t0_dev;
+  A.xhat = xhat; A.atoms = atoms; A.bits = bits; A.n = n; A.tabs = ctx->tabs_dev;
   const size_t smem = kTabBytes + spec_smem();
   static std::once_flag once;
   std::call_once(once, [&] { rc = set_smem(pred_kernel, smem); });
@@ -833,7 +841,7 @@ extern "C" int ffss_eval_lut(ffss_ctx *ctx, const ffss_spec *spec, int party, ff
   PartyArgs A;
   memset(&A, 0, sizeof(A));
   A.spec = spec->dev; A.L = make_layout(spec->host, n); A.kb = keys->buf; A.party = uint32_t(party);
-  A.xhat = xhat; A.payload = payload; A.n = n; A.t0 = ctx->t0_dev;
+  A.xhat = xhat; A.payload = payload; A.n = n; A.tabs = ctx->tabs_dev;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (spec->host.p) {
     case 1: rc = launch_lut<1>(ctx, A, st); break;
@@ -853,7 +861,7 @@ extern "C" int ffss_eval_lut(ffss_ctx *ctx, const ffss_spec *spec, int party, ff
 
 // Split one element's T + M - 1 DCF walks over `slots` threads: longest
 // walks first, each to the least-loaded slot (cost = AES blocks).
-static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
+static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load, uint32_t tb = 256) {
   Sched sc;
   memset(&sc, 0, sizeof(sc));
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
@@ -879,7 +887,7 @@ static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load) {
   for (uint32_t q = slots; q <= kMaxSlots; ++q) sc.off[q] = uint8_t(pos);
   (void)nitems;
   sc.S = slots;
-  sc.E = 256 / slots;
+  sc.E = tb / slots;
   uint64_t mx = 0;
   for (uint64_t l : load) mx = l > mx ? l : mx;
   if (max_load) *max_load = mx;
@@ -916,9 +924,28 @@ static uint64_t gate_waves(const ffss_ctx *ctx, uint64_t n, uint32_t slots) {
   return (tiles + ctx->sm_count - 1) / ctx->sm_count;
 }
 
-// The split a plain gate call of n elements uses: forced by the context, else
-// the measured model of ffss_autotune (least fixed + waves x tile time; ties
-// to more slots), else the AES-count cost model.
+// A small plain launch: n elements fit one wave of tiles at the finest split
+// (32 threads per element, tiles of 8 at 256 threads per party), n <= SMs x 8.
+// All its tiles then run at once, one per SM, so the launch lasts as long as
+// its slowest tile: the finest split and the fewest elements per tile that
+// still fit one wave minimise that.  *tb receives the threads per party
+// (32, 64, 128 or 256: tiles of 1, 2, 4 or 8 elements).
+static bool small_launch(const ffss_ctx *ctx, uint64_t n, uint32_t *tb) {
+  if (ctx->force_slots) return false;
+  for (uint32_t t = kMaxSlots; t <= 256; t *= 2) {
+    const uint64_t e = t / kMaxSlots;
+    if ((n + e - 1) / e <= uint64_t(ctx->sm_count)) {
+      *tb = t;
+      return true;
+    }
+  }
+  return false;
+}
+
+// The split a gate call of n elements takes when it fills waves of tiles:
+// forced by the context, else the measured model of ffss_autotune (least
+// fixed + waves x tile time; ties to more slots), else the AES-count cost
+// model.  (The batched form uses it for every call.)
 static uint32_t gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n) {
   if (ctx->force_slots) return ctx->force_slots;
   if (spec->tuned) {
@@ -966,7 +993,7 @@ static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st)
   if (int rc = gate_attr<R, D>()) return rc;
   const uint64_t tiles = (A.g.n + A.sched.E - 1) / A.sched.E;
   const int grid = int(tiles < uint64_t(ctx->sm_count) ? tiles : uint64_t(ctx->sm_count));
-  gate_kernel<R, D><<<grid, kGateThreads, smem, st>>>(A);
+  gate_kernel<R, D><<<grid, 2 * A.sched.S * A.sched.E, smem, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
 }
@@ -975,15 +1002,16 @@ static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st)
 // the given work split.
 static int eval_pair_split(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
                            const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
-                           uint32_t *z0, uint32_t *z1, uint64_t *comm, uint32_t slots, cudaStream_t st) {
+                           uint32_t *z0, uint32_t *z1, uint64_t *comm, uint32_t slots, uint32_t tb,
+                           cudaStream_t st) {
   GateArgsS AS;
   memset(&AS, 0, sizeof(AS));
   GateArgs &A = AS.g;
   A.spec = spec->dev; A.L = make_layout(spec->host, n);
   A.k0 = k0; A.k1 = k1; A.x0 = x0; A.x1 = x1; A.y0 = y0; A.y1 = y1; A.z0 = z0; A.z1 = z1;
   A.comm = reinterpret_cast<unsigned long long *>(comm);
-  A.n = n; A.t0 = ctx->t0_dev;
-  AS.sched = make_sched(spec->host, slots, nullptr);
+  A.n = n; A.tabs = ctx->tabs_dev;
+  AS.sched = make_sched(spec->host, slots, nullptr, tb);
   const uint32_t R = spec->host.r, D = spec->host.d;
   if (R == 1 && D == 0) return launch_gate<1, 0>(ctx, AS, st);
   if (R == 1 && D == 1) return launch_gate<1, 1>(ctx, AS, st);
@@ -996,10 +1024,22 @@ static int eval_pair_split(const ffss_ctx *ctx, const ffss_spec *spec, const cha
   return fail(FFSS_ERR_UNSUPPORTED, "n_out=%u degree=%u", R, D);
 }
 
+// The work split and threads per party of a plain launch of n elements.
+static void plain_shape(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, uint32_t *slots, uint32_t *tb) {
+  if (small_launch(ctx, n, tb)) {
+    *slots = kMaxSlots;
+  } else {
+    *slots = gate_slots(ctx, spec, n);
+    *tb = 256;
+  }
+}
+
 static int eval_pair_raw(const ffss_ctx *ctx, const ffss_spec *spec, const char *k0, const char *k1,
                          const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t *y0, uint64_t *y1,
                          uint32_t *z0, uint32_t *z1, uint64_t *comm, cudaStream_t st) {
-  return eval_pair_split(ctx, spec, k0, k1, x0, x1, n, y0, y1, z0, z1, comm, gate_slots(ctx, spec, n), st);
+  uint32_t slots = 0, tb = 0;
+  plain_shape(ctx, spec, n, &slots, &tb);
+  return eval_pair_split(ctx, spec, k0, k1, x0, x1, n, y0, y1, z0, z1, comm, slots, tb, st);
 }
 
 extern "C" int ffss_eval_pair(ffss_ctx *ctx, const ffss_spec *spec, ffss_keys *k0, ffss_keys *k1,
@@ -1130,7 +1170,7 @@ static int time_split(const ffss_ctx *ctx, const ffss_spec *spec, const TuneSamp
   double best = 0;
   for (int i = 0; i <= reps; ++i) {
     CUDA_TRY(cudaEventRecord(ev.a, st));
-    int rc = eval_pair_split(ctx, spec, T.k0, T.k1, T.x0, T.x1, T.n, T.y0, T.y1, T.z0, T.z1, T.comm, slots, st);
+    int rc = eval_pair_split(ctx, spec, T.k0, T.k1, T.x0, T.x1, T.n, T.y0, T.y1, T.z0, T.z1, T.comm, slots, 256, st);
     if (rc) return rc;
     CUDA_TRY(cudaEventRecord(ev.b, st));
     CUDA_TRY(cudaEventSynchronize(ev.b));
@@ -1205,7 +1245,8 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
 
 extern "C" int ffss_gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n, uint32_t *slots) {
   if (!ctx || !spec || !slots) return fail(FFSS_ERR_INVALID, "ffss_gate_slots: NULL argument");
-  *slots = gate_slots(ctx, spec, n);
+  uint32_t tb = 0;
+  plain_shape(ctx, spec, n, slots, &tb);
   return FFSS_OK;
 }
 
@@ -1428,14 +1469,24 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
       const DevSpec &S = it.sp->host;
       const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
       if (count == 1 && it.sp->tuned) {
-        // a call alone in its class: choose its head split and its tail's
-        // split together from the tuner's tile times, minimising
-        // (full waves x head tile time) + (re-split tail waves x tail tile time)
+        // a call alone in its class: choose its head split (the tuned one or
+        // half of it: the tile-time model is measured near there) and its
+        // tail's split together from the tuner's tile times, minimising
+        // (full waves x head tile time) + (re-split tail waves x tail tile
+        // time); kept only when it beats the tuned split's waves by 2 %
         const ffss_tune &tn = it.sp->tune;
+        const uint32_t s0 = it.c.sched.S;
+        double base_t = -1;
+        for (uint32_t a = 0; a < tn.n_tried; ++a)
+          if (tn.slots[a] == s0) {
+            const uint64_t e0 = 256 / s0;
+            base_t = double(((it.c.n + e0 - 1) / e0 + P - 1) / P) * tn.tile_us[a];
+          }
         double best_t = -1;
-        uint32_t best_h = it.c.sched.S, best_t_s = it.c.sched.S;
+        uint32_t best_h = s0, best_t_s = s0;
         for (uint32_t a = 0; a < tn.n_tried; ++a) {
           const uint32_t sh = tn.slots[a];
+          if (sh != s0 && 2 * sh != s0) continue;
           const uint64_t eh = 256 / sh, th = (it.c.n + eh - 1) / eh, rr = th % P;
           for (uint32_t b = 0; b < tn.n_tried; ++b) {
             const uint32_t st = tn.slots[b];
@@ -1449,6 +1500,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
             }
           }
         }
+        if (base_t < 0 || best_t < 0 || best_t > 0.98 * base_t) continue;   // the plain shape stays
         it.c.sched = make_sched(S, best_h, &it.tile_cost);
         it.tiles = (it.c.n + it.c.sched.E - 1) / it.c.sched.E;
         const uint64_t rr = it.tiles % P;
@@ -1537,7 +1589,7 @@ extern "C" int ffss_batch_eval(ffss_batch *bt, const ffss_call *calls, uint32_t 
     for (int c = 0; c < kShapeClasses; ++c) {
       if (!(mask >> c & 1u)) continue;
       cudaStreamWaitEvent(bt->branch[c], bt->fork, 0);
-      cudaError_t e2 = launch_batch_class(c, int(grid[c]), dh, dc, sl.counter, ctx->t0_dev, bt->branch[c]);
+      cudaError_t e2 = launch_batch_class(c, int(grid[c]), dh, dc, sl.counter, ctx->tabs_dev, bt->branch[c]);
       if (e2 != cudaSuccess && le == cudaSuccess) le = e2;
       cudaEventRecord(bt->join[c], bt->branch[c]);
       cudaStreamWaitEvent(bt->own, bt->join[c], 0);
@@ -1697,7 +1749,7 @@ extern "C" int ffss_batch_eval_noalloc(ffss_ctx *ctx, const ffss_call *calls, ui
     const int grid = int(std::min<uint64_t>(tbl.hdr.cls[c].total_tiles, uint64_t(ctx->sm_count)));
     cudaError_t e = launch_batch_class(c, grid, reinterpret_cast<const BatchHdr *>(dtab),
                                        reinterpret_cast<const BatchCall *>(dtab + offsetof(NoAllocTable, c)), counter,
-                                       ctx->t0_dev, st);
+                                       ctx->tabs_dev, st);
     if (e != cudaSuccess) return fail(FFSS_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
   }
   for (uint32_t i = 0; i < n_calls; ++i)

@@ -29,7 +29,7 @@ struct KeygenArgs {
   uint32_t call_id;
   uint32_t n_items;    // work items per element: M-1 lookup keys + T comparison keys + 1
   RkParam rk;          // AES-128 key schedule of the run seed (dealer PRG)
-  const uint32_t *t0;  // global T-table 0
+  const uint32_t *tabs;  // T-tables in global memory, in the shared-memory layout
 };
 
 struct GateArgs {
@@ -42,7 +42,7 @@ struct GateArgs {
   unsigned long long *comm;   // [2] bytes sent by party 0 / 1, may be null
   uint64_t n;
   uint64_t e_first;           // element of tile 0 (a batch may run a call's last tiles with another split)
-  const uint32_t *t0;
+  const uint32_t *tabs;  // T-tables in global memory, in the shared-memory layout
 };
 
 struct PartyArgs {
@@ -54,7 +54,7 @@ struct PartyArgs {
   uint32_t *atoms, *bits;    // pred outputs (may be null)
   uint64_t *payload;         // lut output
   uint64_t n;
-  const uint32_t *t0;
+  const uint32_t *tabs;  // T-tables in global memory, in the shared-memory layout
 };
 
 struct RkDcf {
@@ -115,9 +115,9 @@ struct AesDcfCall4 {
 };
 
 // Stage the four rotated T-tables, 32 lane copies each, and the spec.
-__device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, const uint32_t *t0,
+__device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, const uint32_t *tabs,
                                              const DevSpec *spec) {
-  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  stage_tables(tab, tabs);
   const uint32_t *src = reinterpret_cast<const uint32_t *>(spec);
   uint32_t *dst = reinterpret_cast<uint32_t *>(sspec);
   for (uint32_t i = threadIdx.x; i < sizeof(DevSpec) / 4; i += blockDim.x) dst[i] = src[i];
@@ -336,7 +336,9 @@ __device__ __forceinline__ void finish_lut(uint32_t b, const uint64_t *vl, uint6
 // ---------------------------------------------------------------------------
 // the fused two-party gate
 //
-// A CTA of 512 threads works on tiles of E = 256 / S elements.  Thread
+// A CTA of 2 x TB threads (TB = 256 threads per party; 32 to 128 in a small
+// plain launch, so that its few elements spread over more SMs) works on
+// tiles of E = TB / S elements.  Thread
 // (party b, slot s, element le) evaluates the DCF walks the host schedule
 // assigns to slot s (the T comparison keys and M-1 lookup keys of an element
 // split into S groups of near-equal AES count), so one element's walks run
@@ -352,7 +354,8 @@ constexpr uint32_t kMaxItems = kMaxT + kMaxM;
 constexpr uint32_t kMaxSlots = 32;   // threads per element: one walk each for 32-walk specs
 
 struct Sched {
-  uint32_t S, E;                 // slots per element, elements per tile (S * E = 256)
+  uint32_t S, E;                 // slots per element, elements per tile (S * E = threads per party:
+                                 // 256, or 32..128 in a small plain launch)
   uint8_t off[kMaxSlots + 1];    // slot s owns items [off[s], off[s+1])
   uint8_t item[kMaxItems];       // < T: comparison key; >= T: lookup key item - T
 };
@@ -477,8 +480,8 @@ __device__ __forceinline__ PostSrc post_src_key(const DevSpec &S, const KeyLayou
   return m;
 }
 
-// One tile of one call: E = 256 / S elements, both parties.  All 512 threads
-// of the CTA enter together (the barriers inside are CTA-wide).
+// One tile of one call: E = TB / S elements, both parties.  All 2 x TB
+// threads of the CTA enter together (the barriers inside are CTA-wide).
 template <int R, int D>
 __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
                                           uint64_t tile, unsigned long long *sent_io) {
@@ -488,8 +491,9 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   const AesDcfInline aes{tb};
   ulonglong2 *box = G.box;
   const uint32_t NS = SC.S, E = SC.E;
-  const uint32_t b = threadIdx.x >> 8;
-  const uint32_t rem = threadIdx.x & 255u;
+  const uint32_t TB = NS * E;                   // threads per party: 256, or 32..128 for a small launch
+  const uint32_t b = threadIdx.x >= TB ? 1u : 0u;
+  const uint32_t rem = threadIdx.x - b * TB;
   const uint32_t slot = rem / E, le = rem - slot * E;
   const bool lead = slot == 0;
   const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
@@ -650,11 +654,13 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   *sent_io += sent;
 }
 
-__device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned long long sent) {
+// Add this thread's sent bytes into comm[party]; tb threads per party (a
+// multiple of 32, so a warp never mixes the parties).
+__device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned long long sent, uint32_t tb = 256) {
   if (!comm) return;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) sent += __shfl_xor_sync(0xffffffffu, sent, off);
-  if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(comm + (threadIdx.x >> 8), sent);
+  if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(comm + (threadIdx.x >= tb ? 1 : 0), sent);
 }
 
 // Plain form: one launch per operator call, tiles dealt round-robin to the CTAs.
@@ -662,12 +668,12 @@ template <int R, int D>
 __global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_constant__ GateArgsS AS) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GateSmem G = carve_gate_smem(smem);
-  stage_shared(reinterpret_cast<uint32_t *>(smem), G.spec, AS.g.t0, AS.g.spec);
+  stage_shared(reinterpret_cast<uint32_t *>(smem), G.spec, AS.g.tabs, AS.g.spec);
   const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
   unsigned long long sent = 0;
   const uint64_t ntiles = (AS.g.n + AS.sched.E - 1) / AS.sched.E;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) gate_tile<R, D>(AS.g, AS.sched, G, tb, tile, &sent);
-  flush_comm(AS.g.comm, sent);
+  flush_comm(AS.g.comm, sent, AS.sched.S * AS.sched.E);
 }
 
 // ---------------------------------------------------------------------------
@@ -722,7 +728,7 @@ __device__ __forceinline__ KeyLayout device_layout(const DevSpec &s, uint64_t n)
 
 template <int R, int D>
 __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *hdr, const BatchCall *all_calls,
-                                                                unsigned long long *counters, const uint32_t *t0) {
+                                                                unsigned long long *counters, const uint32_t *tabs) {
   constexpr int C = shape_class(R, D);
   extern __shared__ __align__(16) unsigned char smem[];
   const GateSmem G = carve_gate_smem(smem);
@@ -733,7 +739,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
   __shared__ unsigned long long next_tile;
   __shared__ unsigned long long s_begin[kBatchMaxCalls];   // first tile of each call of this class
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
-  for (uint32_t idx = threadIdx.x; idx < kTabBytes / 4; idx += blockDim.x) tab[idx] = tab_word(t0, idx);
+  stage_tables(tab, tabs);
   const BatchCall *calls = all_calls + hdr->cls[C].first;
   const uint32_t n_calls = hdr->cls[C].count;
   const unsigned long long total = hdr->cls[C].total_tiles;
@@ -768,7 +774,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
           cur.n = c.n;
           cur.e_first = c.e_first;
           cur.comm = nullptr;
-          cur.t0 = t0;
+          cur.tabs = tabs;
           cur_sched = c.sched;
         }
         next_tile = tile - s_begin[lo];      // tile index within the call
@@ -800,7 +806,7 @@ __global__ void __launch_bounds__(512, 1) pred_kernel(const __grid_constant__ Pa
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
-  stage_shared(tab, sspec, A.t0, A.spec);
+  stage_shared(tab, sspec, A.tabs, A.spec);
   const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
        e += uint64_t(gridDim.x) * blockDim.x) {
@@ -817,7 +823,7 @@ __global__ void __launch_bounds__(512, 1) lut_kernel(const __grid_constant__ Par
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *tab = reinterpret_cast<uint32_t *>(smem);
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
-  stage_shared(tab, sspec, A.t0, A.spec);
+  stage_shared(tab, sspec, A.tabs, A.spec);
   const AesDcfInline aes{Tab{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2}};
   for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < A.n;
        e += uint64_t(gridDim.x) * blockDim.x) {
@@ -910,7 +916,7 @@ __global__ void __launch_bounds__(kKeygenThreads, 1) keygen_kernel(const __grid_
   DevSpec *sspec = reinterpret_cast<DevSpec *>(smem + kTabBytes);
   uint32_t *rk_prg = reinterpret_cast<uint32_t *>(smem + kTabBytes + ((sizeof(DevSpec) + 15) & ~size_t(15)));
   if (threadIdx.x < 44) rk_prg[threadIdx.x] = A.rk.w[threadIdx.x];
-  stage_shared(tab, sspec, A.t0, A.spec);
+  stage_shared(tab, sspec, A.tabs, A.spec);
   const DevSpec &S = *sspec;
   const KeyLayout &L = A.L;
   const Tab tb{reinterpret_cast<const char *>(tab), (threadIdx.x & 31u) << 2};

@@ -28,7 +28,11 @@ def _walks(sp):
 
 
 def _predicted_slots(tune, n, sms):
-    """The plain gate's rule restated: least fixed + waves x tile time, ties to more slots."""
+    """The plain gate's rule restated: a call that fits one wave at 32
+    threads per element (n <= SMs x 8) takes 32; otherwise the least fixed +
+    waves x tile time, ties to more slots."""
+    if n <= sms * 8:
+        return 32
     best, best_us = None, None
     for s, tile, fixed in zip(tune["slots"], tune["tile_us"], tune["fixed_us"]):
         e = 256 // s

@@ -106,6 +106,24 @@ TR_SPECS = [s for s in SPECS if s.trunc_shift]
 
 
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
+def test_gate_more_than_one_wave_bit_exact(ctx, sp):
+    """More tiles than SMs at the finest split: 32 threads per element
+    (tiles of 8 elements) on 1,301 elements gives 163 tiles, so CTAs loop
+    over several tiles and slots own one walk or none; every share still
+    equals the oracle's."""
+    n = 1301
+    x = I.uniform_x(n, sp.k, 6)
+    ctx.set_slots(32)
+    try:
+        g = gpu_gate(ctx, sp, x, call_id=3)
+    finally:
+        ctx.set_slots(0)
+    o = oracle_gate(sp, x, call_id=3)
+    for key in ("y0", "y1", "z0", "z1"):
+        assert np.array_equal(g[key], o[key]), key
+
+
+@pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
 def test_keygen_and_gate_bit_exact(ctx, sp):
     """GPU dealer keys equal the oracle dealer's; every share equals the
     oracle's; reconstruction equals the plaintext spec; bytes sent equal
