@@ -55,7 +55,7 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.258199e9 + 8.687104e6) / 65536}
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.258327e9 + 8.77056e6) / 65536}
 
 
 def parse():
