@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(kMulThreads) beaver_mul_kernel(const uint64_t 
                                                                  const uint64_t *y0, const uint64_t *y1,
                                                                  uint64_t n, uint64_t group, uint64_t *z0,
                                                                  uint64_t *z1, unsigned long long *comm) {
+  dep_wait();
+  dep_release();
   __shared__ ulonglong2 box[2][kMulThreads / 2];
   const uint32_t b = threadIdx.x / (kMulThreads / 2), le = threadIdx.x % (kMulThreads / 2);
   const uint64_t *T = b ? t1 : t0, *X = b ? x1 : x0, *Y = b ? y1 : y0;
@@ -82,11 +84,15 @@ __global__ void __launch_bounds__(kMulThreads) beaver_mul_kernel(const uint64_t 
 
 // Party-local linear steps on additive shares: every output share of party b
 // depends only on party b's input shares (and public constants added by
-// party 0).  Each kernel runs both parties' arrays.
+// party 0).  Each kernel runs both parties' arrays.  These kernels and the
+// product kernel are launched with programmatic stream serialisation inside
+// the plans (dep_wait before any access).
 
 // One comparison-tree round on rows of n values (h = n / 2): d = c[:, :h] - c[:, h:2h].
 __global__ void tree_diff_kernel(const uint64_t *c0, const uint64_t *c1, uint64_t rows, uint64_t n,
                                  uint64_t *d0, uint64_t *d1) {
+  dep_wait();
+  dep_release();
   const uint64_t h = n / 2;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * h; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t r = i / h, j = i - r * h;
@@ -99,6 +105,8 @@ __global__ void tree_diff_kernel(const uint64_t *c0, const uint64_t *c1, uint64_
 // last value is carried.  o has rows x (h + n % 2) values.
 __global__ void tree_merge_kernel(const uint64_t *c0, const uint64_t *c1, const uint64_t *r0,
                                   const uint64_t *r1, uint64_t rows, uint64_t n, uint64_t *o0, uint64_t *o1) {
+  dep_wait();
+  dep_release();
   const uint64_t h = n / 2, w = h + n % 2;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * w; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t r = i / w, j = i - r * w;
@@ -115,6 +123,8 @@ __global__ void tree_merge_kernel(const uint64_t *c0, const uint64_t *c1, const 
 // o = x - m[row] over rows of L values.
 __global__ void row_sub_kernel(const uint64_t *x0, const uint64_t *x1, const uint64_t *m0, const uint64_t *m1,
                                uint64_t rows, uint64_t L, uint64_t *o0, uint64_t *o1) {
+  dep_wait();
+  dep_release();
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < rows * L; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t r = i / L;
     o0[i] = x0[i] - m0[r];
@@ -126,6 +136,8 @@ __global__ void row_sub_kernel(const uint64_t *x0, const uint64_t *x1, const uin
 // (each party scales its own share); one warp per row.
 __global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t rows, uint64_t L, uint64_t scale,
                                uint64_t *s0, uint64_t *s1) {
+  dep_wait();
+  dep_release();
   const uint32_t lane = threadIdx.x & 31u;
   for (uint64_t r = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32; r < rows;
        r += uint64_t(gridDim.x) * blockDim.x / 32) {
@@ -148,6 +160,8 @@ __global__ void row_sum_kernel(const uint64_t *e0, const uint64_t *e1, uint64_t 
 
 // Party 0 adds the public constant c (rounding offset before a shift gate).
 __global__ void add_const_kernel(uint64_t *x0, uint64_t n, uint64_t c) {
+  dep_wait();
+  dep_release();
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
     x0[i] += c;
 }
@@ -156,6 +170,8 @@ __global__ void add_const_kernel(uint64_t *x0, uint64_t n, uint64_t c) {
 // Newton step, 2 - s t or 3 - v r^2).
 __global__ void const_sub_kernel(const uint64_t *x0, const uint64_t *x1, uint64_t n, uint64_t c, uint64_t *o0,
                                  uint64_t *o1) {
+  dep_wait();
+  dep_release();
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
     o0[i] = c - x0[i];
     o1[i] = 0 - x1[i];
@@ -185,10 +201,8 @@ static int beaver_keygen_raw(const ffss_ctx *ctx, const uint8_t seed[16], uint32
 static int beaver_mul_raw(const ffss_ctx *ctx, const uint64_t *t0, const uint64_t *t1, const uint64_t *x0,
                           const uint64_t *x1, const uint64_t *y0, const uint64_t *y1, uint64_t n, uint64_t group,
                           uint64_t *z0, uint64_t *z1, uint64_t *comm, cudaStream_t st) {
-  beaver_mul_kernel<<<grid_for(ctx, n, kMulThreads / 2), kMulThreads, 0, st>>>(
-      t0, t1, x0, x1, y0, y1, n, group, z0, z1, reinterpret_cast<unsigned long long *>(comm));
-  CUDA_TRY(cudaGetLastError());
-  return FFSS_OK;
+  return launch_dep(beaver_mul_kernel, grid_for(ctx, n, kMulThreads / 2), kMulThreads, 0, st, t0, t1, x0, x1, y0,
+                    y1, n, group, z0, z1, reinterpret_cast<unsigned long long *>(comm));
 }
 
 extern "C" int ffss_beaver_keygen(ffss_ctx *ctx, const uint8_t seed[16], uint32_t call_id, uint64_t n,
@@ -451,23 +465,26 @@ static int softmax_issue(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x
   uint64_t *nx0 = cA0, *nx1 = cA1;
   for (uint64_t n : sm->tn) {
     const uint64_t h = n / 2, w = h + n % 2;
-    tree_diff_kernel<<<grid_for(ctx, rows * h, TB), TB, 0, st>>>(c0, c1, rows, n, d0, d1);
+    if (int rc = launch_dep(tree_diff_kernel, grid_for(ctx, rows * h, TB), TB, 0, st, c0, c1, rows, n, d0,
+                            d1)) return rc;
     if (int rc = gate(d0, d1, r0, r1)) return rc;
-    tree_merge_kernel<<<grid_for(ctx, rows * w, TB), TB, 0, st>>>(c0, c1, r0, r1, rows, n, nx0, nx1);
+    if (int rc = launch_dep(tree_merge_kernel, grid_for(ctx, rows * w, TB), TB, 0, st, c0, c1, r0, r1, rows, n, nx0,
+                            nx1)) return rc;
     c0 = nx0; c1 = nx1;
     nx0 = (nx0 == cA0) ? cB0 : cA0;
     nx1 = (nx1 == cA1) ? cB1 : cA1;
   }
   // c now holds one value per row: the row maxima
   // (2) D = X - m; (3) E = shift_e(exp(D) + half)
-  row_sub_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(x0, x1, c0, c1, rows, L, D0, D1);
+  if (int rc = launch_dep(row_sub_kernel, grid_for(ctx, N, TB), TB, 0, st, x0, x1, c0, c1, rows, L, D0, D1)) return rc;
   if (int rc = gate(D0, D1, E0, E1)) return rc;
-  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(E0, N, half(kSmShiftE));
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, N, TB), TB, 0, st, E0, N, half(kSmShiftE))) return rc;
   if (int rc = gate(E0, E1, F0, F1)) return rc;
   // (4) s = row sums; (5) t = shift_t(recip(s) + half)
-  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(F0, F1, rows, L, 1, s0, s1);
+  if (int rc = launch_dep(row_sum_kernel, grid_for(ctx, rows, TB / 32), TB, 0, st, F0, F1, rows, L, 1, s0,
+                          s1)) return rc;
   if (int rc = gate(s0, s1, t0, t1)) return rc;
-  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(t0, rows, half(kSmShiftT));
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, t0, rows, half(kSmShiftT))) return rc;
   if (int rc = gate(t0, t1, u0, u1)) return rc;
   // (5a) Newton steps t' <- t' (2 - s t') (s at 16, t' at 20 bits):
   // A = s t'; B = shift_n1(A + half) (s t' at 20 bits); C = 2^21 - B;
@@ -482,16 +499,17 @@ static int softmax_issue(ffss_softmax *sm, const uint64_t *x0, const uint64_t *x
   };
   for (uint32_t it = 0; it < sm->newton; ++it) {
     if (int rc = mul(s0, s1, u0, u1, rows, 1, nA0, nA1)) return rc;
-    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(0));
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, nA0, rows, nhalf(0))) return rc;
     if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
-    const_sub_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nB0, nB1, rows, uint64_t(1) << 21, nC0, nC1);
+    if (int rc = launch_dep(const_sub_kernel, grid_for(ctx, rows, TB), TB, 0, st, nB0, nB1, rows, uint64_t(1) << 21,
+                            nC0, nC1)) return rc;
     if (int rc = mul(u0, u1, nC0, nC1, rows, 1, nA0, nA1)) return rc;
-    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(1));
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, nA0, rows, nhalf(1))) return rc;
     if (int rc = gate(nA0, nA1, u0, u1)) return rc;
   }
   // (6) P = E' * t' (t' broadcast over the row); (7) Y = shift_p(P + half)
   if (int rc = mul(F0, F1, u0, u1, N, L, P0, P1)) return rc;
-  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kSmShiftP));
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, N, TB), TB, 0, st, P0, N, half(kSmShiftP))) return rc;
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;
@@ -685,20 +703,24 @@ static int layernorm_issue(ffss_layernorm *ln, const uint64_t *x0, const uint64_
                           comm, st);
   };
   // (1) mu = shift_mu(rowsum(X) c_H + half)
-  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(x0, x1, rows, H, ln->c_H, a0, a1);
-  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(a0, rows, half(kLnShiftMu));
+  if (int rc = launch_dep(row_sum_kernel, grid_for(ctx, rows, TB / 32), TB, 0, st, x0, x1, rows, H, ln->c_H, a0,
+                          a1)) return rc;
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, a0, rows, half(kLnShiftMu))) return rc;
   if (int rc = gate(a0, a1, m0, m1)) return rc;
   // (2) D = X - mu; (3) Q = D * D
-  row_sub_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(x0, x1, m0, m1, rows, H, D0, D1);
+  if (int rc = launch_dep(row_sub_kernel, grid_for(ctx, N, TB), TB, 0, st, x0, x1, m0, m1, rows, H, D0, D1)) return rc;
   if (int rc = mul(D0, D1, D0, D1, 1, Q0, Q1)) return rc;
   // (4) var = shift_var(rowsum(Q) c_H + half) + eps
-  row_sum_kernel<<<grid_for(ctx, rows, TB / 32), TB, 0, st>>>(Q0, Q1, rows, H, ln->c_H, v0, v1);
-  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(v0, rows, half(kLnShiftVar));
+  if (int rc = launch_dep(row_sum_kernel, grid_for(ctx, rows, TB / 32), TB, 0, st, Q0, Q1, rows, H, ln->c_H, v0,
+                          v1)) return rc;
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, v0, rows, half(kLnShiftVar))) return rc;
   if (int rc = gate(v0, v1, w0, w1)) return rc;
-  if (ln->eps) add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(w0, rows, ln->eps);
+  if (ln->eps) {
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, w0, rows, ln->eps)) return rc;
+  }
   // (5) r = shift_r(rsqrt(var) + half)
   if (int rc = gate(w0, w1, q0, q1)) return rc;
-  add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(q0, rows, half(kLnShiftR));
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, q0, rows, half(kLnShiftR))) return rc;
   if (int rc = gate(q0, q1, r0, r1)) return rc;
   // (5a) Newton steps r <- r (3 - v r^2) / 2 (v = w at f bits, r at 20):
   // B = shift_n1(r r + half) (r^2 at 20 bits); B = shift_n2(v B + half)
@@ -706,19 +728,20 @@ static int layernorm_issue(ffss_layernorm *ln, const uint64_t *x0, const uint64_
   auto nhalf = [&](int g) { return uint64_t(1) << (ln->gn[g]->host.trunc_s - 1); };
   for (uint32_t it = 0; it < ln->newton; ++it) {
     if (int rc = mul(r0, r1, r0, r1, 1, nA0, nA1)) return rc;
-    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(0));
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, nA0, rows, nhalf(0))) return rc;
     if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
     if (int rc = mul(w0, w1, nB0, nB1, 1, nA0, nA1)) return rc;
-    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(1));
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, nA0, rows, nhalf(1))) return rc;
     if (int rc = gate(nA0, nA1, nB0, nB1)) return rc;
-    const_sub_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nB0, nB1, rows, uint64_t(3) << 20, nC0, nC1);
+    if (int rc = launch_dep(const_sub_kernel, grid_for(ctx, rows, TB), TB, 0, st, nB0, nB1, rows, uint64_t(3) << 20,
+                            nC0, nC1)) return rc;
     if (int rc = mul(r0, r1, nC0, nC1, 1, nA0, nA1)) return rc;
-    add_const_kernel<<<grid_for(ctx, rows, TB), TB, 0, st>>>(nA0, rows, nhalf(2));
+    if (int rc = launch_dep(add_const_kernel, grid_for(ctx, rows, TB), TB, 0, st, nA0, rows, nhalf(2))) return rc;
     if (int rc = gate(nA0, nA1, r0, r1)) return rc;
   }
   // (6) Y = shift_y(D * r + half), r broadcast over the row
   if (int rc = mul(D0, D1, r0, r1, H, P0, P1)) return rc;
-  add_const_kernel<<<grid_for(ctx, N, TB), TB, 0, st>>>(P0, N, half(kLnShiftY));
+  if (int rc = launch_dep(add_const_kernel, grid_for(ctx, N, TB), TB, 0, st, P0, N, half(kLnShiftY))) return rc;
   if (int rc = gate(P0, P1, y0, y1)) return rc;
   CUDA_TRY(cudaGetLastError());
   return FFSS_OK;

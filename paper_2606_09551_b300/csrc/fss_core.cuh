@@ -68,6 +68,16 @@ __device__ __forceinline__ uint32_t tab_word(const uint32_t *t0, uint32_t idx) {
   return table == 0 ? v : __funnelshift_l(v, v, 8 * table);
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialisation may be scheduled while the kernel before
+// it in the stream still runs; it touches no data of earlier work before
+// dep_wait(), which returns once every prerequisite grid has completed and
+// its writes are visible.  dep_release() then lets the next kernel of the
+// stream be scheduled (its CTAs stage their tables while this one runs).
+// Both do nothing in a kernel launched without the attribute.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Stage the interleaved tables (all kTabBytes) into shared memory from their
 // copy in global memory (same layout; the context expands it once): each
 // thread queues 16-byte asynchronous copies and waits for its own, so the

@@ -720,6 +720,30 @@ static int grid_for(const ffss_ctx *ctx, uint64_t work_items, uint32_t per_block
 
 static size_t spec_smem() { return (sizeof(DevSpec) + 15) & ~size_t(15); }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the kernel before it in the stream still runs, and waits for it with
+// dep_wait() before it touches any data (the kernels launched this way: the
+// plain gate, the Beaver product and the plans' linear steps).  Inside a
+// captured plan this becomes a programmatic graph edge, so a chain of small
+// dependent kernels overlaps each launch and table staging with the kernel
+// before it.
+template <class... K, class... A>
+static int launch_dep(void (*kern)(K...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t st,
+                      A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...));
+  return FFSS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // dealer
 // ---------------------------------------------------------------------------
@@ -894,6 +918,14 @@ static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load, ui
   return sc;
 }
 
+// Tiles of `slots`-way split elements that a plain launch of n elements runs
+// per SM: the whole waves, plus one for a partial last wave (its tiles, spread
+// over every SM and partly filled, still take 0.7 to 0.9 of a full tile).
+static double gate_waves(const ffss_ctx *ctx, uint64_t n, uint32_t slots) {
+  const uint64_t E = 256 / slots, tiles = (n + E - 1) / E;
+  return double((tiles + ctx->sm_count - 1) / ctx->sm_count);
+}
+
 // Choose the slot count: minimise waves x (AES count of the slowest slot),
 // the time model of a launch whose CTAs each keep one SM busy; ties go to
 // more slots (shorter per-element latency).
@@ -906,9 +938,7 @@ static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
     if (slots > 1 && slots > nitems) break;
     uint64_t mx = 0;
     Sched sc = make_sched(S, slots, &mx);
-    const uint64_t tiles = (n + sc.E - 1) / sc.E;
-    const uint64_t waves = (tiles + ctx->sm_count - 1) / ctx->sm_count;
-    const double cost = double(waves) * double(mx ? mx : 1);
+    const double cost = gate_waves(ctx, n, slots) * double(mx ? mx : 1);
     if (!have || cost <= best_cost) {
       best = sc;
       best_cost = cost;
@@ -916,12 +946,6 @@ static Sched choose_sched(const ffss_ctx *ctx, const DevSpec &S, uint64_t n) {
     }
   }
   return best;
-}
-
-// Tiles of `slots`-way split elements that a launch of n elements runs per SM.
-static uint64_t gate_waves(const ffss_ctx *ctx, uint64_t n, uint32_t slots) {
-  const uint64_t tiles = (n + 256 / slots - 1) / (256 / slots);
-  return (tiles + ctx->sm_count - 1) / ctx->sm_count;
 }
 
 // A small plain launch: n elements fit one wave of tiles at the finest split
@@ -953,7 +977,7 @@ static uint32_t gate_slots(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t 
     uint32_t best = t.slots[0];
     double best_us = 0;
     for (uint32_t i = 0; i < t.n_tried; ++i) {
-      const double us = t.fixed_us[i] + double(gate_waves(ctx, n, t.slots[i])) * t.tile_us[i];
+      const double us = t.fixed_us[i] + gate_waves(ctx, n, t.slots[i]) * t.tile_us[i];
       if (i == 0 || us <= best_us) {
         best = t.slots[i];
         best_us = us;
@@ -993,9 +1017,7 @@ static int launch_gate(const ffss_ctx *ctx, const GateArgsS &A, cudaStream_t st)
   if (int rc = gate_attr<R, D>()) return rc;
   const uint64_t tiles = (A.g.n + A.sched.E - 1) / A.sched.E;
   const int grid = int(tiles < uint64_t(ctx->sm_count) ? tiles : uint64_t(ctx->sm_count));
-  gate_kernel<R, D><<<grid, 2 * A.sched.S * A.sched.E, smem, st>>>(A);
-  CUDA_TRY(cudaGetLastError());
-  return FFSS_OK;
+  return launch_dep(gate_kernel<R, D>, grid, 2 * A.sched.S * A.sched.E, smem, st, A);
 }
 
 // Fused two-party gate launch on raw key buffers (no handle checks), with

@@ -480,11 +480,12 @@ __device__ __forceinline__ PostSrc post_src_key(const DevSpec &S, const KeyLayou
   return m;
 }
 
-// One tile of one call: E = TB / S elements, both parties.  All 2 x TB
-// threads of the CTA enter together (the barriers inside are CTA-wide).
+// One tile of one call: elements [e_base, e_base + E) below e_end, E = TB / S,
+// both parties.  All 2 x TB threads of the CTA enter together (the barriers
+// inside are CTA-wide).
 template <int R, int D>
 __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, const GateSmem &G, const Tab tb,
-                                          uint64_t tile, unsigned long long *sent_io) {
+                                          uint64_t e_base, uint64_t e_end, unsigned long long *sent_io) {
   constexpr int P = R * (D + 1);
   const DevSpec &S = *G.spec;
   const KeyLayout &L = A.L;
@@ -498,8 +499,8 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   const bool lead = slot == 0;
   const uint32_t it0 = SC.off[slot], it1 = SC.off[slot + 1];
   const char *kb = b ? A.k1 : A.k0;
-  const uint64_t e = A.e_first + tile * E + le;
-  const bool valid = e < A.n;
+  const uint64_t e = e_base + le;
+  const bool valid = e < e_end;
   unsigned long long sent = 0;
   // (1) shares -> masked opening (App. C): send x_b + r_b, add the peer's.
   // The outbox word .y keeps the sender's own r_b until the DCF walks end.
@@ -663,16 +664,39 @@ __device__ __forceinline__ void flush_comm(unsigned long long *comm, unsigned lo
   if ((threadIdx.x & 31u) == 0 && sent) atomicAdd(comm + (threadIdx.x >= tb ? 1 : 0), sent);
 }
 
-// Plain form: one launch per operator call, tiles dealt round-robin to the CTAs.
+// Elements per CTA of the last, partial wave of a plain launch: its m
+// elements spread evenly over the grid, in whole warps of elements (whole
+// tiles when a tile holds fewer than 32).
+__host__ __device__ __forceinline__ uint64_t gate_chunk(uint64_t m, uint64_t grid, uint64_t E) {
+  const uint64_t q = E < 32 ? E : 32;
+  return ((m + grid - 1) / grid + q - 1) / q * q;
+}
+
+// Plain form: one launch per operator call.  The whole waves of tiles are
+// dealt round-robin (at any moment the CTAs read neighbouring tiles' keys);
+// the elements of the last, partial wave are then spread evenly over all
+// CTAs (gate_chunk each), so that wave's tiles are partly filled on every SM
+// instead of full on some and absent on others.  A tile's idle warps skip
+// their walks: a tile of a quarter of its warps measured 0.7 of a full
+// tile's time, one of five eighths 0.9.
 template <int R, int D>
 __global__ void __launch_bounds__(kGateThreads, 1) gate_kernel(const __grid_constant__ GateArgsS AS) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GateSmem G = carve_gate_smem(smem);
-  stage_shared(reinterpret_cast<uint32_t *>(smem), G.spec, AS.g.tabs, AS.g.spec);
+  stage_shared(reinterpret_cast<uint32_t *>(smem), G.spec, AS.g.tabs, AS.g.spec);   // constant data only
+  dep_wait();
+  dep_release();
   const Tab tb{reinterpret_cast<const char *>(smem), (threadIdx.x & 31u) << 2};
   unsigned long long sent = 0;
-  const uint64_t ntiles = (AS.g.n + AS.sched.E - 1) / AS.sched.E;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) gate_tile<R, D>(AS.g, AS.sched, G, tb, tile, &sent);
+  const uint64_t E = AS.sched.E, n = AS.g.n, grid = gridDim.x;
+  const uint64_t full = (n / E) / grid * grid;          // tiles in whole waves
+  for (uint64_t tile = blockIdx.x; tile < full; tile += grid)
+    gate_tile<R, D>(AS.g, AS.sched, G, tb, tile * E, n, &sent);
+  const uint64_t t0 = full * E;
+  const uint64_t per = gate_chunk(n - t0, grid, E);
+  const uint64_t e0 = t0 + uint64_t(blockIdx.x) * per;
+  const uint64_t e1 = e0 + per < n ? e0 + per : n;
+  for (uint64_t e = e0; e < e1; e += E) gate_tile<R, D>(AS.g, AS.sched, G, tb, e, e1, &sent);
   flush_comm(AS.g.comm, sent, AS.sched.S * AS.sched.E);
 }
 
@@ -793,7 +817,7 @@ __global__ void __launch_bounds__(kGateThreads, 1) batch_kernel(const BatchHdr *
       if (threadIdx.x == 0) cur.L = device_layout(*G.spec, cur.n);
       __syncthreads();
     }
-    gate_tile<R, D>(cur, cur_sched, G, tb, next_tile, &sent);
+    gate_tile<R, D>(cur, cur_sched, G, tb, cur.e_first + next_tile * cur_sched.E, cur.n, &sent);
   }
   flush_comm(hdr->comm, sent);
 }

@@ -27,6 +27,12 @@ def _walks(sp):
     return o.T + (o.M - 1 if o.M > 1 else 0)
 
 
+def _waves(n, e, sms):
+    """Tiles per SM of a plain launch: its whole waves, plus one for a
+    partial last wave (spread over every SM, partly filled)."""
+    return -(-(-(-n // e)) // sms)
+
+
 def _predicted_slots(tune, n, sms):
     """The plain gate's rule restated: a call that fits one wave at 32
     threads per element (n <= SMs x 8) takes 32; otherwise the least fixed +
@@ -35,9 +41,7 @@ def _predicted_slots(tune, n, sms):
         return 32
     best, best_us = None, None
     for s, tile, fixed in zip(tune["slots"], tune["tile_us"], tune["fixed_us"]):
-        e = 256 // s
-        waves = -(-(-(-n // e)) // sms)
-        us = fixed + waves * tile
+        us = fixed + _waves(n, 256 // s, sms) * tile
         if best is None or us <= best_us:
             best, best_us = s, us
     return best

@@ -123,6 +123,40 @@ def test_gate_more_than_one_wave_bit_exact(ctx, sp):
         assert np.array_equal(g[key], o[key]), key
 
 
+@pytest.mark.parametrize("n", [1, 150, 450])
+@pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
+def test_gate_small_launch_bit_exact(ctx, sp, n):
+    """Small plain launches (at most four elements per SM): one, two or four
+    elements per CTA of 32, 64 or 128 threads per party at 32 slots; every
+    share equals the oracle's."""
+    x = I.uniform_x(n, sp.k, 9)
+    g = gpu_gate(ctx, sp, x, call_id=5)
+    o = oracle_gate(sp, x, call_id=5)
+    for key in ("y0", "y1", "z0", "z1"):
+        assert np.array_equal(g[key], o[key]), key
+
+
+EVEN_CASES = [(TR_SPECS[0], 1, 47397), (TR_SPECS[1], 2, 23579), (SPECS[0], 4, 14000), (SPECS[3], 4, 14000)]
+
+
+@pytest.mark.parametrize("sp,slots,n", EVEN_CASES, ids=[f"{c[0].name}_s{c[1]}_n{c[2]}" for c in EVEN_CASES])
+def test_gate_even_ranges_bit_exact(ctx, sp, slots, n):
+    """A plain launch deals its whole waves of tiles round-robin and spreads
+    the last, partial wave evenly over the CTAs in whole warps of elements:
+    with tiles of 256 / slots elements, e.g. 47,397 elements at one slot run
+    one wave of 148 tiles and then 100 partly filled tiles of 96 elements,
+    the last one ragged (5 elements); every share equals the oracle's."""
+    x = I.uniform_x(n, sp.k, 10)
+    ctx.set_slots(slots)
+    try:
+        g = gpu_gate(ctx, sp, x, call_id=6)
+    finally:
+        ctx.set_slots(0)
+    o = oracle_gate(sp, x, call_id=6)
+    for key in ("y0", "y1", "z0", "z1"):
+        assert np.array_equal(g[key], o[key]), key
+
+
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
 def test_keygen_and_gate_bit_exact(ctx, sp):
     """GPU dealer keys equal the oracle dealer's; every share equals the
