@@ -54,6 +54,8 @@ def lib():
                                     C.c_uint32, u32p, u64p, u64p, u32p, C.c_uint32, u32p, u32p, u32p, u32p,
                                     C.c_uint32, C.c_uint32]
         L.or_spec_build.restype = C.c_int
+        L.or_spec_set_dcf_r.argtypes = [C.c_void_p, C.c_uint32]
+        L.or_spec_set_dcf_r.restype = C.c_int
         L.or_spec_bx_shape.argtypes = [C.c_void_p, u32p]
         L.or_elem_trunc.argtypes = [C.c_void_p, u64p, u32p, u64p]
         L.or_beaver_dealer.argtypes = [u8p, C.c_uint32, C.c_uint64, C.c_uint64, u64p, u64p]
@@ -174,7 +176,7 @@ class Spec:
     """Oracle-side compiled operator specification."""
 
     def __init__(self, k, m, d, r, alpha, coeff, partition_bits=True, preds=(), xhat_basis=False,
-                 piecewise=(), trunc_s=0, trunc_signed=False, bx_nodes=None):
+                 piecewise=(), trunc_s=0, trunc_signed=False, bx_nodes=None, dcf_r=2):
         """piecewise: per output j, m entries, one per interval: the tuple
         (f, c, gamma, negate) of a single predicate when bx_nodes is None,
         else the index in bx_nodes of the root of the formula B_i^(j).
@@ -182,7 +184,9 @@ class Spec:
         bit), ("not", a), ("xor", a, b), ("and", a, b), ("or", a, b); the
         children a, b are indices of earlier nodes.
         trunc_s > 0: output 0 gains the shift of the k-bit view by trunc_s
-        (arithmetic when trunc_signed)."""
+        (arithmetic when trunc_signed).
+        dcf_r: input bits per tree level of the gate's DCF keys (arity
+        2^dcf_r, 1..3)."""
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
         alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64))
         coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.uint64).reshape(-1))
@@ -219,6 +223,9 @@ class Spec:
         self.trunc_s, self.trunc_signed = trunc_s, bool(trunc_signed)
         if rc != 0:
             raise ValueError("oracle rejected the operator specification")
+        if lib().or_spec_set_dcf_r(self.ptr, dcf_r) != 0:
+            raise ValueError(f"DCF arity 2^{dcf_r} outside 2..8")
+        self.dcf_r = dcf_r
         sh = np.zeros(6, np.uint32)
         lib().or_spec_shape(self.ptr, _p(sh, u32p))
         self.k, self.m, self.d, self.r = k, m, d, r

@@ -432,8 +432,9 @@ void or_dcf_eval(int b, const or_dcf_key *key, uint64_t u, int *out_bit, uint64_
 
 size_t or_dcf_key_size(void) { return sizeof(or_dcf_key); }
 
-/* The gate's DCF keys: arity 4 (two input bits per level). */
-#define GATE_R 2
+/* The gate's DCF keys: arity 2^dcf_r, dcf_r input bits per tree level
+ * (a per-spec choice, 1..MAXR; 2 unless set). */
+#define GATE_R_DEFAULT 2
 
 
 /* ------------------------------------------------------------------------ */
@@ -462,7 +463,7 @@ typedef struct {
     uint64_t tr_rho_a[2];             /* daBits: additive shares of rho_lo, rho_hi */
 } or_elem_keys;   /* the header of an element's record; its packed DCF keys follow */
 
-static size_t packed_key_bytes(int k, int p);
+static size_t packed_key_bytes(int k, int p, int r);
 
 typedef struct {
     uint32_t f;        /* view width */
@@ -525,9 +526,13 @@ typedef struct {
     uint64_t trunc_c;                 /* view shift: 2^{k-1} for the signed form, else 0 */
     int32_t trunc_q_lo;               /* query of the r-atom 1[x^ mod 2^s < r mod 2^s] */
     int32_t trunc_q_hi;               /* query of the r-atom 1[view_{k,c}(x^) < r mod 2^k] */
+    /* DCF input bits per tree level (arity 2^dcf_r) of the gate's keys */
+    uint32_t dcf_r;
     /* per-element record layout (bytes): header, query keys, lookup keys */
     uint32_t rec_size, q_off[MAXQ], l_off, l_size;
 } or_spec;
+
+static void spec_layout(or_spec *sp);
 
 /* index of primitive predicate (f, c, gamma) in sp->prim, adding it if new;
  * -1 for the sentinels gamma = 0 and gamma = 2^f */
@@ -726,16 +731,31 @@ int or_spec_build(or_spec *sp, uint32_t k, uint32_t m, uint32_t d, uint32_t r,
         }
     }
     sp->T = T;
-    /* record layout */
+    sp->dcf_r = GATE_R_DEFAULT;
+    spec_layout(sp);
+    return 0;
+}
+
+/* per-element record layout: header, then the query keys, then the lookup keys */
+static void spec_layout(or_spec *sp)
+{
     uint32_t off = (uint32_t)((sizeof(or_elem_keys) + 15) & ~(size_t)15);
-    for (uint32_t t = 0; t < T; t++) {
+    for (uint32_t t = 0; t < sp->T; t++) {
         sp->q_off[t] = off;
-        off += (uint32_t)packed_key_bytes((int)sp->q_f[t], 0);
+        off += (uint32_t)packed_key_bytes((int)sp->q_f[t], 0, (int)sp->dcf_r);
     }
     sp->l_off = off;
-    sp->l_size = (uint32_t)packed_key_bytes((int)k, (int)sp->p);
+    sp->l_size = (uint32_t)packed_key_bytes((int)sp->k, (int)sp->p, (int)sp->dcf_r);
     off += (sp->M > 1 ? sp->M - 1 : 0) * sp->l_size;
     sp->rec_size = (off + 15) & ~15u;
+}
+
+/* Choose the arity 2^r of the spec's DCF keys (1 <= r <= MAXR). */
+int or_spec_set_dcf_r(or_spec *sp, uint32_t r)
+{
+    if (r < 1 || r > MAXR) return -1;
+    sp->dcf_r = r;
+    spec_layout(sp);
     return 0;
 }
 
@@ -888,18 +908,18 @@ static const or_elem_keys *celem_at(const or_elem_keys *base, const or_spec *sp,
     return (const or_elem_keys *)((const uint8_t *)base + i * sp->rec_size);
 }
 
-/* Packed gate key (arity 2^GATE_R): root[16], cw[nlev][A][16], then for a
+/* Packed gate key (arity A = 2^r): root[16], cw[nlev][A][16], then for a
  * vector payload vcw[nlev][A][p] uint64 and the leaf CW p uint64, for a bit
  * payload the leaf CW bit in one uint64. */
-static size_t packed_key_bytes(int k, int p)
+static size_t packed_key_bytes(int k, int p, int r)
 {
-    size_t nlev = (size_t)dcf_levels(k, GATE_R), A = (size_t)1 << GATE_R;
+    size_t nlev = (size_t)dcf_levels(k, r), A = (size_t)1 << r;
     return 16 + nlev * A * 16 + (p ? nlev * A * (size_t)p * 8 + 8 * (size_t)p : 8);
 }
 
 static void pack_key(const or_dcf_key *K, uint8_t *dst)
 {
-    int A = 1 << GATE_R;
+    int A = 1 << K->r;
     memcpy(dst, K->root, 16);
     dst += 16;
     for (int i = 0; i < K->nlev; i++)
@@ -912,10 +932,10 @@ static void pack_key(const or_dcf_key *K, uint8_t *dst)
     for (int q = 0; q < K->p; q++) *w++ = K->leaf[q];
 }
 
-static void unpack_key(const uint8_t *src, int k, int p, or_dcf_key *K)
+static void unpack_key(const uint8_t *src, int k, int p, int r, or_dcf_key *K)
 {
-    int A = 1 << GATE_R;
-    K->k = k; K->p = p; K->r = GATE_R; K->nlev = dcf_levels(k, GATE_R);
+    int A = 1 << r;
+    K->k = k; K->p = p; K->r = r; K->nlev = dcf_levels(k, r);
     K->leaf_bit = 0;
     memcpy(K->root, src, 16);
     src += 16;
@@ -1031,7 +1051,7 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
     uint32_t base_roots = DRAW_VLAST + p;
     uint32_t base_triples = base_roots + 2 * (T + M - 1);
     or_dcf_key *G = (or_dcf_key *)malloc(2 * sizeof(or_dcf_key));   /* working keys of both parties */
-    uint8_t rnd[32 * 3 * 16];                                           /* path-child randomness */
+    uint8_t rnd[MAXLV * 3 * 16];                                        /* path-child randomness */
     if (!G) return;
 
     for (uint64_t i = 0; i < n; i++) {
@@ -1072,8 +1092,8 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             uint8_t s0[16], s1[16];
             prg_block(&g, base_roots + 2 * t, e, s0);
             prg_block(&g, base_roots + 2 * t + 1, e, s1);
-            keep_rand(&g, t, dcf_levels((int)sp->q_f[t], GATE_R), 0, e, rnd);
-            or_dcf_gen((int)sp->q_f[t], GATE_R, a, 0, NULL, s0, s1, rnd, &G[0], &G[1]);
+            keep_rand(&g, t, dcf_levels((int)sp->q_f[t], (int)sp->dcf_r), 0, e, rnd);
+            or_dcf_gen((int)sp->q_f[t], (int)sp->dcf_r, a, 0, NULL, s0, s1, rnd, &G[0], &G[1]);
             pack_key(&G[0], (uint8_t *)K0 + sp->q_off[t]);
             pack_key(&G[1], (uint8_t *)K1 + sp->q_off[t]);
         }
@@ -1093,8 +1113,8 @@ void or_dealer(const or_spec *sp, const uint8_t seed[16], uint32_t call_id,
             uint32_t di = base_roots + 2 * (T + j - 1);
             prg_block(&g, di, e, s0);
             prg_block(&g, di + 1, e, s1);
-            keep_rand(&g, T + j - 1, dcf_levels((int)sp->k, GATE_R), (int)p, e, rnd);
-            or_dcf_gen((int)sp->k, GATE_R, B[j], (int)p, beta, s0, s1, rnd, &G[0], &G[1]);
+            keep_rand(&g, T + j - 1, dcf_levels((int)sp->k, (int)sp->dcf_r), (int)p, e, rnd);
+            or_dcf_gen((int)sp->k, (int)sp->dcf_r, B[j], (int)p, beta, s0, s1, rnd, &G[0], &G[1]);
             pack_key(&G[0], (uint8_t *)K0 + sp->l_off + (size_t)(j - 1) * sp->l_size);
             pack_key(&G[1], (uint8_t *)K1 + sp->l_off + (size_t)(j - 1) * sp->l_size);
         }
@@ -1171,7 +1191,7 @@ static uint32_t party_pred_atoms(int b, const or_spec *sp, const or_elem_keys *K
         uint64_t u = view(xhat, sp->q_f[t], sp->q_c[t]);
         int bit;
         or_dcf_key key;
-        unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, &key);
+        unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, (int)sp->dcf_r, &key);
         or_dcf_eval(b, &key, u, &bit, NULL);
         atoms |= (uint32_t)bit << t;
     }
@@ -1262,7 +1282,8 @@ static void party_lookup(int b, const or_spec *sp, const or_elem_keys *K, uint64
     for (uint32_t j = 1; j < sp->M; j++) {
         uint64_t sh[MAXP];
         or_dcf_key key;
-        unpack_key((const uint8_t *)K + sp->l_off + (size_t)(j - 1) * sp->l_size, (int)sp->k, (int)sp->p, &key);
+        unpack_key((const uint8_t *)K + sp->l_off + (size_t)(j - 1) * sp->l_size, (int)sp->k, (int)sp->p,
+                   (int)sp->dcf_r, &key);
         or_dcf_eval(b, &key, u, NULL, sh);
         for (uint32_t q = 0; q < sp->p; q++) pay[q] += sh[q];
     }
@@ -1438,12 +1459,13 @@ void or_reconstruct(const uint64_t *y0, const uint64_t *y1, const uint32_t *z0, 
 
 void or_elem_qkey(const or_spec *sp, const or_elem_keys *K, uint32_t t, or_dcf_key *out)
 {
-    unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, out);
+    unpack_key((const uint8_t *)K + sp->q_off[t], (int)sp->q_f[t], 0, (int)sp->dcf_r, out);
 }
 
 void or_elem_lkey(const or_spec *sp, const or_elem_keys *K, uint32_t j, or_dcf_key *out)
 {
-    unpack_key((const uint8_t *)K + sp->l_off + (size_t)j * sp->l_size, (int)sp->k, (int)sp->p, out);
+    unpack_key((const uint8_t *)K + sp->l_off + (size_t)j * sp->l_size, (int)sp->k, (int)sp->p, (int)sp->dcf_r,
+               out);
 }
 
 /* key material as arrays: root[16], cw[nlev][A][16], vcw[nlev][A][p],

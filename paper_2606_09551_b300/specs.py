@@ -80,6 +80,10 @@ class OperatorSpec:
     # shift of its k-bit two's-complement value when trunc_signed (0 = none)
     trunc_shift: int = 0
     trunc_signed: bool = False
+    # DCF input bits per tree level of the gate's keys (arity 2^dcf_bits, 1..3):
+    # a protocol parameter, not part of the function; fewer levels mean fewer
+    # online AES blocks but larger keys and more dealer work
+    dcf_bits: int = 2
     real_fn: Callable[[np.ndarray], np.ndarray] | None = None
     domain: Tuple[float, float] | None = None
 
@@ -101,13 +105,22 @@ class OperatorSpec:
         return dict(k=self.k, m=self.m, d=self.degree, r=self.n_out, alpha=list(self.alpha), coeff=self.coeff,
                     partition_bits=self.partition_bits, preds=self.pred_tuples(), xhat_basis=self.xhat_basis,
                     piecewise=self.piecewise_tuples(), trunc_s=self.trunc_shift, trunc_signed=self.trunc_signed,
-                    bx_nodes=[nd.astuple() for nd in self.bx_nodes] or None)
+                    bx_nodes=[nd.astuple() for nd in self.bx_nodes] or None, dcf_r=self.dcf_bits)
 
     def variant(self, xhat_basis: bool) -> "OperatorSpec":
         """The same specification evaluated in the other protocol variant."""
         import dataclasses
         return dataclasses.replace(self, xhat_basis=xhat_basis,
                                    name=self.name + ("_xhat" if xhat_basis else ""))
+
+    def arity(self, dcf_bits: int) -> "OperatorSpec":
+        """The same specification with DCF keys of arity 2^dcf_bits."""
+        import dataclasses
+        if dcf_bits == self.dcf_bits:
+            return self
+        base = self.name[:-3] if self.name[-3:-1] == "_a" else self.name
+        return dataclasses.replace(self, dcf_bits=dcf_bits,
+                                   name=base + ("" if dcf_bits == 2 else f"_a{1 << dcf_bits}"))
 
 
 # --------------------------------------------------------------------------

@@ -3,11 +3,12 @@ oracle's per-element key records.  The layout is the library's own choice
 (element-minor sections, each 256-byte aligned); the oracle compares shares
 and, through this transform, key material.
 
-DCF keys have arity 4 (two input bits per tree level).  Per comparison key
-of view width f (L = ceil(f/2) levels): root uint4[n], child correction
-words uint4[L][4][n] (seed CW with the t CW in bit 0 and the value CW in bit
-1), the leaf CW u64[n].  Per lookup key (k bits, payload p): root, child
-CWs uint4[L][4][n], value CWs u64[L][4][p][n], leaf CWs u64[p][n]."""
+DCF keys have arity A = 2^r (r input bits per tree level, the spec's
+dcf_r).  Per comparison key of view width f (L = ceil(f/r) levels): root
+uint4[n], child correction words uint4[L][A][n] (seed CW with the t CW in bit
+0 and the value CW in bit 1), the leaf CW u64[n].  Per lookup key (k bits,
+payload p): root, child CWs uint4[L][A][n], value CWs u64[L][A][p][n], leaf
+CWs u64[p][n]."""
 from __future__ import annotations
 
 import numpy as np
@@ -19,8 +20,8 @@ def _a256(v):
     return (v + 255) & ~255
 
 
-def _lv(f):
-    return (f + 1) // 2
+def _lv(f, r):
+    return (f + r - 1) // r
 
 
 def offsets(ospec: O.Spec, n: int):
@@ -35,15 +36,17 @@ def offsets(ospec: O.Spec, n: int):
     tr = 1 if ospec.trunc_s else 0
     off["trunc"] = o; o = _a256(o + 24 * tr * n)
     off["trunc_rho"] = o; o = _a256(o + 4 * tr * n)
+    r = ospec.dcf_r
+    A = 1 << r
     off["q"] = []
     for (f, c, pr) in ospec.queries():
         off["q"].append(o)
-        o = _a256(o + (16 + 64 * _lv(f) + 8) * n)
+        o = _a256(o + (16 + 16 * A * _lv(f, r) + 8) * n)
     off["l"] = []
     for j in range(ospec.M - 1):
         off["l"].append(o)
-        lv = _lv(ospec.k)
-        o = _a256(o + (16 + 64 * lv + 32 * lv * ospec.p + 8 * ospec.p) * n)
+        lv = _lv(ospec.k, r)
+        o = _a256(o + (16 + 16 * A * lv + 8 * A * lv * ospec.p + 8 * ospec.p) * n)
     off["total"] = max(o, 256)
     return off
 
@@ -60,18 +63,18 @@ def _blocks(buf, off, count):
     return buf[off: off + 16 * count].reshape(count, 16)
 
 
-def _gpu_key(buf, base, n, e, k, p):
-    lv = _lv(k)
-    blk = _blocks(buf, base, (1 + 4 * lv) * n)
+def _gpu_key(buf, base, n, e, k, p, r):
+    lv, A = _lv(k, r), 1 << r
+    blk = _blocks(buf, base, (1 + A * lv) * n)
     root = blk[e].copy()
-    cw = np.stack([blk[(1 + row) * n + e] for row in range(4 * lv)]).reshape(lv, 4, 16)
-    tail = base + 16 * (1 + 4 * lv) * n
+    cw = np.stack([blk[(1 + row) * n + e] for row in range(A * lv)]).reshape(lv, A, 16)
+    tail = base + 16 * (1 + A * lv) * n
     if p == 0:
         return dict(root=root, cw=cw, leaf_bit=int(_u64(buf, tail, n)[e]) & 1)
-    v = _u64(buf, tail, 4 * lv * p * n)
-    vcw = np.array([[[v[((i * 4 + c) * p + q) * n + e] for q in range(p)] for c in range(4)] for i in range(lv)],
+    v = _u64(buf, tail, A * lv * p * n)
+    vcw = np.array([[[v[((i * A + c) * p + q) * n + e] for q in range(p)] for c in range(A)] for i in range(lv)],
                    np.uint64)
-    lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
+    lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
     leaf = np.array([lf[q * n + e] for q in range(p)], np.uint64)
     return dict(root=root, cw=cw, vcw=vcw, leaf=leaf)
 
@@ -96,8 +99,9 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
         tt = _u64(buf, off["trunc"], 3 * n)
         out.update(tr_t=int(tt[e]), tr_rho=int(_u32(buf, off["trunc_rho"], n)[e]),
                    tr_rho_a=np.array([tt[n + e], tt[2 * n + e]], np.uint64))
-    out["q"] = [_gpu_key(buf, off["q"][t], n, e, f, 0) for t, (f, c, pr) in enumerate(ospec.queries())]
-    out["l"] = [_gpu_key(buf, off["l"][j], n, e, k, p) for j in range(ospec.M - 1)]
+    r = ospec.dcf_r
+    out["q"] = [_gpu_key(buf, off["q"][t], n, e, f, 0, r) for t, (f, c, pr) in enumerate(ospec.queries())]
+    out["l"] = [_gpu_key(buf, off["l"][j], n, e, k, p, r) for j in range(ospec.M - 1)]
     return out
 
 
@@ -112,7 +116,7 @@ def oracle_fields(keys: O.ElemKeys, ospec: O.Spec, i: int):
     qk = []
     for t in range(ospec.T):
         fl = keys.qkey(i, t).fields()
-        assert fl["r"] == 2
+        assert fl["r"] == ospec.dcf_r
         qk.append(dict(root=fl["root"], cw=fl["cw"], leaf_bit=fl["leaf_bit"]))
     out["q"] = qk
     lk = []
@@ -174,26 +178,27 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             tt = _u64(buf, off["trunc"], 3 * n)
             tt[e], tt[n + e], tt[2 * n + e] = fl["tr_t"], fl["tr_rho_a"][0], fl["tr_rho_a"][1]
             _u32(buf, off["trunc_rho"], n)[e] = fl["tr_rho"]
+        r_, A = ospec.dcf_r, 1 << ospec.dcf_r
         for t, (f, c, pr) in enumerate(qs):
-            lv = _lv(f)
-            blk = _blocks(buf, off["q"][t], (1 + 4 * lv) * n)
+            lv = _lv(f, r_)
+            blk = _blocks(buf, off["q"][t], (1 + A * lv) * n)
             blk[e] = fl["q"][t]["root"]
-            for row in range(4 * lv):
-                blk[(1 + row) * n + e] = fl["q"][t]["cw"][row // 4, row % 4]
-            _u64(buf, off["q"][t] + 16 * (1 + 4 * lv) * n, n)[e] = fl["q"][t]["leaf_bit"]
+            for row in range(A * lv):
+                blk[(1 + row) * n + e] = fl["q"][t]["cw"][row // A, row % A]
+            _u64(buf, off["q"][t] + 16 * (1 + A * lv) * n, n)[e] = fl["q"][t]["leaf_bit"]
         for j in range(ospec.M - 1):
-            lv = _lv(k)
-            blk = _blocks(buf, off["l"][j], (1 + 4 * lv) * n)
+            lv = _lv(k, r_)
+            blk = _blocks(buf, off["l"][j], (1 + A * lv) * n)
             blk[e] = fl["l"][j]["root"]
-            for row in range(4 * lv):
-                blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // 4, row % 4]
-            tail = off["l"][j] + 16 * (1 + 4 * lv) * n
-            v = _u64(buf, tail, 4 * lv * p * n)
+            for row in range(A * lv):
+                blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // A, row % A]
+            tail = off["l"][j] + 16 * (1 + A * lv) * n
+            v = _u64(buf, tail, A * lv * p * n)
             for i in range(lv):
-                for c in range(4):
+                for c in range(A):
                     for q in range(p):
-                        v[((i * 4 + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
-            lf = _u64(buf, tail + 8 * 4 * lv * p * n, p * n)
+                        v[((i * A + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
+            lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
             for q in range(p):
                 lf[q * n + e] = fl["l"][j]["leaf"][q]
     return buf

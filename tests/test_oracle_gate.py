@@ -90,15 +90,19 @@ def test_plain_evaluator_matches_independent_python():
         assert (y == yp).all() and (z == zp).all()
 
 
+@pytest.mark.parametrize("dcf_bits", [1, 2, 3])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_gate_every_mask_every_input(k):
-    """Reconstruction equals F(x) for all x and all masks r (Lemma 'compiler correctness')."""
+def test_gate_every_mask_every_input(k, dcf_bits):
+    """Reconstruction equals F(x) for all x and all masks r (Lemma 'compiler
+    correctness'), with DCF keys of arity 2, 4 and 8 (for arity 8 and k = 4,
+    5 the first tree level takes one or two input bits)."""
     rng = np.random.default_rng(40 + k)
     N = 2 ** k
     for trial in range(6):
         m = int(rng.integers(1, min(N, 16) + 1))
         d = int(rng.integers(0, 4))
-        sp = S.random_spec(rng, k, m, d, 1, partition_bits=bool(trial % 2), n_extra=int(rng.integers(0, 3)))
+        sp = S.random_spec(rng, k, m, d, 1, partition_bits=bool(trial % 2),
+                           n_extra=int(rng.integers(0, 3))).arity(dcf_bits)
         hi_x = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
         hi_r = rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k)
         xs = np.tile(np.arange(N, dtype=np.uint64), N) + hi_x
@@ -360,8 +364,9 @@ def test_piecewise_relu_sign_select():
     assert np.array_equal(z & 1, (xs < 0).astype(np.uint32))
 
 
+@pytest.mark.parametrize("dcf_bits", [2, 3])
 @pytest.mark.parametrize("k", [2, 3, 5, 7])
-def test_truncation_every_shift_every_mask_every_input(k):
+def test_truncation_every_shift_every_mask_every_input(k, dcf_bits):
     """Shift gate (Def. "specification-compatible scalar gate" with the
     low-bit rewrite of App. "low-bit predicate rewrite"): for every shift s,
     both the logical and the arithmetic form, all x and all masks r, the
@@ -375,7 +380,7 @@ def test_truncation_every_shift_every_mask_every_input(k):
     rs = np.repeat(np.arange(N, dtype=np.uint64), N) + hi_r
     for s_ in range(1, k):
         for signed in (False, True):
-            sp = S.trunc(k, s_, signed)
+            sp = S.trunc(k, s_, signed).arity(dcf_bits)
             o, res, y, z = run_gate(sp, xs, r_override=rs)
             yp, _ = python_plain(sp, xs)
             assert (y == yp).all(), (s_, signed)
@@ -420,8 +425,9 @@ def test_truncation_with_polynomial_and_boolean_outputs(k):
         assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * -(-len(sp.piecewise) * sp.m // 32) + 1)).all()
 
 
+@pytest.mark.parametrize("dcf_bits", [2, 3])
 @pytest.mark.parametrize("k,s", [(40, 20), (63, 49), (63, 1), (48, 47)])
-def test_truncation_wide_views(k, s):
+def test_truncation_wide_views(k, s, dcf_bits):
     """Shift gates on views wider than 32 bits (single-interval specs may use
     k up to 63): random 64-bit x against Python's integer shift of the k-bit
     view; at k = 63 the arithmetic form equals numpy's int64 right shift of
@@ -429,7 +435,7 @@ def test_truncation_wide_views(k, s):
     rng = np.random.default_rng(k * 100 + s)
     x = rng.integers(0, 2 ** 64, size=3000, dtype=np.uint64)
     for signed in (False, True):
-        sp = S.trunc(k, s, signed)
+        sp = S.trunc(k, s, signed).arity(dcf_bits)
         _, res, y, _ = run_gate(sp, x)
         yp, _ = python_plain(sp, x)
         assert np.array_equal(y, yp), signed
