@@ -55,6 +55,13 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
 # captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
 # retaken whenever the kernel changes
+# The AES form of every walk, per spec: the measured forms are the T-table
+# addressing variants and the bitsliced code (roofline.aes_microkernel_blocks_per_s);
+# the interleaved T-table form is the fastest on every pipe, and the bitsliced
+# form (32 independent blocks per thread) cannot run a walk, which chains one
+# block per tree level.
+AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates measured in this run",
+            "alternatives": ["t_table_shift_mask", "t_table_permute_mad", "bitsliced_lop3 (not a walk form)"]}
 GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.258327e9 + 8.77056e6) / 65536}
 
 
@@ -86,6 +93,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=0,
                     help="force the gate's work split (slots per element) for every call (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
+    ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="DCF input bits per tree level of every gate; 0: the library measures each "
+                         "spec at arities 2, 4 and 8 and keeps the fastest for its form")
     return ap.parse_args()
 
 
@@ -276,9 +286,10 @@ def cpu_baseline(calls, cpu_seconds):
     rates, sample, threads = oracle_rates(calls, cpu_seconds)
     total = sum(c.n for c in calls)
     t = sum(c.n * rates[c.name] for c in calls)
+    ar = {c.name: 1 << c.spec.dcf_bits for c in calls}
     return {"value": total / t, "unit": "elements/s", "cores": threads, "kind": "oracle",
             "sample": "oracle eval_pair (both parties) on the first " +
-                      ", ".join(f"{sample[k]} {k}" for k in sample) +
+                      ", ".join(f"{sample[k]} {k} (DCF arity {ar[k]})" for k in sample) +
                       " elements; per-op s/element combined with the full layer's op mix"}
 
 
@@ -299,19 +310,20 @@ def run_ours(args, rank, world, local_rank):
     dev = f"cuda:{local_rank}"
     ctx = F.Context(local_rank)
     calls, config = workload(args.workload)
-    css = {c.name: F.CompiledSpec(c.spec, ctx) for c in calls}
-    # measured launch shape per spec, before any timing: the library times the
-    # gate under every work split on throw-away samples and keeps the model
+    # the DCF arity per spec (resident keys: form 0), then the measured launch
+    # shape, before any timing: the library times the gate under every work
+    # split (and, with --dcf-bits 0, every arity) on throw-away samples
+    css = compile_specs(ctx, calls, args, form=0)
     tuning = None
     if not args.no_autotune:
         tuning = {}
         for c in calls:
             cs = css[c.name]
-            model = cs.gate_slots(c.n)
             t0 = time.perf_counter()
             tune = cs.autotune()
-            tuning[c.name] = dict(tune, elements=c.n, slots_cost_model=model, slots_tuned=cs.gate_slots(c.n),
-                                  tune_s=time.perf_counter() - t0)
+            tuning[c.name] = dict(tune, elements=c.n, slots_tuned=cs.gate_slots(c.n), tune_s=time.perf_counter() - t0,
+                                  aes_form=AES_FORM, dcf_bits=cs.spec.dcf_bits,
+                                  dcf_bits_chosen_by=cs.arity_choice)
     if args.slots:
         ctx.set_slots(args.slots)
         config = dict(config, forced_slots=args.slots)
@@ -551,7 +563,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_served:
         served = run_served(ctx, args, dev)
     if not args.no_large:
-        large = run_large_layer(ctx, dev, tune=not args.no_autotune, no_serial=args.no_serial)
+        large = run_large_layer(ctx, dev, args, no_serial=args.no_serial)
     if not args.no_gpt2:
         gpt2 = run_gpt2_batch(ctx, args, dev)
 
@@ -623,7 +635,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic (seeded activations; random masks, keys and triples from the GPU dealer)",
-        "config": full_config(config, calls, world),
+        "config": full_config(config, calls, world, args),
         "timing": {"key_sets_resident": G, "timed_groups": -(-args.steps // G)},
         "per_op_ms": per_op_ms,
         "autotune": tuning,
@@ -661,13 +673,38 @@ def _stream_aes(pending_ops, nlay):
     return deal, online
 
 
-def _compile_requests(ctx, reqs, tune):
-    """One compiled (and, unless told not to, autotuned) spec per operator."""
+def compile_specs(ctx, calls, args, form, n_of=None):
+    """One compiled spec per call.  With --dcf-bits 0 (and tuning on) the
+    library compiles each at DCF arities 2, 4 and 8, tunes each and keeps the
+    one with the least predicted time for the call's size (form 0: resident
+    keys; form 1: keys dealt as they are used, so the dealer's time counts);
+    every call's spec is replaced by the kept one.  Otherwise the given (or
+    forced) arity, tuned unless --no-autotune."""
     from paper_2606_09551_b300 import fusefss as F
-    css = {op.name: F.CompiledSpec(op.spec, ctx) for op in reqs[0].ops}
-    if tune:
-        for cs in css.values():
-            cs.autotune()
+    css = {}
+    for c in calls:
+        n = n_of(c) if n_of else c.n
+        if args.dcf_bits == 0 and not args.no_autotune:
+            cs = F.CompiledSpec(c.spec, ctx, best_for=(n, form))
+            cs.arity_choice = "measured, form %d at %d elements" % (form, n)
+        else:
+            cs = F.CompiledSpec(c.spec.arity(args.dcf_bits) if args.dcf_bits else c.spec, ctx)
+            cs.arity_choice = "forced" if args.dcf_bits else "default"
+            if not args.no_autotune:
+                cs.autotune()
+        c.spec = cs.spec
+        css[c.name] = cs
+    return css
+
+
+def _compile_requests(ctx, reqs, args, n):
+    """One compiled spec per operator of the requests (the served and streamed
+    forms: keys dealt as they are used), its arity chosen for calls of n
+    elements; every request's op takes the kept spec."""
+    css = compile_specs(ctx, list(reqs[0].ops), args, form=1, n_of=lambda c: n)
+    for rq in reqs:
+        for op in rq.ops:
+            op.spec = css[op.name].spec
     return css
 
 
@@ -694,9 +731,10 @@ def run_rescales(ctx, args, dev, stream, world):
     from paper_2606_09551_b300 import fusefss as F
     from paper_2606_09551_b300 import inputs as I
     calls = I.bert_layer_rescales()
-    cs = F.CompiledSpec(calls[0].spec, ctx)
-    if not args.no_autotune:
-        cs.autotune()
+    # one spec for every product, its arity chosen for the largest call
+    cs = compile_specs(ctx, [calls[0]], args, form=0, n_of=lambda c: max(d.n for d in calls))[calls[0].name]
+    for c in calls:
+        c.spec = cs.spec
     total = sum(c.n for c in calls)
     xp = {c.name: torch.from_numpy(c.x).to(dev) for c in calls}
     outs = {}
@@ -792,14 +830,17 @@ def run_blocks(ctx, args, dev, stream, world):
     def aes_of(gates, counts):
         return sum(2 * g.shape.aes_per_elem * c for g, c in zip(gates, counts))
 
+    def gates_for(specs, sizes):
+        """The block's gates, each with its arity chosen for its call size."""
+        calls = [I.OpCall(f"g{i}", sp_, np.zeros(1, np.uint64), 0) for i, sp_ in enumerate(specs)]
+        css = compile_specs(ctx, calls, args, form=0, n_of=lambda c: sizes[int(c.name[1:])])
+        return [css[c.name] for c in calls]
+
     # softmax
     rows, L = 12 * 128, 128
     sp = S.softmax_specs()
     names = ["relu", "exp", "shift_e", "recip", "shift_t", "shift_p"]
-    gates = [F.CompiledSpec(sp[k], ctx) for k in names]
-    if not args.no_autotune:
-        for g in gates:
-            g.autotune()
+    gates = gates_for([sp[k] for k in names], [rows * L // 2, rows * L, rows * L, rows, rows, rows * L])
     sm = F.Softmax(ctx, gates, rows, L)
     scores = 2.0 * rng.standard_normal((rows, L))
     ms, y, cb = timed(sm, S.encode(scores.reshape(-1), 12), rows * L, 2000)
@@ -822,10 +863,7 @@ def run_blocks(ctx, args, dev, stream, world):
                               "rounding shift gates; one plan, keys dealt before each evaluation"}
     sm.close()
     # the same block with one Newton step refining the reciprocal
-    ngates = [F.CompiledSpec(sp[k], ctx) for k in ("shift_n1", "shift_n2")]
-    if not args.no_autotune:
-        for g in ngates:
-            g.autotune()
+    ngates = gates_for([sp[k] for k in ("shift_n1", "shift_n2")], [rows, rows])
     smn = F.Softmax(ctx, gates, rows, L, newton_gates=ngates, newton=1)
     ms_n, y_n, cb_n = timed(smn, S.encode(scores.reshape(-1), 12), rows * L, 2500)
     aes_n = aes + aes_of(ngates, [rows, rows])
@@ -838,10 +876,7 @@ def run_blocks(ctx, args, dev, stream, world):
     rows, H = 128, 768
     lsp, cH = S.layernorm_specs(H)
     names = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
-    gates = [F.CompiledSpec(lsp[k], ctx) for k in names]
-    if not args.no_autotune:
-        for g in gates:
-            g.autotune()
+    gates = gates_for([lsp[k] for k in names], [rows, rows, rows, rows, rows * H])
     ln = F.LayerNorm(ctx, gates, rows, H, cH)
     hid = rng.standard_normal((rows, H)) * 1.2 + 0.3
     ms, y, cb = timed(ln, S.encode(hid.reshape(-1), 12), rows * H, 3000)
@@ -857,10 +892,7 @@ def run_blocks(ctx, args, dev, stream, world):
                                 "rounding shift gates (no affine weights)"}
     ln.close()
     # the same block with one Newton step refining 1/sqrt
-    ngates = [F.CompiledSpec(lsp[k], ctx) for k in ("shift_n1", "shift_n2", "shift_n3")]
-    if not args.no_autotune:
-        for g in ngates:
-            g.autotune()
+    ngates = gates_for([lsp[k] for k in ("shift_n1", "shift_n2", "shift_n3")], [rows, rows, rows])
     lnn = F.LayerNorm(ctx, gates, rows, H, cH, newton_gates=ngates, newton=1)
     ms_n, y_n, cb_n = timed(lnn, S.encode(hid.reshape(-1), 12), rows * H, 3500)
     aes_n = aes + aes_of(ngates, [rows, rows, rows])
@@ -1041,7 +1073,7 @@ def run_served(ctx, args, dev):
     nreq, nlay = args.served_requests, args.served_layers
     reqs = I.bert_large_trace(nreq)
     lens = [rq.L for rq in reqs]
-    css = _compile_requests(ctx, reqs, not args.no_autotune)
+    css = _compile_requests(ctx, reqs, args, 1 << 22)
     total = 0
     pending = []
     for rq in reqs:
@@ -1060,6 +1092,7 @@ def run_served(ctx, args, dev):
     wall = time.perf_counter() - t0
     st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
+    res["dcf_bits"] = {name: cs.spec.dcf_bits for name, cs in css.items()}
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "offered_requests_per_s": 20.0,
                 "sustainable_requests_per_s": nreq / res["span_s"],
@@ -1093,7 +1126,7 @@ def run_gpt2_batch(ctx, args, dev):
     nreq, nlay = 32, args.gpt2_layers
     reqs = I.gpt2_batch(nreq)
     lens = [rq.L for rq in reqs]
-    css = _compile_requests(ctx, reqs, not args.no_autotune)
+    css = _compile_requests(ctx, reqs, args, 1 << 22)
     total = 0
     pending = []
     for rq in reqs:
@@ -1111,6 +1144,7 @@ def run_gpt2_batch(ctx, args, dev):
     wall = time.perf_counter() - t0
     st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
+    res["dcf_bits"] = {name: cs.spec.dcf_bits for name, cs in css.items()}
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "config": "32 GPT-2-small requests (hidden 768, 12 heads, MLP 3072, 2 LayerNorms), "
                           "L uniform [32, 1024], %d of 12 layers each, 64 GB key budget" % nlay})
@@ -1120,7 +1154,7 @@ def run_gpt2_batch(ctx, args, dev):
     return res
 
 
-def run_large_layer(ctx, dev, tune=True, no_serial=False):
+def run_large_layer(ctx, dev, args, no_serial=False):
     """One GPT-style 2.7B layer (hidden 2560, 32 heads, MLP 10240 with SiLU,
     seq 1024): SiLU on 1024 x 10240, softmax nExp on 32 x 1024 x 1024, the
     reciprocal of the 32 x 1024 row sums and rsqrt for two LayerNorms (2 x
@@ -1133,7 +1167,7 @@ def run_large_layer(ctx, dev, tune=True, no_serial=False):
     from paper_2606_09551_b300 import fusefss as F
     from paper_2606_09551_b300 import inputs as I
     reqs = I.large_layer()
-    css = _compile_requests(ctx, reqs, tune)
+    css = _compile_requests(ctx, reqs, args, 1 << 22)
     ops = _request_ops(css, reqs[0], dev)
     xs = {name: o[1] for name, o in zip(css, ops)}
     call_base = reqs[0].call_base
@@ -1153,6 +1187,7 @@ def run_large_layer(ctx, dev, tune=True, no_serial=False):
     sv.close()
     deal, online = _stream_aes([ops], 1)
     return {"value": total / span_s, "unit": "elements/s", "elements": int(total), "layer_ms": st["layer_ms_max"],
+            "dcf_bits": {name: cs.spec.dcf_bits for name, cs in css.items()},
             "online": None if no_serial else _serial_rates(ctx, [([ops], 0.0, call_base)], 1, (deal, online)),
             "aes_blocks": deal + online, "aes_roofline_frac": (deal + online) / span_s / _aes_roofline(),
             "steps": int(st["steps"]), "chunks": int(st["chunks"]), "keys_tb_streamed": key_tb,
@@ -1166,11 +1201,24 @@ def run_large_layer(ctx, dev, tune=True, no_serial=False):
 # reference arm: the oracle (the paper ships no code), on the host cores
 # ---------------------------------------------------------------------------
 
-def full_config(config, calls, world):
+# The DCF arity the reference arm's oracle runs for the plain form (resident
+# keys): the one the layer's gates measure fastest at on this GPU (arity 8
+# for GeLU-8, nExp and Rsqrt; the measured choice per spec is in the GPU
+# arm's autotune record).  The reference arm has no GPU to measure with.
+PLAIN_DCF_BITS = 3
+
+
+def reference_calls(calls, args):
+    """The calls at the arity the reference arm (and the printed config) uses."""
+    from paper_2606_09551_b300 import inputs as I
+    return I.with_arity(calls, args.dcf_bits or PLAIN_DCF_BITS)
+
+
+def full_config(config, calls, world, args):
     """The workload's config as both arms print it: the workload, how L2 is
     kept out of the measurement, and the process layout."""
     from paper_2606_09551_b300 import fusefss as F
-    key_gb = sum(2 * F.CompiledSpec(c.spec).shape.key_bytes_per_elem * c.n for c in calls) / 1e9
+    key_gb = sum(2 * F.CompiledSpec(c.spec).shape.key_bytes_per_elem * c.n for c in reference_calls(calls, args)) / 1e9
     return dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" % key_gb,
                 parallelism="replicas x %d" % world if world > 1 else "one process; both parties in it")
 
@@ -1187,6 +1235,7 @@ def run_reference(args, world):
     import oracle as O
     from paper_2606_09551_b300 import inputs as I
     calls, config = workload(args.workload)
+    calls = reference_calls(calls, args)
     threads = os.cpu_count() or 1
     step_s = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
     # per-element oracle time estimate: 0.2 us per AES block per core, both parties
@@ -1230,14 +1279,15 @@ def run_reference(args, world):
     per_step_s = statistics.mean(times)
     total = sum(sample.values())
     value = total / per_step_s
+    ar = {c.name: 1 << c.spec.dcf_bits for c in calls}
     desc = ("oracle eval_pair (both parties) per step on %s elements (%.4f of each operator: %s), "
-            "%d threads" % (total, frac, ", ".join(f"{sample[k]} {k}" for k in sample), threads))
+            "%d threads" % (total, frac, ", ".join(f"{sample[k]} {k} (DCF arity {ar[k]})" for k in sample), threads))
     return {
         "impl": "reference",
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
         "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic", "config": full_config(config, calls, world),
+        "dtype": "u64", "data": "synthetic", "config": full_config(config, calls, world, args),
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -158,6 +158,13 @@ typedef struct {
     uint32_t n_bx_nodes;                 /* <= FFSS_MAX_BX_NODES */
     const ffss_bx_node *bx_nodes;
     const uint32_t *piecewise_root;      /* m * n_piecewise node indices */
+    /* DCF input bits per tree level r of the gate's keys (arity 2^r): 1, 2
+     * or 3; 0 means 2.  A protocol parameter, not part of the function: the
+     * outputs are the same for every r.  A walk costs ceil(k / r) AES blocks
+     * (times 1 + V for a lookup key), a key 16 * 2^r bytes per level (plus
+     * 8 p * 2^r for a lookup key), and the dealer expands 2^r children per
+     * level for both parties.  FFSS_ERR_UNSUPPORTED above 3. */
+    uint32_t dcf_bits;
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -359,6 +366,23 @@ typedef struct {
  * keeps the cost model).  The call writes the spec's tuning record: it must
  * not run concurrently with another host thread's call on the same spec. */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
+
+/* Compile `desc` with the DCF arity that measures fastest for calls of n
+ * elements (the arity is a protocol parameter: every choice computes the
+ * same outputs, Def. "operator specification" in Sec. 4.1 fixes none).  With
+ * desc->dcf_bits = 0 the spec is compiled at r = 1, 2 and 3 input bits per
+ * tree level and each is tuned with ffss_autotune (same samples and cost);
+ * with desc->dcf_bits set only that r is.  The one kept has the least
+ * predicted time: for form 0 the plain gate launch's (resident keys: the
+ * plain and batched forms), for form 1 the gate's plus the dealer's for the
+ * same elements (keys dealt as they are used: the served and streamed
+ * forms), the dealer rate taken from the tuner's own key generation.  The
+ * others are freed.  *out receives the tuned spec, *dcf_bits_out (may be
+ * NULL) its r.  Synchronizes the stream.  Errors: those of
+ * ffss_spec_compile and ffss_autotune (the last one, when no arity could be
+ * compiled and tuned), FFSS_ERR_INVALID (NULL argument, form > 1). */
+int ffss_spec_compile_best(ffss_ctx *ctx, const ffss_spec_desc *desc, uint64_t n, uint32_t form, void *stream,
+                           ffss_spec **out, uint32_t *dcf_bits_out);
 
 /* The work split (slots per element) a plain launch of the fused gate of
  * `spec` uses for a call of n elements: forced; else 32 for a call that fits

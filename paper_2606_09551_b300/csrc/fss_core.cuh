@@ -242,30 +242,31 @@ FFSS_CORE uint64_t view(uint64_t u, uint32_t f, uint64_t c) {
 }
 
 // ---------------------------------------------------------------------------
-// DCF of arity 4 (two input bits per tree level; a generalisation of Boyle et
-// al. 2021's comparison DCF): the k-bit input is read as ceil(k/2) digits MSB
-// first, the first digit taking one bit when k is odd.  Expansion of child c
-// of seed s: blk = H(s, c); control bit t = bit 0; bit payload = bit 1; next
-// seed = blk with bits 0, 1 cleared; vector payload V blocks H(s, 4 + cV + q).
-// Each level stores a correction word per child, row (level * 4 + c): the
-// seed CW with the t CW in bit 0 and, for the bit payload, the value CW in
-// bit 1.  A party with t = 1 XORs child c's CWs in.  Leaf: bit 2 of the seed
-// (bit payload) or H(s, 4 + q), plus t times the leaf CW.
+// DCF of arity A = 2^r (r input bits per tree level; a generalisation of Boyle
+// et al. 2021's comparison DCF; r is the spec's dcf_r): the k-bit input is
+// read as ceil(k/r) digits MSB first, the first digit taking the top
+// k - r (levels - 1) bits.  Expansion of child c of seed s: blk = H(s, c);
+// control bit t = bit 0; bit payload = bit 1; next seed = blk with bits 0, 1
+// cleared; vector payload V blocks H(s, A + cV + q).  Each level stores a
+// correction word per child, row (level * A + c): the seed CW with the t CW
+// in bit 0 and, for the bit payload, the value CW in bit 1.  A party with
+// t = 1 XORs child c's CWs in.  Leaf: bit 2 of the seed (bit payload) or
+// H(s, A + q), plus t times the leaf CW.
 // ---------------------------------------------------------------------------
 
-FFSS_CORE uint32_t dcf_levels(uint32_t k) { return (k + 1) / 2; }
+FFSS_CORE uint32_t dcf_levels(uint32_t k, uint32_t r) { return (k + r - 1) / r; }
 
 // Bit payload: returns the XOR share of 1[u < alpha].
-// root: uint4 root[n]; child CW of level i at root[(1 + 4 i + c) n]; leaf: the leaf CW bit.
+// root: uint4 root[n]; child CW of level i at root[(1 + A i + c) n]; leaf: the leaf CW bit.
 template <class AES>
-FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 *root, uint64_t n,
+FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t r, uint64_t u, const uint4 *root, uint64_t n,
                                 uint64_t leaf, const AES &aes) {
-  const uint32_t nlev = dcf_levels(k);
+  const uint32_t nlev = dcf_levels(k, r), dmask = (1u << r) - 1u;
   uint4 s = root[0];
-  uint32_t t = b, v = 0;
-  for (uint32_t i = 0; i < nlev; ++i) {
-    const uint32_t c = uint32_t(u >> (2 * (nlev - 1 - i))) & 3u;
-    const uint4 cw = root[(1 + 4 * uint64_t(i) + c) * n];
+  uint32_t t = b, v = 0, sh = r * (nlev - 1);
+  for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
+    const uint32_t c = uint32_t(u >> sh) & dmask;
+    const uint4 cw = root[(1 + (uint64_t(i) << r) + c) * n];
     const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
     v ^= (blk.x >> 1) ^ (tm & (cw.x >> 1));
@@ -282,17 +283,18 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint64_t u, const uint4 
 
 // Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^c) + t VCW[c]) + leaf
 // term into acc (the caller applies the party sign (-1)^b once).
-// vcw: u64 [levels][4][P][n]; leaf: u64 [P][n].
+// vcw: u64 [levels][A][P][n]; leaf: u64 [P][n].
 template <int P, class AES>
-FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 *root, const uint64_t *vcw,
-                                const uint64_t *leaf, uint64_t n, uint64_t *acc, const AES &aes) {
+FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, const uint4 *root,
+                                const uint64_t *vcw, const uint64_t *leaf, uint64_t n, uint64_t *acc,
+                                const AES &aes) {
   constexpr int V = (P + 1) / 2;
-  const uint32_t nlev = dcf_levels(k);
+  const uint32_t nlev = dcf_levels(k, r), A = 1u << r;
   uint4 s = root[0];
-  uint32_t t = b;
-  for (uint32_t i = 0; i < nlev; ++i) {
-    const uint32_t c = (u >> (2 * (nlev - 1 - i))) & 3u;
-    const uint64_t row = 4 * uint64_t(i) + c;
+  uint32_t t = b, sh = r * (nlev - 1);
+  for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
+    const uint32_t c = (u >> sh) & (A - 1u);
+    const uint64_t row = (uint64_t(i) << r) + c;
     const uint4 cw = root[(1 + row) * n];
     uint64_t vc[P];
 #pragma unroll
@@ -301,7 +303,7 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
     uint64_t conv[2 * V];
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-      const uint4 cb = mmo(s, 4u + c * V + q, aes);
+      const uint4 cb = mmo(s, A + c * V + q, aes);
       conv[2 * q] = lo64(cb);
       conv[2 * q + 1] = hi64(cb);
     }
@@ -319,7 +321,7 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
   uint64_t conv[2 * V];
 #pragma unroll
   for (int q = 0; q < V; ++q) {
-    const uint4 cb = mmo(s, 4u + q, aes);
+    const uint4 cb = mmo(s, A + q, aes);
     conv[2 * q] = lo64(cb);
     conv[2 * q + 1] = hi64(cb);
   }
@@ -333,60 +335,55 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t u, const uint4 
 // (identical for both parties) and the V_CW words into both key sections.
 // ---------------------------------------------------------------------------
 
-// The four children of both parties' seeds: ch[b][c] = H(s_b, c), c < nc
-// (nc = 2 for a one-bit first digit; the other two stay zero).
-template <class AES4>
-FFSS_CORE void expand_children(uint4 s0, uint4 s1, uint32_t nc, uint4 (&ch)[2][4], const AES4 &aes4) {
-  const Blk4 e0 = mmo4(s0, 0, s0, 1, s1, 0, s1, 1, aes4);
-  ch[0][0] = e0.v[0]; ch[0][1] = e0.v[1]; ch[1][0] = e0.v[2]; ch[1][1] = e0.v[3];
-  if (nc == 4) {
-    const Blk4 e1 = mmo4(s0, 2, s0, 3, s1, 2, s1, 3, aes4);
-    ch[0][2] = e1.v[0]; ch[0][3] = e1.v[1]; ch[1][2] = e1.v[2]; ch[1][3] = e1.v[3];
-  } else {
-    ch[0][2] = ch[0][3] = ch[1][2] = ch[1][3] = make_uint4(0, 0, 0, 0);
-  }
-}
-
-// Bit-payload DCF Gen of arity 4 for 1[u < alpha] on k-bit u, both parties.
-// keep4(i0) returns the path child's random block 0 of levels i0 .. i0 + 3
-// (its seed CW, and bit 1 its value CW).  Writes root and child CWs (rows
-// 1 + 4 i + c) and the leaf CW bit into both keys.
+// Bit-payload DCF Gen of arity A = 2^r for 1[u < alpha] on k-bit u, both
+// parties.  keep4(i0) returns the path child's random block 0 of levels
+// i0 .. i0 + 3 (its seed CW, and bit 1 its value CW).  Writes root and child
+// CWs (rows 1 + A i + c; zero for the children a narrow first digit cannot
+// take) and the leaf CW bit into both keys.  Children are expanded in pairs,
+// both parties' seeds in one 4-block call.
 template <class AES4, class KEEP4>
-FFSS_CORE void dcf_bit_gen(uint32_t k, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
+FFSS_CORE void dcf_bit_gen(uint32_t k, uint32_t r, uint64_t alpha, uint4 s0, uint4 s1, uint4 *q0, uint4 *q1,
                            uint64_t *leaf0, uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   q0[0] = s0;
   q1[0] = s1;
-  const uint32_t nlev = dcf_levels(k);
-  uint32_t t0 = 0, t1 = 1, wb = 0;
+  const uint32_t nlev = dcf_levels(k, r), A = 1u << r;
+  uint32_t t0 = 0, t1 = 1, wb = 0, sh = r * (nlev - 1);
   Blk4 R4;
-  for (uint32_t i = 0; i < nlev; ++i) {
-    const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
-    const uint32_t a = uint32_t(alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
-    uint4 ch[2][4];
-    expand_children(s0, s1, nc, ch, aes4);
+  for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
+    const uint32_t nc = i == 0 ? (1u << (k - sh)) : A;   // the first digit takes the top k - sh bits
+    const uint32_t a = uint32_t(alpha >> sh) & (nc - 1u);
     if ((i & 3u) == 0) R4 = keep4(i);
     const uint32_t ri = i & 3u;
     const uint4 R = ri == 0 ? R4.v[0] : ri == 1 ? R4.v[1] : ri == 2 ? R4.v[2] : R4.v[3];
     uint4 ck = make_uint4(0, 0, 0, 0), ka0 = ck, ka1 = ck;
-#pragma unroll
-    for (uint32_t c = 0; c < 4; ++c) {
-      uint4 cw = make_uint4(0, 0, 0, 0);
-      if (c < nc) {
-        if (c != a) {
-          cw = xor4(ch[0][c], ch[1][c]);
-          const uint32_t tcw = cw.x & 1u;
-          const uint32_t vb = ((cw.x >> 1) ^ wb ^ (c < a ? 1u : 0u)) & 1u;
-          cw.x = (cw.x & ~3u) | tcw | (vb << 1);
-        } else {
-          cw = R;
-          cw.x = (cw.x & ~3u) | ((ch[0][c].x ^ ch[1][c].x ^ 1u) & 1u) | (R.x & 2u);
-          ck = cw;
-          ka0 = ch[0][c];
-          ka1 = ch[1][c];
-        }
+    for (uint32_t cp = 0; cp < A; cp += 2) {
+      uint4 e[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      if (cp < nc) {
+        const Blk4 eb = mmo4(s0, cp, s0, cp + 1, s1, cp, s1, cp + 1, aes4);
+        e[0] = eb.v[0]; e[1] = eb.v[1]; e[2] = eb.v[2]; e[3] = eb.v[3];
       }
-      q0[(1 + 4 * uint64_t(i) + c) * n] = cw;
-      q1[(1 + 4 * uint64_t(i) + c) * n] = cw;
+#pragma unroll
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t c = cp + h;
+        const uint4 c0 = e[h], c1 = e[2 + h];     // party 0 / party 1 child c
+        uint4 cw = make_uint4(0, 0, 0, 0);
+        if (c < nc) {
+          if (c != a) {
+            cw = xor4(c0, c1);
+            const uint32_t tcw = cw.x & 1u;
+            const uint32_t vb = ((cw.x >> 1) ^ wb ^ (c < a ? 1u : 0u)) & 1u;
+            cw.x = (cw.x & ~3u) | tcw | (vb << 1);
+          } else {
+            cw = R;
+            cw.x = (cw.x & ~3u) | ((c0.x ^ c1.x ^ 1u) & 1u) | (R.x & 2u);
+            ck = cw;
+            ka0 = c0;
+            ka1 = c1;
+          }
+        }
+        q0[(1 + (uint64_t(i) << r) + c) * n] = cw;
+        q1[(1 + (uint64_t(i) << r) + c) * n] = cw;
+      }
     }
     // the path continues through child a
     wb = (wb ^ (ka0.x >> 1) ^ (ka1.x >> 1) ^ (ck.x >> 1)) & 1u;
@@ -421,27 +418,26 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
   }
 }
 
-// Vector-payload DCF Gen of arity 4 for beta * 1[u < alpha] on k-bit u
+// Vector-payload DCF Gen of arity A = 2^r for beta * 1[u < alpha] on k-bit u
 // (k <= 32), both parties.  keep4(i): the path child's random blocks of
 // level i; block 0 its seed CW, blocks 1..V its value CWs (p little-endian
-// uint64).  Writes root and
-// child CWs (rows 1 + 4 i + c), value CWs vcw [levels][4][P][n] and the
-// leaf CWs [P][n].
+// uint64).  Writes root and child CWs (rows 1 + A i + c), value CWs vcw
+// [levels][A][P][n] and the leaf CWs [P][n].
 template <int P, class AES4, class KEEP4>
-FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
+FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t r, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
                            uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t *leaf0,
                            uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   constexpr uint32_t V = (P + 1) / 2;
   l0[0] = s0;
   l1[0] = s1;
-  const uint32_t nlev = dcf_levels(k);
-  uint32_t t0 = 0, t1 = 1;
+  const uint32_t nlev = dcf_levels(k, r), A = 1u << r;
+  uint32_t t0 = 0, t1 = 1, sh = r * (nlev - 1);
   uint64_t W[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) W[q] = 0;
-  for (uint32_t i = 0; i < nlev; ++i) {
-    const uint32_t nc = (i == 0 && (k & 1u)) ? 2u : 4u;
-    const uint32_t a = (alpha >> (2 * (nlev - 1 - i))) & (nc - 1u);
+  for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
+    const uint32_t nc = i == 0 ? (1u << (k - sh)) : A;   // the first digit takes the top k - sh bits
+    const uint32_t a = (alpha >> sh) & (nc - 1u);
     const bool neg = t1 != 0;
     const Blk4 K4 = keep4(i);
     uint4 ck = make_uint4(0, 0, 0, 0), ka0 = ck, ka1 = ck;
@@ -449,15 +445,14 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
 #pragma unroll
     for (int q = 0; q < P; ++q) vk[q] = ca0[q] = ca1[q] = 0;
     // children in pairs (cp, cp + 1): seeds of both parties in one 4-block call
-#pragma unroll
-    for (uint32_t cp = 0; cp < 4; cp += 2) {
+    for (uint32_t cp = 0; cp < A; cp += 2) {
       uint4 e[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
       uint64_t pv[2][2][P + 1];     // [child - cp][party][word]
       if (cp < nc) {
         const Blk4 sb = mmo4(s0, cp, s1, cp, s0, cp + 1, s1, cp + 1, aes4);
         e[0] = sb.v[0]; e[1] = sb.v[1]; e[2] = sb.v[2]; e[3] = sb.v[3];
         if (V == 1) {
-          const Blk4 pb = mmo4(s0, 4u + cp, s1, 4u + cp, s0, 4u + cp + 1, s1, 4u + cp + 1, aes4);
+          const Blk4 pb = mmo4(s0, A + cp, s1, A + cp, s0, A + cp + 1, s1, A + cp + 1, aes4);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             pv[w >> 1][w & 1][0] = lo64(pb.v[w]);
@@ -468,7 +463,7 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
           Blk8 in;
 #pragma unroll
           for (uint32_t h = 0; h < 2; ++h) {
-            const uint32_t j = 4u + (cp + h) * V;
+            const uint32_t j = A + (cp + h) * V;
             in.v[4 * h + 0] = s0; in.v[4 * h + 0].x ^= j;
             in.v[4 * h + 1] = s0; in.v[4 * h + 1].x ^= j + 1;
             in.v[4 * h + 2] = s1; in.v[4 * h + 2].x ^= j;
@@ -520,7 +515,7 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
             ka1 = c1;
           }
         }
-        const uint64_t row = 4 * uint64_t(i) + c;
+        const uint64_t row = (uint64_t(i) << r) + c;
         l0[(1 + row) * n] = cw;
         l1[(1 + row) * n] = cw;
 #pragma unroll
@@ -543,9 +538,9 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t alpha, const uint64_t *beta, uin
     const uint32_t nt0 = (ka0.x ^ (t0 & tk)) & 1u, nt1 = (ka1.x ^ (t1 & tk)) & 1u;
     s0 = ns0; s1 = ns1; t0 = nt0; t1 = nt1;
   }
-  // leaf CW from both parties' leaf conversions H(s, 4 + q)
+  // leaf CW from both parties' leaf conversions H(s, A + q)
   const uint4 sd[4] = {s0, s1, s0, s1};
-  const uint32_t j0[4] = {4u, 4u, 4u, 4u};
+  const uint32_t j0[4] = {A, A, A, A};
   uint64_t f[4][P + 1];
   conv4<P>(sd, j0, f, aes4);
   const bool neg = t1 != 0;

@@ -285,6 +285,8 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   memset(&S, 0, sizeof(S));
   S.k = d->k; S.m = d->m; S.d = d->degree; S.r = d->n_out; S.p = p;
   S.V = (p + 1) / 2;
+  if (d->dcf_bits > 3) return fail(FFSS_ERR_UNSUPPORTED, "dcf_bits=%u outside 1..3", d->dcf_bits);
+  S.dcf_r = d->dcf_bits ? d->dcf_bits : 2;
   S.M = d->m == 1 ? 1 : d->m + 1;
   if (S.M > 1 && d->k > FFSS_MAX_K_LOOKUP)
     return fail(FFSS_ERR_UNSUPPORTED, "k=%u > %d with an interval lookup (m > 1)", d->k, FFSS_MAX_K_LOOKUP);
@@ -890,8 +892,9 @@ static Sched make_sched(const DevSpec &S, uint32_t slots, uint64_t *max_load, ui
   memset(&sc, 0, sizeof(sc));
   const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
   std::vector<std::pair<uint64_t, uint32_t>> items;
-  for (uint32_t t = 0; t < S.T; ++t) items.push_back({key_levels(S.q_f[t]), t});
-  for (uint32_t j = 0; j + 1 < S.M; ++j) items.push_back({uint64_t(key_levels(S.k)) * (1 + S.V) + S.V, S.T + j});
+  for (uint32_t t = 0; t < S.T; ++t) items.push_back({key_levels(S.q_f[t], S.dcf_r), t});
+  for (uint32_t j = 0; j + 1 < S.M; ++j)
+    items.push_back({uint64_t(key_levels(S.k, S.dcf_r)) * (1 + S.V) + S.V, S.T + j});
   std::stable_sort(items.begin(), items.end(), [](auto &a, auto &b) { return a.first > b.first; });
   std::vector<uint64_t> load(slots, 0);
   std::vector<std::vector<uint32_t>> own(slots);
@@ -1262,6 +1265,61 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
   spec->tune = t;
   spec->tuned = true;
   if (out) *out = t;
+  return FFSS_OK;
+}
+
+// Predicted time of a plain gate launch of n elements from the spec's tuning
+// record: the least fixed + waves x tile time over the measured splits (a
+// small launch, n <= SMs x 8, is taken as one tile at the finest split).
+static double predicted_gate_us(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n) {
+  const ffss_tune &t = spec->tune;
+  uint32_t tb = 0;
+  if (small_launch(ctx, n, &tb)) return t.fixed_us[t.n_tried - 1] + t.tile_us[t.n_tried - 1];
+  double best = -1;
+  for (uint32_t i = 0; i < t.n_tried; ++i) {
+    const double us = t.fixed_us[i] + gate_waves(ctx, n, t.slots[i]) * t.tile_us[i];
+    if (best < 0 || us < best) best = us;
+  }
+  return best;
+}
+
+extern "C" int ffss_spec_compile_best(ffss_ctx *ctx, const ffss_spec_desc *desc, uint64_t n, uint32_t form,
+                                      void *stream, ffss_spec **out, uint32_t *dcf_bits_out) {
+  if (!ctx || !desc || !out) return fail(FFSS_ERR_INVALID, "ffss_spec_compile_best: NULL argument");
+  if (form > 1) return fail(FFSS_ERR_INVALID, "ffss_spec_compile_best: form %u is not 0 or 1", form);
+  ffss_spec *best = nullptr;
+  double best_us = -1;
+  uint32_t best_r = 0;
+  int last_rc = FFSS_OK;
+  const uint32_t r0 = desc->dcf_bits ? desc->dcf_bits : 1, r1 = desc->dcf_bits ? desc->dcf_bits : 3;
+  for (uint32_t r = r0; r <= r1; ++r) {
+    ffss_spec_desc d = *desc;
+    d.dcf_bits = r;
+    ffss_spec *sp = nullptr;
+    int rc = ffss_spec_compile(ctx, &d, &sp);
+    if (!rc) rc = ffss_autotune(ctx, sp, nullptr, stream);
+    if (rc) {
+      if (sp) ffss_spec_free(sp);
+      last_rc = rc;
+      continue;
+    }
+    double us = predicted_gate_us(ctx, sp, n);
+    if (form == 1) {
+      // the tuner dealt 3 x SMs x 256 elements (its two samples) in dealer_ms
+      us += sp->tune.dealer_ms * 1000.0 / (1.5 * sp->tune.sample_elems) * double(n);
+    }
+    if (best_us < 0 || us < best_us) {
+      if (best) ffss_spec_free(best);
+      best = sp;
+      best_us = us;
+      best_r = r;
+    } else {
+      ffss_spec_free(sp);
+    }
+  }
+  if (!best) return last_rc ? last_rc : fail(FFSS_ERR_INVALID, "ffss_spec_compile_best: no arity compiled");
+  *out = best;
+  if (dcf_bits_out) *dcf_bits_out = best_r;
   return FFSS_OK;
 }
 

@@ -132,10 +132,10 @@ __device__ __forceinline__ void stage_shared(uint32_t *tab, DevSpec *sspec, cons
 // the walk at the cost of the bare AES chain plus a few operations per level;
 // inlined into the fused gate the compiler emitted about 40 % more
 // instructions per level.  One call per walk.
-__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint64_t u, const uint4 *root, uint64_t n,
-                                          uint64_t leaf, const char *tab, uint32_t lane4) {
+__device__ __noinline__ uint32_t bit_walk(uint32_t b, uint32_t f, uint32_t r, uint64_t u, const uint4 *root,
+                                          uint64_t n, uint64_t leaf, const char *tab, uint32_t lane4) {
   const AesDcfInline aes{Tab{tab, lane4}};
-  return dcf_bit_eval(b, f, u, root, n, leaf, aes);
+  return dcf_bit_eval(b, f, r, u, root, n, leaf, aes);
 }
 
 // One packed-comparison query t (App. I): XOR share of 1[view_{k_t,c_t}(x^) < theta_t].
@@ -145,8 +145,10 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   const char *q = kb + L.off_q[t];
   const uint32_t f = S.q_f[t];
   const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
-  const uint64_t leaf = reinterpret_cast<const uint64_t *>(q + 16ull * (1 + 4ull * key_levels(f)) * L.n)[e];
-  return bit_walk(b, f, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
+  const uint32_t r = S.dcf_r;
+  const uint64_t leaf =
+      reinterpret_cast<const uint64_t *>(q + 16ull * (1 + (uint64_t(key_levels(f, r)) << r)) * L.n)[e];
+  return bit_walk(b, f, r, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
 }
 
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
@@ -156,11 +158,12 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
                                          const AesDcfInline &aes) {
   const uint32_t k = S.k;
   const char *l = kb + L.off_l[j];
-  const uint64_t lv = key_levels(k);
+  const uint32_t r = S.dcf_r;
+  const uint64_t rows = uint64_t(key_levels(k, r)) << r;    // levels x children
   const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
-  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + 4 * lv) * L.n) + e;
-  const uint64_t *leaf = vcw + 4 * lv * P * L.n;
-  dcf_vec_eval_acc<P>(b, k, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + rows) * L.n) + e;
+  const uint64_t *leaf = vcw + rows * P * L.n;
+  dcf_vec_eval_acc<P>(b, k, r, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -892,12 +895,11 @@ __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &
     return mmo4(base, 4u * lvl, base, 4u * lvl + 1, base, 4u * lvl + 2, base, 4u * lvl + 3, rkd);
   };
   char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
-  const uint64_t lv = key_levels(S.k);
-  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + 4 * lv) * n) + e;
-  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + 4 * lv) * n) + e;
-  dcf_vec_gen<P>(S.k, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + 4 * lv * P * n, v1 + 4 * lv * P * n, n, rkd,
-                 keep4);
+  const uint64_t rows = uint64_t(key_levels(S.k, S.dcf_r)) << S.dcf_r;    // levels x children
+  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + rows) * n) + e;
+  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + rows) * n) + e;
+  dcf_vec_gen<P>(S.k, S.dcf_r, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
+                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + rows * P * n, v1 + rows * P * n, n, rkd, keep4);
 }
 
 __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,
@@ -919,11 +921,10 @@ __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S
     return mmo4(base, 4u * lvl0, base, 4u * (lvl0 + 1), base, 4u * (lvl0 + 2), base, 4u * (lvl0 + 3), rkd);
   };
   char *q0 = A.k0 + L.off_q[t], *q1 = A.k1 + L.off_q[t];
-  const uint64_t lv = key_levels(f);
-  dcf_bit_gen(f, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e,
-              reinterpret_cast<uint4 *>(q1) + e,
-              reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + 4 * lv) * n) + e,
-              reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + 4 * lv) * n) + e, n, rkd, keep4);
+  const uint64_t rows = uint64_t(key_levels(f, S.dcf_r)) << S.dcf_r;    // levels x children
+  dcf_bit_gen(f, S.dcf_r, alpha, s0, s1, reinterpret_cast<uint4 *>(q0) + e, reinterpret_cast<uint4 *>(q1) + e,
+              reinterpret_cast<uint64_t *>(q0 + 16ull * (1 + rows) * n) + e,
+              reinterpret_cast<uint64_t *>(q1 + 16ull * (1 + rows) * n) + e, n, rkd, keep4);
 }
 
 // 256 threads per CTA: up to 255 registers per thread keep a key's running

@@ -46,6 +46,7 @@ constexpr uint32_t kDrawKeep = 0x100000u;
 // query list of App. F step (4) in its fixed descriptor order.
 struct DevSpec {
   uint32_t k, m, d, r, p, M, T, n_bool, n_prim, V;   // V = ceil(8p / 16) AES blocks of payload
+  uint32_t dcf_r;              // DCF input bits per tree level: arity 2^dcf_r (1..3)
   uint32_t q_f[kMaxT];         // query view width
   int32_t q_prim[kMaxT];       // -1: the 1[view < r_f] atom; else the predicate it thresholds
   uint64_t q_c[kMaxT];         // query view shift
@@ -104,10 +105,11 @@ struct DevSpec {
 //   Boolean triples  u32  [n_bw][3][n]             (a, b, c), one bit per AND gate
 //   shift gate       u64  [3][n] ((r mod 2^k) >> s share, daBit additive shares lo, hi),
 //                    u32  [n] (daBit XOR shares, bits 0 and 1)
-//   query t          uint4 root[n], uint4 cw[L_t][4][n] (per child: seed CW | t CW |
-//                    value CW << 1), u64 leaf[n] (bit 0); L_t = ceil(k_t / 2) levels
-//   lookup key j     uint4 root[n], uint4 cw[L][4][n], u64 vcw[L][4][p][n],
-//                    u64 leaf[p][n]; L = ceil(k / 2)
+//   query t          uint4 root[n], uint4 cw[L_t][A][n] (per child: seed CW | t CW |
+//                    value CW << 1), u64 leaf[n] (bit 0); L_t = ceil(k_t / r) levels
+//   lookup key j     uint4 root[n], uint4 cw[L][A][n], u64 vcw[L][A][p][n],
+//                    u64 leaf[p][n]; L = ceil(k / r)
+// with r = dcf_r input bits per tree level and A = 2^r children.
 struct KeyLayout {
   uint64_t n;
   uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip, off_trunc, off_trunc_rho;
@@ -118,13 +120,16 @@ struct KeyLayout {
 
 FFSS_HD uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-// Tree levels of a k-bit DCF with two input bits per level (arity 4).
-FFSS_HD uint32_t key_levels(uint32_t k) { return (k + 1) / 2; }
+// Tree levels of a k-bit DCF with r input bits per level (arity 2^r); the
+// first level takes the top k - r (levels - 1) bits.
+FFSS_HD uint32_t key_levels(uint32_t k, uint32_t r) { return (k + r - 1) / r; }
+// Children of the first level (2^(its bit count)).
+FFSS_HD uint32_t first_children(uint32_t k, uint32_t r) { return 1u << (k - r * (key_levels(k, r) - 1)); }
 
 // Bytes per element of one comparison key (view width f) and one lookup key.
-FFSS_HD uint64_t query_key_bytes(uint32_t f) { return 16 + 64ull * key_levels(f) + 8; }
-FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p) {
-  return 16 + 64ull * key_levels(k) + 32ull * key_levels(k) * p + 8ull * p;
+FFSS_HD uint64_t query_key_bytes(uint32_t f, uint32_t r) { return 16 + (16ull << r) * key_levels(f, r) + 8; }
+FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p, uint32_t r) {
+  return 16 + (16ull << r) * key_levels(k, r) + (8ull << r) * key_levels(k, r) * p + 8ull * p;
 }
 
 FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
@@ -141,11 +146,11 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   L.off_trunc_rho = o; o = align256(o + 4ull * tr * n);
   for (uint32_t t = 0; t < s.T; ++t) {
     L.off_q[t] = o;
-    o = align256(o + query_key_bytes(s.q_f[t]) * n);
+    o = align256(o + query_key_bytes(s.q_f[t], s.dcf_r) * n);
   }
   for (uint32_t j = 0; j + 1 < s.M; ++j) {
     L.off_l[j] = o;
-    o = align256(o + lookup_key_bytes(s.k, s.p) * n);
+    o = align256(o + lookup_key_bytes(s.k, s.p, s.dcf_r) * n);
   }
   L.total = o < 256 ? 256 : o;
   return L;
@@ -154,8 +159,8 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 // Per-element key bytes (without alignment padding).
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
   uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_bw + (s.trunc_s ? 28 : 0);
-  for (uint32_t t = 0; t < s.T; ++t) b += query_key_bytes(s.q_f[t]);
-  if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p);
+  for (uint32_t t = 0; t < s.T; ++t) b += query_key_bytes(s.q_f[t], s.dcf_r);
+  if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p, s.dcf_r);
   return b;
 }
 
@@ -163,8 +168,8 @@ inline uint64_t key_bytes_per_elem(const DevSpec &s) {
 // comparison key, (1 + V) per level plus V at the leaf of a lookup key.
 inline uint64_t aes_per_elem(const DevSpec &s) {
   uint64_t a = 0;
-  for (uint32_t t = 0; t < s.T; ++t) a += key_levels(s.q_f[t]);
-  if (s.M > 1) a += (s.M - 1) * (uint64_t(key_levels(s.k)) * (1 + s.V) + s.V);
+  for (uint32_t t = 0; t < s.T; ++t) a += key_levels(s.q_f[t], s.dcf_r);
+  if (s.M > 1) a += (s.M - 1) * (uint64_t(key_levels(s.k, s.dcf_r)) * (1 + s.V) + s.V);
   return a;
 }
 
@@ -172,18 +177,20 @@ inline uint64_t aes_per_elem(const DevSpec &s) {
 // children's random correction words: one block per level of a comparison
 // key, 1 + V per level of a lookup key), then per level both parties'
 // children (2 x arity blocks) and, for a lookup key, their payload blocks
-// (2 x arity x V); the leaf needs both parties' conversions (2V).  A one-bit
-// first digit has arity 2.
+// (2 x arity x V); the leaf needs both parties' conversions (2V).  The first
+// level has first_children(k, r) children.
 inline uint64_t keygen_aes_per_elem(const DevSpec &s) {
   uint64_t a = 4 + s.p + 2ull * (s.T + (s.M > 1 ? s.M - 1 : 0)) + 5ull * s.n_mults + 5ull * s.n_bw +
                (s.trunc_s ? 5 : 0);
+  const uint32_t A = 1u << s.dcf_r;
   for (uint32_t t = 0; t < s.T; ++t) {
-    const uint32_t lv = key_levels(s.q_f[t]);
-    a += lv + 8ull * lv - ((s.q_f[t] & 1u) ? 4 : 0);
+    const uint32_t lv = key_levels(s.q_f[t], s.dcf_r);
+    a += lv + 2ull * (uint64_t(A) * (lv - 1) + first_children(s.q_f[t], s.dcf_r));
   }
   if (s.M > 1) {
-    const uint32_t lv = key_levels(s.k);
-    const uint64_t per = uint64_t(lv) * (1 + s.V) + (8ull * lv - ((s.k & 1u) ? 4 : 0)) * (1 + s.V) + 2ull * s.V;
+    const uint32_t lv = key_levels(s.k, s.dcf_r);
+    const uint64_t ch = uint64_t(A) * (lv - 1) + first_children(s.k, s.dcf_r);
+    const uint64_t per = uint64_t(lv) * (1 + s.V) + 2ull * ch * (1 + s.V) + 2ull * s.V;
     a += (s.M - 1) * per;
   }
   return a;

@@ -51,7 +51,7 @@ class SpecDesc(C.Structure):
                 ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc)),
                 ("trunc_shift", C.c_uint32), ("trunc_signed", C.c_uint32),
                 ("n_bx_nodes", C.c_uint32), ("bx_nodes", C.POINTER(BxNode)),
-                ("piecewise_root", C.POINTER(C.c_uint32))]
+                ("piecewise_root", C.POINTER(C.c_uint32)), ("dcf_bits", C.c_uint32)]
 
 
 class Shape(C.Structure):
@@ -149,6 +149,8 @@ def lib():
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
         L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
         L.ffss_autotune.argtypes = [vp, vp, C.POINTER(Tune), vp]
+        L.ffss_spec_compile_best.argtypes = [vp, C.POINTER(SpecDesc), C.c_uint64, C.c_uint32, vp, C.POINTER(vp),
+                                             C.POINTER(C.c_uint32)]
         L.ffss_gate_slots.argtypes = [vp, vp, C.c_uint64, C.POINTER(C.c_uint32)]
         L.ffss_batch_create.argtypes = [vp, C.c_uint32, C.POINTER(vp)]
         L.ffss_batch_destroy.argtypes = [vp]
@@ -241,7 +243,13 @@ class Context:
 class CompiledSpec:
     """An operator specification compiled by the library (public shape)."""
 
-    def __init__(self, spec: S.OperatorSpec, ctx: Optional[Context] = None):
+    def __init__(self, spec: S.OperatorSpec, ctx: Optional[Context] = None, best_for: Optional[tuple] = None,
+                 stream=None):
+        """best_for = (n, form): let the library compile the spec at each DCF
+        arity, tune each and keep the fastest for calls of n elements
+        (ffss_spec_compile_best; form 0: resident keys, 1: keys dealt as they
+        are used); the kept arity is in self.spec.dcf_bits.  Otherwise the
+        spec is compiled at spec.dcf_bits."""
         self.spec = spec
         self.ctx = ctx
         alpha = np.ascontiguousarray(np.asarray(spec.alpha, dtype=np.uint64))
@@ -271,9 +279,16 @@ class CompiledSpec:
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
                      len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw,
-                     spec.trunc_shift, int(spec.trunc_signed), nbx, nodes, roots)
+                     spec.trunc_shift, int(spec.trunc_signed), nbx, nodes, roots, spec.dcf_bits)
         h = vp()
-        _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
+        if best_for is None:
+            _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
+        else:
+            bits = C.c_uint32()
+            d.dcf_bits = 0
+            _check(lib().ffss_spec_compile_best(ctx.h, C.byref(d), int(best_for[0]), int(best_for[1]),
+                                                _stream(stream), C.byref(h), C.byref(bits)))
+            self.spec = spec.arity(bits.value)
         self.h = h
         sh = Shape()
         _check(lib().ffss_spec_shape(self.h, C.byref(sh)))

@@ -33,6 +33,11 @@ class OpCall:
         return int(self.x.size)
 
 
+def with_arity(calls: List[OpCall], dcf_bits: int) -> List[OpCall]:
+    """The same calls (inputs, call ids) with DCF keys of arity 2^dcf_bits."""
+    return [OpCall(c.name, c.spec.arity(dcf_bits), c.x, c.call_id) for c in calls]
+
+
 def _rng(tag: int) -> np.random.Generator:
     return np.random.default_rng([MASTER_SEED, tag])
 

@@ -72,11 +72,13 @@ def _shape_vs_oracle(sp, may_reject=False):
     assert sh.trunc_shift == sp.trunc_shift
     assert sh.comm_bytes_per_elem == 8 + 16 * o.n_mults + 8 * o.n_bw + tr
     qs = o.queries()
-    lv = lambda f: (f + 1) // 2          # tree levels: two input bits per level (arity 4)
-    # a comparison key: root, 4 child CWs per level, the leaf CW word
-    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_bw + 28 * tr + sum(16 + 64 * lv(f) + 8 for f, _, _ in qs)
-    if o.M > 1:   # a lookup key: root, 4 child CWs and 4 x p value CWs per level, p leaf CWs
-        kb += (o.M - 1) * (16 + 64 * lv(o.k) + 32 * lv(o.k) * o.p + 8 * o.p)
+    r = sp.dcf_bits
+    A = 1 << r
+    lv = lambda f: -(-f // r)          # tree levels: r input bits per level (arity A = 2^r)
+    # a comparison key: root, A child CWs per level, the leaf CW word
+    kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_bw + 28 * tr + sum(16 + 16 * A * lv(f) + 8 for f, _, _ in qs)
+    if o.M > 1:   # a lookup key: root, A child CWs and A x p value CWs per level, p leaf CWs
+        kb += (o.M - 1) * (16 + 16 * A * lv(o.k) + 8 * A * lv(o.k) * o.p + 8 * o.p)
     assert sh.key_bytes_per_elem == kb
     V = (o.p + 1) // 2
     aes = sum(lv(f) for f, _, _ in qs) + ((o.M - 1) * (lv(o.k) * (1 + V) + V) if o.M > 1 else 0)
@@ -100,6 +102,15 @@ def test_workload_spec_shapes():
     # shift gate: two bit-DCF queries of s and k levels, 9 bytes online
     sh = _shape_vs_oracle(S.trunc(32, 12, True))
     assert (sh.T, sh.M, sh.aes_per_elem, sh.comm_bytes_per_elem) == (2, 1, 6 + 16, 9)
+    # arity 8 (three input bits per level) and 2 (one)
+    sh = _shape_vs_oracle(S.nexp16().arity(3))
+    assert sh.aes_per_elem == 16 * 8 + 16 * (8 * 3 + 2)
+    sh = _shape_vs_oracle(S.gelu8().arity(3))
+    assert sh.aes_per_elem == 8 * 6 + 8 * (6 * 3 + 2)
+    sh = _shape_vs_oracle(S.trunc(32, 12, True).arity(3))
+    assert sh.aes_per_elem == 4 + 11
+    sh = _shape_vs_oracle(S.gelu4().arity(1))
+    assert sh.aes_per_elem == 4 * 16 + 4 * (16 * 3 + 2)
 
 
 def test_random_spec_shapes():
@@ -117,11 +128,11 @@ def test_random_spec_shapes():
             sp = S.random_formulas(rng, sp, int(rng.integers(1, 5)), n_nodes=int(rng.integers(4, 40)))
         if trial % 5 < 2:
             sp.trunc_shift, sp.trunc_signed = int(rng.integers(1, k)), bool(trial % 5)
-        _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)), may_reject=True)
+        _shape_vs_oracle(sp.variant(bool(trial % 3 == 0)).arity(1 + trial % 3), may_reject=True)
 
 
 @pytest.mark.parametrize("bad", ["alpha_order", "alpha_end", "m_too_big", "payload", "pred_f", "k0",
-                                 "pw_count", "pw_f", "pw_gamma", "trunc_s", "trunc_signed"])
+                                 "pw_count", "pw_f", "pw_gamma", "trunc_s", "trunc_signed", "dcf_bits"])
 def test_invalid_specs_rejected(bad):
     sp = S.random_spec(np.random.default_rng(1), 8, 4, 1)
     if bad == "alpha_order":
@@ -148,6 +159,8 @@ def test_invalid_specs_rejected(bad):
         sp.trunc_shift = sp.k
     elif bad == "trunc_signed":
         sp.trunc_shift, sp.trunc_signed = 3, 2
+    elif bad == "dcf_bits":
+        sp.dcf_bits = 4
     with pytest.raises(F.FfssError):
         F.CompiledSpec(sp)
 

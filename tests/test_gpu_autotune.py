@@ -96,6 +96,26 @@ def test_autotune_model_and_parity(ctx, sp):
                 assert np.array_equal(got[name].reshape(ref[name].shape), ref[name]), name
 
 
+@pytest.mark.parametrize("form", [0, 1])
+def test_arity_chosen_by_measurement(ctx, form):
+    """ffss_spec_compile_best compiles the spec at DCF arities 2, 4 and 8,
+    tunes each and keeps one; the kept spec is tuned, carries its arity, and
+    its calls, plain and batched, are bit-exact to the oracle at that arity."""
+    sp = S.gelu4()
+    cs = F.CompiledSpec(sp, ctx, best_for=(65536, form))
+    assert cs.spec.dcf_bits in (1, 2, 3)
+    assert cs.shape.aes_per_elem == F.CompiledSpec(sp.arity(cs.spec.dcf_bits)).shape.aes_per_elem
+    o = O.Spec(**cs.spec.descriptor())
+    bt = F.Batch(ctx, 2)
+    n = 2999
+    x = I.uniform_x(n, sp.k, 510 + form)
+    k0, k1, x0, x1 = O.dealer(o, I.KEY_SEED, 60 + form, 0, n, x)
+    ref = O.eval_pair(o, k0, k1, x0, x1)
+    for got in (_gate(ctx, cs, cs.spec, x, 60 + form), _gate(ctx, cs, cs.spec, x, 60 + form, batch=bt)):
+        for name in ("y0", "y1", "z0", "z1"):
+            assert np.array_equal(got[name].reshape(ref[name].shape), ref[name]), name
+
+
 def test_split_limits(ctx):
     """Splits are powers of two up to 32 slots per element; others are refused."""
     bt = F.Batch(ctx, 2)

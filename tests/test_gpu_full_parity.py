@@ -2,7 +2,8 @@
 
 Every workload runs on the GPU at its full size, in the form the benchmark
 times: the single GeLU-4 operator and the BERT-base layer as plain
-per-operator launches (and the layer once more as one batched launch), the
+per-operator launches (and once more as one batched launch), with DCF keys
+of arity 4 and of arity 8 (the plain form's measured choice), the
 GPT-2 batch, the BERT-large trace and the 2.7B-scale layer through the
 continuous-batching server with on-device key streaming (64 GB pool, 4 M
 element chunks), all with autotuned work splits.  The GPU shares of every
@@ -179,6 +180,25 @@ def test_bert_layer_every_element_plain_and_batched(ctx):
     checked = _check("bert_layer", reqs, _plain(ctx, reqs, css))
     assert sum(checked.values()) == 591488
     _check("bert_layer", reqs, _batched(ctx, reqs, css))
+
+
+def test_single_gelu4_arity8_every_element(ctx):
+    """The same call with DCF keys of arity 8 (the plain and batched forms'
+    measured choice for this spec): plain and batched, every element."""
+    reqs = D.build("gelu4_a8")
+    css = _compile(ctx, reqs)
+    assert all(cs.spec.dcf_bits == 3 for cs in css.values())
+    checked = _check("gelu4_a8", reqs, _plain(ctx, reqs, css))
+    assert checked["gelu4"] == 65536
+    _check("gelu4_a8", reqs, _batched(ctx, reqs, css))
+
+
+def test_bert_layer_arity8_every_element_plain_and_batched(ctx):
+    reqs = D.build("bert_layer_a8")
+    css = _compile(ctx, reqs)
+    checked = _check("bert_layer_a8", reqs, _plain(ctx, reqs, css))
+    assert sum(checked.values()) == 591488
+    _check("bert_layer_a8", reqs, _batched(ctx, reqs, css))
 
 
 def test_gpt2_batch_streamed(ctx):
