@@ -62,7 +62,9 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # block per tree level.
 AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates measured in this run",
             "alternatives": ["t_table_shift_mask", "t_table_permute_mad", "bitsliced_lop3 (not a walk form)"]}
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": (6.258327e9 + 8.77056e6) / 65536}
+# spec -> (DRAM bytes read + written per element, elements of the ncu capture)
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16": ((6.258327e9 + 8.77056e6) / 65536, 65536),
+                            "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576)}
 
 
 def parse():
@@ -93,19 +95,23 @@ def parse():
     ap.add_argument("--slots", type=int, default=0,
                     help="force the gate's work split (slots per element) for every call (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
+    ap.add_argument("--elements", type=int, default=0,
+                    help="elements of the exp_small profiling workload (default 65536)")
     ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3],
                     help="DCF input bits per tree level of every gate; 0: the library measures each "
                          "spec at arities 2, 4 and 8 and keeps the fastest for its form")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, elements=0):
     from paper_2606_09551_b300 import inputs as I
     if name == "exp_small":
-        # profiling case: the BERT-layer softmax nExp spec on 65,536 elements (3.4 GB of keys)
+        # profiling case: the BERT-layer softmax nExp spec on 65,536 elements
+        # (6.6 GB of keys at arity 4, 8.8 GB at arity 8), or the first `elements`
+        n = elements or 65536
         c = I.bert_layer()[1]
-        c.x = c.x[:65536]
-        return [c], {"workload": "nexp16_65536", "spec": "nExp-16 k=24 f=12 d=3", "elements": 65536,
+        c.x = c.x[:n]
+        return [c], {"workload": "nexp16_%d" % n, "spec": "nExp-16 k=24 f=12 d=3", "elements": n,
                      "form": "plain"}
     if name == "bert_rescale":
         # the shift gates of one BERT-base layer alone (each matrix product's
@@ -309,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = f"cuda:{local_rank}"
     ctx = F.Context(local_rank)
-    calls, config = workload(args.workload)
+    calls, config = workload(args.workload, args.elements)
     # the DCF arity per spec (resident keys: form 0), then the measured launch
     # shape, before any timing: the library times the gate under every work
     # split (and, with --dcf-bits 0, every arity) on throw-away samples
@@ -590,6 +596,9 @@ def run_ours(args, rank, world, local_rank):
         "aes_microkernel_blocks_per_s": aes_rates,
         "lop3_peak_gops_measured": lop3_rate / 1e9,
         "key_bytes_per_launch": key_bytes_launch,
+        # every key byte over the launch time (an upper bound: a walk reads one
+        # child's correction words of the level's 2^r, and DRAM serves the
+        # sectors that hold them; the measured traffic is below)
         "hbm_gbs_achieved": key_bytes_launch / dom_s / 1e9,
         "traffic": None,
     }
@@ -618,11 +627,14 @@ def run_ours(args, rank, world, local_rank):
     # DRAM traffic of this kernel per element, from an ncu capture of a
     # smaller launch of the same spec, scaled by elements (traffic grows in
     # proportion: one-time keys are read once, outputs written once)
-    per_elem = GATE_DRAM_BYTES_PER_ELEM.get(dom.spec.name)
-    if per_elem is not None:
+    cap = GATE_DRAM_BYTES_PER_ELEM.get(dom.spec.name)
+    if cap is not None:
+        per_elem, cap_n = cap
         roof["traffic"] = per_elem * dom.n
         roof["traffic_basis"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of gate_kernel on %s, "
-                                 "65,536 elements, scaled to %d elements" % (dom.spec.name, dom.n))
+                                 "%d elements, scaled to %d elements" % (dom.spec.name, cap_n, dom.n))
+        roof["hbm_traffic_gbs"] = roof["traffic"] / dom_s / 1e9
+        roof["hbm_traffic_frac_of_measured"] = roof["hbm_traffic_gbs"] / HBM_GBS
 
     res = {
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
@@ -1234,7 +1246,7 @@ def run_reference(args, world):
 
     import oracle as O
     from paper_2606_09551_b300 import inputs as I
-    calls, config = workload(args.workload)
+    calls, config = workload(args.workload, args.elements)
     calls = reference_calls(calls, args)
     threads = os.cpu_count() or 1
     step_s = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))

@@ -1269,12 +1269,14 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
 }
 
 // Predicted time of a plain gate launch of n elements from the spec's tuning
-// record: the least fixed + waves x tile time over the measured splits (a
-// small launch, n <= SMs x 8, is taken as one tile at the finest split).
+// record: the least fixed + waves x tile time over the measured splits.  A
+// small launch (n <= SMs x 8) is taken as one tile at the finest split,
+// without the fixed part: that is the difference of two timings, noisier
+// than the latency gap between arities, and the same for every arity.
 static double predicted_gate_us(const ffss_ctx *ctx, const ffss_spec *spec, uint64_t n) {
   const ffss_tune &t = spec->tune;
   uint32_t tb = 0;
-  if (small_launch(ctx, n, &tb)) return t.fixed_us[t.n_tried - 1] + t.tile_us[t.n_tried - 1];
+  if (small_launch(ctx, n, &tb)) return t.tile_us[t.n_tried - 1];
   double best = -1;
   for (uint32_t i = 0; i < t.n_tried; ++i) {
     const double us = t.fixed_us[i] + gate_waves(ctx, n, t.slots[i]) * t.tile_us[i];
