@@ -64,7 +64,8 @@ AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates mea
             "alternatives": ["t_table_shift_mask", "t_table_permute_mad", "bitsliced_lop3 (not a walk form)"]}
 # spec -> (DRAM bytes read + written per element, elements of the ncu capture)
 GATE_DRAM_BYTES_PER_ELEM = {"nexp16": ((6.258327e9 + 8.77056e6) / 65536, 65536),
-                            "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576)}
+                            "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576),
+                            "nexp16_a8_rec": ((1.458830e9 + 5.251840e6) / 24576, 24576)}
 
 
 def parse():
@@ -97,6 +98,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     ap.add_argument("--elements", type=int, default=0,
                     help="elements of the exp_small profiling workload (default 65536)")
+    ap.add_argument("--records", action="store_true",
+                    help="with --dcf-bits N: lay the lookup keys out as per-child records")
     ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3],
                     help="DCF input bits per tree level of every gate; 0: the library measures each "
                          "spec at arities 2, 4 and 8 and keeps the fastest for its form")
@@ -328,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             tune = cs.autotune()
             tuning[c.name] = dict(tune, elements=c.n, slots_tuned=cs.gate_slots(c.n), tune_s=time.perf_counter() - t0,
-                                  aes_form=AES_FORM, dcf_bits=cs.spec.dcf_bits,
+                                  aes_form=AES_FORM, dcf_bits=cs.spec.dcf_bits, lookup_records=cs.records,
                                   dcf_bits_chosen_by=cs.arity_choice)
     if args.slots:
         ctx.set_slots(args.slots)
@@ -627,7 +630,7 @@ def run_ours(args, rank, world, local_rank):
     # DRAM traffic of this kernel per element, from an ncu capture of a
     # smaller launch of the same spec, scaled by elements (traffic grows in
     # proportion: one-time keys are read once, outputs written once)
-    cap = GATE_DRAM_BYTES_PER_ELEM.get(dom.spec.name)
+    cap = GATE_DRAM_BYTES_PER_ELEM.get(dom.spec.name + ("_rec" if css[dom.name].records else ""))
     if cap is not None:
         per_elem, cap_n = cap
         roof["traffic"] = per_elem * dom.n
@@ -700,7 +703,8 @@ def compile_specs(ctx, calls, args, form, n_of=None):
             cs = F.CompiledSpec(c.spec, ctx, best_for=(n, form))
             cs.arity_choice = "measured, form %d at %d elements" % (form, n)
         else:
-            cs = F.CompiledSpec(c.spec.arity(args.dcf_bits) if args.dcf_bits else c.spec, ctx)
+            cs = F.CompiledSpec(c.spec.arity(args.dcf_bits) if args.dcf_bits else c.spec, ctx,
+                                records=bool(args.dcf_bits and args.records))
             cs.arity_choice = "forced" if args.dcf_bits else "default"
             if not args.no_autotune:
                 cs.autotune()
@@ -1105,6 +1109,7 @@ def run_served(ctx, args, dev):
     st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
     res["dcf_bits"] = {name: cs.spec.dcf_bits for name, cs in css.items()}
+    res["lookup_records"] = {name: cs.records for name, cs in css.items()}
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "offered_requests_per_s": 20.0,
                 "sustainable_requests_per_s": nreq / res["span_s"],
@@ -1157,6 +1162,7 @@ def run_gpt2_batch(ctx, args, dev):
     st, res = _server_result(sv, nreq, clk, wall, _stream_aes([p_[0][0] for p_ in pending], nlay))
     assert st["elements"] == total
     res["dcf_bits"] = {name: cs.spec.dcf_bits for name, cs in css.items()}
+    res["lookup_records"] = {name: cs.records for name, cs in css.items()}
     res.update({"layers_per_request": nlay, "seq_lens": [int(v) for v in lens],
                 "config": "32 GPT-2-small requests (hidden 768, 12 heads, MLP 3072, 2 LayerNorms), "
                           "L uniform [32, 1024], %d of 12 layers each, 64 GB key budget" % nlay})
@@ -1200,6 +1206,7 @@ def run_large_layer(ctx, dev, args, no_serial=False):
     deal, online = _stream_aes([ops], 1)
     return {"value": total / span_s, "unit": "elements/s", "elements": int(total), "layer_ms": st["layer_ms_max"],
             "dcf_bits": {name: cs.spec.dcf_bits for name, cs in css.items()},
+            "lookup_records": {name: cs.records for name, cs in css.items()},
             "online": None if no_serial else _serial_rates(ctx, [([ops], 0.0, call_base)], 1, (deal, online)),
             "aes_blocks": deal + online, "aes_roofline_frac": (deal + online) / span_s / _aes_roofline(),
             "steps": int(st["steps"]), "chunks": int(st["chunks"]), "keys_tb_streamed": key_tb,

@@ -165,6 +165,17 @@ typedef struct {
      * 8 p * 2^r for a lookup key), and the dealer expands 2^r children per
      * level for both parties.  FFSS_ERR_UNSUPPORTED above 3. */
     uint32_t dcf_bits;
+    /* Layout of the lookup keys' correction words (this library's choice; the
+     * outputs do not depend on it).  0: rows, one array per (level, child)
+     * for the seed CWs and one per (level, child, payload word) for the
+     * value CWs, consecutive elements side by side (a warp's loads coalesce
+     * into few lines; DRAM reads most of the other children's words with
+     * them).  1: one record per (level, child, element) holding the seed CW
+     * and the p value CWs, 16 (1 + ceil(p/2)) bytes (DRAM reads little of
+     * the children a walk does not take; each load touches more lines).
+     * Built for payload p = 4 (FFSS_ERR_UNSUPPORTED for another p with a
+     * lookup); FFSS_ERR_INVALID above 1. */
+    uint32_t lookup_records;
 } ffss_spec_desc;
 
 /* Public, mask-independent shape of a compiled gate (Prop. "mask-independent
@@ -188,6 +199,8 @@ typedef struct {
     uint32_t trunc_shift;          /* the shift s, 0 = none */
     uint32_t bx_rounds;            /* exchange rounds of the piecewise outputs' AND gates */
     uint32_t bx_words;             /* packed Boolean AND triples per element */
+    uint32_t dcf_bits;             /* DCF input bits per tree level of the keys */
+    uint32_t lookup_records;       /* lookup-key layout (see ffss_spec_desc) */
 } ffss_shape;
 
 /* ---- context ------------------------------------------------------------ */
@@ -367,12 +380,13 @@ typedef struct {
  * not run concurrently with another host thread's call on the same spec. */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 
-/* Compile `desc` with the DCF arity that measures fastest for calls of n
- * elements (the arity is a protocol parameter: every choice computes the
- * same outputs, Def. "operator specification" in Sec. 4.1 fixes none).  With
- * desc->dcf_bits = 0 the spec is compiled at r = 1, 2 and 3 input bits per
- * tree level and each is tuned with ffss_autotune (same samples and cost);
- * with desc->dcf_bits set only that r is.  The one kept has the least
+/* Compile `desc` with the DCF arity and lookup-key layout that measure
+ * fastest for calls of n elements (both are free choices: every one computes
+ * the same outputs, Def. "operator specification" in Sec. 4.1 fixes none).
+ * With desc->dcf_bits = 0 the spec is compiled at r = 1, 2 and 3 input bits
+ * per tree level, each in both lookup-key layouts (one, when the spec has no
+ * lookup or p != 4), and each is tuned with ffss_autotune (same samples and cost);
+ * with desc->dcf_bits set only that r is (in both layouts).  The one kept has the least
  * predicted time: for form 0 the plain gate launch's (resident keys: the
  * plain and batched forms), for form 1 the gate's plus the dealer's for the
  * same elements (keys dealt as they are used: the served and streamed

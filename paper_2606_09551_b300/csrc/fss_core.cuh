@@ -283,22 +283,40 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t r, uint64_t u, 
 
 // Vector payload (Z_{2^64}^P): adds sum_levels (Conv(v^c) + t VCW[c]) + leaf
 // term into acc (the caller applies the party sign (-1)^b once).
-// vcw: u64 [levels][A][P][n]; leaf: u64 [P][n].
-template <int P, class AES>
+// REC = false (rows): child CW of (level, child) row at root[(1 + row) n],
+// value CWs at vcw[(row P + q) n].  REC = true (records): this element's
+// record of the row at vcw-as-uint4 rec[row (1 + V) n]: the seed CW, then
+// the P value CWs (u64 pairs).  leaf: u64 [P][n].
+template <int P, bool REC, class AES>
 FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, const uint4 *root,
-                                const uint64_t *vcw, const uint64_t *leaf, uint64_t n, uint64_t *acc,
+                                const void *vcw_or_rec, const uint64_t *leaf, uint64_t n, uint64_t *acc,
                                 const AES &aes) {
   constexpr int V = (P + 1) / 2;
   const uint32_t nlev = dcf_levels(k, r), A = 1u << r;
+  const uint64_t rstride = uint64_t(1 + V) * n;
+  const uint4 *rec = static_cast<const uint4 *>(vcw_or_rec);
+  const uint64_t *vcw = static_cast<const uint64_t *>(vcw_or_rec);
   uint4 s = root[0];
   uint32_t t = b, sh = r * (nlev - 1);
   for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
     const uint32_t c = (u >> sh) & (A - 1u);
     const uint64_t row = (uint64_t(i) << r) + c;
-    const uint4 cw = root[(1 + row) * n];
-    uint64_t vc[P];
+    uint4 cw;
+    uint64_t vc[2 * V];
+    if constexpr (REC) {
+      const uint4 *rr = rec + row * rstride;
+      cw = rr[0];
 #pragma unroll
-    for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
+      for (int q = 0; q < V; ++q) {
+        const uint4 w = rr[1 + q];
+        vc[2 * q] = lo64(w);
+        vc[2 * q + 1] = hi64(w);
+      }
+    } else {
+      cw = root[(1 + row) * n];
+#pragma unroll
+      for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
+    }
     const uint4 blk = mmo(s, c, aes);
     uint64_t conv[2 * V];
 #pragma unroll
@@ -421,11 +439,14 @@ FFSS_CORE void conv4(const uint4 *sd, const uint32_t *j0, uint64_t (*out)[P + 1]
 // Vector-payload DCF Gen of arity A = 2^r for beta * 1[u < alpha] on k-bit u
 // (k <= 32), both parties.  keep4(i): the path child's random blocks of
 // level i; block 0 its seed CW, blocks 1..V its value CWs (p little-endian
-// uint64).  Writes root and child CWs (rows 1 + A i + c), value CWs vcw
-// [levels][A][P][n] and the leaf CWs [P][n].
+// uint64).  Writes the roots, the child CWs and value CWs of row A i + c in
+// the spec's layout (rec = 0: CW at l[(1 + row) n], value CWs at
+// vcw[(row P + q) n]; rec = 1: this element's record at vcw-as-uint4
+// [row (1 + V) n], seed CW then the P value CWs, zero padded) and the leaf
+// CWs [P][n].
 template <int P, class AES4, class KEEP4>
-FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t r, uint32_t alpha, const uint64_t *beta, uint4 s0, uint4 s1,
-                           uint4 *l0, uint4 *l1, uint64_t *vcw0, uint64_t *vcw1, uint64_t *leaf0,
+FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t r, uint32_t rec, uint32_t alpha, const uint64_t *beta, uint4 s0,
+                           uint4 s1, uint4 *l0, uint4 *l1, void *vcw_or_rec0, void *vcw_or_rec1, uint64_t *leaf0,
                            uint64_t *leaf1, uint64_t n, const AES4 &aes4, const KEEP4 &keep4) {
   constexpr uint32_t V = (P + 1) / 2;
   l0[0] = s0;
@@ -489,9 +510,9 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t r, uint32_t alpha, const uint64_
         const uint32_t c = cp + h;
         const uint4 c0 = e[h * 2], c1 = e[h * 2 + 1];   // party 0 / party 1 child c
         uint4 cw = make_uint4(0, 0, 0, 0);
-        uint64_t vc[P];
+        uint64_t vc[2 * V];
 #pragma unroll
-        for (int q = 0; q < P; ++q) vc[q] = 0;
+        for (uint32_t q = 0; q < 2 * V; ++q) vc[q] = 0;
         if (c < nc) {
           if (c != a) {
             cw = xor4(c0, c1);
@@ -516,12 +537,27 @@ FFSS_CORE void dcf_vec_gen(uint32_t k, uint32_t r, uint32_t alpha, const uint64_
           }
         }
         const uint64_t row = (uint64_t(i) << r) + c;
-        l0[(1 + row) * n] = cw;
-        l1[(1 + row) * n] = cw;
+        if (rec) {
+          uint4 *r0 = static_cast<uint4 *>(vcw_or_rec0), *r1 = static_cast<uint4 *>(vcw_or_rec1);
+          const uint64_t at = row * (1 + V) * n;
+          r0[at] = cw;
+          r1[at] = cw;
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-          vcw0[(row * P + q) * n] = vc[q];
-          vcw1[(row * P + q) * n] = vc[q];
+          for (uint32_t q = 0; q < V; ++q) {
+            const uint4 w = make_uint4(uint32_t(vc[2 * q]), uint32_t(vc[2 * q] >> 32), uint32_t(vc[2 * q + 1]),
+                                       uint32_t(vc[2 * q + 1] >> 32));
+            r0[at + 1 + q] = w;
+            r1[at + 1 + q] = w;
+          }
+        } else {
+          uint64_t *v0 = static_cast<uint64_t *>(vcw_or_rec0), *v1 = static_cast<uint64_t *>(vcw_or_rec1);
+          l0[(1 + row) * n] = cw;
+          l1[(1 + row) * n] = cw;
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            v0[(row * P + q) * n] = vc[q];
+            v1[(row * P + q) * n] = vc[q];
+          }
         }
       }
     }

@@ -287,7 +287,11 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   S.V = (p + 1) / 2;
   if (d->dcf_bits > 3) return fail(FFSS_ERR_UNSUPPORTED, "dcf_bits=%u outside 1..3", d->dcf_bits);
   S.dcf_r = d->dcf_bits ? d->dcf_bits : 2;
+  if (d->lookup_records > 1) return fail(FFSS_ERR_INVALID, "lookup_records=%u must be 0 or 1", d->lookup_records);
   S.M = d->m == 1 ? 1 : d->m + 1;
+  S.lookup_rec = S.M > 1 ? d->lookup_records : 0;   // no lookup keys: nothing to lay out
+  if (S.lookup_rec && p != 4)
+    return fail(FFSS_ERR_UNSUPPORTED, "lookup_records with payload p=%u (records are built for p = 4)", p);
   if (S.M > 1 && d->k > FFSS_MAX_K_LOOKUP)
     return fail(FFSS_ERR_UNSUPPORTED, "k=%u > %d with an interval lookup (m > 1)", d->k, FFSS_MAX_K_LOOKUP);
   if (d->xhat_basis > 1) return fail(FFSS_ERR_INVALID, "xhat_basis must be 0 or 1");
@@ -484,6 +488,7 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   ffss_shape &sh = sp->shape;
   sh.k = S.k; sh.m = S.m; sh.degree = S.d; sh.n_out = S.r;
   sh.T = S.T; sh.M = S.M; sh.p = S.p; sh.n_mults = S.n_mults; sh.n_bool = S.n_bool + S.n_pw;
+  sh.dcf_bits = S.dcf_r; sh.lookup_records = S.lookup_rec;
   sh.n_piecewise = S.n_pw;
   sh.bx_rounds = S.n_pw ? S.n_bxr : 0;
   sh.bx_words = S.n_bw;
@@ -1294,9 +1299,13 @@ extern "C" int ffss_spec_compile_best(ffss_ctx *ctx, const ffss_spec_desc *desc,
   uint32_t best_r = 0;
   int last_rc = FFSS_OK;
   const uint32_t r0 = desc->dcf_bits ? desc->dcf_bits : 1, r1 = desc->dcf_bits ? desc->dcf_bits : 3;
-  for (uint32_t r = r0; r <= r1; ++r) {
+  // the lookup-key layouts: records exist for p = 4 lookups only
+  const uint32_t layouts = (desc->m > 1 && desc->n_out * (desc->degree + 1) == 4) ? 2 : 1;
+  for (uint32_t v = 0; v < (r1 - r0 + 1) * layouts; ++v) {
+    const uint32_t r = r0 + v / layouts;
     ffss_spec_desc d = *desc;
     d.dcf_bits = r;
+    d.lookup_records = v % layouts;
     ffss_spec *sp = nullptr;
     int rc = ffss_spec_compile(ctx, &d, &sp);
     if (!rc) rc = ffss_autotune(ctx, sp, nullptr, stream);

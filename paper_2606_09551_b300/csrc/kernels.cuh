@@ -159,11 +159,21 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
   const uint32_t k = S.k;
   const char *l = kb + L.off_l[j];
   const uint32_t r = S.dcf_r;
+  const uint32_t u = uint32_t(view(xhat, k, 0));             // lookups: k <= 32
   const uint64_t rows = uint64_t(key_levels(k, r)) << r;    // levels x children
-  const uint4 *root = reinterpret_cast<const uint4 *>(l) + e;
-  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(l + 16ull * (1 + rows) * L.n) + e;
-  const uint64_t *leaf = vcw + rows * P * L.n;
-  dcf_vec_eval_acc<P>(b, k, r, uint32_t(view(xhat, k, 0)), root, vcw, leaf, L.n, acc, aes);   // lookups: k <= 32
+  const uint4 *root = reinterpret_cast<const uint4 *>(l);
+  // records exist for P = 4 only (the layout compile accepts); other
+  // payload lengths keep one walk body, and their kernels' registers
+  if constexpr (P == 4) {
+    if (S.lookup_rec) {                                      // uniform: one spec per tile
+      constexpr uint32_t W = 1 + (P + 1) / 2;                // uint4 words per record
+      const uint64_t *leaf = reinterpret_cast<const uint64_t *>(root + (1 + rows * W) * L.n) + e;
+      dcf_vec_eval_acc<P, true>(b, k, r, u, root + e, root + L.n + e * W, leaf, L.n, acc, aes);
+      return;
+    }
+  }
+  const uint64_t *vcw = reinterpret_cast<const uint64_t *>(root + (1 + rows) * L.n) + e;
+  dcf_vec_eval_acc<P, false>(b, k, r, u, root + e, vcw, vcw + rows * P * L.n, L.n, acc, aes);
 }
 
 // Local mask rewrite (Lemma "masked rewrite for unsigned comparison", App. E):
@@ -894,12 +904,27 @@ __device__ __noinline__ void gen_lookup_key(const KeygenArgs &A, const DevSpec &
   auto keep4 = [&](uint32_t lvl) {   // the 4 blocks of level lvl: H(base, 4 lvl + w)
     return mmo4(base, 4u * lvl, base, 4u * lvl + 1, base, 4u * lvl + 2, base, 4u * lvl + 3, rkd);
   };
-  char *l0 = A.k0 + L.off_l[j - 1], *l1 = A.k1 + L.off_l[j - 1];
+  uint4 *l0 = reinterpret_cast<uint4 *>(A.k0 + L.off_l[j - 1]);
+  uint4 *l1 = reinterpret_cast<uint4 *>(A.k1 + L.off_l[j - 1]);
   const uint64_t rows = uint64_t(key_levels(S.k, S.dcf_r)) << S.dcf_r;    // levels x children
-  uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + 16ull * (1 + rows) * n) + e;
-  uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + 16ull * (1 + rows) * n) + e;
-  dcf_vec_gen<P>(S.k, S.dcf_r, uint32_t(B[j]), beta, s0, s1, reinterpret_cast<uint4 *>(l0) + e,
-                 reinterpret_cast<uint4 *>(l1) + e, v0, v1, v0 + rows * P * n, v1 + rows * P * n, n, rkd, keep4);
+  void *w0, *w1;
+  uint64_t *f0, *f1;
+  if (S.lookup_rec) {
+    constexpr uint32_t W = 1 + (P + 1) / 2;                                   // uint4 words per record
+    w0 = l0 + n + e * W;
+    w1 = l1 + n + e * W;
+    f0 = reinterpret_cast<uint64_t *>(l0 + (1 + rows * W) * n) + e;
+    f1 = reinterpret_cast<uint64_t *>(l1 + (1 + rows * W) * n) + e;
+  } else {
+    uint64_t *v0 = reinterpret_cast<uint64_t *>(l0 + (1 + rows) * n) + e;
+    uint64_t *v1 = reinterpret_cast<uint64_t *>(l1 + (1 + rows) * n) + e;
+    w0 = v0;
+    w1 = v1;
+    f0 = v0 + rows * P * n;
+    f1 = v1 + rows * P * n;
+  }
+  dcf_vec_gen<P>(S.k, S.dcf_r, S.lookup_rec, uint32_t(B[j]), beta, s0, s1, l0 + e, l1 + e, w0, w1, f0, f1, n,
+                 rkd, keep4);
 }
 
 __device__ __noinline__ void gen_query_key(const KeygenArgs &A, const DevSpec &S, const uint32_t *rk_prg, const Tab tb,

@@ -47,6 +47,7 @@ constexpr uint32_t kDrawKeep = 0x100000u;
 struct DevSpec {
   uint32_t k, m, d, r, p, M, T, n_bool, n_prim, V;   // V = ceil(8p / 16) AES blocks of payload
   uint32_t dcf_r;              // DCF input bits per tree level: arity 2^dcf_r (1..3)
+  uint32_t lookup_rec;         // lookup-key layout: 0 rows, 1 per-child records
   uint32_t q_f[kMaxT];         // query view width
   int32_t q_prim[kMaxT];       // -1: the 1[view < r_f] atom; else the predicate it thresholds
   uint64_t q_c[kMaxT];         // query view shift
@@ -107,9 +108,19 @@ struct DevSpec {
 //                    u32  [n] (daBit XOR shares, bits 0 and 1)
 //   query t          uint4 root[n], uint4 cw[L_t][A][n] (per child: seed CW | t CW |
 //                    value CW << 1), u64 leaf[n] (bit 0); L_t = ceil(k_t / r) levels
-//   lookup key j     uint4 root[n], uint4 cw[L][A][n], u64 vcw[L][A][p][n],
-//                    u64 leaf[p][n]; L = ceil(k / r)
-// with r = dcf_r input bits per tree level and A = 2^r children.
+//   lookup key j     rows (lookup_rec = 0): uint4 root[n], uint4 cw[L][A][n],
+//                    u64 vcw[L][A][p][n], u64 leaf[p][n];
+//                    records (lookup_rec = 1): uint4 root[n], rec[L][A][n] of
+//                    1 + V uint4 (the child's seed CW, then its p value CWs as
+//                    u64, zero padded), u64 leaf[p][n]; L = ceil(k / r),
+//                    V = ceil(p / 2)
+// with r = dcf_r input bits per tree level and A = 2^r children.  A walk of a
+// lookup key reads one child's words per level.  In rows a warp's loads
+// coalesce into few lines, but DRAM brings most other children's words
+// along (whole 128-byte lines); in records it reads 16 (1 + V) contiguous
+// bytes, so the lines it touches hold little of the children it does not
+// take, at the price of more lines per warp load (competing with the
+// T-table lookups on the same pipe).  ffss_spec_compile_best measures both.
 struct KeyLayout {
   uint64_t n;
   uint64_t off_r, off_carry, off_vlast, off_trip, off_btrip, off_trunc, off_trunc_rho;
@@ -128,8 +139,11 @@ FFSS_HD uint32_t first_children(uint32_t k, uint32_t r) { return 1u << (k - r * 
 
 // Bytes per element of one comparison key (view width f) and one lookup key.
 FFSS_HD uint64_t query_key_bytes(uint32_t f, uint32_t r) { return 16 + (16ull << r) * key_levels(f, r) + 8; }
-FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p, uint32_t r) {
-  return 16 + (16ull << r) * key_levels(k, r) + (8ull << r) * key_levels(k, r) * p + 8ull * p;
+// uint4 words of one lookup-key record (seed CW + p value CWs).
+FFSS_HD uint32_t lookup_rec_words(uint32_t p) { return 1 + (p + 1) / 2; }
+FFSS_HD uint64_t lookup_key_bytes(uint32_t k, uint32_t p, uint32_t r, uint32_t rec) {
+  const uint64_t per_child = rec ? 16ull * lookup_rec_words(p) : 16ull + 8ull * p;
+  return 16 + (per_child << r) * key_levels(k, r) + 8ull * p;
 }
 
 FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
@@ -150,7 +164,7 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
   }
   for (uint32_t j = 0; j + 1 < s.M; ++j) {
     L.off_l[j] = o;
-    o = align256(o + lookup_key_bytes(s.k, s.p, s.dcf_r) * n);
+    o = align256(o + lookup_key_bytes(s.k, s.p, s.dcf_r, s.lookup_rec) * n);
   }
   L.total = o < 256 ? 256 : o;
   return L;
@@ -160,7 +174,7 @@ FFSS_HD KeyLayout make_layout(const DevSpec &s, uint64_t n) {
 inline uint64_t key_bytes_per_elem(const DevSpec &s) {
   uint64_t b = 8 + 4 + 8ull * s.p + 24ull * s.n_mults + 12ull * s.n_bw + (s.trunc_s ? 28 : 0);
   for (uint32_t t = 0; t < s.T; ++t) b += query_key_bytes(s.q_f[t], s.dcf_r);
-  if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p, s.dcf_r);
+  if (s.M > 1) b += (s.M - 1) * lookup_key_bytes(s.k, s.p, s.dcf_r, s.lookup_rec);
   return b;
 }
 

@@ -51,7 +51,8 @@ class SpecDesc(C.Structure):
                 ("n_piecewise", C.c_uint32), ("piecewise", C.POINTER(PredDesc)),
                 ("trunc_shift", C.c_uint32), ("trunc_signed", C.c_uint32),
                 ("n_bx_nodes", C.c_uint32), ("bx_nodes", C.POINTER(BxNode)),
-                ("piecewise_root", C.POINTER(C.c_uint32)), ("dcf_bits", C.c_uint32)]
+                ("piecewise_root", C.POINTER(C.c_uint32)), ("dcf_bits", C.c_uint32),
+                ("lookup_records", C.c_uint32)]
 
 
 class Shape(C.Structure):
@@ -61,7 +62,8 @@ class Shape(C.Structure):
                 ("key_bytes_per_elem", C.c_uint64), ("comm_bytes_per_elem", C.c_uint64),
                 ("aes_per_elem", C.c_uint64), ("keygen_aes_per_elem", C.c_uint64),
                 ("n_piecewise", C.c_uint32), ("trunc_shift", C.c_uint32),
-                ("bx_rounds", C.c_uint32), ("bx_words", C.c_uint32)]
+                ("bx_rounds", C.c_uint32), ("bx_words", C.c_uint32), ("dcf_bits", C.c_uint32),
+                ("lookup_records", C.c_uint32)]
 
     def asdict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -244,12 +246,14 @@ class CompiledSpec:
     """An operator specification compiled by the library (public shape)."""
 
     def __init__(self, spec: S.OperatorSpec, ctx: Optional[Context] = None, best_for: Optional[tuple] = None,
-                 stream=None):
+                 stream=None, records: bool = False):
         """best_for = (n, form): let the library compile the spec at each DCF
-        arity, tune each and keep the fastest for calls of n elements
-        (ffss_spec_compile_best; form 0: resident keys, 1: keys dealt as they
-        are used); the kept arity is in self.spec.dcf_bits.  Otherwise the
-        spec is compiled at spec.dcf_bits."""
+        arity and lookup-key layout, tune each and keep the fastest for calls
+        of n elements (ffss_spec_compile_best; form 0: resident keys, 1: keys
+        dealt as they are used); the kept arity is in self.spec.dcf_bits and
+        the layout in self.records.  Otherwise the spec is compiled at
+        spec.dcf_bits in the given lookup-key layout (records: one record
+        per child and element instead of rows)."""
         self.spec = spec
         self.ctx = ctx
         alpha = np.ascontiguousarray(np.asarray(spec.alpha, dtype=np.uint64))
@@ -279,7 +283,8 @@ class CompiledSpec:
         d = SpecDesc(spec.k, spec.frac_bits, spec.m, spec.degree, spec.n_out, 1 if spec.partition_bits else 0,
                      alpha.ctypes.data_as(C.POINTER(C.c_uint64)), coeff.ctypes.data_as(C.POINTER(C.c_uint64)),
                      len(spec.preds), preds, 1 if spec.xhat_basis else 0, npw, pw,
-                     spec.trunc_shift, int(spec.trunc_signed), nbx, nodes, roots, spec.dcf_bits)
+                     spec.trunc_shift, int(spec.trunc_signed), nbx, nodes, roots, spec.dcf_bits,
+                     1 if records else 0)
         h = vp()
         if best_for is None:
             _check(lib().ffss_spec_compile(ctx.h if ctx else None, C.byref(d), C.byref(h)))
@@ -293,6 +298,7 @@ class CompiledSpec:
         sh = Shape()
         _check(lib().ffss_spec_shape(self.h, C.byref(sh)))
         self.shape = sh
+        self.records = bool(sh.lookup_records)
 
     def autotune(self, stream=None) -> dict:
         """Measure the fused gate under every work split on throw-away samples

@@ -7,8 +7,10 @@ DCF keys have arity A = 2^r (r input bits per tree level, the spec's
 dcf_r).  Per comparison key of view width f (L = ceil(f/r) levels): root
 uint4[n], child correction words uint4[L][A][n] (seed CW with the t CW in bit
 0 and the value CW in bit 1), the leaf CW u64[n].  Per lookup key (k bits,
-payload p): root, child CWs uint4[L][A][n], value CWs u64[L][A][p][n], leaf
-CWs u64[p][n]."""
+payload p, V = ceil(p/2)), in rows: root uint4[n], child CWs uint4[L][A][n],
+value CWs u64[L][A][p][n], leaf CWs u64[p][n]; in records (the spec's
+lookup_records): root uint4[n], records uint4[L][A][n][1 + V] (the child's
+seed CW, then its p value CWs as u64, zero padded), leaf CWs u64[p][n]."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,7 +26,7 @@ def _lv(f, r):
     return (f + r - 1) // r
 
 
-def offsets(ospec: O.Spec, n: int):
+def offsets(ospec: O.Spec, n: int, records: bool = False):
     """Section offsets for n elements (the library's layout, restated)."""
     o = 0
     off = {}
@@ -46,7 +48,8 @@ def offsets(ospec: O.Spec, n: int):
     for j in range(ospec.M - 1):
         off["l"].append(o)
         lv = _lv(ospec.k, r)
-        o = _a256(o + (16 + 16 * A * lv + 8 * A * lv * ospec.p + 8 * ospec.p) * n)
+        per_child = 16 * (1 + (ospec.p + 1) // 2) if records else 16 + 8 * ospec.p
+        o = _a256(o + (16 + per_child * A * lv + 8 * ospec.p) * n)
     off["total"] = max(o, 256)
     return off
 
@@ -63,25 +66,39 @@ def _blocks(buf, off, count):
     return buf[off: off + 16 * count].reshape(count, 16)
 
 
-def _gpu_key(buf, base, n, e, k, p, r):
+def _gpu_key(buf, base, n, e, k, p, r, records=False):
     lv, A = _lv(k, r), 1 << r
-    blk = _blocks(buf, base, (1 + A * lv) * n)
-    root = blk[e].copy()
-    cw = np.stack([blk[(1 + row) * n + e] for row in range(A * lv)]).reshape(lv, A, 16)
-    tail = base + 16 * (1 + A * lv) * n
+    if p and not records:
+        blk = _blocks(buf, base, (1 + A * lv) * n)
+        root = blk[e].copy()
+        cw = np.stack([blk[(1 + row) * n + e] for row in range(A * lv)]).reshape(lv, A, 16)
+        tail = base + 16 * (1 + A * lv) * n
+        v = _u64(buf, tail, A * lv * p * n)
+        vcw = np.array([[[v[((i * A + c) * p + q) * n + e] for q in range(p)] for c in range(A)]
+                        for i in range(lv)], np.uint64)
+        lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
+        return dict(root=root, cw=cw, vcw=vcw, leaf=np.array([lf[q * n + e] for q in range(p)], np.uint64))
     if p == 0:
+        blk = _blocks(buf, base, (1 + A * lv) * n)
+        root = blk[e].copy()
+        cw = np.stack([blk[(1 + row) * n + e] for row in range(A * lv)]).reshape(lv, A, 16)
+        tail = base + 16 * (1 + A * lv) * n
         return dict(root=root, cw=cw, leaf_bit=int(_u64(buf, tail, n)[e]) & 1)
-    v = _u64(buf, tail, A * lv * p * n)
-    vcw = np.array([[[v[((i * A + c) * p + q) * n + e] for q in range(p)] for c in range(A)] for i in range(lv)],
-                   np.uint64)
-    lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
+    W = 1 + (p + 1) // 2
+    root = _blocks(buf, base, n)[e].copy()
+    rec = _blocks(buf, base + 16 * n, A * lv * n * W)
+    at = [(row * n + e) * W for row in range(A * lv)]
+    cw = np.stack([rec[a] for a in at]).reshape(lv, A, 16)
+    vals = np.stack([rec[a + 1: a + W].reshape(-1).view(np.uint64)[:p] for a in at])
+    vcw = vals.reshape(lv, A, p).astype(np.uint64)
+    lf = _u64(buf, base + 16 * (1 + A * lv * W) * n, p * n)
     leaf = np.array([lf[q * n + e] for q in range(p)], np.uint64)
     return dict(root=root, cw=cw, vcw=vcw, leaf=leaf)
 
 
-def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
+def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int, records: bool = False):
     """Key material of element e in the oracle's field vocabulary."""
-    off = offsets(ospec, n)
+    off = offsets(ospec, n, records)
     p, k, nm = ospec.p, ospec.k, ospec.n_mults
     out = dict(
         r_share=int(_u64(buf, off["r"], n)[e]),
@@ -101,7 +118,7 @@ def gpu_fields(buf: np.ndarray, ospec: O.Spec, n: int, e: int):
                    tr_rho_a=np.array([tt[n + e], tt[2 * n + e]], np.uint64))
     r = ospec.dcf_r
     out["q"] = [_gpu_key(buf, off["q"][t], n, e, f, 0, r) for t, (f, c, pr) in enumerate(ospec.queries())]
-    out["l"] = [_gpu_key(buf, off["l"][j], n, e, k, p, r) for j in range(ospec.M - 1)]
+    out["l"] = [_gpu_key(buf, off["l"][j], n, e, k, p, r, records) for j in range(ospec.M - 1)]
     return out
 
 
@@ -150,9 +167,9 @@ def fields_equal(a, b) -> bool:
     return True
 
 
-def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
+def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int, records: bool = False) -> np.ndarray:
     """Pack oracle key records of n elements into the library's layout."""
-    off = offsets(ospec, n)
+    off = offsets(ospec, n, records)
     buf = np.zeros(off["total"], np.uint8)
     p, k, nm = ospec.p, ospec.k, ospec.n_mults
     r = _u64(buf, off["r"], n)
@@ -188,17 +205,33 @@ def oracle_to_gpu(keys: O.ElemKeys, ospec: O.Spec, n: int) -> np.ndarray:
             _u64(buf, off["q"][t] + 16 * (1 + A * lv) * n, n)[e] = fl["q"][t]["leaf_bit"]
         for j in range(ospec.M - 1):
             lv = _lv(k, r_)
-            blk = _blocks(buf, off["l"][j], (1 + A * lv) * n)
-            blk[e] = fl["l"][j]["root"]
-            for row in range(A * lv):
-                blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // A, row % A]
-            tail = off["l"][j] + 16 * (1 + A * lv) * n
-            v = _u64(buf, tail, A * lv * p * n)
+            if not records:
+                blk = _blocks(buf, off["l"][j], (1 + A * lv) * n)
+                blk[e] = fl["l"][j]["root"]
+                for row in range(A * lv):
+                    blk[(1 + row) * n + e] = fl["l"][j]["cw"][row // A, row % A]
+                tail = off["l"][j] + 16 * (1 + A * lv) * n
+                v = _u64(buf, tail, A * lv * p * n)
+                for i in range(lv):
+                    for c in range(A):
+                        for q in range(p):
+                            v[((i * A + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
+                lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
+                for q in range(p):
+                    lf[q * n + e] = fl["l"][j]["leaf"][q]
+                continue
+            W = 1 + (p + 1) // 2
+            base = off["l"][j]
+            _blocks(buf, base, n)[e] = fl["l"][j]["root"]
+            rec = _blocks(buf, base + 16 * n, A * lv * n * W)
             for i in range(lv):
                 for c in range(A):
-                    for q in range(p):
-                        v[((i * A + c) * p + q) * n + e] = fl["l"][j]["vcw"][i, c, q]
-            lf = _u64(buf, tail + 8 * A * lv * p * n, p * n)
+                    a_ = ((i * A + c) * n + e) * W
+                    rec[a_] = fl["l"][j]["cw"][i, c]
+                    words = np.zeros(2 * (W - 1), np.uint64)
+                    words[:p] = fl["l"][j]["vcw"][i, c, :p]
+                    rec[a_ + 1: a_ + W] = words.view(np.uint8).reshape(W - 1, 16)
+            lf = _u64(buf, base + 16 * (1 + A * lv * W) * n, p * n)
             for q in range(p):
                 lf[q * n + e] = fl["l"][j]["leaf"][q]
     return buf

@@ -77,7 +77,7 @@ def _shape_vs_oracle(sp, may_reject=False):
     lv = lambda f: -(-f // r)          # tree levels: r input bits per level (arity A = 2^r)
     # a comparison key: root, A child CWs per level, the leaf CW word
     kb = 8 + 4 + 8 * o.p + 24 * o.n_mults + 12 * o.n_bw + 28 * tr + sum(16 + 16 * A * lv(f) + 8 for f, _, _ in qs)
-    if o.M > 1:   # a lookup key: root, A child CWs and A x p value CWs per level, p leaf CWs
+    if o.M > 1:   # a lookup key: root, per level A child CWs and A x p value CWs, p leaf CWs (rows layout)
         kb += (o.M - 1) * (16 + 16 * A * lv(o.k) + 8 * A * lv(o.k) * o.p + 8 * o.p)
     assert sh.key_bytes_per_elem == kb
     V = (o.p + 1) // 2

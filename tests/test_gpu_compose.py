@@ -49,18 +49,20 @@ def test_beaver_mul_matches_oracle(ctx, group):
     assert np.array_equal(r0 + r1, (x0 + x1) * np.repeat(y0 + y1, group))
 
 
-def _softmax_gates(ctx):
-    sp = S.softmax_specs()
+def _softmax_gates(ctx, dcf_bits=2):
+    sp = {k: v.arity(dcf_bits) for k, v in S.softmax_specs().items()}
     order = ["relu", "exp", "shift_e", "recip", "shift_t", "shift_p"]
     return ([F.CompiledSpec(sp[k], ctx) for k in order], {k: O.Spec(**sp[k].descriptor()) for k in order})
 
 
-@pytest.mark.parametrize("rows,L", [(3, 1), (5, 7), (4, 16), (12, 128), (2, 300)])
-def test_softmax_matches_oracle(ctx, rows, L):
+@pytest.mark.parametrize("rows,L,dcf_bits", [(3, 1, 2), (5, 7, 2), (4, 16, 2), (12, 128, 2), (2, 300, 2),
+                                             (5, 7, 3), (12, 128, 3)])
+def test_softmax_matches_oracle(ctx, rows, L, dcf_bits):
     """Shares of every output bit-exact to the oracle's composition; bytes
-    equal; the reconstruction equals the plaintext pipeline."""
+    equal; the reconstruction equals the plaintext pipeline (gates with DCF
+    keys of arity 4, and of arity 8 as the benchmark's blocks choose)."""
     import torch
-    gates, og = _softmax_gates(ctx)
+    gates, og = _softmax_gates(ctx, dcf_bits)
     rng = np.random.default_rng(rows * 1000 + L)
     g = 2.0 * rng.standard_normal((rows, L))
     x = S.encode(g.reshape(-1), 12).reshape(rows, L)
@@ -97,10 +99,11 @@ def test_softmax_rejects_non_shift_gates(ctx):
         F.Softmax(ctx, bad, 2, 8)
 
 
-@pytest.mark.parametrize("rows,H", [(3, 1), (4, 5), (16, 768)])
-def test_layernorm_matches_oracle(ctx, rows, H):
+@pytest.mark.parametrize("rows,H,dcf_bits", [(3, 1, 2), (4, 5, 2), (16, 768, 2), (4, 5, 3), (16, 768, 3)])
+def test_layernorm_matches_oracle(ctx, rows, H, dcf_bits):
     import torch
     sp, cH = S.layernorm_specs(H)
+    sp = {k: v.arity(dcf_bits) for k, v in sp.items()}
     order = ["shift_mu", "shift_var", "rsqrt", "shift_r", "shift_y"]
     gates = [F.CompiledSpec(sp[k], ctx) for k in order]
     og = {k: O.Spec(**sp[k].descriptor()) for k in order}

@@ -36,10 +36,12 @@ def ctx():
     return F.Context(0)
 
 
-def _compile(ctx, reqs):
+def _compile(ctx, reqs, records=False):
+    """records: lay out the lookup keys of the p = 4 specs as per-child
+    records (the other specs keep rows: records are built for p = 4)."""
     css = {}
     for op in reqs[0].ops:
-        css[op.name] = F.CompiledSpec(op.spec, ctx)
+        css[op.name] = F.CompiledSpec(op.spec, ctx, records=records and op.spec.p == 4 and op.spec.m > 1)
         css[op.name].autotune()
     return css
 
@@ -193,9 +195,10 @@ def test_single_gelu4_arity8_every_element(ctx):
     _check("gelu4_a8", reqs, _batched(ctx, reqs, css))
 
 
-def test_bert_layer_arity8_every_element_plain_and_batched(ctx):
+@pytest.mark.parametrize("records", [False, True])
+def test_bert_layer_arity8_every_element_plain_and_batched(ctx, records):
     reqs = D.build("bert_layer_a8")
-    css = _compile(ctx, reqs)
+    css = _compile(ctx, reqs, records)
     checked = _check("bert_layer_a8", reqs, _plain(ctx, reqs, css))
     assert sum(checked.values()) == 591488
     _check("bert_layer_a8", reqs, _batched(ctx, reqs, css))

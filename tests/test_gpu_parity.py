@@ -29,10 +29,10 @@ def ospec(sp):
     return O.Spec(**sp.descriptor())
 
 
-def gpu_gate(ctx, sp, x, call_id=0):
+def gpu_gate(ctx, sp, x, call_id=0, records=False):
     """GPU dealer + fused gate for plaintext inputs x (numpy uint64)."""
     import torch
-    cs = F.CompiledSpec(sp, ctx)
+    cs = F.CompiledSpec(sp, ctx, records=records)
     n = x.size
     dev = "cuda:0"
     k0, k1 = F.Keys(cs, n, 0), F.Keys(cs, n, 1)
@@ -160,6 +160,27 @@ def test_gate_even_ranges_bit_exact(ctx, sp, slots, n):
     o = oracle_gate(sp, x, call_id=6)
     for key in ("y0", "y1", "z0", "z1"):
         assert np.array_equal(g[key], o[key]), key
+
+
+REC_SPECS = [s for s in SPECS if s.m > 1 and s.p == 4]
+
+
+@pytest.mark.parametrize("sp", REC_SPECS, ids=[s.name for s in REC_SPECS])
+def test_record_layout_keys_and_gate_bit_exact(ctx, sp):
+    """Lookup keys laid out as one record per (level, child, element): the
+    GPU dealer's key fields equal the oracle dealer's, every share equals the
+    oracle's, at n = 777 and in a small launch (n = 150)."""
+    for n in (777, 150):
+        x = I.uniform_x(n, sp.k, 11)
+        g = gpu_gate(ctx, sp, x, call_id=7, records=True)
+        assert g["cs"].records
+        o = oracle_gate(sp, x, call_id=7)
+        osp = o["ospec"]
+        for e in [0, 1, n // 2, n - 1]:
+            assert fields_equal(gpu_fields(g["keybufs"][0], osp, n, e, True), oracle_fields(o["keys0"], osp, e)), e
+            assert fields_equal(gpu_fields(g["keybufs"][1], osp, n, e, True), oracle_fields(o["keys1"], osp, e)), e
+        for key in ("y0", "y1", "z0", "z1"):
+            assert np.array_equal(g[key], o[key]), key
 
 
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])

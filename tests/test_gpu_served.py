@@ -41,12 +41,14 @@ def _shares(layers):
     return [[tuple(t.cpu().numpy().copy() for t in op[2:]) for op in layer] for layer in layers]
 
 
-def test_alone_equals_mixed_and_plain(ctx):
+@pytest.mark.parametrize("dcf_bits,records", [(2, False), (3, True)])
+def test_alone_equals_mixed_and_plain(ctx, dcf_bits, records):
+    """(also with arity-8 keys whose lookup keys are laid out as records)"""
     import torch
     # GeLU-8 with two piecewise Boolean outputs: their Boolean triples are
     # dealt per chunk too
-    gelu_pw = S.random_piecewise(np.random.default_rng(8), S.gelu8(), 2)
-    css = [F.CompiledSpec(gelu_pw, ctx), F.CompiledSpec(S.nexp16(), ctx)]
+    gelu_pw = S.random_piecewise(np.random.default_rng(8), S.gelu8(), 2).arity(dcf_bits)
+    css = [F.CompiledSpec(gelu_pw, ctx), F.CompiledSpec(S.nexp16().arity(dcf_bits), ctx, records=records)]
     sizes = [[2500, 900], [700, 1300], [4000, 64], [300, 2000]]
     # alone, roomy budget
     sv = F.Server(ctx, 256 << 20, 4, 1 << 20, I.KEY_SEED)
