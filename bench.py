@@ -74,7 +74,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small", "bert_rescale"], default="bert_layer")
+    ap.add_argument("--workload", choices=["bert_layer", "gelu4", "exp_small", "gelu_small", "bert_rescale"],
+                    default="bert_layer")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-served", action="store_true")
@@ -97,12 +98,12 @@ def parse():
                     help="force the gate's work split (slots per element) for every call (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     ap.add_argument("--elements", type=int, default=0,
-                    help="elements of the exp_small profiling workload (default 65536)")
+                    help="elements of the exp_small / gelu_small profiling workloads (default 65536)")
     ap.add_argument("--records", action="store_true",
                     help="with --dcf-bits N: lay the lookup keys out as per-child records")
     ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3],
                     help="DCF input bits per tree level of every gate; 0: the library measures each "
-                         "spec at arities 2, 4 and 8 and keeps the fastest for its form")
+                         "spec at arities 2, 4, 8 and 16 and keeps the fastest for its form")
     return ap.parse_args()
 
 
@@ -116,6 +117,12 @@ def workload(name, elements=0):
         c.x = c.x[:n]
         return [c], {"workload": "nexp16_%d" % n, "spec": "nExp-16 k=24 f=12 d=3", "elements": n,
                      "form": "plain"}
+    if name == "gelu_small":
+        # profiling case: the BERT-layer GeLU-8 spec on the first 65,536 elements (or `elements`)
+        n = elements or 65536
+        c = I.bert_layer()[0]
+        c.x = c.x[:n]
+        return [c], {"workload": "gelu8_%d" % n, "spec": "GeLU-8 k=16 f=12 d=2", "elements": n, "form": "plain"}
     if name == "bert_rescale":
         # the shift gates of one BERT-base layer alone (each matrix product's
         # output shifted right by 12 on a 32-bit signed view)
@@ -518,7 +525,7 @@ def run_ours(args, rank, world, local_rank):
     # x^ (no Beaver rounds, no triples); plain per-operator launches
     xhat = None
     if not args.no_xhat:
-        vcss = {c.name: F.CompiledSpec(c.spec.variant(True), ctx) for c in calls}
+        vcss = {c.name: F.CompiledSpec(c.spec.variant(True), ctx, records=css[c.name].records) for c in calls}
         if not args.no_autotune:
             for cs in vcss.values():
                 cs.autotune()
@@ -690,7 +697,7 @@ def _stream_aes(pending_ops, nlay):
 
 def compile_specs(ctx, calls, args, form, n_of=None):
     """One compiled spec per call.  With --dcf-bits 0 (and tuning on) the
-    library compiles each at DCF arities 2, 4 and 8, tunes each and keeps the
+    library compiles each at DCF arities 2, 4, 8 and 16, tunes each and keeps the
     one with the least predicted time for the call's size (form 0: resident
     keys; form 1: keys dealt as they are used, so the dealer's time counts);
     every call's spec is replaced by the kept one.  Otherwise the given (or

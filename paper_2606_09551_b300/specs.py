@@ -80,7 +80,7 @@ class OperatorSpec:
     # shift of its k-bit two's-complement value when trunc_signed (0 = none)
     trunc_shift: int = 0
     trunc_signed: bool = False
-    # DCF input bits per tree level of the gate's keys (arity 2^dcf_bits, 1..3):
+    # DCF input bits per tree level of the gate's keys (arity 2^dcf_bits, 1..4):
     # a protocol parameter, not part of the function; fewer levels mean fewer
     # online AES blocks but larger keys and more dealer work
     dcf_bits: int = 2
@@ -118,7 +118,8 @@ class OperatorSpec:
         import dataclasses
         if dcf_bits == self.dcf_bits:
             return self
-        base = self.name[:-3] if self.name[-3:-1] == "_a" else self.name
+        import re
+        base = re.sub(r"_a\d+$", "", self.name)
         return dataclasses.replace(self, dcf_bits=dcf_bits,
                                    name=base + ("" if dcf_bits == 2 else f"_a{1 << dcf_bits}"))
 

@@ -3,7 +3,7 @@
 Every workload runs on the GPU at its full size, in the form the benchmark
 times: the single GeLU-4 operator and the BERT-base layer as plain
 per-operator launches (and once more as one batched launch), with DCF keys
-of arity 4 and of arity 8 (the plain form's measured choice), the
+of arity 4, 8 and 16 (the plain form measures 8 and 16 fastest), the
 GPT-2 batch, the BERT-large trace and the 2.7B-scale layer through the
 continuous-batching server with on-device key streaming (64 GB pool, 4 M
 element chunks), all with autotuned work splits.  The GPU shares of every
@@ -202,6 +202,28 @@ def test_bert_layer_arity8_every_element_plain_and_batched(ctx, records):
     checked = _check("bert_layer_a8", reqs, _plain(ctx, reqs, css))
     assert sum(checked.values()) == 591488
     _check("bert_layer_a8", reqs, _batched(ctx, reqs, css))
+
+
+def test_single_gelu4_arity16_every_element(ctx):
+    """Arity 16 (four input bits per level), the plain form's measured
+    choice for GeLU-4 on this GPU: plain and batched, every element."""
+    reqs = D.build("gelu4_a16")
+    css = _compile(ctx, reqs)
+    assert all(cs.spec.dcf_bits == 4 for cs in css.values())
+    checked = _check("gelu4_a16", reqs, _plain(ctx, reqs, css))
+    assert checked["gelu4"] == 65536
+    _check("gelu4_a16", reqs, _batched(ctx, reqs, css))
+
+
+@pytest.mark.parametrize("records", [False, True])
+def test_bert_layer_arity16_every_element_plain_and_batched(ctx, records):
+    """Arity 16, lookup keys of the p = 4 operators in rows and in records
+    (the bench's choice for nExp, Recip and Rsqrt): every element."""
+    reqs = D.build("bert_layer_a16")
+    css = _compile(ctx, reqs, records)
+    checked = _check("bert_layer_a16", reqs, _plain(ctx, reqs, css))
+    assert sum(checked.values()) == 591488
+    _check("bert_layer_a16", reqs, _batched(ctx, reqs, css))
 
 
 def test_gpt2_batch_streamed(ctx):
