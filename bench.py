@@ -65,7 +65,8 @@ AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates mea
 # spec -> (DRAM bytes read + written per element, elements of the ncu capture)
 GATE_DRAM_BYTES_PER_ELEM = {"nexp16": ((6.258327e9 + 8.77056e6) / 65536, 65536),
                             "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576),
-                            "nexp16_a8_rec": ((1.458830e9 + 5.251840e6) / 24576, 24576)}
+                            "nexp16_a8_rec": ((1.458830e9 + 5.251840e6) / 24576, 24576),
+                            "nexp16_a16_rec": ((835.614208e6 + 4.251136e6) / 16384, 16384)}
 
 
 def parse():
@@ -101,7 +102,7 @@ def parse():
                     help="elements of the exp_small / gelu_small profiling workloads (default 65536)")
     ap.add_argument("--records", action="store_true",
                     help="with --dcf-bits N: lay the lookup keys out as per-child records")
-    ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="DCF input bits per tree level of every gate; 0: the library measures each "
                          "spec at arities 2, 4, 8 and 16 and keeps the fastest for its form")
     return ap.parse_args()
@@ -1228,10 +1229,10 @@ def run_large_layer(ctx, dev, args, no_serial=False):
 # ---------------------------------------------------------------------------
 
 # The DCF arity the reference arm's oracle runs for the plain form (resident
-# keys): the one the layer's gates measure fastest at on this GPU (arity 8
-# for GeLU-8, nExp and Rsqrt; the measured choice per spec is in the GPU
-# arm's autotune record).  The reference arm has no GPU to measure with.
-PLAIN_DCF_BITS = 3
+# keys): the one the layer's gates measure fastest at on this GPU (arity 16
+# for all four operators; the measured choice per spec is in the GPU arm's
+# autotune record).  The reference arm has no GPU to measure with.
+PLAIN_DCF_BITS = 4
 
 
 def reference_calls(calls, args):

@@ -173,8 +173,8 @@ typedef struct {
      * them).  1: one record per (level, child, element) holding the seed CW
      * and the p value CWs, 16 (1 + ceil(p/2)) bytes (DRAM reads little of
      * the children a walk does not take; each load touches more lines).
-     * Built for payload p = 4 (FFSS_ERR_UNSUPPORTED for another p with a
-     * lookup); FFSS_ERR_INVALID above 1. */
+     * Built for payloads p = 3 and 4 (FFSS_ERR_UNSUPPORTED for another p
+     * with a lookup); FFSS_ERR_INVALID above 1. */
     uint32_t lookup_records;
 } ffss_spec_desc;
 
@@ -385,7 +385,7 @@ int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
  * the same outputs, Def. "operator specification" in Sec. 4.1 fixes none).
  * With desc->dcf_bits = 0 the spec is compiled at r = 1, 2, 3 and 4 input bits
  * per tree level, each in both lookup-key layouts (one, when the spec has no
- * lookup or p != 4), and each is tuned with ffss_autotune (same samples and cost);
+ * lookup or p is not 3 or 4), and each is tuned with ffss_autotune (same samples and cost);
  * with desc->dcf_bits set only that r is (in both layouts).  The one kept has the least
  * predicted time: for form 0 the plain gate launch's (resident keys: the
  * plain and batched forms), for form 1 the gate's plus the dealer's for the

@@ -290,8 +290,8 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   if (d->lookup_records > 1) return fail(FFSS_ERR_INVALID, "lookup_records=%u must be 0 or 1", d->lookup_records);
   S.M = d->m == 1 ? 1 : d->m + 1;
   S.lookup_rec = S.M > 1 ? d->lookup_records : 0;   // no lookup keys: nothing to lay out
-  if (S.lookup_rec && p != 4)
-    return fail(FFSS_ERR_UNSUPPORTED, "lookup_records with payload p=%u (records are built for p = 4)", p);
+  if (S.lookup_rec && p != 3 && p != 4)
+    return fail(FFSS_ERR_UNSUPPORTED, "lookup_records with payload p=%u (records are built for p = 3, 4)", p);
   if (S.M > 1 && d->k > FFSS_MAX_K_LOOKUP)
     return fail(FFSS_ERR_UNSUPPORTED, "k=%u > %d with an interval lookup (m > 1)", d->k, FFSS_MAX_K_LOOKUP);
   if (d->xhat_basis > 1) return fail(FFSS_ERR_INVALID, "xhat_basis must be 0 or 1");
@@ -1299,8 +1299,9 @@ extern "C" int ffss_spec_compile_best(ffss_ctx *ctx, const ffss_spec_desc *desc,
   uint32_t best_r = 0;
   int last_rc = FFSS_OK;
   const uint32_t r0 = desc->dcf_bits ? desc->dcf_bits : 1, r1 = desc->dcf_bits ? desc->dcf_bits : 4;
-  // the lookup-key layouts: records exist for p = 4 lookups only
-  const uint32_t layouts = (desc->m > 1 && desc->n_out * (desc->degree + 1) == 4) ? 2 : 1;
+  // the lookup-key layouts: records exist for p = 3 and 4 lookups only
+  const uint32_t pp = desc->n_out * (desc->degree + 1);
+  const uint32_t layouts = (desc->m > 1 && (pp == 3 || pp == 4)) ? 2 : 1;
   for (uint32_t v = 0; v < (r1 - r0 + 1) * layouts; ++v) {
     const uint32_t r = r0 + v / layouts;
     ffss_spec_desc d = *desc;

@@ -162,9 +162,9 @@ __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const Key
   const uint32_t u = uint32_t(view(xhat, k, 0));             // lookups: k <= 32
   const uint64_t rows = uint64_t(key_levels(k, r)) << r;    // levels x children
   const uint4 *root = reinterpret_cast<const uint4 *>(l);
-  // records exist for P = 4 only (the layout compile accepts); other
-  // payload lengths keep one walk body, and their kernels' registers
-  if constexpr (P == 4) {
+  // records exist for P = 3 and 4 only (the layouts the compile accepts);
+  // other payload lengths keep one walk body, and their kernels' registers
+  if constexpr (P == 3 || P == 4) {
     if (S.lookup_rec) {                                      // uniform: one spec per tile
       constexpr uint32_t W = 1 + (P + 1) / 2;                // uint4 words per record
       const uint64_t *leaf = reinterpret_cast<const uint64_t *>(root + (1 + rows * W) * L.n) + e;

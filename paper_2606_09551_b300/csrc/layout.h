@@ -115,7 +115,7 @@ struct DevSpec {
 //                    u64, zero padded), u64 leaf[p][n]; L = ceil(k / r),
 //                    V = ceil(p / 2)
 // with r = dcf_r input bits per tree level and A = 2^r children.  A walk of a
-// lookup key reads one child's words per level.  In rows a warp's loads
+// lookup key reads one child's words per level (records: p = 3 and 4).  In rows a warp's loads
 // coalesce into few lines, but DRAM brings most other children's words
 // along (whole 128-byte lines); in records it reads 16 (1 + V) contiguous
 // bytes, so the lines it touches hold little of the children it does not

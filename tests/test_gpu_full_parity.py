@@ -37,11 +37,11 @@ def ctx():
 
 
 def _compile(ctx, reqs, records=False):
-    """records: lay out the lookup keys of the p = 4 specs as per-child
-    records (the other specs keep rows: records are built for p = 4)."""
+    """records: lay out the lookup keys of the p = 3, 4 specs as per-child
+    records (the others keep rows: records are built for p = 3, 4)."""
     css = {}
     for op in reqs[0].ops:
-        css[op.name] = F.CompiledSpec(op.spec, ctx, records=records and op.spec.p == 4 and op.spec.m > 1)
+        css[op.name] = F.CompiledSpec(op.spec, ctx, records=records and op.spec.p in (3, 4) and op.spec.m > 1)
         css[op.name].autotune()
     return css
 
@@ -204,11 +204,13 @@ def test_bert_layer_arity8_every_element_plain_and_batched(ctx, records):
     _check("bert_layer_a8", reqs, _batched(ctx, reqs, css))
 
 
-def test_single_gelu4_arity16_every_element(ctx):
+@pytest.mark.parametrize("records", [False, True])
+def test_single_gelu4_arity16_every_element(ctx, records):
     """Arity 16 (four input bits per level), the plain form's measured
-    choice for GeLU-4 on this GPU: plain and batched, every element."""
+    choice for GeLU-4 on this GPU, lookup keys in rows and in records:
+    plain and batched, every element."""
     reqs = D.build("gelu4_a16")
-    css = _compile(ctx, reqs)
+    css = _compile(ctx, reqs, records)
     assert all(cs.spec.dcf_bits == 4 for cs in css.values())
     checked = _check("gelu4_a16", reqs, _plain(ctx, reqs, css))
     assert checked["gelu4"] == 65536
@@ -217,8 +219,8 @@ def test_single_gelu4_arity16_every_element(ctx):
 
 @pytest.mark.parametrize("records", [False, True])
 def test_bert_layer_arity16_every_element_plain_and_batched(ctx, records):
-    """Arity 16, lookup keys of the p = 4 operators in rows and in records
-    (the bench's choice for nExp, Recip and Rsqrt): every element."""
+    """Arity 16, lookup keys in rows and in records (records for p = 3
+    and 4: all four operators): every element."""
     reqs = D.build("bert_layer_a16")
     css = _compile(ctx, reqs, records)
     checked = _check("bert_layer_a16", reqs, _plain(ctx, reqs, css))

@@ -164,7 +164,7 @@ def test_gate_even_ranges_bit_exact(ctx, sp, slots, n):
         assert np.array_equal(g[key], o[key]), key
 
 
-REC_SPECS = [s for s in SPECS if s.m > 1 and s.p == 4]
+REC_SPECS = [s for s in SPECS if s.m > 1 and s.p in (3, 4)]
 
 
 @pytest.mark.parametrize("sp", REC_SPECS, ids=[s.name for s in REC_SPECS])

@@ -25,8 +25,8 @@ def test_layout_round_trip_and_size(sp, dcf_bits, records):
     x = I.uniform_x(n, sp.k, 3)
     k0, _, _, _ = O.dealer(osp, I.KEY_SEED, 9, 0, n, x)
     buf = oracle_to_gpu(k0, osp, n, records)
-    if records and osp.M > 1 and osp.p != 4:
-        with pytest.raises(F.FfssError):        # records are built for p = 4 lookups
+    if records and osp.M > 1 and osp.p not in (3, 4):
+        with pytest.raises(F.FfssError):        # records are built for p = 3, 4 lookups
             F.CompiledSpec(sp, records=True)
         return
     cs = F.CompiledSpec(sp, records=records)
