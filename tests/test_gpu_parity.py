@@ -98,12 +98,13 @@ def _specs():
                            preds=[S.PredDesc(50, 0, 1 << 49, 1), S.PredDesc(50, 12345, (1 << 49) + 77, 0),
                                   S.PredDesc(37, 999, 5 << 30, 1)])]
     # DCF keys of arity 8 (three input bits per level; one- and two-bit first
-    # digits at k = 16, 20, 32), arity 2 (one bit per level) and arity 16
-    # (four bits; a three-bit first digit at k = 63)
+    # digits at k = 16, 20, 32), arity 2 (one bit per level), arity 16
+    # (four bits; a three-bit first digit at k = 63) and arity 32
     arity = [S.gelu4().arity(3), out[4].arity(3), S.nexp16().arity(3), pw[1].arity(3), bx[2].arity(3),
              out[8].arity(3), tr[0].arity(3), wide[0].arity(3), wide[3].arity(3), S.gelu8().variant(True).arity(3),
              out[3].arity(1), tr[1].arity(1), S.relu(5).arity(1),
-             S.gelu4().arity(4), S.nexp16().arity(4), pw[1].arity(4), tr[0].arity(4), wide[0].arity(4)]
+             S.gelu4().arity(4), S.nexp16().arity(4), pw[1].arity(4), tr[0].arity(4), wide[0].arity(4),
+             S.nexp16().arity(5), S.gelu4().arity(5), tr[0].arity(5), wide[3].arity(5)]
     return out + pw + bx + tr + wide + arity
 
 

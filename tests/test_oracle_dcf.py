@@ -1,7 +1,7 @@
 """Pins for the oracle's DCF (a generalisation of Boyle et al., EUROCRYPT
 2021, to arity 2^r: r input bits per tree level) by brute force:
 Eval_0 (+) Eval_1 = beta * 1[u < alpha] for every alpha and every u at small
-k, for r = 1, 2, 3 and 4 (every arity the gates take), including k not a
+k, for r = 1 to 5 (every arity the gates take), including k not a
 multiple of r."""
 import numpy as np
 import pytest
@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_bit_dcf_all_alpha_all_u(k, r):
     rng = np.random.default_rng(100 + k + 10 * r)
@@ -28,7 +28,7 @@ def test_bit_dcf_k10_sampled_alpha_all_u():
             assert O.dcf_eval(0, a, u, 0) ^ O.dcf_eval(1, b, u, 0) == (1 if u < alpha else 0)
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("k,p", [(1, 1), (3, 2), (5, 3), (5, 4), (6, 1)])
 def test_vector_dcf_all_alpha_all_u(k, p, r):
     rng = np.random.default_rng(200 + 10 * k + p + 100 * r)
