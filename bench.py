@@ -530,9 +530,12 @@ def run_ours(args, rank, world, local_rank):
         if not args.no_autotune:
             for cs in vcss.values():
                 cs.autotune()
-        vsets = []
-        nx = sets_that_fit(sum(2 * vcss[c.name].key_bytes(c.n) for c in calls), args.steps + 1) - 1
-        for s_ in range(nx + 1):
+        # as many timed key sets as fit beside one warm-up set; when only one
+        # set fits, the warm-up set is dealt again (untimed) and timed once
+        nfit = sets_that_fit(sum(2 * vcss[c.name].key_bytes(c.n) for c in calls), args.steps + 1)
+        nx = max(1, nfit - 1)
+
+        def vdeal(s_):
             ks = {}
             for c in calls:
                 x0 = torch.empty(c.n, dtype=torch.uint64, device=dev)
@@ -540,14 +543,23 @@ def run_ours(args, rank, world, local_rank):
                 k0, k1 = F.Keys(vcss[c.name], c.n, 0), F.Keys(vcss[c.name], c.n, 1)
                 F.keygen(ctx, vcss[c.name], I.KEY_SEED, c.call_id + 16 * (400 + s_), c.n, k0, k1, xp[c.name], x0, x1)
                 ks[c.name] = (k0, k1, x0, x1)
-            vsets.append(ks)
+            return ks
+
         vcomm = torch.zeros(2, dtype=torch.uint64, device=dev)
 
         def vstep(ks, cm=None):
             for c in calls:
                 F.eval_pair(ctx, vcss[c.name], *ks[c.name], *outs[c.name], cm)
 
-        vstep(vsets[-1])                      # warm-up
+        if nfit >= 2:
+            vsets = [vdeal(s_) for s_ in range(nx + 1)]
+            vstep(vsets[-1])                  # warm-up
+        else:
+            vsets = [vdeal(nx)]
+            vstep(vsets[0])                   # warm-up
+            del vsets
+            torch.cuda.empty_cache()
+            vsets = [vdeal(0)]
         torch.cuda.synchronize()
         barrier(world)
         v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
