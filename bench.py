@@ -1241,10 +1241,11 @@ def run_large_layer(ctx, dev, args, no_serial=False):
 # ---------------------------------------------------------------------------
 
 # The DCF arity the reference arm's oracle runs for the plain form (resident
-# keys): the one the layer's gates measure fastest at on this GPU (arity 16
-# for all four operators; the measured choice per spec is in the GPU arm's
-# autotune record).  The reference arm has no GPU to measure with.
-PLAIN_DCF_BITS = 4
+# keys): the one the layer's gates measure fastest at on this GPU (arity 32
+# for all four operators, lookup keys in records; the measured choice per
+# spec is in the GPU arm's autotune record).  The reference arm has no GPU
+# to measure with.
+PLAIN_DCF_BITS = 5
 
 
 def reference_calls(calls, args):
@@ -1257,7 +1258,8 @@ def full_config(config, calls, world, args):
     """The workload's config as both arms print it: the workload, how L2 is
     kept out of the measurement, and the process layout."""
     from paper_2606_09551_b300 import fusefss as F
-    key_gb = sum(2 * F.CompiledSpec(c.spec).shape.key_bytes_per_elem * c.n for c in reference_calls(calls, args)) / 1e9
+    key_gb = sum(2 * F.CompiledSpec(c.spec, records=c.spec.m > 1 and c.spec.p in (3, 4)).shape.key_bytes_per_elem * c.n
+                 for c in reference_calls(calls, args)) / 1e9
     return dict(config, l2="inputs > L2: every step reads %.1f GB of fresh one-time keys" % key_gb,
                 parallelism="replicas x %d" % world if world > 1 else "one process; both parties in it")
 
