@@ -66,7 +66,8 @@ AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates mea
 GATE_DRAM_BYTES_PER_ELEM = {"nexp16": ((6.258327e9 + 8.77056e6) / 65536, 65536),
                             "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576),
                             "nexp16_a8_rec": ((1.458830e9 + 5.251840e6) / 24576, 24576),
-                            "nexp16_a16_rec": ((835.614208e6 + 4.251136e6) / 16384, 16384)}
+                            "nexp16_a16_rec": ((835.614208e6 + 4.251136e6) / 16384, 16384),
+                            "nexp16_a32_rec": ((370.123264e6 + 3.480832e6) / 8192, 8192)}
 
 
 def parse():
