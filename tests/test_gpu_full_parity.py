@@ -228,6 +228,31 @@ def test_bert_layer_arity16_every_element_plain_and_batched(ctx, records):
     _check("bert_layer_a16", reqs, _batched(ctx, reqs, css))
 
 
+@pytest.mark.parametrize("records", [False, True])
+def test_single_gelu4_arity32_every_element(ctx, records):
+    """Arity 32 (five input bits per level; the first of GeLU-4's two
+    levels takes one bit), the layout the plain form picks for it:
+    plain and batched, every element."""
+    reqs = D.build("gelu4_a32")
+    css = _compile(ctx, reqs, records)
+    assert all(cs.spec.dcf_bits == 5 for cs in css.values())
+    checked = _check("gelu4_a32", reqs, _plain(ctx, reqs, css))
+    assert checked["gelu4"] == 65536
+    _check("gelu4_a32", reqs, _batched(ctx, reqs, css))
+
+
+@pytest.mark.parametrize("records", [False, True])
+def test_bert_layer_arity32_every_element_plain_and_batched(ctx, records):
+    """Arity 32 in both lookup-key layouts (records: the keys the bench's
+    BERT-base layer runs on): every element, plain and batched."""
+    reqs = D.build("bert_layer_a32")
+    css = _compile(ctx, reqs, records)
+    assert all(cs.spec.dcf_bits == 5 for cs in css.values())
+    checked = _check("bert_layer_a32", reqs, _plain(ctx, reqs, css))
+    assert sum(checked.values()) == 591488
+    _check("bert_layer_a32", reqs, _batched(ctx, reqs, css))
+
+
 def test_gpt2_batch_streamed(ctx):
     reqs = D.build("gpt2_batch")
     css = _compile(ctx, reqs)
