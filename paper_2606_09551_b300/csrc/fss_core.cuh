@@ -256,6 +256,18 @@ FFSS_CORE uint64_t view(uint64_t u, uint32_t f, uint64_t c) {
 
 FFSS_CORE uint32_t dcf_levels(uint32_t k, uint32_t r) { return (k + r - 1) / r; }
 
+// Brings the 128-byte line holding p into L2 ahead of its load.  A walk's
+// child digits are digits of the public input, so the correction word the
+// next level reads is known before this level's AES ends: fetching its line
+// early holds no register and leaves the load an L2 hit.
+FFSS_CORE void prefetch_l2(const void *p) {
+#ifdef __CUDA_ARCH__
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+#else
+  (void)p;
+#endif
+}
+
 // Bit payload: returns the XOR share of 1[u < alpha].
 // root: uint4 root[n]; child CW of level i at root[(1 + A i + c) n]; leaf: the leaf CW bit.
 template <class AES>
@@ -266,6 +278,7 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t r, uint64_t u, 
   uint32_t t = b, v = 0, sh = r * (nlev - 1);
   for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
     const uint32_t c = uint32_t(u >> sh) & dmask;
+    if (i + 1 < nlev) prefetch_l2(root + (1 + (uint64_t(i + 1) << r) + (uint32_t(u >> (sh - r)) & dmask)) * n);
     const uint4 cw = root[(1 + (uint64_t(i) << r) + c) * n];
     const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
@@ -301,6 +314,20 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, 
   for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
     const uint32_t c = (u >> sh) & (A - 1u);
     const uint64_t row = (uint64_t(i) << r) + c;
+    if (i + 1 < nlev) {
+      const uint64_t rn = (uint64_t(i + 1) << r) + ((u >> (sh - r)) & (A - 1u));
+      if constexpr (REC) {
+        prefetch_l2(rec + rn * rstride);          // the record's first and last words
+        prefetch_l2(rec + rn * rstride + V);
+      } else {
+        prefetch_l2(root + (1 + rn) * n);
+#pragma unroll
+        for (int q = 0; q < P; ++q) prefetch_l2(vcw + (rn * P + q) * n);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) prefetch_l2(leaf + uint64_t(q) * n);
+    }
     uint4 cw;
     uint64_t vc[2 * V];
     if constexpr (REC) {

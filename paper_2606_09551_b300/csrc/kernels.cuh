@@ -151,6 +151,39 @@ __device__ __forceinline__ uint32_t bit_item(uint32_t b, const DevSpec &S, const
   return bit_walk(b, f, r, view(xhat, f, S.q_c[t]), root, L.n, leaf, aes.tb.base, aes.tb.lane4);
 }
 
+// Prefetch (into L2) of the first loads of a slot's next walk, item it of
+// the spec's items (comparison queries first, then the boundary lookups):
+// its root seed, its level-0 correction words and, for a comparison, its
+// leaf word.  Issued while the current walk runs.
+__device__ __forceinline__ void walk_prefetch(const DevSpec &S, const KeyLayout &L, const char *kb, uint64_t e,
+                                              uint64_t xhat, uint32_t item) {
+  const uint32_t r = S.dcf_r, dmask = (1u << r) - 1u;
+  if (item < S.T) {
+    const uint32_t f = S.q_f[item], nlev = key_levels(f, r);
+    const char *q = kb + L.off_q[item];
+    const uint4 *root = reinterpret_cast<const uint4 *>(q) + e;
+    const uint32_t c = uint32_t(view(xhat, f, S.q_c[item]) >> (r * (nlev - 1))) & dmask;
+    prefetch_l2(root);
+    prefetch_l2(root + (1 + c) * L.n);
+    prefetch_l2(reinterpret_cast<const uint64_t *>(q + 16ull * (1 + (uint64_t(nlev) << r)) * L.n) + e);
+    return;
+  }
+  const uint32_t j = item - S.T, k = S.k, nlev = key_levels(k, r);
+  const uint4 *root = reinterpret_cast<const uint4 *>(kb + L.off_l[j]);
+  const uint32_t c = (uint32_t(view(xhat, k, 0)) >> (r * (nlev - 1))) & dmask;
+  prefetch_l2(root + e);
+  if (S.lookup_rec) {
+    const uint32_t W = 1 + (S.p + 1) / 2;
+    const uint4 *rec = root + L.n + (uint64_t(c) * L.n + e) * W;
+    prefetch_l2(rec);
+    prefetch_l2(rec + W - 1);
+  } else {
+    prefetch_l2(root + (1 + c) * L.n + e);
+    const uint64_t *vcw = reinterpret_cast<const uint64_t *>(root + (1 + (uint64_t(nlev) << r)) * L.n) + e;
+    for (uint32_t q = 0; q < S.p; ++q) prefetch_l2(vcw + (uint64_t(c) * S.p + q) * L.n);
+  }
+}
+
 // One boundary DCF j of the telescoped lookup, added into acc (unsigned sum).
 template <int P>
 __device__ __forceinline__ void vec_item(uint32_t b, const DevSpec &S, const KeyLayout &L, const char *kb,
@@ -543,11 +576,16 @@ __device__ __forceinline__ void gate_tile(const GateArgs &A, const Sched &SC, co
   if (valid) {
     // a slot's items are sorted: comparison keys (< T) first, then lookup keys
     uint32_t it = it0;
+    if (it < it1) walk_prefetch(S, L, kb, e, xhat, SC.item[it]);
     for (; it < it1 && SC.item[it] < S.T; ++it) {
       const uint32_t t = SC.item[it];
+      if (it + 1 < it1) walk_prefetch(S, L, kb, e, xhat, SC.item[it + 1]);
       atoms |= bit_item(b, S, L, kb, e, xhat, t, aes) << t;
     }
-    for (; it < it1; ++it) vec_item<P>(b, S, L, kb, e, xhat, SC.item[it] - S.T, acc, aes);
+    for (; it < it1; ++it) {
+      if (it + 1 < it1) walk_prefetch(S, L, kb, e, xhat, SC.item[it + 1]);
+      vec_item<P>(b, S, L, kb, e, xhat, SC.item[it] - S.T, acc, aes);
+    }
   }
   const uint64_t r_b = lead ? box[b * E + le].y : 0;
   const uint32_t ri = (b * NS + slot) * E + le;
