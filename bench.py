@@ -103,9 +103,9 @@ def parse():
                     help="elements of the exp_small / gelu_small profiling workloads (default 65536)")
     ap.add_argument("--records", action="store_true",
                     help="with --dcf-bits N: lay the lookup keys out as per-child records")
-    ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="DCF input bits per tree level of every gate; 0: the library measures each "
-                         "spec at arities 2 to 32 and keeps the fastest for its form")
+                         "spec at arities 2 to 64 and keeps the fastest for its form")
     return ap.parse_args()
 
 
@@ -711,7 +711,7 @@ def _stream_aes(pending_ops, nlay):
 
 def compile_specs(ctx, calls, args, form, n_of=None):
     """One compiled spec per call.  With --dcf-bits 0 (and tuning on) the
-    library compiles each at DCF arities 2 to 32, tunes each and keeps the
+    library compiles each at DCF arities 2 to 64, tunes each and keeps the
     one with the least predicted time for the call's size (form 0: resident
     keys; form 1: keys dealt as they are used, so the dealer's time counts);
     every call's spec is replaced by the kept one.  Otherwise the given (or

@@ -159,11 +159,11 @@ typedef struct {
     const ffss_bx_node *bx_nodes;
     const uint32_t *piecewise_root;      /* m * n_piecewise node indices */
     /* DCF input bits per tree level r of the gate's keys (arity 2^r): 1 to
-     * 5; 0 means 2.  A protocol parameter, not part of the function: the
+     * 6; 0 means 2.  A protocol parameter, not part of the function: the
      * outputs are the same for every r.  A walk costs ceil(k / r) AES blocks
      * (times 1 + V for a lookup key), a key 16 * 2^r bytes per level (plus
      * 8 p * 2^r for a lookup key), and the dealer expands 2^r children per
-     * level for both parties.  FFSS_ERR_UNSUPPORTED above 5. */
+     * level for both parties.  FFSS_ERR_UNSUPPORTED above 6. */
     uint32_t dcf_bits;
     /* Layout of the lookup keys' correction words (this library's choice; the
      * outputs do not depend on it).  0: rows, one array per (level, child)
@@ -383,7 +383,7 @@ int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 /* Compile `desc` with the DCF arity and lookup-key layout that measure
  * fastest for calls of n elements (both are free choices: every one computes
  * the same outputs, Def. "operator specification" in Sec. 4.1 fixes none).
- * With desc->dcf_bits = 0 the spec is compiled at r = 1 to 5 input bits
+ * With desc->dcf_bits = 0 the spec is compiled at r = 1 to 6 input bits
  * per tree level, each in both lookup-key layouts (one, when the spec has no
  * lookup or p is not 3 or 4), and each is tuned with ffss_autotune (same samples and cost);
  * with desc->dcf_bits set only that r is (in both layouts).  The one kept has the least

@@ -186,7 +186,7 @@ class Spec:
         trunc_s > 0: output 0 gains the shift of the k-bit view by trunc_s
         (arithmetic when trunc_signed).
         dcf_r: input bits per tree level of the gate's DCF keys (arity
-        2^dcf_r, 1..5)."""
+        2^dcf_r, 1..6)."""
         self.buf = np.zeros(lib().or_spec_size(), np.uint8)
         alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64))
         coeff = np.ascontiguousarray(np.asarray(coeff, dtype=np.uint64).reshape(-1))
@@ -224,7 +224,7 @@ class Spec:
         if rc != 0:
             raise ValueError("oracle rejected the operator specification")
         if lib().or_spec_set_dcf_r(self.ptr, dcf_r) != 0:
-            raise ValueError(f"DCF arity 2^{dcf_r} outside 2..32")
+            raise ValueError(f"DCF arity 2^{dcf_r} outside 2..64")
         self.dcf_r = dcf_r
         sh = np.zeros(6, np.uint32)
         lib().or_spec_shape(self.ptr, _p(sh, u32p))

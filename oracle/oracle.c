@@ -207,8 +207,8 @@ void or_mmo(const uint8_t s[16], uint32_t j, uint8_t out[16]) { mmo(s, j, out); 
 #define MAXK 63     /* view width k <= 63 */
 #define MAXKL 32    /* view width of a spec with an interval lookup */
 #define MAXP 4      /* payload length p = r (d + 1) <= 4 */
-#define MAXR 5      /* DCF input bits per tree level: arity 2^r <= 32 */
-#define MAXC 32     /* children per level */
+#define MAXR 6      /* DCF input bits per tree level: arity 2^r <= 64 */
+#define MAXC 64     /* children per level */
 #define MAXLV 63    /* tree levels (r = 1, k = 63) */
 
 static int nblocks_for(int p) { return (8 * p + 15) / 16; }   /* V = ceil(8p/16) */

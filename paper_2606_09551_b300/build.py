@@ -30,7 +30,7 @@ def _sources():
 def _hash() -> str:
     h = hashlib.sha256()
     for f in _sources():
-        h.update(f.encode())
+        h.update(os.path.relpath(f, ROOT).encode())   # the same hash wherever the tree is copied
         with open(f, "rb") as fh:
             h.update(fh.read())
     h.update(" ".join(NVCC_FLAGS).encode())

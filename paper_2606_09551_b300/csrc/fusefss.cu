@@ -285,7 +285,7 @@ extern "C" int ffss_spec_compile(ffss_ctx *ctx, const ffss_spec_desc *d, ffss_sp
   memset(&S, 0, sizeof(S));
   S.k = d->k; S.m = d->m; S.d = d->degree; S.r = d->n_out; S.p = p;
   S.V = (p + 1) / 2;
-  if (d->dcf_bits > 5) return fail(FFSS_ERR_UNSUPPORTED, "dcf_bits=%u outside 1..5", d->dcf_bits);
+  if (d->dcf_bits > 6) return fail(FFSS_ERR_UNSUPPORTED, "dcf_bits=%u outside 1..6", d->dcf_bits);
   S.dcf_r = d->dcf_bits ? d->dcf_bits : 2;
   if (d->lookup_records > 1) return fail(FFSS_ERR_INVALID, "lookup_records=%u must be 0 or 1", d->lookup_records);
   S.M = d->m == 1 ? 1 : d->m + 1;
@@ -1298,7 +1298,7 @@ extern "C" int ffss_spec_compile_best(ffss_ctx *ctx, const ffss_spec_desc *desc,
   double best_us = -1;
   uint32_t best_r = 0;
   int last_rc = FFSS_OK;
-  const uint32_t r0 = desc->dcf_bits ? desc->dcf_bits : 1, r1 = desc->dcf_bits ? desc->dcf_bits : 5;
+  const uint32_t r0 = desc->dcf_bits ? desc->dcf_bits : 1, r1 = desc->dcf_bits ? desc->dcf_bits : 6;
   // the lookup-key layouts: records exist for p = 3 and 4 lookups only
   const uint32_t pp = desc->n_out * (desc->degree + 1);
   const uint32_t layouts = (desc->m > 1 && (pp == 3 || pp == 4)) ? 2 : 1;

@@ -46,7 +46,7 @@ constexpr uint32_t kDrawKeep = 0x100000u;
 // query list of App. F step (4) in its fixed descriptor order.
 struct DevSpec {
   uint32_t k, m, d, r, p, M, T, n_bool, n_prim, V;   // V = ceil(8p / 16) AES blocks of payload
-  uint32_t dcf_r;              // DCF input bits per tree level: arity 2^dcf_r (1..5)
+  uint32_t dcf_r;              // DCF input bits per tree level: arity 2^dcf_r (1..6)
   uint32_t lookup_rec;         // lookup-key layout: 0 rows, 1 per-child records
   uint32_t q_f[kMaxT];         // query view width
   int32_t q_prim[kMaxT];       // -1: the 1[view < r_f] atom; else the predicate it thresholds

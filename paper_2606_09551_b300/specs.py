@@ -80,7 +80,7 @@ class OperatorSpec:
     # shift of its k-bit two's-complement value when trunc_signed (0 = none)
     trunc_shift: int = 0
     trunc_signed: bool = False
-    # DCF input bits per tree level of the gate's keys (arity 2^dcf_bits, 1..5):
+    # DCF input bits per tree level of the gate's keys (arity 2^dcf_bits, 1..6):
     # a protocol parameter, not part of the function; fewer levels mean fewer
     # online AES blocks but larger keys and more dealer work
     dcf_bits: int = 2

@@ -160,7 +160,7 @@ def test_invalid_specs_rejected(bad):
     elif bad == "trunc_signed":
         sp.trunc_shift, sp.trunc_signed = 3, 2
     elif bad == "dcf_bits":
-        sp.dcf_bits = 6
+        sp.dcf_bits = 7
     with pytest.raises(F.FfssError):
         F.CompiledSpec(sp)
 

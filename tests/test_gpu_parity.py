@@ -99,12 +99,15 @@ def _specs():
                                   S.PredDesc(37, 999, 5 << 30, 1)])]
     # DCF keys of arity 8 (three input bits per level; one- and two-bit first
     # digits at k = 16, 20, 32), arity 2 (one bit per level), arity 16
-    # (four bits; a three-bit first digit at k = 63) and arity 32
+    # (four bits; a three-bit first digit at k = 63), arity 32 and arity 64
+    # (six bits; first digits of 4 bits at k = 16, 6 at k = 24, 3 at k = 63)
     arity = [S.gelu4().arity(3), out[4].arity(3), S.nexp16().arity(3), pw[1].arity(3), bx[2].arity(3),
              out[8].arity(3), tr[0].arity(3), wide[0].arity(3), wide[3].arity(3), S.gelu8().variant(True).arity(3),
              out[3].arity(1), tr[1].arity(1), S.relu(5).arity(1),
              S.gelu4().arity(4), S.nexp16().arity(4), pw[1].arity(4), tr[0].arity(4), wide[0].arity(4),
-             S.nexp16().arity(5), S.gelu4().arity(5), tr[0].arity(5), wide[3].arity(5)]
+             S.nexp16().arity(5), S.gelu4().arity(5), tr[0].arity(5), wide[3].arity(5),
+             S.nexp16().arity(6), S.gelu8().arity(6), S.gelu4().arity(6), pw[1].arity(6), tr[0].arity(6),
+             wide[0].arity(6)]
     return out + pw + bx + tr + wide + arity
 
 

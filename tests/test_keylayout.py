@@ -16,7 +16,7 @@ SPECS = [S.gelu4(), S.gelu8(), S.nexp16(), S.trunc(32, 12, True), S.relu(5),
 
 
 @pytest.mark.parametrize("records", [False, True])
-@pytest.mark.parametrize("dcf_bits", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dcf_bits", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("sp", SPECS, ids=[s.name for s in SPECS])
 def test_layout_round_trip_and_size(sp, dcf_bits, records):
     sp = sp.arity(dcf_bits)

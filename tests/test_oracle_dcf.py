@@ -1,15 +1,15 @@
 """Pins for the oracle's DCF (a generalisation of Boyle et al., EUROCRYPT
 2021, to arity 2^r: r input bits per tree level) by brute force:
 Eval_0 (+) Eval_1 = beta * 1[u < alpha] for every alpha and every u at small
-k, for r = 1 to 5 (every arity the gates take), including k not a
-multiple of r."""
+k, for r = 1 to 6 (every arity the gates take), including k not a
+multiple of r, and over two and three levels at arities 32 and 64."""
 import numpy as np
 import pytest
 
 import oracle as O
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_bit_dcf_all_alpha_all_u(k, r):
     rng = np.random.default_rng(100 + k + 10 * r)
@@ -28,7 +28,7 @@ def test_bit_dcf_k10_sampled_alpha_all_u():
             assert O.dcf_eval(0, a, u, 0) ^ O.dcf_eval(1, b, u, 0) == (1 if u < alpha else 0)
 
 
-@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("k,p", [(1, 1), (3, 2), (5, 3), (5, 4), (6, 1)])
 def test_vector_dcf_all_alpha_all_u(k, p, r):
     rng = np.random.default_rng(200 + 10 * k + p + 100 * r)
@@ -39,6 +39,29 @@ def test_vector_dcf_all_alpha_all_u(k, p, r):
             got = O.dcf_eval(0, a, u, p) + O.dcf_eval(1, b, u, p)
             want = beta if u < alpha else np.zeros(p, np.uint64)
             assert (got == want).all()
+
+
+@pytest.mark.parametrize("r,k", [(5, 11), (6, 7), (6, 8), (6, 13)])
+@pytest.mark.parametrize("p", [0, 4])
+def test_dcf_wide_arity_every_u(r, k, p):
+    """Arities 32 and 64 over two or three levels (a first digit of 1 to 3
+    bits): every u, for alpha at 0, 1, the top, each side of a digit
+    boundary and at random."""
+    rng = np.random.default_rng(500 + 10 * r + k + p)
+    top = 2 ** k
+    alphas = {0, 1, top - 1, top // 2, 2 ** r - 1, 2 ** r, 2 ** r + 1, 3 * 2 ** r}
+    alphas |= {int(v) for v in rng.integers(0, top, 3)}
+    u = np.arange(top)
+    for alpha in sorted(a for a in alphas if a < top):
+        beta = rng.integers(0, 2 ** 64, size=p, dtype=np.uint64) if p else None
+        a, b = O.dcf_gen(k, alpha, p, beta, rng.bytes(16), rng.bytes(16), r=r)
+        if p == 0:
+            got = np.array([O.dcf_eval(0, a, int(x), 0) ^ O.dcf_eval(1, b, int(x), 0) for x in u])
+            assert np.array_equal(got, (u < alpha).astype(got.dtype)), alpha
+        else:
+            for x in u:
+                got = O.dcf_eval(0, a, int(x), p) + O.dcf_eval(1, b, int(x), p)
+                assert (got == (beta if x < alpha else np.zeros(p, np.uint64))).all(), (alpha, x)
 
 
 def test_path_child_randomness_hides_alpha():

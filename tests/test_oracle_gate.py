@@ -90,7 +90,7 @@ def test_plain_evaluator_matches_independent_python():
         assert (y == yp).all() and (z == zp).all()
 
 
-@pytest.mark.parametrize("dcf_bits", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dcf_bits", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_gate_every_mask_every_input(k, dcf_bits):
     """Reconstruction equals F(x) for all x and all masks r (Lemma 'compiler
@@ -364,7 +364,7 @@ def test_piecewise_relu_sign_select():
     assert np.array_equal(z & 1, (xs < 0).astype(np.uint32))
 
 
-@pytest.mark.parametrize("dcf_bits", [2, 3, 4, 5])
+@pytest.mark.parametrize("dcf_bits", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("k", [2, 3, 5, 7])
 def test_truncation_every_shift_every_mask_every_input(k, dcf_bits):
     """Shift gate (Def. "specification-compatible scalar gate" with the
@@ -425,7 +425,7 @@ def test_truncation_with_polynomial_and_boolean_outputs(k):
         assert (res["comm"] == xs.size * (8 + 16 * mults + 8 * -(-len(sp.piecewise) * sp.m // 32) + 1)).all()
 
 
-@pytest.mark.parametrize("dcf_bits", [2, 3, 4, 5])
+@pytest.mark.parametrize("dcf_bits", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("k,s", [(40, 20), (63, 49), (63, 1), (48, 47)])
 def test_truncation_wide_views(k, s, dcf_bits):
     """Shift gates on views wider than 32 bits (single-interval specs may use
