@@ -30,9 +30,9 @@ PER_OP = 1_000_000
 HEAD = 64
 GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "share_digests")
 
-# workload name -> (builder, every element?); the _a8, _a16 and _a32
-# workloads are the same calls with DCF keys of arity 8, 16 and 32 (the
-# plain and batched forms measure those fastest)
+# workload name -> (builder, every element?); the _a8 to _a64 workloads are
+# the same calls with DCF keys of arity 8 to 64 (the plain and batched forms
+# measure those fastest)
 WORKLOADS = {
     "gelu4": (lambda: [I.Request(0, 0.0, 0, I.single_gelu4())], True),
     "bert_layer": (lambda: [I.Request(128, 0.0, 0, I.bert_layer())], True),
@@ -42,6 +42,8 @@ WORKLOADS = {
     "bert_layer_a16": (lambda: [I.Request(128, 0.0, 0, I.with_arity(I.bert_layer(), 4))], True),
     "gelu4_a32": (lambda: [I.Request(0, 0.0, 0, I.with_arity(I.single_gelu4(), 5))], True),
     "bert_layer_a32": (lambda: [I.Request(128, 0.0, 0, I.with_arity(I.bert_layer(), 5))], True),
+    "gelu4_a64": (lambda: [I.Request(0, 0.0, 0, I.with_arity(I.single_gelu4(), 6))], True),
+    "bert_layer_a64": (lambda: [I.Request(128, 0.0, 0, I.with_arity(I.bert_layer(), 6))], True),
     "gpt2_batch": (I.gpt2_batch, False),
     "bert_large_trace": (I.bert_large_trace, False),
     "large_layer": (I.large_layer, False),

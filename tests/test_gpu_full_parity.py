@@ -3,7 +3,7 @@
 Every workload runs on the GPU at its full size, in the form the benchmark
 times: the single GeLU-4 operator and the BERT-base layer as plain
 per-operator launches (and once more as one batched launch), with DCF keys
-of arity 4, 8, 16 and 32 (the plain form measures 32 fastest), the
+of arity 4 to 64 (the plain form measures 32 and 64 fastest), the
 GPT-2 batch, the BERT-large trace and the 2.7B-scale layer through the
 continuous-batching server with on-device key streaming (64 GB pool, 4 M
 element chunks), all with autotuned work splits.  The GPU shares of every
@@ -262,6 +262,30 @@ def test_bert_layer_arity32_every_element_plain_and_batched(ctx, records):
     checked = _check("bert_layer_a32", reqs, _plain(ctx, reqs, css))
     assert sum(checked.values()) == 591488
     _check("bert_layer_a32", reqs, _batched(ctx, reqs, css))
+
+
+@pytest.mark.parametrize("records", [False, True])
+def test_single_gelu4_arity64_every_element(ctx, records):
+    """Arity 64 (six input bits per level: a four-bit first digit, then
+    two six-bit levels), plain and batched, every element."""
+    reqs = D.build("gelu4_a64")
+    css = _compile(ctx, reqs, records)
+    assert all(cs.spec.dcf_bits == 6 for cs in css.values())
+    checked = _check("gelu4_a64", reqs, _plain(ctx, reqs, css))
+    assert checked["gelu4"] == 65536
+    _check("gelu4_a64", reqs, _batched(ctx, reqs, css))
+
+
+@pytest.mark.parametrize("records", [False, True])
+def test_bert_layer_arity64_every_element_plain_and_batched(ctx, records):
+    """Arity 64 in both lookup-key layouts (one key set of the layer is
+    182 GB in records): every element, plain and batched."""
+    reqs = D.build("bert_layer_a64")
+    css = _compile(ctx, reqs, records)
+    assert all(cs.spec.dcf_bits == 6 for cs in css.values())
+    checked = _check("bert_layer_a64", reqs, _plain(ctx, reqs, css))
+    assert sum(checked.values()) == 591488
+    _check("bert_layer_a64", reqs, _batched(ctx, reqs, css))
 
 
 def test_gpt2_batch_streamed(ctx):
