@@ -520,6 +520,7 @@ def run_ours(args, rank, world, local_rank):
                    "form": "one persistent work-queue launch per layer, CUDA graph replay"}
         bt.close()
 
+    ks = k0 = k1 = None                          # the loops' last references to a key set
     del sets
     torch.cuda.empty_cache()
 
