@@ -7,7 +7,9 @@ Elements with such masks were found by tests/golden/make_edge_masks.py (the
 dealer PRG is counter based, so element e of a call can be dealt alone:
 ffss_keygen_range on the GPU, the oracle dealer with e0 = e).  For each one
 the GPU keys must equal the oracle dealer's field by field and every share
-must equal the oracle's; reconstructions must equal the plaintext spec."""
+must equal the oracle's; reconstructions must equal the plaintext spec.
+Each check runs with the default DCF keys (arity 4, rows) and with the
+layer's plain-form keys (arity 64, record-layout lookup keys)."""
 import numpy as np
 import pytest
 
@@ -19,6 +21,15 @@ from paper_2606_09551_b300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 SPECS = EC.edge_specs()
+# DCF arity and lookup-key layout: the default (arity 4, rows) and the plain
+# form's choice on the BERT-base layer (arity 64, records where p = 3, 4)
+LAYOUTS = {"a4": (2, False), "a64": (6, True)}
+
+
+def _at(sp, layout):
+    """The spec at a layout's arity, and whether its lookup keys are records."""
+    bits, rec = LAYOUTS[layout]
+    return sp.arity(bits), rec and sp.m > 1 and sp.p in (3, 4)
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +65,17 @@ def _oracle(osp, call_id, e0, x):
     return (k0, k1), O.eval_pair(osp, k0, k1, x0, x1)
 
 
+@pytest.mark.parametrize("layout", list(LAYOUTS))
 @pytest.mark.parametrize("name", list(SPECS))
-def test_edge_masks(ctx, name):
-    sp = SPECS[name]
+def test_edge_masks(ctx, name, layout):
+    """(The masks are drawn apart from the DCF keys, so each hit holds at
+    every arity.)"""
+    sp, records = _at(SPECS[name], layout)
     edge = EC.load()
     rec = edge["specs"][name]
     assert not rec["missing"], rec["missing"]
     call = edge["call_id"]
-    cs = F.CompiledSpec(sp, ctx)
+    cs = F.CompiledSpec(sp, ctx, records=records)
     osp = O.Spec(**sp.descriptor())
     hits = rec["hits"]
     xs = EC.edge_inputs(sp, [h[1] for h in hits], range(len(hits)), 4000)
@@ -71,8 +85,8 @@ def test_edge_masks(ctx, name):
         kb, g = _gpu(ctx, cs, sp, call, e, xa)
         (ok0, ok1), o = _oracle(osp, call, e, xa)
         assert int(ok0.fields(osp, 0)["r_share"] + ok1.fields(osp, 0)["r_share"]) % (1 << sp.k) == rk
-        assert fields_equal(gpu_fields(kb[0], osp, 1, 0), oracle_fields(ok0, osp, 0)), (e, tag)
-        assert fields_equal(gpu_fields(kb[1], osp, 1, 0), oracle_fields(ok1, osp, 0)), (e, tag)
+        assert fields_equal(gpu_fields(kb[0], osp, 1, 0, records), oracle_fields(ok0, osp, 0)), (e, tag)
+        assert fields_equal(gpu_fields(kb[1], osp, 1, 0, records), oracle_fields(ok1, osp, 0)), (e, tag)
         for key in ("y0", "y1", "z0", "z1"):
             assert np.array_equal(g[key], o[key]), (e, tag, key)
         yp, zp = osp.plain_eval(xa)
@@ -81,13 +95,14 @@ def test_edge_masks(ctx, name):
     assert tags == set(EC.edge_values(sp).values())
 
 
+@pytest.mark.parametrize("layout", list(LAYOUTS))
 @pytest.mark.parametrize("name", list(SPECS))
-def test_boundary_inputs_random_masks(ctx, name):
+def test_boundary_inputs_random_masks(ctx, name, layout):
     """Every boundary input target on ordinary masks: elements [0, n) of a
     call, x chosen from each element's own mask (read from the oracle's
     dealer) so that x and x^ sit on or beside every boundary."""
-    sp = SPECS[name]
-    cs = F.CompiledSpec(sp, ctx)
+    sp, records = _at(SPECS[name], layout)
+    cs = F.CompiledSpec(sp, ctx, records=records)
     osp = O.Spec(**sp.descriptor())
     call = 0xED6F
     n = 4 * len(EC.input_targets(sp, 0))
@@ -97,8 +112,8 @@ def test_boundary_inputs_random_masks(ctx, name):
     kb, g = _gpu(ctx, cs, sp, call, 0, x)
     (ok0, ok1), o = _oracle(osp, call, 0, x)
     for e in (0, n // 2, n - 1):
-        assert fields_equal(gpu_fields(kb[0], osp, n, e), oracle_fields(ok0, osp, e)), e
-        assert fields_equal(gpu_fields(kb[1], osp, n, e), oracle_fields(ok1, osp, e)), e
+        assert fields_equal(gpu_fields(kb[0], osp, n, e, records), oracle_fields(ok0, osp, e)), e
+        assert fields_equal(gpu_fields(kb[1], osp, n, e, records), oracle_fields(ok1, osp, e)), e
     for key in ("y0", "y1", "z0", "z1"):
         assert np.array_equal(g[key], o[key]), key
     yp, zp = osp.plain_eval(x)
