@@ -53,8 +53,9 @@ def _measured_peaks():
 
 HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # gate_kernel DRAM bytes (read + write) per element by spec, from ncu
-# captures of 65,536-element launches (profiles/gate_kernel_<spec>_65536.md);
-# retaken whenever the kernel changes
+# captures of small launches of the same spec and layout
+# (profiles/gate_kernel_nexp16_gelu8_a64.md); retaken whenever the kernel
+# changes
 # The AES form of every walk, per spec: the measured forms are the T-table
 # addressing variants and the bitsliced code (roofline.aes_microkernel_blocks_per_s);
 # the interleaved T-table form is the fastest on every pipe, and the bitsliced
@@ -62,12 +63,11 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 # block per tree level.
 AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates measured in this run",
             "alternatives": ["t_table_shift_mask", "t_table_permute_mad", "bitsliced_lop3 (not a walk form)"]}
-# spec -> (DRAM bytes read + written per element, elements of the ncu capture)
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16": ((6.258327e9 + 8.77056e6) / 65536, 65536),
-                            "nexp16_a8": ((2.545450e9 + 5.157376e6) / 24576, 24576),
-                            "nexp16_a8_rec": ((1.458830e9 + 5.251840e6) / 24576, 24576),
-                            "nexp16_a16_rec": ((835.614208e6 + 4.251136e6) / 16384, 16384),
-                            "nexp16_a32_rec": ((370.123264e6 + 3.480832e6) / 8192, 8192)}
+# spec -> (DRAM bytes read + written per element, elements of the ncu capture),
+# for the kernel as it stands (walks with L2 prefetch); a spec without a
+# capture of this kernel reports traffic null
+GATE_DRAM_BYTES_PER_ELEM = {"nexp16_a32_rec": ((381.796864e6 + 3.750656e6) / 8192, 8192),
+                            "nexp16_a64_rec": ((321.164032e6 + 3.726080e6) / 8192, 8192)}
 
 
 def parse():
@@ -101,6 +101,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-work budget per op sample")
     ap.add_argument("--elements", type=int, default=0,
                     help="elements of the exp_small / gelu_small profiling workloads (default 65536)")
+    ap.add_argument("--tuning-from", default="",
+                    help="replay the DCF arity, key layout and tuning record of each operator from the JSON "
+                         "line of an earlier run of the same workload (for a run under a profiler, whose "
+                         "serialised launches distort the tuner's timings)")
     ap.add_argument("--records", action="store_true",
                     help="with --dcf-bits N: lay the lookup keys out as per-child records")
     ap.add_argument("--dcf-bits", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
@@ -331,14 +335,18 @@ def run_ours(args, rank, world, local_rank):
     # the DCF arity per spec (resident keys: form 0), then the measured launch
     # shape, before any timing: the library times the gate under every work
     # split (and, with --dcf-bits 0, every arity) on throw-away samples
-    css = compile_specs(ctx, calls, args, form=0)
+    replay = load_tuning(args.tuning_from) if args.tuning_from else None
+    css = compile_specs(ctx, calls, args, form=0, replay=replay)
     tuning = None
     if not args.no_autotune:
         tuning = {}
         for c in calls:
             cs = css[c.name]
             t0 = time.perf_counter()
-            tune = cs.autotune()
+            if replay and c.name in replay:
+                tune = {k: replay[c.name][k] for k in ("slots", "tile_us", "fixed_us", "sample_elems", "dealer_ms")}
+            else:
+                tune = cs.autotune()
             tuning[c.name] = dict(tune, elements=c.n, slots_tuned=cs.gate_slots(c.n), tune_s=time.perf_counter() - t0,
                                   aes_form=AES_FORM, dcf_bits=cs.spec.dcf_bits, lookup_records=cs.records,
                                   dcf_bits_chosen_by=cs.arity_choice)
@@ -620,11 +628,9 @@ def run_ours(args, rank, world, local_rank):
         "aes_blocks_per_s": aes_launch / dom_s,
         "aes_microkernel_blocks_per_s": aes_rates,
         "lop3_peak_gops_measured": lop3_rate / 1e9,
+        # the key bytes the launch holds; a walk reads one child's correction
+        # words of each level's 2^r, so DRAM moves far fewer (traffic, below)
         "key_bytes_per_launch": key_bytes_launch,
-        # every key byte over the launch time (an upper bound: a walk reads one
-        # child's correction words of the level's 2^r, and DRAM serves the
-        # sectors that hold them; the measured traffic is below)
-        "hbm_gbs_achieved": key_bytes_launch / dom_s / 1e9,
         "traffic": None,
     }
     # AES roofline: per SM a T-table block needs ALU_OPS_PER_AES integer-ALU
@@ -646,7 +652,6 @@ def run_ours(args, rank, world, local_rank):
                                  ALU_OPS_PER_AES,
                         "bitsliced_measured": aes_rates["bitsliced_lop3"] / 1e9,
                         "frac_of_bitsliced": roof["achieved"] / (aes_rates["bitsliced_lop3"] / 1e9)}
-    roof["hbm_frac_of_measured"] = roof["hbm_gbs_achieved"] / HBM_GBS
     roof["hbm_peak_gbs"] = HBM_GBS
     roof["hbm_peak_basis"] = PEAKS_BASIS
     # DRAM traffic of this kernel per element, from an ncu capture of a
@@ -710,18 +715,31 @@ def _stream_aes(pending_ops, nlay):
     return deal, online
 
 
-def compile_specs(ctx, calls, args, form, n_of=None):
+def load_tuning(path):
+    """The per-operator autotune records of an earlier bench JSON line."""
+    with open(path) as fh:
+        line = [ln for ln in fh if ln.lstrip().startswith("{")][-1]
+    return json.loads(line)["autotune"]
+
+
+def compile_specs(ctx, calls, args, form, n_of=None, replay=None):
     """One compiled spec per call.  With --dcf-bits 0 (and tuning on) the
     library compiles each at DCF arities 2 to 64, tunes each and keeps the
     one with the least predicted time for the call's size (form 0: resident
     keys; form 1: keys dealt as they are used, so the dealer's time counts);
     every call's spec is replaced by the kept one.  Otherwise the given (or
-    forced) arity, tuned unless --no-autotune."""
+    forced) arity, tuned unless --no-autotune.  replay: saved records by call
+    name (load_tuning), installed instead of measuring."""
     from paper_2606_09551_b300 import fusefss as F
     css = {}
     for c in calls:
         n = n_of(c) if n_of else c.n
-        if args.dcf_bits == 0 and not args.no_autotune:
+        if replay and c.name in replay:
+            rec = replay[c.name]
+            cs = F.CompiledSpec(c.spec.arity(rec["dcf_bits"]), ctx, records=bool(rec["lookup_records"]))
+            cs.set_tune(rec)
+            cs.arity_choice = "replayed (%s)" % rec.get("dcf_bits_chosen_by", "saved")
+        elif args.dcf_bits == 0 and not args.no_autotune:
             cs = F.CompiledSpec(c.spec, ctx, best_for=(n, form))
             cs.arity_choice = "measured, form %d at %d elements" % (form, n)
         else:

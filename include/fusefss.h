@@ -380,6 +380,19 @@ typedef struct {
  * not run concurrently with another host thread's call on the same spec. */
 int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, void *stream);
 
+/* Install a tuning record that ffss_autotune wrote earlier (for this spec
+ * descriptor, on the same GPU model), as if the tuner had just measured it:
+ * a saved tuning replays the same work splits without timing anything, for
+ * example in a process run under a profiler, whose serialised launches
+ * would distort the tuner's timings.  Host-only: no device work, no stream.
+ * The record is checked, not trusted: n_tried 1..6, slots strictly
+ * increasing powers of two, each at most 32 and (but the first) at most the
+ * spec's walks per element, every tile_us positive and finite, every
+ * fixed_us non-negative and finite.  Results never depend on the split.
+ * Errors: FFSS_ERR_INVALID (NULL argument, a record that fails a check; the
+ * spec keeps its previous model).  Same threading rule as ffss_autotune. */
+int ffss_spec_set_tune(ffss_spec *spec, const ffss_tune *tune);
+
 /* Compile `desc` with the DCF arity and lookup-key layout that measure
  * fastest for calls of n elements (both are free choices: every one computes
  * the same outputs, Def. "operator specification" in Sec. 4.1 fixes none).

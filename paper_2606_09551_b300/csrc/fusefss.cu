@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstddef>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -1270,6 +1271,26 @@ extern "C" int ffss_autotune(ffss_ctx *ctx, ffss_spec *spec, ffss_tune *out, voi
   spec->tune = t;
   spec->tuned = true;
   if (out) *out = t;
+  return FFSS_OK;
+}
+
+extern "C" int ffss_spec_set_tune(ffss_spec *spec, const ffss_tune *t) {
+  if (!spec || !t) return fail(FFSS_ERR_INVALID, "ffss_spec_set_tune: NULL argument");
+  const DevSpec &S = spec->host;
+  const uint32_t nitems = S.T + (S.M > 1 ? S.M - 1 : 0);
+  if (t->n_tried < 1 || t->n_tried > 6)
+    return fail(FFSS_ERR_INVALID, "ffss_spec_set_tune: n_tried=%u outside 1..6", t->n_tried);
+  for (uint32_t i = 0; i < t->n_tried; ++i) {
+    const uint32_t s = t->slots[i];
+    if (s == 0 || (s & (s - 1)) || s > kMaxSlots || (i > 0 && (s <= t->slots[i - 1] || s > nitems)))
+      return fail(FFSS_ERR_INVALID, "ffss_spec_set_tune: slots[%u]=%u is not a valid split for this spec", i, s);
+    if (!(t->tile_us[i] > 0) || !std::isfinite(t->tile_us[i]) || !(t->fixed_us[i] >= 0) ||
+        !std::isfinite(t->fixed_us[i]))
+      return fail(FFSS_ERR_INVALID, "ffss_spec_set_tune: split %u has tile_us=%g fixed_us=%g", i, t->tile_us[i],
+                  t->fixed_us[i]);
+  }
+  spec->tune = *t;
+  spec->tuned = true;
   return FFSS_OK;
 }
 

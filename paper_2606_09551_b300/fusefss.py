@@ -151,6 +151,7 @@ def lib():
         L.ffss_reconstruct.argtypes = [vp, vp, vp, vp, C.c_uint64, C.c_uint32, vp, vp, vp]
         L.ffss_ctx_set_slots.argtypes = [vp, C.c_uint32]
         L.ffss_autotune.argtypes = [vp, vp, C.POINTER(Tune), vp]
+        L.ffss_spec_set_tune.argtypes = [vp, C.POINTER(Tune)]
         L.ffss_spec_compile_best.argtypes = [vp, C.POINTER(SpecDesc), C.c_uint64, C.c_uint32, vp, C.POINTER(vp),
                                              C.POINTER(C.c_uint32)]
         L.ffss_gate_slots.argtypes = [vp, vp, C.c_uint64, C.POINTER(C.c_uint32)]
@@ -306,6 +307,18 @@ class CompiledSpec:
         t = Tune()
         _check(lib().ffss_autotune(self.ctx.h, self.h, C.byref(t), _stream(stream)))
         return t.as_dict()
+
+    def set_tune(self, rec: dict):
+        """Install a tuning record autotune() returned earlier (its slots,
+        tile_us and fixed_us lists; sample_elems and dealer_ms if present)."""
+        t = Tune()
+        n = len(rec["slots"])
+        t.n_tried = n
+        for i in range(min(n, 6)):
+            t.slots[i], t.tile_us[i], t.fixed_us[i] = rec["slots"][i], rec["tile_us"][i], rec["fixed_us"][i]
+        t.sample_elems = int(rec.get("sample_elems", 0))
+        t.dealer_ms = float(rec.get("dealer_ms", 0.0))
+        _check(lib().ffss_spec_set_tune(self.h, C.byref(t)))
 
     def gate_slots(self, n: int) -> int:
         """Slots per element the fused gate uses for a call of n elements."""

@@ -51,6 +51,34 @@ def test_autotune_rejects_null_arguments(libpath):
     assert L.ffss_autotune(None, cs.h, None, None) == -1
 
 
+def test_set_tune_checks_the_record(libpath):
+    """ffss_spec_set_tune is host-only: a valid record is installed, each
+    kind of invalid one is refused with FFSS_ERR_INVALID."""
+    cs = F.CompiledSpec(S.nexp16())              # 16 + 15 walks per element
+    good = {"slots": [1, 2, 4, 8, 16, 32], "tile_us": [540.0, 275.0, 139.0, 72.0, 41.0, 27.0],
+            "fixed_us": [3.0, 2.0, 2.0, 1.0, 0.0, 0.0], "sample_elems": 75776, "dealer_ms": 30.0}
+    cs.set_tune(good)
+    bad = [dict(good, slots=[]), dict(good, slots=[1, 2, 4, 8, 16, 32, 64]),
+           dict(good, slots=[1, 2, 4, 8, 16, 16]), dict(good, slots=[1, 3, 4, 8, 16, 32]),
+           dict(good, slots=[1, 2, 4, 8, 16, 64]), dict(good, tile_us=[540.0, 0.0, 139.0, 72.0, 41.0, 27.0]),
+           dict(good, tile_us=[540.0, float("inf"), 139.0, 72.0, 41.0, 27.0]),
+           dict(good, fixed_us=[3.0, -1.0, 2.0, 1.0, 0.0, 0.0]),
+           dict(good, fixed_us=[3.0, float("nan"), 2.0, 1.0, 0.0, 0.0])]
+    for rec in bad:
+        n = len(rec["slots"])
+        rec = dict(rec, tile_us=(rec["tile_us"] * 2)[:max(n, 1)], fixed_us=(rec["fixed_us"] * 2)[:max(n, 1)])
+        with pytest.raises(F.FfssError) as ei:
+            cs.set_tune(rec)
+        assert ei.value.code == -1, rec
+    # a split above the spec's walks per element: GeLU-4 has 4 + 4 walks
+    g4 = F.CompiledSpec(S.gelu4())
+    for n in (6, 5):
+        with pytest.raises(F.FfssError):
+            g4.set_tune({k: (v[:n] if isinstance(v, list) else v) for k, v in good.items()})
+    g4.set_tune({k: (v[:4] if isinstance(v, list) else v) for k, v in good.items()})
+    assert F.lib().ffss_spec_set_tune(None, None) == -1
+
+
 def _shape_vs_oracle(sp, may_reject=False):
     try:
         o = O.Spec(**sp.descriptor())

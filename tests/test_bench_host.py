@@ -35,3 +35,26 @@ def test_network_projection_bert_layer():
     assert p["lan"]["t_proj_ms"] == pytest.approx(10.0 + 2e3 * b / 1e9 + 15 * 0.5)
     assert p["wan"]["t_proj_ms"] == pytest.approx(10.0 + 2e3 * b / 400e6 + 15 * 4.0)
     assert not bench.network_projection(calls, css, 10.0, [b * 3 + 1, b * 3], 3)["counted_bytes_match"]
+
+
+def test_tuning_replay_installs_saved_records(tmp_path):
+    """--tuning-from: the last JSON line's autotune records give each call
+    its saved arity and layout, and the saved model is installed (host-only
+    compile, so the arity and layout are checked on the compiled shape)."""
+    import json
+    rec = {"slots": [1, 2, 4], "tile_us": [200.0, 100.0, 60.0], "fixed_us": [2.0, 1.0, 1.0],
+           "sample_elems": 75776, "dealer_ms": 10.0, "dcf_bits": 6, "lookup_records": True,
+           "dcf_bits_chosen_by": "measured, form 0 at 393216 elements"}
+    path = tmp_path / "run.json"
+    path.write_text("log line\n" + json.dumps({"autotune": {"gelu": dict(rec, dcf_bits=3)}}) + "\n"
+                    + json.dumps({"autotune": {"gelu": rec}}) + "\n")
+    saved = bench.load_tuning(str(path))
+    assert saved["gelu"]["dcf_bits"] == 6
+
+    class Args:
+        dcf_bits, no_autotune, records = 0, False, False
+    calls = [c for c in I.bert_layer() if c.name == "gelu"]
+    css = bench.compile_specs(None, calls, Args(), form=0, replay=saved)
+    cs = css["gelu"]
+    assert cs.spec.dcf_bits == 6 and cs.records and cs.shape.dcf_bits == 6 and cs.shape.lookup_records == 1
+    assert cs.arity_choice.startswith("replayed")

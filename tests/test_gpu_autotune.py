@@ -133,6 +133,23 @@ def test_split_limits(ctx):
         bt.set_slots(0)
 
 
+def test_saved_tuning_replays_the_same_splits(ctx):
+    """A record ffss_autotune wrote, installed on a fresh compile of the same
+    spec with ffss_spec_set_tune, picks the same split at every size, and
+    the shares of the two compiles are equal."""
+    sp = S.nexp16().arity(6)
+    cs = F.CompiledSpec(sp, ctx, records=True)
+    rec = cs.autotune()
+    again = F.CompiledSpec(sp, ctx, records=True)
+    again.set_tune(rec)
+    for n in (1, 128, 1536, 4736, 37888, 196608, 393216):
+        assert again.gate_slots(n) == cs.gate_slots(n), n
+    x = I.uniform_x(3000, sp.k, 21)
+    a, b = _gate(ctx, cs, sp, x, 77), _gate(ctx, again, sp, x, 77)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
 def test_forced_split_overrides_tuning(ctx):
     cs = F.CompiledSpec(S.gelu8(), ctx)
     cs.autotune()
