@@ -279,7 +279,8 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t r, uint64_t u, 
   for (uint32_t i = 0; i < nlev; ++i, sh -= r) {
     const uint32_t c = uint32_t(u >> sh) & dmask;
     if (i + 1 < nlev) prefetch_l2(root + (1 + (uint64_t(i + 1) << r) + (uint32_t(u >> (sh - r)) & dmask)) * n);
-    const uint4 cw = root[(1 + (uint64_t(i) << r) + c) * n];
+    // the CW enters only when t = 1 (masked by t below), so only then is it read
+    const uint4 cw = t ? root[(1 + (uint64_t(i) << r) + c) * n] : make_uint4(0, 0, 0, 0);
     const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
     v ^= (blk.x >> 1) ^ (tm & (cw.x >> 1));
@@ -328,21 +329,27 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, 
 #pragma unroll
       for (int q = 0; q < P; ++q) prefetch_l2(leaf + uint64_t(q) * n);
     }
-    uint4 cw;
+    // the child's CWs enter only when t = 1 (masked by t below), so only
+    // then are they read
+    uint4 cw = make_uint4(0, 0, 0, 0);
     uint64_t vc[2 * V];
-    if constexpr (REC) {
-      const uint4 *rr = rec + row * rstride;
-      cw = rr[0];
 #pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const uint4 w = rr[1 + q];
-        vc[2 * q] = lo64(w);
-        vc[2 * q + 1] = hi64(w);
+    for (int q = 0; q < 2 * V; ++q) vc[q] = 0;
+    if (t) {
+      if constexpr (REC) {
+        const uint4 *rr = rec + row * rstride;
+        cw = rr[0];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const uint4 w = rr[1 + q];
+          vc[2 * q] = lo64(w);
+          vc[2 * q + 1] = hi64(w);
+        }
+      } else {
+        cw = root[(1 + row) * n];
+#pragma unroll
+        for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
       }
-    } else {
-      cw = root[(1 + row) * n];
-#pragma unroll
-      for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
     }
     const uint4 blk = mmo(s, c, aes);
     uint64_t conv[2 * V];
@@ -370,9 +377,12 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, 
     conv[2 * q] = lo64(cb);
     conv[2 * q + 1] = hi64(cb);
   }
-  const uint64_t tm64 = 0ull - uint64_t(t);
+  if (t) {
 #pragma unroll
-  for (int q = 0; q < P; ++q) acc[q] += conv[q] + (leaf[uint64_t(q) * n] & tm64);
+    for (int q = 0; q < P; ++q) acc[q] += leaf[uint64_t(q) * n];
+  }
+#pragma unroll
+  for (int q = 0; q < P; ++q) acc[q] += conv[q];
 }
 
 // ---------------------------------------------------------------------------
