@@ -64,10 +64,12 @@ HBM_GBS, SM_MAX_MHZ, PEAKS_BASIS = _measured_peaks()
 AES_FORM = {"walks": "t_table_interleaved", "chosen_by": "micro-kernel rates measured in this run",
             "alternatives": ["t_table_shift_mask", "t_table_permute_mad", "bitsliced_lop3 (not a walk form)"]}
 # spec -> (DRAM bytes read + written per element, elements of the ncu capture),
-# for the kernel as it stands (walks with L2 prefetch that read a level's
-# correction words only when the control bit is set); a spec without a
-# capture of this kernel reports traffic null
-GATE_DRAM_BYTES_PER_ELEM = {"nexp16_a64_rec": ((310.599680e6 + 3.703808e6) / 8192, 8192)}
+# for the kernel as it stands; a spec without a capture of this kernel
+# reports traffic null.  (The last capture, 38,367 B per nExp arity-64
+# element pair, was of the walks that branched around their predicated
+# correction-word loads; the branch-free form reads the same lines but has
+# not been captured.)
+GATE_DRAM_BYTES_PER_ELEM = {}
 
 
 def parse():

@@ -268,6 +268,32 @@ FFSS_CORE void prefetch_l2(const void *p) {
 #endif
 }
 
+// Loads that happen only when pred is nonzero (else zero), as predicated
+// instructions rather than a branch: a warp's lanes disagree on the control
+// bit, and a branch around the loads costs more instructions than it saves.
+FFSS_CORE uint4 load16_if(const uint4 *p, uint32_t pred) {
+#ifdef __CUDA_ARCH__
+  uint4 v = make_uint4(0, 0, 0, 0);
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t@q ld.global.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
+      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+      : "r"(pred), "l"(p));
+  return v;
+#else
+  return pred ? *p : make_uint4(0, 0, 0, 0);
+#endif
+}
+FFSS_CORE uint64_t load8_if(const uint64_t *p, uint32_t pred) {
+#ifdef __CUDA_ARCH__
+  uint64_t v = 0;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q ld.global.u64 %0, [%2];\n\t}"
+      : "+l"(v)
+      : "r"(pred), "l"(p));
+  return v;
+#else
+  return pred ? *p : 0;
+#endif
+}
+
 // Bit payload: returns the XOR share of 1[u < alpha].
 // root: uint4 root[n]; child CW of level i at root[(1 + A i + c) n]; leaf: the leaf CW bit.
 template <class AES>
@@ -280,7 +306,7 @@ FFSS_CORE uint32_t dcf_bit_eval(uint32_t b, uint32_t k, uint32_t r, uint64_t u, 
     const uint32_t c = uint32_t(u >> sh) & dmask;
     if (i + 1 < nlev) prefetch_l2(root + (1 + (uint64_t(i + 1) << r) + (uint32_t(u >> (sh - r)) & dmask)) * n);
     // the CW enters only when t = 1 (masked by t below), so only then is it read
-    const uint4 cw = t ? root[(1 + (uint64_t(i) << r) + c) * n] : make_uint4(0, 0, 0, 0);
+    const uint4 cw = load16_if(root + (1 + (uint64_t(i) << r) + c) * n, t);
     const uint4 blk = mmo(s, c, aes);
     const uint32_t tm = 0u - t;
     v ^= (blk.x >> 1) ^ (tm & (cw.x >> 1));
@@ -331,25 +357,21 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, 
     }
     // the child's CWs enter only when t = 1 (masked by t below), so only
     // then are they read
-    uint4 cw = make_uint4(0, 0, 0, 0);
+    uint4 cw;
     uint64_t vc[2 * V];
+    if constexpr (REC) {
+      const uint4 *rr = rec + row * rstride;
+      cw = load16_if(rr, t);
 #pragma unroll
-    for (int q = 0; q < 2 * V; ++q) vc[q] = 0;
-    if (t) {
-      if constexpr (REC) {
-        const uint4 *rr = rec + row * rstride;
-        cw = rr[0];
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-          const uint4 w = rr[1 + q];
-          vc[2 * q] = lo64(w);
-          vc[2 * q + 1] = hi64(w);
-        }
-      } else {
-        cw = root[(1 + row) * n];
-#pragma unroll
-        for (int q = 0; q < P; ++q) vc[q] = vcw[(row * P + q) * n];
+      for (int q = 0; q < V; ++q) {
+        const uint4 w = load16_if(rr + 1 + q, t);
+        vc[2 * q] = lo64(w);
+        vc[2 * q + 1] = hi64(w);
       }
+    } else {
+      cw = load16_if(root + (1 + row) * n, t);
+#pragma unroll
+      for (int q = 0; q < P; ++q) vc[q] = load8_if(vcw + (row * P + q) * n, t);
     }
     const uint4 blk = mmo(s, c, aes);
     uint64_t conv[2 * V];
@@ -377,12 +399,8 @@ FFSS_CORE void dcf_vec_eval_acc(uint32_t b, uint32_t k, uint32_t r, uint32_t u, 
     conv[2 * q] = lo64(cb);
     conv[2 * q + 1] = hi64(cb);
   }
-  if (t) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) acc[q] += leaf[uint64_t(q) * n];
-  }
-#pragma unroll
-  for (int q = 0; q < P; ++q) acc[q] += conv[q];
+  for (int q = 0; q < P; ++q) acc[q] += conv[q] + load8_if(leaf + uint64_t(q) * n, t);
 }
 
 // ---------------------------------------------------------------------------
