@@ -114,13 +114,15 @@ def test_gate_every_mask_every_input(k, dcf_bits):
         assert (res["comm"] == xs.size * (8 + 16 * d * sp.n_out)).all()
 
 
-def test_relu_worked_example_closed_form():
+@pytest.mark.parametrize("dcf_bits", [2, 6])
+def test_relu_worked_example_closed_form(dcf_bits):
     """App. N: y = max(x, 0) and z = MSB(x) on signed k-bit inputs, with the
-    stated compiled shapes."""
+    stated compiled shapes; with DCF keys of arity 4 and of arity 64 (three
+    levels at k = 16, the arity the plain form picks for the layer's gates)."""
     fx = dict(line.split() for line in open(golden("relu_worked_example.txt"))
               if line.strip() and not line.startswith("#"))
     k = 16
-    sp = S.relu(k)
+    sp = S.relu(k).arity(dcf_bits)
     rng = np.random.default_rng(5)
     xs_signed = np.concatenate([np.array([0, 1, -1, 2 ** 15 - 1, -(2 ** 15)], dtype=np.int64),
                                 rng.integers(-(2 ** 15), 2 ** 15, size=3000, dtype=np.int64)])
