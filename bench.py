@@ -1299,18 +1299,29 @@ def run_reference(args, world):
     from paper_2606_09551_b300 import inputs as I
     calls, config = workload(args.workload, args.elements)
     calls = reference_calls(calls, args)
+    from paper_2606_09551_b300 import fusefss as F
     threads = os.cpu_count() or 1
     step_s = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
-    # per-element oracle time estimate: 0.2 us per AES block per core, both parties
-    per_elem = {}
+    # per-element oracle time estimate: 0.2 us per AES block per core, both
+    # parties, at the keys' arity; the sample's keys stay in host memory, so
+    # they also get a budget: a quarter of the available memory, at most 32 GB
+    per_elem, key_elem = {}, {}
     ospec = {}
     for c in calls:
         o = O.Spec(**c.spec.descriptor())
         ospec[c.name] = o
-        per_elem[c.name] = 0.2e-6 * 2 * (sum(f for f, _, _ in o.queries())
-                                        + (o.M - 1) * (o.k * (1 + (o.p + 1) // 2) + (o.p + 1) // 2))
+        r = c.spec.dcf_bits
+        lv = lambda f: -(-f // r)
+        per_elem[c.name] = 0.2e-6 * 2 * (sum(lv(f) for f, _, _ in o.queries())
+                                        + (o.M - 1) * (lv(o.k) * (1 + (o.p + 1) // 2) + (o.p + 1) // 2))
+        key_elem[c.name] = 2 * F.CompiledSpec(c.spec).shape.key_bytes_per_elem
     est = sum(c.n * per_elem[c.name] for c in calls) / threads
-    frac = min(1.0, step_s / est)
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 16 << 30
+    mem_budget = min(avail / 4, 32e9)
+    frac = min(1.0, step_s / est, mem_budget / sum(c.n * key_elem[c.name] for c in calls))
     sample = {c.name: max(1, int(round(c.n * frac))) for c in calls}
     work = []
     for c in calls:
@@ -1344,7 +1355,9 @@ def run_reference(args, world):
     value = total / per_step_s
     ar = {c.name: 1 << c.spec.dcf_bits for c in calls}
     desc = ("oracle eval_pair (both parties) per step on %s elements (%.4f of each operator: %s), "
-            "%d threads" % (total, frac, ", ".join(f"{sample[k]} {k} (DCF arity {ar[k]})" for k in sample), threads))
+            "%d threads; the sample bounded by %.0f s of estimated work per step and %.1f GB of host "
+            "memory for its keys" % (total, frac, ", ".join(f"{sample[k]} {k} (DCF arity {ar[k]})" for k in sample),
+                                     threads, step_s, mem_budget / 1e9))
     return {
         "impl": "reference",
         "metric": "FSS-evaluated elements/s per nonlinear op (both parties, online phase)",
