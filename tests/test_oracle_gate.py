@@ -114,6 +114,28 @@ def test_gate_every_mask_every_input(k, dcf_bits):
         assert (res["comm"] == xs.size * (8 + 16 * d * sp.n_out)).all()
 
 
+@pytest.mark.parametrize("dcf_bits", [5, 6])
+def test_gate_every_mask_every_input_two_levels_wide_arity(dcf_bits):
+    """The whole gate at k = 7 with arity-32 and arity-64 keys, whose walks
+    take two levels (a first digit of 2 or 1 bits): reconstruction equals
+    F(x) for all x and all masks r, for a plain piecewise polynomial and for
+    one with a shift gate on its output."""
+    rng = np.random.default_rng(70 + dcf_bits)
+    k = 7
+    N = 2 ** k
+    xs = np.tile(np.arange(N, dtype=np.uint64), N) + (rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k))
+    rs = np.repeat(np.arange(N, dtype=np.uint64), N) + (rng.integers(0, 2 ** 40, size=N * N, dtype=np.uint64) << np.uint64(k))
+    for trial in range(2):
+        sp = S.random_spec(rng, k, int(rng.integers(5, 17)), int(rng.integers(1, 4)), 1, partition_bits=bool(trial),
+                           n_extra=2)
+        if trial:
+            sp.trunc_shift, sp.trunc_signed = 3, True
+        sp = sp.arity(dcf_bits)
+        o, res, y, z = run_gate(sp, xs, r_override=rs)
+        yp, zp = python_plain(sp, xs)
+        assert (y == yp).all() and (z == zp).all(), trial
+
+
 @pytest.mark.parametrize("dcf_bits", [2, 6])
 def test_relu_worked_example_closed_form(dcf_bits):
     """App. N: y = max(x, 0) and z = MSB(x) on signed k-bit inputs, with the
